@@ -1,0 +1,563 @@
+/*
+ * Plain, slow CPU oracle for the semi-coherent F-statistic of the hierarchical
+ * SmBBH search (Fu, Wang, Mohanty, arXiv:2407.10797).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no code, header, table or constant generator with
+ * the CUDA library: every formula below is written out again from the paper.
+ *
+ * Precision: FP64 throughout, except the template phase, which is evaluated in
+ * long double (the phase reaches 1e8 rad, where one FP64 ulp is 1e-8 rad).
+ * Compile with -ffp-contract=off so that the same source gives the same bits
+ * on x86-64 and aarch64.
+ *
+ * What each part follows:
+ *   inner product            Sec. II.A, Eq. (inner_product)
+ *   amplitude basis A^i      Sec. II.A, Eq. (response)
+ *   F = 1/2 N^T M^-1 N       Sec. II.A, Eqs. (coherent_F_stat), (aandMN)-(aandMN3)
+ *   segments, F-hat          Sec. II.B, Eq. (semi-cohF) and the segment inner product
+ *   segment outer edges      Sec. II.B, last paragraph before Fig. 1
+ *   waveform h(f), Psi(f)    Appendix A, Eqs. (A1)-(A3)
+ *   response x(f) = T(f)h(f) Sec. IV, Eq. (freDres) with N = 0 and no higher d(t) terms
+ *   t(f)                     Sec. IV, stationary-phase time t_f = (1/2pi) dPhi/df
+ *   PSO update               Sec. III.A, Eqs. (pso_position_update), (pso_velocity_update)
+ *   extrinsic parameters     Appendix B, Eqs. (B1)-(B3)
+ *
+ * Readings of points the paper leaves open (each also listed in the design doc):
+ *   - PN coefficients alpha_k: non-spinning TaylorF2 through 2PN (k <= 4).
+ *   - phi_e: leading-order e0^2 correction with e0 defined at f0 = 10 mHz.
+ *   - phi_p is carried by the F+/Fx basis (psi = 0); phi_D = 2 pi f R sin(theta)
+ *     cos(alpha(t_f) - phi); t(f) uses the orbital phase only.
+ *   - rigid equilateral constellation on a 1 AU circular guiding-centre orbit
+ *     (first-order-in-eccentricity orbits), long-wavelength Michelson X.
+ *   - constants -phi_c - pi/4 of Psi are carried by the amplitudes a_i.
+ *   - segment outer edges at the first/last bin whose t(f_k) lies in [0, T];
+ *     interior edges equal-width in frequency; a bin belongs to segment p iff
+ *     e_p <= f_k < e_{p+1} (last segment closed).
+ *   - a segment with fewer than 4 bins, or with M11 M22 - M12^2 <= 1e-12 M11 M22,
+ *     contributes F_p = 0.
+ *   - the library returns the SUM over segments; F-hat = sum / N_seg.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- constants (this file's own copy) ---------------------------------- */
+#define OR_MSUN_S 4.925490947e-6
+#define OR_YEAR_S 31557600.0
+#define OR_AU_S 499.004784
+#define OR_PI 3.14159265358979323846
+#define OR_PI_L 3.141592653589793238462643383279502884L
+#define OR_F0_ECC 0.01 /* Hz: e0 is the eccentricity at this GW frequency */
+
+typedef struct {
+    double Mc;  /* chirp mass, solar masses */
+    double tc;  /* coalescence time, s */
+    double lat; /* ecliptic latitude beta, rad (theta = pi/2 - beta) */
+    double lon; /* ecliptic longitude lambda = phi, rad */
+    double e0;  /* eccentricity at f0 = 10 mHz */
+    double q;   /* mass ratio m1/m2 >= 1 */
+} or_params;
+
+typedef struct {
+    double f_min, df, T_obs;
+    int64_t n;
+    int response; /* 0: LISA response; 1: F+ = 1, Fx = 0, no Doppler (test mode) */
+    int pn_order; /* highest k kept in sum_k alpha_k x^(k/2), 0..4 */
+    double alpha0; /* orbital phase of the guiding centre at t = 0, rad */
+    double orient; /* orientation of the constellation at t = 0, rad */
+} or_model;
+
+/* ---- masses and PN coefficients (Appendix A) --------------------------- */
+static double or_eta(double q) { return q / ((1.0 + q) * (1.0 + q)); }
+
+/* Non-spinning TaylorF2 coefficients alpha_k(eta), k = 0..4. */
+static void or_alpha(double eta, int order, double a[5]) {
+    a[0] = 1.0;
+    a[1] = 0.0;
+    a[2] = 3715.0 / 756.0 + 55.0 * eta / 9.0;
+    a[3] = -16.0 * OR_PI;
+    a[4] = 15293365.0 / 508032.0 + 27145.0 * eta / 504.0 + 3085.0 * eta * eta / 72.0;
+    for (int k = order + 1; k < 5; k++) a[k] = 0.0;
+}
+
+/* Stationary-phase time t(f) = t_c + (1/2pi) d/df [Psi_PN(f) + phi_e(f)]. */
+static double or_time(const or_params* P, const or_model* m, double f) {
+    double eta = or_eta(P->q);
+    double Mc = P->Mc * OR_MSUN_S;
+    double M = Mc * pow(eta, -0.6);
+    double a[5];
+    or_alpha(eta, m->pn_order, a);
+    double v = cbrt(OR_PI * M * f);
+    double lead = (3.0 / 128.0) * pow(OR_PI * Mc * f, -5.0 / 3.0);
+    /* d/df of lead * sum_k a_k v^k, with lead ~ f^-5/3 and v^k ~ f^(k/3) */
+    double s = 0.0, vk = 1.0;
+    for (int k = 0; k <= 4; k++) {
+        s += a[k] * ((double)(k - 5) / 3.0) * vk;
+        vk *= v;
+    }
+    double dpsi = lead * s / f;
+    double phie = -(2355.0 / 1462.0) * P->e0 * P->e0 * lead * pow(OR_F0_ECC / f, 19.0 / 9.0);
+    double dphie = -(34.0 / 9.0) * phie / f;
+    return P->tc + (dpsi + dphie) / (2.0 * OR_PI);
+}
+
+/* Orbital part of the phase in cycles, Psi_orb(f)/(2 pi) with
+ * Psi_orb = 2 pi f t_c + Psi_PN(f) + phi_e(f), in long double. */
+static long double or_phase_orb_cycles(const or_params* P, const or_model* m, long double f) {
+    long double eta = (long double)or_eta(P->q);
+    long double Mc = (long double)P->Mc * (long double)OR_MSUN_S;
+    long double M = Mc * powl(eta, -0.6L);
+    double ad[5];
+    or_alpha((double)eta, m->pn_order, ad);
+    long double a[5];
+    a[0] = 1.0L;
+    a[1] = 0.0L;
+    a[2] = 3715.0L / 756.0L + 55.0L * eta / 9.0L;
+    a[3] = -16.0L * OR_PI_L;
+    a[4] = 15293365.0L / 508032.0L + 27145.0L * eta / 504.0L + 3085.0L * eta * eta / 72.0L;
+    for (int k = m->pn_order + 1; k < 5; k++) a[k] = 0.0L;
+    (void)ad;
+    long double v = cbrtl(OR_PI_L * M * f);
+    long double lead = (3.0L / 128.0L) * powl(OR_PI_L * Mc * f, -5.0L / 3.0L);
+    long double s = 0.0L, vk = 1.0L;
+    for (int k = 0; k <= 4; k++) {
+        s += a[k] * vk;
+        vk *= v;
+    }
+    long double e0 = (long double)P->e0;
+    long double phie = -(2355.0L / 1462.0L) * e0 * e0 * lead * powl((long double)OR_F0_ECC / f, 19.0L / 9.0L);
+    return f * (long double)P->tc + (lead * s + phie) / (2.0L * OR_PI_L);
+}
+
+/* ---- detector (Sec. IV): rigid constellation, vector geometry ----------- */
+static double or_orbit_phase(const or_model* m, double t) {
+    return 2.0 * OR_PI * t / OR_YEAR_S + m->alpha0;
+}
+
+/* Position of spacecraft n (0,1,2) relative to the guiding centre, in units
+ * of e*R (first-order-in-eccentricity orbits; only directions are used). */
+static void or_sc_offset(const or_model* m, int n, double alpha, double r[3]) {
+    double beta = 2.0 * OR_PI * n / 3.0 + m->orient;
+    r[0] = 0.5 * (cos(2.0 * alpha - beta) - 3.0 * cos(beta));
+    r[1] = 0.5 * (sin(2.0 * alpha - beta) - 3.0 * sin(beta));
+    r[2] = -sqrt(3.0) * cos(alpha - beta);
+}
+
+/* F+ and Fx of the long-wavelength Michelson with vertex at spacecraft 0:
+ * F_A = D : e_A, D = (a a - b b)/2, e+ = p p - q q, ex = p q + q p. */
+static void or_antenna(const or_params* P, const or_model* m, double t, double* Fp, double* Fx) {
+    if (m->response == 1) {
+        *Fp = 1.0;
+        *Fx = 0.0;
+        return;
+    }
+    double alpha = or_orbit_phase(m, t);
+    double r0[3], r1[3], r2[3], a[3], b[3];
+    or_sc_offset(m, 0, alpha, r0);
+    or_sc_offset(m, 1, alpha, r1);
+    or_sc_offset(m, 2, alpha, r2);
+    double na = 0.0, nb = 0.0;
+    for (int i = 0; i < 3; i++) {
+        a[i] = r1[i] - r0[i];
+        b[i] = r2[i] - r0[i];
+        na += a[i] * a[i];
+        nb += b[i] * b[i];
+    }
+    na = sqrt(na);
+    nb = sqrt(nb);
+    for (int i = 0; i < 3; i++) {
+        a[i] /= na;
+        b[i] /= nb;
+    }
+    double D[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) D[i][j] = 0.5 * (a[i] * a[j] - b[i] * b[j]);
+    double sb = sin(P->lat), cb = cos(P->lat), sl = sin(P->lon), cl = cos(P->lon);
+    /* theta = pi/2 - beta: p = theta-hat, q = phi-hat of the source direction */
+    double p[3] = {sb * cl, sb * sl, -cb};
+    double qv[3] = {-sl, cl, 0.0};
+    double fp = 0.0, fx = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double ep = p[i] * p[j] - qv[i] * qv[j];
+            double ex = p[i] * qv[j] + qv[i] * p[j];
+            fp += D[i][j] * ep;
+            fx += D[i][j] * ex;
+        }
+    *Fp = fp;
+    *Fx = fx;
+}
+
+/* Doppler delay d(t) = n . r_gc(t) = R sin(theta) cos(alpha(t) - phi). */
+static double or_doppler_delay(const or_params* P, const or_model* m, double t) {
+    if (m->response == 1) return 0.0;
+    double alpha = or_orbit_phase(m, t);
+    return OR_AU_S * cos(P->lat) * cos(alpha - P->lon);
+}
+
+static int or_params_finite(const or_params* P) {
+    return isfinite(P->Mc) && isfinite(P->tc) && isfinite(P->lat) && isfinite(P->lon) &&
+           isfinite(P->e0) && isfinite(P->q) && P->Mc > 0.0 && P->q > 0.0;
+}
+
+/* ---- public helpers ----------------------------------------------------- */
+double or_time_of_freq(const or_params* P, const or_model* m, double f) { return or_time(P, m, f); }
+
+/* Total template phase in cycles at bin frequency f (long double), and its
+ * fractional part.  Phi = Psi_orb/2pi - f d(t_f). */
+double or_phase_frac(const or_params* P, const or_model* m, double f_min, double df, int64_t k) {
+    long double f = (long double)f_min + (long double)k * (long double)df;
+    long double ph = or_phase_orb_cycles(P, m, f);
+    double t = or_time(P, m, (double)f);
+    ph -= f * (long double)or_doppler_delay(P, m, t);
+    long double fr = ph - roundl(ph);
+    return (double)fr;
+}
+
+long double or_phase_orb_cycles_ld(const or_params* P, const or_model* m, long double f) {
+    return or_phase_orb_cycles(P, m, f);
+}
+
+double or_phase_orb_cycles_d(const or_params* P, const or_model* m, double f) {
+    return (double)or_phase_orb_cycles(P, m, (long double)f);
+}
+
+void or_antenna_at(const or_params* P, const or_model* m, double t, double* Fp, double* Fx) {
+    or_antenna(P, m, t, Fp, Fx);
+}
+
+double or_doppler_at(const or_params* P, const or_model* m, double t) { return or_doppler_delay(P, m, t); }
+
+/* Basis waveforms A^i at bins k0..k1-1 (Eq. response with the Sec. IV
+ * response): h0 = f^-7/6 e^{-2 pi i Phi}, A1 = F+ h0, A2 = Fx h0,
+ * A3 = -i F+ h0, A4 = -i Fx h0.  out: [4][k1-k0] re and im. */
+void or_basis(const or_params* P, const or_model* m, int64_t k0, int64_t k1, double* re, double* im) {
+    int64_t n = k1 - k0;
+    for (int64_t j = 0; j < n; j++) {
+        int64_t k = k0 + j;
+        double f = m->f_min + (double)k * m->df;
+        double t = or_time(P, m, f);
+        double Fp, Fx;
+        or_antenna(P, m, t, &Fp, &Fx);
+        double fr = or_phase_frac(P, m, m->f_min, m->df, k);
+        double c = cos(2.0 * OR_PI * fr), s = sin(2.0 * OR_PI * fr);
+        double amp = pow(f, -7.0 / 6.0);
+        double h_re = amp * c, h_im = -amp * s;   /* h0 */
+        re[0 * n + j] = Fp * h_re;
+        im[0 * n + j] = Fp * h_im;
+        re[1 * n + j] = Fx * h_re;
+        im[1 * n + j] = Fx * h_im;
+        /* -i (x + i y) = y - i x */
+        re[2 * n + j] = Fp * h_im;
+        im[2 * n + j] = -Fp * h_re;
+        re[3 * n + j] = Fx * h_im;
+        im[3 * n + j] = -Fx * h_re;
+    }
+}
+
+/* Segment outer edges (Sec. II.B): first and last bin whose stationary-phase
+ * time lies in [0, T_obs].  t(f) increases with f on the search range.
+ * Returns 0 and sets *klo > *khi when no bin qualifies. */
+int or_band(const or_params* P, const or_model* m, int64_t* klo, int64_t* khi) {
+    int64_t n = m->n;
+    /* smallest k with t(f_k) >= 0 */
+    int64_t lo = 0, hi = n; /* answer in [lo, hi]; hi = n means none */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        double t = or_time(P, m, m->f_min + (double)mid * m->df);
+        if (t >= 0.0) hi = mid; else lo = mid + 1;
+    }
+    int64_t a = lo;
+    /* largest k with t(f_k) <= T: one less than the smallest k with t > T */
+    lo = 0;
+    hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        double t = or_time(P, m, m->f_min + (double)mid * m->df);
+        if (t > m->T_obs) hi = mid; else lo = mid + 1;
+    }
+    int64_t b = lo - 1;
+    *klo = a;
+    *khi = b;
+    return 0;
+}
+
+/* Start bin of every segment: starts[p] for p = 0..Np, segment p is
+ * [starts[p], starts[p+1]).  Global edges (if given) are used as they are.
+ * Per-particle edges: e_p = f_lo + p (f_hi - f_lo)/Np with f_lo = f_{klo},
+ * f_hi = f_{khi}; bin k is in p iff e_p <= f_k < e_{p+1}, last segment closed.
+ * In bin units e_p sits at klo + p (khi - klo)/Np, so the first bin of
+ * segment p is klo + ceil(p (khi - klo) / Np). */
+static void or_segment_starts(const or_params* P, const or_model* m, const int64_t* edges, int Np,
+                              int64_t* starts) {
+    if (edges) {
+        for (int p = 0; p <= Np; p++) starts[p] = edges[p];
+        return;
+    }
+    int64_t klo, khi;
+    or_band(P, m, &klo, &khi);
+    if (klo > khi) {
+        for (int p = 0; p <= Np; p++) starts[p] = 0;
+        return;
+    }
+    int64_t w = khi - klo;
+    for (int p = 0; p < Np; p++) {
+        int64_t num = (int64_t)p * w;
+        starts[p] = klo + (num + Np - 1) / Np;
+    }
+    starts[Np] = khi + 1;
+    if (w == 0)
+        for (int p = 1; p < Np; p++) starts[p] = khi + 1;
+}
+
+/* Per-segment N^i = <d, A^i> and M^ij = <A^i, A^j> (Eqs. aandMN, aandMN2)
+ * with the segment inner product <a,b>_l = 4 df Re sum_k a_k conj(b_k)/S_k. */
+void or_segment_sums(const or_params* P, const or_model* m, const double* d_re, const double* d_im,
+                     const double* psd, const int64_t* edges, int Np, double* Nout /*[Np][4]*/,
+                     double* Mout /*[Np][16]*/, int64_t* nbins /*[Np]*/) {
+    int64_t* starts = (int64_t*)malloc(sizeof(int64_t) * (Np + 1));
+    or_segment_starts(P, m, edges, Np, starts);
+    for (int p = 0; p < Np; p++) {
+        int64_t k0 = starts[p], k1 = starts[p + 1];
+        if (k1 < k0) k1 = k0;
+        int64_t n = k1 - k0;
+        nbins[p] = n;
+        double N[4] = {0, 0, 0, 0}, M[16];
+        memset(M, 0, sizeof(M));
+        if (n > 0) {
+            double* re = (double*)malloc(sizeof(double) * 4 * n);
+            double* im = (double*)malloc(sizeof(double) * 4 * n);
+            or_basis(P, m, k0, k1, re, im);
+            for (int64_t j = 0; j < n; j++) {
+                int64_t k = k0 + j;
+                double w = 4.0 * m->df / psd[k];
+                for (int i = 0; i < 4; i++) {
+                    /* Re(d conj(A)) = d_re A_re + d_im A_im */
+                    N[i] += w * (d_re[k] * re[i * n + j] + d_im[k] * im[i * n + j]);
+                    for (int l = 0; l < 4; l++)
+                        M[i * 4 + l] += w * (re[i * n + j] * re[l * n + j] + im[i * n + j] * im[l * n + j]);
+                }
+            }
+            free(re);
+            free(im);
+        }
+        memcpy(Nout + 4 * p, N, sizeof(N));
+        memcpy(Mout + 16 * p, M, sizeof(M));
+    }
+    free(starts);
+}
+
+/* F_p = 1/2 N^T M^-1 N by Cholesky factorisation of the 4x4 M; the
+ * degenerate-segment rule returns 0. */
+double or_segment_F(const double* N, const double* M, int64_t nbins) {
+    if (nbins < 4) return 0.0;
+    double m11 = M[0], m12 = M[1], m22 = M[5];
+    if (m11 * m22 - m12 * m12 <= 1e-12 * m11 * m22) return 0.0;
+    double L[4][4];
+    memset(L, 0, sizeof(L));
+    for (int i = 0; i < 4; i++) {
+        for (int j = 0; j <= i; j++) {
+            double s = M[i * 4 + j];
+            for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) return 0.0;
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    }
+    /* solve L y = N; then N^T M^-1 N = y . y */
+    double y[4];
+    for (int i = 0; i < 4; i++) {
+        double s = N[i];
+        for (int k = 0; k < i; k++) s -= L[i][k] * y[k];
+        y[i] = s / L[i][i];
+    }
+    return 0.5 * (y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+}
+
+/* Batched semi-coherent F: F[b] = sum_p F_p (the paper's F-hat is F[b]/Np),
+ * Fpart[b*Np + p] = F_p (may be NULL).  edges: Np+1 global segment start
+ * bins, or NULL for per-particle segments.  nthreads <= 0: all cores. */
+int or_fstat_batch(const or_params* params, int B, const or_model* m, const double* d_re,
+                   const double* d_im, const double* psd, const int64_t* edges, int Np, double* F,
+                   double* Fpart, int nthreads) {
+    if (B < 0 || Np < 1 || !m || m->n < 1) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < B; b++) {
+        const or_params* P = params + b;
+        double* Nb = (double*)malloc(sizeof(double) * 4 * Np);
+        double* Mb = (double*)malloc(sizeof(double) * 16 * Np);
+        int64_t* nb = (int64_t*)malloc(sizeof(int64_t) * Np);
+        double tot = 0.0;
+        if (!or_params_finite(P)) {
+            tot = NAN;
+            if (Fpart)
+                for (int p = 0; p < Np; p++) Fpart[(int64_t)b * Np + p] = NAN;
+        } else {
+            or_segment_sums(P, m, d_re, d_im, psd, edges, Np, Nb, Mb, nb);
+            for (int p = 0; p < Np; p++) {
+                double Fp = or_segment_F(Nb + 4 * p, Mb + 16 * p, nb[p]);
+                if (Fpart) Fpart[(int64_t)b * Np + p] = Fp;
+                tot += Fp;
+            }
+        }
+        F[b] = tot;
+        free(Nb);
+        free(Mb);
+        free(nb);
+    }
+    return 0;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---- Appendix B --------------------------------------------------------- */
+/* Eq. (B1): amplitudes a_i from (D_L, psi, iota, phi_c). */
+void or_extrinsic_to_a(double DL, double psi, double iota, double phic, double a[4]) {
+    double c2p = cos(2.0 * psi), s2p = sin(2.0 * psi), ci = cos(iota);
+    double ap = 0.5 * (1.0 + ci * ci), cf = cos(phic), sf = sin(phic);
+    a[0] = (c2p * ap * cf - s2p * ci * sf) / DL;
+    a[1] = -(s2p * ap * cf + c2p * ci * sf) / DL;
+    a[2] = -(c2p * ap * sf + s2p * ci * cf) / DL;
+    a[3] = (s2p * ap * sf - c2p * ci * cf) / DL;
+}
+
+/* Eqs. (B2)-(B3): (D_L, iota, psi, phi_c) from a_i. */
+void or_a_to_extrinsic(const double a[4], double* DL, double* iota, double* psi, double* phic) {
+    double r1 = sqrt((a[0] + a[3]) * (a[0] + a[3]) + (a[1] - a[2]) * (a[1] - a[2]));
+    double r2 = sqrt((a[0] - a[3]) * (a[0] - a[3]) + (a[1] + a[2]) * (a[1] + a[2]));
+    double Ap = r1 + r2, Ax = r1 - r2;
+    double A = Ap + sqrt(Ap * Ap - Ax * Ax);
+    *DL = 2.0 / A;
+    *iota = acos(-Ax / (Ap + sqrt(Ap * Ap - Ax * Ax)));
+    double ps = 0.5 * atan2(Ap * a[3] - Ax * a[0], -(Ax * a[1] + Ap * a[2]));
+    *psi = ps;
+    double c = (sin(2.0 * ps) > 0.0) ? 1.0 : ((sin(2.0 * ps) < 0.0) ? -1.0 : 0.0);
+    *phic = atan2(c * (Ap * a[3] - Ax * a[0]), -c * (Ax * a[2] + Ap * a[1]));
+}
+
+/* ---- Philox4x32-10 (Salmon et al. 2011), written from its definition ---- */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+static double or_u53(uint32_t lo, uint32_t hi) {
+    uint64_t w = ((uint64_t)hi << 32) | lo;
+    return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ---- PSO (Sec. III.A) ---------------------------------------------------- */
+/* Initial positions x ~ U[0,1]^D and velocities v ~ U[-x, 1-x] in the
+ * normalised search space; Philox counter (0xFFFFFFFF, particle, dim, run). */
+void or_pso_init(int R, int Npart, int D, uint64_t seed, double* x, double* v) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int r = 0; r < R; r++)
+        for (int i = 0; i < Npart; i++)
+            for (int j = 0; j < D; j++) {
+                uint32_t ctr[4] = {0xFFFFFFFFu, (uint32_t)i, (uint32_t)j, (uint32_t)r}, o[4];
+                or_philox4x32_10(ctr, key, o);
+                int64_t idx = ((int64_t)r * Npart + i) * D + j;
+                double u1 = or_u53(o[0], o[1]), u2 = or_u53(o[2], o[3]);
+                x[idx] = u1;
+                v[idx] = u2 - u1;
+            }
+}
+
+/* One PSO iteration for R independent runs of Npart particles in D dims.
+ * fit[r*Npart+i] is the fitness of the current position (NaN counts as -inf).
+ *  1. personal best: replaced only on a strictly greater fitness;
+ *  2. local best: best personal best on the ring {i-1, i, i+1}, ties to the
+ *     lowest particle index;
+ *  3. v <- w v + c1 r1 (p - x) + c2 r2 (l - x), r1, r2 ~ U[0,1) from Philox
+ *     counter (iteration, particle, dim, run), key = seed;
+ *  4. v clamped to [-vmax, vmax]; 5. x <- x + v.
+ * Evaluated in this exact order with no fused multiply-add. */
+void or_pso_step(int R, int Npart, int D, double* x, double* v, double* pbest_x, double* pbest_f,
+                 const double* fit, uint64_t seed, uint32_t iteration, double w, double c1, double c2,
+                 double vmax, int* lbest_idx_out) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int r = 0; r < R; r++)
+        for (int i = 0; i < Npart; i++) {
+            int64_t pi = (int64_t)r * Npart + i;
+            double f = fit[pi];
+            if (f > pbest_f[pi]) { /* NaN compares false */
+                pbest_f[pi] = f;
+                for (int j = 0; j < D; j++) pbest_x[pi * D + j] = x[pi * D + j];
+            }
+        }
+    int* lb = (int*)malloc(sizeof(int) * (size_t)R * Npart);
+    for (int r = 0; r < R; r++)
+        for (int i = 0; i < Npart; i++) {
+            int cand[3] = {(i + Npart - 1) % Npart, i, (i + 1) % Npart};
+            int best = -1;
+            for (int c = 0; c < 3; c++) {
+                int j = cand[c];
+                if (best < 0) { best = j; continue; }
+                double fj = pbest_f[(int64_t)r * Npart + j], fb = pbest_f[(int64_t)r * Npart + best];
+                if (fj > fb || (fj == fb && j < best)) best = j;
+            }
+            lb[r * Npart + i] = best;
+        }
+    for (int r = 0; r < R; r++)
+        for (int i = 0; i < Npart; i++) {
+            int64_t pi = (int64_t)r * Npart + i;
+            int64_t li = (int64_t)r * Npart + lb[r * Npart + i];
+            if (lbest_idx_out) lbest_idx_out[pi] = lb[r * Npart + i];
+            for (int j = 0; j < D; j++) {
+                uint32_t ctr[4] = {iteration, (uint32_t)i, (uint32_t)j, (uint32_t)r}, o[4];
+                or_philox4x32_10(ctr, key, o);
+                double r1 = or_u53(o[0], o[1]), r2 = or_u53(o[2], o[3]);
+                double xv = x[pi * D + j];
+                double cog = c1 * r1;
+                cog = cog * (pbest_x[pi * D + j] - xv);
+                double soc = c2 * r2;
+                soc = soc * (pbest_x[li * D + j] - xv);
+                double nv = w * v[pi * D + j];
+                nv = nv + cog;
+                nv = nv + soc;
+                if (nv > vmax) nv = vmax;
+                if (nv < -vmax) nv = -vmax;
+                v[pi * D + j] = nv;
+                x[pi * D + j] = xv + nv;
+            }
+        }
+    free(lb);
+}

@@ -1,0 +1,402 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms, exact invariants of the F-statistic,
+textbook special cases and brute force on tiny inputs.  None of these needs a
+GPU.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2407_10797_gb300 import synth as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tc_for(Mc, f, t):
+    """Coalescence time that puts the Newtonian stationary-phase time of
+    frequency f at t (test helper: chooses in-band particles)."""
+    m = Mc * S.MSUN_S
+    return t + 5.0 / 256.0 * m * (np.pi * m * f) ** (-8.0 / 3.0)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    g = S.tiny_grid(n=4096, f_min=0.02)
+    psd = S.lisa_like_psd(g.freqs())
+    return g, psd, O.OracleModel.from_grid(g)
+
+
+def _inject(p, m, psd, df, snr):
+    """Signal of particle p, present only at the bins swept during [0, T]."""
+    a = O.extrinsic_to_a(1.0, S.INJ_PSI, S.INJ_IOTA, S.INJ_PHIC)
+    k0, k1 = O.band(p, m)
+    h = O.inject(p, m, a, k0, k1 + 1)
+    s = snr / math.sqrt(O.inner(h, h, psd, df))
+    return h * s, a * s
+
+
+# ---------------------------------------------------------------- Philox
+def _kat():
+    rows = []
+    for line in open(os.path.join(GOLD, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        rows.append((w[:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answers_oracle():
+    for ctr, key, out in _kat():
+        assert list(O.philox(ctr, key)) == out
+
+
+def test_philox_known_answers_input_generator():
+    for ctr, key, out in _kat():
+        got = S.philox4x32_10(np.array(ctr, np.uint32), np.array(key, np.uint32))
+        assert list(got) == out
+
+
+# ---------------------------------------------------------------- p1: (h|h)
+def test_inner_product_matches_analytic_integral():
+    """Test-mode response (F+ = 1, Fx = 0, no Doppler), flat PSD S0:
+    <A1, A1> = 4 df sum f_k^-7/3 / S0 is the midpoint rule of
+    4/S0 int f^-7/3 df = (3/S0)(fa^-4/3 - fb^-4/3) over [f_lo - df/2, f_hi + df/2]."""
+    g = S.tiny_grid(n=20000, f_min=0.01, stride=200)
+    m = O.OracleModel.from_grid(g, response=1)
+    S0 = 3.7e-40
+    psd = np.full(g.n, S0)
+    p = np.array([20.0, 0.0, 0.1, 0.2, 0.0, 1.0])
+    edges = np.array([0, 7000, 20000], dtype=np.int64)
+    N, M, nb = O.segment_sums(p, m, np.zeros(g.n, complex), psd, 2, edges)
+    for s in range(2):
+        k0, k1 = edges[s], edges[s + 1]
+        fa = g.f_min + (k0 - 0.5) * g.df
+        fb = g.f_min + (k1 - 0.5) * g.df
+        exact = 3.0 / S0 * (fa ** (-4 / 3) - fb ** (-4 / 3))
+        # midpoint-rule error bound: (b-a) h^2 max|f''| / 24, f'' = (7/3)(10/3) x^(-13/3)
+        bound = 4.0 / S0 * (fb - fa) * g.df ** 2 * (70.0 / 9.0) * fa ** (-13 / 3) / 24.0
+        assert abs(M[s, 0, 0] - exact) <= bound
+        assert abs(M[s, 0, 0] - exact) <= 1e-4 * exact
+        # A3 = -i A1 has the same norm and is orthogonal to A1
+        assert M[s, 2, 2] == pytest.approx(M[s, 0, 0], rel=1e-14)
+        assert M[s, 0, 2] == 0.0
+        assert nb[s] == k1 - k0
+
+
+# ---------------------------------------------------------------- p2/p3
+@pytest.mark.parametrize("Np", [1, 3, 8, 16])
+def test_F_equals_half_snr_squared_at_truth(tiny, Np):
+    g, psd, m = tiny
+    p = np.array([30.0, tc_for(30.0, 0.02, 0.5 * g.T_obs), 0.3, 1.0, 0.05, 1.0])
+    d, a = _inject(p, m, psd, g.df, 12.0)
+    F, Fp = O.fstat_batch(p[None], m, d, psd, Np)
+    assert F[0] == pytest.approx(72.0, rel=1e-12)
+    # per segment: F_p = (h|h)_p / 2
+    N, M, nb = O.segment_sums(p, m, d, psd, Np)
+    for s in range(Np):
+        hh = a @ M[s] @ a
+        assert Fp[0, s] == pytest.approx(0.5 * hh, rel=1e-10)
+
+
+def test_amplitudes_recovered_and_appendix_b_round_trip(tiny):
+    g, psd, m = tiny
+    p = np.array([25.0, tc_for(25.0, 0.02, 0.4 * g.T_obs), -0.7, 4.0, 0.02, 1.0])
+    d, a = _inject(p, m, psd, g.df, 10.0)
+    N, M, nb = O.segment_sums(p, m, d, psd, 1)
+    a_hat = np.linalg.solve(M[0], N[0])          # Eq. (aandMN3)
+    assert np.allclose(a_hat, a, rtol=1e-9, atol=0)
+    # Appendix B: a -> (D_L, iota, psi, phi_c) -> a
+    DL, iota, psi, phic = O.a_to_extrinsic(a_hat)
+    a_back = O.extrinsic_to_a(DL, psi, iota, phic)
+    assert np.allclose(a_back, a_hat, rtol=1e-10, atol=0)
+    # the injected extrinsics (Table I) are recovered modulo the (psi, phi_c) -> (psi + pi/2, phi_c + pi) symmetry
+    assert iota == pytest.approx(S.INJ_IOTA, abs=1e-8)
+    two_psi = (2 * psi - 2 * S.INJ_PSI) % (2 * np.pi)
+    assert min(two_psi, 2 * np.pi - two_psi) == pytest.approx(0.0, abs=1e-8) or \
+        abs(two_psi - np.pi) < 1e-8
+
+
+# ---------------------------------------------------------------- p4: chi^2
+@pytest.mark.parametrize("Np", [1, 4])
+def test_noise_only_2F_is_chi_square_4Np(Np):
+    from scipy import stats
+    g = S.tiny_grid(n=1024, f_min=0.02)
+    psd = S.lisa_like_psd(g.freqs())
+    m = O.OracleModel.from_grid(g)
+    noise = S.gaussian_noise(g, psd, 11)
+    P = S.draw_params(S.Prior(tc_lo=0.2 * g.T_obs, tc_hi=0.8 * g.T_obs), 600, 3)
+    P[:, 1] = tc_for(P[:, 0], 0.02, P[:, 1])
+    F, Fp = O.fstat_batch(P, m, noise, psd, Np)
+    assert np.all(F > 0)
+    ks = stats.kstest(2.0 * F, stats.chi2(4 * Np).cdf)
+    assert ks.pvalue > 1e-3
+    assert np.mean(2 * F) == pytest.approx(4 * Np, rel=5 * np.sqrt(8 * Np / 600) / (4 * Np))
+
+
+# ---------------------------------------------------------------- p5: invariances
+def test_invariances(tiny):
+    g, psd, m = tiny
+    noise = S.gaussian_noise(g, psd, 2)
+    P = S.draw_params(S.Prior(tc_lo=0.3 * g.T_obs, tc_hi=0.7 * g.T_obs), 6, 9)
+    P[:, 1] = tc_for(P[:, 0], 0.02, P[:, 1])
+    d = noise + _inject(P[0], m, psd, g.df, 8.0)[0]
+    F0, _ = O.fstat_batch(P, m, d, psd, 4)
+    # constant phase of the data (phi_c, pi/4 are absorbed by the amplitudes)
+    F1, _ = O.fstat_batch(P, m, d * np.exp(0.731j), psd, 4)
+    assert np.allclose(F1, F0, rtol=1e-11)
+    # (d, S) -> (c d, c^2 S)
+    F2, _ = O.fstat_batch(P, m, 3.0e5 * d, 9.0e10 * psd, 4)
+    assert np.allclose(F2, F0, rtol=1e-11)
+
+
+def test_bins_outside_band_do_not_contribute():
+    """Per-particle segments: data outside [f_lo, f_hi] is ignored."""
+    g = S.tiny_grid(n=3000, f_min=0.03, stride=300)
+    psd = S.lisa_like_psd(g.freqs())
+    m = O.OracleModel.from_grid(g)
+    p = np.array([10.0, tc_for(10.0, 0.03, -0.05 * g.T_obs), 0.2, 2.0, 0.03, 1.0])
+    k0, k1 = O.band(p, m)
+    assert 0 < k0 <= k1 < g.n - 1
+    noise = S.gaussian_noise(g, psd, 4)
+    F0, _ = O.fstat_batch(p[None], m, noise, psd, 8)
+    d2 = noise.copy()
+    d2[:k0] *= -7.0
+    d2[k1 + 1:] = 1e3 * d2[k1 + 1:] + 1.0
+    F1, _ = O.fstat_batch(p[None], m, d2, psd, 8)
+    assert F1[0] == F0[0]
+
+
+# ---------------------------------------------------------------- p6: t(f)
+def test_time_is_derivative_of_phase(tiny):
+    g, psd, m = tiny
+    for Mc, e0 in [(12.0, 0.0), (30.0, 0.08), (48.0, 0.03)]:
+        p = np.array([Mc, tc_for(Mc, 0.02, 0.5 * g.T_obs), 0.3, 1.0, e0, 1.0])
+        for f in (0.0200, 0.02003):
+            h = 1e-7
+            dphi = (O.phase_orb_cycles(p, m, f + h) - O.phase_orb_cycles(p, m, f - h)) / (2 * h)
+            t = O.time_of_freq(p, m, f)
+            assert dphi == pytest.approx(t, abs=0.05)
+
+
+def test_newtonian_time_and_band_edges():
+    """pn_order 0 and e0 = 0: t(f) = t_c - (5/256) Mc (pi Mc f)^(-8/3), and the
+    band edges are the bins around f(t) = (1/pi) (5/(256 (t_c - t)))^(3/8) Mc^(-5/8)."""
+    g = S.Grid(f_min=0.01, df=1e-5, n=4000, T_obs=2.5 * S.YEAR_S)
+    m = O.OracleModel.from_grid(g, pn_order=0)
+    for Mc, tcf in [(15.0, 0.9), (30.0, 0.6), (45.0, 1.3)]:
+        p = np.array([Mc, tcf * g.T_obs, 0.1, 0.5, 0.0, 1.0])
+        mc = Mc * S.MSUN_S
+        for f in (0.012, 0.03, 0.045):
+            t = O.time_of_freq(p, m, f)
+            assert t - p[1] == pytest.approx(-5.0 / 256.0 * mc * (np.pi * mc * f) ** (-8 / 3), rel=1e-12)
+
+        def f_of_t(t):
+            if t >= p[1]:
+                return np.inf
+            return (5.0 / (256.0 * (p[1] - t))) ** 0.375 * mc ** (-0.625) / np.pi
+
+        klo, khi = O.band(p, m)
+        flo, fhi = f_of_t(0.0), f_of_t(g.T_obs)
+        exp_lo = max(0, math.ceil((flo - g.f_min) / g.df))
+        exp_hi = g.n - 1 if not np.isfinite(fhi) else min(g.n - 1, math.floor((fhi - g.f_min) / g.df))
+        assert klo == exp_lo and khi == exp_hi
+
+
+def test_pn_coefficients_from_energy_balance():
+    """t(f) of the oracle equals the stationary-phase time obtained from the
+    textbook 2PN binding energy and flux (non-spinning, circular):
+    E = -(mu v^2/2)[1 - (3/4 + eta/12) v^2 - (27/8 - 19 eta/8 + eta^2/24) v^4],
+    F = (32/5) eta^2 v^10 [1 - (1247/336 + 35 eta/12) v^2 + 4 pi v^3
+        - (44711/9072 - 9271 eta/504 - 65 eta^2/18) v^4],
+    dt/dv = -(dE/dv)/F expanded to O(v^4) and integrated term by term."""
+    import sympy as sp
+    v, eta = sp.symbols("v eta", positive=True)
+    e2 = -(sp.Rational(3, 4) + eta / 12)
+    e4 = -(sp.Rational(27, 8) - sp.Rational(19, 8) * eta + eta ** 2 / 24)
+    f2 = -(sp.Rational(1247, 336) + sp.Rational(35, 12) * eta)
+    f3 = 4 * sp.pi
+    f4 = -(sp.Rational(44711, 9072) - sp.Rational(9271, 504) * eta - sp.Rational(65, 18) * eta ** 2)
+    num = 1 + 2 * e2 * v ** 2 + 3 * e4 * v ** 4     # -(dE/dv)/(mu v)
+    den = 1 + f2 * v ** 2 + f3 * v ** 3 + f4 * v ** 4
+    R = sp.series(num / den, v, 0, 5).removeO()
+    # t(v) = t_c - (5 M /(32 eta)) sum_k r_k v^(k-8)/(8-k)
+    tv = sum(-sp.Rational(5, 32) / eta * R.coeff(v, k) * v ** (k - 8) / (8 - k) for k in range(5))
+    tfun = sp.lambdify((v, eta), tv, "math")
+    g = S.tiny_grid(n=10, f_min=0.01)
+    m = O.OracleModel.from_grid(g)
+    for Mc, q in [(10.0, 1.0), (37.0, 1.0), (20.0, 3.0)]:
+        p = np.array([Mc, 1.0e7, 0.0, 0.0, 0.0, q])
+        et = q / (1 + q) ** 2
+        M = Mc * S.MSUN_S * et ** (-0.6)
+        for f in (0.01, 0.02, 0.05):
+            vv = (np.pi * M * f) ** (1 / 3)
+            expect = tfun(vv, et) * M
+            got = O.time_of_freq(p, m, f) - p[1]
+            assert got == pytest.approx(expect, rel=1e-12)
+
+
+# ---------------------------------------------------------------- p7: antenna
+def test_antenna_sky_polarisation_average():
+    """<F+^2 + Fx^2> over the sky = 2 * 3/20 for a 60-degree Michelson
+    (the psi-average of F+^2 is (F+^2 + Fx^2)/2 and <F+^2> = (2/5) D:D =
+    (2/5)(1/2) sin^2(60 deg)).  F+^2 + Fx^2 is a degree-4 polynomial in the
+    direction, so a Gauss-Legendre x uniform-longitude rule is exact."""
+    g = S.tiny_grid(n=10)
+    m = O.OracleModel.from_grid(g)
+    xs, ws = np.polynomial.legendre.leggauss(6)
+    nl = 12
+    for t in (0.0, 0.37 * S.YEAR_S, 1.71 * S.YEAR_S):
+        acc = 0.0
+        for x, w in zip(xs, ws):
+            for j in range(nl):
+                p = np.array([20.0, 0.0, math.asin(x), 2 * np.pi * j / nl, 0.0, 1.0])
+                fp, fx = O.antenna(p, m, t)
+                acc += w * (fp * fp + fx * fx) / nl
+        assert acc / 2.0 == pytest.approx(2 * 3.0 / 20.0, rel=1e-12)
+
+
+def test_doppler_vanishes_at_ecliptic_poles_and_peaks_in_plane():
+    g = S.tiny_grid(n=10)
+    m = O.OracleModel.from_grid(g)
+    for t in (0.0, 1.0e7, 5.5e7):
+        for lat in (np.pi / 2, -np.pi / 2):
+            assert abs(O.doppler_delay([20, 0, lat, 1.0, 0, 1], m, t)) < 1e-12 * S.AU_S
+    # in the ecliptic plane, facing the guiding centre: d = R
+    assert O.doppler_delay([20, 0, 0.0, 0.0, 0, 1], m, 0.0) == pytest.approx(S.AU_S, rel=1e-15)
+
+
+# ---------------------------------------------------------------- p8: eccentricity
+def test_eccentric_correction_scales_as_e0_squared():
+    g = S.tiny_grid(n=10)
+    m = O.OracleModel.from_grid(g)
+    base = np.array([25.0, 1.0e8, 0.0, 0.0, 0.0, 1.0])
+    for f in (0.01, 0.02, 0.04):
+        ph0 = O.phase_orb_cycles(base, m, f)
+        d1 = O.phase_orb_cycles(base + [0, 0, 0, 0, 0.03, 0], m, f) - ph0
+        d2 = O.phase_orb_cycles(base + [0, 0, 0, 0, 0.06, 0], m, f) - ph0
+        assert d2 / d1 == pytest.approx(4.0, rel=1e-7)
+        # and matches -(2355/1462) e0^2 (3/128)(pi Mc f)^-5/3 (f0/f)^(19/9) / (2 pi)
+        mc = 25.0 * S.MSUN_S
+        expect = -(2355 / 1462) * 0.03 ** 2 * 3 / 128 * (np.pi * mc * f) ** (-5 / 3) \
+            * (0.01 / f) ** (19 / 9) / (2 * np.pi)
+        assert d1 == pytest.approx(expect, rel=1e-7)
+
+
+# ---------------------------------------------------------------- segments
+def test_segment_membership_exact():
+    """Bin k lies in segment p iff e_p <= f_k < e_{p+1} (last one closed), with
+    e_p = f_lo + p (f_hi - f_lo)/Np, checked in exact rational arithmetic."""
+    g = S.Grid(f_min=0.01, df=1.0 / 1024.0 / 1024.0 / 32.0, n=3001, T_obs=2.5 * S.YEAR_S)
+    m = O.OracleModel.from_grid(g)
+    for Mc, tcf, Np in [(20.0, 0.9, 7), (33.0, 0.95, 256), (45.0, 0.8, 64), (11.0, 1.05, 3)]:
+        p = np.array([Mc, tcf * g.T_obs, 0.1, 0.5, 0.02, 1.0])
+        p[1] = tc_for(Mc, 0.01 + 1500 * g.df, tcf * g.T_obs * 0.5)
+        klo, khi = O.band(p, m)
+        _, _, nb = O.segment_sums(p, m, np.zeros(g.n, complex), np.ones(g.n), Np)
+        fmin, df = Fraction(g.f_min), Fraction(g.df)
+        fk = lambda k: fmin + k * df
+        cnt = np.zeros(Np, dtype=np.int64)
+        if klo <= khi:
+            flo, fhi = fk(klo), fk(khi)
+            for k in range(klo, khi + 1):
+                e = [flo + Fraction(j) * (fhi - flo) / Np for j in range(Np + 1)]
+                for s in range(Np):
+                    if e[s] <= fk(k) < e[s + 1] or (s == Np - 1 and fk(k) == e[Np]):
+                        cnt[s] += 1
+                        break
+        assert list(nb) == list(cnt)
+
+
+def test_degenerate_segments_give_zero():
+    N = np.array([1.0, 2.0, 3.0, 4.0])
+    M = np.eye(4)
+    assert O.segment_F(N, M, 3) == 0.0
+    assert O.segment_F(N, M, 4) == pytest.approx(15.0)
+    Ms = np.diag([1.0, 1.0, 1.0, 1.0])
+    Ms[0, 1] = Ms[1, 0] = 1.0 - 1e-14          # M11 M22 - M12^2 below 1e-12 M11 M22
+    assert O.segment_F(N, Ms, 100) == 0.0
+
+
+def test_nonfinite_parameters_give_nan(tiny):
+    g, psd, m = tiny
+    P = np.array([[np.nan, 1e8, 0, 0, 0, 1], [20.0, 1e8, 0, 0, 0, 1]])
+    F, Fp = O.fstat_batch(P, m, np.zeros(g.n, complex), psd, 2)
+    assert np.isnan(F[0]) and np.all(np.isnan(Fp[0]))
+
+
+# ---------------------------------------------------------------- p9: brute force
+def test_brute_force_scan_peaks_at_truth_and_broadens_with_Np():
+    """Noise-free 1-D M_c scan: the argmax is the injected M_c for every Np and
+    the half-maximum width grows with Np (Fig. 1, left panel)."""
+    g = S.tiny_grid(n=2048, f_min=0.02, stride=64)
+    psd = S.lisa_like_psd(g.freqs())
+    m = O.OracleModel.from_grid(g)
+    Mc0 = 30.0
+    p = np.array([Mc0, tc_for(Mc0, 0.02, 0.9 * g.T_obs), 0.4, 2.1, 0.01, 1.0])
+    d, _ = _inject(p, m, psd, g.df, 20.0)
+    grid = Mc0 * (1.0 + np.linspace(-4e-5, 4e-5, 81))
+    P = np.repeat(p[None], len(grid), axis=0)
+    P[:, 0] = grid
+    widths = []
+    for Np in (1, 16):
+        F, _ = O.fstat_batch(P, m, d, psd, Np)
+        assert np.argmax(F) == 40
+        widths.append(np.sum(F > 0.5 * F.max()))
+    assert widths[1] > widths[0]
+
+
+# ---------------------------------------------------------------- PSO
+def test_pso_converges_on_sphere_function():
+    R, Np, D = 2, 40, 5
+    x, v = O.pso_init(R, Np, D, seed=7)
+    assert np.all((x >= 0) & (x < 1)) and np.all(x + v >= 0) and np.all(x + v <= 1)
+    pbx = x.copy()
+    pbf = np.full((R, Np), -np.inf)
+    target = np.array([0.3, 0.7, 0.5, 0.2, 0.9])
+    iters = 300
+    for it in range(iters):
+        inside = np.all((x >= 0) & (x <= 1), axis=2)
+        fit = np.where(inside, -np.sum((x - target) ** 2, axis=2), -np.inf)
+        w = 0.9 - 0.5 * it / (iters - 1)
+        O.pso_step(x, v, pbx, pbf, fit, seed=7, iteration=it, w=w)
+    best = pbx[np.arange(R), np.argmax(pbf, axis=1)]
+    assert np.all(np.abs(best - target) < 1e-3)
+
+
+def test_pso_step_rules():
+    """pbest only on strictly greater fitness, lbest on the ring with ties to
+    the lowest index, symmetric velocity clamp."""
+    R, Np, D = 1, 6, 2
+    x = np.arange(R * Np * D, dtype=float).reshape(R, Np, D) / 20
+    v = np.zeros_like(x)
+    pbx = x.copy() + 0.5
+    pbf = np.array([[1.0, 2.0, 2.0, 0.5, 3.0, 3.0]])
+    fit = np.array([[1.0, 5.0, -np.inf, np.nan, 3.0, 1.0]])
+    pbx0 = pbx.copy()
+    lb = O.pso_step(x, v, pbx, pbf, fit, seed=1, iteration=3, w=0.5, vmax=0.05)
+    assert list(pbf[0]) == [1.0, 5.0, 2.0, 0.5, 3.0, 3.0]
+    assert np.array_equal(pbx[0, 0], pbx0[0, 0]) and np.array_equal(pbx[0, 1], x[0, 1] - v[0, 1])
+    # ring neighbourhoods {5,0,1} {0,1,2} {1,2,3} {2,3,4} {3,4,5} {4,5,0}
+    assert list(lb[0]) == [1, 1, 1, 4, 4, 4]
+    assert np.all(np.abs(v) <= 0.05)
+
+
+def test_constants_agree_with_input_module():
+    src = open(os.path.join(os.path.dirname(O.__file__), "fstat_oracle.c")).read()
+
+    def grab(name):
+        for line in src.splitlines():
+            if line.startswith(f"#define {name} "):
+                return float(line.split()[2])
+        raise KeyError(name)
+
+    assert grab("OR_MSUN_S") == S.MSUN_S
+    assert grab("OR_YEAR_S") == S.YEAR_S
+    assert grab("OR_AU_S") == S.AU_S
