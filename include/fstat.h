@@ -1,0 +1,153 @@
+/*
+ * fstat.h - C ABI of the GB300 (sm_103a) semi-coherent F-statistic library.
+ *
+ * The library evaluates, for a batch of particles (intrinsic parameters
+ * Theta_I), the semi-coherent F-statistic of the hierarchical SmBBH search of
+ * Fu, Wang & Mohanty (arXiv:2407.10797):
+ *
+ *   F_sum(Theta_I) = sum_{l=1..N_seg} F_l,  F_l = 1/2 N_l^T M_l^{-1} N_l,
+ *   N_l^i = <d, A^i>_l,  M_l^ij = <A^i, A^j>_l,
+ *   <a, b>_l = 4 Re sum_{k in segment l} a_k conj(b_k) / S_k * df
+ *
+ * (Sec. II.A Eqs. inner_product, response, coherent_F_stat, aandMN-aandMN3;
+ * Sec. II.B Eq. semi-cohF and the segment inner product).  The paper's
+ * F-hat is F_sum / N_seg.  Templates follow Appendix A (restricted PN phase,
+ * TaylorF2 through 2PN, leading e0^2 eccentricity correction at 10 mHz) with
+ * the frequency-domain LISA response of Sec. IV (Eq. freDres, N = 0): the
+ * antenna patterns and the Doppler phase are taken at the stationary-phase
+ * time t(f) = (1/2pi) dPsi/df.
+ *
+ * Conventions
+ *   - Units: G = c = 1 with times in seconds; masses in solar masses on input.
+ *   - Frequency grid: f_k = f_min + k*df, k = 0..n_bins-1 (uniform).
+ *   - All `*_dev` pointers are device pointers owned by the caller; `*_host`
+ *     pointers are host memory owned by the caller.  The plan owns its own
+ *     workspace (per-bin tables, per-particle coefficients, partial sums).
+ *   - Every call is asynchronous and ordered on the plan's stream, unless its
+ *     comment says otherwise.  No call keeps a pointer to caller memory.
+ *   - Errors: every function returns fs_status; on failure fs_last_error()
+ *     returns a message (thread-local, valid until the next call on the same
+ *     thread).  Invalid sizes or arguments give FS_EINVAL and launch nothing.
+ *   - Thread safety: one plan must not be used from two threads at once.
+ */
+#ifndef FSTAT_H
+#define FSTAT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FS_API __attribute__((visibility("default")))
+#else
+#define FS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FS_OK = 0,
+    FS_EINVAL = -1,        /* invalid argument or size */
+    FS_ECUDA = -2,         /* a CUDA runtime call failed */
+    FS_ENOMEM = -3,        /* device allocation failed */
+    FS_ETIMEOUT = -4,      /* a bounded device-side wait expired */
+    FS_EUNSUPPORTED = -5   /* valid request this build does not implement */
+} fs_status;
+
+typedef enum {
+    FS_FP64 = 0,   /* every step in FP64; the phase in double-double where it exceeds 2^23 cycles */
+    FS_MIXED = 1   /* FP64 anchors + exact fixed-point phase steps, FP32 response and products */
+} fs_precision;
+
+/* Intrinsic parameters of one particle (Sec. II.A, Theta_I without delta_mu;
+ * the mass ratio q = m1/m2 >= 1 fixes eta = q/(1+q)^2). */
+typedef struct {
+    double Mc;   /* chirp mass, solar masses (> 0) */
+    double tc;   /* time of coalescence, s, measured from the start of the data */
+    double lat;  /* ecliptic latitude beta, rad (theta = pi/2 - beta) */
+    double lon;  /* ecliptic longitude lambda = phi, rad */
+    double e0;   /* orbital eccentricity at GW frequency 10 mHz */
+    double q;    /* mass ratio (1 = equal masses) */
+} fs_params;
+
+typedef struct fs_plan fs_plan;
+
+/* Create a plan for one frequency grid and precision mode.
+ *   n_bins > 0, f_min > 0, df > 0, T_obs > 0 (observation span: segment outer
+ *   edges are the bins whose stationary-phase time lies in [0, T_obs],
+ *   Sec. II.B); mode is an fs_precision; stream is a cudaStream_t (NULL = the
+ *   legacy default stream).  Allocates the per-bin tables on the current
+ *   device.  Synchronous.  *out is NULL on failure. */
+FS_API fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df, double T_obs,
+                         int mode, void* stream);
+
+/* Free a plan and its workspace (waits for the plan's stream).  NULL is a no-op. */
+FS_API fs_status fs_plan_destroy(fs_plan* plan);
+
+/* Load one data set.  data_dev: n_bins complex values as interleaved FP64
+ * (re, im); psd_dev: n_bins one-sided PSD values S_k > 0.  Precomputes the
+ * particle-independent per-bin tables (noise-weighted data 4 df d_k f^-7/6 / S_k,
+ * weights 4 df f^-7/3 / S_k, frequency powers).  Asynchronous; the caller's
+ * buffers may be reused once the plan's stream has passed this call. */
+FS_API fs_status fs_plan_set_data(fs_plan* plan, const double* data_dev, const double* psd_dev);
+
+/* Pre-size the plan's workspace for batches of up to B_max particles and
+ * N_p_max segments, so that later fs_fstat_batch calls allocate nothing (and
+ * can be captured in a CUDA graph).  Synchronous. */
+FS_API fs_status fs_plan_reserve(fs_plan* plan, int B_max, int N_p_max);
+
+/* Batched semi-coherent F-statistic (Sec. II.B, Eq. semi-cohF).
+ *   params_dev : B particles (device array of fs_params).
+ *   B          : 0 <= B; B = 0 launches nothing.
+ *   edges_host : NULL for per-particle segments: the outer edges are the first
+ *                and last bin whose t(f_k) lies in [0, T_obs] and the N_p
+ *                segments are equal-width in frequency between them (bin k is
+ *                in segment p iff e_p <= f_k < e_{p+1}, the last one closed).
+ *                Otherwise N_p + 1 non-decreasing bin indices in [0, n_bins]:
+ *                segment p is bins [edges[p], edges[p+1]) for every particle.
+ *   N_p        : 1 <= N_p <= 4096.
+ *   F_dev      : B doubles, F_sum = sum_p F_p (the paper's F-hat times N_p).
+ *   F_part_dev : B*N_p doubles (F_p, row-major by particle) or NULL.
+ * A segment with fewer than 4 bins, or with M11 M22 - M12^2 <= 1e-12 M11 M22,
+ * contributes F_p = 0.  A particle with a non-finite parameter, Mc <= 0 or
+ * q <= 0 gets F = NaN (and NaN segments).  Grows the workspace (synchronously)
+ * if B or N_p exceed the reservation. */
+FS_API fs_status fs_fstat_batch(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
+                         int N_p, double* F_dev, double* F_part_dev);
+
+/* Add the signal h = sum_i a_i A^i of one particle to data_dev (n_bins
+ * interleaved complex FP64, device) at the bins of the particle's band
+ * [first, last bin with t(f_k) in [0, T_obs]]; the other bins are untouched.
+ * The basis is A1 = F+ h0, A2 = Fx h0, A3 = -i F+ h0, A4 = -i Fx h0 with
+ * h0 = f^-7/6 exp(-i Psi(f)) (Appendix A with the Sec. IV response); a_host
+ * holds the four amplitudes of Eq. (response).  Evaluated in FP64. */
+FS_API fs_status fs_add_signal(fs_plan* plan, const fs_params* params_host, const double* a_host,
+                        double* data_dev);
+
+/* Segment outer edges of each particle (Sec. II.B): bands_dev receives
+ * 2*B int64 values (first, last) per particle, the first and last bin whose
+ * stationary-phase time lies in [0, T_obs]; first > last means no such bin
+ * (and a particle with invalid parameters reports (1, 0)).  Asynchronous. */
+FS_API fs_status fs_particle_bands(fs_plan* plan, const fs_params* params_dev, int B, int64_t* bands_dev);
+
+/* Kernel timing on the plan's stream.  While enabled, every kernel the plan
+ * launches is bracketed by CUDA events.  fs_plan_read_profile waits for the
+ * plan's stream, returns the summed duration (ms) and launch count of one
+ * kernel kind since the last read (0 = per-particle setup, 1 = fused
+ * template/reduction kernel, 2 = segment solve and sum, 3 = per-bin
+ * precompute) and resets that kind's counters. */
+FS_API fs_status fs_plan_set_profiling(fs_plan* plan, int enable);
+FS_API fs_status fs_plan_read_profile(fs_plan* plan, int kernel, double* total_ms, int64_t* launches);
+
+/* Constants compiled into the library: out[0] = solar mass in s, out[1] =
+ * year in s, out[2] = AU/c in s, out[3] = eccentricity reference frequency (Hz). */
+FS_API fs_status fs_constants(double* out_host);
+
+/* Message of the last failed call on this thread ("" if none). */
+FS_API const char* fs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSTAT_H */

@@ -1,0 +1,375 @@
+// fs_api.cu - the C ABI of include/fstat.h: plan lifetime, workspace and
+// the launch sequence of one batched F-statistic evaluation.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fs_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+fs_status fail(fs_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+fs_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) return fail(FS_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(FS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct fs_plan {
+    fs::Grid grid;
+    int mode;
+    int device;
+    cudaStream_t stream;
+    fs::Tables tab;
+    double* tab_base;
+    int data_set;
+    // workspace
+    int B_cap, Np_cap;
+    fs::Particle* parts;
+    double* H;
+    double* T;
+    double* S;
+    double* Fpart;
+    int ntiles;
+    // segment edges (global mode)
+    int64_t* edges_dev;
+    int64_t* edges_cache;
+    int edges_np;
+    // single-particle scratch for fs_add_signal
+    fs_params* one_param;
+    fs::Particle* one_part;
+    double* one_a;
+    // kernel timing
+    struct ProfRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    int profiling;
+    std::vector<ProfRec>* prof;       // recorded, unread
+    std::vector<cudaEvent_t>* spare;  // reusable events
+};
+
+namespace {
+
+constexpr int kKinds = 4;
+
+cudaEvent_t take_event(fs_plan* p) {
+    if (!p->spare->empty()) {
+        cudaEvent_t e = p->spare->back();
+        p->spare->pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Bracket a launch sequence with events when profiling is on.
+struct ProfScope {
+    fs_plan* p;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(fs_plan* pl, int k) : p(pl), kind(k) {
+        if (p->profiling) {
+            a = take_event(p);
+            if (a) cudaEventRecord(a, p->stream);
+        }
+    }
+    ~ProfScope() {
+        if (a) {
+            cudaEvent_t b = take_event(p);
+            if (b) {
+                cudaEventRecord(b, p->stream);
+                p->prof->push_back({kind, a, b});
+            } else {
+                p->spare->push_back(a);
+            }
+        }
+    }
+};
+
+void free_workspace(fs_plan* p) {
+    cudaFree(p->parts);
+    cudaFree(p->H);
+    cudaFree(p->T);
+    cudaFree(p->S);
+    cudaFree(p->Fpart);
+    p->parts = nullptr;
+    p->H = p->T = p->S = p->Fpart = nullptr;
+    p->B_cap = p->Np_cap = 0;
+}
+
+fs_status ensure_workspace(fs_plan* p, int B, int Np) {
+    if (B <= p->B_cap && Np <= p->Np_cap) return FS_OK;
+    int nb = B > p->B_cap ? B : p->B_cap;
+    int nn = Np > p->Np_cap ? Np : p->Np_cap;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    free_workspace(p);
+    size_t nt = (size_t)p->ntiles;
+    if ((e = cudaMalloc(&p->parts, sizeof(fs::Particle) * nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->H, sizeof(double) * 7 * nt * nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->T, sizeof(double) * 7 * nt * nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->S, sizeof(double) * 7 * (size_t)nn * nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->Fpart, sizeof(double) * (size_t)nn * nb)) != cudaSuccess) {
+        free_workspace(p);
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    p->B_cap = nb;
+    p->Np_cap = nn;
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fs_last_error(void) { return g_err; }
+
+fs_status fs_constants(double* out) {
+    if (!out) return fail(FS_EINVAL, "fs_constants: out is NULL");
+    out[0] = fs::kMsunS;
+    out[1] = fs::kYearS;
+    out[2] = fs::kAuS;
+    out[3] = fs::kF0Ecc;
+    return FS_OK;
+}
+
+fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df, double T_obs, int mode,
+                         void* stream) {
+    g_err[0] = 0;
+    if (!out) return fail(FS_EINVAL, "fs_plan_create: out is NULL");
+    *out = nullptr;
+    if (n_bins <= 0 || !(f_min > 0.0) || !(df > 0.0) || !(T_obs > 0.0) || !isfinite(f_min) || !isfinite(df) ||
+        !isfinite(T_obs))
+        return fail(FS_EINVAL, "fs_plan_create: need n_bins > 0 and finite f_min, df, T_obs > 0");
+    if (mode != FS_FP64 && mode != FS_MIXED) return fail(FS_EINVAL, "fs_plan_create: unknown mode %d", mode);
+    if (mode == FS_MIXED) return fail(FS_EUNSUPPORTED, "fs_plan_create: FS_MIXED is not built yet");
+    if (n_bins > ((int64_t)1 << 40)) return fail(FS_EINVAL, "fs_plan_create: n_bins too large");
+    fs_plan* p = new (std::nothrow) fs_plan;
+    if (!p) return fail(FS_ENOMEM, "fs_plan_create: host allocation failed");
+    memset(p, 0, sizeof(*p));
+    p->grid.n = n_bins;
+    p->grid.f_min = f_min;
+    p->grid.df = df;
+    p->grid.T_obs = T_obs;
+    p->grid.alpha0 = 0.0;
+    p->grid.orient = 0.0;
+    p->mode = mode;
+    p->stream = (cudaStream_t)stream;
+    p->ntiles = (int)((n_bins + fs::kTile - 1) / fs::kTile);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    size_t bytes = sizeof(double) * (size_t)n_bins * fs::kNumTables;
+    if ((e = cudaMalloc(&p->tab_base, bytes)) != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaMalloc(tables)");
+    }
+    double* q = p->tab_base;
+    double** slots[fs::kNumTables] = {&p->tab.fh, &p->tab.fl, &p->tab.u, &p->tab.g0h, &p->tab.g0l,
+                                      &p->tab.e19, &p->tab.dwr, &p->tab.dwi, &p->tab.W};
+    for (int i = 0; i < fs::kNumTables; i++) *slots[i] = q + (size_t)i * n_bins;
+    if ((e = cudaMalloc(&p->edges_dev, sizeof(int64_t) * (fs::kNpMax + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->one_param, sizeof(fs_params))) != cudaSuccess ||
+        (e = cudaMalloc(&p->one_part, sizeof(fs::Particle))) != cudaSuccess ||
+        (e = cudaMalloc(&p->one_a, sizeof(double) * 4)) != cudaSuccess) {
+        fs_plan_destroy(p);
+        return cuda_fail(e, "cudaMalloc(plan)");
+    }
+    p->edges_cache = (int64_t*)malloc(sizeof(int64_t) * (fs::kNpMax + 1));
+    p->edges_np = 0;
+    p->prof = new std::vector<fs_plan::ProfRec>();
+    p->spare = new std::vector<cudaEvent_t>();
+    *out = p;
+    return FS_OK;
+}
+
+fs_status fs_plan_destroy(fs_plan* p) {
+    if (!p) return FS_OK;
+    cudaStreamSynchronize(p->stream);
+    free_workspace(p);
+    cudaFree(p->tab_base);
+    cudaFree(p->edges_dev);
+    cudaFree(p->one_param);
+    cudaFree(p->one_part);
+    cudaFree(p->one_a);
+    free(p->edges_cache);
+    if (p->prof) {
+        for (auto& r : *p->prof) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        delete p->prof;
+    }
+    if (p->spare) {
+        for (auto e : *p->spare) cudaEventDestroy(e);
+        delete p->spare;
+    }
+    delete p;
+    return FS_OK;
+}
+
+fs_status fs_plan_set_data(fs_plan* p, const double* data_dev, const double* psd_dev) {
+    g_err[0] = 0;
+    if (!p || !data_dev || !psd_dev) return fail(FS_EINVAL, "fs_plan_set_data: NULL argument");
+    ProfScope ps(p, 3);
+    cudaError_t e = fs::launch_precompute(p->grid, data_dev, psd_dev, p->tab, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
+    p->data_set = 1;
+    return FS_OK;
+}
+
+fs_status fs_plan_reserve(fs_plan* p, int B_max, int Np_max) {
+    g_err[0] = 0;
+    if (!p || B_max < 0 || Np_max < 1 || Np_max > fs::kNpMax)
+        return fail(FS_EINVAL, "fs_plan_reserve: need B_max >= 0 and 1 <= Np_max <= %d", fs::kNpMax);
+    return ensure_workspace(p, B_max > 0 ? B_max : 1, Np_max);
+}
+
+fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+                         double* F_dev, double* F_part_dev) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_fstat_batch: plan is NULL");
+    if (B < 0) return fail(FS_EINVAL, "fs_fstat_batch: B = %d < 0", B);
+    if (Np < 1 || Np > fs::kNpMax) return fail(FS_EINVAL, "fs_fstat_batch: N_p = %d not in [1, %d]", Np, fs::kNpMax);
+    if (B == 0) return FS_OK;
+    if (!params_dev || !F_dev) return fail(FS_EINVAL, "fs_fstat_batch: NULL params or F");
+    if (!p->data_set) return fail(FS_EINVAL, "fs_fstat_batch: fs_plan_set_data was not called");
+    int global = edges_host != nullptr;
+    if (global) {
+        for (int i = 0; i <= Np; i++) {
+            if (edges_host[i] < 0 || edges_host[i] > p->grid.n)
+                return fail(FS_EINVAL, "fs_fstat_batch: edge %d = %lld outside [0, n_bins]", i,
+                            (long long)edges_host[i]);
+            if (i > 0 && edges_host[i] < edges_host[i - 1])
+                return fail(FS_EINVAL, "fs_fstat_batch: edges must be non-decreasing");
+        }
+        if (edges_host[Np] == edges_host[0])
+            return fail(FS_EINVAL, "fs_fstat_batch: edges span no bins");
+    }
+    fs_status st = ensure_workspace(p, B, Np);
+    if (st != FS_OK) return st;
+    cudaError_t e;
+    if (global && (p->edges_np != Np || memcmp(p->edges_cache, edges_host, sizeof(int64_t) * (Np + 1)) != 0)) {
+        memcpy(p->edges_cache, edges_host, sizeof(int64_t) * (Np + 1));
+        p->edges_np = Np;
+        e = cudaMemcpyAsync(p->edges_dev, p->edges_cache, sizeof(int64_t) * (Np + 1), cudaMemcpyHostToDevice,
+                            p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(edges)");
+        // the host cache is rewritten only on a change; wait so a later change cannot race this copy
+        e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(edges)");
+    }
+    fs::Segs sg;
+    sg.Np = Np;
+    sg.global = global;
+    sg.edges = p->edges_dev;
+    fs::Partials pa;
+    pa.H = p->H;
+    pa.T = p->T;
+    pa.S = p->S;
+    pa.ntiles = p->ntiles;
+    double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
+    {
+        ProfScope ps(p, 0);
+        if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, global, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "setup launch");
+    }
+    {
+        ProfScope ps(p, 1);
+        if ((e = fs::launch_fp64_main(p->grid, p->tab, p->parts, B, sg, pa, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "fp64 main launch");
+    }
+    {
+        ProfScope ps(p, 2);
+        if ((e = fs::launch_reduce(p->grid, p->parts, B, sg, pa, Fpart, F_dev, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "reduce launch");
+    }
+    return FS_OK;
+}
+
+fs_status fs_particle_bands(fs_plan* p, const fs_params* params_dev, int B, int64_t* bands_dev) {
+    g_err[0] = 0;
+    if (!p || B < 0) return fail(FS_EINVAL, "fs_particle_bands: bad plan or B");
+    if (B == 0) return FS_OK;
+    if (!params_dev || !bands_dev) return fail(FS_EINVAL, "fs_particle_bands: NULL argument");
+    fs_status st = ensure_workspace(p, B, p->Np_cap > 0 ? p->Np_cap : 1);
+    if (st != FS_OK) return st;
+    cudaError_t e;
+    if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, 0, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "setup launch");
+    if ((e = fs::launch_bands(p->parts, B, bands_dev, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "bands launch");
+    return FS_OK;
+}
+
+fs_status fs_plan_set_profiling(fs_plan* p, int enable) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_plan_set_profiling: plan is NULL");
+    p->profiling = enable ? 1 : 0;
+    return FS_OK;
+}
+
+fs_status fs_plan_read_profile(fs_plan* p, int kind, double* total_ms, int64_t* launches) {
+    g_err[0] = 0;
+    if (!p || kind < 0 || kind >= kKinds || !total_ms || !launches)
+        return fail(FS_EINVAL, "fs_plan_read_profile: bad argument");
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    double tot = 0.0;
+    int64_t n = 0;
+    std::vector<fs_plan::ProfRec> keep;
+    for (auto& r : *p->prof) {
+        if (r.kind != kind) {
+            keep.push_back(r);
+            continue;
+        }
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, r.a, r.b)) != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        tot += ms;
+        n++;
+        p->spare->push_back(r.a);
+        p->spare->push_back(r.b);
+    }
+    *p->prof = keep;
+    *total_ms = tot;
+    *launches = n;
+    return FS_OK;
+}
+
+fs_status fs_add_signal(fs_plan* p, const fs_params* params_host, const double* a_host, double* data_dev) {
+    g_err[0] = 0;
+    if (!p || !params_host || !a_host || !data_dev) return fail(FS_EINVAL, "fs_add_signal: NULL argument");
+    if (!p->data_set) return fail(FS_EINVAL, "fs_add_signal: fs_plan_set_data was not called");
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(p->one_param, params_host, sizeof(fs_params), cudaMemcpyHostToDevice, p->stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(p->one_a, a_host, sizeof(double) * 4, cudaMemcpyHostToDevice, p->stream)) !=
+            cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(signal parameters)");
+    if ((e = fs::launch_setup(p->grid, p->one_param, 1, p->one_part, 0, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "setup launch");
+    if ((e = fs::launch_add_signal(p->grid, p->tab, p->one_part, p->one_a, data_dev, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "add_signal launch");
+    e = cudaStreamSynchronize(p->stream);   // the host arguments are pageable: finish before returning
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return FS_OK;
+}
+
+}  // extern "C"

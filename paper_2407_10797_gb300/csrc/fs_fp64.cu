@@ -1,0 +1,476 @@
+// fs_fp64.cu - per-dataset precompute, per-particle setup, the FP64 fused
+// template + segmented-reduction kernel and the per-segment 4x4 solve.
+//
+//   precompute (once per data set)      Sec. II.A Eq. inner_product, App. A Eq. A1
+//   setup (per particle)                App. A Eq. A3, Sec. II.B segment edges, Sec. IV t_f
+//   fp64_main (per particle x bin)      Sec. II.A Eqs. response, aandMN, aandMN2; Sec. IV Eq. freDres
+//   reduce (per particle x segment)     Sec. II.A Eq. coherent_F_stat, Sec. II.B Eq. semi-cohF
+#include <cfloat>
+#include <climits>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+// ---------------------------------------------------------------------------
+// A0: per-bin tables.  Templates are f^-7/6 e^{-i Psi}; the amplitude and the
+// noise weighting do not depend on the particle, so they are folded into the
+// data (dw) and into the weight W of the Gram matrix.
+// ---------------------------------------------------------------------------
+__global__ void precompute_kernel(Grid g, const double* __restrict__ data, const double* __restrict__ psd,
+                                  Tables t) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    // f_k = f_min + k df as a double-double
+    double p, e, s, s2;
+    two_prod((double)k, g.df, p, e);
+    two_sum(g.f_min, p, s, s2);
+    double fh, fl;
+    fast_two_sum(s, s2 + e, fh, fl);
+    double u = rcbrt(fh);
+    // f^-5/3 to double-double: y0 ~ u^5, then one Newton step on y^-3 = f^5
+    double y0 = u * u;
+    y0 = y0 * y0 * u;
+    double y2h, y2l, y3h, y3l, f2h, f2l, f4h, f4l, f5h, f5l, ph, pl;
+    dd_mul(y0, 0.0, y0, 0.0, y2h, y2l);
+    dd_mul(y2h, y2l, y0, 0.0, y3h, y3l);
+    dd_mul(fh, fl, fh, fl, f2h, f2l);
+    dd_mul(f2h, f2l, f2h, f2l, f4h, f4l);
+    dd_mul(f4h, f4l, fh, fl, f5h, f5l);
+    dd_mul(y3h, y3l, f5h, f5l, ph, pl);
+    double r = (1.0 - ph) - pl;
+    double gh, gl;
+    fast_two_sum(y0, y0 * r * (1.0 / 3.0), gh, gl);
+    double S = psd[k];
+    double w4 = 4.0 * g.df / S;
+    double amp = pow(fh, -7.0 / 6.0);
+    double u7 = u * u * u;
+    u7 = u7 * u7 * u;
+    t.fh[k] = fh;
+    t.fl[k] = fl;
+    t.u[k] = u;
+    t.g0h[k] = gh;
+    t.g0l[k] = gl;
+    t.e19[k] = pow(kF0Ecc / fh, 19.0 / 9.0);
+    t.dwr[k] = w4 * amp * data[2 * k];
+    t.dwi[k] = w4 * amp * data[2 * k + 1];
+    t.W[k] = w4 * u7;
+}
+
+cudaError_t launch_precompute(const Grid& g, const double* data, const double* psd, const Tables& t,
+                              cudaStream_t s) {
+    int threads = 256;
+    int64_t blocks = (g.n + threads - 1) / threads;
+    precompute_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, data, psd, t);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// A1: per-particle coefficients and band edges.
+// ---------------------------------------------------------------------------
+__device__ FreqPowers powers_of(double f) {
+    FreqPowers w;
+    w.u = rcbrt(f);
+    double u2 = w.u * w.u;
+    w.g0h = u2 * u2 * w.u;
+    w.e19 = pow(kF0Ecc / f, 19.0 / 9.0);
+    return w;
+}
+
+__device__ __forceinline__ double bin_freq(const Grid& g, int64_t k) {
+    // the same two roundings as f_min + (double)k * df without contraction
+    return __dadd_rn(g.f_min, __dmul_rn((double)k, g.df));
+}
+
+__global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int B, Particle* parts,
+                             int global) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    ::fs_params in = params[b];
+    Particle P;
+    memset(&P, 0, sizeof(P));
+    bool ok = isfinite(in.Mc) && isfinite(in.tc) && isfinite(in.lat) && isfinite(in.lon) &&
+              isfinite(in.e0) && isfinite(in.q) && in.Mc > 0.0 && in.q > 0.0;
+    P.valid = ok ? 1 : 0;
+    if (!ok) {
+        P.klo = 1;
+        P.khi = 0;
+        parts[b] = P;
+        return;
+    }
+    double eta = in.q / ((1.0 + in.q) * (1.0 + in.q));
+    // Mc in seconds (exact product as a double-double), x = pi Mc
+    double mh, ml;
+    two_prod(in.Mc, kMsunS, mh, ml);
+    double xh, xl;
+    dd_mul(kPi, kPiLo, mh, ml, xh, xl);
+    // y = x^-5/3 (double-double): Newton step on y^-3 = x^5
+    double y0 = pow(xh, -5.0 / 3.0);
+    double y2h, y2l, y3h, y3l, x2h, x2l, x4h, x4l, x5h, x5l, ph, pl;
+    dd_mul(y0, 0.0, y0, 0.0, y2h, y2l);
+    dd_mul(y2h, y2l, y0, 0.0, y3h, y3l);
+    dd_mul(xh, xl, xh, xl, x2h, x2l);
+    dd_mul(x2h, x2l, x2h, x2l, x4h, x4l);
+    dd_mul(x4h, x4l, xh, xl, x5h, x5l);
+    dd_mul(y3h, y3l, x5h, x5l, ph, pl);
+    double r = (1.0 - ph) - pl;
+    double yh, yl;
+    fast_two_sum(y0, y0 * r * (1.0 / 3.0), yh, yl);
+    // P0 = (3/256) y / pi   (Psi_PN/(2 pi) with (3/128)(pi Mc f)^-5/3 at leading order)
+    double ah, al;
+    dd_mul(3.0 / 256.0, 0.0, yh, yl, ah, al);
+    dd_mul(ah, al, kInvPi, kInvPiLo, P.P0h, P.P0l);
+    // PN coefficients alpha_k (non-spinning TaylorF2 to 2PN)
+    double a2 = 3715.0 / 756.0 + 55.0 * eta / 9.0;
+    double a3 = -16.0 * kPi;
+    double a4 = 15293365.0 / 508032.0 + 27145.0 * eta / 504.0 + 3085.0 * eta * eta / 72.0;
+    double M = mh * pow(eta, -0.6);
+    double v1 = cbrt(kPi * M);   // (pi M)^(1/3)
+    double P0 = P.P0h;
+    P.P2 = P0 * a2 * v1 * v1;
+    P.P3 = P0 * a3 * v1 * v1 * v1;
+    P.P4 = P0 * a4 * v1 * v1 * v1 * v1;
+    P.E0 = -(2355.0 / 1462.0) * in.e0 * in.e0 * P0;
+    // t(f) = dPhi/df: T_k = P_k (k - 5)/3, eccentric part -(34/9) E0 f^-8/3 (f0/f)^(19/9)
+    P.T0 = -(5.0 / 3.0) * P0;
+    P.T2 = -P.P2;
+    P.T3 = -(2.0 / 3.0) * P.P3;
+    P.T4 = -(1.0 / 3.0) * P.P4;
+    P.TE = -(34.0 / 9.0) * P.E0;
+    P.tc = in.tc;
+    // Doppler: d(t) = R sin(theta) cos(alpha - phi), theta = pi/2 - beta
+    double sb, cb, sl, cl;
+    sincos(in.lat, &sb, &cb);
+    sincos(in.lon, &sl, &cl);
+    P.AD = kAuS * cb;
+    P.clon = cl;
+    P.slon = sl;
+    // antenna: arm unit vectors u_nm = (dr_m - dr_n)/L of the rigid constellation,
+    // u = [k(dc C2 + ds S2 - 3 dc), k(dc S2 - ds C2 - 3 ds), -(dc C1 + ds S1)/2],
+    // k = 1/(4 sqrt 3), dc = cos b_m - cos b_n, ds = sin b_m - sin b_n, b_n = 2 pi n/3 + orient.
+    double cbn[3], sbn[3];
+    for (int n = 0; n < 3; n++) sincos(2.0 * kPi * n / 3.0 + g.orient, &sbn[n], &cbn[n]);
+    const double kap = 1.0 / (4.0 * sqrt(3.0));
+    double pv[3] = {sb * cl, sb * sl, -cb};   // theta-hat
+    double qv[3] = {-sl, cl, 0.0};            // phi-hat
+    for (int arm = 0; arm < 2; arm++) {
+        int m = arm + 1;
+        double dc = cbn[m] - cbn[0], ds = sbn[m] - sbn[0];
+        for (int j = 0; j < 2; j++) {
+            const double* w = j == 0 ? pv : qv;
+            double* c = P.pr[arm * 2 + j];
+            c[0] = -3.0 * kap * (dc * w[0] + ds * w[1]);
+            c[1] = -0.5 * dc * w[2];
+            c[2] = -0.5 * ds * w[2];
+            c[3] = kap * (dc * w[0] - ds * w[1]);
+            c[4] = kap * (ds * w[0] + dc * w[1]);
+        }
+    }
+    // band: first bin with t >= 0 and last bin with t <= T_obs (binary searches on k)
+    if (global) {
+        P.klo = 0;
+        P.khi = g.n - 1;
+    } else {
+        int64_t lo = 0, hi = g.n;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            double f = bin_freq(g, mid);
+            double t = time_of(P, powers_of(f));
+            if (t >= 0.0) hi = mid; else lo = mid + 1;
+        }
+        P.klo = lo;
+        lo = 0;
+        hi = g.n;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            double f = bin_freq(g, mid);
+            double t = time_of(P, powers_of(f));
+            if (t > g.T_obs) hi = mid; else lo = mid + 1;
+        }
+        P.khi = lo - 1;
+    }
+    parts[b] = P;
+}
+
+cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Particle* parts, int global,
+                         cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    int threads = 64;
+    setup_kernel<<<(B + threads - 1) / threads, threads, 0, s>>>(g, params, B, parts, global);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Segment helpers (device)
+// ---------------------------------------------------------------------------
+struct SegView {
+    int Np;
+    int global;
+    const int64_t* edges;
+    int64_t lo, hi;   // band [lo, hi] inclusive
+    __device__ int seg(int64_t k) const {
+        if (!global) return seg_of_bin(k, lo, hi, Np);
+        // largest p with edges[p] <= k (edges non-decreasing, k in [edges[0], edges[Np]))
+        int a = 0, b = Np;   // invariant: edges[a] <= k < edges[b]
+        while (b - a > 1) {
+            int m = (a + b) >> 1;
+            if (edges[m] <= k) a = m; else b = m;
+        }
+        return a;
+    }
+    // first bin of segment p (p = 0..Np)
+    __device__ int64_t start(int p) const {
+        if (global) return edges[p];
+        if (p >= Np) return hi + 1;
+        int64_t w = hi - lo;
+        if (w == 0) return p == 0 ? lo : hi + 1;
+        int64_t num = (int64_t)p * w;
+        return lo + (num + Np - 1) / Np;
+    }
+};
+
+__device__ __forceinline__ SegView seg_view(const Segs& sg, const Particle& P) {
+    SegView v;
+    v.Np = sg.Np;
+    v.global = sg.global;
+    v.edges = sg.edges;
+    if (sg.global) {
+        v.lo = sg.edges[0];
+        v.hi = sg.edges[sg.Np] - 1;
+    } else {
+        v.lo = P.klo;
+        v.hi = P.khi;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// A2-A4 (FP64): one warp per (particle, tile); lanes stride over the bins.
+// Each bin: phase, t(f), response, z = dw e^{+2 pi i Phi}; accumulate
+//   X+ = sum F+ z, Xx = sum Fx z, P = sum W F+^2, Q = sum W F+ Fx, R = sum W Fx^2
+// per segment.  The first segment touched in the tile goes to H, the last to
+// T, segments that start and end inside the tile go straight to S.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.y * kWarpsPerCta + (threadIdx.x >> 5);
+    const int tile = blockIdx.x;
+    if (b >= B) return;
+    const Particle P = parts[b];
+    if (!P.valid) return;
+    const SegView sv = seg_view(sg, P);
+    int64_t lo = (int64_t)tile * kTile, hi = lo + kTile;
+    if (lo < sv.lo) lo = sv.lo;
+    if (hi > sv.hi + 1) hi = sv.hi + 1;
+    if (lo >= hi) return;
+    const int64_t slot = (int64_t)b * pa.ntiles + tile;
+
+    double acc[7];
+#pragma unroll
+    for (int c = 0; c < 7; c++) acc[c] = 0.0;
+    int cur = sv.seg(lo);
+    int nflush = 0;
+
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t k = base + lane;
+        const bool valid = k < hi;
+        int pk = INT_MAX;
+        double t7[7];
+#pragma unroll
+        for (int c = 0; c < 7; c++) t7[c] = 0.0;
+        if (valid) {
+            pk = sv.seg(k);
+            FreqPowers w;
+            w.u = tb.u[k];
+            w.g0h = tb.g0h[k];
+            w.e19 = tb.e19[k];
+            BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
+            double sn, cs;
+            sincospi(2.0 * ev.frac, &sn, &cs);
+            double dr = tb.dwr[k], di = tb.dwi[k], W = tb.W[k];
+            double zr = fma(dr, cs, -di * sn);
+            double zi = fma(dr, sn, di * cs);
+            t7[0] = ev.Fp * zr;
+            t7[1] = ev.Fp * zi;
+            t7[2] = ev.Fx * zr;
+            t7[3] = ev.Fx * zi;
+            double wp = W * ev.Fp;
+            t7[4] = wp * ev.Fp;
+            t7[5] = wp * ev.Fx;
+            t7[6] = W * ev.Fx * ev.Fx;
+        }
+        while (true) {
+            if (valid && pk == cur) {
+#pragma unroll
+                for (int c = 0; c < 7; c++) acc[c] += t7[c];
+            }
+            unsigned more = __ballot_sync(0xffffffffu, valid && pk > cur);
+            if (!more) break;
+            // segment `cur` ends inside this tile: flush it
+            double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
+#pragma unroll
+            for (int c = 0; c < 7; c++) {
+                double v = warp_sum(acc[c]);
+                if (lane == 0) dst[c] = v;
+                acc[c] = 0.0;
+            }
+            nflush++;
+            int cand = (valid && pk > cur) ? pk : INT_MAX;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+            cur = cand;
+        }
+    }
+    double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
+#pragma unroll
+    for (int c = 0; c < 7; c++) {
+        double v = warp_sum(acc[c]);
+        if (lane == 0) dst[c] = v;
+    }
+}
+
+cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
+                             const Partials& pa, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    dim3 grid((unsigned)pa.ntiles, (unsigned)((B + kWarpsPerCta - 1) / kWarpsPerCta));
+    fp64_main_kernel<<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// A5: per-(particle, segment) sums over the tiles the segment spans, then
+//   F_p = [R |X+|^2 - 2 Q Re(X+ conj Xx) + P |Xx|^2] / (2 (P R - Q^2))
+// which is 1/2 N^T M^-1 N for M = diag(K, K), K = [[P, Q], [Q, R]],
+// N = (Re X+, Re Xx, -Im X+, -Im Xx).
+// ---------------------------------------------------------------------------
+__global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
+                              double* Fpart) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= (int64_t)B * sg.Np) return;
+    const int b = (int)(wid / sg.Np);
+    const int p = (int)(wid % sg.Np);
+    const Particle& P = parts[b];
+    if (!P.valid) {
+        if (lane == 0) Fpart[wid] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    const SegView sv = seg_view(sg, P);
+    double acc[7];
+#pragma unroll
+    for (int c = 0; c < 7; c++) acc[c] = 0.0;
+    int64_t s0 = 0, s1 = 0;
+    if (sv.lo <= sv.hi) {
+        s0 = sv.start(p);
+        s1 = sv.start(p + 1);
+    }
+    const int64_t nb = s1 > s0 ? s1 - s0 : 0;
+    if (nb > 0) {
+        const int64_t t0 = s0 / kTile, t1 = (s1 - 1) / kTile;
+        for (int64_t t = t0 + lane; t <= t1; t += 32) {
+            int64_t tlo = t * kTile, thi = tlo + kTile - 1;
+            if (tlo < sv.lo) tlo = sv.lo;
+            if (thi > sv.hi) thi = sv.hi;
+            const int pf = sv.seg(tlo), pl = sv.seg(thi);
+            const double* src;
+            if (p == pf) src = pa.H + ((int64_t)b * pa.ntiles + t) * 7;
+            else if (p == pl) src = pa.T + ((int64_t)b * pa.ntiles + t) * 7;
+            else src = pa.S + ((int64_t)b * sg.Np + p) * 7;
+#pragma unroll
+            for (int c = 0; c < 7; c++) acc[c] += src[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 7; c++) acc[c] = warp_sum(acc[c]);
+    if (lane == 0) {
+        double Xpr = acc[0], Xpi = acc[1], Xxr = acc[2], Xxi = acc[3];
+        double Pp = acc[4], Qq = acc[5], Rr = acc[6];
+        double det = Pp * Rr - Qq * Qq;
+        double F = 0.0;
+        if (nb >= 4 && det > 1e-12 * Pp * Rr) {
+            double num = Rr * (Xpr * Xpr + Xpi * Xpi) - 2.0 * Qq * (Xpr * Xxr + Xpi * Xxi) +
+                         Pp * (Xxr * Xxr + Xxi * Xxi);
+            F = 0.5 * num / det;
+        }
+        Fpart[wid] = F;
+    }
+}
+
+__global__ void sum_segments_kernel(const Particle* __restrict__ parts, int B, int Np, const double* Fpart,
+                                    double* F) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int p = lane; p < Np; p += 32) s += Fpart[b * Np + p];
+    s = warp_sum(s);
+    if (lane == 0) F[b] = parts[b].valid ? s : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
+                          double* Fpart, double* F, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    const int threads = 256;
+    int64_t warps = (int64_t)B * sg.Np;
+    int64_t blocks = (warps * 32 + threads - 1) / threads;
+    reduce_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t blocks2 = ((int64_t)B * 32 + threads - 1) / threads;
+    sum_segments_kernel<<<(unsigned)blocks2, threads, 0, s>>>(parts, B, sg.Np, Fpart, F);
+    return cudaGetLastError();
+}
+
+__global__ void bands_kernel(const Particle* __restrict__ parts, int B, int64_t* bands) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    bands[2 * b] = parts[b].klo;
+    bands[2 * b + 1] = parts[b].khi;
+}
+
+cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    bands_kernel<<<(B + 127) / 128, 128, 0, s>>>(parts, B, bands);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Signal synthesis: data += sum_i a_i A^i over the particle's band (FP64).
+// ---------------------------------------------------------------------------
+__global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict__ part, const double* a,
+                                  double* data) {
+    const Particle P = *part;
+    if (!P.valid) return;
+    int64_t k = P.klo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > P.khi) return;
+    FreqPowers w;
+    w.u = tb.u[k];
+    w.g0h = tb.g0h[k];
+    w.e19 = tb.e19[k];
+    BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
+    double sn, cs;
+    sincospi(2.0 * ev.frac, &sn, &cs);
+    double amp = pow(tb.fh[k], -7.0 / 6.0);
+    double c = a[0] * ev.Fp + a[1] * ev.Fx;   // coefficient of h0
+    double s = a[2] * ev.Fp + a[3] * ev.Fx;   // coefficient of -i h0
+    // (c - i s) (cos - i sin) * amp
+    data[2 * k] += amp * (c * cs - s * sn);
+    data[2 * k + 1] += amp * (-c * sn - s * cs);
+}
+
+cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,
+                              double* data, cudaStream_t s) {
+    int threads = 256;
+    int64_t blocks = (g.n + threads - 1) / threads;
+    add_signal_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data);
+    return cudaGetLastError();
+}
+
+}  // namespace fs

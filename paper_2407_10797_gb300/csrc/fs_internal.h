@@ -1,0 +1,63 @@
+// fs_internal.h - plan layout and kernel launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fs_common.cuh"
+#include "fstat.h"
+
+namespace fs {
+
+constexpr int kTile = 2048;          // bins per (particle, tile) work item of the FP64 kernel
+constexpr int kWarpsPerCta = 8;      // particles per CTA of the FP64 kernel
+constexpr int kNpMax = 4096;
+
+// Per-bin tables (structure of arrays, length n).
+struct Tables {
+    double* fh;    // f_k, double-double head
+    double* fl;    // f_k, double-double tail
+    double* u;     // f^-1/3
+    double* g0h;   // f^-5/3 head
+    double* g0l;   // f^-5/3 tail
+    double* e19;   // (f0/f)^(19/9)
+    double* dwr;   // Re 4 df d_k f^-7/6 / S_k
+    double* dwi;   // Im of the same
+    double* W;     // 4 df f^-7/3 / S_k
+};
+constexpr int kNumTables = 9;
+
+struct Grid {
+    int64_t n;
+    double f_min, df, T_obs;
+    double alpha0, orient;   // detector orbital phase and orientation at t = 0
+};
+
+// Segment description for one batch.
+struct Segs {
+    int Np;
+    int global;               // 1: edges[] apply to every particle
+    const int64_t* edges;     // device, Np+1 (global mode only)
+};
+
+struct Partials {
+    double* H;    // [B][ntiles][7] first segment of each (particle, tile)
+    double* T;    // [B][ntiles][7] last segment of each (particle, tile)
+    double* S;    // [B][Np][7] segments complete inside one tile
+    int ntiles;
+};
+
+cudaError_t launch_precompute(const Grid& g, const double* data, const double* psd, const Tables& t,
+                              cudaStream_t s);
+cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Particle* parts, int global,
+                         cudaStream_t s);
+cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
+                             const Partials& pa, cudaStream_t s);
+cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
+                          double* Fpart, double* F, cudaStream_t s);
+cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);
+cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,
+                              double* data, cudaStream_t s);
+
+}  // namespace fs

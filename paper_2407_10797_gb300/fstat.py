@@ -1,0 +1,201 @@
+"""Thin ctypes binding of the C ABI in include/fstat.h.
+
+Argument marshalling only: every step of the F-statistic path runs in the
+library's CUDA kernels.  PyTorch provides device memory and the stream; the
+binding passes raw device pointers.  There is no CPU fallback: if the shared
+library cannot be loaded, or a tensor is not on a CUDA device, the call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FS_OK, FS_EINVAL, FS_ECUDA, FS_ENOMEM, FS_ETIMEOUT, FS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+FS_FP64, FS_MIXED = 0, 1
+_STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ECUDA", -3: "FS_ENOMEM", -4: "FS_ETIMEOUT",
+           -5: "FS_EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FstatError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fs_params(C.Structure):
+    _fields_ = [("Mc", C.c_double), ("tc", C.c_double), ("lat", C.c_double), ("lon", C.c_double),
+                ("e0", C.c_double), ("q", C.c_double)]
+
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libfs_gb300.so (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+        L = C.CDLL(_build.LIB)
+        L.fs_plan_create.argtypes = [C.POINTER(_vp), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int, _vp]
+        L.fs_plan_destroy.argtypes = [_vp]
+        L.fs_plan_set_data.argtypes = [_vp, _vp, _vp]
+        L.fs_plan_reserve.argtypes = [_vp, C.c_int, C.c_int]
+        L.fs_fstat_batch.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp]
+        L.fs_add_signal.argtypes = [_vp, C.POINTER(fs_params), _dp, _vp]
+        L.fs_constants.argtypes = [_dp]
+        L.fs_particle_bands.argtypes = [_vp, _vp, C.c_int, _vp]
+        L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
+        L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
+        L.fs_last_error.restype = C.c_char_p
+        for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
+                     "fs_fstat_batch", "fs_add_signal", "fs_constants", "fs_particle_bands",
+                     "fs_plan_set_profiling", "fs_plan_read_profile"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(st: int):
+    if st != FS_OK:
+        raise FstatError(st, load().fs_last_error().decode())
+
+
+def constants() -> np.ndarray:
+    out = np.zeros(4)
+    _check(load().fs_constants(out.ctypes.data_as(_dp)))
+    return out
+
+
+def _cuda_ptr(t, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """One frequency grid + precision mode; wraps fs_plan."""
+
+    def __init__(self, n_bins: int, f_min: float, df: float, T_obs: float, mode: int = FS_FP64, stream=None):
+        import torch
+        L = load()
+        self._L = L
+        self.n = int(n_bins)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(L.fs_plan_create(C.byref(h), self.n, float(f_min), float(df), float(T_obs), int(mode),
+                                _stream_handle(self.stream)))
+        self._h = h
+
+    @classmethod
+    def from_grid(cls, grid, mode: int = FS_FP64, stream=None) -> "Plan":
+        return cls(grid.n, grid.f_min, grid.df, grid.T_obs, mode, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.fs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, data, psd):
+        """data: complex128 CUDA tensor [n] (or float64 [n, 2]); psd: float64 CUDA tensor [n]."""
+        import torch
+        if data.dtype == torch.complex128:
+            data = torch.view_as_real(data)
+        if data.shape != (self.n, 2) or psd.shape != (self.n,):
+            raise ValueError("data must be [n] complex and psd [n]")
+        # keep the inputs alive until the stream has consumed them
+        self._data_keep = data.contiguous()
+        self._psd_keep = psd.contiguous()
+        _check(self._L.fs_plan_set_data(self._h, _cuda_ptr(self._data_keep, torch.float64),
+                                        _cuda_ptr(self._psd_keep, torch.float64)))
+
+    def reserve(self, B_max: int, Np_max: int):
+        _check(self._L.fs_plan_reserve(self._h, int(B_max), int(Np_max)))
+
+    def fstat(self, params, Np: int, edges=None, F=None, F_part=None, want_parts: bool = True):
+        """Semi-coherent F for params (float64 CUDA tensor [B, 6]: Mc, tc, lat, lon, e0, q).
+        Returns (F [B], F_part [B, Np] or None) as CUDA tensors."""
+        import torch
+        if params.dim() != 2 or params.shape[1] != 6:
+            raise ValueError("params must be [B, 6]")
+        B = params.shape[0]
+        dev = params.device
+        if F is None:
+            F = torch.empty(B, dtype=torch.float64, device=dev)
+        if want_parts and F_part is None:
+            F_part = torch.empty(B, Np, dtype=torch.float64, device=dev)
+        e = None
+        if edges is not None:
+            arr = np.ascontiguousarray(edges, dtype=np.int64)
+            if arr.shape != (Np + 1,):
+                raise ValueError("edges must have N_p + 1 entries")
+            e = arr.ctypes.data_as(C.POINTER(C.c_int64))
+        _check(self._L.fs_fstat_batch(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(B), e, int(Np),
+                                      _cuda_ptr(F, torch.float64),
+                                      _cuda_ptr(F_part, torch.float64) if F_part is not None else None))
+        return F, F_part
+
+    def bands(self, params, out=None):
+        """Per-particle (first, last) in-band bin, int64 CUDA tensor [B, 2]."""
+        import torch
+        B = params.shape[0]
+        if out is None:
+            out = torch.empty(B, 2, dtype=torch.int64, device=params.device)
+        _check(self._L.fs_particle_bands(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(B),
+                                         _cuda_ptr(out, torch.int64)))
+        return out
+
+    KERNELS = {"setup": 0, "main": 1, "reduce": 2, "precompute": 3}
+
+    def set_profiling(self, enable: bool):
+        _check(self._L.fs_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def read_profile(self, kernel: str) -> tuple[float, int]:
+        """(summed ms, launches) of one kernel kind since the last read; waits for the stream."""
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(self._L.fs_plan_read_profile(self._h, self.KERNELS[kernel], C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def add_signal(self, p, a, data):
+        """data += sum_i a_i A^i(p) over the particle's band (data: complex128 CUDA tensor)."""
+        import torch
+        if data.dtype == torch.complex128:
+            view = torch.view_as_real(data)
+        else:
+            view = data
+        pp = fs_params(*[float(x) for x in np.asarray(p, dtype=np.float64)[:6]])
+        aa = np.ascontiguousarray(a, dtype=np.float64)
+        _check(self._L.fs_add_signal(self._h, C.byref(pp), aa.ctypes.data_as(_dp), _cuda_ptr(view, torch.float64)))
+        return data
