@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one small evaluation for kernel profiling: paper grid, 64 particles, N_p = 16")
     return ap.parse_args()
 
 
@@ -380,8 +382,27 @@ def run_gpu(args, world, rank, local):
     return out
 
 
+def run_profile_case(args):
+    """Paper-scale grid (tables 227 MB > L2), 64 particles, one N_p = 16 launch
+    after one warm-up launch: a short capture target for kernel profilers."""
+    import torch
+    from paper_2407_10797_gb300 import fstat
+    w, g, psd, noise, P, inj = workload_inputs(0)
+    plan = fstat.Plan.from_grid(g, mode=fstat.FS_FP64)
+    plan.set_data(torch.from_numpy(noise).cuda(), torch.from_numpy(psd).cuda())
+    P_dev = torch.from_numpy(P[:64]).cuda()
+    for _ in range(2):
+        F, _ = plan.fstat(P_dev, 16, want_parts=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "paper grid, B=64, N_p=16", "F_mean": float(F.mean().item())}))
+    plan.close()
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -80,7 +80,8 @@ def test_fp64_per_particle_segments_small(fst, Np):
     at different bins; injection + noise."""
     g = S.tiny_grid(n=5000, f_min=0.02, stride=16)
     P = in_band_params(g, 37, 5, 0.02 + 2500 * g.df, spread=(-0.3, 1.3))
-    d, psd = make_data(g, 3, inj=P[0])
+    inj = in_band_params(g, 1, 6, 0.02 + 2500 * g.df, spread=(0.5, 0.5))[0]
+    d, psd = make_data(g, 3, inj=inj)
     Fg, Fpg = run_gpu(fst, g, d, psd, P, Np)
     Fo, Fpo = O.fstat_batch(P, O.OracleModel.from_grid(g), d, psd, Np)
     assert np.any(Fo > 0) and np.any(Fo == 0)   # some particles have no band at all
