@@ -37,6 +37,8 @@
  *     e_p <= f_k < e_{p+1} (last segment closed).
  *   - a segment with fewer than 4 bins, or with M11 M22 - M12^2 <= 1e-12 M11 M22,
  *     contributes F_p = 0.
+ *   - the Gram sums and the 4x4 solve are carried in long double (see
+ *     or_segment_sums_ld: short segments make M nearly singular).
  *   - the library returns the SUM over segments; F-hat = sum / N_seg.
  */
 #include <math.h>
@@ -114,8 +116,6 @@ static long double or_phase_orb_cycles(const or_params* P, const or_model* m, lo
     long double eta = (long double)or_eta(P->q);
     long double Mc = (long double)P->Mc * (long double)OR_MSUN_S;
     long double M = Mc * powl(eta, -0.6L);
-    double ad[5];
-    or_alpha((double)eta, m->pn_order, ad);
     long double a[5];
     a[0] = 1.0L;
     a[1] = 0.0L;
@@ -123,7 +123,6 @@ static long double or_phase_orb_cycles(const or_params* P, const or_model* m, lo
     a[3] = -16.0L * OR_PI_L;
     a[4] = 15293365.0L / 508032.0L + 27145.0L * eta / 504.0L + 3085.0L * eta * eta / 72.0L;
     for (int k = m->pn_order + 1; k < 5; k++) a[k] = 0.0L;
-    (void)ad;
     long double v = cbrtl(OR_PI_L * M * f);
     long double lead = (3.0L / 128.0L) * powl(OR_PI_L * Mc * f, -5.0L / 3.0L);
     long double s = 0.0L, vk = 1.0L;
@@ -318,10 +317,14 @@ static void or_segment_starts(const or_params* P, const or_model* m, const int64
 }
 
 /* Per-segment N^i = <d, A^i> and M^ij = <A^i, A^j> (Eqs. aandMN, aandMN2)
- * with the segment inner product <a,b>_l = 4 df Re sum_k a_k conj(b_k)/S_k. */
-void or_segment_sums(const or_params* P, const or_model* m, const double* d_re, const double* d_im,
-                     const double* psd, const int64_t* edges, int Np, double* Nout /*[Np][4]*/,
-                     double* Mout /*[Np][16]*/, int64_t* nbins /*[Np]*/) {
+ * with the segment inner product <a,b>_l = 4 df Re sum_k a_k conj(b_k)/S_k.
+ * Products and sums are formed in long double: on short segments F+ and Fx
+ * are nearly proportional and M is close to singular (M11 M22 - M12^2 down
+ * to ~1e-10 M11 M22), so the Gram sums need more than FP64 precision for
+ * F_p to be reliable to 1e-9. */
+static void or_segment_sums_ld(const or_params* P, const or_model* m, const double* d_re, const double* d_im,
+                               const double* psd, const int64_t* edges, int Np, long double* Nout,
+                               long double* Mout, int64_t* nbins) {
     int64_t* starts = (int64_t*)malloc(sizeof(int64_t) * (Np + 1));
     or_segment_starts(P, m, edges, Np, starts);
     for (int p = 0; p < Np; p++) {
@@ -329,59 +332,81 @@ void or_segment_sums(const or_params* P, const or_model* m, const double* d_re, 
         if (k1 < k0) k1 = k0;
         int64_t n = k1 - k0;
         nbins[p] = n;
-        double N[4] = {0, 0, 0, 0}, M[16];
-        memset(M, 0, sizeof(M));
+        long double N[4] = {0, 0, 0, 0}, M[16];
+        for (int i = 0; i < 16; i++) M[i] = 0.0L;
         if (n > 0) {
             double* re = (double*)malloc(sizeof(double) * 4 * n);
             double* im = (double*)malloc(sizeof(double) * 4 * n);
             or_basis(P, m, k0, k1, re, im);
             for (int64_t j = 0; j < n; j++) {
                 int64_t k = k0 + j;
-                double w = 4.0 * m->df / psd[k];
+                long double w = 4.0L * (long double)m->df / (long double)psd[k];
+                long double dr = d_re[k], di = d_im[k];
                 for (int i = 0; i < 4; i++) {
+                    long double ar = re[i * n + j], ai = im[i * n + j];
                     /* Re(d conj(A)) = d_re A_re + d_im A_im */
-                    N[i] += w * (d_re[k] * re[i * n + j] + d_im[k] * im[i * n + j]);
+                    N[i] += w * (dr * ar + di * ai);
                     for (int l = 0; l < 4; l++)
-                        M[i * 4 + l] += w * (re[i * n + j] * re[l * n + j] + im[i * n + j] * im[l * n + j]);
+                        M[i * 4 + l] += w * (ar * (long double)re[l * n + j] + ai * (long double)im[l * n + j]);
                 }
             }
             free(re);
             free(im);
         }
-        memcpy(Nout + 4 * p, N, sizeof(N));
-        memcpy(Mout + 16 * p, M, sizeof(M));
+        for (int i = 0; i < 4; i++) Nout[4 * p + i] = N[i];
+        for (int i = 0; i < 16; i++) Mout[16 * p + i] = M[i];
     }
     free(starts);
 }
 
-/* F_p = 1/2 N^T M^-1 N by Cholesky factorisation of the 4x4 M; the
- * degenerate-segment rule returns 0. */
-double or_segment_F(const double* N, const double* M, int64_t nbins) {
-    if (nbins < 4) return 0.0;
-    double m11 = M[0], m12 = M[1], m22 = M[5];
-    if (m11 * m22 - m12 * m12 <= 1e-12 * m11 * m22) return 0.0;
-    double L[4][4];
-    memset(L, 0, sizeof(L));
+void or_segment_sums(const or_params* P, const or_model* m, const double* d_re, const double* d_im,
+                     const double* psd, const int64_t* edges, int Np, double* Nout /*[Np][4]*/,
+                     double* Mout /*[Np][16]*/, int64_t* nbins /*[Np]*/) {
+    long double* N = (long double*)malloc(sizeof(long double) * 4 * Np);
+    long double* M = (long double*)malloc(sizeof(long double) * 16 * Np);
+    or_segment_sums_ld(P, m, d_re, d_im, psd, edges, Np, N, M, nbins);
+    for (int i = 0; i < 4 * Np; i++) Nout[i] = (double)N[i];
+    for (int i = 0; i < 16 * Np; i++) Mout[i] = (double)M[i];
+    free(N);
+    free(M);
+}
+
+/* F_p = 1/2 N^T M^-1 N by Cholesky factorisation of the 4x4 M (long double);
+ * the degenerate-segment rule returns 0. */
+static long double or_segment_F_ld(const long double* N, const long double* M, int64_t nbins) {
+    if (nbins < 4) return 0.0L;
+    long double m11 = M[0], m12 = M[1], m22 = M[5];
+    if (m11 * m22 - m12 * m12 <= 1e-12L * m11 * m22) return 0.0L;
+    long double L[4][4];
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) L[i][j] = 0.0L;
     for (int i = 0; i < 4; i++) {
         for (int j = 0; j <= i; j++) {
-            double s = M[i * 4 + j];
+            long double s = M[i * 4 + j];
             for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k];
             if (i == j) {
-                if (!(s > 0.0)) return 0.0;
-                L[i][i] = sqrt(s);
+                if (!(s > 0.0L)) return 0.0L;
+                L[i][i] = sqrtl(s);
             } else {
                 L[i][j] = s / L[j][j];
             }
         }
     }
     /* solve L y = N; then N^T M^-1 N = y . y */
-    double y[4];
+    long double y[4];
     for (int i = 0; i < 4; i++) {
-        double s = N[i];
+        long double s = N[i];
         for (int k = 0; k < i; k++) s -= L[i][k] * y[k];
         y[i] = s / L[i][i];
     }
-    return 0.5 * (y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+    return 0.5L * (y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+}
+
+double or_segment_F(const double* N, const double* M, int64_t nbins) {
+    long double Nl[4], Ml[16];
+    for (int i = 0; i < 4; i++) Nl[i] = N[i];
+    for (int i = 0; i < 16; i++) Ml[i] = M[i];
+    return (double)or_segment_F_ld(Nl, Ml, nbins);
 }
 
 /* Batched semi-coherent F: F[b] = sum_p F_p (the paper's F-hat is F[b]/Np),
@@ -397,23 +422,23 @@ int or_fstat_batch(const or_params* params, int B, const or_model* m, const doub
 #endif
     for (int b = 0; b < B; b++) {
         const or_params* P = params + b;
-        double* Nb = (double*)malloc(sizeof(double) * 4 * Np);
-        double* Mb = (double*)malloc(sizeof(double) * 16 * Np);
+        long double* Nb = (long double*)malloc(sizeof(long double) * 4 * Np);
+        long double* Mb = (long double*)malloc(sizeof(long double) * 16 * Np);
         int64_t* nb = (int64_t*)malloc(sizeof(int64_t) * Np);
-        double tot = 0.0;
+        long double tot = 0.0L;
         if (!or_params_finite(P)) {
             tot = NAN;
             if (Fpart)
                 for (int p = 0; p < Np; p++) Fpart[(int64_t)b * Np + p] = NAN;
         } else {
-            or_segment_sums(P, m, d_re, d_im, psd, edges, Np, Nb, Mb, nb);
+            or_segment_sums_ld(P, m, d_re, d_im, psd, edges, Np, Nb, Mb, nb);
             for (int p = 0; p < Np; p++) {
-                double Fp = or_segment_F(Nb + 4 * p, Mb + 16 * p, nb[p]);
-                if (Fpart) Fpart[(int64_t)b * Np + p] = Fp;
+                long double Fp = or_segment_F_ld(Nb + 4 * p, Mb + 16 * p, nb[p]);
+                if (Fpart) Fpart[(int64_t)b * Np + p] = (double)Fp;
                 tot += Fp;
             }
         }
-        F[b] = tot;
+        F[b] = (double)tot;
         free(Nb);
         free(Mb);
         free(nb);

@@ -43,6 +43,7 @@ struct fs_plan {
     double* T;
     double* S;
     double* Fpart;
+    double2* rot;
     int ntiles;
     // segment edges (global mode)
     int64_t* edges_dev;
@@ -107,7 +108,9 @@ void free_workspace(fs_plan* p) {
     cudaFree(p->T);
     cudaFree(p->S);
     cudaFree(p->Fpart);
+    cudaFree(p->rot);
     p->parts = nullptr;
+    p->rot = nullptr;
     p->H = p->T = p->S = p->Fpart = nullptr;
     p->B_cap = p->Np_cap = 0;
 }
@@ -124,7 +127,8 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
         (e = cudaMalloc(&p->H, sizeof(double) * 7 * nt * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->T, sizeof(double) * 7 * nt * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->S, sizeof(double) * 7 * (size_t)nn * nb)) != cudaSuccess ||
-        (e = cudaMalloc(&p->Fpart, sizeof(double) * (size_t)nn * nb)) != cudaSuccess) {
+        (e = cudaMalloc(&p->Fpart, sizeof(double) * (size_t)nn * nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess) {
         free_workspace(p);
         return cuda_fail(e, "cudaMalloc(workspace)");
     }
@@ -284,12 +288,15 @@ fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const i
     pa.H = p->H;
     pa.T = p->T;
     pa.S = p->S;
+    pa.rot = p->rot;
     pa.ntiles = p->ntiles;
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
     {
         ProfScope ps(p, 0);
         if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, global, p->stream)) != cudaSuccess)
             return cuda_fail(e, "setup launch");
+        if ((e = fs::launch_rotation(p->grid, p->parts, B, sg, p->rot, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "rotation launch");
     }
     {
         ProfScope ps(p, 1);

@@ -251,13 +251,58 @@ __device__ __forceinline__ double warp_sum(double x) {
 }
 
 // ---------------------------------------------------------------------------
+// Per-segment antenna basis.  F_p is invariant under any invertible change of
+// the amplitude basis (Eq. coherent_F_stat), so each segment uses
+//   G1 = c F+ + s Fx,  G2 = c Fx - s F+,  (c, s) = F(t_mid)/|F(t_mid)|
+// taken at the segment's central bin.  On a short segment F+ and Fx are nearly
+// proportional and the Gram matrix of (F+, Fx) is close to singular; in the
+// rotated basis G2 is small but computed directly, and the Gram matrix of
+// (G1, G2) is well conditioned, so FP64 sums keep F_p accurate.
+// ---------------------------------------------------------------------------
+__global__ void rotation_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, double2* rot) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * sg.Np) return;
+    const int b = (int)(i / sg.Np);
+    const int p = (int)(i % sg.Np);
+    const Particle& P = parts[b];
+    double2 r = make_double2(1.0, 0.0);
+    if (P.valid) {
+        const SegView sv = seg_view(sg, P);
+        if (sv.lo <= sv.hi) {
+            int64_t s0 = sv.start(p), s1 = sv.start(p + 1);
+            if (s1 > s0) {
+                int64_t mid = s0 + (s1 - 1 - s0) / 2;
+                double f = bin_freq(g, mid);
+                double t = time_of(P, powers_of(f));
+                double sn, cs;
+                sincos(fma(kTwoPi / kYearS, t, g.alpha0), &sn, &cs);
+                double Fp, Fx;
+                antenna_of(P, cs, sn, Fp, Fx);
+                double nrm = sqrt(Fp * Fp + Fx * Fx);
+                if (nrm > 1e-300) r = make_double2(Fp / nrm, Fx / nrm);
+            }
+        }
+    }
+    rot[i] = r;
+}
+
+cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const Segs& sg, double2* rot,
+                            cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    int64_t n = (int64_t)B * sg.Np;
+    rotation_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, parts, B, sg, rot);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // A2-A4 (FP64): one warp per (particle, tile); lanes stride over the bins.
-// Each bin: phase, t(f), response, z = dw e^{+2 pi i Phi}; accumulate
-//   X+ = sum F+ z, Xx = sum Fx z, P = sum W F+^2, Q = sum W F+ Fx, R = sum W Fx^2
+// Each bin: phase, t(f), response, z = dw e^{+2 pi i Phi}; accumulate, in the
+// segment's rotated antenna basis (G1, G2),
+//   X1 = sum G1 z, X2 = sum G2 z, K11 = sum W G1^2, K12 = sum W G1 G2, K22 = sum W G2^2
 // per segment.  The first segment touched in the tile goes to H, the last to
 // T, segments that start and end inside the tile go straight to S.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 1)
 fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa) {
     const int lane = threadIdx.x & 31;
     const int b = blockIdx.y * kWarpsPerCta + (threadIdx.x >> 5);
@@ -294,17 +339,20 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
             BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
             double sn, cs;
             sincospi(2.0 * ev.frac, &sn, &cs);
+            const double2 rc = pa.rot[(int64_t)b * sg.Np + pk];
+            const double G1 = fma(rc.x, ev.Fp, rc.y * ev.Fx);
+            const double G2 = fma(rc.x, ev.Fx, -rc.y * ev.Fp);
             double dr = tb.dwr[k], di = tb.dwi[k], W = tb.W[k];
             double zr = fma(dr, cs, -di * sn);
             double zi = fma(dr, sn, di * cs);
-            t7[0] = ev.Fp * zr;
-            t7[1] = ev.Fp * zi;
-            t7[2] = ev.Fx * zr;
-            t7[3] = ev.Fx * zi;
-            double wp = W * ev.Fp;
-            t7[4] = wp * ev.Fp;
-            t7[5] = wp * ev.Fx;
-            t7[6] = W * ev.Fx * ev.Fx;
+            t7[0] = G1 * zr;
+            t7[1] = G1 * zi;
+            t7[2] = G2 * zr;
+            t7[3] = G2 * zi;
+            double wg = W * G1;
+            t7[4] = wg * G1;
+            t7[5] = wg * G2;
+            t7[6] = W * G2 * G2;
         }
         while (true) {
             if (valid && pk == cur) {
@@ -346,9 +394,11 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
 
 // ---------------------------------------------------------------------------
 // A5: per-(particle, segment) sums over the tiles the segment spans, then
-//   F_p = [R |X+|^2 - 2 Q Re(X+ conj Xx) + P |Xx|^2] / (2 (P R - Q^2))
-// which is 1/2 N^T M^-1 N for M = diag(K, K), K = [[P, Q], [Q, R]],
-// N = (Re X+, Re Xx, -Im X+, -Im Xx).
+//   F_p = [K22 |X1|^2 - 2 K12 Re(X1 conj X2) + K11 |X2|^2] / (2 (K11 K22 - K12^2))
+// which is 1/2 N^T M^-1 N for M = diag(K, K), K = [[K11, K12], [K12, K22]],
+// N = (Re X1, Re X2, -Im X1, -Im X2) in the basis G1 h0, G2 h0, -i G1 h0, -i G2 h0.
+// The degenerate-segment rule is stated in the (F+, Fx) basis:
+// det <= 1e-12 P R with P = sum W F+^2, R = sum W Fx^2 recovered from K.
 // ---------------------------------------------------------------------------
 __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
                               double* Fpart) {
@@ -390,13 +440,17 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
 #pragma unroll
     for (int c = 0; c < 7; c++) acc[c] = warp_sum(acc[c]);
     if (lane == 0) {
-        double Xpr = acc[0], Xpi = acc[1], Xxr = acc[2], Xxi = acc[3];
-        double Pp = acc[4], Qq = acc[5], Rr = acc[6];
-        double det = Pp * Rr - Qq * Qq;
+        double X1r = acc[0], X1i = acc[1], X2r = acc[2], X2i = acc[3];
+        double K11 = acc[4], K12 = acc[5], K22 = acc[6];
+        double det = K11 * K22 - K12 * K12;
+        const double2 rc = pa.rot[wid];
+        const double cc = rc.x * rc.x, ss = rc.y * rc.y, cs2 = 2.0 * rc.x * rc.y;
+        double Pp = cc * K11 - cs2 * K12 + ss * K22;   // sum W F+^2
+        double Rr = ss * K11 + cs2 * K12 + cc * K22;   // sum W Fx^2
         double F = 0.0;
         if (nb >= 4 && det > 1e-12 * Pp * Rr) {
-            double num = Rr * (Xpr * Xpr + Xpi * Xpi) - 2.0 * Qq * (Xpr * Xxr + Xpi * Xxi) +
-                         Pp * (Xxr * Xxr + Xxi * Xxi);
+            double num = K22 * (X1r * X1r + X1i * X1i) - 2.0 * K12 * (X1r * X2r + X1i * X2i) +
+                         K11 * (X2r * X2r + X2i * X2i);
             F = 0.5 * num / det;
         }
         Fpart[wid] = F;

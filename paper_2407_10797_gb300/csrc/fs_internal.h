@@ -45,6 +45,7 @@ struct Partials {
     double* H;    // [B][ntiles][7] first segment of each (particle, tile)
     double* T;    // [B][ntiles][7] last segment of each (particle, tile)
     double* S;    // [B][Np][7] segments complete inside one tile
+    double2* rot; // [B][Np] (c, s): antenna basis G1 = c F+ + s Fx, G2 = c Fx - s F+ of each segment
     int ntiles;
 };
 
@@ -52,6 +53,8 @@ cudaError_t launch_precompute(const Grid& g, const double* data, const double* p
                               cudaStream_t s);
 cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Particle* parts, int global,
                          cudaStream_t s);
+cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const Segs& sg, double2* rot,
+                            cudaStream_t s);
 cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
                              const Partials& pa, cudaStream_t s);
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
