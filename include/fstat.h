@@ -139,6 +139,30 @@ FS_API fs_status fs_particle_bands(fs_plan* plan, const fs_params* params_dev, i
 FS_API fs_status fs_plan_set_profiling(fs_plan* plan, int enable);
 FS_API fs_status fs_plan_read_profile(fs_plan* plan, int kernel, double* total_ms, int64_t* launches);
 
+/* fs_fstat_batch without any device allocation, for callers that cannot
+ * call cudaMalloc (code inside an allocator-free library or host callback, a
+ * process whose device memory is owned by another runtime, or a caller with a
+ * fixed memory budget).  The paper has no counterpart: it is a deployment
+ * variant of fs_fstat_batch in FS_FP64 mode, not part of the method.
+ *   Inputs are the grid (n_bins, f_min, df, T_obs as for fs_plan_create), the
+ *   data and PSD (as for fs_plan_set_data), params_dev / B / edges_host / N_p
+ *   (as for fs_fstat_batch); outputs F_dev and F_part_dev (may be NULL) as for
+ *   fs_fstat_batch; stream is a cudaStream_t (NULL = legacy default stream).
+ *   Limits: n_bins <= 32768, 0 <= B <= 1024, 1 <= N_p <= 64; larger requests
+ *   return FS_EINVAL with a message naming the limit.
+ * Workspace: a 10 MiB file-scope device array of the library, held by every
+ * GPU that loads the library until the process exits.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and each call overwrites what it needs, so calls that
+ * may overlap on the GPU (different streams, or different host threads on the
+ * same device) race and must be serialised by the caller.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Asynchronous. */
+FS_API fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double df, double T_obs,
+                                        const double* data_dev, const double* psd_dev, const fs_params* params_dev,
+                                        int B, const int64_t* edges_host, int N_p, double* F_dev,
+                                        double* F_part_dev, void* stream);
+
 /* Constants compiled into the library: out[0] = solar mass in s, out[1] =
  * year in s, out[2] = AU/c in s, out[3] = eccentricity reference frequency (Hz). */
 FS_API fs_status fs_constants(double* out_host);

@@ -28,6 +28,14 @@ fs_status cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
+fs_status fs::set_error(fs_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 struct fs_plan {
     fs::Grid grid;
     int mode;

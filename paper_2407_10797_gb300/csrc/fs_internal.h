@@ -49,6 +49,9 @@ struct Partials {
     int ntiles;
 };
 
+// Record an error message for fs_last_error() and return st.
+fs_status set_error(fs_status st, const char* fmt, ...);
+
 cudaError_t launch_precompute(const Grid& g, const double* data, const double* psd, const Tables& t,
                               cudaStream_t s);
 cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Particle* parts, int global,

@@ -59,12 +59,14 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_add_signal.argtypes = [_vp, C.POINTER(fs_params), _dp, _vp]
         L.fs_constants.argtypes = [_dp]
         L.fs_particle_bands.argtypes = [_vp, _vp, C.c_int, _vp]
+        L.fs_fstat_batch_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp,
+                                             C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp, _vp]
         L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
         for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_add_signal", "fs_constants", "fs_particle_bands",
-                     "fs_plan_set_profiling", "fs_plan_read_profile"):
+                     "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -199,3 +201,32 @@ class Plan:
         aa = np.ascontiguousarray(a, dtype=np.float64)
         _check(self._L.fs_add_signal(self._h, C.byref(pp), aa.ctypes.data_as(_dp), _cuda_ptr(view, torch.float64)))
         return data
+
+
+def fstat_batch_noalloc(grid, data, psd, params, Np: int, edges=None, F=None, F_part=None, stream=None):
+    """fs_fstat_batch_noalloc: FP64 F-statistic that allocates no device memory
+    (workspace in the library's fixed 10 MiB device array; n_bins <= 32768,
+    B <= 1024, N_p <= 64).  For callers that cannot allocate device memory; the
+    output tensors here are made by the caller (this wrapper creates them with
+    torch if not given).  Calls that overlap on the GPU race on the shared
+    workspace."""
+    import torch
+    L = load()
+    if data.dtype == torch.complex128:
+        data = torch.view_as_real(data)
+    B = params.shape[0]
+    if F is None:
+        F = torch.empty(B, dtype=torch.float64, device=params.device)
+    e = None
+    if edges is not None:
+        arr = np.ascontiguousarray(edges, dtype=np.int64)
+        if arr.shape != (Np + 1,):
+            raise ValueError("edges must have N_p + 1 entries")
+        e = arr.ctypes.data_as(C.POINTER(C.c_int64))
+    _check(L.fs_fstat_batch_noalloc(int(grid.n), float(grid.f_min), float(grid.df), float(grid.T_obs),
+                                    _cuda_ptr(data, torch.float64), _cuda_ptr(psd, torch.float64),
+                                    _cuda_ptr(params, torch.float64), int(B), e, int(Np),
+                                    _cuda_ptr(F, torch.float64),
+                                    _cuda_ptr(F_part, torch.float64) if F_part is not None else None,
+                                    _stream_handle(stream)))
+    return F, F_part
