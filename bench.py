@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--profile-case", action="store_true",
+    ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
                     help="one small evaluation for kernel profiling: paper grid, 64 particles, N_p = 16")
     return ap.parse_args()
 
@@ -258,6 +258,50 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def time_mode(args, world, plan, P_dev, B, F_out, stream, kernel_prof=True):
+    """Warm up, then time `steps` evaluations at every N_p with CUDA events on
+    the plan's stream (barrier + synchronize on both sides).  Returns
+    (ms for all steps, max over ranks; fused-kernel ms and launches; clocks)."""
+    import torch
+
+    def step(params):
+        for Np in NP_LIST:
+            plan.fstat(params, Np, F=F_out[Np], want_parts=False)
+
+    for _ in range(args.warmup):
+        step(P_dev)
+    torch.cuda.synchronize()
+    for k in ("main", "setup", "reduce"):
+        plan.read_profile(k)
+    plan.set_profiling(kernel_prof)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(P_dev)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    plan.set_profiling(False)
+    ms = allmax(world, ev0.elapsed_time(ev1))
+    prof = {k: plan.read_profile(k) for k in ("main", "setup", "reduce")}
+    return ms, prof, clk.summary(), step
+
+
+def fp32_peak_tflops() -> float:
+    """FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) at
+    2070 MHz (80.5 TFLOP/s)."""
+    return 152 * 128 * 2 * 2070e6 / 1e12
+
+
+# FP32-pipe operations per in-band particle*bin of the mixed kernel's body
+# (algorithmic count, FMA = 2 flop; integer phase steps and the SFU sincos
+# counted as one flop per instruction).
+MIXED_FLOP_PER_PBIN = 150.0
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_2407_10797_gb300 import fstat
@@ -284,40 +328,14 @@ def run_gpu(args, world, rank, local):
     bands = plan.bands(P_dev).cpu().numpy()
     inband = int(np.maximum(bands[:, 1] - bands[:, 0] + 1, 0).sum())
     pbins_per_step = inband * len(NP_LIST)
+    total_pbins = allsum(world, float(pbins_per_step * args.steps))
     F_out = {Np: torch.empty(B, dtype=torch.float64, device=dev) for Np in NP_LIST}
 
-    def step(params):
-        for Np in NP_LIST:
-            plan.fstat(params, Np, F=F_out[Np], want_parts=False)
-
-    for _ in range(args.warmup):
-        step(P_dev)
-    torch.cuda.synchronize()
-    plan.read_profile("main")
-    plan.read_profile("setup")
-    plan.read_profile("reduce")
-
-    # ---- device-resident timed region
-    plan.set_profiling(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier(world)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step(P_dev)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-    plan.set_profiling(False)
-    ms = ev0.elapsed_time(ev1)
-    ms_max = allmax(world, ms)
-    main_ms, main_n = plan.read_profile("main")
-    setup_ms, setup_n = plan.read_profile("setup")
-    red_ms, red_n = plan.read_profile("reduce")
-    launches = args.steps * len(NP_LIST) * 4
-    total_pbins = allsum(world, float(pbins_per_step * args.steps))
-    value = total_pbins / (ms_max / 1e3)
+    # ---- FP64 mode (the paper-scale FP64 configuration): device-resident timing
+    ms, prof, clocks, step = time_mode(args, world, plan, P_dev, B, F_out, stream)
+    value = total_pbins / (ms / 1e3)
+    main_ms, main_n = prof["main"]
+    F64 = {Np: F_out[Np].cpu().numpy() for Np in NP_LIST}
 
     # ---- end to end through the C ABI with host buffers (pinned)
     P_host = torch.from_numpy(P).pin_memory()
@@ -338,19 +356,29 @@ def run_gpu(args, world, rank, local):
     barrier(world)
     e2e_ms = allmax(world, e0.elapsed_time(e1))
     e2e_value = total_pbins / (e2e_ms / 1e3)
+    plan.close()
 
-    # ---- roofline of the dominant kernel (the fused FP64 kernel)
-    clocks = clk.summary()
+    # ---- mixed mode on the same data and particles
+    planm = fstat.Plan.from_grid(g, mode=fstat.FS_MIXED, stream=stream)
+    planm.set_data(d_dev, psd_dev)
+    planm.reserve(B, max(NP_LIST))
+    ms_m, prof_m, clocks_m, _ = time_mode(args, world, planm, P_dev, B, F_out, stream)
+    value_m = total_pbins / (ms_m / 1e3)
+    mix_err = max(float(np.max(np.abs(F_out[Np].cpu().numpy() - F64[Np]) / np.maximum(np.abs(F64[Np]), 2.0 * Np)))
+                  for Np in NP_LIST)
+    planm.close()
+
+    # ---- roofline of the dominant kernels (average launch duration, live events)
     main_avg_ms = main_ms / max(main_n, 1)
-    flops_per_launch = FP64_FLOP_PER_PBIN * inband
-    achieved_tf = flops_per_launch / (main_avg_ms / 1e3) / 1e12
+    achieved_tf = FP64_FLOP_PER_PBIN * inband / (main_avg_ms / 1e3) / 1e12
     peak_tf = fp64_peak_tflops()
-    out = None
+    mm_ms, mm_n = prof_m["main"]
+    mm_avg = mm_ms / max(mm_n, 1)
+    ach_m = MIXED_FLOP_PER_PBIN * inband / (mm_avg / 1e3) / 1e12
+    peak_m = fp32_peak_tflops()
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            from oracle import oracle as O
-            m = O.OracleModel.from_grid(g)
             data_h = d_dev.cpu().numpy()
             pb, el, thr, npart = oracle_sample(g, P, psd, data_h, args.cpu_seconds)
             cpu = {"value": pb / el, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -358,28 +386,34 @@ def run_gpu(args, world, rank, local):
                              f"{el:.1f} s"}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_bins": g.n, "f_band_hz": [0.01, 0.05], "T_obs_s": g.T_obs,
                        "B": B, "runs_x_particles": "8x40", "N_p": list(NP_LIST), "mode": "fp64",
                        "inband_particle_bins_per_launch": inband, "grid_particle_bins_per_launch": B * g.n,
                        "l2": "inputs exceed L2: per-bin tables 227 MB > 129 MB L2", "parallelism": f"dp{world}"},
-            "gpu_launches": launches,
-            "kernel_ms": {"fused_fp64_avg": main_avg_ms, "setup_avg": setup_ms / max(setup_n, 1),
-                          "solve_avg": red_ms / max(red_n, 1),
+            "gpu_launches": args.steps * len(NP_LIST) * 5,
+            "kernel_ms": {"fused_fp64_avg": main_avg_ms, "setup_avg": prof["setup"][0] / max(prof["setup"][1], 1),
+                          "solve_avg": prof["reduce"][0] / max(prof["reduce"][1], 1),
                           "fused_share_of_step": main_ms / max(ms, 1e-9)},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / peak_tf, "traffic": None,
-                         "pipe": "fp64", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts)",
+                         "frac": achieved_tf / peak_tf, "traffic": None, "pipe": "fp64",
+                         "peak_source": "unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                          "flop_per_pbin": FP64_FLOP_PER_PBIN},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(P.nbytes),
                     "d2h_bytes_per_step": int(8 * B * len(NP_LIST))},
+            "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps, "dtype": "f64 anchors + f32",
+                      "max_rel_err_vs_fp64": mix_err, "error_metric": "|dF|/max(|F|, 2 N_p)",
+                      "kernel_ms": {"fused_mixed_avg": mm_avg, "fused_share_of_step": mm_ms / max(ms_m, 1e-9)},
+                      "roofline": {"bound": "alu", "achieved": ach_m, "peak": peak_m, "unit": "TFLOP/s",
+                                   "frac": ach_m / peak_m, "traffic": None, "pipe": "fp32",
+                                   "peak_source": "unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+                                   "flop_per_pbin": MIXED_FLOP_PER_PBIN},
+                      "clocks": clocks_m},
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
-    plan.close()
-    return out
 
 
 def run_profile_case(args):
@@ -388,13 +422,15 @@ def run_profile_case(args):
     import torch
     from paper_2407_10797_gb300 import fstat
     w, g, psd, noise, P, inj = workload_inputs(0)
-    plan = fstat.Plan.from_grid(g, mode=fstat.FS_FP64)
+    mode = fstat.FS_MIXED if args.profile_case == "mixed" else fstat.FS_FP64
+    plan = fstat.Plan.from_grid(g, mode=mode)
     plan.set_data(torch.from_numpy(noise).cuda(), torch.from_numpy(psd).cuda())
-    P_dev = torch.from_numpy(P[:64]).cuda()
+    P_dev = torch.from_numpy(P[:64] if mode == fstat.FS_FP64 else P).cuda()
     for _ in range(2):
         F, _ = plan.fstat(P_dev, 16, want_parts=False)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "paper grid, B=64, N_p=16", "F_mean": float(F.mean().item())}))
+    print(json.dumps({"profile_case": f"paper grid, {args.profile_case}, B={P_dev.shape[0]}, N_p=16",
+                      "F_mean": float(F.mean().item())}))
     plan.close()
 
 

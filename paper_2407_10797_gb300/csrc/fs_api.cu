@@ -52,7 +52,11 @@ struct fs_plan {
     double* S;
     double* Fpart;
     double2* rot;
+    float2* rot32;
     int ntiles;
+    // mixed mode: FP32 (dw, W) tables and the scale exponent
+    float4* tab32;
+    int* emax;
     // segment edges (global mode)
     int64_t* edges_dev;
     int64_t* edges_cache;
@@ -117,8 +121,10 @@ void free_workspace(fs_plan* p) {
     cudaFree(p->S);
     cudaFree(p->Fpart);
     cudaFree(p->rot);
+    cudaFree(p->rot32);
     p->parts = nullptr;
     p->rot = nullptr;
+    p->rot32 = nullptr;
     p->H = p->T = p->S = p->Fpart = nullptr;
     p->B_cap = p->Np_cap = 0;
 }
@@ -136,7 +142,8 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
         (e = cudaMalloc(&p->T, sizeof(double) * 7 * nt * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->S, sizeof(double) * 7 * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->Fpart, sizeof(double) * (size_t)nn * nb)) != cudaSuccess ||
-        (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess) {
+        (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess) {
         free_workspace(p);
         return cuda_fail(e, "cudaMalloc(workspace)");
     }
@@ -169,7 +176,8 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
         !isfinite(T_obs))
         return fail(FS_EINVAL, "fs_plan_create: need n_bins > 0 and finite f_min, df, T_obs > 0");
     if (mode != FS_FP64 && mode != FS_MIXED) return fail(FS_EINVAL, "fs_plan_create: unknown mode %d", mode);
-    if (mode == FS_MIXED) return fail(FS_EUNSUPPORTED, "fs_plan_create: FS_MIXED is not built yet");
+    if (mode == FS_MIXED && n_bins >= ((int64_t)1 << 31))
+        return fail(FS_EINVAL, "fs_plan_create: FS_MIXED needs n_bins < 2^31");
     if (n_bins > ((int64_t)1 << 40)) return fail(FS_EINVAL, "fs_plan_create: n_bins too large");
     fs_plan* p = new (std::nothrow) fs_plan;
     if (!p) return fail(FS_ENOMEM, "fs_plan_create: host allocation failed");
@@ -204,6 +212,12 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
         fs_plan_destroy(p);
         return cuda_fail(e, "cudaMalloc(plan)");
     }
+    if (mode == FS_MIXED &&
+        ((e = cudaMalloc(&p->tab32, sizeof(float4) * (size_t)n_bins)) != cudaSuccess ||
+         (e = cudaMalloc(&p->emax, sizeof(int))) != cudaSuccess)) {
+        fs_plan_destroy(p);
+        return cuda_fail(e, "cudaMalloc(mixed tables)");
+    }
     p->edges_cache = (int64_t*)malloc(sizeof(int64_t) * (fs::kNpMax + 1));
     p->edges_np = 0;
     p->prof = new std::vector<fs_plan::ProfRec>();
@@ -221,6 +235,8 @@ fs_status fs_plan_destroy(fs_plan* p) {
     cudaFree(p->one_param);
     cudaFree(p->one_part);
     cudaFree(p->one_a);
+    cudaFree(p->tab32);
+    cudaFree(p->emax);
     free(p->edges_cache);
     if (p->prof) {
         for (auto& r : *p->prof) {
@@ -243,6 +259,8 @@ fs_status fs_plan_set_data(fs_plan* p, const double* data_dev, const double* psd
     ProfScope ps(p, 3);
     cudaError_t e = fs::launch_precompute(p->grid, data_dev, psd_dev, p->tab, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
+    if (p->mode == FS_MIXED && (e = fs::launch_tables32(p->grid, p->tab, p->emax, p->tab32, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "mixed tables launch");
     p->data_set = 1;
     return FS_OK;
 }
@@ -260,6 +278,7 @@ fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const i
     if (!p) return fail(FS_EINVAL, "fs_fstat_batch: plan is NULL");
     if (B < 0) return fail(FS_EINVAL, "fs_fstat_batch: B = %d < 0", B);
     if (Np < 1 || Np > fs::kNpMax) return fail(FS_EINVAL, "fs_fstat_batch: N_p = %d not in [1, %d]", Np, fs::kNpMax);
+    if (B > 65535 * 8) return fail(FS_EINVAL, "fs_fstat_batch: B = %d exceeds %d", B, 65535 * 8);
     if (B == 0) return FS_OK;
     if (!params_dev || !F_dev) return fail(FS_EINVAL, "fs_fstat_batch: NULL params or F");
     if (!p->data_set) return fail(FS_EINVAL, "fs_fstat_batch: fs_plan_set_data was not called");
@@ -297,19 +316,26 @@ fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const i
     pa.T = p->T;
     pa.S = p->S;
     pa.rot = p->rot;
-    pa.ntiles = p->ntiles;
+    const bool mixed = p->mode == FS_MIXED;
+    pa.rot32 = mixed ? p->rot32 : nullptr;
+    pa.tile = mixed ? fs::mixed_span() : fs::kTile;
+    pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
     {
         ProfScope ps(p, 0);
         if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, global, p->stream)) != cudaSuccess)
             return cuda_fail(e, "setup launch");
-        if ((e = fs::launch_rotation(p->grid, p->parts, B, sg, p->rot, p->stream)) != cudaSuccess)
+        if ((e = fs::launch_rotation(p->grid, p->parts, B, sg, p->rot, pa.rot32, p->stream)) != cudaSuccess)
             return cuda_fail(e, "rotation launch");
     }
     {
         ProfScope ps(p, 1);
-        if ((e = fs::launch_fp64_main(p->grid, p->tab, p->parts, B, sg, pa, p->stream)) != cudaSuccess)
+        if (mixed) {
+            if ((e = fs::launch_mixed_main(p->grid, p->tab, p->tab32, p->parts, B, sg, pa, p->stream)) != cudaSuccess)
+                return cuda_fail(e, "mixed main launch");
+        } else if ((e = fs::launch_fp64_main(p->grid, p->tab, p->parts, B, sg, pa, p->stream)) != cudaSuccess) {
             return cuda_fail(e, "fp64 main launch");
+        }
     }
     {
         ProfScope ps(p, 2);

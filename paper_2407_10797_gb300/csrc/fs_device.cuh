@@ -1,0 +1,72 @@
+// fs_device.cuh - device helpers shared by the FP64 and mixed-precision kernels.
+#pragma once
+
+#include "fs_internal.h"
+
+namespace fs {
+
+__device__ __forceinline__ FreqPowers powers_of(double f) {
+    FreqPowers w;
+    w.u = rcbrt(f);
+    double u2 = w.u * w.u;
+    w.g0h = u2 * u2 * w.u;
+    w.e19 = pow(kF0Ecc / f, 19.0 / 9.0);
+    return w;
+}
+
+__device__ __forceinline__ double bin_freq(const Grid& g, int64_t k) {
+    // the same two roundings as f_min + (double)k * df without contraction
+    return __dadd_rn(g.f_min, __dmul_rn((double)k, g.df));
+}
+
+// ---------------------------------------------------------------------------
+// Segment helpers (device)
+// ---------------------------------------------------------------------------
+struct SegView {
+    int Np;
+    int global;
+    const int64_t* edges;
+    int64_t lo, hi;   // band [lo, hi] inclusive
+    __device__ int seg(int64_t k) const {
+        if (!global) return seg_of_bin(k, lo, hi, Np);
+        // largest p with edges[p] <= k (edges non-decreasing, k in [edges[0], edges[Np]))
+        int a = 0, b = Np;   // invariant: edges[a] <= k < edges[b]
+        while (b - a > 1) {
+            int m = (a + b) >> 1;
+            if (edges[m] <= k) a = m; else b = m;
+        }
+        return a;
+    }
+    // first bin of segment p (p = 0..Np)
+    __device__ int64_t start(int p) const {
+        if (global) return edges[p];
+        if (p >= Np) return hi + 1;
+        int64_t w = hi - lo;
+        if (w == 0) return p == 0 ? lo : hi + 1;
+        int64_t num = (int64_t)p * w;
+        return lo + (num + Np - 1) / Np;
+    }
+};
+
+__device__ __forceinline__ SegView seg_view(const Segs& sg, const Particle& P) {
+    SegView v;
+    v.Np = sg.Np;
+    v.global = sg.global;
+    v.edges = sg.edges;
+    if (sg.global) {
+        v.lo = sg.edges[0];
+        v.hi = sg.edges[sg.Np] - 1;
+    } else {
+        v.lo = P.klo;
+        v.hi = P.khi;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+}  // namespace fs

@@ -9,6 +9,7 @@
 #include <climits>
 
 #include "fs_internal.h"
+#include "fs_device.cuh"
 
 namespace fs {
 
@@ -68,20 +69,6 @@ cudaError_t launch_precompute(const Grid& g, const double* data, const double* p
 // ---------------------------------------------------------------------------
 // A1: per-particle coefficients and band edges.
 // ---------------------------------------------------------------------------
-__device__ FreqPowers powers_of(double f) {
-    FreqPowers w;
-    w.u = rcbrt(f);
-    double u2 = w.u * w.u;
-    w.g0h = u2 * u2 * w.u;
-    w.e19 = pow(kF0Ecc / f, 19.0 / 9.0);
-    return w;
-}
-
-__device__ __forceinline__ double bin_freq(const Grid& g, int64_t k) {
-    // the same two roundings as f_min + (double)k * df without contraction
-    return __dadd_rn(g.f_min, __dmul_rn((double)k, g.df));
-}
-
 __global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int B, Particle* parts,
                              int global) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -201,56 +188,6 @@ cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Partic
 }
 
 // ---------------------------------------------------------------------------
-// Segment helpers (device)
-// ---------------------------------------------------------------------------
-struct SegView {
-    int Np;
-    int global;
-    const int64_t* edges;
-    int64_t lo, hi;   // band [lo, hi] inclusive
-    __device__ int seg(int64_t k) const {
-        if (!global) return seg_of_bin(k, lo, hi, Np);
-        // largest p with edges[p] <= k (edges non-decreasing, k in [edges[0], edges[Np]))
-        int a = 0, b = Np;   // invariant: edges[a] <= k < edges[b]
-        while (b - a > 1) {
-            int m = (a + b) >> 1;
-            if (edges[m] <= k) a = m; else b = m;
-        }
-        return a;
-    }
-    // first bin of segment p (p = 0..Np)
-    __device__ int64_t start(int p) const {
-        if (global) return edges[p];
-        if (p >= Np) return hi + 1;
-        int64_t w = hi - lo;
-        if (w == 0) return p == 0 ? lo : hi + 1;
-        int64_t num = (int64_t)p * w;
-        return lo + (num + Np - 1) / Np;
-    }
-};
-
-__device__ __forceinline__ SegView seg_view(const Segs& sg, const Particle& P) {
-    SegView v;
-    v.Np = sg.Np;
-    v.global = sg.global;
-    v.edges = sg.edges;
-    if (sg.global) {
-        v.lo = sg.edges[0];
-        v.hi = sg.edges[sg.Np] - 1;
-    } else {
-        v.lo = P.klo;
-        v.hi = P.khi;
-    }
-    return v;
-}
-
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-// ---------------------------------------------------------------------------
 // Per-segment antenna basis.  F_p is invariant under any invertible change of
 // the amplitude basis (Eq. coherent_F_stat), so each segment uses
 //   G1 = c F+ + s Fx,  G2 = c Fx - s F+,  (c, s) = F(t_mid)/|F(t_mid)|
@@ -259,7 +196,8 @@ __device__ __forceinline__ double warp_sum(double x) {
 // rotated basis G2 is small but computed directly, and the Gram matrix of
 // (G1, G2) is well conditioned, so FP64 sums keep F_p accurate.
 // ---------------------------------------------------------------------------
-__global__ void rotation_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, double2* rot) {
+__global__ void rotation_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, double2* rot,
+                                float2* rot32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)B * sg.Np) return;
     const int b = (int)(i / sg.Np);
@@ -284,13 +222,14 @@ __global__ void rotation_kernel(Grid g, const Particle* __restrict__ parts, int 
         }
     }
     rot[i] = r;
+    if (rot32) rot32[i] = make_float2((float)r.x, (float)r.y);
 }
 
 cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const Segs& sg, double2* rot,
-                            cudaStream_t s) {
+                            float2* rot32, cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
     int64_t n = (int64_t)B * sg.Np;
-    rotation_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, parts, B, sg, rot);
+    rotation_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, parts, B, sg, rot, rot32);
     return cudaGetLastError();
 }
 
@@ -423,9 +362,9 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
     }
     const int64_t nb = s1 > s0 ? s1 - s0 : 0;
     if (nb > 0) {
-        const int64_t t0 = s0 / kTile, t1 = (s1 - 1) / kTile;
+        const int64_t t0 = s0 / pa.tile, t1 = (s1 - 1) / pa.tile;
         for (int64_t t = t0 + lane; t <= t1; t += 32) {
-            int64_t tlo = t * kTile, thi = tlo + kTile - 1;
+            int64_t tlo = t * pa.tile, thi = tlo + pa.tile - 1;
             if (tlo < sv.lo) tlo = sv.lo;
             if (thi > sv.hi) thi = sv.hi;
             const int pf = sv.seg(tlo), pl = sv.seg(thi);

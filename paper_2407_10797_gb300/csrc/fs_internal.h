@@ -46,7 +46,9 @@ struct Partials {
     double* T;    // [B][ntiles][7] last segment of each (particle, tile)
     double* S;    // [B][Np][7] segments complete inside one tile
     double2* rot; // [B][Np] (c, s): antenna basis G1 = c F+ + s Fx, G2 = c Fx - s F+ of each segment
-    int ntiles;
+    float2* rot32; // the same rotations in FP32 (mixed mode), or NULL
+    int ntiles;   // number of tiles (slots of H and T per particle)
+    int tile;     // bins per tile
 };
 
 // Record an error message for fs_last_error() and return st.
@@ -57,11 +59,15 @@ cudaError_t launch_precompute(const Grid& g, const double* data, const double* p
 cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Particle* parts, int global,
                          cudaStream_t s);
 cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const Segs& sg, double2* rot,
-                            cudaStream_t s);
+                            float2* rot32, cudaStream_t s);
 cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
                              const Partials& pa, cudaStream_t s);
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
                           double* Fpart, double* F, cudaStream_t s);
+cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s);
+cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
+                              const Segs& sg, const Partials& pa, cudaStream_t s);
+int mixed_span();   // bins per H/T slot of the mixed path
 cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);
 cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,
                               double* data, cudaStream_t s);

@@ -1,0 +1,340 @@
+// fs_mixed.cu - the FS_MIXED path: FP64 anchors, exact fixed-point phase
+// steps, FP32 response and products, FP64 partial sums.
+//
+// Per (particle, tile of 1024 bins) an anchor at the tile's central in-band bin
+// k_a is evaluated in FP64 (double-double where the phase needs it):
+//   Phi(k) = Phi_orb(f_k) - f_k d(t_{f_k})                  (App. A Eq. A3, Sec. IV)
+//   Phi_orb(f_a + dk df) ~ c0 + c1 dk + c2 dk^2 + c3 dk^3    (Taylor, cycles)
+//   t(f_a + dk df)       ~ t_a + t' df dk + t'' df^2 dk^2 / 2
+// The phase polynomial is kept in 64-bit fixed point (units of 2^-64 cycle):
+// integer arithmetic is exact modulo one cycle, so each lane walks its bins
+// (step 32) by forward differences with no phase drift.  The Doppler phase and
+// the antenna patterns are evaluated per bin as small-angle deltas from the
+// anchor's orbital phase alpha_a (FP32), the phase goes through the SFU sincos,
+// and the seven segment sums accumulate in FP32 per tile and in FP64 across
+// tiles.  A tile whose Taylor remainder bound exceeds 1e-6 cycle (or whose
+// orbital-phase excursion exceeds 0.25 rad) is evaluated bin by bin in FP64
+// instead, so the mode stays correct on any grid.
+#include <cfloat>
+#include <climits>
+
+#include "fs_internal.h"
+#include "fs_device.cuh"
+
+namespace fs {
+
+constexpr int kTileMix = 1024;                        // bins per anchor: 32 lanes x 32 steps
+constexpr int kTilesPerSpan = 32;                     // anchors per warp span (one per lane in phase A)
+constexpr int kSpanMix = kTileMix * kTilesPerSpan;    // 32768 bins: H/T granularity of this path
+constexpr int kWarpsMix = 8;                          // particles per CTA
+
+struct Anchor {
+    unsigned long long c[4];   // c0..c3 of the phase polynomial, cycles mod 1 in units of 2^-64
+    float w1, w2;              // d(alpha) = w1 dk + w2 dk^2, rad
+    float ca, sa;              // cos, sin alpha_a
+    float cda, sda;            // cos, sin (alpha_a - phi)
+    float ADfa, ADdf;          // AU cos(beta) f_a and AU cos(beta) df, cycles
+    int64_t ja, lo, hi;        // anchor bin and in-band range [lo, hi) of the tile
+    int mode;                  // 0: no in-band bin, 1: polynomial, 2: bin-by-bin FP64
+    int pad;
+};
+
+__device__ __forceinline__ unsigned long long to_fixed(double x) {
+    double y = x - floor(x);          // [0, 1)
+    double a = y * 4294967296.0;
+    double hi = floor(a);
+    double lo = (a - hi) * 4294967296.0;
+    return ((unsigned long long)hi << 32) + (unsigned long long)lo;
+}
+
+// Phase polynomial at integer offset d (exact modulo 2^64).
+__device__ __forceinline__ unsigned long long poly_fx(const unsigned long long c[4], long long d) {
+    unsigned long long u = (unsigned long long)d;
+    return c[0] + u * (c[1] + u * (c[2] + u * c[3]));
+}
+
+// Bin-by-bin FP64 evaluation for tiles where the anchor expansion is not valid.
+__device__ __noinline__ void eval_bin_fallback(const Particle& P, const Tables& tb, int64_t k, double alpha0,
+                                               float* ph, float* Fp, float* Fx) {
+    FreqPowers fw;
+    fw.u = tb.u[k];
+    fw.g0h = tb.g0h[k];
+    fw.e19 = tb.e19[k];
+    const BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], fw, tb.g0l[k], alpha0);
+    *ph = (float)ev.frac;
+    *Fp = (float)ev.Fp;
+    *Fx = (float)ev.Fx;
+}
+
+__device__ void make_anchor(const Grid& g, const Tables& tb, const Particle& P, int64_t lo, int64_t hi, Anchor& A) {
+    A.lo = lo;
+    A.hi = hi;
+    if (lo >= hi) {
+        A.mode = 0;
+        return;
+    }
+    const int64_t ja = lo + (hi - lo - 1) / 2;
+    const double hmax = (double)max(ja - lo, hi - 1 - ja);
+    A.ja = ja;
+    const double fh = tb.fh[ja], fl = tb.fl[ja], u = tb.u[ja], g0h = tb.g0h[ja], g0l = tb.g0l[ja],
+                 e19 = tb.e19[ja];
+    // orbital phase mod 1 (double-double leading term, exact f t_c)
+    double p, e;
+    two_prod(P.P0h, g0h, p, e);
+    e = fma(P.P0h, g0l, e);
+    e = fma(P.P0l, g0h, e);
+    double acc = (p - rint(p)) + e;
+    double q, eq;
+    two_prod(fh, P.tc, q, eq);
+    eq = fma(fl, P.tc, eq);
+    acc += (q - rint(q)) + eq;
+    const double u2 = u * u, u3 = u2 * u;
+    const double T0 = P.P0h * g0h, T2 = P.P2 * u3, T3 = P.P3 * u2, T4 = P.P4 * u, Te = P.E0 * g0h * e19;
+    double rest = T2 + T3 + T4 + Te;
+    acc += rest - rint(rest);
+    // derivatives of sum_m T_m (f/f_a)^{p_m}: d^n/df^n = sum_m p_m (p_m - 1) ... T_m / f^n
+    const double p0 = -5.0 / 3.0, p2 = -1.0, p3 = -2.0 / 3.0, p4 = -1.0 / 3.0, pe = -34.0 / 9.0;
+    double k0 = p0, k2 = p2, k3 = p3, k4 = p4, ke = pe;
+    const double S1 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
+    k0 *= p0 - 1.0; k2 *= p2 - 1.0; k3 *= p3 - 1.0; k4 *= p4 - 1.0; ke *= pe - 1.0;
+    const double S2 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
+    k0 *= p0 - 2.0; k2 *= p2 - 2.0; k3 *= p3 - 2.0; k4 *= p4 - 2.0; ke *= pe - 2.0;
+    const double S3 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
+    k0 *= p0 - 3.0; k2 *= p2 - 3.0; k3 *= p3 - 3.0; k4 *= p4 - 3.0; ke *= pe - 3.0;
+    const double S4 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
+    const double inv = 1.0 / fh;
+    const double ta = P.tc + S1 * inv;           // t(f_a) = dPhi_orb/df
+    const double d2 = S2 * inv * inv;            // dt/df
+    const double d3 = S3 * inv * inv * inv;      // d2t/df2
+    const double d4 = S4 * inv * inv * inv * inv;
+    // orbit and Doppler at the anchor
+    const double Om = kTwoPi / kYearS;
+    double sa, ca;
+    sincos(fma(Om, ta, g.alpha0), &sa, &ca);
+    const double cda = fma(ca, P.clon, sa * P.slon);
+    const double sda = fma(sa, P.clon, -ca * P.slon);
+    acc -= fh * P.AD * cda;
+    const double df = g.df;
+    A.c[0] = to_fixed(acc);
+    A.c[1] = to_fixed(ta * df);
+    A.c[2] = to_fixed(0.5 * d2 * df * df);
+    A.c[3] = to_fixed(d3 * df * df * df / 6.0);
+    A.w1 = (float)(Om * d2 * df);
+    A.w2 = (float)(0.5 * Om * d3 * df * df);
+    A.ca = (float)ca;
+    A.sa = (float)sa;
+    A.cda = (float)cda;
+    A.sda = (float)sda;
+    A.ADfa = (float)(P.AD * fh);
+    A.ADdf = (float)(P.AD * df);
+    // validity of the truncated expansions over |dk| <= hmax
+    const double H = hmax * df;
+    const double rem_phase = 1.2 * fabs(d4) * H * H * H * H / 24.0;     // cycles
+    const double rem_alpha = 1.2 * Om * fabs(d4) * H * H * H / 6.0;     // rad
+    const double da_max = fabs(Om * d2 * df) * hmax + fabs(0.5 * Om * d3 * df * df) * hmax * hmax;
+    A.mode = (rem_phase <= 1e-6 && rem_alpha <= 1e-6 && da_max <= 0.25) ? 1 : 2;
+}
+
+__global__ void __launch_bounds__(kWarpsMix * 32)
+mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts, int B,
+                  Segs sg, Partials pa) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Anchor* anc = reinterpret_cast<Anchor*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int b = blockIdx.y * kWarpsMix + w;
+    const int span = blockIdx.x;
+    const int64_t span_lo = (int64_t)span * kSpanMix;
+
+    // ---- phase A: one anchor per thread (particle w, tile lane of the span)
+    bool active = b < B && parts[b].valid;
+    SegView sv;
+    if (active) {
+        const Particle& P = parts[b];
+        sv = seg_view(sg, P);
+        int64_t lo = span_lo + (int64_t)lane * kTileMix, hi = lo + kTileMix;
+        if (lo < sv.lo) lo = sv.lo;
+        if (hi > sv.hi + 1) hi = sv.hi + 1;
+        make_anchor(g, tb, P, lo, hi, anc[threadIdx.x]);
+    } else {
+        anc[threadIdx.x].mode = 0;
+    }
+    __syncthreads();
+    if (!active) return;
+
+    // ---- phase B: warp w walks its particle's tiles of the span
+    const Particle& P = parts[b];
+    float pr[4][5];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 5; j++) pr[i][j] = (float)P.pr[i][j];
+    const int64_t slot = (int64_t)b * pa.ntiles + span;
+    const float2* rotb = pa.rot32 + (int64_t)b * sg.Np;
+
+    double accD[7];
+#pragma unroll
+    for (int c = 0; c < 7; c++) accD[c] = 0.0;
+    float acc[7];
+    int cur = -1;        // warp-uniform current segment
+    int nflush = 0;
+    int pk = -1;         // this lane's segment
+    int64_t nxt = -1;    // first bin of the segment after pk
+    float2 rc = make_float2(1.f, 0.f);
+
+    for (int ti = 0; ti < kTilesPerSpan; ti++) {
+        const Anchor& A = anc[w * 32 + ti];
+        if (A.mode == 0) continue;
+        const int64_t lo = A.lo, hi = A.hi;
+        if (cur < 0) cur = sv.seg(lo);
+#pragma unroll
+        for (int c = 0; c < 7; c++) acc[c] = 0.f;
+        const int64_t k0 = lo + lane;
+        // fixed-point forward differences of the phase along this lane (step 32)
+        unsigned long long F = 0, D1 = 0, D2 = 0, D3 = 0;
+        if (A.mode == 1) {
+            const long long d0 = (long long)(k0 - A.ja);
+            const unsigned long long y0 = poly_fx(A.c, d0), y1 = poly_fx(A.c, d0 + 32), y2 = poly_fx(A.c, d0 + 64),
+                                     y3 = poly_fx(A.c, d0 + 96);
+            F = y0;
+            D1 = y1 - y0;
+            D2 = y2 - 2ull * y1 + y0;
+            D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
+        }
+        for (int64_t base = lo; base < hi; base += 32) {
+            const int64_t k = base + lane;
+            const bool valid = k < hi;
+            float t7[7];
+#pragma unroll
+            for (int c = 0; c < 7; c++) t7[c] = 0.f;
+            if (valid) {
+                if (k >= nxt) {
+                    pk = sv.seg(k);
+                    nxt = sv.start(pk + 1);
+                    rc = rotb[pk];
+                }
+                float ph, Fp, Fx;
+                if (A.mode == 1) {
+                    const float d = (float)(k - A.ja);
+                    const float da = fmaf(A.w2, d, A.w1) * d;
+                    const float x2 = da * da;
+                    const float sd = da * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
+                    const float cm1 = x2 * fmaf(x2, fmaf(x2, -1.f / 720.f, 1.f / 24.f), -0.5f);
+                    const float cal = A.ca + fmaf(A.ca, cm1, -A.sa * sd);
+                    const float sal = A.sa + fmaf(A.sa, cm1, A.ca * sd);
+                    const float dcd = fmaf(A.cda, cm1, -A.sda * sd);       // cos(alpha - phi) - cos(alpha_a - phi)
+                    const float dop = fmaf(A.ADdf * d, A.cda + dcd, A.ADfa * dcd);   // Doppler phase minus its anchor value
+                    ph = (float)(int)(F >> 32) * 2.3283064365386963e-10f - dop;
+                    ph -= rintf(ph);
+                    const float c2 = fmaf(2.f * cal, cal, -1.f), s2 = 2.f * sal * cal;
+                    float pj[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        pj[i] = fmaf(pr[i][4], s2, fmaf(pr[i][3], c2, fmaf(pr[i][2], sal, fmaf(pr[i][1], cal, pr[i][0]))));
+                    Fp = 0.5f * ((pj[0] * pj[0] - pj[1] * pj[1]) - (pj[2] * pj[2] - pj[3] * pj[3]));
+                    Fx = pj[0] * pj[1] - pj[2] * pj[3];
+                } else {
+                    eval_bin_fallback(P, tb, k, g.alpha0, &ph, &Fp, &Fx);
+                }
+                float sn, cs;
+                __sincosf(6.283185307179586f * ph, &sn, &cs);
+                const float G1 = fmaf(rc.x, Fp, rc.y * Fx);
+                const float G2 = fmaf(rc.x, Fx, -rc.y * Fp);
+                const float4 tw = t32[k];
+                const float zr = fmaf(tw.x, cs, -tw.y * sn);
+                const float zi = fmaf(tw.x, sn, tw.y * cs);
+                t7[0] = G1 * zr;
+                t7[1] = G1 * zi;
+                t7[2] = G2 * zr;
+                t7[3] = G2 * zi;
+                const float wg = tw.z * G1;
+                t7[4] = wg * G1;
+                t7[5] = wg * G2;
+                t7[6] = tw.z * G2 * G2;
+            }
+            while (true) {
+                if (valid && pk == cur) {
+#pragma unroll
+                    for (int c = 0; c < 7; c++) acc[c] += t7[c];
+                }
+                const unsigned more = __ballot_sync(0xffffffffu, valid && pk > cur);
+                if (!more) break;
+                double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
+#pragma unroll
+                for (int c = 0; c < 7; c++) {
+                    const double v = warp_sum(accD[c] + (double)acc[c]);
+                    if (lane == 0) dst[c] = v;
+                    accD[c] = 0.0;
+                    acc[c] = 0.f;
+                }
+                nflush++;
+                int cand = (valid && pk > cur) ? pk : INT_MAX;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+                cur = cand;
+            }
+            F += D1;
+            D1 += D2;
+            D2 += D3;
+        }
+#pragma unroll
+        for (int c = 0; c < 7; c++) accD[c] += (double)acc[c];
+    }
+    if (cur < 0) return;   // no in-band bin in this span (warp-uniform)
+    double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
+#pragma unroll
+    for (int c = 0; c < 7; c++) {
+        const double v = warp_sum(accD[c]);
+        if (lane == 0) dst[c] = v;
+    }
+}
+
+cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
+                              const Segs& sg, const Partials& pa, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    dim3 grid((unsigned)pa.ntiles, (unsigned)((B + kWarpsMix - 1) / kWarpsMix));
+    const size_t smem = sizeof(Anchor) * kWarpsMix * 32;
+    mixed_main_kernel<<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa);
+    return cudaGetLastError();
+}
+
+int mixed_span() { return kSpanMix; }
+
+// ---------------------------------------------------------------------------
+// FP32 tables of the mixed path: (dw_re, dw_im, W) scaled by powers of two so
+// that max W ~ 1 (F is invariant under (d, S) -> (c d, c^2 S), and a power of
+// two changes no mantissa).
+// ---------------------------------------------------------------------------
+__global__ void w_exponent_kernel(Grid g, Tables t, int* emax) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int e = INT_MIN;
+    if (k < g.n) {
+        const double W = t.W[k];
+        if (W > 0.0 && isfinite(W)) e = ilogb(W);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e != INT_MIN) atomicMax(emax, e);
+}
+
+__global__ void tables32_kernel(Grid g, Tables t, const int* emax, float4* t32) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    int e = *emax;
+    e += e & 1;                       // even, so that the data scale is an exact power of two too
+    const double sW = ldexp(1.0, -e), sd = ldexp(1.0, -e / 2);
+    t32[k] = make_float4((float)(t.dwr[k] * sd), (float)(t.dwi[k] * sd), (float)(t.W[k] * sW), 0.f);
+}
+
+cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s) {
+    const int threads = 256;
+    const int64_t blocks = (g.n + threads - 1) / threads;
+    cudaError_t e = cudaMemsetAsync(emax, 0x80, sizeof(int), s);   // INT_MIN-ish start (0x80808080)
+    if (e != cudaSuccess) return e;
+    w_exponent_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t, emax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tables32_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t, emax, t32);
+    return cudaGetLastError();
+}
+
+}  // namespace fs

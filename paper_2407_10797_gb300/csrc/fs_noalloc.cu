@@ -140,7 +140,9 @@ extern "C" fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double
     pa.T = (double*)(sp + L.T);
     pa.S = (double*)(sp + L.S);
     pa.rot = (double2*)(sp + L.rot);
+    pa.rot32 = nullptr;
     pa.ntiles = (int)((n_bins + fs::kTile - 1) / fs::kTile);
+    pa.tile = fs::kTile;
     double* Fpart = F_part_dev ? F_part_dev : (double*)(sp + L.Fpart);
 
     // Every scratch byte a kernel reads is written earlier in this same call
@@ -152,7 +154,7 @@ extern "C" fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double
         return fs::set_error(FS_ECUDA, "cudaMemcpyAsync(edges): %s", cudaGetErrorString(e));
     if ((e = fs::launch_precompute(g, data_dev, psd_dev, tb, s)) != cudaSuccess ||
         (e = fs::launch_setup(g, params_dev, B, parts, global, s)) != cudaSuccess ||
-        (e = fs::launch_rotation(g, parts, B, sg, pa.rot, s)) != cudaSuccess ||
+        (e = fs::launch_rotation(g, parts, B, sg, pa.rot, nullptr, s)) != cudaSuccess ||
         (e = fs::launch_fp64_main(g, tb, parts, B, sg, pa, s)) != cudaSuccess ||
         (e = fs::launch_reduce(g, parts, B, sg, pa, Fpart, F_dev, s)) != cudaSuccess)
         return fs::set_error(FS_ECUDA, "fs_fstat_batch_noalloc launch: %s", cudaGetErrorString(e));
