@@ -130,6 +130,11 @@ FS_API fs_status fs_add_signal(fs_plan* plan, const fs_params* params_host, cons
  * (and a particle with invalid parameters reports (1, 0)).  Asynchronous. */
 FS_API fs_status fs_particle_bands(fs_plan* plan, const fs_params* params_dev, int B, int64_t* bands_dev);
 
+/* Select the launch variant of the FS_MIXED fused kernel: 0 = 2 CTAs per SM
+ * (up to 128 registers per thread), 1 = 3 CTAs per SM (up to 80).  Results are
+ * identical; only the speed differs.  Default 0. */
+FS_API fs_status fs_plan_set_variant(fs_plan* plan, int variant);
+
 /* Kernel timing on the plan's stream.  While enabled, every kernel the plan
  * launches is bracketed by CUDA events.  fs_plan_read_profile waits for the
  * plan's stream, returns the summed duration (ms) and launch count of one

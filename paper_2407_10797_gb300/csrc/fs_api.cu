@@ -57,6 +57,9 @@ struct fs_plan {
     // mixed mode: FP32 (dw, W) tables and the scale exponent
     float4* tab32;
     int* emax;
+    int mixed_variant;   // kernel variant of the mixed path (see fs_plan_set_variant)
+    int* span_list;      // [B][nspans] in-band particles per span (mixed path)
+    int* span_cnt;       // [nspans]
     // segment edges (global mode)
     int64_t* edges_dev;
     int64_t* edges_cache;
@@ -122,6 +125,9 @@ void free_workspace(fs_plan* p) {
     cudaFree(p->Fpart);
     cudaFree(p->rot);
     cudaFree(p->rot32);
+    cudaFree(p->span_list);
+    cudaFree(p->span_cnt);
+    p->span_list = p->span_cnt = nullptr;
     p->parts = nullptr;
     p->rot = nullptr;
     p->rot32 = nullptr;
@@ -143,7 +149,9 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
         (e = cudaMalloc(&p->S, sizeof(double) * 7 * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->Fpart, sizeof(double) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess ||
-        (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess) {
+        (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->span_list, sizeof(int) * (size_t)nb * (nt > 0 ? nt : 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->span_cnt, sizeof(int) * (nt > 0 ? nt : 1))) != cudaSuccess) {
         free_workspace(p);
         return cuda_fail(e, "cudaMalloc(workspace)");
     }
@@ -331,7 +339,8 @@ fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const i
     {
         ProfScope ps(p, 1);
         if (mixed) {
-            if ((e = fs::launch_mixed_main(p->grid, p->tab, p->tab32, p->parts, B, sg, pa, p->stream)) != cudaSuccess)
+            if ((e = fs::launch_mixed_main(p->grid, p->tab, p->tab32, p->parts, B, sg, pa, p->mixed_variant,
+                                           p->span_list, p->span_cnt, p->stream)) != cudaSuccess)
                 return cuda_fail(e, "mixed main launch");
         } else if ((e = fs::launch_fp64_main(p->grid, p->tab, p->parts, B, sg, pa, p->stream)) != cudaSuccess) {
             return cuda_fail(e, "fp64 main launch");
@@ -357,6 +366,13 @@ fs_status fs_particle_bands(fs_plan* p, const fs_params* params_dev, int B, int6
         return cuda_fail(e, "setup launch");
     if ((e = fs::launch_bands(p->parts, B, bands_dev, p->stream)) != cudaSuccess)
         return cuda_fail(e, "bands launch");
+    return FS_OK;
+}
+
+fs_status fs_plan_set_variant(fs_plan* p, int variant) {
+    g_err[0] = 0;
+    if (!p || variant < 0 || variant > 1) return fail(FS_EINVAL, "fs_plan_set_variant: variant must be 0 or 1");
+    p->mixed_variant = variant;
     return FS_OK;
 }
 

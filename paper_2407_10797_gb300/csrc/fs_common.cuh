@@ -64,6 +64,7 @@ struct Particle {
     double AD;                // R sin(theta) = AU cos(beta), s
     double clon, slon;
     double pr[4][5];          // a.p, a.q, b.p, b.q: c0 + c1 cos a + s1 sin a + c2 cos 2a + s2 sin 2a
+    double harm[2][9];        // F+ and Fx as A0 + sum_{h=1..4} (A_h cos h a + B_h sin h a): A0, A1, B1, ..., A4, B4
     int64_t klo, khi;         // band: first/last bin with t(f_k) in [0, T_obs] (klo > khi: empty)
     int valid;                // 0: non-finite or unphysical parameters
     int pad;

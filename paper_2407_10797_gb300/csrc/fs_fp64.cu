@@ -153,6 +153,33 @@ __global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int
             c[4] = kap * (ds * w[0] + dc * w[1]);
         }
     }
+    // F+ and Fx are degree-4 trig polynomials in alpha: their harmonics by a
+    // 9-point discrete Fourier transform (exact for degree <= 4).
+    {
+        double fp9[9], fx9[9];
+        for (int j = 0; j < 9; j++) {
+            double sj, cj;
+            sincospi(2.0 * j / 9.0, &sj, &cj);
+            antenna_of(P, cj, sj, fp9[j], fx9[j]);
+        }
+        for (int f = 0; f < 2; f++) {
+            const double* v = f == 0 ? fp9 : fx9;
+            double a0 = 0.0;
+            for (int j = 0; j < 9; j++) a0 += v[j];
+            P.harm[f][0] = a0 / 9.0;
+            for (int h = 1; h <= 4; h++) {
+                double ah = 0.0, bh = 0.0;
+                for (int j = 0; j < 9; j++) {
+                    double sj, cj;
+                    sincospi(2.0 * h * j / 9.0, &sj, &cj);
+                    ah += v[j] * cj;
+                    bh += v[j] * sj;
+                }
+                P.harm[f][2 * h - 1] = 2.0 * ah / 9.0;
+                P.harm[f][2 * h] = 2.0 * bh / 9.0;
+            }
+        }
+    }
     // band: first bin with t >= 0 and last bin with t <= T_obs (binary searches on k)
     if (global) {
         P.klo = 0;

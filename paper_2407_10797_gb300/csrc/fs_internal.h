@@ -65,8 +65,10 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
                           double* Fpart, double* F, cudaStream_t s);
 cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s);
+// variant 0: 2 CTAs/SM (up to 128 registers), 1: 3 CTAs/SM (up to 80 registers)
 cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
-                              const Segs& sg, const Partials& pa, cudaStream_t s);
+                              const Segs& sg, const Partials& pa, int variant, int* list, int* cnt,
+                              cudaStream_t s);
 int mixed_span();   // bins per H/T slot of the mixed path
 cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);
 cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,

@@ -29,14 +29,14 @@ constexpr int kSpanMix = kTileMix * kTilesPerSpan;    // 32768 bins: H/T granula
 constexpr int kWarpsMix = 8;                          // particles per CTA
 
 struct Anchor {
-    unsigned long long c[4];   // c0..c3 of the phase polynomial, cycles mod 1 in units of 2^-64
+    unsigned long long c[4];   // c0..c3 of the orbital-minus-Doppler phase polynomial, cycles mod 1, units 2^-64
+    double Fpa, Fxa;           // F+ and Fx at alpha_a (FP64)
     float w1, w2;              // d(alpha) = w1 dk + w2 dk^2, rad
-    float ca, sa;              // cos, sin alpha_a
-    float cda, sda;            // cos, sin (alpha_a - phi)
-    float ADfa, ADdf;          // AU cos(beta) f_a and AU cos(beta) df, cycles
-    int64_t ja, lo, hi;        // anchor bin and in-band range [lo, hi) of the tile
+    float e[5];                // Doppler: AU cos(beta) f_a cos^(n)(alpha_a - phi)/n!, n = 1..5 (cycles)
+    float q[4];                // Doppler: AU cos(beta) df cos^(n)(alpha_a - phi)/n!, n = 0..3 (cycles per bin)
+    float Fd[6][2];            // F+^(n)(alpha_a)/n!, Fx^(n)(alpha_a)/n!, n = 1..6
+    int ja, lo, hi;            // anchor bin and in-band range [lo, hi) of the tile, relative to the span start
     int mode;                  // 0: no in-band bin, 1: polynomial, 2: bin-by-bin FP64
-    int pad;
 };
 
 __device__ __forceinline__ unsigned long long to_fixed(double x) {
@@ -53,29 +53,31 @@ __device__ __forceinline__ unsigned long long poly_fx(const unsigned long long c
     return c[0] + u * (c[1] + u * (c[2] + u * c[3]));
 }
 
-// Bin-by-bin FP64 evaluation for tiles where the anchor expansion is not valid.
+// Bin-by-bin FP64 evaluation for tiles where the anchor expansion is not
+// valid; returns the phase mod 1 and the rotated antenna pair (G1, G2).
 __device__ __noinline__ void eval_bin_fallback(const Particle& P, const Tables& tb, int64_t k, double alpha0,
-                                               float* ph, float* Fp, float* Fx) {
+                                               double2 cs, float* ph, float* G1, float* G2) {
     FreqPowers fw;
     fw.u = tb.u[k];
     fw.g0h = tb.g0h[k];
     fw.e19 = tb.e19[k];
     const BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], fw, tb.g0l[k], alpha0);
     *ph = (float)ev.frac;
-    *Fp = (float)ev.Fp;
-    *Fx = (float)ev.Fx;
+    *G1 = (float)fma(cs.x, ev.Fp, cs.y * ev.Fx);
+    *G2 = (float)fma(cs.x, ev.Fx, -cs.y * ev.Fp);
 }
 
-__device__ void make_anchor(const Grid& g, const Tables& tb, const Particle& P, int64_t lo, int64_t hi, Anchor& A) {
-    A.lo = lo;
-    A.hi = hi;
+__device__ __noinline__ void make_anchor(const Grid& g, const Tables& tb, const Particle& P, int64_t span_lo, int64_t lo,
+                            int64_t hi, Anchor& A) {
+    A.lo = (int)(lo - span_lo);
+    A.hi = (int)(hi - span_lo);
     if (lo >= hi) {
         A.mode = 0;
         return;
     }
     const int64_t ja = lo + (hi - lo - 1) / 2;
     const double hmax = (double)max(ja - lo, hi - 1 - ja);
-    A.ja = ja;
+    A.ja = (int)(ja - span_lo);
     const double fh = tb.fh[ja], fl = tb.fl[ja], u = tb.u[ja], g0h = tb.g0h[ja], g0l = tb.g0l[ja],
                  e19 = tb.e19[ja];
     // orbital phase mod 1 (double-double leading term, exact f t_c)
@@ -111,8 +113,8 @@ __device__ void make_anchor(const Grid& g, const Tables& tb, const Particle& P, 
     const double Om = kTwoPi / kYearS;
     double sa, ca;
     sincos(fma(Om, ta, g.alpha0), &sa, &ca);
-    const double cda = fma(ca, P.clon, sa * P.slon);
-    const double sda = fma(sa, P.clon, -ca * P.slon);
+    const double cda = fma(ca, P.clon, sa * P.slon);   // cos(alpha_a - phi)
+    const double sda = fma(sa, P.clon, -ca * P.slon);  // sin(alpha_a - phi)
     acc -= fh * P.AD * cda;
     const double df = g.df;
     A.c[0] = to_fixed(acc);
@@ -121,33 +123,123 @@ __device__ void make_anchor(const Grid& g, const Tables& tb, const Particle& P, 
     A.c[3] = to_fixed(d3 * df * df * df / 6.0);
     A.w1 = (float)(Om * d2 * df);
     A.w2 = (float)(0.5 * Om * d3 * df * df);
-    A.ca = (float)ca;
-    A.sa = (float)sa;
-    A.cda = (float)cda;
-    A.sda = (float)sda;
-    A.ADfa = (float)(P.AD * fh);
-    A.ADdf = (float)(P.AD * df);
+    // Doppler phase minus its anchor value, with x = alpha - phi = x_a + da:
+    //   AD [f_a (cos x - cos x_a) + dk df cos x],  cos^(n)(x_a) cycles through (c, -s, -c, s)
+    {
+        const double cn[6] = {cda, -sda, -cda, sda, cda, -sda};
+        double fact = 1.0;
+        const double ADfa = P.AD * fh, ADdf = P.AD * df;
+        for (int n = 0; n <= 5; n++) {
+            if (n > 0) fact *= n;
+            if (n >= 1) A.e[n - 1] = (float)(ADfa * cn[n] / fact);
+            if (n <= 3) A.q[n] = (float)(ADdf * cn[n] / fact);
+        }
+    }
+    // antenna: F(alpha_a + da) = sum_n F^(n)(alpha_a) da^n / n!, from the harmonics;
+    // F(alpha_a) in FP64, the derivative terms (multiplied by da^n <= 0.06^n) in FP32
+    {
+        double ch[5], sh[5];
+        ch[1] = ca;
+        sh[1] = sa;
+#pragma unroll
+        for (int h = 2; h <= 4; h++) {
+            ch[h] = ch[h - 1] * ca - sh[h - 1] * sa;
+            sh[h] = sh[h - 1] * ca + ch[h - 1] * sa;
+        }
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+            const double* H = P.harm[f];
+            double F0 = H[0];
+            float uu[5], vv[5];
+#pragma unroll
+            for (int h = 1; h <= 4; h++) {
+                const double u_h = H[2 * h - 1] * ch[h] + H[2 * h] * sh[h];    // A cos + B sin
+                F0 += u_h;
+                uu[h] = (float)u_h;
+                vv[h] = (float)(H[2 * h] * ch[h] - H[2 * h - 1] * sh[h]);   // derivative / h
+            }
+            if (f == 0) A.Fpa = F0; else A.Fxa = F0;
+            // d^n/da^n of (u cos + v sin)-pairs: h^n (u, v, -u, -v)[n mod 4]
+            const float inv_fact[7] = {1.f, 1.f, 0.5f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f, 1.f / 720.f};
+#pragma unroll
+            for (int n = 1; n <= 6; n++) {
+                float sum = 0.f;
+#pragma unroll
+                for (int h = 1; h <= 4; h++) {
+                    float hn = 1.f;
+#pragma unroll
+                    for (int j = 0; j < n; j++) hn *= (float)h;
+                    const int r = n & 3;
+                    const float t = (r == 0) ? uu[h] : (r == 1) ? vv[h] : (r == 2) ? -uu[h] : -vv[h];
+                    sum = fmaf(hn, t, sum);
+                }
+                A.Fd[n - 1][f] = sum * inv_fact[n];
+            }
+        }
+    }
     // validity of the truncated expansions over |dk| <= hmax
     const double H = hmax * df;
     const double rem_phase = 1.2 * fabs(d4) * H * H * H * H / 24.0;     // cycles
     const double rem_alpha = 1.2 * Om * fabs(d4) * H * H * H / 6.0;     // rad
     const double da_max = fabs(Om * d2 * df) * hmax + fabs(0.5 * Om * d3 * df * df) * hmax * hmax;
-    A.mode = (rem_phase <= 1e-6 && rem_alpha <= 1e-6 && da_max <= 0.25) ? 1 : 2;
+    A.mode = (rem_phase <= 1e-6 && rem_alpha <= 1e-6 && da_max <= 0.06) ? 1 : 2;
 }
 
-__global__ void __launch_bounds__(kWarpsMix * 32)
+// Coefficients of G1 = c F+ + s Fx and G2 = c Fx - s F+ in powers of d(alpha)
+// for one (tile, segment): the constant terms in FP64 (G2 nearly cancels on a
+// short segment), the others in FP32.
+__device__ __forceinline__ void segment_coeffs(const Anchor& A, double2 r64, float2 r32, float g1[7], float g2[7]) {
+    g1[0] = (float)fma(r64.x, A.Fpa, r64.y * A.Fxa);
+    g2[0] = (float)fma(r64.x, A.Fxa, -r64.y * A.Fpa);
+#pragma unroll
+    for (int n = 1; n <= 6; n++) {
+        g1[n] = fmaf(r32.x, A.Fd[n - 1][0], r32.y * A.Fd[n - 1][1]);
+        g2[n] = fmaf(r32.x, A.Fd[n - 1][1], -r32.y * A.Fd[n - 1][0]);
+    }
+}
+
+// In-band particles of every span, in increasing particle order: one warp per
+// span.  list[span * B + j] is the j-th particle whose band meets the span and
+// cnt[span] their number.  The fused kernel gives each CTA 8 of them, so no
+// warp of a launched CTA idles on a particle that has no bin in the span.
+__global__ void span_lists_kernel(const Particle* __restrict__ parts, int B, Segs sg, int nspans, int* list,
+                                  int* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int span = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (span >= nspans) return;
+    const int64_t lo = (int64_t)span * kSpanMix, hi = lo + kSpanMix - 1;
+    int n = 0;
+    for (int b0 = 0; b0 < B; b0 += 32) {
+        const int b = b0 + lane;
+        bool in = false;
+        if (b < B && parts[b].valid) {
+            const SegView sv = seg_view(sg, parts[b]);
+            in = sv.lo <= sv.hi && sv.lo <= hi && sv.hi >= lo;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) list[(int64_t)span * B + n + __popc(m & ((1u << lane) - 1u))] = b;
+        n += __popc(m);
+    }
+    if (lane == 0) cnt[span] = n;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kWarpsMix * 32, MINB)
 mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts, int B,
-                  Segs sg, Partials pa) {
+                  Segs sg, Partials pa, const int* __restrict__ list, const int* __restrict__ cnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Anchor* anc = reinterpret_cast<Anchor*>(smem_raw);
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    const int b = blockIdx.y * kWarpsMix + w;
     const int span = blockIdx.x;
+    const int n_in = cnt[span];
+    if ((int)blockIdx.y * kWarpsMix >= n_in) return;   // whole CTA idle (uniform)
+    const int j = blockIdx.y * kWarpsMix + w;
+    const int b = j < n_in ? list[(int64_t)span * B + j] : B;
     const int64_t span_lo = (int64_t)span * kSpanMix;
 
     // ---- phase A: one anchor per thread (particle w, tile lane of the span)
-    bool active = b < B && parts[b].valid;
+    const bool active = b < B;
     SegView sv;
     if (active) {
         const Particle& P = parts[b];
@@ -155,7 +247,7 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
         int64_t lo = span_lo + (int64_t)lane * kTileMix, hi = lo + kTileMix;
         if (lo < sv.lo) lo = sv.lo;
         if (hi > sv.hi + 1) hi = sv.hi + 1;
-        make_anchor(g, tb, P, lo, hi, anc[threadIdx.x]);
+        make_anchor(g, tb, P, span_lo, lo, hi, anc[threadIdx.x]);
     } else {
         anc[threadIdx.x].mode = 0;
     }
@@ -164,33 +256,29 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
 
     // ---- phase B: warp w walks its particle's tiles of the span
     const Particle& P = parts[b];
-    float pr[4][5];
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 5; j++) pr[i][j] = (float)P.pr[i][j];
     const int64_t slot = (int64_t)b * pa.ntiles + span;
-    const float2* rotb = pa.rot32 + (int64_t)b * sg.Np;
+    const double2* rot64 = pa.rot + (int64_t)b * sg.Np;
+    const float2* rot32 = pa.rot32 + (int64_t)b * sg.Np;
+    const float4* tw_span = t32 + span_lo;
 
-    double accD[7];
+    float accS[7], acc[7];
 #pragma unroll
-    for (int c = 0; c < 7; c++) accD[c] = 0.0;
-    float acc[7];
+    for (int c = 0; c < 7; c++) accS[c] = 0.f;
     int cur = -1;        // warp-uniform current segment
     int nflush = 0;
     int pk = -1;         // this lane's segment
-    int64_t nxt = -1;    // first bin of the segment after pk
-    float2 rc = make_float2(1.f, 0.f);
+    int nxt = -1;        // first bin (span-relative) of the segment after pk
+    float g1[7], g2[7];
 
     for (int ti = 0; ti < kTilesPerSpan; ti++) {
         const Anchor& A = anc[w * 32 + ti];
         if (A.mode == 0) continue;
-        const int64_t lo = A.lo, hi = A.hi;
-        if (cur < 0) cur = sv.seg(lo);
+        const int lo = A.lo, hi = A.hi;
+        if (cur < 0) cur = sv.seg(span_lo + lo);
 #pragma unroll
         for (int c = 0; c < 7; c++) acc[c] = 0.f;
-        const int64_t k0 = lo + lane;
-        // fixed-point forward differences of the phase along this lane (step 32)
+        const int k0 = lo + lane;
+        bool fresh = true;   // segment coefficients must be (re)built for this tile
         unsigned long long F = 0, D1 = 0, D2 = 0, D3 = 0;
         if (A.mode == 1) {
             const long long d0 = (long long)(k0 - A.ja);
@@ -201,46 +289,40 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
             D2 = y2 - 2ull * y1 + y0;
             D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
         }
-        for (int64_t base = lo; base < hi; base += 32) {
-            const int64_t k = base + lane;
+        float d = (float)(k0 - A.ja);
+        for (int base = lo; base < hi; base += 32, d += 32.f) {
+            const int k = base + lane;
             const bool valid = k < hi;
             float t7[7];
 #pragma unroll
             for (int c = 0; c < 7; c++) t7[c] = 0.f;
             if (valid) {
+                const float4 tw = tw_span[k];
                 if (k >= nxt) {
-                    pk = sv.seg(k);
-                    nxt = sv.start(pk + 1);
-                    rc = rotb[pk];
+                    pk = sv.seg(span_lo + k);
+                    nxt = (int)(sv.start(pk + 1) - span_lo);
+                    fresh = true;
                 }
-                float ph, Fp, Fx;
+                float ph, G1, G2;
                 if (A.mode == 1) {
-                    const float d = (float)(k - A.ja);
+                    if (fresh) {
+                        segment_coeffs(A, rot64[pk], rot32[pk], g1, g2);
+                        fresh = false;
+                    }
                     const float da = fmaf(A.w2, d, A.w1) * d;
-                    const float x2 = da * da;
-                    const float sd = da * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
-                    const float cm1 = x2 * fmaf(x2, fmaf(x2, -1.f / 720.f, 1.f / 24.f), -0.5f);
-                    const float cal = A.ca + fmaf(A.ca, cm1, -A.sa * sd);
-                    const float sal = A.sa + fmaf(A.sa, cm1, A.ca * sd);
-                    const float dcd = fmaf(A.cda, cm1, -A.sda * sd);       // cos(alpha - phi) - cos(alpha_a - phi)
-                    const float dop = fmaf(A.ADdf * d, A.cda + dcd, A.ADfa * dcd);   // Doppler phase minus its anchor value
-                    ph = (float)(int)(F >> 32) * 2.3283064365386963e-10f - dop;
+                    G1 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g1[6], da, g1[5]), da, g1[4]), da, g1[3]), da, g1[2]), da, g1[1]),
+                              da, g1[0]);
+                    G2 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g2[6], da, g2[5]), da, g2[4]), da, g2[3]), da, g2[2]), da, g2[1]),
+                              da, g2[0]);
+                    const float dop1 = da * fmaf(fmaf(fmaf(fmaf(A.e[4], da, A.e[3]), da, A.e[2]), da, A.e[1]), da, A.e[0]);
+                    const float dop2 = d * fmaf(fmaf(fmaf(A.q[3], da, A.q[2]), da, A.q[1]), da, A.q[0]);
+                    ph = (float)(int)(F >> 32) * 2.3283064365386963e-10f - (dop1 + dop2);
                     ph -= rintf(ph);
-                    const float c2 = fmaf(2.f * cal, cal, -1.f), s2 = 2.f * sal * cal;
-                    float pj[4];
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-                        pj[i] = fmaf(pr[i][4], s2, fmaf(pr[i][3], c2, fmaf(pr[i][2], sal, fmaf(pr[i][1], cal, pr[i][0]))));
-                    Fp = 0.5f * ((pj[0] * pj[0] - pj[1] * pj[1]) - (pj[2] * pj[2] - pj[3] * pj[3]));
-                    Fx = pj[0] * pj[1] - pj[2] * pj[3];
                 } else {
-                    eval_bin_fallback(P, tb, k, g.alpha0, &ph, &Fp, &Fx);
+                    eval_bin_fallback(P, tb, span_lo + k, g.alpha0, rot64[pk], &ph, &G1, &G2);
                 }
                 float sn, cs;
                 __sincosf(6.283185307179586f * ph, &sn, &cs);
-                const float G1 = fmaf(rc.x, Fp, rc.y * Fx);
-                const float G2 = fmaf(rc.x, Fx, -rc.y * Fp);
-                const float4 tw = t32[k];
                 const float zr = fmaf(tw.x, cs, -tw.y * sn);
                 const float zi = fmaf(tw.x, sn, tw.y * cs);
                 t7[0] = G1 * zr;
@@ -262,9 +344,9 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
                 double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
 #pragma unroll
                 for (int c = 0; c < 7; c++) {
-                    const double v = warp_sum(accD[c] + (double)acc[c]);
+                    const double v = warp_sum((double)accS[c] + (double)acc[c]);
                     if (lane == 0) dst[c] = v;
-                    accD[c] = 0.0;
+                    accS[c] = 0.f;
                     acc[c] = 0.f;
                 }
                 nflush++;
@@ -278,23 +360,31 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
             D2 += D3;
         }
 #pragma unroll
-        for (int c = 0; c < 7; c++) accD[c] += (double)acc[c];
+        for (int c = 0; c < 7; c++) accS[c] += acc[c];
     }
     if (cur < 0) return;   // no in-band bin in this span (warp-uniform)
     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
 #pragma unroll
     for (int c = 0; c < 7; c++) {
-        const double v = warp_sum(accD[c]);
+        const double v = warp_sum((double)accS[c]);
         if (lane == 0) dst[c] = v;
     }
 }
 
 cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
-                              const Segs& sg, const Partials& pa, cudaStream_t s) {
+                              const Segs& sg, const Partials& pa, int variant, int* list, int* cnt,
+                              cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
-    dim3 grid((unsigned)pa.ntiles, (unsigned)((B + kWarpsMix - 1) / kWarpsMix));
+    const int nspans = pa.ntiles;
+    span_lists_kernel<<<(unsigned)((nspans * 32 + 255) / 256), 256, 0, s>>>(parts, B, sg, nspans, list, cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)nspans, (unsigned)((B + kWarpsMix - 1) / kWarpsMix));
     const size_t smem = sizeof(Anchor) * kWarpsMix * 32;
-    mixed_main_kernel<<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa);
+    if (variant == 1)
+        mixed_main_kernel<3><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, cnt);
+    else
+        mixed_main_kernel<2><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, cnt);
     return cudaGetLastError();
 }
 

@@ -62,11 +62,13 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_fstat_batch_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp,
                                              C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp, _vp]
         L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
+        L.fs_plan_set_variant.argtypes = [_vp, C.c_int]
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
         for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_add_signal", "fs_constants", "fs_particle_bands",
-                     "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc"):
+                     "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
+                     "fs_plan_set_variant"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -179,6 +181,9 @@ class Plan:
         return out
 
     KERNELS = {"setup": 0, "main": 1, "reduce": 2, "precompute": 3}
+
+    def set_variant(self, variant: int):
+        _check(self._L.fs_plan_set_variant(self._h, int(variant)))
 
     def set_profiling(self, enable: bool):
         _check(self._L.fs_plan_set_profiling(self._h, 1 if enable else 0))
