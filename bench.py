@@ -296,10 +296,12 @@ def fp32_peak_tflops() -> float:
     return 152 * 128 * 2 * 2070e6 / 1e12
 
 
-# FP32-pipe operations per in-band particle*bin of the mixed kernel's body
-# (algorithmic count, FMA = 2 flop; integer phase steps and the SFU sincos
-# counted as one flop per instruction).
-MIXED_FLOP_PER_PBIN = 150.0
+# Operations per in-band particle*bin of the mixed kernel's body (algorithmic
+# count, FMA = 2): orbital-phase offset 3, antenna pair G1, G2 as degree-6
+# polynomials 24, Doppler polynomial 17, phase assembly and reduction 5, SFU
+# sincos 3, z = dw e^{i Phi} 6, seven sums 16, fixed-point phase steps 6
+# (integer adds counted as one each).
+MIXED_FLOP_PER_PBIN = 80.0
 
 
 def run_gpu(args, world, rank, local):

@@ -11,8 +11,9 @@
 // (step 32) by forward differences with no phase drift.  The Doppler phase and
 // the antenna patterns are evaluated per bin as small-angle deltas from the
 // anchor's orbital phase alpha_a (FP32), the phase goes through the SFU sincos,
-// and the seven segment sums accumulate in FP32 per tile and in FP64 across
-// tiles.  A tile whose Taylor remainder bound exceeds 1e-6 cycle (or whose
+// and the seven segment sums accumulate in FP32 per lane (per tile, then per
+// span of 32 tiles), are summed across the warp in FP32 and stored as FP64
+// partials that the solve kernel adds in FP64.  A tile whose Taylor remainder bound exceeds 1e-6 cycle (or whose
 // orbital-phase excursion exceeds 0.25 rad) is evaluated bin by bin in FP64
 // instead, so the mode stays correct on any grid.
 #include <cfloat>
@@ -198,6 +199,41 @@ __device__ __forceinline__ void segment_coeffs(const Anchor& A, double2 r64, flo
     }
 }
 
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// One bin of a polynomial tile inside a single segment: phase from the
+// fixed-point value Fv, antenna and Doppler from the orbital-phase offset,
+// seven sums into acc.
+__device__ __forceinline__ void mixed_bin(unsigned long long Fv, float d, float4 tw, float w1, float w2,
+                                          const float g1[7], const float g2[7], const float e[5], const float q[4],
+                                          float acc[7]) {
+    const float da = fmaf(w2, d, w1) * d;
+    const float G1 =
+        fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g1[6], da, g1[5]), da, g1[4]), da, g1[3]), da, g1[2]), da, g1[1]), da, g1[0]);
+    const float G2 =
+        fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g2[6], da, g2[5]), da, g2[4]), da, g2[3]), da, g2[2]), da, g2[1]), da, g2[0]);
+    const float dop = fmaf(da, fmaf(fmaf(fmaf(fmaf(e[4], da, e[3]), da, e[2]), da, e[1]), da, e[0]),
+                           d * fmaf(fmaf(fmaf(q[3], da, q[2]), da, q[1]), da, q[0]));
+    float ph = fmaf((float)(int)(Fv >> 32), 2.3283064365386963e-10f, -dop);
+    ph -= rintf(ph);
+    float sn, cs;
+    __sincosf(6.283185307179586f * ph, &sn, &cs);
+    const float zr = fmaf(tw.x, cs, -tw.y * sn);
+    const float zi = fmaf(tw.x, sn, tw.y * cs);
+    acc[0] = fmaf(G1, zr, acc[0]);
+    acc[1] = fmaf(G1, zi, acc[1]);
+    acc[2] = fmaf(G2, zr, acc[2]);
+    acc[3] = fmaf(G2, zi, acc[3]);
+    const float wg = tw.z * G1;
+    acc[4] = fmaf(wg, G1, acc[4]);
+    acc[5] = fmaf(wg, G2, acc[5]);
+    acc[6] = fmaf(tw.z * G2, G2, acc[6]);
+}
+
 // In-band particles of every span, in increasing particle order: one warp per
 // span.  list[span * B + j] is the j-th particle whose band meets the span and
 // cnt[span] their number.  The fused kernel gives each CTA 8 of them, so no
@@ -277,87 +313,106 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
         if (cur < 0) cur = sv.seg(span_lo + lo);
 #pragma unroll
         for (int c = 0; c < 7; c++) acc[c] = 0.f;
-        const int k0 = lo + lane;
-        bool fresh = true;   // segment coefficients must be (re)built for this tile
-        unsigned long long F = 0, D1 = 0, D2 = 0, D3 = 0;
         if (A.mode == 1) {
-            const long long d0 = (long long)(k0 - A.ja);
-            const unsigned long long y0 = poly_fx(A.c, d0), y1 = poly_fx(A.c, d0 + 32), y2 = poly_fx(A.c, d0 + 64),
-                                     y3 = poly_fx(A.c, d0 + 96);
-            F = y0;
-            D1 = y1 - y0;
-            D2 = y2 - 2ull * y1 + y0;
-            D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
-        }
-        float d = (float)(k0 - A.ja);
-        for (int base = lo; base < hi; base += 32, d += 32.f) {
-            const int k = base + lane;
-            const bool valid = k < hi;
-            float t7[7];
+            // polynomial tile, walked as single-segment pieces [pa_lo, pa_hi)
+            const float w1 = A.w1, w2 = A.w2;
+            const float e[5] = {A.e[0], A.e[1], A.e[2], A.e[3], A.e[4]};
+            const float q[4] = {A.q[0], A.q[1], A.q[2], A.q[3]};
+            int pa_lo = lo;
+            while (pa_lo < hi) {
+                const int sp = sv.seg(span_lo + pa_lo);   // warp-uniform
+                if (sp != cur) {
+                    // segment `cur` ended before this piece: flush it
+                    double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
 #pragma unroll
-            for (int c = 0; c < 7; c++) t7[c] = 0.f;
-            if (valid) {
-                const float4 tw = tw_span[k];
-                if (k >= nxt) {
-                    pk = sv.seg(span_lo + k);
-                    nxt = (int)(sv.start(pk + 1) - span_lo);
-                    fresh = true;
-                }
-                float ph, G1, G2;
-                if (A.mode == 1) {
-                    if (fresh) {
-                        segment_coeffs(A, rot64[pk], rot32[pk], g1, g2);
-                        fresh = false;
+                    for (int c = 0; c < 7; c++) {
+                        const float v = warp_sum_f(accS[c] + acc[c]);
+                        if (lane == 0) dst[c] = (double)v;
+                        accS[c] = 0.f;
+                        acc[c] = 0.f;
                     }
-                    const float da = fmaf(A.w2, d, A.w1) * d;
-                    G1 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g1[6], da, g1[5]), da, g1[4]), da, g1[3]), da, g1[2]), da, g1[1]),
-                              da, g1[0]);
-                    G2 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g2[6], da, g2[5]), da, g2[4]), da, g2[3]), da, g2[2]), da, g2[1]),
-                              da, g2[0]);
-                    const float dop1 = da * fmaf(fmaf(fmaf(fmaf(A.e[4], da, A.e[3]), da, A.e[2]), da, A.e[1]), da, A.e[0]);
-                    const float dop2 = d * fmaf(fmaf(fmaf(A.q[3], da, A.q[2]), da, A.q[1]), da, A.q[0]);
-                    ph = (float)(int)(F >> 32) * 2.3283064365386963e-10f - (dop1 + dop2);
-                    ph -= rintf(ph);
-                } else {
+                    nflush++;
+                    cur = sp;
+                }
+                const int64_t nb = sv.start(sp + 1) - span_lo;
+                const int pa_hi = nb < hi ? (int)nb : hi;
+                segment_coeffs(A, rot64[sp], rot32[sp], g1, g2);
+                const int k0 = pa_lo + lane;
+                const long long d0 = (long long)(k0 - A.ja);
+                const unsigned long long y0 = poly_fx(A.c, d0), y1 = poly_fx(A.c, d0 + 32),
+                                         y2 = poly_fx(A.c, d0 + 64), y3 = poly_fx(A.c, d0 + 96);
+                unsigned long long F = y0, D1 = y1 - y0, D2 = y2 - 2ull * y1 + y0,
+                                   D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
+                float d = (float)(k0 - A.ja);
+                int k = k0;
+                // two bins per lane per iteration (k and k + 32): two independent chains
+                for (; k + 32 < pa_hi; k += 64, d += 64.f) {
+                    const float4 twa = tw_span[k];
+                    const float4 twb = tw_span[k + 32];
+                    const unsigned long long Fa = F, Fb = F + D1;
+                    F = Fb + D1 + D2;
+                    D1 += 2ull * D2 + D3;
+                    D2 += 2ull * D3;
+                    mixed_bin(Fa, d, twa, w1, w2, g1, g2, e, q, acc);
+                    mixed_bin(Fb, d + 32.f, twb, w1, w2, g1, g2, e, q, acc);
+                }
+                if (k < pa_hi) mixed_bin(F, d, tw_span[k], w1, w2, g1, g2, e, q, acc);
+                pa_lo = pa_hi;
+            }
+            // lanes' segment trackers are stale after this tile; the fallback path re-derives them
+            pk = -1;
+            nxt = -1;
+        } else {
+            // bin-by-bin FP64 tile (anchor expansion not valid)
+            for (int base = lo; base < hi; base += 32) {
+                const int k = base + lane;
+                const bool valid = k < hi;
+                float t7[7];
+#pragma unroll
+                for (int c = 0; c < 7; c++) t7[c] = 0.f;
+                if (valid) {
+                    const float4 tw = tw_span[k];
+                    if (k >= nxt) {
+                        pk = sv.seg(span_lo + k);
+                        nxt = (int)(sv.start(pk + 1) - span_lo);
+                    }
+                    float ph, G1, G2;
                     eval_bin_fallback(P, tb, span_lo + k, g.alpha0, rot64[pk], &ph, &G1, &G2);
+                    float sn, cs;
+                    __sincosf(6.283185307179586f * ph, &sn, &cs);
+                    const float zr = fmaf(tw.x, cs, -tw.y * sn);
+                    const float zi = fmaf(tw.x, sn, tw.y * cs);
+                    t7[0] = G1 * zr;
+                    t7[1] = G1 * zi;
+                    t7[2] = G2 * zr;
+                    t7[3] = G2 * zi;
+                    const float wg = tw.z * G1;
+                    t7[4] = wg * G1;
+                    t7[5] = wg * G2;
+                    t7[6] = tw.z * G2 * G2;
                 }
-                float sn, cs;
-                __sincosf(6.283185307179586f * ph, &sn, &cs);
-                const float zr = fmaf(tw.x, cs, -tw.y * sn);
-                const float zi = fmaf(tw.x, sn, tw.y * cs);
-                t7[0] = G1 * zr;
-                t7[1] = G1 * zi;
-                t7[2] = G2 * zr;
-                t7[3] = G2 * zi;
-                const float wg = tw.z * G1;
-                t7[4] = wg * G1;
-                t7[5] = wg * G2;
-                t7[6] = tw.z * G2 * G2;
+                while (true) {
+                    if (valid && pk == cur) {
+#pragma unroll
+                        for (int c = 0; c < 7; c++) acc[c] += t7[c];
+                    }
+                    const unsigned more = __ballot_sync(0xffffffffu, valid && pk > cur);
+                    if (!more) break;
+                    double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
+#pragma unroll
+                    for (int c = 0; c < 7; c++) {
+                        const float v = warp_sum_f(accS[c] + acc[c]);
+                        if (lane == 0) dst[c] = (double)v;
+                        accS[c] = 0.f;
+                        acc[c] = 0.f;
+                    }
+                    nflush++;
+                    int cand = (valid && pk > cur) ? pk : INT_MAX;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+                    cur = cand;
+                }
             }
-            while (true) {
-                if (valid && pk == cur) {
-#pragma unroll
-                    for (int c = 0; c < 7; c++) acc[c] += t7[c];
-                }
-                const unsigned more = __ballot_sync(0xffffffffu, valid && pk > cur);
-                if (!more) break;
-                double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
-#pragma unroll
-                for (int c = 0; c < 7; c++) {
-                    const double v = warp_sum((double)accS[c] + (double)acc[c]);
-                    if (lane == 0) dst[c] = v;
-                    accS[c] = 0.f;
-                    acc[c] = 0.f;
-                }
-                nflush++;
-                int cand = (valid && pk > cur) ? pk : INT_MAX;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
-                cur = cand;
-            }
-            F += D1;
-            D1 += D2;
-            D2 += D3;
         }
 #pragma unroll
         for (int c = 0; c < 7; c++) accS[c] += acc[c];
@@ -366,8 +421,8 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
 #pragma unroll
     for (int c = 0; c < 7; c++) {
-        const double v = warp_sum((double)accS[c]);
-        if (lane == 0) dst[c] = v;
+        const float v = warp_sum_f(accS[c]);
+        if (lane == 0) dst[c] = (double)v;
     }
 }
 
