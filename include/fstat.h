@@ -130,6 +130,62 @@ FS_API fs_status fs_add_signal(fs_plan* plan, const fs_params* params_host, cons
  * (and a particle with invalid parameters reports (1, 0)).  Asynchronous. */
 FS_API fs_status fs_particle_bands(fs_plan* plan, const fs_params* params_dev, int B, int64_t* bands_dev);
 
+/* ---- Particle swarm optimisation on the device (Sec. III.A) ------------- */
+
+/* State of R independent PSO runs of n_part particles each in the 5-D
+ * normalised search space [0,1]^5 of (M_c, t_c, sin(lat), lon, e0).  All
+ * pointers are device memory owned by the caller. */
+typedef struct {
+    int R;                 /* independent runs */
+    int n_part;            /* particles per run */
+    double* x;             /* [R][n_part][5] normalised positions */
+    double* v;             /* [R][n_part][5] velocities */
+    double* pbest_x;       /* [R][n_part][5] personal-best positions */
+    double* pbest_f;       /* [R][n_part] personal-best fitness */
+    double* fit;           /* [R][n_part] fitness of x (written by fs_pso_evaluate) */
+    const double* box;     /* [R][5][2] search box of each run: (lo, hi) of M_c [Msun], t_c [s],
+                              sin(lat), lon [rad], e0; x maps linearly onto it */
+    double q;              /* mass ratio of every particle */
+    unsigned int* iter;    /* device iteration counter, used by fs_pso_step(iteration < 0) and the graph */
+} fs_swarm;
+
+/* Initial state: x ~ U[0,1)^5, v ~ U[-x, 1-x) (Sec. III.A), pbest_x = x,
+ * pbest_f = fit = -inf; random numbers from Philox4x32-10 with counter
+ * (0xFFFFFFFF, particle, dim, run) and key = seed.  Asynchronous. */
+FS_API fs_status fs_pso_init(fs_plan* plan, const fs_swarm* swarm, uint64_t seed);
+
+/* Fitness of the current positions: fit = F_sum / N_p (the paper's F-hat,
+ * Eq. semi-cohF) with the segments of fs_fstat_batch (edges_host as there);
+ * a particle outside [0,1]^5 is not evaluated and gets -inf ("let them fly").
+ * R * n_part must not exceed the plan's reservation if the call is captured. */
+FS_API fs_status fs_pso_evaluate(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p);
+
+/* One PSO update (Eqs. pso_position_update, pso_velocity_update): personal
+ * bests on a strictly greater fitness, ring local best {i-1, i, i+1} with ties
+ * to the lowest index, v <- w v + c1 r1 (p - x) + c2 r2 (l - x) clamped to
+ * [-vmax, vmax], x <- x + v.  w = w0 - (w0 - w1) k / (n_iter - 1) at iteration
+ * k; r1, r2 from Philox4x32-10 with counter (k, particle, dim, run), key = seed.
+ * iteration >= 0 gives k directly; iteration < 0 reads k from *swarm->iter and
+ * increments it afterwards (on the device).  lbest_dev: optional [R][n_part]
+ * local-best indices.  Asynchronous. */
+FS_API fs_status fs_pso_step(fs_plan* plan, const fs_swarm* swarm, uint64_t seed, int iteration, double w0,
+                             double w1, int n_iter, double c1, double c2, double vmax, int* lbest_dev);
+
+/* Best personal best of every run: best_f_dev [R], best_idx_dev [R] (lowest
+ * particle index among equals).  Asynchronous. */
+FS_API fs_status fs_pso_best(fs_plan* plan, const fs_swarm* swarm, double* best_f_dev, int* best_idx_dev);
+
+/* Capture one full PSO iteration (fs_pso_evaluate + fs_pso_step with the
+ * device iteration counter) as a CUDA graph on the plan's stream, which must
+ * not be the legacy default stream.  Reserve the workspace first (B >= R *
+ * n_part).  Replaces any graph the plan held.  Synchronous. */
+FS_API fs_status fs_pso_graph_build(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p,
+                                    uint64_t seed, double w0, double w1, int n_iter, double c1, double c2,
+                                    double vmax);
+
+/* Launch the captured iteration n times on the plan's stream.  Asynchronous. */
+FS_API fs_status fs_pso_graph_run(fs_plan* plan, int n);
+
 /* Select the launch variant of the FS_MIXED fused kernel: 0 = 2 CTAs per SM
  * (up to 128 registers per thread), 1 = 3 CTAs per SM (up to 80).  Results are
  * identical; only the speed differs.  Default 0. */

@@ -60,6 +60,11 @@ struct fs_plan {
     int mixed_variant;   // kernel variant of the mixed path (see fs_plan_set_variant)
     int* span_list;      // [B][nspans] in-band particles per span (mixed path)
     int* span_cnt;       // [nspans]
+    // swarm evaluation scratch and the captured PSO iteration
+    fs_params* pso_params;   // [B_cap]
+    double* pso_F;           // [B_cap]
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
     // segment edges (global mode)
     int64_t* edges_dev;
     int64_t* edges_cache;
@@ -127,6 +132,10 @@ void free_workspace(fs_plan* p) {
     cudaFree(p->rot32);
     cudaFree(p->span_list);
     cudaFree(p->span_cnt);
+    cudaFree(p->pso_params);
+    cudaFree(p->pso_F);
+    p->pso_params = nullptr;
+    p->pso_F = nullptr;
     p->span_list = p->span_cnt = nullptr;
     p->parts = nullptr;
     p->rot = nullptr;
@@ -151,7 +160,9 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
         (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->span_list, sizeof(int) * (size_t)nb * (nt > 0 ? nt : 1))) != cudaSuccess ||
-        (e = cudaMalloc(&p->span_cnt, sizeof(int) * (nt > 0 ? nt : 1))) != cudaSuccess) {
+        (e = cudaMalloc(&p->span_cnt, sizeof(int) * (nt > 0 ? nt : 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->pso_params, sizeof(fs_params) * (size_t)nb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->pso_F, sizeof(double) * (size_t)nb)) != cudaSuccess) {
         free_workspace(p);
         return cuda_fail(e, "cudaMalloc(workspace)");
     }
@@ -237,6 +248,8 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
 fs_status fs_plan_destroy(fs_plan* p) {
     if (!p) return FS_OK;
     cudaStreamSynchronize(p->stream);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
     free_workspace(p);
     cudaFree(p->tab_base);
     cudaFree(p->edges_dev);
@@ -366,6 +379,126 @@ fs_status fs_particle_bands(fs_plan* p, const fs_params* params_dev, int B, int6
         return cuda_fail(e, "setup launch");
     if ((e = fs::launch_bands(p->parts, B, bands_dev, p->stream)) != cudaSuccess)
         return cuda_fail(e, "bands launch");
+    return FS_OK;
+}
+
+static fs_status check_swarm(const fs_swarm* w) {
+    if (!w || w->R < 0 || w->n_part < 1 || !w->x || !w->v || !w->pbest_x || !w->pbest_f || !w->fit)
+        return fail(FS_EINVAL, "swarm: need R >= 0, n_part >= 1 and non-NULL state arrays");
+    if ((int64_t)w->R * w->n_part > 65535 * 8) return fail(FS_EINVAL, "swarm: R * n_part too large");
+    return FS_OK;
+}
+
+fs_status fs_pso_init(fs_plan* p, const fs_swarm* w, uint64_t seed) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_pso_init: plan is NULL");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    cudaError_t e = fs::launch_pso_init(w->R, w->n_part, seed, w->x, w->v, w->pbest_x, w->pbest_f, w->fit, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pso init launch");
+    if (w->iter && (e = cudaMemsetAsync(w->iter, 0, sizeof(unsigned int), p->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync(iter)");
+    return FS_OK;
+}
+
+fs_status fs_pso_evaluate(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_pso_evaluate: plan is NULL");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    if (!w->box) return fail(FS_EINVAL, "fs_pso_evaluate: box is NULL");
+    const int n = w->R * w->n_part;
+    if (n == 0) return FS_OK;
+    if ((st = ensure_workspace(p, n, Np)) != FS_OK) return st;
+    cudaError_t e = fs::launch_pso_map(w->R, w->n_part, w->x, w->box, w->q, p->pso_params, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pso map launch");
+    if ((st = fs_fstat_batch(p, p->pso_params, n, edges_host, Np, p->pso_F, nullptr)) != FS_OK) return st;
+    if ((e = fs::launch_pso_fitness(n, p->pso_F, Np, w->fit, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "pso fitness launch");
+    return FS_OK;
+}
+
+fs_status fs_pso_step(fs_plan* p, const fs_swarm* w, uint64_t seed, int iteration, double w0, double w1, int n_iter,
+                      double c1, double c2, double vmax, int* lbest_dev) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_pso_step: plan is NULL");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    if (n_iter < 1 || !(vmax > 0.0)) return fail(FS_EINVAL, "fs_pso_step: need n_iter >= 1 and vmax > 0");
+    if (iteration < 0 && !w->iter) return fail(FS_EINVAL, "fs_pso_step: iteration < 0 needs swarm->iter");
+    const bool dev_iter = iteration < 0;
+    cudaError_t e = fs::launch_pso_step(w->R, w->n_part, seed, dev_iter ? w->iter : nullptr,
+                                        dev_iter ? 0u : (unsigned int)iteration, w0, w1, n_iter, c1, c2, vmax, w->x,
+                                        w->v, w->pbest_x, w->pbest_f, w->fit, lbest_dev,
+                                        dev_iter ? w->iter : nullptr, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pso step launch");
+    return FS_OK;
+}
+
+fs_status fs_pso_best(fs_plan* p, const fs_swarm* w, double* best_f, int* best_i) {
+    g_err[0] = 0;
+    if (!p || !best_f || !best_i) return fail(FS_EINVAL, "fs_pso_best: NULL argument");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    cudaError_t e = fs::launch_pso_best(w->R, w->n_part, w->pbest_f, best_f, best_i, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pso best launch");
+    return FS_OK;
+}
+
+fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np, uint64_t seed,
+                             double w0, double w1, int n_iter, double c1, double c2, double vmax) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_pso_graph_build: plan is NULL");
+    if (!p->stream) return fail(FS_EINVAL, "fs_pso_graph_build: the plan's stream is the legacy default stream");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    if (!w->iter) return fail(FS_EINVAL, "fs_pso_graph_build: swarm->iter is NULL");
+    const int n = w->R * w->n_part;
+    // everything that may allocate, copy or synchronise happens before capture
+    if ((st = ensure_workspace(p, n > 0 ? n : 1, Np)) != FS_OK) return st;
+    if ((st = fs_pso_evaluate(p, w, edges_host, Np)) != FS_OK) return st;   // also uploads the edges
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const int prof = p->profiling;
+    p->profiling = 0;
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+    }
+    if (p->graph) {
+        cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    if ((e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        p->profiling = prof;
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    fs_status s1 = fs_pso_evaluate(p, w, edges_host, Np);
+    fs_status s2 = s1 == FS_OK ? fs_pso_step(p, w, seed, -1, w0, w1, n_iter, c1, c2, vmax, nullptr) : s1;
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(p->stream, &gr);
+    p->profiling = prof;
+    if (s2 != FS_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s2;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if ((e = cudaGraphInstantiate(&p->graph_exec, gr, 0)) != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    p->graph = gr;
+    return FS_OK;
+}
+
+fs_status fs_pso_graph_run(fs_plan* p, int n) {
+    g_err[0] = 0;
+    if (!p || n < 0) return fail(FS_EINVAL, "fs_pso_graph_run: bad argument");
+    if (!p->graph_exec) return fail(FS_EINVAL, "fs_pso_graph_run: no graph (call fs_pso_graph_build)");
+    for (int i = 0; i < n; i++) {
+        cudaError_t e = cudaGraphLaunch(p->graph_exec, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
     return FS_OK;
 }
 

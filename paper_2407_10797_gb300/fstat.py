@@ -40,6 +40,11 @@ _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 
 
+class fs_swarm(C.Structure):
+    _fields_ = [("R", C.c_int), ("n_part", C.c_int), ("x", _vp), ("v", _vp), ("pbest_x", _vp),
+                ("pbest_f", _vp), ("fit", _vp), ("box", _vp), ("q", C.c_double), ("iter", _vp)]
+
+
 def load(build_if_missing: bool = True) -> C.CDLL:
     """Load libfs_gb300.so (compiling it first if it is missing or stale)."""
     global _lib
@@ -63,12 +68,23 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                              C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp, _vp]
         L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
         L.fs_plan_set_variant.argtypes = [_vp, C.c_int]
+        _sw = C.POINTER(fs_swarm)
+        _ep = C.POINTER(C.c_int64)
+        L.fs_pso_init.argtypes = [_vp, _sw, C.c_uint64]
+        L.fs_pso_evaluate.argtypes = [_vp, _sw, _ep, C.c_int]
+        L.fs_pso_step.argtypes = [_vp, _sw, C.c_uint64, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
+                                  C.c_double, C.c_double, _vp]
+        L.fs_pso_best.argtypes = [_vp, _sw, _vp, _vp]
+        L.fs_pso_graph_build.argtypes = [_vp, _sw, _ep, C.c_int, C.c_uint64, C.c_double, C.c_double, C.c_int,
+                                         C.c_double, C.c_double, C.c_double]
+        L.fs_pso_graph_run.argtypes = [_vp, C.c_int]
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
         for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_add_signal", "fs_constants", "fs_particle_bands",
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
-                     "fs_plan_set_variant"):
+                     "fs_plan_set_variant", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
+                     "fs_pso_graph_build", "fs_pso_graph_run"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -235,3 +251,72 @@ def fstat_batch_noalloc(grid, data, psd, params, Np: int, edges=None, F=None, F_
                                     _cuda_ptr(F_part, torch.float64) if F_part is not None else None,
                                     _stream_handle(stream)))
     return F, F_part
+
+
+def _edges_arg(edges, Np):
+    if edges is None:
+        return None, None
+    arr = np.ascontiguousarray(edges, dtype=np.int64)
+    if arr.shape != (Np + 1,):
+        raise ValueError("edges must have N_p + 1 entries")
+    return arr, arr.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+class Swarm:
+    """Device state of R PSO runs x n_part particles in [0,1]^5 (fs_swarm).
+
+    box: float64 [R, 5, 2] search boxes (lo, hi) of (M_c [Msun], t_c [s],
+    sin(lat), lon [rad], e0)."""
+
+    def __init__(self, plan: "Plan", R: int, n_part: int, box, q: float = 1.0):
+        import torch
+        self.plan = plan
+        self.R, self.n_part = int(R), int(n_part)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        z = lambda *shape: torch.zeros(*shape, dtype=torch.float64, device=dev)
+        self.x = z(R, n_part, 5)
+        self.v = z(R, n_part, 5)
+        self.pbest_x = z(R, n_part, 5)
+        self.pbest_f = z(R, n_part)
+        self.fit = z(R, n_part)
+        self.box = torch.as_tensor(np.ascontiguousarray(box, dtype=np.float64)).to(dev).reshape(R, 5, 2).contiguous()
+        self.iter = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.best_f = z(R)
+        self.best_i = torch.zeros(R, dtype=torch.int32, device=dev)
+        self.c = fs_swarm(self.R, self.n_part, self.x.data_ptr(), self.v.data_ptr(), self.pbest_x.data_ptr(),
+                          self.pbest_f.data_ptr(), self.fit.data_ptr(), self.box.data_ptr(), float(q),
+                          self.iter.data_ptr())
+
+    def set_box(self, box):
+        self.box.copy_(torch_tensor(box).reshape(self.R, 5, 2))
+
+    def init(self, seed: int):
+        _check(load().fs_pso_init(self.plan._h, C.byref(self.c), int(seed)))
+
+    def evaluate(self, Np: int, edges=None):
+        arr, e = _edges_arg(edges, Np)
+        _check(load().fs_pso_evaluate(self.plan._h, C.byref(self.c), e, int(Np)))
+
+    def step(self, seed: int, iteration: int, w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5, lbest=None):
+        _check(load().fs_pso_step(self.plan._h, C.byref(self.c), int(seed), int(iteration), float(w0), float(w1),
+                                  int(n_iter), float(c1), float(c2), float(vmax),
+                                  None if lbest is None else C.c_void_p(lbest.data_ptr())))
+
+    def best(self):
+        """(best fitness [R], best particle index [R]) as CUDA tensors."""
+        _check(load().fs_pso_best(self.plan._h, C.byref(self.c), C.c_void_p(self.best_f.data_ptr()),
+                                  C.c_void_p(self.best_i.data_ptr())))
+        return self.best_f, self.best_i
+
+    def graph_build(self, Np: int, seed: int, edges=None, w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5):
+        arr, e = _edges_arg(edges, Np)
+        _check(load().fs_pso_graph_build(self.plan._h, C.byref(self.c), e, int(Np), int(seed), float(w0),
+                                         float(w1), int(n_iter), float(c1), float(c2), float(vmax)))
+
+    def graph_run(self, n: int):
+        _check(load().fs_pso_graph_run(self.plan._h, int(n)))
+
+
+def torch_tensor(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()

@@ -1,0 +1,132 @@
+"""Device PSO step (Sec. III.A) against the CPU oracle, bit for bit, and the
+captured PSO iteration against eager launches."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2407_10797_gb300 import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_10797_gb300 import fstat
+    fstat.load()
+    return fstat
+
+
+@pytest.fixture(scope="module")
+def plan(fst):
+    g = S.tiny_grid(n=6000, f_min=0.02, stride=4)
+    psd = S.lisa_like_psd(g.freqs())
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p = fst.Plan.from_grid(g, mode=fst.FS_MIXED, stream=s)
+        p.set_data(torch.from_numpy(S.gaussian_noise(g, psd, 3)).cuda(), torch.from_numpy(psd).cuda())
+    torch.cuda.synchronize()
+    p.grid = g
+    p.psd = psd
+    yield p
+    p.close()
+
+
+def unit_box(R):
+    return np.tile(np.array([[10.0, 50.0], [0.0, 1e8], [-1.0, 1.0], [0.0, 2 * np.pi], [0.0, 0.1]]), (R, 1, 1))
+
+
+def test_init_matches_oracle(fst, plan):
+    R, Np = 3, 40
+    sw = fst.Swarm(plan, R, Np, unit_box(R))
+    sw.init(seed=12345)
+    torch.cuda.synchronize()
+    xo, vo = O.pso_init(R, Np, 5, 12345)
+    assert np.array_equal(sw.x.cpu().numpy(), xo)
+    assert np.array_equal(sw.v.cpu().numpy(), vo)
+    assert np.all(np.isneginf(sw.pbest_f.cpu().numpy()))
+
+
+def test_steps_bit_exact_with_oracle(fst, plan):
+    """Random fitness arrays with NaN, -inf and ties; several iterations."""
+    R, Np, seed, n_iter = 4, 40, 99, 7
+    sw = fst.Swarm(plan, R, Np, unit_box(R))
+    sw.init(seed)
+    torch.cuda.synchronize()
+    x = sw.x.cpu().numpy().copy()
+    v = sw.v.cpu().numpy().copy()
+    pbx = sw.pbest_x.cpu().numpy().copy()
+    pbf = sw.pbest_f.cpu().numpy().copy()
+    rng = np.random.default_rng(0)
+    lb_dev = torch.zeros(R, Np, dtype=torch.int32, device="cuda")
+    for it in range(n_iter):
+        fit = np.round(rng.normal(size=(R, Np)), 1)          # many ties
+        fit[rng.random((R, Np)) < 0.1] = -np.inf
+        fit[rng.random((R, Np)) < 0.05] = np.nan
+        sw.fit.copy_(torch.from_numpy(fit))
+        sw.step(seed, it, w0=0.9, w1=0.4, n_iter=n_iter, c1=2.0, c2=2.0, vmax=0.5, lbest=lb_dev)
+        w = 0.9 - (0.9 - 0.4) * (it / (n_iter - 1))
+        lb = O.pso_step(x, v, pbx, pbf, fit, seed, it, w, 2.0, 2.0, 0.5)
+        torch.cuda.synchronize()
+        assert np.array_equal(lb_dev.cpu().numpy(), lb)
+        assert np.array_equal(sw.pbest_f.cpu().numpy(), pbf)
+        assert np.array_equal(sw.pbest_x.cpu().numpy(), pbx)
+        assert np.array_equal(sw.v.cpu().numpy(), v)
+        assert np.array_equal(sw.x.cpu().numpy(), x)
+
+
+def test_device_iteration_counter_and_graph_replay(fst, plan):
+    R, Np, seed = 2, 40, 5
+    box = unit_box(R)
+    g = plan.grid
+    box[:, 1] = [0.3 * g.T_obs, 1.5 * g.T_obs]
+
+    def fresh():
+        sw = fst.Swarm(plan, R, Np, box)
+        with torch.cuda.stream(plan.stream):
+            sw.init(seed)
+        return sw
+
+    eager, graphed = fresh(), fresh()
+    with torch.cuda.stream(plan.stream):
+        for it in range(5):
+            eager.evaluate(16)
+            eager.step(seed, -1, n_iter=5)
+        graphed.graph_build(16, seed, n_iter=5)
+        graphed.graph_run(5)
+    torch.cuda.synchronize()
+    assert int(graphed.iter.item()) == 5 and int(eager.iter.item()) == 5
+    for name in ("x", "v", "pbest_x", "pbest_f", "fit"):
+        assert torch.equal(getattr(eager, name), getattr(graphed, name)), name
+
+
+def test_evaluate_is_F_hat_and_let_them_fly(fst, plan):
+    R, Np = 2, 40
+    g = plan.grid
+    box = unit_box(R)
+    box[:, 1] = [0.3 * g.T_obs, 1.5 * g.T_obs]
+    sw = fst.Swarm(plan, R, Np, box)
+    with torch.cuda.stream(plan.stream):
+        sw.init(7)
+        sw.x[0, :5] += 2.0   # outside the unit box
+        sw.evaluate(8)
+    torch.cuda.synchronize()
+    fit = sw.fit.cpu().numpy()
+    assert np.all(np.isneginf(fit[0, :5]))
+    # the inside particles: F_sum / N_p of the mapped parameters
+    x = sw.x.cpu().numpy()
+    y = box[:, None, :, 0] + x * (box[:, None, :, 1] - box[:, None, :, 0])
+    P = np.stack([y[..., 0], y[..., 1], np.arcsin(np.clip(y[..., 2], -1, 1)), y[..., 3], y[..., 4],
+                  np.ones_like(y[..., 0])], axis=-1).reshape(-1, 6)
+    with torch.cuda.stream(plan.stream):
+        F, _ = plan.fstat(torch.from_numpy(P).cuda(), 8)
+    torch.cuda.synchronize()
+    Fh = F.cpu().numpy().reshape(R, Np) / 8
+    inside = ~np.isneginf(fit)
+    # the host mapping rounds t_c differently from the device FMA by an ulp,
+    # which moves F by ~1e-9; a wrong mapping would move it by O(1)
+    assert np.allclose(fit[inside], Fh[inside], rtol=1e-6, atol=0)
