@@ -1,0 +1,212 @@
+"""Hierarchical search controller (Sec. III.B): stages of PSO runs over
+search boxes, each stage narrowing the boxes around the previous winners.
+
+All runs of a stage -- n_boxes boxes x runs_per_box runs x n_part particles,
+each run with its own box -- are one swarm on the device, so one PSO iteration
+is one batched F-statistic launch; the iteration (map, F-statistic, fitness,
+update) is captured once as a CUDA graph and replayed n_iter times.  The host
+only builds boxes and picks best-of-runs winners between stages.
+
+Stage layout (the paper's three stages, Sec. III.B, generalised to the
+four-stage N_p = 256 -> 64 -> 16 -> 1 schedule with a fixed number of boxes
+per stage):
+  stage 1: the t_c prior split into n_boxes contiguous intervals of uneven
+           (Dirichlet) widths, every other parameter over its full prior;
+  stage 2: boxes centred on the stage-1 winners, narrowed in t_c and M_c;
+  stage 3: boxes centred on the stage-2 winners, narrowed in every parameter;
+  stage 4: boxes centred on the best stage-3 winner and on its mirror image
+           in ecliptic latitude (theta -> pi - theta, Sec. III.B stage 3),
+           fully coherent (N_p = 1).
+Best-of-runs and ties: the run with the largest fitness, lowest index first.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+from dataclasses import asdict, dataclass, field
+
+import numpy as np
+
+from . import fstat
+from . import synth as S
+
+YEAR = S.YEAR_S
+
+
+@dataclass
+class StageSpec:
+    Np: int
+    n_iter: int
+    rule: str                      # "split_tc" | "around" | "around_best_mirror"
+    widths: tuple = ()             # full widths (M_c [Msun], t_c [s], sin(lat), lon [rad], e0); None = prior
+    w0: float = 0.9
+    w1: float = 0.4
+
+
+def default_stages(n_iter: int = 2000) -> list[StageSpec]:
+    """Widths follow the paper's stage 2 (0.01 yr, 0.6 Msun) and stage 3
+    (0.004 yr, 0.3 Msun, 0.4 rad, 0.4 rad, 0.006) boxes; stage 4 halves stage 3."""
+    return [
+        StageSpec(256, n_iter, "split_tc"),
+        StageSpec(64, n_iter, "around", (0.6, 0.01 * YEAR, None, None, None)),
+        StageSpec(16, n_iter, "around", (0.3, 0.004 * YEAR, 0.4, 0.4, 0.006)),
+        StageSpec(1, n_iter, "around_best_mirror", (0.15, 0.002 * YEAR, 0.2, 0.2, 0.003)),
+    ]
+
+
+def prior_box(prior: S.Prior) -> np.ndarray:
+    return np.array([[prior.Mc_lo, prior.Mc_hi], [prior.tc_lo, prior.tc_hi], [-1.0, 1.0], [0.0, 2.0 * np.pi],
+                     [0.0, prior.e0_hi]])
+
+
+def to_physical(xn: np.ndarray, box: np.ndarray, q: float = 1.0) -> np.ndarray:
+    """Normalised position [5] in box [5, 2] -> (M_c, t_c, lat, lon, e0, q)."""
+    y = box[:, 0] + xn * (box[:, 1] - box[:, 0])
+    return np.array([y[0], y[1], math.asin(max(-1.0, min(1.0, y[2]))), y[3], y[4], q])
+
+
+def to_normal_coords(p: np.ndarray) -> np.ndarray:
+    """(M_c, t_c, lat, lon, e0) -> the search coordinates (M_c, t_c, sin(lat), lon, e0)."""
+    return np.array([p[0], p[1], math.sin(p[2]), p[3], p[4]])
+
+
+def box_around(center: np.ndarray, widths, prior: np.ndarray) -> np.ndarray:
+    """Box of the given full widths centred on `center` (search coordinates),
+    shifted to stay inside the prior; None keeps the prior range."""
+    b = prior.copy()
+    for j, wj in enumerate(widths):
+        if wj is None:
+            continue
+        lo, hi = center[j] - 0.5 * wj, center[j] + 0.5 * wj
+        if j == 3:   # longitude is periodic: no clipping
+            b[j] = [lo, hi]
+            continue
+        if lo < prior[j, 0]:
+            lo, hi = prior[j, 0], min(prior[j, 1], prior[j, 0] + wj)
+        if hi > prior[j, 1]:
+            lo, hi = max(prior[j, 0], prior[j, 1] - wj), prior[j, 1]
+        b[j] = [lo, hi]
+    return b
+
+
+@dataclass
+class StageResult:
+    stage: int
+    Np: int
+    boxes: list
+    winners: list          # physical parameters of the best run of every box
+    winner_f: list         # their fitness (F-hat)
+    seconds: float
+
+
+class HierarchicalSearch:
+    def __init__(self, plan: "fstat.Plan", prior: S.Prior, stages: list[StageSpec] | None = None,
+                 n_boxes: int = 16, runs_per_box: int = 8, n_part: int = 40, seed: int = 0, q: float = 1.0,
+                 checkpoint_dir: str | None = None, c1: float = 2.0, c2: float = 2.0, vmax: float = 0.5,
+                 bounds: np.ndarray | None = None):
+        """bounds: optional [5, 2] search bounds overriding the prior's (a zero
+        width pins a coordinate)."""
+        self.plan = plan
+        self.prior = prior
+        self.bounds = None if bounds is None else np.asarray(bounds, dtype=np.float64)
+        self.stages = stages if stages is not None else default_stages()
+        self.n_boxes, self.runs_per_box, self.n_part = n_boxes, runs_per_box, n_part
+        self.seed, self.q = seed, q
+        self.ckpt = checkpoint_dir
+        self.c1, self.c2, self.vmax = c1, c2, vmax
+        self.results: list[StageResult] = []
+
+    # ---------------------------------------------------------------- boxes
+    def stage_boxes(self, i: int) -> np.ndarray:
+        spec = self.stages[i]
+        pb = prior_box(self.prior) if self.bounds is None else self.bounds.copy()
+        if spec.rule == "split_tc":
+            u = S.uniforms(self.seed, 0x53504C54, self.n_boxes)           # "SPLT"
+            w = -np.log1p(-u)                                              # Dirichlet(1) via exponentials
+            edges = pb[1, 0] + (pb[1, 1] - pb[1, 0]) * np.concatenate([[0.0], np.cumsum(w) / np.sum(w)])
+            boxes = np.repeat(pb[None], self.n_boxes, axis=0)
+            boxes[:, 1, 0] = edges[:-1]
+            boxes[:, 1, 1] = edges[1:]
+            return boxes
+        prev = self.results[i - 1]
+        if spec.rule == "around":
+            centers = [to_normal_coords(np.array(p)) for p in prev.winners]
+        elif spec.rule == "around_best_mirror":
+            best = np.array(prev.winners[int(np.argmax(prev.winner_f))])
+            c = to_normal_coords(best)
+            m = c.copy()
+            m[2] = -m[2]                                                   # theta -> pi - theta
+            centers = [c if k % 2 == 0 else m for k in range(self.n_boxes)]
+        else:
+            raise ValueError(spec.rule)
+        return np.stack([box_around(c, spec.widths, pb) for c in centers])
+
+    # ---------------------------------------------------------------- one stage
+    def run_stage(self, i: int) -> StageResult:
+        import torch
+        spec = self.stages[i]
+        boxes = self.stage_boxes(i)
+        R = self.n_boxes * self.runs_per_box
+        run_boxes = np.repeat(boxes, self.runs_per_box, axis=0)
+        stage_seed = (self.seed << 8) + i
+        t0 = time.perf_counter()
+        with torch.cuda.stream(self.plan.stream):
+            sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q)
+            sw.init(stage_seed)
+            sw.graph_build(spec.Np, stage_seed, n_iter=spec.n_iter, w0=spec.w0, w1=spec.w1, c1=self.c1,
+                           c2=self.c2, vmax=self.vmax)
+            sw.graph_run(spec.n_iter - 1)      # graph_build evaluated once; the graph does evaluate + step
+            sw.evaluate(spec.Np)               # fitness of the final positions
+            sw.step(stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter)   # folds them into pbest
+            best_f, best_i = sw.best()
+            bf = best_f.cpu().numpy()
+            bi = best_i.cpu().numpy()
+            pbx = sw.pbest_x.cpu().numpy()
+        winners, wf = [], []
+        for k in range(self.n_boxes):
+            runs = np.arange(k * self.runs_per_box, (k + 1) * self.runs_per_box)
+            r = runs[int(np.argmax(bf[runs]))]
+            winners.append(to_physical(pbx[r, bi[r]], run_boxes[r], self.q).tolist())
+            wf.append(float(bf[r]))
+        res = StageResult(i, spec.Np, boxes.tolist(), winners, wf, time.perf_counter() - t0)
+        self._save(res)
+        return res
+
+    # ---------------------------------------------------------------- checkpoints
+    def _path(self, i):
+        return None if not self.ckpt else os.path.join(self.ckpt, f"stage{i}.json")
+
+    def _save(self, res: StageResult):
+        if not self.ckpt:
+            return
+        os.makedirs(self.ckpt, exist_ok=True)
+        tmp = self._path(res.stage) + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump({"seed": self.seed, "spec": asdict(self.stages[res.stage]), "result": asdict(res)}, f)
+        os.replace(tmp, self._path(res.stage))
+
+    def _load(self, i) -> StageResult | None:
+        p = self._path(i)
+        if not p or not os.path.exists(p):
+            return None
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("seed") != self.seed or d.get("spec") != json.loads(json.dumps(asdict(self.stages[i]))):
+            raise ValueError(f"checkpoint {p} belongs to a different search")
+        return StageResult(**d["result"])
+
+    # ---------------------------------------------------------------- all stages
+    def run(self) -> dict:
+        self.results = []
+        for i in range(len(self.stages)):
+            res = self._load(i)
+            if res is None:
+                res = self.run_stage(i)
+            self.results.append(res)
+        last = self.results[-1]
+        k = int(np.argmax(last.winner_f))
+        return {"best": last.winners[k], "best_F_hat": last.winner_f[k],
+                "stages": [asdict(r) for r in self.results],
+                "seconds": sum(r.seconds for r in self.results)}

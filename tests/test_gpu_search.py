@@ -1,0 +1,105 @@
+"""Hierarchical search controller on the GPU: a reduced four-stage search on a
+short data set finds the injected signal, is deterministic, and resumes from
+its stage checkpoints to the same result."""
+import math
+import os
+import shutil
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2407_10797_gb300 import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def tc_for(Mc, f, t):
+    m = Mc * S.MSUN_S
+    return t + 5.0 / 256.0 * m * (np.pi * m * f) ** (-8.0 / 3.0)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_10797_gb300 import fstat, search
+    g = S.tiny_grid(n=60000, f_min=0.02, stride=4)
+    psd = S.lisa_like_psd(g.freqs())
+    m = O.OracleModel.from_grid(g)
+    truth = np.array([30.0, tc_for(30.0, 0.02 + 30000 * g.df, 0.5 * g.T_obs), 0.6, 2.1, 0.02, 1.0])
+    a = O.extrinsic_to_a(1.0, S.INJ_PSI, S.INJ_IOTA, S.INJ_PHIC)
+    k0, k1 = O.band(truth, m)
+    h = O.inject(truth, m, a, k0, k1 + 1)
+    d = S.gaussian_noise(g, psd, 21) + h * (40.0 / math.sqrt(O.inner(h, h, psd, g.df)))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = fstat.Plan.from_grid(g, mode=fstat.FS_MIXED, stream=s)
+        plan.data_dev = torch.from_numpy(d).cuda()
+        plan.psd_dev = torch.from_numpy(psd).cuda()
+        plan.set_data(plan.data_dev, plan.psd_dev)
+        plan.reserve(16 * 40, 256)
+    plan.grid = g
+    prior = S.Prior(Mc_lo=27.0, Mc_hi=33.0, tc_lo=truth[1] - 3e5, tc_hi=truth[1] + 3e5, e0_hi=0.05)
+    stages = [search.StageSpec(256, 60, "split_tc"),
+              search.StageSpec(64, 60, "around", (0.6, 6e4, None, None, None)),
+              search.StageSpec(16, 60, "around", (0.2, 2e4, 0.4, 0.4, 0.02)),
+              search.StageSpec(1, 120, "around_best_mirror", (0.05, 5e3, 0.2, 0.2, 0.01))]
+    yield fstat, search, plan, prior, stages, truth
+    plan.close()
+
+
+def test_search_reaches_brute_force_maximum(setup):
+    """(M_c, t_c) search with the sky and e0 pinned at the truth (zero-width
+    boxes): the four-stage search ends at least as high as the maximum of a
+    201 x 201 brute-force grid of the fully coherent F-hat (FP64 mode) and
+    within two grid cells of it."""
+    fstat, search, plan, prior, stages, truth = setup
+    lat_s = math.sin(truth[2])
+    bounds = np.array([[29.9, 30.1], [truth[1] - 2e4, truth[1] + 2e4], [lat_s, lat_s], [truth[3], truth[3]],
+                       [truth[4], truth[4]]])
+    st2 = [search.StageSpec(256, 100, "split_tc"),
+           search.StageSpec(64, 100, "around", (0.1, 2e4, None, None, None)),
+           search.StageSpec(16, 100, "around", (0.1, 1e4, None, None, None)),
+           search.StageSpec(1, 400, "around_best_mirror", (0.1, 1e4, None, None, None))]
+    hs = search.HierarchicalSearch(plan, prior, st2, n_boxes=4, runs_per_box=4, n_part=40, seed=3,
+                                   bounds=bounds)
+    res = hs.run()
+    best = np.array(res["best"])
+    Mc = np.linspace(29.9, 30.1, 201)
+    tc = np.linspace(truth[1] - 2e4, truth[1] + 2e4, 201)
+    G = np.array([[m, t, truth[2], truth[3], truth[4], 1.0] for m in Mc for t in tc])
+    p64 = fstat.Plan.from_grid(plan.grid, mode=fstat.FS_FP64)
+    p64.set_data(plan.data_dev, plan.psd_dev)
+    Fg = p64.fstat(torch.from_numpy(G).cuda(), 1, want_parts=False)[0].cpu().numpy()
+    p64.close()
+    k = int(np.argmax(Fg))
+    assert res["best_F_hat"] >= 0.999 * Fg[k]
+    assert abs(best[0] - G[k, 0]) <= 2 * (Mc[1] - Mc[0])
+    assert abs(best[1] - G[k, 1]) <= 2 * (tc[1] - tc[0])
+
+
+def test_search_is_deterministic_and_resumes(setup):
+    fstat, search, plan, prior, stages, truth = setup
+    d = tempfile.mkdtemp()
+    try:
+        a = search.HierarchicalSearch(plan, prior, stages, n_boxes=4, runs_per_box=2, n_part=40, seed=8,
+                                      checkpoint_dir=d).run()
+        assert sorted(os.listdir(d)) == [f"stage{i}.json" for i in range(4)]
+        # a fresh controller resumes everything from the checkpoints
+        b = search.HierarchicalSearch(plan, prior, stages, n_boxes=4, runs_per_box=2, n_part=40, seed=8,
+                                      checkpoint_dir=d).run()
+        assert b["best"] == a["best"]
+        # losing the last stage recomputes it to the same bits
+        os.remove(os.path.join(d, "stage3.json"))
+        c = search.HierarchicalSearch(plan, prior, stages, n_boxes=4, runs_per_box=2, n_part=40, seed=8,
+                                      checkpoint_dir=d).run()
+        assert c["best"] == a["best"] and c["best_F_hat"] == a["best_F_hat"]
+        # a checkpoint of another search is refused
+        with pytest.raises(ValueError):
+            search.HierarchicalSearch(plan, prior, stages, n_boxes=4, runs_per_box=2, n_part=40, seed=9,
+                                      checkpoint_dir=d).run()
+    finally:
+        shutil.rmtree(d)
