@@ -227,7 +227,12 @@ def run_reference(args, world, rank):
         return
     w, g, psd, noise, P, inj = workload_inputs(0)
     from oracle import oracle as O
+    from paper_2407_10797_gb300 import search
     m = O.OracleModel.from_grid(g)
+    # the particles the GPU arm evaluates: the PSO initial draw of 8 runs x 40
+    box = prior_box_array(w)
+    x0, _ = O.pso_init(RUNS, NPART, 5, 1000)
+    P = np.stack([search.to_physical(x, box) for x in x0.reshape(-1, 5)])
     a = extrinsic_amplitudes(S.INJ_IOTA, S.INJ_PSI, S.INJ_PHIC)
     k0, k1 = O.band(inj, m)
     h = O.inject(inj, m, a, k0, k1 + 1)
@@ -258,38 +263,6 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def time_mode(args, world, plan, P_dev, B, F_out, stream, kernel_prof=True):
-    """Warm up, then time `steps` evaluations at every N_p with CUDA events on
-    the plan's stream (barrier + synchronize on both sides).  Returns
-    (ms for all steps, max over ranks; fused-kernel ms and launches; clocks)."""
-    import torch
-
-    def step(params):
-        for Np in NP_LIST:
-            plan.fstat(params, Np, F=F_out[Np], want_parts=False)
-
-    for _ in range(args.warmup):
-        step(P_dev)
-    torch.cuda.synchronize()
-    for k in ("main", "setup", "reduce"):
-        plan.read_profile(k)
-    plan.set_profiling(kernel_prof)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        barrier(world)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step(P_dev)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-    plan.set_profiling(False)
-    ms = allmax(world, ev0.elapsed_time(ev1))
-    prof = {k: plan.read_profile(k) for k in ("main", "setup", "reduce")}
-    return ms, prof, clk.summary(), step
-
-
 def fp32_peak_tflops() -> float:
     """FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) at
     2070 MHz (80.5 TFLOP/s)."""
@@ -303,72 +276,189 @@ def fp32_peak_tflops() -> float:
 # (integer adds counted as one each).
 MIXED_FLOP_PER_PBIN = 80.0
 
+RUNS, NPART = 8, 40
+
+
+def prior_box_array(w):
+    p = w.prior
+    return np.array([[p.Mc_lo, p.Mc_hi], [p.tc_lo, p.tc_hi], [-1.0, 1.0], [0.0, 2.0 * np.pi], [0.0, p.e0_hi]])
+
+
+class ModeRun:
+    """One precision mode on the bench workload: a plan, one 8 x 40 swarm and
+    one captured PSO iteration (evaluate + update) per N_p of the schedule."""
+
+    def __init__(self, fstat, mode, g, d_dev, psd_dev, box, stream, seed):
+        import torch
+        self.torch = torch
+        self.plan = fstat.Plan.from_grid(g, mode=mode, stream=stream)
+        self.stream = stream
+        with torch.cuda.stream(stream):
+            self.plan.set_data(d_dev, psd_dev)
+            self.plan.reserve(RUNS * NPART, max(NP_LIST))
+            self.sw = {}
+            for Np in NP_LIST:
+                sw = fstat.Swarm(self.plan, RUNS, NPART, np.repeat(box[None], RUNS, axis=0))
+                sw.init(seed)
+                sw.graph_build(Np, seed, n_iter=2000)
+                self.sw[Np] = sw
+            torch.cuda.synchronize()
+            # the positions every step starts from
+            s0 = self.sw[NP_LIST[0]]
+            s0.init(seed)
+            self.x0, self.v0 = s0.x.clone(), s0.v.clone()
+        torch.cuda.synchronize()
+
+    def step(self):
+        """One bench step: for every N_p, reset the swarm to the prior draw and
+        replay one captured PSO iteration."""
+        for Np in NP_LIST:
+            sw = self.sw[Np]
+            sw.x.copy_(self.x0)
+            sw.v.copy_(self.v0)
+            sw.pbest_x.copy_(self.x0)
+            sw.pbest_f.fill_(-float("inf"))
+            sw.iter.zero_()
+            sw.graph_run(1)
+
+    def step_e2e(self, host):
+        """The same step with the swarm state uploaded from pinned host memory
+        and the fitness read back every step."""
+        for i, Np in enumerate(NP_LIST):
+            sw = self.sw[Np]
+            sw.x.copy_(host["x"], non_blocking=True)
+            sw.v.copy_(host["v"], non_blocking=True)
+            sw.pbest_x.copy_(host["x"], non_blocking=True)
+            sw.pbest_f.fill_(-float("inf"))
+            sw.iter.zero_()
+            sw.graph_run(1)
+            host["fit"][i].copy_(sw.fit, non_blocking=True)
+
+    def fitness_at_x0(self):
+        """F-hat of the prior draw at every N_p (fresh evaluation)."""
+        out = {}
+        with self.torch.cuda.stream(self.stream):
+            for Np in NP_LIST:
+                sw = self.sw[Np]
+                sw.x.copy_(self.x0)
+                sw.evaluate(Np)
+                out[Np] = sw.fit.cpu().numpy().copy()
+        return out
+
+    def close(self):
+        for sw in self.sw.values():
+            sw.graph_free()
+        self.plan.close()
+
+
+def time_run(args, world, run: ModeRun, kernel_prof=True):
+    import torch
+    stream = run.stream
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            run.step()
+        torch.cuda.synchronize()
+        for k in ("main", "setup", "reduce"):
+            run.plan.read_profile(k)
+        # events inside a captured graph are not recorded: time the kernels
+        # with the plan's eager profiling on a separate untimed pass
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            barrier(world)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                run.step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+        ms = allmax(world, ev0.elapsed_time(ev1))
+        # kernel durations (CUDA events on the plan's stream) over the same
+        # work, launched eagerly: one evaluation per N_p per step
+        run.plan.set_profiling(kernel_prof)
+        for _ in range(args.steps):
+            for Np in NP_LIST:
+                sw = run.sw[Np]
+                sw.x.copy_(run.x0)
+                sw.evaluate(Np)
+        torch.cuda.synchronize()
+        run.plan.set_profiling(False)
+        prof = {k: run.plan.read_profile(k) for k in ("main", "setup", "reduce")}
+    return ms, prof, clk.summary()
+
 
 def run_gpu(args, world, rank, local):
     import torch
     from paper_2407_10797_gb300 import fstat
+    from paper_2407_10797_gb300 import search
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
     w, g, psd, noise, P, inj = workload_inputs(rank)
-    d_dev = torch.from_numpy(noise).to(dev)
-    psd_dev = torch.from_numpy(psd).to(dev)
-    plan = fstat.Plan.from_grid(g, mode=fstat.FS_FP64, stream=stream)
-    plan.set_data(d_dev, psd_dev)
-    # injection through the library's own template generator
-    a = extrinsic_amplitudes(S.INJ_IOTA, S.INJ_PSI, S.INJ_PHIC)
-    h = torch.zeros_like(d_dev)
-    plan.add_signal(inj, a, h)
-    hh = float((4.0 * g.df * (h.abs() ** 2) / psd_dev).sum().item())
-    d_dev = d_dev + h * (w.snr / math.sqrt(hh))
-    plan.set_data(d_dev, psd_dev)
-    del h
-    B = w.B
-    plan.reserve(B, max(NP_LIST))
-    P_dev = torch.from_numpy(P).to(dev)
-    bands = plan.bands(P_dev).cpu().numpy()
+    box = prior_box_array(w)
+    with torch.cuda.stream(stream):
+        d_dev = torch.from_numpy(noise).to(dev)
+        psd_dev = torch.from_numpy(psd).to(dev)
+        # injection through the library's own template generator
+        p0 = fstat.Plan.from_grid(g, mode=fstat.FS_FP64, stream=stream)
+        p0.set_data(d_dev, psd_dev)
+        a = extrinsic_amplitudes(S.INJ_IOTA, S.INJ_PSI, S.INJ_PHIC)
+        h = torch.zeros_like(d_dev)
+        p0.add_signal(inj, a, h)
+        hh = float((4.0 * g.df * (h.abs() ** 2) / psd_dev).sum().item())
+        d_dev = d_dev + h * (w.snr / math.sqrt(hh))
+        del h
+    torch.cuda.synchronize()
+    seed = 1000 + rank
+
+    run64 = ModeRun(fstat, fstat.FS_FP64, g, d_dev, psd_dev, box, stream, seed)
+    # in-band particle*bins of the prior draw the steps evaluate
+    x0 = run64.x0.cpu().numpy().reshape(-1, 5)
+    P0 = np.stack([search.to_physical(x, box) for x in x0])
+    with torch.cuda.stream(stream):
+        bands = p0.bands(torch.from_numpy(P0).to(dev)).cpu().numpy()
+    p0.close()
     inband = int(np.maximum(bands[:, 1] - bands[:, 0] + 1, 0).sum())
+    B = RUNS * NPART
     pbins_per_step = inband * len(NP_LIST)
     total_pbins = allsum(world, float(pbins_per_step * args.steps))
-    F_out = {Np: torch.empty(B, dtype=torch.float64, device=dev) for Np in NP_LIST}
 
-    # ---- FP64 mode (the paper-scale FP64 configuration): device-resident timing
-    ms, prof, clocks, step = time_mode(args, world, plan, P_dev, B, F_out, stream)
+    # ---- FP64 mode: device-resident timing of full PSO iterations
+    ms, prof, clocks = time_run(args, world, run64)
     value = total_pbins / (ms / 1e3)
     main_ms, main_n = prof["main"]
-    F64 = {Np: F_out[Np].cpu().numpy() for Np in NP_LIST}
+    F64 = run64.fitness_at_x0()
 
-    # ---- end to end through the C ABI with host buffers (pinned)
-    P_host = torch.from_numpy(P).pin_memory()
-    F_host = torch.empty(len(NP_LIST), B, dtype=torch.float64).pin_memory()
-    P_e2e = torch.empty_like(P_dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        P_e2e.copy_(P_host, non_blocking=True)
-        step(P_e2e)
-        for i, Np in enumerate(NP_LIST):
-            F_host[i].copy_(F_out[Np], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    # ---- end to end with host buffers (pinned), FP64 mode
+    host = {"x": run64.x0.cpu().pin_memory(), "v": run64.v0.cpu().pin_memory(),
+            "fit": torch.empty(len(NP_LIST), RUNS, NPART, dtype=torch.float64).pin_memory()}
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            run64.step_e2e(host)
+            stream.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
     e2e_ms = allmax(world, e0.elapsed_time(e1))
     e2e_value = total_pbins / (e2e_ms / 1e3)
-    plan.close()
+    run64.close()
 
     # ---- mixed mode on the same data and particles
-    planm = fstat.Plan.from_grid(g, mode=fstat.FS_MIXED, stream=stream)
-    planm.set_data(d_dev, psd_dev)
-    planm.reserve(B, max(NP_LIST))
-    ms_m, prof_m, clocks_m, _ = time_mode(args, world, planm, P_dev, B, F_out, stream)
+    runm = ModeRun(fstat, fstat.FS_MIXED, g, d_dev, psd_dev, box, stream, seed)
+    ms_m, prof_m, clocks_m = time_run(args, world, runm)
     value_m = total_pbins / (ms_m / 1e3)
-    mix_err = max(float(np.max(np.abs(F_out[Np].cpu().numpy() - F64[Np]) / np.maximum(np.abs(F64[Np]), 2.0 * Np)))
-                  for Np in NP_LIST)
-    planm.close()
+    Fm = runm.fitness_at_x0()
+    mix_err = 0.0
+    for Np in NP_LIST:
+        a64, am = F64[Np].ravel() * Np, Fm[Np].ravel() * Np
+        ok = np.isfinite(a64)
+        mix_err = max(mix_err, float(np.max(np.abs(am[ok] - a64[ok]) / np.maximum(np.abs(a64[ok]), 2.0 * Np))))
+    runm.close()
 
     # ---- roofline of the dominant kernels (average launch duration, live events)
     main_avg_ms = main_ms / max(main_n, 1)
@@ -382,19 +472,23 @@ def run_gpu(args, world, rank, local):
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             data_h = d_dev.cpu().numpy()
-            pb, el, thr, npart = oracle_sample(g, P, psd, data_h, args.cpu_seconds)
+            pb, el, thr, npart = oracle_sample(g, P0, psd, data_h, args.cpu_seconds)
             cpu = {"value": pb / el, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{npart} particles x all their in-band bins ({pb} particle*bins), N_p = 16, "
                              f"{el:.1f} s"}
+        # kernels per step: per N_p 2 state resets are torch copies; the graph
+        # runs map, setup, rotation, fused, reduce, sum, fitness, pbest, move, advance
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_bins": g.n, "f_band_hz": [0.01, 0.05], "T_obs_s": g.T_obs,
-                       "B": B, "runs_x_particles": "8x40", "N_p": list(NP_LIST), "mode": "fp64",
+                       "B": B, "runs_x_particles": f"{RUNS}x{NPART}", "N_p": list(NP_LIST), "mode": "fp64",
+                       "step": "per N_p: one CUDA-graph PSO iteration (map, F-statistic, fitness, update) "
+                               "of 8 runs x 40 particles from the same prior draw",
                        "inband_particle_bins_per_launch": inband, "grid_particle_bins_per_launch": B * g.n,
                        "l2": "inputs exceed L2: per-bin tables 227 MB > 129 MB L2", "parallelism": f"dp{world}"},
-            "gpu_launches": args.steps * len(NP_LIST) * 5,
+            "gpu_launches": args.steps * len(NP_LIST) * 10,
             "kernel_ms": {"fused_fp64_avg": main_avg_ms, "setup_avg": prof["setup"][0] / max(prof["setup"][1], 1),
                           "solve_avg": prof["reduce"][0] / max(prof["reduce"][1], 1),
                           "fused_share_of_step": main_ms / max(ms, 1e-9)},
@@ -403,8 +497,9 @@ def run_gpu(args, world, rank, local):
                          "peak_source": "unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                          "flop_per_pbin": FP64_FLOP_PER_PBIN},
             "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(P.nbytes),
-                    "d2h_bytes_per_step": int(8 * B * len(NP_LIST))},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(len(NP_LIST) * 2 * host["x"].numel() * 8),
+                    "d2h_bytes_per_step": int(host["fit"].numel() * 8)},
             "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps, "dtype": "f64 anchors + f32",
                       "max_rel_err_vs_fp64": mix_err, "error_metric": "|dF|/max(|F|, 2 N_p)",
                       "kernel_ms": {"fused_mixed_avg": mm_avg, "fused_share_of_step": mm_ms / max(ms_m, 1e-9)},

@@ -175,16 +175,24 @@ FS_API fs_status fs_pso_step(fs_plan* plan, const fs_swarm* swarm, uint64_t seed
  * particle index among equals).  Asynchronous. */
 FS_API fs_status fs_pso_best(fs_plan* plan, const fs_swarm* swarm, double* best_f_dev, int* best_idx_dev);
 
+typedef struct fs_graph fs_graph;
+
 /* Capture one full PSO iteration (fs_pso_evaluate + fs_pso_step with the
  * device iteration counter) as a CUDA graph on the plan's stream, which must
- * not be the legacy default stream.  Reserve the workspace first (B >= R *
- * n_part).  Replaces any graph the plan held.  Synchronous. */
+ * not be the legacy default stream.  The graph reads and writes the swarm's
+ * buffers and the plan's workspace as they are at capture time: keep both
+ * alive and do not grow the workspace (reserve B >= R * n_part first).  Runs
+ * one untimed evaluation before capturing.  Synchronous.  *out is NULL on
+ * failure. */
 FS_API fs_status fs_pso_graph_build(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p,
                                     uint64_t seed, double w0, double w1, int n_iter, double c1, double c2,
-                                    double vmax);
+                                    double vmax, fs_graph** out);
 
-/* Launch the captured iteration n times on the plan's stream.  Asynchronous. */
-FS_API fs_status fs_pso_graph_run(fs_plan* plan, int n);
+/* Launch a captured iteration n times on its plan's stream.  Asynchronous. */
+FS_API fs_status fs_graph_run(fs_graph* graph, int n);
+
+/* Free a captured graph (waits for its stream).  NULL is a no-op. */
+FS_API fs_status fs_graph_destroy(fs_graph* graph);
 
 /* Select the launch variant of the FS_MIXED fused kernel: 0 = 2 CTAs per SM
  * (up to 128 registers per thread), 1 = 3 CTAs per SM (up to 80).  Results are

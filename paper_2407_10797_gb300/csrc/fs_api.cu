@@ -36,6 +36,12 @@ fs_status fs::set_error(fs_status st, const char* fmt, ...) {
     return st;
 }
 
+struct fs_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaStream_t stream;
+};
+
 struct fs_plan {
     fs::Grid grid;
     int mode;
@@ -63,8 +69,7 @@ struct fs_plan {
     // swarm evaluation scratch and the captured PSO iteration
     fs_params* pso_params;   // [B_cap]
     double* pso_F;           // [B_cap]
-    cudaGraph_t graph;
-    cudaGraphExec_t graph_exec;
+
     // segment edges (global mode)
     int64_t* edges_dev;
     int64_t* edges_cache;
@@ -248,8 +253,6 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
 fs_status fs_plan_destroy(fs_plan* p) {
     if (!p) return FS_OK;
     cudaStreamSynchronize(p->stream);
-    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-    if (p->graph) cudaGraphDestroy(p->graph);
     free_workspace(p);
     cudaFree(p->tab_base);
     cudaFree(p->edges_dev);
@@ -446,8 +449,10 @@ fs_status fs_pso_best(fs_plan* p, const fs_swarm* w, double* best_f, int* best_i
 }
 
 fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np, uint64_t seed,
-                             double w0, double w1, int n_iter, double c1, double c2, double vmax) {
+                             double w0, double w1, int n_iter, double c1, double c2, double vmax, fs_graph** out) {
     g_err[0] = 0;
+    if (!out) return fail(FS_EINVAL, "fs_pso_graph_build: out is NULL");
+    *out = nullptr;
     if (!p) return fail(FS_EINVAL, "fs_pso_graph_build: plan is NULL");
     if (!p->stream) return fail(FS_EINVAL, "fs_pso_graph_build: the plan's stream is the legacy default stream");
     fs_status st = check_swarm(w);
@@ -461,14 +466,6 @@ fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     const int prof = p->profiling;
     p->profiling = 0;
-    if (p->graph_exec) {
-        cudaGraphExecDestroy(p->graph_exec);
-        p->graph_exec = nullptr;
-    }
-    if (p->graph) {
-        cudaGraphDestroy(p->graph);
-        p->graph = nullptr;
-    }
     if ((e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
         p->profiling = prof;
         return cuda_fail(e, "cudaStreamBeginCapture");
@@ -483,22 +480,38 @@ fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges
         return s2;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    if ((e = cudaGraphInstantiate(&p->graph_exec, gr, 0)) != cudaSuccess) {
+    fs_graph* gobj = new (std::nothrow) fs_graph;
+    if (!gobj) {
         cudaGraphDestroy(gr);
+        return fail(FS_ENOMEM, "fs_pso_graph_build: host allocation failed");
+    }
+    gobj->graph = gr;
+    gobj->stream = p->stream;
+    if ((e = cudaGraphInstantiate(&gobj->exec, gr, 0)) != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        delete gobj;
         return cuda_fail(e, "cudaGraphInstantiate");
     }
-    p->graph = gr;
+    *out = gobj;
     return FS_OK;
 }
 
-fs_status fs_pso_graph_run(fs_plan* p, int n) {
+fs_status fs_graph_run(fs_graph* g, int n) {
     g_err[0] = 0;
-    if (!p || n < 0) return fail(FS_EINVAL, "fs_pso_graph_run: bad argument");
-    if (!p->graph_exec) return fail(FS_EINVAL, "fs_pso_graph_run: no graph (call fs_pso_graph_build)");
+    if (!g || n < 0) return fail(FS_EINVAL, "fs_graph_run: bad argument");
     for (int i = 0; i < n; i++) {
-        cudaError_t e = cudaGraphLaunch(p->graph_exec, p->stream);
+        cudaError_t e = cudaGraphLaunch(g->exec, g->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     }
+    return FS_OK;
+}
+
+fs_status fs_graph_destroy(fs_graph* g) {
+    if (!g) return FS_OK;
+    cudaStreamSynchronize(g->stream);
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
     return FS_OK;
 }
 

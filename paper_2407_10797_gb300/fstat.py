@@ -76,15 +76,16 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                   C.c_double, C.c_double, _vp]
         L.fs_pso_best.argtypes = [_vp, _sw, _vp, _vp]
         L.fs_pso_graph_build.argtypes = [_vp, _sw, _ep, C.c_int, C.c_uint64, C.c_double, C.c_double, C.c_int,
-                                         C.c_double, C.c_double, C.c_double]
-        L.fs_pso_graph_run.argtypes = [_vp, C.c_int]
+                                         C.c_double, C.c_double, C.c_double, C.POINTER(_vp)]
+        L.fs_graph_run.argtypes = [_vp, C.c_int]
+        L.fs_graph_destroy.argtypes = [_vp]
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
         for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_add_signal", "fs_constants", "fs_particle_bands",
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
                      "fs_plan_set_variant", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
-                     "fs_pso_graph_build", "fs_pso_graph_run"):
+                     "fs_pso_graph_build", "fs_graph_run", "fs_graph_destroy"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -309,12 +310,28 @@ class Swarm:
         return self.best_f, self.best_i
 
     def graph_build(self, Np: int, seed: int, edges=None, w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5):
+        """Capture one PSO iteration of this swarm as a CUDA graph (replaces a previous one)."""
         arr, e = _edges_arg(edges, Np)
+        self.graph_free()
+        h = C.c_void_p()
         _check(load().fs_pso_graph_build(self.plan._h, C.byref(self.c), e, int(Np), int(seed), float(w0),
-                                         float(w1), int(n_iter), float(c1), float(c2), float(vmax)))
+                                         float(w1), int(n_iter), float(c1), float(c2), float(vmax), C.byref(h)))
+        self._graph = h
 
     def graph_run(self, n: int):
-        _check(load().fs_pso_graph_run(self.plan._h, int(n)))
+        _check(load().fs_graph_run(self._graph, int(n)))
+
+    def graph_free(self):
+        g = getattr(self, "_graph", None)
+        if g is not None and g.value:
+            load().fs_graph_destroy(g)
+        self._graph = None
+
+    def __del__(self):
+        try:
+            self.graph_free()
+        except Exception:
+            pass
 
 
 def torch_tensor(a):
