@@ -400,3 +400,62 @@ def test_constants_agree_with_input_module():
     assert grab("OR_MSUN_S") == S.MSUN_S
     assert grab("OR_YEAR_S") == S.YEAR_S
     assert grab("OR_AU_S") == S.AU_S
+
+
+# ---------------------------------------------------------------- p11: MLP oracle
+def test_mlp_oracle_bf16_rounding_known_values():
+    from oracle import mlp_oracle as M
+    # exact bf16 values stay, halfway cases round to even, 1 + 2^-9 rounds down
+    vals = np.array([1.0, -2.5, 1.0 + 2 ** -8, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, 65504.0])
+    got = M.bf16(vals)
+    assert got[0] == 1.0 and got[1] == -2.5
+    assert got[2] == 1.0            # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even -> 1
+    assert got[3] == 1.0
+    assert got[4] == 1.0 + 2 ** -7  # above halfway
+    assert got[5] == 65536.0
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    """Central differences of the loss in float64 without the bf16 rounding of
+    the weights (rounding removed so the loss is smooth) match the analytic
+    gradient of the same network."""
+    from oracle import mlp_oracle as M
+    rng = np.random.default_rng(1)
+    W = 16
+    shapes = M.param_shapes(W)
+    theta = np.concatenate([rng.normal(scale=0.5, size=int(np.prod(s))) for _, s in shapes])
+    X = rng.random((20, 5))
+    t = rng.normal(size=20)
+    t[3] = np.nan                   # ignored sample
+    orig = M.bf16
+    try:
+        M.bf16 = lambda a: np.asarray(a, dtype=np.float64)
+        L0, g = M.loss_and_grad(theta, X, t, W)
+        idx = rng.choice(len(theta), 40, replace=False)
+        for i in idx:
+            h = 1e-6
+            tp = theta.copy()
+            tp[i] += h
+            tm = theta.copy()
+            tm[i] -= h
+            fd = (M.loss_and_grad(tp, X, t, W)[0] - M.loss_and_grad(tm, X, t, W)[0]) / (2 * h)
+            assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9)
+    finally:
+        M.bf16 = orig
+
+
+def test_mlp_oracle_adam_fits_a_smooth_function():
+    from oracle import mlp_oracle as M
+    rng = np.random.default_rng(2)
+    W = 32
+    theta = np.concatenate([rng.uniform(-1, 1, size=int(np.prod(s))) * np.sqrt(6.0 / (s[1] if len(s) == 2 else 1))
+                            * (len(s) == 2) for _, s in M.param_shapes(W)])
+    X = rng.random((256, 5))
+    t = np.sin(3 * X[:, 0]) + X[:, 1] ** 2 - X[:, 2] * X[:, 3]
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    L_first = M.loss_and_grad(theta, X, t, W)[0]
+    for s in range(1, 301):
+        L, g = M.loss_and_grad(theta, X, t, W)
+        theta, m, v = M.adam(theta, g, m, v, s, 3e-3)
+    assert L < 0.05 * L_first
