@@ -194,6 +194,49 @@ FS_API fs_status fs_graph_run(fs_graph* graph, int n);
 /* Free a captured graph (waits for its stream).  NULL is a no-op. */
 FS_API fs_status fs_graph_destroy(fs_graph* graph);
 
+/* ---- Surrogate MLP (not in the paper: ranks candidate PSO moves) ---------- */
+
+/* A 5 -> width -> width -> width -> 1 network with ReLU hidden layers: bf16
+ * weights and layer inputs, fp32 accumulation on the tensor cores, fp32
+ * master weights trained with Adam on the (particle, F-hat) pairs a search
+ * produces.  Inputs are normalised PSO positions in [0,1]^5. */
+typedef struct fs_mlp fs_mlp;
+
+/* Number of fp32 parameters: W1 [width][5], b1, W2 [width][width], b2, W3, b3,
+ * W4 [width], b4, in that order (row-major), -1 for an invalid width. */
+FS_API int64_t fs_mlp_num_params(int width);
+
+/* Create with Kaiming-uniform weights from Philox4x32-10 (key = seed), zero
+ * biases and Adam state.  width: a multiple of 8 in [8, 1024]; max_batch:
+ * rows per internal pass (larger forward batches are chunked, training
+ * batches must fit).  stream: cudaStream_t.  Synchronous. */
+FS_API fs_status fs_mlp_create(fs_mlp** out, int width, int max_batch, uint64_t seed, void* stream);
+FS_API fs_status fs_mlp_destroy(fs_mlp* mlp);
+
+/* Copy the fp32 master weights in or out (device buffers of
+ * fs_mlp_num_params floats).  Setting weights resets the Adam step count
+ * and the target standardisation.  set is synchronous, get asynchronous. */
+FS_API fs_status fs_mlp_set_params(fs_mlp* mlp, const float* theta_dev);
+FS_API fs_status fs_mlp_get_params(fs_mlp* mlp, float* theta_dev);
+
+/* Predictions y_dev [N] for X_dev [N][5] (fp32, device), in the units of
+ * the targets of the last fs_mlp_train call (raw network output before any
+ * training).  Asynchronous. */
+FS_API fs_status fs_mlp_forward(fs_mlp* mlp, const float* X_dev, int N, float* y_dev);
+
+/* Loss L = (1/2n) sum (y - t)^2 over the n finite targets t_dev [N] (NaN =
+ * ignored, no standardisation) and its gradient with respect to the fp32
+ * master weights (grad_dev: fs_mlp_num_params floats, may be NULL; loss_dev:
+ * 1 float, may be NULL).  1 <= N <= max_batch.  Asynchronous. */
+FS_API fs_status fs_mlp_loss_grad(fs_mlp* mlp, const float* X_dev, const float* t_dev, int N, float* grad_dev,
+                                  float* loss_dev);
+
+/* `steps` full-batch Adam steps (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8)
+ * on (X_dev, t_dev) with the finite targets standardised by their mean and
+ * standard deviation; loss_dev: optional [steps] losses.  Asynchronous. */
+FS_API fs_status fs_mlp_train(fs_mlp* mlp, const float* X_dev, const float* t_dev, int N, int steps, float lr,
+                              float* loss_dev);
+
 /* Select the launch variant of the FS_MIXED fused kernel: 0 = 2 CTAs per SM
  * (up to 128 registers per thread), 1 = 3 CTAs per SM (up to 80).  Results are
  * identical; only the speed differs.  Default 0. */

@@ -1,0 +1,603 @@
+// fs_mlp.cu - the surrogate MLP that ranks candidate PSO moves: 5 -> W -> W
+// -> W -> 1 with ReLU hidden layers, bf16 weights and layer inputs, fp32
+// accumulation, fp32 master weights trained with Adam.
+//
+// The hidden-layer products and their gradients run on the tensor cores
+// through one templated bf16 GEMM (mma.sync m16n8k16, fp32 accumulators)
+// with fused epilogues: bias + ReLU (forward), ReLU mask (backward through an
+// activation) and plain fp32 (weight gradients).  The 5-wide input layer is
+// padded to K = 16; the 1-wide output layer is a warp-per-row dot product.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kInPad = 16;   // input features padded to one mma K step
+
+// ---------------------------------------------------------------------------
+// C[M, N] = A[M, K] . B[N, K]^T  (bf16 in, fp32 accumulate)
+//   TA: A stored [K][M] (element (m, k) at A[k * lda + m]) instead of [M][K]
+//   TB: B stored [K][N] instead of [N][K]
+// ---------------------------------------------------------------------------
+enum Epi { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32 = 2 };
+
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8, GEMM_THREADS = 128;
+
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <bool TRANS>
+__device__ __forceinline__ void load_tile(bf16 (*S)[BK + PAD], const bf16* __restrict__ G, int ld, int row0, int rows,
+                                          int k0, int K) {
+    const bf16 zero = __float2bfloat16(0.f);
+#pragma unroll
+    for (int i = 0; i < (BM * BK) / GEMM_THREADS; i++) {
+        const int e = threadIdx.x + i * GEMM_THREADS;
+        int r, c;
+        if (!TRANS) {   // k contiguous in memory: consecutive threads walk k
+            r = e / BK;
+            c = e % BK;
+        } else {        // row contiguous in memory: consecutive threads walk rows
+            c = e / BM;
+            r = e % BM;
+        }
+        const int gr = row0 + r, gk = k0 + c;
+        bf16 v = zero;
+        if (gr < rows && gk < K) v = TRANS ? G[(int64_t)gk * ld + gr] : G[(int64_t)gr * ld + gk];
+        S[r][c] = v;
+    }
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS)
+gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb,
+                 const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, void* out, int ldo) {
+    __shared__ __align__(16) bf16 As[BM][BK + PAD];
+    __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[i][j][c] = 0.f;
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        load_tile<TA>(As, A, lda, m0, M, k0, K);
+        load_tile<TB>(Bs, B, ldb, n0, N, k0, K);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int r = wm + i * 16 + g;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int c = wn + j * 8 + g;
+                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue: accumulator element (i, j, c) sits at row wm + 16 i + g (+8 for c >= 2),
+    // column wn + 8 j + 2 t (+1 for odd c)
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int m = m0 + wm + i * 16 + g + (c >= 2 ? 8 : 0);
+                const int n = n0 + wn + j * 8 + 2 * t + (c & 1);
+                if (m >= M || n >= N) continue;
+                const float v = acc[i][j][c];
+                if (EPI == EPI_BIAS_RELU_BF16) {
+                    static_cast<bf16*>(out)[(int64_t)m * ldo + n] = __float2bfloat16(fmaxf(v + bias[n], 0.f));
+                } else if (EPI == EPI_MASK_BF16) {
+                    const float a = __bfloat162float(mask[(int64_t)m * ldm + n]);
+                    static_cast<bf16*>(out)[(int64_t)m * ldo + n] = __float2bfloat16(a > 0.f ? v : 0.f);
+                } else {
+                    static_cast<float*>(out)[(int64_t)m * ldo + n] = v;
+                }
+            }
+}
+
+template <bool TA, bool TB, int EPI>
+static cudaError_t gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias,
+                        const bf16* mask, int ldm, void* out, int ldo, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+    gemm_bf16_kernel<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+__global__ void input_pad_kernel(int N, const float* __restrict__ X, bf16* Xb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * kInPad) return;
+    const int64_t n = i / kInPad;
+    const int c = (int)(i % kInPad);
+    Xb[i] = __float2bfloat16(c < 5 ? X[n * 5 + c] : 0.f);
+}
+
+// y[n] = a3[n, :] . w4 + b4 (fp32 accumulation of bf16 products), then y * scale + shift
+__global__ void output_kernel(int N, int W, const bf16* __restrict__ A3, const bf16* __restrict__ w4,
+                              const float* __restrict__ b4, const float* __restrict__ stdz, float* y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int k = lane; k < W; k += 32) s = fmaf(__bfloat162float(A3[n * W + k]), __bfloat162float(w4[k]), s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const float v = s + b4[0];
+        y[n] = stdz ? fmaf(v, stdz[1], stdz[0]) : v;
+    }
+}
+
+// mean and standard deviation of the finite targets (single block, fixed order)
+__global__ void standardize_kernel(int N, const float* __restrict__ t, float* stdz) {
+    __shared__ double s1[256], s2[256], sc[256];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float v = t[i];
+        if (isfinite(v)) {
+            a += v;
+            b += (double)v * v;
+            c += 1.0;
+        }
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double n = sc[0] > 0 ? sc[0] : 1.0;
+        const double mu = s1[0] / n;
+        const double var = s2[0] / n - mu * mu;
+        stdz[0] = (float)mu;
+        stdz[1] = (float)(var > 1e-30 ? sqrt(var) : 1.0);
+        stdz[2] = (float)sc[0];
+    }
+}
+
+// dy[n] = (y[n] - t'[n]) / count for finite targets, t' = (t - mu)/sigma if
+// standardising; also the per-sample squared error for the loss.
+__global__ void dloss_kernel(int N, const float* __restrict__ y, const float* __restrict__ t,
+                             const float* __restrict__ stdz, const float* __restrict__ count, float* dy, float* sq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float tv = t[i];
+    float r = 0.f;
+    if (isfinite(tv)) {
+        const float tt = stdz ? (tv - stdz[0]) / stdz[1] : tv;
+        r = y[i] - tt;
+    }
+    const float c = count[0] > 0.f ? count[0] : 1.f;
+    dy[i] = r / c;
+    sq[i] = 0.5f * r * r / c;
+}
+
+// dZ3[n, k] = dy[n] * w4[k] * (a3[n, k] > 0)
+__global__ void dz_last_kernel(int N, int W, const float* __restrict__ dy, const bf16* __restrict__ w4,
+                               const bf16* __restrict__ A3, bf16* dZ) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * W) return;
+    const int64_t n = i / W;
+    const int k = (int)(i % W);
+    const float a = __bfloat162float(A3[i]);
+    dZ[i] = __float2bfloat16(a > 0.f ? dy[n] * __bfloat162float(w4[k]) : 0.f);
+}
+
+// column sums (fixed order): out[k] = sum_n M[n, k] (bf16 or fp32 input), and
+// the output-layer gradients dW4[k] = sum_n dy[n] a3[n, k], db4 = sum dy.
+template <typename T>
+__device__ __forceinline__ float as_f(T v);
+template <>
+__device__ __forceinline__ float as_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float as_f<bf16>(bf16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__global__ void colsum_kernel(int N, int W, const T* __restrict__ Mx, const float* __restrict__ wrow, float* out) {
+    const int k = blockIdx.x;
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const float v = Mx ? as_f<T>(Mx[(int64_t)n * W + k]) : 1.f;
+        s = fmaf(wrow ? wrow[n] : 1.f, v, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0];
+}
+
+__global__ void sum_kernel(int N, const float* __restrict__ v, float* out) {
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) s += v[n];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// gradient of the padded first layer [W][16] -> the [W][5] slot of the flat gradient
+__global__ void unpad_kernel(int W, const float* __restrict__ g16, float* g5) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * 5) return;
+    g5[i] = g16[(i / 5) * kInPad + i % 5];
+}
+
+// fp32 master weights -> bf16 copies (first layer padded to 16 inputs)
+__global__ void refresh_kernel(int W, const float* __restrict__ th, bf16* W1b, bf16* W2b, bf16* W3b, bf16* W4b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nW1 = (int64_t)W * 5, nWW = (int64_t)W * W;
+    const float* W1 = th;
+    const float* W2 = W1 + nW1 + W;
+    const float* W3 = W2 + nWW + W;
+    const float* W4 = W3 + nWW + W;
+    if (i < (int64_t)W * kInPad) {
+        const int64_t r = i / kInPad;
+        const int c = (int)(i % kInPad);
+        W1b[i] = __float2bfloat16(c < 5 ? W1[r * 5 + c] : 0.f);
+    }
+    if (i < nWW) {
+        W2b[i] = __float2bfloat16(W2[i]);
+        W3b[i] = __float2bfloat16(W3[i]);
+    }
+    if (i < W) W4b[i] = __float2bfloat16(W4[i]);
+}
+
+__global__ void adam_kernel(int64_t P, float* th, const float* __restrict__ g, float* m, float* v, float lr,
+                            float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+// Kaiming-uniform weights, zero biases (Philox counter (index, 0x4D4C5000, 0, 0), key = seed)
+__device__ __forceinline__ void philox_mlp(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+__global__ void init_kernel(int W, unsigned long long seed, float* th) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nW1 = (int64_t)W * 5, nWW = (int64_t)W * W;
+    const int64_t P = nW1 + W + 2 * (nWW + W) + W + 1;
+    if (i >= P) return;
+    int64_t o = i;
+    float fan = 0.f;
+    if (o < nW1) fan = 5.f;
+    else if ((o -= nW1) < W) fan = 0.f;
+    else if ((o -= W) < nWW) fan = (float)W;
+    else if ((o -= nWW) < W) fan = 0.f;
+    else if ((o -= W) < nWW) fan = (float)W;
+    else if ((o -= nWW) < W) fan = 0.f;
+    else if ((o -= W) < W) fan = (float)W;
+    else fan = 0.f;
+    if (fan == 0.f) {
+        th[i] = 0.f;
+        return;
+    }
+    uint32_t c[4] = {(uint32_t)i, 0x4D4C5000u, (uint32_t)(i >> 32), 0u};
+    philox_mlp(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const float u = (float)(c[0] >> 8) * (1.0f / 16777216.0f);
+    th[i] = (2.f * u - 1.f) * sqrtf(6.f / fan);
+}
+
+}  // namespace fs
+
+// ---------------------------------------------------------------------------
+// Module state and C ABI
+// ---------------------------------------------------------------------------
+struct fs_mlp {
+    int W, cap;
+    int64_t P;
+    cudaStream_t stream;
+    float* th;      // fp32 master weights [P]
+    float* gr;      // gradient [P]
+    float* m;       // Adam moments
+    float* v;
+    int64_t step;
+    fs::bf16 *W1b, *W2b, *W3b, *W4b;
+    fs::bf16 *Xb, *A1, *A2, *A3, *dZa, *dZb;
+    float *y, *dy, *sq, *g16, *stdz, *loss;
+};
+
+namespace {
+
+int64_t nparams(int W) { return (int64_t)W * 5 + W + 2 * ((int64_t)W * W + W) + W + 1; }
+
+fs_status mlp_fail(cudaError_t e, const char* what) {
+    return fs::set_error(e == cudaErrorMemoryAllocation ? FS_ENOMEM : FS_ECUDA, "%s: %s", what,
+                         cudaGetErrorString(e));
+}
+
+void mlp_free(fs_mlp* m) {
+    void* ps[] = {m->th, m->gr, m->m, m->v, m->W1b, m->W2b, m->W3b, m->W4b, m->Xb, m->A1, m->A2, m->A3,
+                  m->dZa, m->dZb, m->y, m->dy, m->sq, m->g16, m->stdz, m->loss};
+    for (void* p : ps) cudaFree(p);
+}
+
+// Forward pass for N <= cap rows of X (fp32 [N][5]); activations kept.
+cudaError_t mlp_forward(fs_mlp* m, const float* X, int N, float* y, bool destandardize) {
+    using namespace fs;
+    const int W = m->W;
+    cudaStream_t s = m->stream;
+    input_pad_kernel<<<(unsigned)(((int64_t)N * kInPad + 255) / 256), 256, 0, s>>>(N, X, m->Xb);
+    const float* b1 = m->th + (int64_t)W * 5;
+    const float* b2 = b1 + W + (int64_t)W * W;
+    const float* b3 = b2 + W + (int64_t)W * W;
+    const float* b4 = b3 + W + W;
+    cudaError_t e;
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, kInPad, m->Xb, kInPad, m->W1b, kInPad, b1, nullptr, 0, m->A1,
+                                                     W, s)) != cudaSuccess)
+        return e;
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A1, W, m->W2b, W, b2, nullptr, 0, m->A2, W, s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A2, W, m->W3b, W, b3, nullptr, 0, m->A3, W, s)) !=
+        cudaSuccess)
+        return e;
+    output_kernel<<<(unsigned)(((int64_t)N * 32 + 255) / 256), 256, 0, s>>>(N, W, m->A3, m->W4b, b4,
+                                                                          destandardize ? m->stdz : nullptr, y);
+    return cudaGetLastError();
+}
+
+// Loss and gradient for N rows (targets t, NaN = ignored); stdz: standardise targets.
+cudaError_t mlp_backward(fs_mlp* m, const float* X, const float* t, int N, bool standardize) {
+    using namespace fs;
+    const int W = m->W;
+    cudaStream_t s = m->stream;
+    cudaError_t e;
+    // training standardises the targets with (mu, sigma) kept for inference
+    // in stdz[0..2]; the raw-target loss uses stdz[4..6] only for the count
+    float* st = standardize ? m->stdz : m->stdz + 4;
+    standardize_kernel<<<1, 256, 0, s>>>(N, t, st);
+    if ((e = mlp_forward(m, X, N, m->y, false)) != cudaSuccess) return e;
+    dloss_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, m->y, t, standardize ? m->stdz : nullptr, st + 2, m->dy, m->sq);
+    sum_kernel<<<1, 256, 0, s>>>(N, m->sq, m->loss);
+    const int64_t nW1 = (int64_t)W * 5, nWW = (int64_t)W * W;
+    float* gW1 = m->gr;
+    float* gb1 = gW1 + nW1;
+    float* gW2 = gb1 + W;
+    float* gb2 = gW2 + nWW;
+    float* gW3 = gb2 + W;
+    float* gb3 = gW3 + nWW;
+    float* gW4 = gb3 + W;
+    float* gb4 = gW4 + W;
+    // output layer
+    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->A3, m->dy, gW4);
+    sum_kernel<<<1, 256, 0, s>>>(N, m->dy, gb4);
+    dz_last_kernel<<<(unsigned)(((int64_t)N * W + 255) / 256), 256, 0, s>>>(N, W, m->dy, m->W4b, m->A3, m->dZa);
+    // layer 3: dW3 = dZ3^T A2, db3, dZ2 = (dZ3 W3) * (A2 > 0)
+    if ((e = gemm<true, true, EPI_F32>(W, W, N, m->dZa, W, m->A2, W, nullptr, nullptr, 0, gW3, W, s)) != cudaSuccess)
+        return e;
+    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->dZa, nullptr, gb3);
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZa, W, m->W3b, W, nullptr, m->A2, W, m->dZb, W, s)) !=
+        cudaSuccess)
+        return e;
+    // layer 2
+    if ((e = gemm<true, true, EPI_F32>(W, W, N, m->dZb, W, m->A1, W, nullptr, nullptr, 0, gW2, W, s)) != cudaSuccess)
+        return e;
+    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->dZb, nullptr, gb2);
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZb, W, m->W2b, W, nullptr, m->A1, W, m->dZa, W, s)) !=
+        cudaSuccess)
+        return e;
+    // layer 1 (padded input)
+    if ((e = gemm<true, true, EPI_F32>(W, kInPad, N, m->dZa, W, m->Xb, kInPad, nullptr, nullptr, 0, m->g16, kInPad,
+                                       s)) != cudaSuccess)
+        return e;
+    unpad_kernel<<<(W * 5 + 255) / 256, 256, 0, s>>>(W, m->g16, gW1);
+    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->dZa, nullptr, gb1);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_refresh(fs_mlp* m) {
+    const int64_t n = (int64_t)m->W * (m->W > fs::kInPad ? m->W : fs::kInPad);
+    fs::refresh_kernel<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->W, m->th, m->W1b, m->W2b, m->W3b, m->W4b);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t fs_mlp_num_params(int width) { return width > 0 ? nparams(width) : -1; }
+
+fs_status fs_mlp_create(fs_mlp** out, int width, int max_batch, uint64_t seed, void* stream) {
+    fs::set_error(FS_OK, "");
+    if (!out) return fs::set_error(FS_EINVAL, "fs_mlp_create: out is NULL");
+    *out = nullptr;
+    if (width < 8 || width > 1024 || width % 8 != 0 || max_batch < 1)
+        return fs::set_error(FS_EINVAL, "fs_mlp_create: need width in [8, 1024], a multiple of 8, max_batch >= 1");
+    fs_mlp* m = new (std::nothrow) fs_mlp;
+    if (!m) return fs::set_error(FS_ENOMEM, "fs_mlp_create: host allocation failed");
+    memset(m, 0, sizeof(*m));
+    m->W = width;
+    m->cap = max_batch;
+    m->P = nparams(width);
+    m->stream = (cudaStream_t)stream;
+    const int W = width;
+    const size_t act = sizeof(fs::bf16) * (size_t)max_batch * W;
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->th, sizeof(float) * m->P)) != cudaSuccess ||
+        (e = cudaMalloc(&m->gr, sizeof(float) * m->P)) != cudaSuccess ||
+        (e = cudaMalloc(&m->m, sizeof(float) * m->P)) != cudaSuccess ||
+        (e = cudaMalloc(&m->v, sizeof(float) * m->P)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W1b, sizeof(fs::bf16) * W * fs::kInPad)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W2b, sizeof(fs::bf16) * W * W)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W3b, sizeof(fs::bf16) * W * W)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W4b, sizeof(fs::bf16) * W)) != cudaSuccess ||
+        (e = cudaMalloc(&m->Xb, sizeof(fs::bf16) * (size_t)max_batch * fs::kInPad)) != cudaSuccess ||
+        (e = cudaMalloc(&m->A1, act)) != cudaSuccess || (e = cudaMalloc(&m->A2, act)) != cudaSuccess ||
+        (e = cudaMalloc(&m->A3, act)) != cudaSuccess || (e = cudaMalloc(&m->dZa, act)) != cudaSuccess ||
+        (e = cudaMalloc(&m->dZb, act)) != cudaSuccess ||
+        (e = cudaMalloc(&m->y, sizeof(float) * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&m->dy, sizeof(float) * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&m->sq, sizeof(float) * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&m->g16, sizeof(float) * W * fs::kInPad)) != cudaSuccess ||
+        (e = cudaMalloc(&m->stdz, sizeof(float) * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&m->loss, sizeof(float) * 1)) != cudaSuccess) {
+        mlp_free(m);
+        delete m;
+        return mlp_fail(e, "fs_mlp_create: cudaMalloc");
+    }
+    const float one[4] = {0.f, 1.f, 0.f, 0.f};
+    fs::init_kernel<<<(unsigned)((m->P + 255) / 256), 256, 0, m->stream>>>(W, seed, m->th);
+    if ((e = cudaMemsetAsync(m->m, 0, sizeof(float) * m->P, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->v, 0, sizeof(float) * m->P, m->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(m->stdz, one, sizeof(one), cudaMemcpyHostToDevice, m->stream)) != cudaSuccess ||
+        (e = mlp_refresh(m)) != cudaSuccess || (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+        mlp_free(m);
+        delete m;
+        return mlp_fail(e, "fs_mlp_create: initialisation");
+    }
+    *out = m;
+    return FS_OK;
+}
+
+fs_status fs_mlp_destroy(fs_mlp* m) {
+    if (!m) return FS_OK;
+    cudaStreamSynchronize(m->stream);
+    mlp_free(m);
+    delete m;
+    return FS_OK;
+}
+
+fs_status fs_mlp_set_params(fs_mlp* m, const float* theta_dev) {
+    fs::set_error(FS_OK, "");
+    if (!m || !theta_dev) return fs::set_error(FS_EINVAL, "fs_mlp_set_params: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(m->th, theta_dev, sizeof(float) * m->P, cudaMemcpyDeviceToDevice, m->stream);
+    if (e != cudaSuccess || (e = mlp_refresh(m)) != cudaSuccess) return mlp_fail(e, "fs_mlp_set_params");
+    const float one[4] = {0.f, 1.f, 0.f, 0.f};
+    if ((e = cudaMemcpyAsync(m->stdz, one, sizeof(one), cudaMemcpyHostToDevice, m->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(m->stream)) != cudaSuccess)
+        return mlp_fail(e, "fs_mlp_set_params");
+    m->step = 0;
+    return FS_OK;
+}
+
+fs_status fs_mlp_get_params(fs_mlp* m, float* theta_dev) {
+    fs::set_error(FS_OK, "");
+    if (!m || !theta_dev) return fs::set_error(FS_EINVAL, "fs_mlp_get_params: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(theta_dev, m->th, sizeof(float) * m->P, cudaMemcpyDeviceToDevice, m->stream);
+    if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_get_params");
+    return FS_OK;
+}
+
+fs_status fs_mlp_forward(fs_mlp* m, const float* X_dev, int N, float* y_dev) {
+    fs::set_error(FS_OK, "");
+    if (!m || N < 0 || (N > 0 && (!X_dev || !y_dev))) return fs::set_error(FS_EINVAL, "fs_mlp_forward: bad argument");
+    for (int off = 0; off < N; off += m->cap) {
+        const int n = N - off < m->cap ? N - off : m->cap;
+        cudaError_t e = mlp_forward(m, X_dev + (int64_t)off * 5, n, y_dev + off, true);
+        if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_forward");
+    }
+    return FS_OK;
+}
+
+fs_status fs_mlp_loss_grad(fs_mlp* m, const float* X_dev, const float* t_dev, int N, float* grad_dev,
+                           float* loss_dev) {
+    fs::set_error(FS_OK, "");
+    if (!m || N < 1 || N > m->cap || !X_dev || !t_dev)
+        return fs::set_error(FS_EINVAL, "fs_mlp_loss_grad: need 1 <= N <= max_batch and non-NULL X, t");
+    cudaError_t e = mlp_backward(m, X_dev, t_dev, N, false);
+    if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_loss_grad");
+    if (grad_dev && (e = cudaMemcpyAsync(grad_dev, m->gr, sizeof(float) * m->P, cudaMemcpyDeviceToDevice,
+                                         m->stream)) != cudaSuccess)
+        return mlp_fail(e, "fs_mlp_loss_grad copy");
+    if (loss_dev && (e = cudaMemcpyAsync(loss_dev, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, m->stream)) !=
+                        cudaSuccess)
+        return mlp_fail(e, "fs_mlp_loss_grad copy");
+    return FS_OK;
+}
+
+fs_status fs_mlp_train(fs_mlp* m, const float* X_dev, const float* t_dev, int N, int steps, float lr,
+                       float* loss_dev) {
+    fs::set_error(FS_OK, "");
+    if (!m || N < 1 || N > m->cap || steps < 0 || !X_dev || !t_dev || !(lr > 0.f))
+        return fs::set_error(FS_EINVAL, "fs_mlp_train: need 1 <= N <= max_batch, steps >= 0, lr > 0");
+    for (int it = 0; it < steps; it++) {
+        cudaError_t e = mlp_backward(m, X_dev, t_dev, N, true);
+        if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_train backward");
+        m->step++;
+        const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)m->step)));
+        const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)m->step)));
+        fs::adam_kernel<<<(unsigned)((m->P + 255) / 256), 256, 0, m->stream>>>(m->P, m->th, m->gr, m->m, m->v, lr, c1,
+                                                                                c2);
+        if ((e = cudaGetLastError()) != cudaSuccess || (e = mlp_refresh(m)) != cudaSuccess)
+            return mlp_fail(e, "fs_mlp_train update");
+        if (loss_dev && (e = cudaMemcpyAsync(loss_dev + it, m->loss, sizeof(float), cudaMemcpyDeviceToDevice,
+                                             m->stream)) != cudaSuccess)
+            return mlp_fail(e, "fs_mlp_train copy");
+    }
+    return FS_OK;
+}
+
+}  // extern "C"

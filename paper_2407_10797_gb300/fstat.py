@@ -79,13 +79,24 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                          C.c_double, C.c_double, C.c_double, C.POINTER(_vp)]
         L.fs_graph_run.argtypes = [_vp, C.c_int]
         L.fs_graph_destroy.argtypes = [_vp]
+        L.fs_mlp_num_params.argtypes = [C.c_int]
+        L.fs_mlp_num_params.restype = C.c_int64
+        L.fs_mlp_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_uint64, _vp]
+        L.fs_mlp_destroy.argtypes = [_vp]
+        L.fs_mlp_set_params.argtypes = [_vp, _vp]
+        L.fs_mlp_get_params.argtypes = [_vp, _vp]
+        L.fs_mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp]
+        L.fs_mlp_loss_grad.argtypes = [_vp, _vp, _vp, C.c_int, _vp, _vp]
+        L.fs_mlp_train.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp]
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
         for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_add_signal", "fs_constants", "fs_particle_bands",
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
                      "fs_plan_set_variant", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
-                     "fs_pso_graph_build", "fs_graph_run", "fs_graph_destroy"):
+                     "fs_pso_graph_build", "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
+                     "fs_mlp_destroy", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
+                     "fs_mlp_loss_grad", "fs_mlp_train"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -337,3 +348,66 @@ class Swarm:
 def torch_tensor(a):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+class MLP:
+    """Surrogate network (fs_mlp): 5 -> width^3 -> 1, bf16 tensor-core kernels."""
+
+    def __init__(self, width: int = 256, max_batch: int = 8192, seed: int = 0, stream=None):
+        import torch
+        self._L = load()
+        self.width = int(width)
+        self.P = int(self._L.fs_mlp_num_params(self.width))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(self._L.fs_mlp_create(C.byref(h), self.width, int(max_batch), int(seed), _stream_handle(self.stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.fs_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import torch
+        out = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        _check(self._L.fs_mlp_get_params(self._h, _cuda_ptr(out, torch.float32)))
+        return out
+
+    def set_params(self, theta):
+        import torch
+        theta = theta.to(torch.float32).contiguous()
+        _check(self._L.fs_mlp_set_params(self._h, _cuda_ptr(theta, torch.float32)))
+
+    def forward(self, X, y=None):
+        import torch
+        X = X.to(torch.float32).contiguous()
+        if y is None:
+            y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(self._L.fs_mlp_forward(self._h, _cuda_ptr(X, torch.float32), int(X.shape[0]), _cuda_ptr(y, torch.float32)))
+        return y
+
+    def loss_grad(self, X, t):
+        import torch
+        X = X.to(torch.float32).contiguous()
+        t = t.to(torch.float32).contiguous()
+        g = torch.empty(self.P, dtype=torch.float32, device=X.device)
+        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(self._L.fs_mlp_loss_grad(self._h, _cuda_ptr(X, torch.float32), _cuda_ptr(t, torch.float32),
+                                        int(X.shape[0]), _cuda_ptr(g, torch.float32), _cuda_ptr(L, torch.float32)))
+        return L, g
+
+    def train(self, X, t, steps: int, lr: float = 1e-3):
+        import torch
+        X = X.to(torch.float32).contiguous()
+        t = t.to(torch.float32).contiguous()
+        losses = torch.empty(max(int(steps), 1), dtype=torch.float32, device=X.device)
+        _check(self._L.fs_mlp_train(self._h, _cuda_ptr(X, torch.float32), _cuda_ptr(t, torch.float32),
+                                    int(X.shape[0]), int(steps), float(lr), _cuda_ptr(losses, torch.float32)))
+        return losses

@@ -1,0 +1,76 @@
+"""Surrogate MLP on the tensor cores against the CPU oracle (same bf16
+rounding points, fp64 sums): forward pass, loss, gradients, Adam training."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_10797_gb300 import fstat
+    fstat.load()
+    return fstat
+
+
+def rand_theta(W, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shp in M.param_shapes(W):
+        fan = shp[1] if len(shp) == 2 else 1
+        parts.append(rng.uniform(-1, 1, size=int(np.prod(shp))) * scale * np.sqrt(6.0 / fan))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("W,N", [(256, 1000), (64, 77)])
+def test_forward_and_gradients_match_oracle(fst, W, N):
+    theta = rand_theta(W, 1)
+    theta32 = theta.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(2)
+    X = rng.random((N, 5)).astype(np.float32)
+    t = (np.sin(4 * X[:, 0]) + X[:, 1] - X[:, 2] * X[:, 4]).astype(np.float32)
+    t[::13] = np.nan
+    net = fst.MLP(W, max_batch=2048, seed=0)
+    net.set_params(torch.from_numpy(theta32.astype(np.float32)).cuda())
+    y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    yo = M.forward(theta32, X.astype(np.float64), W)
+    scale = np.max(np.abs(yo))
+    assert np.max(np.abs(y - yo)) <= 1e-2 * scale
+    assert np.median(np.abs(y - yo)) <= 1e-4 * scale
+    L, g = net.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    Lo, go = M.loss_and_grad(theta32, X.astype(np.float64), t.astype(np.float64), W)
+    assert float(L) == pytest.approx(Lo, rel=1e-2)
+    g = g.cpu().numpy().astype(np.float64)
+    o = 0
+    for name, shp in M.param_shapes(W):
+        n = int(np.prod(shp))
+        gi, goi = g[o:o + n], go[o:o + n]
+        assert np.linalg.norm(gi - goi) <= 1e-2 * np.linalg.norm(goi) + 1e-12, name
+        o += n
+    net.close()
+
+
+def test_training_fits_smooth_target_and_is_deterministic(fst):
+    rng = np.random.default_rng(3)
+    X = torch.from_numpy(rng.random((4096, 5)).astype(np.float32)).cuda()
+    Xc = X.cpu().numpy()
+    t = torch.from_numpy((10.0 + 3.0 * (np.sin(3 * Xc[:, 0]) + Xc[:, 1] ** 2 - Xc[:, 2] * Xc[:, 3]))
+                         .astype(np.float32)).cuda()
+    runs = []
+    for _ in range(2):
+        net = fst.MLP(256, max_batch=4096, seed=11)
+        losses = net.train(X, t, steps=300, lr=2e-3).cpu().numpy()
+        y = net.forward(X)
+        runs.append((losses, y.cpu().numpy(), net.params().cpu().numpy()))
+        net.close()
+    losses, y, th = runs[0]
+    assert losses[-1] < 0.02 * losses[0]
+    # predictions come back in the units of the targets
+    rel = np.sqrt(np.mean((y - t.cpu().numpy()) ** 2)) / np.std(t.cpu().numpy())
+    assert rel < 0.15
+    assert np.array_equal(runs[0][2], runs[1][2]) and np.array_equal(runs[0][1], runs[1][1])
