@@ -237,6 +237,19 @@ FS_API fs_status fs_mlp_loss_grad(fs_mlp* mlp, const float* X_dev, const float* 
 FS_API fs_status fs_mlp_train(fs_mlp* mlp, const float* X_dev, const float* t_dev, int N, int steps, float lr,
                               float* loss_dev);
 
+/* fs_pso_step with surrogate screening: after the personal-best update, n_cand
+ * candidate moves are drawn per particle (candidate c uses the Philox counter
+ * (k, particle, dim, run | c << 20), so candidate 0 is the fs_pso_step move),
+ * the network predicts their fitness, and each particle takes the candidate
+ * with the highest prediction (lowest index among equals; candidates outside
+ * [0,1]^5 rank last).  1 <= n_cand <= 64; R * n_part * n_cand candidates go
+ * through the network in chunks of its max_batch.  The network must run on the
+ * plan's stream.  Asynchronous; allocates its candidate buffers in the plan
+ * (synchronously) when they are too small. */
+FS_API fs_status fs_pso_step_screened(fs_plan* plan, const fs_swarm* swarm, fs_mlp* mlp, int n_cand, uint64_t seed,
+                                      int iteration, double w0, double w1, int n_iter, double c1, double c2,
+                                      double vmax);
+
 /* Select the launch variant of the FS_MIXED fused kernel: 0 = 2 CTAs per SM
  * (up to 128 registers per thread), 1 = 3 CTAs per SM (up to 80).  Results are
  * identical; only the speed differs.  Default 0. */

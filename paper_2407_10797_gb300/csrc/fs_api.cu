@@ -69,6 +69,11 @@ struct fs_plan {
     // swarm evaluation scratch and the captured PSO iteration
     fs_params* pso_params;   // [B_cap]
     double* pso_F;           // [B_cap]
+    // surrogate screening candidates
+    int64_t cand_cap;
+    double *cand_x, *cand_v;
+    float *cand_in, *cand_score;
+    unsigned char* cand_inside;
 
     // segment edges (global mode)
     int64_t* edges_dev;
@@ -262,6 +267,11 @@ fs_status fs_plan_destroy(fs_plan* p) {
     cudaFree(p->tab32);
     cudaFree(p->emax);
     free(p->edges_cache);
+    cudaFree(p->cand_x);
+    cudaFree(p->cand_v);
+    cudaFree(p->cand_in);
+    cudaFree(p->cand_score);
+    cudaFree(p->cand_inside);
     if (p->prof) {
         for (auto& r : *p->prof) {
             cudaEventDestroy(r.a);
@@ -435,6 +445,45 @@ fs_status fs_pso_step(fs_plan* p, const fs_swarm* w, uint64_t seed, int iteratio
                                         w->v, w->pbest_x, w->pbest_f, w->fit, lbest_dev,
                                         dev_iter ? w->iter : nullptr, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso step launch");
+    return FS_OK;
+}
+
+fs_status fs_pso_step_screened(fs_plan* p, const fs_swarm* w, fs_mlp* mlp, int n_cand, uint64_t seed, int iteration,
+                               double w0, double w1, int n_iter, double c1, double c2, double vmax) {
+    g_err[0] = 0;
+    if (!p || !mlp) return fail(FS_EINVAL, "fs_pso_step_screened: NULL plan or network");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    if (n_cand < 1 || n_cand > 64) return fail(FS_EINVAL, "fs_pso_step_screened: n_cand must be in [1, 64]");
+    if (n_iter < 1 || !(vmax > 0.0)) return fail(FS_EINVAL, "fs_pso_step_screened: need n_iter >= 1 and vmax > 0");
+    if (iteration < 0 && !w->iter) return fail(FS_EINVAL, "fs_pso_step_screened: iteration < 0 needs swarm->iter");
+    const int64_t nc = (int64_t)w->R * w->n_part * n_cand;
+    cudaError_t e;
+    if (nc > p->cand_cap) {
+        if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        cudaFree(p->cand_x);
+        cudaFree(p->cand_v);
+        cudaFree(p->cand_in);
+        cudaFree(p->cand_score);
+        cudaFree(p->cand_inside);
+        p->cand_x = p->cand_v = nullptr;
+        p->cand_in = p->cand_score = nullptr;
+        p->cand_inside = nullptr;
+        p->cand_cap = 0;
+        if ((e = cudaMalloc(&p->cand_x, sizeof(double) * 5 * nc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->cand_v, sizeof(double) * 5 * nc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->cand_in, sizeof(float) * 5 * nc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->cand_score, sizeof(float) * nc)) != cudaSuccess ||
+            (e = cudaMalloc(&p->cand_inside, nc)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(candidates)");
+        p->cand_cap = nc;
+    }
+    const bool dev_iter = iteration < 0;
+    e = fs::launch_pso_screened(w->R, w->n_part, n_cand, seed, dev_iter ? w->iter : nullptr,
+                                dev_iter ? 0u : (unsigned int)iteration, w0, w1, n_iter, c1, c2, vmax, w->x, w->v,
+                                w->pbest_x, w->pbest_f, w->fit, p->cand_x, p->cand_v, p->cand_in, p->cand_inside,
+                                p->cand_score, mlp, dev_iter ? w->iter : nullptr, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "screened step");
     return FS_OK;
 }
 

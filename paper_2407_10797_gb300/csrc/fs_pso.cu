@@ -159,6 +159,89 @@ __global__ void pso_move_kernel(int R, int Np, int D, unsigned long long seed, c
 
 __global__ void pso_advance_kernel(unsigned int* iter_dev) { *iter_dev += 1u; }
 
+// Candidate moves for surrogate screening: n_cand velocity draws per particle,
+// candidate c with Philox counter (k, particle, dim, run | c << 20), so
+// candidate 0 is the plain move.  Writes x, v of every candidate (fp64) and
+// the fp32 network input; `inside` flags candidates in the unit box.
+__global__ void pso_candidates_kernel(int R, int Np, int D, int C, unsigned long long seed,
+                                      const unsigned int* iter_dev, unsigned int iter_host, double w0, double w1,
+                                      int n_iter, double c1, double c2, double vmax, const double* __restrict__ x,
+                                      const double* __restrict__ v, const double* __restrict__ pbx,
+                                      const double* __restrict__ pbf, double* cx, double* cv, float* cin,
+                                      unsigned char* inside) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)R * Np * C) return;
+    const int c = (int)(idx % C);
+    const int i = (int)(idx / C);
+    const unsigned int it = iter_dev ? *iter_dev : iter_host;
+    const double w = (n_iter > 1) ? __dsub_rn(w0, __dmul_rn(__dsub_rn(w0, w1), __ddiv_rn((double)it, (double)(n_iter - 1))))
+                                  : w0;
+    const int r = i / Np, p = i % Np;
+    const int cand[3] = {(p + Np - 1) % Np, p, (p + 1) % Np};
+    int best = -1;
+    for (int q = 0; q < 3; q++) {
+        const int jn = cand[q];
+        if (best < 0) {
+            best = jn;
+            continue;
+        }
+        const double fj = pbf[r * Np + jn], fb = pbf[r * Np + best];
+        if (fj > fb || (fj == fb && jn < best)) best = jn;
+    }
+    const int64_t li = (int64_t)r * Np + best;
+    bool in = true;
+    for (int j = 0; j < D; j++) {
+        uint32_t ctr[4] = {it, (uint32_t)p, (uint32_t)j, (uint32_t)r | ((uint32_t)c << 20)};
+        philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const double r1 = u53(ctr[0], ctr[1]), r2 = u53(ctr[2], ctr[3]);
+        const int64_t ij = (int64_t)i * D + j;
+        const double xv = x[ij];
+        double cog = __dmul_rn(c1, r1);
+        cog = __dmul_rn(cog, __dsub_rn(pbx[ij], xv));
+        double soc = __dmul_rn(c2, r2);
+        soc = __dmul_rn(soc, __dsub_rn(pbx[li * D + j], xv));
+        double nv = __dmul_rn(w, v[ij]);
+        nv = __dadd_rn(nv, cog);
+        nv = __dadd_rn(nv, soc);
+        if (nv > vmax) nv = vmax;
+        if (nv < -vmax) nv = -vmax;
+        const double nx = __dadd_rn(xv, nv);
+        cv[idx * D + j] = nv;
+        cx[idx * D + j] = nx;
+        cin[idx * D + j] = (float)nx;
+        in = in && nx >= 0.0 && nx <= 1.0;
+    }
+    inside[idx] = in ? 1 : 0;
+}
+
+// Keep the candidate with the highest predicted fitness (lowest index among
+// equals; out-of-box candidates rank last, and if all are out of the box the
+// plain move, candidate 0, is kept).
+__global__ void pso_select_kernel(int R, int Np, int D, int C, const float* __restrict__ score,
+                                  const unsigned char* __restrict__ inside, const double* __restrict__ cx,
+                                  const double* __restrict__ cv, double* x, double* v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * Np) return;
+    int best = 0;
+    float bs = -INFINITY;
+    bool any = false;
+    for (int c = 0; c < C; c++) {
+        const int64_t k = (int64_t)i * C + c;
+        if (!inside[k]) continue;
+        const float sc = isnan(score[k]) ? -INFINITY : score[k];
+        if (!any || sc > bs) {
+            bs = sc;
+            best = c;
+            any = true;
+        }
+    }
+    const int64_t k = (int64_t)i * C + best;
+    for (int j = 0; j < D; j++) {
+        x[(int64_t)i * D + j] = cx[k * D + j];
+        v[(int64_t)i * D + j] = cv[k * D + j];
+    }
+}
+
 // Best personal best of every run (lowest index among equals).
 __global__ void pso_best_kernel(int R, int Np, const double* __restrict__ pbf, double* best_f, int* best_i) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -209,6 +292,27 @@ cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsign
                                                     x, v, pbx, pbf, lbest);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !iter_advance) return e;
+    pso_advance_kernel<<<1, 1, 0, s>>>(iter_advance);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, const unsigned int* iter_dev,
+                                unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2,
+                                double vmax, double* x, double* v, double* pbx, double* pbf, const double* fit,
+                                double* cx, double* cv, float* cin, unsigned char* inside, float* score,
+                                fs_mlp* mlp, unsigned int* iter_advance, cudaStream_t s) {
+    const int n = R * Np;
+    if (n == 0) return cudaSuccess;
+    pso_pbest_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, x, fit, pbx, pbf);
+    const int64_t nc = (int64_t)n * C;
+    pso_candidates_kernel<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(R, Np, 5, C, seed, iter_dev, iter_host, w0, w1,
+                                                                       n_iter, c1, c2, vmax, x, v, pbx, pbf, cx, cv,
+                                                                       cin, inside);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (fs_mlp_forward(mlp, cin, (int)nc, score) != FS_OK) return cudaErrorLaunchFailure;
+    pso_select_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, C, score, inside, cx, cv, x, v);
+    if ((e = cudaGetLastError()) != cudaSuccess || !iter_advance) return e;
     pso_advance_kernel<<<1, 1, 0, s>>>(iter_advance);
     return cudaGetLastError();
 }

@@ -79,6 +79,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                          C.c_double, C.c_double, C.c_double, C.POINTER(_vp)]
         L.fs_graph_run.argtypes = [_vp, C.c_int]
         L.fs_graph_destroy.argtypes = [_vp]
+        L.fs_pso_step_screened.argtypes = [_vp, _sw, _vp, C.c_int, C.c_uint64, C.c_int, C.c_double, C.c_double,
+                                           C.c_int, C.c_double, C.c_double, C.c_double]
         L.fs_mlp_num_params.argtypes = [C.c_int]
         L.fs_mlp_num_params.restype = C.c_int64
         L.fs_mlp_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_uint64, _vp]
@@ -96,7 +98,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                      "fs_plan_set_variant", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
                      "fs_pso_graph_build", "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
                      "fs_mlp_destroy", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
-                     "fs_mlp_loss_grad", "fs_mlp_train"):
+                     "fs_mlp_loss_grad", "fs_mlp_train", "fs_pso_step_screened"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -313,6 +315,12 @@ class Swarm:
         _check(load().fs_pso_step(self.plan._h, C.byref(self.c), int(seed), int(iteration), float(w0), float(w1),
                                   int(n_iter), float(c1), float(c2), float(vmax),
                                   None if lbest is None else C.c_void_p(lbest.data_ptr())))
+
+    def step_screened(self, mlp: "MLP", n_cand: int, seed: int, iteration: int, w0=0.9, w1=0.4, n_iter=2, c1=2.0,
+                      c2=2.0, vmax=0.5):
+        _check(load().fs_pso_step_screened(self.plan._h, C.byref(self.c), mlp._h, int(n_cand), int(seed),
+                                           int(iteration), float(w0), float(w1), int(n_iter), float(c1), float(c2),
+                                           float(vmax)))
 
     def best(self):
         """(best fitness [R], best particle index [R]) as CUDA tensors."""

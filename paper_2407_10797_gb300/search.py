@@ -92,6 +92,22 @@ def box_around(center: np.ndarray, widths, prior: np.ndarray) -> np.ndarray:
 
 
 @dataclass
+class SurrogateSpec:
+    """Surrogate screening of PSO moves (not in the paper): every exact
+    evaluation adds its (position, F-hat) pairs to a per-stage buffer, the MLP
+    is retrained every `train_every` iterations, and after `warm` iterations
+    each particle takes the best of `n_cand` candidate moves as ranked by the
+    network.  The number of exact F-statistic evaluations is unchanged."""
+    n_cand: int = 16
+    warm: int = 20
+    train_every: int = 10
+    train_steps: int = 40
+    lr: float = 1e-3
+    buffer: int = 8192
+    width: int = 256
+
+
+@dataclass
 class StageResult:
     stage: int
     Np: int
@@ -105,7 +121,7 @@ class HierarchicalSearch:
     def __init__(self, plan: "fstat.Plan", prior: S.Prior, stages: list[StageSpec] | None = None,
                  n_boxes: int = 16, runs_per_box: int = 8, n_part: int = 40, seed: int = 0, q: float = 1.0,
                  checkpoint_dir: str | None = None, c1: float = 2.0, c2: float = 2.0, vmax: float = 0.5,
-                 bounds: np.ndarray | None = None):
+                 bounds: np.ndarray | None = None, surrogate: SurrogateSpec | None = None):
         """bounds: optional [5, 2] search bounds overriding the prior's (a zero
         width pins a coordinate)."""
         self.plan = plan
@@ -117,6 +133,9 @@ class HierarchicalSearch:
         self.ckpt = checkpoint_dir
         self.c1, self.c2, self.vmax = c1, c2, vmax
         self.results: list[StageResult] = []
+        self.surrogate = surrogate
+        self.mlp = None
+        self.history: dict[int, list] = {}   # best fitness after each iteration (surrogate runs)
 
     # ---------------------------------------------------------------- boxes
     def stage_boxes(self, i: int) -> np.ndarray:
@@ -155,9 +174,13 @@ class HierarchicalSearch:
         with torch.cuda.stream(self.plan.stream):
             sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q)
             sw.init(stage_seed)
-            sw.graph_build(spec.Np, stage_seed, n_iter=spec.n_iter, w0=spec.w0, w1=spec.w1, c1=self.c1,
-                           c2=self.c2, vmax=self.vmax)
-            sw.graph_run(spec.n_iter - 1)      # graph_build evaluated once; the graph does evaluate + step
+            if self.surrogate is None:
+                sw.graph_build(spec.Np, stage_seed, n_iter=spec.n_iter, w0=spec.w0, w1=spec.w1, c1=self.c1,
+                               c2=self.c2, vmax=self.vmax)
+                sw.graph_run(spec.n_iter - 1)      # the graph does evaluate + step
+                sw.graph_free()
+            else:
+                self._run_screened(sw, spec, stage_seed, i)
             sw.evaluate(spec.Np)               # fitness of the final positions
             sw.step(stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter)   # folds them into pbest
             best_f, best_i = sw.best()
@@ -173,6 +196,38 @@ class HierarchicalSearch:
         res = StageResult(i, spec.Np, boxes.tolist(), winners, wf, time.perf_counter() - t0)
         self._save(res)
         return res
+
+    def _run_screened(self, sw, spec: StageSpec, stage_seed: int, stage: int):
+        """n_iter - 1 iterations of evaluate + (screened) step, collecting
+        training pairs; eager launches on the plan's stream."""
+        import torch
+        sp = self.surrogate
+        if self.mlp is None:
+            self.mlp = fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed, stream=self.plan.stream)
+        n = sw.R * sw.n_part
+        cap = sp.buffer
+        bx = torch.zeros(cap, 5, dtype=torch.float32, device=sw.x.device)
+        bt = torch.full((cap,), float("nan"), dtype=torch.float32, device=sw.x.device)
+        count = 0
+        hist = []
+        for it in range(spec.n_iter - 1):
+            sw.evaluate(spec.Np)
+            idx = (torch.arange(n, device=sw.x.device) + count) % cap
+            bx[idx] = sw.x.reshape(-1, 5).float()
+            f = sw.fit.reshape(-1)
+            bt[idx] = torch.where(torch.isfinite(f), f, torch.full_like(f, float("nan"))).float()
+            count += n
+            if it >= sp.warm:
+                if (it - sp.warm) % sp.train_every == 0:
+                    m = min(count, cap)
+                    self.mlp.train(bx[:m], bt[:m], sp.train_steps, sp.lr)
+                sw.step_screened(self.mlp, sp.n_cand, stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter,
+                                 c1=self.c1, c2=self.c2, vmax=self.vmax)
+            else:
+                sw.step(stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter, c1=self.c1, c2=self.c2,
+                        vmax=self.vmax)
+            hist.append(sw.pbest_f.max())
+        self.history[stage] = [float(h) for h in torch.stack(hist).cpu().numpy()] if hist else []
 
     # ---------------------------------------------------------------- checkpoints
     def _path(self, i):
