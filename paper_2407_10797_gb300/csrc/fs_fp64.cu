@@ -69,148 +69,172 @@ cudaError_t launch_precompute(const Grid& g, const double* data, const double* p
 // ---------------------------------------------------------------------------
 // A1: per-particle coefficients and band edges.
 // ---------------------------------------------------------------------------
-__global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int B, Particle* parts,
-                             int global) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    ::fs_params in = params[b];
-    Particle P;
-    memset(&P, 0, sizeof(P));
-    bool ok = isfinite(in.Mc) && isfinite(in.tc) && isfinite(in.lat) && isfinite(in.lon) &&
-              isfinite(in.e0) && isfinite(in.q) && in.Mc > 0.0 && in.q > 0.0;
-    P.valid = ok ? 1 : 0;
+// First k in [lo, hi) with pred(k) true for a predicate that is false then
+// true along k (hi if none), searched by a whole warp: each round probes 32
+// points and keeps the interval between the last false and first true probe.
+template <typename Pred>
+__device__ int64_t warp_search_first(int64_t lo, int64_t hi, Pred pred) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const int64_t w = hi - lo;
+        const int64_t q = lo + (w * (lane + 1)) / 33;   // strictly increasing in lane, inside [lo, hi)
+        const unsigned m = __ballot_sync(0xffffffffu, pred(q));
+        if (m == 0u) {
+            lo = __shfl_sync(0xffffffffu, q, 31) + 1;
+        } else {
+            const int f = __ffs(m) - 1;
+            const int64_t qf = __shfl_sync(0xffffffffu, q, f);
+            const int64_t qp = __shfl_sync(0xffffffffu, q, f > 0 ? f - 1 : 0);
+            if (f > 0) lo = qp + 1;
+            hi = qf;
+        }
+    }
+    const int64_t k = lo + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, k < hi && pred(k));
+    return m ? lo + (__ffs(m) - 1) : hi;
+}
+
+// One warp per particle: lane 0 derives the coefficients, nine lanes sample the
+// antenna patterns for their harmonics, and the warp searches the band edges.
+__global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int B, Particle* parts, int global) {
+    __shared__ Particle sp[4];
+    __shared__ double fs9[4][2][9], cs9[4][9], sn9[4][9];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int b = blockIdx.x * 4 + wl;
+    if (b >= B) return;   // warp-uniform
+    Particle& P = sp[wl];
+    const ::fs_params in = params[b];
+    const bool ok = isfinite(in.Mc) && isfinite(in.tc) && isfinite(in.lat) && isfinite(in.lon) &&
+                    isfinite(in.e0) && isfinite(in.q) && in.Mc > 0.0 && in.q > 0.0;
     if (!ok) {
-        P.klo = 1;
-        P.khi = 0;
-        parts[b] = P;
+        if (lane == 0) {
+            Particle Q;
+            memset(&Q, 0, sizeof(Q));
+            Q.valid = 0;
+            Q.klo = 1;
+            Q.khi = 0;
+            parts[b] = Q;
+        }
         return;
     }
-    double eta = in.q / ((1.0 + in.q) * (1.0 + in.q));
-    // Mc in seconds (exact product as a double-double), x = pi Mc
-    double mh, ml;
-    two_prod(in.Mc, kMsunS, mh, ml);
-    double xh, xl;
-    dd_mul(kPi, kPiLo, mh, ml, xh, xl);
-    // y = x^-5/3 (double-double): Newton step on y^-3 = x^5
-    double y0 = pow(xh, -5.0 / 3.0);
-    double y2h, y2l, y3h, y3l, x2h, x2l, x4h, x4l, x5h, x5l, ph, pl;
-    dd_mul(y0, 0.0, y0, 0.0, y2h, y2l);
-    dd_mul(y2h, y2l, y0, 0.0, y3h, y3l);
-    dd_mul(xh, xl, xh, xl, x2h, x2l);
-    dd_mul(x2h, x2l, x2h, x2l, x4h, x4l);
-    dd_mul(x4h, x4l, xh, xl, x5h, x5l);
-    dd_mul(y3h, y3l, x5h, x5l, ph, pl);
-    double r = (1.0 - ph) - pl;
-    double yh, yl;
-    fast_two_sum(y0, y0 * r * (1.0 / 3.0), yh, yl);
-    // P0 = (3/256) y / pi   (Psi_PN/(2 pi) with (3/128)(pi Mc f)^-5/3 at leading order)
-    double ah, al;
-    dd_mul(3.0 / 256.0, 0.0, yh, yl, ah, al);
-    dd_mul(ah, al, kInvPi, kInvPiLo, P.P0h, P.P0l);
-    // PN coefficients alpha_k (non-spinning TaylorF2 to 2PN)
-    double a2 = 3715.0 / 756.0 + 55.0 * eta / 9.0;
-    double a3 = -16.0 * kPi;
-    double a4 = 15293365.0 / 508032.0 + 27145.0 * eta / 504.0 + 3085.0 * eta * eta / 72.0;
-    double M = mh * pow(eta, -0.6);
-    double v1 = cbrt(kPi * M);   // (pi M)^(1/3)
-    double P0 = P.P0h;
-    P.P2 = P0 * a2 * v1 * v1;
-    P.P3 = P0 * a3 * v1 * v1 * v1;
-    P.P4 = P0 * a4 * v1 * v1 * v1 * v1;
-    P.E0 = -(2355.0 / 1462.0) * in.e0 * in.e0 * P0;
-    // t(f) = dPhi/df: T_k = P_k (k - 5)/3, eccentric part -(34/9) E0 f^-8/3 (f0/f)^(19/9)
-    P.T0 = -(5.0 / 3.0) * P0;
-    P.T2 = -P.P2;
-    P.T3 = -(2.0 / 3.0) * P.P3;
-    P.T4 = -(1.0 / 3.0) * P.P4;
-    P.TE = -(34.0 / 9.0) * P.E0;
-    P.tc = in.tc;
-    // Doppler: d(t) = R sin(theta) cos(alpha - phi), theta = pi/2 - beta
-    double sb, cb, sl, cl;
-    sincos(in.lat, &sb, &cb);
-    sincos(in.lon, &sl, &cl);
-    P.AD = kAuS * cb;
-    P.clon = cl;
-    P.slon = sl;
-    // antenna: arm unit vectors u_nm = (dr_m - dr_n)/L of the rigid constellation,
-    // u = [k(dc C2 + ds S2 - 3 dc), k(dc S2 - ds C2 - 3 ds), -(dc C1 + ds S1)/2],
-    // k = 1/(4 sqrt 3), dc = cos b_m - cos b_n, ds = sin b_m - sin b_n, b_n = 2 pi n/3 + orient.
-    double cbn[3], sbn[3];
-    for (int n = 0; n < 3; n++) sincos(2.0 * kPi * n / 3.0 + g.orient, &sbn[n], &cbn[n]);
-    const double kap = 1.0 / (4.0 * sqrt(3.0));
-    double pv[3] = {sb * cl, sb * sl, -cb};   // theta-hat
-    double qv[3] = {-sl, cl, 0.0};            // phi-hat
-    for (int arm = 0; arm < 2; arm++) {
-        int m = arm + 1;
-        double dc = cbn[m] - cbn[0], ds = sbn[m] - sbn[0];
-        for (int j = 0; j < 2; j++) {
-            const double* w = j == 0 ? pv : qv;
-            double* c = P.pr[arm * 2 + j];
-            c[0] = -3.0 * kap * (dc * w[0] + ds * w[1]);
-            c[1] = -0.5 * dc * w[2];
-            c[2] = -0.5 * ds * w[2];
-            c[3] = kap * (dc * w[0] - ds * w[1]);
-            c[4] = kap * (ds * w[0] + dc * w[1]);
-        }
-    }
-    // F+ and Fx are degree-4 trig polynomials in alpha: their harmonics by a
-    // 9-point discrete Fourier transform (exact for degree <= 4).
-    {
-        double fp9[9], fx9[9];
-        for (int j = 0; j < 9; j++) {
-            double sj, cj;
-            sincospi(2.0 * j / 9.0, &sj, &cj);
-            antenna_of(P, cj, sj, fp9[j], fx9[j]);
-        }
-        for (int f = 0; f < 2; f++) {
-            const double* v = f == 0 ? fp9 : fx9;
-            double a0 = 0.0;
-            for (int j = 0; j < 9; j++) a0 += v[j];
-            P.harm[f][0] = a0 / 9.0;
-            for (int h = 1; h <= 4; h++) {
-                double ah = 0.0, bh = 0.0;
-                for (int j = 0; j < 9; j++) {
-                    double sj, cj;
-                    sincospi(2.0 * h * j / 9.0, &sj, &cj);
-                    ah += v[j] * cj;
-                    bh += v[j] * sj;
-                }
-                P.harm[f][2 * h - 1] = 2.0 * ah / 9.0;
-                P.harm[f][2 * h] = 2.0 * bh / 9.0;
+    if (lane == 0) {
+        memset(&P, 0, sizeof(P));
+        P.valid = 1;
+        const double eta = in.q / ((1.0 + in.q) * (1.0 + in.q));
+        // Mc in seconds (exact product as a double-double), x = pi Mc
+        double mh, ml;
+        two_prod(in.Mc, kMsunS, mh, ml);
+        double xh, xl;
+        dd_mul(kPi, kPiLo, mh, ml, xh, xl);
+        // y = x^-5/3 (double-double): Newton step on y^-3 = x^5
+        const double y0 = pow(xh, -5.0 / 3.0);
+        double y2h, y2l, y3h, y3l, x2h, x2l, x4h, x4l, x5h, x5l, ph, pl;
+        dd_mul(y0, 0.0, y0, 0.0, y2h, y2l);
+        dd_mul(y2h, y2l, y0, 0.0, y3h, y3l);
+        dd_mul(xh, xl, xh, xl, x2h, x2l);
+        dd_mul(x2h, x2l, x2h, x2l, x4h, x4l);
+        dd_mul(x4h, x4l, xh, xl, x5h, x5l);
+        dd_mul(y3h, y3l, x5h, x5l, ph, pl);
+        const double r = (1.0 - ph) - pl;
+        double yh, yl;
+        fast_two_sum(y0, y0 * r * (1.0 / 3.0), yh, yl);
+        // P0 = (3/256) y / pi   (Psi_PN/(2 pi) with (3/128)(pi Mc f)^-5/3 at leading order)
+        double ah, al;
+        dd_mul(3.0 / 256.0, 0.0, yh, yl, ah, al);
+        dd_mul(ah, al, kInvPi, kInvPiLo, P.P0h, P.P0l);
+        // PN coefficients alpha_k (non-spinning TaylorF2 to 2PN)
+        const double a2 = 3715.0 / 756.0 + 55.0 * eta / 9.0;
+        const double a3 = -16.0 * kPi;
+        const double a4 = 15293365.0 / 508032.0 + 27145.0 * eta / 504.0 + 3085.0 * eta * eta / 72.0;
+        const double M = mh * pow(eta, -0.6);
+        const double v1 = cbrt(kPi * M);   // (pi M)^(1/3)
+        const double P0 = P.P0h;
+        P.P2 = P0 * a2 * v1 * v1;
+        P.P3 = P0 * a3 * v1 * v1 * v1;
+        P.P4 = P0 * a4 * v1 * v1 * v1 * v1;
+        P.E0 = -(2355.0 / 1462.0) * in.e0 * in.e0 * P0;
+        // t(f) = dPhi/df: T_k = P_k (k - 5)/3, eccentric part -(34/9) E0 f^-8/3 (f0/f)^(19/9)
+        P.T0 = -(5.0 / 3.0) * P0;
+        P.T2 = -P.P2;
+        P.T3 = -(2.0 / 3.0) * P.P3;
+        P.T4 = -(1.0 / 3.0) * P.P4;
+        P.TE = -(34.0 / 9.0) * P.E0;
+        P.tc = in.tc;
+        // Doppler: d(t) = R sin(theta) cos(alpha - phi), theta = pi/2 - beta
+        double sb, cb, sl, cl;
+        sincos(in.lat, &sb, &cb);
+        sincos(in.lon, &sl, &cl);
+        P.AD = kAuS * cb;
+        P.clon = cl;
+        P.slon = sl;
+        // antenna: arm unit vectors u_nm = (dr_m - dr_n)/L of the rigid constellation,
+        // u = [k(dc C2 + ds S2 - 3 dc), k(dc S2 - ds C2 - 3 ds), -(dc C1 + ds S1)/2],
+        // k = 1/(4 sqrt 3), dc = cos b_m - cos b_n, ds = sin b_m - sin b_n, b_n = 2 pi n/3 + orient.
+        double cbn[3], sbn[3];
+        for (int n = 0; n < 3; n++) sincos(2.0 * kPi * n / 3.0 + g.orient, &sbn[n], &cbn[n]);
+        const double kap = 1.0 / (4.0 * sqrt(3.0));
+        const double pv[3] = {sb * cl, sb * sl, -cb};   // theta-hat
+        const double qv[3] = {-sl, cl, 0.0};            // phi-hat
+        for (int arm = 0; arm < 2; arm++) {
+            const int m = arm + 1;
+            const double dc = cbn[m] - cbn[0], ds = sbn[m] - sbn[0];
+            for (int j = 0; j < 2; j++) {
+                const double* w = j == 0 ? pv : qv;
+                double* c = P.pr[arm * 2 + j];
+                c[0] = -3.0 * kap * (dc * w[0] + ds * w[1]);
+                c[1] = -0.5 * dc * w[2];
+                c[2] = -0.5 * ds * w[2];
+                c[3] = kap * (dc * w[0] - ds * w[1]);
+                c[4] = kap * (ds * w[0] + dc * w[1]);
             }
         }
     }
-    // band: first bin with t >= 0 and last bin with t <= T_obs (binary searches on k)
-    if (global) {
-        P.klo = 0;
-        P.khi = g.n - 1;
-    } else {
-        int64_t lo = 0, hi = g.n;
-        while (lo < hi) {
-            int64_t mid = lo + (hi - lo) / 2;
-            double f = bin_freq(g, mid);
-            double t = time_of(P, powers_of(f));
-            if (t >= 0.0) hi = mid; else lo = mid + 1;
-        }
-        P.klo = lo;
-        lo = 0;
-        hi = g.n;
-        while (lo < hi) {
-            int64_t mid = lo + (hi - lo) / 2;
-            double f = bin_freq(g, mid);
-            double t = time_of(P, powers_of(f));
-            if (t > g.T_obs) hi = mid; else lo = mid + 1;
-        }
-        P.khi = lo - 1;
+    __syncwarp();
+    // F+ and Fx are degree-4 trig polynomials in alpha: their harmonics by a
+    // 9-point discrete Fourier transform (exact for degree <= 4); lane j < 9
+    // samples alpha_j = 2 pi j / 9.
+    if (lane < 9) {
+        double sj, cj;
+        sincospi(2.0 * lane / 9.0, &sj, &cj);
+        cs9[wl][lane] = cj;
+        sn9[wl][lane] = sj;
+        antenna_of(P, cj, sj, fs9[wl][0][lane], fs9[wl][1][lane]);
     }
-    parts[b] = P;
+    __syncwarp();
+    if (lane < 10) {   // lane = 2 h + f: harmonic h of pattern f (h = 0..4)
+        const int h = lane >> 1, f = lane & 1;
+        double ah = 0.0, bh = 0.0;
+        for (int j = 0; j < 9; j++) {
+            const int a = (h * j) % 9;   // cos/sin(2 pi h j / 9) = table entry (h j mod 9)
+            ah += fs9[wl][f][j] * cs9[wl][a];
+            bh += fs9[wl][f][j] * sn9[wl][a];
+        }
+        if (h == 0) {
+            P.harm[f][0] = ah / 9.0;
+        } else {
+            P.harm[f][2 * h - 1] = 2.0 * ah / 9.0;
+            P.harm[f][2 * h] = 2.0 * bh / 9.0;
+        }
+    }
+    __syncwarp();
+    // band: first bin with t >= 0 and last bin with t <= T_obs
+    int64_t klo = 0, khi = g.n - 1;
+    if (!global) {
+        klo = warp_search_first(0, g.n, [&](int64_t k) { return time_of(P, powers_of(bin_freq(g, k))) >= 0.0; });
+        khi = warp_search_first(0, g.n, [&](int64_t k) { return time_of(P, powers_of(bin_freq(g, k))) > g.T_obs; }) - 1;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        P.klo = klo;
+        P.khi = khi;
+        parts[b] = P;
+    }
 }
 
 cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Particle* parts, int global,
                          cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
-    int threads = 64;
-    setup_kernel<<<(B + threads - 1) / threads, threads, 0, s>>>(g, params, B, parts, global);
+    setup_kernel<<<(B + 3) / 4, 128, 0, s>>>(g, params, B, parts, global);
     return cudaGetLastError();
 }
 
