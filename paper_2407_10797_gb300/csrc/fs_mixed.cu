@@ -48,6 +48,12 @@ __device__ __forceinline__ unsigned long long to_fixed(double x) {
     return ((unsigned long long)hi << 32) + (unsigned long long)lo;
 }
 
+// Fixed-point fraction of a small value (|x| < 0.5 cycle) without the floor.
+__device__ __forceinline__ unsigned long long to_fixed_small(double x) {
+    if (!(fabs(x) < 0.5)) return to_fixed(x);
+    return (unsigned long long)__double2ll_rn(x * 18446744073709551616.0);
+}
+
 // Phase polynomial at integer offset d (exact modulo 2^64).
 __device__ __forceinline__ unsigned long long poly_fx(const unsigned long long c[4], long long d) {
     unsigned long long u = (unsigned long long)d;
@@ -96,20 +102,25 @@ __device__ __noinline__ void make_anchor(const Grid& g, const Tables& tb, const 
     double rest = T2 + T3 + T4 + Te;
     acc += rest - rint(rest);
     // derivatives of sum_m T_m (f/f_a)^{p_m}: d^n/df^n = sum_m p_m (p_m - 1) ... T_m / f^n
+    // (S1, S2 in FP64: t_a to 1e-15 relative and c2 to 1e-10; S3, S4 only
+    // enter c3, the alpha offset and the validity bound, where FP32 suffices)
     const double p0 = -5.0 / 3.0, p2 = -1.0, p3 = -2.0 / 3.0, p4 = -1.0 / 3.0, pe = -34.0 / 9.0;
-    double k0 = p0, k2 = p2, k3 = p3, k4 = p4, ke = pe;
-    const double S1 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
-    k0 *= p0 - 1.0; k2 *= p2 - 1.0; k3 *= p3 - 1.0; k4 *= p4 - 1.0; ke *= pe - 1.0;
-    const double S2 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
-    k0 *= p0 - 2.0; k2 *= p2 - 2.0; k3 *= p3 - 2.0; k4 *= p4 - 2.0; ke *= pe - 2.0;
-    const double S3 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
-    k0 *= p0 - 3.0; k2 *= p2 - 3.0; k3 *= p3 - 3.0; k4 *= p4 - 3.0; ke *= pe - 3.0;
-    const double S4 = k0 * T0 + k2 * T2 + k3 * T3 + k4 * T4 + ke * Te;
+    const double S1 = p0 * T0 + p2 * T2 + p3 * T3 + p4 * T4 + pe * Te;
+    const double S2 = (p0 * (p0 - 1.0)) * T0 + (p2 * (p2 - 1.0)) * T2 + (p3 * (p3 - 1.0)) * T3 +
+                      (p4 * (p4 - 1.0)) * T4 + (pe * (pe - 1.0)) * Te;
+    const float T0f = (float)T0, T2f = (float)T2, T3f = (float)T3, T4f = (float)T4, Tef = (float)Te;
+    constexpr float q30 = (float)(p0 * (p0 - 1.0) * (p0 - 2.0)), q32 = (float)(p2 * (p2 - 1.0) * (p2 - 2.0)),
+                    q33 = (float)(p3 * (p3 - 1.0) * (p3 - 2.0)), q34 = (float)(p4 * (p4 - 1.0) * (p4 - 2.0)),
+                    q3e = (float)(pe * (pe - 1.0) * (pe - 2.0));
+    const float S3 = q30 * T0f + q32 * T2f + q33 * T3f + q34 * T4f + q3e * Tef;
+    const float S4 = q30 * (float)(p0 - 3.0) * T0f + q32 * (float)(p2 - 3.0) * T2f + q33 * (float)(p3 - 3.0) * T3f +
+                     q34 * (float)(p4 - 3.0) * T4f + q3e * (float)(pe - 3.0) * Tef;
     const double inv = 1.0 / fh;
     const double ta = P.tc + S1 * inv;           // t(f_a) = dPhi_orb/df
     const double d2 = S2 * inv * inv;            // dt/df
-    const double d3 = S3 * inv * inv * inv;      // d2t/df2
-    const double d4 = S4 * inv * inv * inv * inv;
+    const float invf = (float)inv;
+    const float d3 = S3 * invf * invf * invf;    // d2t/df2
+    const float d4 = S4 * invf * invf * invf * invf;
     // orbit and Doppler at the anchor
     const double Om = kTwoPi / kYearS;
     double sa, ca;
@@ -118,23 +129,25 @@ __device__ __noinline__ void make_anchor(const Grid& g, const Tables& tb, const 
     const double sda = fma(sa, P.clon, -ca * P.slon);  // sin(alpha_a - phi)
     acc -= fh * P.AD * cda;
     const double df = g.df;
+    const float dff = (float)df;
     A.c[0] = to_fixed(acc);
     A.c[1] = to_fixed(ta * df);
-    A.c[2] = to_fixed(0.5 * d2 * df * df);
-    A.c[3] = to_fixed(d3 * df * df * df / 6.0);
+    A.c[2] = to_fixed_small(0.5 * d2 * df * df);
+    A.c[3] = to_fixed_small((double)(d3 * dff * dff * dff) * (1.0 / 6.0));
+    const float Omf = (float)Om;
     A.w1 = (float)(Om * d2 * df);
-    A.w2 = (float)(0.5 * Om * d3 * df * df);
+    A.w2 = 0.5f * Omf * d3 * dff * dff;
     // Doppler phase minus its anchor value, with x = alpha - phi = x_a + da:
     //   AD [f_a (cos x - cos x_a) + dk df cos x],  cos^(n)(x_a) cycles through (c, -s, -c, s)
     {
-        const double cn[6] = {cda, -sda, -cda, sda, cda, -sda};
-        double fact = 1.0;
-        const double ADfa = P.AD * fh, ADdf = P.AD * df;
-        for (int n = 0; n <= 5; n++) {
-            if (n > 0) fact *= n;
-            if (n >= 1) A.e[n - 1] = (float)(ADfa * cn[n] / fact);
-            if (n <= 3) A.q[n] = (float)(ADdf * cn[n] / fact);
-        }
+        const float cf = (float)cda, sf = (float)sda;
+        const float cn[6] = {cf, -sf, -cf, sf, cf, -sf};
+        const float inv_fact[6] = {1.f, 1.f, 0.5f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f};
+        const float ADfa = (float)(P.AD * fh), ADdf = (float)(P.AD * df);
+#pragma unroll
+        for (int n = 1; n <= 5; n++) A.e[n - 1] = ADfa * cn[n] * inv_fact[n];
+#pragma unroll
+        for (int n = 0; n <= 3; n++) A.q[n] = ADdf * cn[n] * inv_fact[n];
     }
     // antenna: F(alpha_a + da) = sum_n F^(n)(alpha_a) da^n / n!, from the harmonics;
     // F(alpha_a) in FP64, the derivative terms (multiplied by da^n <= 0.06^n) in FP32
@@ -179,11 +192,13 @@ __device__ __noinline__ void make_anchor(const Grid& g, const Tables& tb, const 
         }
     }
     // validity of the truncated expansions over |dk| <= hmax
-    const double H = hmax * df;
-    const double rem_phase = 1.2 * fabs(d4) * H * H * H * H / 24.0;     // cycles
-    const double rem_alpha = 1.2 * Om * fabs(d4) * H * H * H / 6.0;     // rad
-    const double da_max = fabs(Om * d2 * df) * hmax + fabs(0.5 * Om * d3 * df * df) * hmax * hmax;
-    A.mode = (rem_phase <= 1e-6 && rem_alpha <= 1e-6 && da_max <= 0.06) ? 1 : 2;
+    const float hm = (float)hmax;
+    const float H = hm * dff;
+    const float rem_phase = 1.2f * fabsf(d4) * H * H * H * H * (1.f / 24.f);    // cycles
+    const float rem_alpha = 1.2f * Omf * fabsf(d4) * H * H * H * (1.f / 6.f);    // rad
+    const float da_max = fabsf(A.w1) * hm + fabsf(A.w2) * hm * hm;
+    const bool finite = isfinite(rem_phase) && isfinite(da_max);
+    A.mode = (finite && rem_phase <= 1e-6f && rem_alpha <= 1e-6f && da_max <= 0.06f) ? 1 : 2;
 }
 
 // Coefficients of G1 = c F+ + s Fx and G2 = c Fx - s F+ in powers of d(alpha)
@@ -287,7 +302,8 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
     } else {
         anc[threadIdx.x].mode = 0;
     }
-    __syncthreads();
+    // each warp reads only its own 32 anchors
+    __syncwarp();
     if (!active) return;
 
     // ---- phase B: warp w walks its particle's tiles of the span
