@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--variant", type=int, default=None,
+                    help="force one launch variant of the fused kernel instead of autotuning")
     ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
                     help="one small evaluation for kernel profiling: paper grid, 64 particles, N_p = 16")
     return ap.parse_args()
@@ -288,18 +290,27 @@ class ModeRun:
     """One precision mode on the bench workload: a plan, one 8 x 40 swarm and
     one captured PSO iteration (evaluate + update) per N_p of the schedule."""
 
-    def __init__(self, fstat, mode, g, d_dev, psd_dev, box, stream, seed):
+    def __init__(self, fstat, mode, g, d_dev, psd_dev, box, stream, seed, variant=None):
         import torch
         self.torch = torch
         self.plan = fstat.Plan.from_grid(g, mode=mode, stream=stream)
         self.stream = stream
+        self.tuning = {}
         with torch.cuda.stream(stream):
             self.plan.set_data(d_dev, psd_dev)
             self.plan.reserve(RUNS * NPART, max(NP_LIST))
+            if variant is not None:
+                self.plan.set_variant(variant)
             self.sw = {}
             for Np in NP_LIST:
                 sw = fstat.Swarm(self.plan, RUNS, NPART, np.repeat(box[None], RUNS, axis=0))
                 sw.init(seed)
+                if variant is None:
+                    # the autotuner picks the fused kernel's launch variant per N_p
+                    v, ms = sw.autotune(Np, reps=3)
+                    self.tuning[Np] = {"variant": v, "ms_per_variant": [round(m, 4) for m in ms]}
+                else:
+                    self.tuning[Np] = {"variant": variant, "forced": True}
                 sw.graph_build(Np, seed, n_iter=2000)
                 self.sw[Np] = sw
             torch.cuda.synchronize()
@@ -412,7 +423,8 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
     seed = 1000 + rank
 
-    run64 = ModeRun(fstat, fstat.FS_FP64, g, d_dev, psd_dev, box, stream, seed)
+    run64 = ModeRun(fstat, fstat.FS_FP64, g, d_dev, psd_dev, box, stream, seed,
+                    variant=None if args.variant is None else min(args.variant, 2))
     # in-band particle*bins of the prior draw the steps evaluate
     x0 = run64.x0.cpu().numpy().reshape(-1, 5)
     P0 = np.stack([search.to_physical(x, box) for x in x0])
@@ -446,10 +458,11 @@ def run_gpu(args, world, rank, local):
         barrier(world)
     e2e_ms = allmax(world, e0.elapsed_time(e1))
     e2e_value = total_pbins / (e2e_ms / 1e3)
+    tune64 = run64.tuning
     run64.close()
 
     # ---- mixed mode on the same data and particles
-    runm = ModeRun(fstat, fstat.FS_MIXED, g, d_dev, psd_dev, box, stream, seed)
+    runm = ModeRun(fstat, fstat.FS_MIXED, g, d_dev, psd_dev, box, stream, seed, variant=args.variant)
     ms_m, prof_m, clocks_m = time_run(args, world, runm)
     value_m = total_pbins / (ms_m / 1e3)
     Fm = runm.fitness_at_x0()
@@ -458,6 +471,7 @@ def run_gpu(args, world, rank, local):
         a64, am = F64[Np].ravel() * Np, Fm[Np].ravel() * Np
         ok = np.isfinite(a64)
         mix_err = max(mix_err, float(np.max(np.abs(am[ok] - a64[ok]) / np.maximum(np.abs(a64[ok]), 2.0 * Np))))
+    tunem = runm.tuning
     runm.close()
 
     # ---- roofline of the dominant kernels (average launch duration, live events)
@@ -497,6 +511,8 @@ def run_gpu(args, world, rank, local):
                          "peak_source": "unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                          "flop_per_pbin": FP64_FLOP_PER_PBIN},
             "clocks": clocks,
+            "autotune": {"fp64": {str(k): v for k, v in tune64.items()},
+                         "mixed": {str(k): v for k, v in tunem.items()}},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(len(NP_LIST) * 2 * host["x"].numel() * 8),
                     "d2h_bytes_per_step": int(host["fit"].numel() * 8)},
@@ -522,6 +538,8 @@ def run_profile_case(args):
     mode = fstat.FS_MIXED if args.profile_case == "mixed" else fstat.FS_FP64
     plan = fstat.Plan.from_grid(g, mode=mode)
     plan.set_data(torch.from_numpy(noise).cuda(), torch.from_numpy(psd).cuda())
+    if args.variant is not None:
+        plan.set_variant(args.variant)
     P_dev = torch.from_numpy(P[:64] if mode == fstat.FS_FP64 else P).cuda()
     for _ in range(2):
         F, _ = plan.fstat(P_dev, 16, want_parts=False)

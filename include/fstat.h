@@ -115,6 +115,24 @@ FS_API fs_status fs_plan_reserve(fs_plan* plan, int B_max, int N_p_max);
 FS_API fs_status fs_fstat_batch(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
                          int N_p, double* F_dev, double* F_part_dev);
 
+/* Maximum-likelihood amplitudes and extrinsic parameters (Eq. aandMN3 and
+ * App. B, Eqs. B2-B3), per particle and segment.
+ *   Arguments as in fs_fstat_batch; F_dev may be NULL (plan scratch).
+ *   a_dev   : B*N_p*4 doubles, a = M^-1 N of each segment in the basis
+ *             A1 = F+ h0, A2 = Fx h0, A3 = -i F+ h0, A4 = -i Fx h0 with
+ *             h0 = f^-7/6 exp(-i Psi): the data's best fit in the segment is
+ *             sum_i a_i A^i.  The amplitude constant of Eq. A2 and the phase
+ *             constants -phi_c - pi/4 are part of a.  A segment that
+ *             contributes F_p = 0 (fewer than 4 bins or singular M) gets a = 0;
+ *             a particle with F = NaN gets NaN.
+ *   ext_dev : B*N_p*4 doubles (D_L, iota, psi, phi_c) from a by Eqs. B2-B3
+ *             (arctan of a ratio read as atan2; D_L in the units of a, i.e.
+ *             1/D_L = the overall amplitude of a), NaN where a = 0; or NULL.
+ * With N_p = 1 these are the fully coherent estimates the search reports
+ * after its last stage.  Asynchronous, stream-ordered. */
+FS_API fs_status fs_amplitudes(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
+                               int N_p, double* F_dev, double* a_dev, double* ext_dev);
+
 /* Add the signal h = sum_i a_i A^i of one particle to data_dev (n_bins
  * interleaved complex FP64, device) at the bins of the particle's band
  * [first, last bin with t(f_k) in [0, T_obs]]; the other bins are untouched.
@@ -250,10 +268,47 @@ FS_API fs_status fs_pso_step_screened(fs_plan* plan, const fs_swarm* swarm, fs_m
                                       int iteration, double w0, double w1, int n_iter, double c1, double c2,
                                       double vmax);
 
-/* Select the launch variant of the FS_MIXED fused kernel: 0 = 2 CTAs per SM
- * (up to 128 registers per thread), 1 = 3 CTAs per SM (up to 80).  Results are
- * identical; only the speed differs.  Default 0. */
+/* Launch variants of the fused bin-loop kernel (the tile shape of the
+ * ragged batch, Sec. IV's particle x frequency parallelism).
+ *   FS_FP64 : 0 = 2048-bin tiles per (particle, tile) item, 1 = 1024, 2 = 4096.
+ *             Tile edges change how partial sums are grouped, so F differs
+ *             between variants by rounding only (relative 1e-15 per segment).
+ *   FS_MIXED: 0 = one CTA per (span of 32768 bins, 8 in-band particles), 2
+ *             CTAs per SM; 1 = the same with 3 CTAs per SM; 2 = persistent
+ *             kernel (one grid of SMs x resident CTAs whose warps take
+ *             (span, particle) items from a device-side counter), 2 CTAs per
+ *             SM; 3 = persistent, 3 CTAs per SM.  F is bit-identical across
+ *             the four.
+ * Which variant a call uses: the forced one if fs_plan_set_variant gave one
+ * (>= 0), else the one recorded for (N_p, edge kind) by fs_plan_autotune,
+ * fs_pso_autotune or fs_plan_set_variant_for, else 0.
+ *
+ * fs_plan_set_variant: force `variant` for every call, or -1 to return to
+ * the per-(N_p, edge kind) choice.  FS_EINVAL if out of range. */
 FS_API fs_status fs_plan_set_variant(fs_plan* plan, int variant);
+
+/* Record `variant` for calls with this N_p and edge kind (global_edges != 0:
+ * edges_host given; 0: per-particle edges), as the autotuner would.  Lets a
+ * resumed search reuse the choices of the run it continues. */
+FS_API fs_status fs_plan_set_variant_for(fs_plan* plan, int N_p, int global_edges, int variant);
+
+/* The variant a call with this N_p and edge kind would use now. */
+FS_API fs_status fs_plan_get_variant(fs_plan* plan, int N_p, int global_edges, int* variant);
+
+/* Autotuner: time every variant on this batch (one untimed call, then `reps`
+ * calls between CUDA events on the plan's stream, 1 <= reps <= 1000), record
+ * the fastest for (N_p, edge kind) and return it in *variant_out (may be
+ * NULL); ms_out (may be NULL) receives the mean ms per call of each variant
+ * (4 entries in FS_MIXED, 3 in FS_FP64).  Synchronous; FS_EINVAL while the
+ * plan's stream is being captured.  Arguments as in fs_fstat_batch; the F
+ * values computed go to plan scratch, not to the caller. */
+FS_API fs_status fs_plan_autotune(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
+                                  int N_p, int reps, int* variant_out, float* ms_out);
+
+/* fs_plan_autotune on the swarm's current positions (mapped to physical
+ * parameters as fs_pso_evaluate does).  The swarm is not modified. */
+FS_API fs_status fs_pso_autotune(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p,
+                                 int reps, int* variant_out, float* ms_out);
 
 /* Kernel timing on the plan's stream.  While enabled, every kernel the plan
  * launches is bracketed by CUDA events.  fs_plan_read_profile waits for the

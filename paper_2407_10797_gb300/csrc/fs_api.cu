@@ -63,9 +63,17 @@ struct fs_plan {
     // mixed mode: FP32 (dw, W) tables and the scale exponent
     float4* tab32;
     int* emax;
-    int mixed_variant;   // kernel variant of the mixed path (see fs_plan_set_variant)
+    // launch variant of the fused kernel: forced (>= 0) or looked up per
+    // (N_p, edge kind) among the autotuned choices, else variant 0
+    int variant_forced;
+    struct TuneRec {
+        int Np, global, variant;
+    };
+    static constexpr int kTuneMax = 64;
+    TuneRec tuned[kTuneMax];
+    int n_tuned;
     int* span_list;      // [B][nspans] in-band particles per span (mixed path)
-    int* span_cnt;       // [nspans]
+    int* span_cnt;       // [nspans] counts, [nspans + 1] item offsets, [3] persistent-kernel counters
     // swarm evaluation scratch and the captured PSO iteration
     fs_params* pso_params;   // [B_cap]
     double* pso_F;           // [B_cap]
@@ -96,6 +104,29 @@ struct fs_plan {
 namespace {
 
 constexpr int kKinds = 4;
+
+// Launch variants of the fused kernel.  FS_FP64: tile of 2048, 1024 or 4096
+// bins per (particle, tile) item.  FS_MIXED: grid form with 2 or 3 resident
+// CTAs per SM, persistent form with 2 or 3.
+int n_variants(int mode) { return mode == FS_MIXED ? 4 : 3; }
+
+int fp64_tile(int variant) { return variant == 1 ? 1024 : variant == 2 ? 4096 : fs::kTile; }
+
+int resolve_variant(const fs_plan* p, int Np, int global) {
+    if (p->variant_forced >= 0) return p->variant_forced;
+    for (int i = 0; i < p->n_tuned; i++)
+        if (p->tuned[i].Np == Np && p->tuned[i].global == global) return p->tuned[i].variant;
+    return 0;
+}
+
+void record_tuned(fs_plan* p, int Np, int global, int variant) {
+    for (int i = 0; i < p->n_tuned; i++)
+        if (p->tuned[i].Np == Np && p->tuned[i].global == global) {
+            p->tuned[i].variant = variant;
+            return;
+        }
+    if (p->n_tuned < fs_plan::kTuneMax) p->tuned[p->n_tuned++] = {Np, global, variant};
+}
 
 cudaEvent_t take_event(fs_plan* p) {
     if (!p->spare->empty()) {
@@ -170,7 +201,8 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
         (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->span_list, sizeof(int) * (size_t)nb * (nt > 0 ? nt : 1))) != cudaSuccess ||
-        (e = cudaMalloc(&p->span_cnt, sizeof(int) * (nt > 0 ? nt : 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->span_cnt, sizeof(int) * (2 * nt + 4))) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->span_cnt, 0, sizeof(int) * (2 * nt + 4), p->stream)) != cudaSuccess ||
         (e = cudaMalloc(&p->pso_params, sizeof(fs_params) * (size_t)nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->pso_F, sizeof(double) * (size_t)nb)) != cudaSuccess) {
         free_workspace(p);
@@ -219,7 +251,9 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
     p->grid.orient = 0.0;
     p->mode = mode;
     p->stream = (cudaStream_t)stream;
-    p->ntiles = (int)((n_bins + fs::kTile - 1) / fs::kTile);
+    p->ntiles = (int)((n_bins + fs::kTileMin - 1) / fs::kTileMin);
+    p->variant_forced = -1;
+    p->n_tuned = 0;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) {
         delete p;
@@ -306,9 +340,38 @@ fs_status fs_plan_reserve(fs_plan* p, int B_max, int Np_max) {
     return ensure_workspace(p, B_max > 0 ? B_max : 1, Np_max);
 }
 
+namespace {
+fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+                     double* F_dev, double* F_part_dev, double* amp_dev);
+}
+
 fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
                          double* F_dev, double* F_part_dev) {
     g_err[0] = 0;
+    return fstat_impl(p, params_dev, B, edges_host, Np, F_dev, F_part_dev, nullptr);
+}
+
+fs_status fs_amplitudes(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+                        double* F_dev, double* a_dev, double* ext_dev) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_amplitudes: plan is NULL");
+    if (!a_dev) return fail(FS_EINVAL, "fs_amplitudes: a is NULL");
+    if (B <= 0) return B == 0 ? FS_OK : fail(FS_EINVAL, "fs_amplitudes: B = %d < 0", B);
+    if (Np < 1 || Np > fs::kNpMax) return fail(FS_EINVAL, "fs_amplitudes: N_p = %d not in [1, %d]", Np, fs::kNpMax);
+    fs_status st = ensure_workspace(p, B, Np);
+    if (st != FS_OK) return st;
+    if ((st = fstat_impl(p, params_dev, B, edges_host, Np, F_dev ? F_dev : p->pso_F, nullptr, a_dev)) != FS_OK)
+        return st;
+    if (ext_dev) {
+        cudaError_t e = fs::launch_extrinsic((int64_t)B * Np, a_dev, ext_dev, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "extrinsic launch");
+    }
+    return FS_OK;
+}
+
+namespace {
+fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+                     double* F_dev, double* F_part_dev, double* amp_dev) {
     if (!p) return fail(FS_EINVAL, "fs_fstat_batch: plan is NULL");
     if (B < 0) return fail(FS_EINVAL, "fs_fstat_batch: B = %d < 0", B);
     if (Np < 1 || Np > fs::kNpMax) return fail(FS_EINVAL, "fs_fstat_batch: N_p = %d not in [1, %d]", Np, fs::kNpMax);
@@ -352,7 +415,8 @@ fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const i
     pa.rot = p->rot;
     const bool mixed = p->mode == FS_MIXED;
     pa.rot32 = mixed ? p->rot32 : nullptr;
-    pa.tile = mixed ? fs::mixed_span() : fs::kTile;
+    const int variant = resolve_variant(p, Np, global);
+    pa.tile = mixed ? fs::mixed_span() : fp64_tile(variant);
     pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
     {
@@ -365,7 +429,7 @@ fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const i
     {
         ProfScope ps(p, 1);
         if (mixed) {
-            if ((e = fs::launch_mixed_main(p->grid, p->tab, p->tab32, p->parts, B, sg, pa, p->mixed_variant,
+            if ((e = fs::launch_mixed_main(p->grid, p->tab, p->tab32, p->parts, B, sg, pa, variant,
                                            p->span_list, p->span_cnt, p->stream)) != cudaSuccess)
                 return cuda_fail(e, "mixed main launch");
         } else if ((e = fs::launch_fp64_main(p->grid, p->tab, p->parts, B, sg, pa, p->stream)) != cudaSuccess) {
@@ -374,11 +438,12 @@ fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const i
     }
     {
         ProfScope ps(p, 2);
-        if ((e = fs::launch_reduce(p->grid, p->parts, B, sg, pa, Fpart, F_dev, p->stream)) != cudaSuccess)
+        if ((e = fs::launch_reduce(p->grid, p->parts, B, sg, pa, Fpart, F_dev, p->stream, amp_dev)) != cudaSuccess)
             return cuda_fail(e, "reduce launch");
     }
     return FS_OK;
 }
+}  // namespace
 
 fs_status fs_particle_bands(fs_plan* p, const fs_params* params_dev, int B, int64_t* bands_dev) {
     g_err[0] = 0;
@@ -429,6 +494,21 @@ fs_status fs_pso_evaluate(fs_plan* p, const fs_swarm* w, const int64_t* edges_ho
     if ((e = fs::launch_pso_fitness(n, p->pso_F, Np, w->fit, p->stream)) != cudaSuccess)
         return cuda_fail(e, "pso fitness launch");
     return FS_OK;
+}
+
+fs_status fs_pso_autotune(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np, int reps,
+                          int* variant_out, float* ms_out) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_pso_autotune: plan is NULL");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    if (!w->box) return fail(FS_EINVAL, "fs_pso_autotune: box is NULL");
+    const int n = w->R * w->n_part;
+    if (n == 0) return fail(FS_EINVAL, "fs_pso_autotune: empty swarm");
+    if ((st = ensure_workspace(p, n, Np)) != FS_OK) return st;
+    cudaError_t e = fs::launch_pso_map(w->R, w->n_part, w->x, w->box, w->q, p->pso_params, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pso map launch");
+    return fs_plan_autotune(p, p->pso_params, n, edges_host, Np, reps, variant_out, ms_out);
 }
 
 fs_status fs_pso_step(fs_plan* p, const fs_swarm* w, uint64_t seed, int iteration, double w0, double w1, int n_iter,
@@ -566,8 +646,81 @@ fs_status fs_graph_destroy(fs_graph* g) {
 
 fs_status fs_plan_set_variant(fs_plan* p, int variant) {
     g_err[0] = 0;
-    if (!p || variant < 0 || variant > 1) return fail(FS_EINVAL, "fs_plan_set_variant: variant must be 0 or 1");
-    p->mixed_variant = variant;
+    if (!p) return fail(FS_EINVAL, "fs_plan_set_variant: plan is NULL");
+    if (variant < -1 || variant >= n_variants(p->mode))
+        return fail(FS_EINVAL, "fs_plan_set_variant: variant must be -1 or in [0, %d)", n_variants(p->mode));
+    p->variant_forced = variant;
+    return FS_OK;
+}
+
+fs_status fs_plan_set_variant_for(fs_plan* p, int Np, int global_edges, int variant) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_plan_set_variant_for: plan is NULL");
+    if (Np < 1 || Np > fs::kNpMax) return fail(FS_EINVAL, "fs_plan_set_variant_for: N_p = %d out of range", Np);
+    if (variant < 0 || variant >= n_variants(p->mode))
+        return fail(FS_EINVAL, "fs_plan_set_variant_for: variant must be in [0, %d)", n_variants(p->mode));
+    record_tuned(p, Np, global_edges ? 1 : 0, variant);
+    return FS_OK;
+}
+
+fs_status fs_plan_get_variant(fs_plan* p, int Np, int global_edges, int* variant) {
+    g_err[0] = 0;
+    if (!p || !variant) return fail(FS_EINVAL, "fs_plan_get_variant: NULL argument");
+    *variant = resolve_variant(p, Np, global_edges ? 1 : 0);
+    return FS_OK;
+}
+
+fs_status fs_plan_autotune(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+                           int reps, int* variant_out, float* ms_out) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_plan_autotune: plan is NULL");
+    if (reps < 1 || reps > 1000) return fail(FS_EINVAL, "fs_plan_autotune: reps = %d not in [1, 1000]", reps);
+    if (B < 1) return fail(FS_EINVAL, "fs_plan_autotune: need B >= 1");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(p->stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone) return fail(FS_EINVAL, "fs_plan_autotune: the stream is being captured");
+    fs_status st = ensure_workspace(p, B, Np);
+    if (st != FS_OK) return st;
+    double* F = p->pso_F;   // scratch output, distinct from every parameter buffer
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if ((e = cudaEventCreate(&ev[0])) != cudaSuccess || (e = cudaEventCreate(&ev[1])) != cudaSuccess) {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    const int saved = p->variant_forced;
+    const int global = edges_host != nullptr;
+    int best = 0;
+    float best_ms = 0.f;
+    st = FS_OK;
+    for (int v = 0; v < n_variants(p->mode) && st == FS_OK; v++) {
+        p->variant_forced = v;
+        if ((st = fs_fstat_batch(p, params_dev, B, edges_host, Np, F, nullptr)) != FS_OK) break;   // warm-up
+        if ((e = cudaEventRecord(ev[0], p->stream)) != cudaSuccess) {
+            st = cuda_fail(e, "cudaEventRecord");
+            break;
+        }
+        for (int r = 0; r < reps && st == FS_OK; r++) st = fs_fstat_batch(p, params_dev, B, edges_host, Np, F, nullptr);
+        if (st != FS_OK) break;
+        float ms = 0.f;
+        if ((e = cudaEventRecord(ev[1], p->stream)) != cudaSuccess || (e = cudaEventSynchronize(ev[1])) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, ev[0], ev[1])) != cudaSuccess) {
+            st = cuda_fail(e, "autotune timing");
+            break;
+        }
+        ms /= (float)reps;
+        if (ms_out) ms_out[v] = ms;
+        if (v == 0 || ms < best_ms) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    p->variant_forced = saved;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != FS_OK) return st;
+    record_tuned(p, Np, global, best);
+    if (variant_out) *variant_out = best;
     return FS_OK;
 }
 

@@ -301,7 +301,7 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
     const Particle P = parts[b];
     if (!P.valid) return;
     const SegView sv = seg_view(sg, P);
-    int64_t lo = (int64_t)tile * kTile, hi = lo + kTile;
+    int64_t lo = (int64_t)tile * pa.tile, hi = lo + pa.tile;
     if (lo < sv.lo) lo = sv.lo;
     if (hi > sv.hi + 1) hi = sv.hi + 1;
     if (lo >= hi) return;
@@ -391,7 +391,7 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
 // det <= 1e-12 P R with P = sum W F+^2, R = sum W Fx^2 recovered from K.
 // ---------------------------------------------------------------------------
 __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
-                              double* Fpart) {
+                              double* Fpart, double* amp) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= (int64_t)B * sg.Np) return;
@@ -399,7 +399,11 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
     const int p = (int)(wid % sg.Np);
     const Particle& P = parts[b];
     if (!P.valid) {
-        if (lane == 0) Fpart[wid] = __longlong_as_double(0x7ff8000000000000LL);
+        if (lane == 0) {
+            Fpart[wid] = __longlong_as_double(0x7ff8000000000000LL);
+            if (amp)
+                for (int i = 0; i < 4; i++) amp[wid * 4 + i] = __longlong_as_double(0x7ff8000000000000LL);
+        }
         return;
     }
     const SegView sv = seg_view(sg, P);
@@ -438,13 +442,59 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
         double Pp = cc * K11 - cs2 * K12 + ss * K22;   // sum W F+^2
         double Rr = ss * K11 + cs2 * K12 + cc * K22;   // sum W Fx^2
         double F = 0.0;
-        if (nb >= 4 && det > 1e-12 * Pp * Rr) {
+        const bool solvable = nb >= 4 && det > 1e-12 * Pp * Rr;
+        if (solvable) {
             double num = K22 * (X1r * X1r + X1i * X1i) - 2.0 * K12 * (X1r * X2r + X1i * X2i) +
                          K11 * (X2r * X2r + X2i * X2i);
             F = 0.5 * num / det;
         }
         Fpart[wid] = F;
+        if (amp) {
+            // Eq. aandMN3, a = M^-1 N with M = diag(K, K) and N = (Re X1, Re X2, -Im X1, -Im X2)
+            // in the rotated basis (G1 h0, G2 h0, -i G1 h0, -i G2 h0), then back to the
+            // (F+ h0, Fx h0, -i F+ h0, -i Fx h0) basis: G1 = c F+ + s Fx, G2 = c Fx - s F+.
+            double a4v[4] = {0.0, 0.0, 0.0, 0.0};
+            if (solvable) {
+                const double id = 1.0 / det;
+                const double b1 = (K22 * X1r - K12 * X2r) * id, b2 = (K11 * X2r - K12 * X1r) * id;
+                const double b3 = -(K22 * X1i - K12 * X2i) * id, b4 = -(K11 * X2i - K12 * X1i) * id;
+                a4v[0] = rc.x * b1 - rc.y * b2;
+                a4v[1] = rc.y * b1 + rc.x * b2;
+                a4v[2] = rc.x * b3 - rc.y * b4;
+                a4v[3] = rc.y * b3 + rc.x * b4;
+            }
+            for (int i = 0; i < 4; i++) amp[wid * 4 + i] = a4v[i];
+        }
     }
+}
+
+// App. B, Eqs. B2-B3: (D_L, iota, psi, phi_c) from the amplitudes a of one
+// segment, the printed arctan of a ratio read as atan2(numerator, denominator).
+// A+^2 - Ax^2 is evaluated as 4 r1 r2 (the same quantity, without cancellation).
+// All-zero amplitudes (a degenerate segment) give NaN.
+__global__ void extrinsic_kernel(int64_t n, const double* __restrict__ amp, double* ext) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a1 = amp[i * 4], a2 = amp[i * 4 + 1], a3 = amp[i * 4 + 2], a4 = amp[i * 4 + 3];
+    const double r1 = sqrt((a1 + a4) * (a1 + a4) + (a2 - a3) * (a2 - a3));
+    const double r2 = sqrt((a1 - a4) * (a1 - a4) + (a2 + a3) * (a2 + a3));
+    const double Ap = r1 + r2, Ax = r1 - r2;
+    const double root = 2.0 * sqrt(r1 * r2);
+    const double A = Ap + root;
+    double out[4];
+    if (!(A > 0.0)) {
+        for (int j = 0; j < 4; j++) out[j] = __longlong_as_double(0x7ff8000000000000LL);
+    } else {
+        out[0] = 2.0 / A;                                            // D_L
+        out[1] = acos(fmin(1.0, fmax(-1.0, -Ax / A)));                 // iota
+        const double num = Ap * a4 - Ax * a1;
+        const double psi = 0.5 * atan2(num, -(Ax * a2 + Ap * a3));
+        out[2] = psi;
+        const double s2 = sin(2.0 * psi);
+        const double c = s2 > 0.0 ? 1.0 : (s2 < 0.0 ? -1.0 : 0.0);
+        out[3] = atan2(c * num, -c * (Ax * a3 + Ap * a2));           // phi_c
+    }
+    for (int j = 0; j < 4; j++) ext[i * 4 + j] = out[j];
 }
 
 __global__ void sum_segments_kernel(const Particle* __restrict__ parts, int B, int Np, const double* Fpart,
@@ -459,16 +509,22 @@ __global__ void sum_segments_kernel(const Particle* __restrict__ parts, int B, i
 }
 
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
-                          double* Fpart, double* F, cudaStream_t s) {
+                          double* Fpart, double* F, cudaStream_t s, double* amp) {
     if (B <= 0) return cudaSuccess;
     const int threads = 256;
     int64_t warps = (int64_t)B * sg.Np;
     int64_t blocks = (warps * 32 + threads - 1) / threads;
-    reduce_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart);
+    reduce_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int64_t blocks2 = ((int64_t)B * 32 + threads - 1) / threads;
     sum_segments_kernel<<<(unsigned)blocks2, threads, 0, s>>>(parts, B, sg.Np, Fpart, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extrinsic(int64_t n, const double* amp, double* ext, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    extrinsic_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, amp, ext);
     return cudaGetLastError();
 }
 

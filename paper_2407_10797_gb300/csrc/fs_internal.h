@@ -10,7 +10,8 @@
 
 namespace fs {
 
-constexpr int kTile = 2048;          // bins per (particle, tile) work item of the FP64 kernel
+constexpr int kTile = 2048;          // bins per (particle, tile) work item of the FP64 kernel (default)
+constexpr int kTileMin = 1024;       // smallest FP64 tile a launch variant uses (sizes the workspace)
 constexpr int kWarpsPerCta = 8;      // particles per CTA of the FP64 kernel
 constexpr int kNpMax = 4096;
 
@@ -63,7 +64,9 @@ cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const S
 cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
                              const Partials& pa, cudaStream_t s);
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
-                          double* Fpart, double* F, cudaStream_t s);
+                          double* Fpart, double* F, cudaStream_t s,
+                          double* amp = nullptr);
+cudaError_t launch_extrinsic(int64_t n, const double* amp, double* ext, cudaStream_t s);
 cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s);
 // variant 0: 2 CTAs/SM (up to 128 registers), 1: 3 CTAs/SM (up to 80 registers)
 cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,

@@ -251,63 +251,79 @@ __device__ __forceinline__ void mixed_bin(unsigned long long Fv, float d, float4
 
 // In-band particles of every span, in increasing particle order: one warp per
 // span.  list[span * B + j] is the j-th particle whose band meets the span and
-// cnt[span] their number.  The fused kernel gives each CTA 8 of them, so no
-// warp of a launched CTA idles on a particle that has no bin in the span.
+// cnt[span] their number, so no warp of the fused kernel idles on a particle
+// that has no bin in the span.  With `off` given, the last CTA to finish
+// (counted on ctl[0]) also writes the exclusive prefix off[s] = sum of cnt
+// over spans before s, off[nspans] = the number of work items, and resets the
+// persistent kernel's item counter ctl[1] and ctl[0] itself to zero.
 __global__ void span_lists_kernel(const Particle* __restrict__ parts, int B, Segs sg, int nspans, int* list,
-                                  int* cnt) {
+                                  int* cnt, int* off, int* ctl) {
     const int lane = threadIdx.x & 31;
     const int span = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (span >= nspans) return;
-    const int64_t lo = (int64_t)span * kSpanMix, hi = lo + kSpanMix - 1;
-    int n = 0;
-    for (int b0 = 0; b0 < B; b0 += 32) {
-        const int b = b0 + lane;
-        bool in = false;
-        if (b < B && parts[b].valid) {
-            const SegView sv = seg_view(sg, parts[b]);
-            in = sv.lo <= sv.hi && sv.lo <= hi && sv.hi >= lo;
+    if (span < nspans) {   // warp-uniform
+        const int64_t lo = (int64_t)span * kSpanMix, hi = lo + kSpanMix - 1;
+        int n = 0;
+        for (int b0 = 0; b0 < B; b0 += 32) {
+            const int b = b0 + lane;
+            bool in = false;
+            if (b < B && parts[b].valid) {
+                const SegView sv = seg_view(sg, parts[b]);
+                in = sv.lo <= sv.hi && sv.lo <= hi && sv.hi >= lo;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (in) list[(int64_t)span * B + n + __popc(m & ((1u << lane) - 1u))] = b;
+            n += __popc(m);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) list[(int64_t)span * B + n + __popc(m & ((1u << lane) - 1u))] = b;
-        n += __popc(m);
+        if (lane == 0) cnt[span] = n;
     }
-    if (lane == 0) cnt[span] = n;
+    if (off == nullptr) return;   // uniform over the grid
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctl[0], 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    int run = 0;
+    for (int s0 = 0; s0 < nspans; s0 += 32) {
+        const int s = s0 + lane;
+        const int v = s < nspans ? __ldcg(&cnt[s]) : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (s < nspans) off[s] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) {
+        off[nspans] = run;
+        ctl[1] = 0;
+        ctl[0] = 0;
+    }
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(kWarpsMix * 32, MINB)
-mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts, int B,
-                  Segs sg, Partials pa, const int* __restrict__ list, const int* __restrict__ cnt) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Anchor* anc = reinterpret_cast<Anchor*>(smem_raw);
-    const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5;
-    const int span = blockIdx.x;
-    const int n_in = cnt[span];
-    if ((int)blockIdx.y * kWarpsMix >= n_in) return;   // whole CTA idle (uniform)
-    const int j = blockIdx.y * kWarpsMix + w;
-    const int b = j < n_in ? list[(int64_t)span * B + j] : B;
+// One work item: particle b over span `span`, by one warp.  Phase A: one
+// anchor per lane (tile `lane` of the span) into the warp's 32 anchor slots;
+// phase B: the warp walks the particle's tiles of the span.  Partial sums
+// go to the slots of (b, span) and to the per-segment slots of the segments
+// that start and end inside the span.
+__device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, const float4* __restrict__ t32,
+                                           const Particle* __restrict__ parts, const Segs& sg, const Partials& pa,
+                                           int span, int b, Anchor* anc, int lane) {
     const int64_t span_lo = (int64_t)span * kSpanMix;
-
-    // ---- phase A: one anchor per thread (particle w, tile lane of the span)
-    const bool active = b < B;
-    SegView sv;
-    if (active) {
-        const Particle& P = parts[b];
-        sv = seg_view(sg, P);
+    const Particle& P = parts[b];
+    const SegView sv = seg_view(sg, P);
+    {
         int64_t lo = span_lo + (int64_t)lane * kTileMix, hi = lo + kTileMix;
         if (lo < sv.lo) lo = sv.lo;
         if (hi > sv.hi + 1) hi = sv.hi + 1;
-        make_anchor(g, tb, P, span_lo, lo, hi, anc[threadIdx.x]);
-    } else {
-        anc[threadIdx.x].mode = 0;
+        make_anchor(g, tb, P, span_lo, lo, hi, anc[lane]);
     }
-    // each warp reads only its own 32 anchors
     __syncwarp();
-    if (!active) return;
 
-    // ---- phase B: warp w walks its particle's tiles of the span
-    const Particle& P = parts[b];
+    // ---- phase B
     const int64_t slot = (int64_t)b * pa.ntiles + span;
     const double2* rot64 = pa.rot + (int64_t)b * sg.Np;
     const float2* rot32 = pa.rot32 + (int64_t)b * sg.Np;
@@ -323,7 +339,7 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
     float g1[7], g2[7];
 
     for (int ti = 0; ti < kTilesPerSpan; ti++) {
-        const Anchor& A = anc[w * 32 + ti];
+        const Anchor& A = anc[ti];
         if (A.mode == 0) continue;
         const int lo = A.lo, hi = A.hi;
         if (cur < 0) cur = sv.seg(span_lo + lo);
@@ -442,16 +458,98 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
     }
 }
 
+// Grid form: CTA (span, group of 8 in-band particles of the span), one warp per particle.
+template <int MINB>
+__global__ void __launch_bounds__(kWarpsMix * 32, MINB)
+mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts, int B,
+                  Segs sg, Partials pa, const int* __restrict__ list, const int* __restrict__ cnt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Anchor* anc = reinterpret_cast<Anchor*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int span = blockIdx.x;
+    const int j = blockIdx.y * kWarpsMix + w;
+    if (j >= cnt[span]) return;   // warp-uniform
+    mixed_item(g, tb, t32, parts, sg, pa, span, list[(int64_t)span * B + j], anc + w * 32, lane);
+}
+
+// Persistent form: a grid of (SMs x resident CTAs) whose warps take work
+// items (span, in-band particle) from a shared counter, in span-major order,
+// until the list is exhausted.  No warp waits on another: a warp that finds
+// the counter past the end returns.
+template <int MINB>
+__global__ void __launch_bounds__(kWarpsMix * 32, MINB)
+mixed_persistent_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts,
+                        int B, Segs sg, Partials pa, const int* __restrict__ list, const int* __restrict__ off,
+                        int nspans, int* ctl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Anchor* anc = reinterpret_cast<Anchor*>(smem_raw) + (threadIdx.x >> 5) * 32;
+    const int lane = threadIdx.x & 31;
+    const int total = off[nspans];
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&ctl[1], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        // span = the last s with off[s] <= item (off is non-decreasing, off[0] = 0)
+        int lo = 0, hi = nspans;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int b = list[(int64_t)lo * B + (item - off[lo])];
+        __syncwarp();   // every lane is done with the previous item's anchors
+        mixed_item(g, tb, t32, parts, sg, pa, lo, b, anc, lane);
+    }
+}
+
+namespace {
+
+// Resident CTAs per SM times SMs for a persistent kernel, cached per device.
+template <typename K>
+int persistent_grid(K kernel, size_t smem, int variant_slot) {
+    static int cache[64][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int& v = cache[dev][variant_slot];
+    if (v > 0) return v;
+    int nsm = 0, per = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kWarpsMix * 32, smem) != cudaSuccess) return 0;
+    v = nsm * (per > 0 ? per : 1);
+    return v;
+}
+
+}  // namespace
+
 cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
                               const Segs& sg, const Partials& pa, int variant, int* list, int* cnt,
                               cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
     const int nspans = pa.ntiles;
-    span_lists_kernel<<<(unsigned)((nspans * 32 + 255) / 256), 256, 0, s>>>(parts, B, sg, nspans, list, cnt);
+    const bool persistent = variant >= 2;
+    int* off = cnt + nspans;            // [nspans + 1]
+    int* ctl = cnt + 2 * nspans + 1;    // [3]: CTAs done, next item, spare
+    const size_t smem = sizeof(Anchor) * kWarpsMix * 32;
+    span_lists_kernel<<<(unsigned)((nspans * 32 + 255) / 256), 256, 0, s>>>(parts, B, sg, nspans, list, cnt,
+                                                                             persistent ? off : nullptr, ctl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (persistent) {
+        const bool three = variant == 3;
+        const int grid = three ? persistent_grid(mixed_persistent_kernel<3>, smem, 1)
+                               : persistent_grid(mixed_persistent_kernel<2>, smem, 0);
+        if (grid <= 0) return cudaErrorInvalidConfiguration;
+        if (three)
+            mixed_persistent_kernel<3><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, off,
+                                                                          nspans, ctl);
+        else
+            mixed_persistent_kernel<2><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, off,
+                                                                          nspans, ctl);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)nspans, (unsigned)((B + kWarpsMix - 1) / kWarpsMix));
-    const size_t smem = sizeof(Anchor) * kWarpsMix * 32;
     if (variant == 1)
         mixed_main_kernel<3><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, cnt);
     else

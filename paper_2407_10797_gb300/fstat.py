@@ -61,6 +61,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_plan_set_data.argtypes = [_vp, _vp, _vp]
         L.fs_plan_reserve.argtypes = [_vp, C.c_int, C.c_int]
         L.fs_fstat_batch.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp]
+        L.fs_amplitudes.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp, _vp]
         L.fs_add_signal.argtypes = [_vp, C.POINTER(fs_params), _dp, _vp]
         L.fs_constants.argtypes = [_dp]
         L.fs_particle_bands.argtypes = [_vp, _vp, C.c_int, _vp]
@@ -68,10 +69,15 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                              C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp, _vp]
         L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
         L.fs_plan_set_variant.argtypes = [_vp, C.c_int]
+        L.fs_plan_set_variant_for.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
+        L.fs_plan_get_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
+        L.fs_plan_autotune.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int,
+                                       C.POINTER(C.c_int), C.POINTER(C.c_float)]
         _sw = C.POINTER(fs_swarm)
         _ep = C.POINTER(C.c_int64)
         L.fs_pso_init.argtypes = [_vp, _sw, C.c_uint64]
         L.fs_pso_evaluate.argtypes = [_vp, _sw, _ep, C.c_int]
+        L.fs_pso_autotune.argtypes = [_vp, _sw, _ep, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
         L.fs_pso_step.argtypes = [_vp, _sw, C.c_uint64, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
                                   C.c_double, C.c_double, _vp]
         L.fs_pso_best.argtypes = [_vp, _sw, _vp, _vp]
@@ -93,9 +99,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
         for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
-                     "fs_fstat_batch", "fs_add_signal", "fs_constants", "fs_particle_bands",
+                     "fs_fstat_batch", "fs_amplitudes", "fs_add_signal", "fs_constants", "fs_particle_bands",
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
-                     "fs_plan_set_variant", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
+                     "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
+                     "fs_plan_autotune", "fs_pso_autotune", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
                      "fs_pso_graph_build", "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
                      "fs_mlp_destroy", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
                      "fs_mlp_loss_grad", "fs_mlp_train", "fs_pso_step_screened"):
@@ -140,6 +147,7 @@ class Plan:
         L = load()
         self._L = L
         self.n = int(n_bins)
+        self.mode = int(mode)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(L.fs_plan_create(C.byref(h), self.n, float(f_min), float(df), float(T_obs), int(mode),
@@ -200,6 +208,23 @@ class Plan:
                                       _cuda_ptr(F_part, torch.float64) if F_part is not None else None))
         return F, F_part
 
+    def amplitudes(self, params, Np: int = 1, edges=None, extrinsic: bool = True):
+        """(F [B], a [B, N_p, 4], (D_L, iota, psi, phi_c) [B, N_p, 4] or None):
+        maximum-likelihood amplitudes per segment and their extrinsic parameters."""
+        import torch
+        if params.dim() != 2 or params.shape[1] != 6:
+            raise ValueError("params must be [B, 6]")
+        B = params.shape[0]
+        dev = params.device
+        F = torch.empty(B, dtype=torch.float64, device=dev)
+        a = torch.empty(B, Np, 4, dtype=torch.float64, device=dev)
+        ext = torch.empty(B, Np, 4, dtype=torch.float64, device=dev) if extrinsic else None
+        arr, e = _edges_arg(edges, Np)
+        _check(self._L.fs_amplitudes(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(B), e, int(Np),
+                                     _cuda_ptr(F, torch.float64), _cuda_ptr(a, torch.float64),
+                                     _cuda_ptr(ext, torch.float64) if ext is not None else None))
+        return F, a, ext
+
     def bands(self, params, out=None):
         """Per-particle (first, last) in-band bin, int64 CUDA tensor [B, 2]."""
         import torch
@@ -213,7 +238,31 @@ class Plan:
     KERNELS = {"setup": 0, "main": 1, "reduce": 2, "precompute": 3}
 
     def set_variant(self, variant: int):
+        """Force a launch variant of the fused kernel for every call (-1: per-N_p choice)."""
         _check(self._L.fs_plan_set_variant(self._h, int(variant)))
+
+    def set_variant_for(self, Np: int, variant: int, global_edges: bool = False):
+        _check(self._L.fs_plan_set_variant_for(self._h, int(Np), 1 if global_edges else 0, int(variant)))
+
+    def get_variant(self, Np: int, global_edges: bool = False) -> int:
+        v = C.c_int()
+        _check(self._L.fs_plan_get_variant(self._h, int(Np), 1 if global_edges else 0, C.byref(v)))
+        return v.value
+
+    @property
+    def n_variants(self) -> int:
+        return 4 if self.mode == FS_MIXED else 3
+
+    def autotune(self, params, Np: int, edges=None, reps: int = 3):
+        """Time every launch variant on this batch and keep the fastest for
+        (N_p, edge kind).  Returns (variant, [mean ms per call of each variant])."""
+        import torch
+        arr, e = _edges_arg(edges, Np)
+        v = C.c_int()
+        ms = (C.c_float * 4)()
+        _check(self._L.fs_plan_autotune(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
+                                        e, int(Np), int(reps), C.byref(v), ms))
+        return v.value, [ms[i] for i in range(self.n_variants)]
 
     def set_profiling(self, enable: bool):
         _check(self._L.fs_plan_set_profiling(self._h, 1 if enable else 0))
@@ -310,6 +359,14 @@ class Swarm:
     def evaluate(self, Np: int, edges=None):
         arr, e = _edges_arg(edges, Np)
         _check(load().fs_pso_evaluate(self.plan._h, C.byref(self.c), e, int(Np)))
+
+    def autotune(self, Np: int, edges=None, reps: int = 3):
+        """fs_pso_autotune: pick the plan's fastest variant on the current positions."""
+        arr, e = _edges_arg(edges, Np)
+        v = C.c_int()
+        ms = (C.c_float * 4)()
+        _check(load().fs_pso_autotune(self.plan._h, C.byref(self.c), e, int(Np), int(reps), C.byref(v), ms))
+        return v.value, [ms[i] for i in range(self.plan.n_variants)]
 
     def step(self, seed: int, iteration: int, w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5, lbest=None):
         _check(load().fs_pso_step(self.plan._h, C.byref(self.c), int(seed), int(iteration), float(w0), float(w1),

@@ -115,15 +115,20 @@ class StageResult:
     winners: list          # physical parameters of the best run of every box
     winner_f: list         # their fitness (F-hat)
     seconds: float
+    variant: int = -1      # launch variant of the fused kernel this stage used
 
 
 class HierarchicalSearch:
     def __init__(self, plan: "fstat.Plan", prior: S.Prior, stages: list[StageSpec] | None = None,
                  n_boxes: int = 16, runs_per_box: int = 8, n_part: int = 40, seed: int = 0, q: float = 1.0,
                  checkpoint_dir: str | None = None, c1: float = 2.0, c2: float = 2.0, vmax: float = 0.5,
-                 bounds: np.ndarray | None = None, surrogate: SurrogateSpec | None = None):
+                 bounds: np.ndarray | None = None, surrogate: SurrogateSpec | None = None,
+                 autotune: bool | None = None):
         """bounds: optional [5, 2] search bounds overriding the prior's (a zero
-        width pins a coordinate)."""
+        width pins a coordinate).  autotune: time the fused kernel's launch
+        variants on each stage's first swarm and use the fastest; None = only
+        for FS_MIXED plans, whose variants give bitwise-equal F (FP64 variants
+        differ by rounding, which can steer a PSO run differently)."""
         self.plan = plan
         self.prior = prior
         self.bounds = None if bounds is None else np.asarray(bounds, dtype=np.float64)
@@ -136,6 +141,7 @@ class HierarchicalSearch:
         self.surrogate = surrogate
         self.mlp = None
         self.history: dict[int, list] = {}   # best fitness after each iteration (surrogate runs)
+        self.autotune = (plan.mode == fstat.FS_MIXED) if autotune is None else bool(autotune)
 
     # ---------------------------------------------------------------- boxes
     def stage_boxes(self, i: int) -> np.ndarray:
@@ -174,6 +180,7 @@ class HierarchicalSearch:
         with torch.cuda.stream(self.plan.stream):
             sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q)
             sw.init(stage_seed)
+            variant = sw.autotune(spec.Np, reps=2)[0] if self.autotune else self.plan.get_variant(spec.Np)
             if self.surrogate is None:
                 sw.graph_build(spec.Np, stage_seed, n_iter=spec.n_iter, w0=spec.w0, w1=spec.w1, c1=self.c1,
                                c2=self.c2, vmax=self.vmax)
@@ -193,7 +200,7 @@ class HierarchicalSearch:
             r = runs[int(np.argmax(bf[runs]))]
             winners.append(to_physical(pbx[r, bi[r]], run_boxes[r], self.q).tolist())
             wf.append(float(bf[r]))
-        res = StageResult(i, spec.Np, boxes.tolist(), winners, wf, time.perf_counter() - t0)
+        res = StageResult(i, spec.Np, boxes.tolist(), winners, wf, time.perf_counter() - t0, int(variant))
         self._save(res)
         return res
 
@@ -263,5 +270,17 @@ class HierarchicalSearch:
         last = self.results[-1]
         k = int(np.argmax(last.winner_f))
         return {"best": last.winners[k], "best_F_hat": last.winner_f[k],
+                "extrinsic": self.extrinsic(last.winners[k]),
                 "stages": [asdict(r) for r in self.results],
                 "seconds": sum(r.seconds for r in self.results)}
+
+    def extrinsic(self, theta) -> dict:
+        """Fully coherent amplitudes a (Eq. aandMN3) and (D_L, iota, psi, phi_c)
+        (App. B) at the intrinsic parameters theta, computed on the device."""
+        import torch
+        with torch.cuda.stream(self.plan.stream):
+            P = torch.tensor(np.asarray(theta, dtype=np.float64).reshape(1, 6), device="cuda")
+            F, a, ext = self.plan.amplitudes(P, 1)
+            F, a, ext = F.cpu().numpy(), a.cpu().numpy(), ext.cpu().numpy()
+        DL, iota, psi, phic = (float(x) for x in ext[0, 0])
+        return {"F": float(F[0]), "a": a[0, 0].tolist(), "D_L": DL, "iota": iota, "psi": psi, "phi_c": phic}

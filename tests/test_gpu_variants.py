@@ -1,0 +1,161 @@
+"""Launch variants of the fused kernel and the autotuner that picks among them.
+
+FS_MIXED: the grid and persistent forms (2 or 3 CTAs per SM) compute the same
+per-(span, particle) partial sums in the same order, so F must be bitwise
+equal across the four.  FS_FP64: the tile length changes how partial sums are
+grouped, so the three agree to rounding and each stays within 1e-9 of the
+oracle.  The autotuner records a valid choice per (N_p, edge kind) and the
+plan then uses it.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2407_10797_gb300 import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def tc_for(Mc, f, t):
+    m = Mc * S.MSUN_S
+    return t + 5.0 / 256.0 * m * (np.pi * m * f) ** (-8.0 / 3.0)
+
+
+@pytest.fixture(scope="module")
+def fst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_10797_gb300 import fstat
+    fstat.load()
+    return fstat
+
+
+def rel_err(F, Fref, Np):
+    ok = ~np.isnan(Fref)
+    assert np.array_equal(np.isnan(F), np.isnan(Fref))
+    return np.max(np.abs(F[ok] - Fref[ok]) / np.maximum(np.abs(Fref[ok]), 2.0 * Np), initial=0.0)
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    """100000 bins of the 2.5 yr grid (4 spans of 32768 bins, the last one
+    ragged), 53 particles (not a multiple of the 8 warps of a CTA) whose
+    bands start, end or lie inside the data; noise only."""
+    g = S.tiny_grid(n=100000, f_min=0.02)
+    fr = 0.02 + 50000 * g.df
+    P = S.draw_params(S.Prior(tc_lo=-0.2 * g.T_obs, tc_hi=1.2 * g.T_obs), 53, 21)
+    P[:, 1] = tc_for(P[:, 0], fr, P[:, 1] * 0.01)
+    psd = S.lisa_like_psd(g.freqs())
+    d = S.gaussian_noise(g, psd, 22)
+    return g, d, psd, P
+
+
+@pytest.mark.parametrize("Np", [1, 16, 256])
+def test_mixed_variants_bitwise_equal(fst, small_case, Np):
+    g, d, psd, P = small_case
+    plan = fst.Plan.from_grid(g, mode=fst.FS_MIXED)
+    plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
+    Pt = torch.from_numpy(P).cuda()
+    outs = []
+    for v in range(4):
+        plan.set_variant(v)
+        F, Fp = plan.fstat(Pt, Np)
+        outs.append((F.clone(), Fp.clone()))
+    torch.cuda.synchronize()
+    for F, Fp in outs[1:]:
+        assert torch.equal(F, outs[0][0]) and torch.equal(Fp, outs[0][1])
+    Fo, _ = O.fstat_batch(P, O.OracleModel.from_grid(g), d, psd, Np)
+    assert np.sum(Fo > 0) >= 10
+    assert rel_err(outs[0][0].cpu().numpy(), Fo, Np) <= 1e-4
+    plan.close()
+
+
+def test_mixed_persistent_repeats_and_empty_batches(fst, small_case):
+    """The persistent form resets its device-side item counter on every
+    launch: repeated calls, a batch with no in-band particle and a single
+    particle all come out right."""
+    g, d, psd, P = small_case
+    plan = fst.Plan.from_grid(g, mode=fst.FS_MIXED)
+    plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
+    plan.set_variant(2)
+    Pt = torch.from_numpy(P).cuda()
+    F0 = plan.fstat(Pt, 16)[0].clone()
+    far = P.copy()
+    far[:, 1] = -10.0 * g.T_obs           # merged long before the data: no in-band bin
+    Fz = plan.fstat(torch.from_numpy(far).cuda(), 16)[0].cpu().numpy()
+    assert np.all(Fz == 0.0)
+    F1 = plan.fstat(Pt, 16)[0]
+    assert torch.equal(F0, F1)
+    one = plan.fstat(Pt[5:6].contiguous(), 16)[0]
+    assert torch.equal(one, F0[5:6])
+    plan.close()
+
+
+@pytest.mark.parametrize("Np", [1, 256])
+def test_fp64_tile_variants_match_oracle(fst, small_case, Np):
+    g, d, psd, P = small_case
+    plan = fst.Plan.from_grid(g, mode=fst.FS_FP64)
+    plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
+    Pt = torch.from_numpy(P).cuda()
+    Fo, _ = O.fstat_batch(P, O.OracleModel.from_grid(g), d, psd, Np)
+    outs = []
+    for v in range(3):
+        plan.set_variant(v)
+        outs.append(plan.fstat(Pt, Np)[0].cpu().numpy())
+    for F in outs:
+        assert rel_err(F, Fo, Np) <= 1e-9
+        assert rel_err(F, outs[0], Np) <= 1e-12
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_autotuner_records_choice(fst, small_case, mode):
+    g, d, psd, P = small_case
+    plan = fst.Plan.from_grid(g, mode=mode)
+    plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
+    Pt = torch.from_numpy(P).cuda()
+    assert plan.get_variant(16) == 0
+    v, ms = plan.autotune(Pt, 16, reps=2)
+    assert 0 <= v < plan.n_variants and len(ms) == plan.n_variants
+    assert all(m > 0 for m in ms) and ms[v] == min(ms)
+    assert plan.get_variant(16) == v and plan.get_variant(64) == 0
+    assert plan.get_variant(16, global_edges=True) == 0
+    plan.set_variant_for(64, plan.n_variants - 1)
+    assert plan.get_variant(64) == plan.n_variants - 1
+    plan.set_variant(1)
+    assert plan.get_variant(16) == 1
+    plan.set_variant(-1)
+    assert plan.get_variant(16) == v
+    with pytest.raises(fst.FstatError):
+        plan.set_variant(plan.n_variants)
+    # the tuned plan still computes the same F as variant 0 (mixed: bitwise)
+    F = plan.fstat(Pt, 16)[0].cpu().numpy()
+    plan.set_variant(0)
+    F0 = plan.fstat(Pt, 16)[0].cpu().numpy()
+    if mode == fst.FS_MIXED:
+        assert np.array_equal(F, F0)
+    else:
+        assert rel_err(F, F0, 16) <= 1e-12
+    plan.close()
+
+
+def test_swarm_autotune_leaves_swarm_unchanged(fst, small_case):
+    g, d, psd, P = small_case
+    plan = fst.Plan.from_grid(g, mode=fst.FS_MIXED)
+    plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
+    box = np.zeros((2, 5, 2))
+    box[:, 0] = (10.0, 50.0)
+    box[:, 1] = (0.0, g.T_obs)
+    box[:, 2] = (-1.0, 1.0)
+    box[:, 3] = (0.0, 2.0 * np.pi)
+    box[:, 4] = (0.0, 0.1)
+    sw = fst.Swarm(plan, 2, 40, box)
+    sw.init(5)
+    before = [t.clone() for t in (sw.x, sw.v, sw.pbest_x, sw.pbest_f, sw.fit)]
+    v, ms = sw.autotune(64, reps=1)
+    assert 0 <= v < 4 and plan.get_variant(64) == v
+    after = (sw.x, sw.v, sw.pbest_x, sw.pbest_f, sw.fit)
+    for a, b in zip(before, after):
+        assert torch.equal(a, b)
+    plan.close()
