@@ -39,10 +39,35 @@ METRIC = "F-stat particle·bins/s on 1 GB300 (FP64 vs mixed at ≤1e-4 rel err);
 UNIT = "particle*bins/s"
 NP_LIST = (256, 64, 16, 1)
 
-# FP64 operations per in-band particle*bin of the fused kernel (algorithmic
-# count of the template + response + reduction arithmetic, FMA = 2, with each
-# of the two FP64 trig evaluations counted as 40).
-FP64_FLOP_PER_PBIN = 203.0
+# FP64 operations per in-band particle*bin of the fused kernel, FMA = 2.
+# Direct form (launch variants 0-2) and the anchored form's bin-by-bin
+# fallback: the template + response + reduction arithmetic of every bin, each
+# of its two FP64 trig evaluations counted as 40.  Anchored form (variants 3,
+# 4), per degree tier (antenna NG, Doppler NE and NQ): 60 + 4 NG + 2 (NE - 1)
+# + 2 NQ, i.e. d^2 1, quartic/quintic phase 4, orbital-phase offset 7, Doppler
+# polynomials 2 (NE - 1) + 2 NQ + 3, fixed-point phase correction 2,
+# exp(2 pi i Phi) from the table and its Taylor series 21, antenna pair
+# 4 NG, z = dw e^{i Phi} 6, seven sums 16 (integer phase steps and
+# conversions not counted).  Keys: the anchor modes of fs_plan_census.
+FP64_DIRECT_FLOP = 203.0
+FP64_TIER_FLOP = {1: 114.0, 2: FP64_DIRECT_FLOP, 3: 100.0, 4: 92.0}
+
+
+def census_sum(counts_by_np):
+    return [int(sum(c[m] for c in counts_by_np.values())) for m in range(5)]
+
+
+def flop_per_pbin(counts_by_np, table, direct):
+    """Mean operations per in-band particle*bin over the launches of a step,
+    from the per-mode bin counts of fs_plan_census (direct form: no anchors)."""
+    num = den = 0.0
+    for counts in counts_by_np.values():
+        n = sum(counts[1:])
+        if n == 0:
+            continue
+        num += sum(counts[m] * table[m] for m in table)
+        den += n
+    return num / den if den > 0 else direct
 
 
 def parse():
@@ -55,6 +80,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=None,
                     help="force one launch variant of the fused kernel instead of autotuning")
+    ap.add_argument("--search", choices=["fp64", "mixed", "surrogate"], default=None,
+                    help="time the full hierarchical search (4 stages) instead of the F-statistic step")
+    ap.add_argument("--seeds", type=int, nargs="+", default=[0],
+                    help="search mode: data/injection seeds (independent noise and injection per seed)")
+    ap.add_argument("--iters", type=int, default=2000, help="search mode: PSO iterations per stage")
     ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
                     help="one small evaluation for kernel profiling: paper grid, 64 particles, N_p = 16")
     return ap.parse_args()
@@ -275,8 +305,10 @@ def fp32_peak_tflops() -> float:
 # count, FMA = 2): orbital-phase offset 3, antenna pair G1, G2 as degree-6
 # polynomials 24, Doppler polynomial 17, phase assembly and reduction 5, SFU
 # sincos 3, z = dw e^{i Phi} 6, seven sums 16, fixed-point phase steps 6
-# (integer adds counted as one each).
+# (integer adds counted as one each).  Fallback bins (anchor mode 2) are FP64
+# work; the census reports how many there are (none on the paper workload).
 MIXED_FLOP_PER_PBIN = 80.0
+MIXED_TIER_FLOP = {1: MIXED_FLOP_PER_PBIN, 2: MIXED_FLOP_PER_PBIN}
 
 RUNS, NPART = 8, 40
 
@@ -344,6 +376,11 @@ class ModeRun:
             sw.iter.zero_()
             sw.graph_run(1)
             host["fit"][i].copy_(sw.fit, non_blocking=True)
+
+    def census(self, P_dev):
+        """Anchor-mode bin counts of the prior draw per N_p (outside any timing)."""
+        with self.torch.cuda.stream(self.stream):
+            return {Np: self.plan.census(P_dev, Np) for Np in NP_LIST}
 
     def fitness_at_x0(self):
         """F-hat of the prior draw at every N_p (fresh evaluation)."""
@@ -424,7 +461,7 @@ def run_gpu(args, world, rank, local):
     seed = 1000 + rank
 
     run64 = ModeRun(fstat, fstat.FS_FP64, g, d_dev, psd_dev, box, stream, seed,
-                    variant=None if args.variant is None else min(args.variant, 2))
+                    variant=args.variant)
     # in-band particle*bins of the prior draw the steps evaluate
     x0 = run64.x0.cpu().numpy().reshape(-1, 5)
     P0 = np.stack([search.to_physical(x, box) for x in x0])
@@ -432,6 +469,8 @@ def run_gpu(args, world, rank, local):
         bands = p0.bands(torch.from_numpy(P0).to(dev)).cpu().numpy()
     p0.close()
     inband = int(np.maximum(bands[:, 1] - bands[:, 0] + 1, 0).sum())
+    P0_dev = torch.from_numpy(P0).to(dev)
+    census64 = run64.census(P0_dev)
     B = RUNS * NPART
     pbins_per_step = inband * len(NP_LIST)
     total_pbins = allsum(world, float(pbins_per_step * args.steps))
@@ -462,7 +501,9 @@ def run_gpu(args, world, rank, local):
     run64.close()
 
     # ---- mixed mode on the same data and particles
-    runm = ModeRun(fstat, fstat.FS_MIXED, g, d_dev, psd_dev, box, stream, seed, variant=args.variant)
+    runm = ModeRun(fstat, fstat.FS_MIXED, g, d_dev, psd_dev, box, stream, seed,
+                   variant=None if args.variant is None else min(args.variant, 3))
+    censusm = runm.census(P0_dev)
     ms_m, prof_m, clocks_m = time_run(args, world, runm)
     value_m = total_pbins / (ms_m / 1e3)
     Fm = runm.fitness_at_x0()
@@ -476,11 +517,14 @@ def run_gpu(args, world, rank, local):
 
     # ---- roofline of the dominant kernels (average launch duration, live events)
     main_avg_ms = main_ms / max(main_n, 1)
-    achieved_tf = FP64_FLOP_PER_PBIN * inband / (main_avg_ms / 1e3) / 1e12
+    # flops per fused launch from the anchor-mode census of the same particles
+    flop64 = flop_per_pbin(census64, FP64_TIER_FLOP, FP64_DIRECT_FLOP)
+    achieved_tf = flop64 * inband / (main_avg_ms / 1e3) / 1e12
     peak_tf = fp64_peak_tflops()
     mm_ms, mm_n = prof_m["main"]
     mm_avg = mm_ms / max(mm_n, 1)
-    ach_m = MIXED_FLOP_PER_PBIN * inband / (mm_avg / 1e3) / 1e12
+    flopm = flop_per_pbin(censusm, MIXED_TIER_FLOP, MIXED_FLOP_PER_PBIN)
+    ach_m = flopm * inband / (mm_avg / 1e3) / 1e12
     peak_m = fp32_peak_tflops()
     if rank == 0:
         cpu = None
@@ -509,7 +553,7 @@ def run_gpu(args, world, rank, local):
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": achieved_tf / peak_tf, "traffic": None, "pipe": "fp64",
                          "peak_source": "unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                         "flop_per_pbin": FP64_FLOP_PER_PBIN},
+                         "flop_per_pbin": flop64, "census_bins_by_mode": census_sum(census64)},
             "clocks": clocks,
             "autotune": {"fp64": {str(k): v for k, v in tune64.items()},
                          "mixed": {str(k): v for k, v in tunem.items()}},
@@ -522,7 +566,8 @@ def run_gpu(args, world, rank, local):
                       "roofline": {"bound": "alu", "achieved": ach_m, "peak": peak_m, "unit": "TFLOP/s",
                                    "frac": ach_m / peak_m, "traffic": None, "pipe": "fp32",
                                    "peak_source": "unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
-                                   "flop_per_pbin": MIXED_FLOP_PER_PBIN},
+                                   "flop_per_pbin": flopm,
+                                   "census_bins_by_mode": census_sum(censusm)},
                       "clocks": clocks_m},
             "cpu_baseline": cpu,
         }
@@ -539,7 +584,7 @@ def run_profile_case(args):
     plan = fstat.Plan.from_grid(g, mode=mode)
     plan.set_data(torch.from_numpy(noise).cuda(), torch.from_numpy(psd).cuda())
     if args.variant is not None:
-        plan.set_variant(args.variant)
+        plan.set_variant(min(args.variant, plan.n_variants - 1))
     P_dev = torch.from_numpy(P[:64] if mode == fstat.FS_FP64 else P).cuda()
     for _ in range(2):
         F, _ = plan.fstat(P_dev, 16, want_parts=False)
@@ -549,10 +594,88 @@ def run_profile_case(args):
     plan.close()
 
 
+def sky_angle(lat1, lon1, lat2, lon2):
+    c = math.sin(lat1) * math.sin(lat2) + math.cos(lat1) * math.cos(lat2) * math.cos(lon1 - lon2)
+    return math.acos(max(-1.0, min(1.0, c)))
+
+
+def run_search(args):
+    """Full hierarchical search (N_p = 256 -> 64 -> 16 -> 1, 16 boxes x 8 runs x
+    40 particles per stage) on the paper grid, one run per seed: LISA-like
+    noise plus one injection at SNR 12.5 with its own parameters per seed.
+    Prints one JSON line with the wall time of each search and the errors of
+    the recovered parameters."""
+    import torch
+    from paper_2407_10797_gb300 import fstat
+    from paper_2407_10797_gb300 import search
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    mode = fstat.FS_FP64 if args.search == "fp64" else fstat.FS_MIXED
+    w = S.paper_workload()
+    g = w.grid
+    T = g.T_obs
+    psd = S.lisa_like_psd(g.freqs())
+    psd_dev = torch.from_numpy(psd).to(dev)
+    # search prior: the injection prior's t_c window (0.5 yr, the paper's stage-1 range) and M_c in [10, 50]
+    prior = S.Prior(Mc_lo=10.0, Mc_hi=50.0, tc_lo=0.9 * T, tc_hi=1.1 * T, e0_hi=0.1)
+    out = []
+    for seed in args.seeds:
+        stream = torch.cuda.Stream()
+        noise = S.gaussian_noise(g, psd, 7000 + seed)
+        inj = S.draw_params(S.Prior(Mc_lo=20.0, Mc_hi=40.0, tc_lo=0.95 * T, tc_hi=1.05 * T, e0_hi=0.1), 1,
+                            7000 + seed, stream=S.STREAM_INJECTION)[0]
+        with torch.cuda.stream(stream):
+            plan = fstat.Plan.from_grid(g, mode=mode, stream=stream)
+            d_dev = torch.from_numpy(noise).to(dev)
+            plan.set_data(d_dev, psd_dev)
+            h = torch.zeros_like(d_dev)
+            plan.add_signal(inj, extrinsic_amplitudes(S.INJ_IOTA, S.INJ_PSI, S.INJ_PHIC), h)
+            hh = float((4.0 * g.df * (h.abs() ** 2) / psd_dev).sum().item())
+            d_dev = d_dev + h * (w.snr / math.sqrt(hh))
+            del h
+            plan.set_data(d_dev, psd_dev)
+            plan.reserve(16 * 8 * 40, 256)
+            truth = torch.from_numpy(inj[None].copy()).to(dev)
+            F_truth = {Np: float(plan.fstat(truth, Np)[0][0].item()) / Np for Np in NP_LIST}
+        torch.cuda.synchronize()
+        hs = search.HierarchicalSearch(plan, prior, search.default_stages(args.iters), n_boxes=16, runs_per_box=8,
+                                       n_part=40, seed=seed,
+                                       surrogate=search.SurrogateSpec() if args.search == "surrogate" else None)
+        t0 = time.perf_counter()
+        res = hs.run()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        best = res["best"]
+        out.append({"seed": seed, "wall_s": wall, "stage_s": [st["seconds"] for st in res["stages"]],
+                    "stage_variant": [st["variant"] for st in res["stages"]],
+                    "best_F_hat": res["best_F_hat"], "F_hat_at_truth": F_truth,
+                    "truth": [float(x) for x in inj[:5]], "best": [float(x) for x in best[:5]],
+                    "Mc_rel_err": abs(best[0] - inj[0]) / inj[0], "tc_err_s": abs(best[1] - inj[1]),
+                    "sky_err_deg": math.degrees(sky_angle(best[2], best[3], inj[2], inj[3])),
+                    "e0_err": abs(best[4] - inj[4]), "extrinsic": res["extrinsic"]})
+        plan.close()
+    walls = [o["wall_s"] for o in out]
+    line = {"metric": "search wall time", "value": float(np.mean(walls)), "unit": "s", "higher_is_better": False,
+            "mode": args.search, "n_gpus": 1, "dtype": "f64" if mode == fstat.FS_FP64 else "f64 anchors + f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n_bins": g.n, "stages_N_p": list(NP_LIST), "boxes": 16, "runs_per_box": 8,
+                       "particles": 40, "iterations_per_stage": args.iters, "snr": w.snr,
+                       "prior": {"Mc": [prior.Mc_lo, prior.Mc_hi], "tc": [prior.tc_lo, prior.tc_hi],
+                                 "e0": [0.0, prior.e0_hi], "sky": "full sphere"},
+                       "surrogate": args.search == "surrogate"},
+            "exact_F_evaluations": 4 * 16 * 8 * 40 * args.iters,
+            "Mc_rel_err": [o["Mc_rel_err"] for o in out], "runs": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.search:
+        run_search(args)
         return
     world, rank, local = dist_init(args)
     if args.impl == "reference":

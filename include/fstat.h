@@ -270,9 +270,15 @@ FS_API fs_status fs_pso_step_screened(fs_plan* plan, const fs_swarm* swarm, fs_m
 
 /* Launch variants of the fused bin-loop kernel (the tile shape of the
  * ragged batch, Sec. IV's particle x frequency parallelism).
- *   FS_FP64 : 0 = 2048-bin tiles per (particle, tile) item, 1 = 1024, 2 = 4096.
- *             Tile edges change how partial sums are grouped, so F differs
- *             between variants by rounding only (relative 1e-15 per segment).
+ *   FS_FP64 : direct form, the whole template evaluated at every bin:
+ *             0 = 2048-bin tiles per (particle, tile) item, 1 = 1024, 2 = 4096;
+ *             anchored form, each 1024-bin tile expanded about its centre
+ *             bin (exact 64-bit fixed-point cubic phase plus FP64 higher
+ *             terms and polynomials, truncation bounded per tile, bin-by-bin
+ *             fallback): 3 = grid form, 4 = persistent form.  The direct
+ *             variants differ by rounding only (relative 1e-15); the
+ *             anchored ones by their truncation bounds as well (phase
+ *             1e-11 cycle per bin: relative 1e-10 or less on F).
  *   FS_MIXED: 0 = one CTA per (span of 32768 bins, 8 in-band particles), 2
  *             CTAs per SM; 1 = the same with 3 CTAs per SM; 2 = persistent
  *             kernel (one grid of SMs x resident CTAs whose warps take
@@ -281,7 +287,8 @@ FS_API fs_status fs_pso_step_screened(fs_plan* plan, const fs_swarm* swarm, fs_m
  *             the four.
  * Which variant a call uses: the forced one if fs_plan_set_variant gave one
  * (>= 0), else the one recorded for (N_p, edge kind) by fs_plan_autotune,
- * fs_pso_autotune or fs_plan_set_variant_for, else 0.
+ * fs_pso_autotune or fs_plan_set_variant_for, else the mode's default
+ * (FS_FP64: 4, FS_MIXED: 3).
  *
  * fs_plan_set_variant: force `variant` for every call, or -1 to return to
  * the per-(N_p, edge kind) choice.  FS_EINVAL if out of range. */
@@ -295,11 +302,23 @@ FS_API fs_status fs_plan_set_variant_for(fs_plan* plan, int N_p, int global_edge
 /* The variant a call with this N_p and edge kind would use now. */
 FS_API fs_status fs_plan_get_variant(fs_plan* plan, int N_p, int global_edges, int* variant);
 
+/* Census of the anchored kernels' evaluation modes for one batch: runs
+ * fs_fstat_batch once (F to plan scratch) with the variant the call resolves
+ * to, counting in-band particle*bins per tile mode, and returns them in
+ * counts[5]: [1] expansion with the wide degrees (FS_FP64) or the FP32
+ * polynomial body (FS_MIXED), [2] bin-by-bin fallback, [3] and [4] the mid and
+ * narrow degree tiers (FS_FP64 only), [0] unused.  All zero for the direct
+ * FS_FP64 variants (0-2), which have no anchors.  Synchronous; must not be
+ * called while the plan's stream is being captured.  For roofline accounting
+ * (the operation count per bin differs between modes and tiers). */
+FS_API fs_status fs_plan_census(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
+                                int N_p, int64_t* counts);
+
 /* Autotuner: time every variant on this batch (one untimed call, then `reps`
  * calls between CUDA events on the plan's stream, 1 <= reps <= 1000), record
  * the fastest for (N_p, edge kind) and return it in *variant_out (may be
  * NULL); ms_out (may be NULL) receives the mean ms per call of each variant
- * (4 entries in FS_MIXED, 3 in FS_FP64).  Synchronous; FS_EINVAL while the
+ * (4 entries in FS_MIXED, 5 in FS_FP64).  Synchronous; FS_EINVAL while the
  * plan's stream is being captured.  Arguments as in fs_fstat_batch; the F
  * values computed go to plan scratch, not to the caller. */
 FS_API fs_status fs_plan_autotune(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,

@@ -66,6 +66,8 @@ struct fs_plan {
     // launch variant of the fused kernel: forced (>= 0) or looked up per
     // (N_p, edge kind) among the autotuned choices, else variant 0
     int variant_forced;
+    unsigned long long* census;   // [5] device counters of fs_plan_census
+    int census_on;
     struct TuneRec {
         int Np, global, variant;
     };
@@ -105,18 +107,23 @@ namespace {
 
 constexpr int kKinds = 4;
 
-// Launch variants of the fused kernel.  FS_FP64: tile of 2048, 1024 or 4096
-// bins per (particle, tile) item.  FS_MIXED: grid form with 2 or 3 resident
-// CTAs per SM, persistent form with 2 or 3.
-int n_variants(int mode) { return mode == FS_MIXED ? 4 : 3; }
+// Launch variants of the fused kernel.  FS_FP64: direct form with a tile of
+// 2048, 1024 or 4096 bins per (particle, tile) item, anchored form (grid or
+// persistent).  FS_MIXED: grid form with 2 or 3 resident CTAs per SM,
+// persistent form with 2 or 3.
+int n_variants(int mode) { return mode == FS_MIXED ? 4 : 5; }
 
 int fp64_tile(int variant) { return variant == 1 ? 1024 : variant == 2 ? 4096 : fs::kTile; }
+
+// Untuned default: the anchored persistent form (FS_FP64), the persistent
+// form with 3 CTAs per SM (FS_MIXED).
+int default_variant(int mode) { return mode == FS_MIXED ? 3 : 4; }
 
 int resolve_variant(const fs_plan* p, int Np, int global) {
     if (p->variant_forced >= 0) return p->variant_forced;
     for (int i = 0; i < p->n_tuned; i++)
         if (p->tuned[i].Np == Np && p->tuned[i].global == global) return p->tuned[i].variant;
-    return 0;
+    return default_variant(p->mode);
 }
 
 void record_tuned(fs_plan* p, int Np, int global, int variant) {
@@ -293,6 +300,7 @@ fs_status fs_plan_destroy(fs_plan* p) {
     if (!p) return FS_OK;
     cudaStreamSynchronize(p->stream);
     free_workspace(p);
+    cudaFree(p->census);
     cudaFree(p->tab_base);
     cudaFree(p->edges_dev);
     cudaFree(p->one_param);
@@ -369,6 +377,31 @@ fs_status fs_amplitudes(fs_plan* p, const fs_params* params_dev, int B, const in
     return FS_OK;
 }
 
+fs_status fs_plan_census(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+                         int64_t* counts) {
+    g_err[0] = 0;
+    if (!p || !counts) return fail(FS_EINVAL, "fs_plan_census: NULL plan or counts");
+    for (int i = 0; i < 5; i++) counts[i] = 0;
+    if (B <= 0) return B == 0 ? FS_OK : fail(FS_EINVAL, "fs_plan_census: B = %d < 0", B);
+    cudaError_t e;
+    if (!p->census && (e = cudaMalloc(&p->census, 5 * sizeof(unsigned long long))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(census)");
+    fs_status st = ensure_workspace(p, B, Np);
+    if (st != FS_OK) return st;
+    if ((e = cudaMemsetAsync(p->census, 0, 5 * sizeof(unsigned long long), p->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync(census)");
+    p->census_on = 1;
+    st = fstat_impl(p, params_dev, B, edges_host, Np, p->pso_F, nullptr, nullptr);
+    p->census_on = 0;
+    if (st != FS_OK) return st;
+    unsigned long long h[5];
+    if ((e = cudaMemcpyAsync(h, p->census, sizeof(h), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+        return cuda_fail(e, "census read-back");
+    for (int i = 0; i < 5; i++) counts[i] = (int64_t)h[i];
+    return FS_OK;
+}
+
 namespace {
 fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
                      double* F_dev, double* F_part_dev, double* amp_dev) {
@@ -409,6 +442,7 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64
     sg.global = global;
     sg.edges = p->edges_dev;
     fs::Partials pa;
+    pa.census = p->census_on ? p->census : nullptr;
     pa.H = p->H;
     pa.T = p->T;
     pa.S = p->S;
@@ -416,7 +450,8 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64
     const bool mixed = p->mode == FS_MIXED;
     pa.rot32 = mixed ? p->rot32 : nullptr;
     const int variant = resolve_variant(p, Np, global);
-    pa.tile = mixed ? fs::mixed_span() : fp64_tile(variant);
+    const bool anchored = !mixed && variant >= 3;
+    pa.tile = mixed ? fs::mixed_span() : anchored ? fs::fp64a_span() : fp64_tile(variant);
     pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
     {
@@ -432,13 +467,18 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64
             if ((e = fs::launch_mixed_main(p->grid, p->tab, p->tab32, p->parts, B, sg, pa, variant,
                                            p->span_list, p->span_cnt, p->stream)) != cudaSuccess)
                 return cuda_fail(e, "mixed main launch");
+        } else if (anchored) {
+            if ((e = fs::launch_fp64a_main(p->grid, p->tab, p->parts, B, sg, pa, variant == 4, p->span_list,
+                                           p->span_cnt, p->stream)) != cudaSuccess)
+                return cuda_fail(e, "fp64 anchored main launch");
         } else if ((e = fs::launch_fp64_main(p->grid, p->tab, p->parts, B, sg, pa, p->stream)) != cudaSuccess) {
             return cuda_fail(e, "fp64 main launch");
         }
     }
     {
         ProfScope ps(p, 2);
-        if ((e = fs::launch_reduce(p->grid, p->parts, B, sg, pa, Fpart, F_dev, p->stream, amp_dev)) != cudaSuccess)
+        if ((e = fs::launch_reduce(p->grid, p->parts, B, sg, pa, Fpart, F_dev, p->stream, amp_dev,
+                                   mixed ? p->emax : nullptr)) != cudaSuccess)
             return cuda_fail(e, "reduce launch");
     }
     return FS_OK;

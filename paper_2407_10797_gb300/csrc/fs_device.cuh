@@ -69,4 +69,46 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
+// ---------------------------------------------------------------------------
+// 64-bit fixed-point phase (cycles mod 1 in units of 2^-64)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long to_fixed(double x) {
+    double y = x - floor(x);          // [0, 1)
+    double a = y * 4294967296.0;
+    double hi = floor(a);
+    double lo = (a - hi) * 4294967296.0;
+    return ((unsigned long long)hi << 32) + (unsigned long long)lo;
+}
+
+// Fixed-point fraction of a small value (|x| < 0.5 cycle) without the floor.
+__device__ __forceinline__ unsigned long long to_fixed_small(double x) {
+    if (!(fabs(x) < 0.5)) return to_fixed(x);
+    return (unsigned long long)__double2ll_rn(x * 18446744073709551616.0);
+}
+
+// Phase polynomial at integer offset d (exact modulo 2^64).
+__device__ __forceinline__ unsigned long long poly_fx(const unsigned long long c[4], long long d) {
+    unsigned long long u = (unsigned long long)d;
+    return c[0] + u * (c[1] + u * (c[2] + u * c[3]));
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers (host)
+// ---------------------------------------------------------------------------
+// Resident CTAs per SM times SMs for a persistent kernel, cached per device.
+template <typename K>
+inline int persistent_grid(K kernel, int threads, size_t smem, int variant_slot) {
+    static int cache[64][4];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int& v = cache[dev][variant_slot];
+    if (v > 0) return v;
+    int nsm = 0, per = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) return 0;
+    v = nsm * (per > 0 ? per : 1);
+    return v;
+}
+
+
 }  // namespace fs

@@ -391,7 +391,7 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
 // det <= 1e-12 P R with P = sum W F+^2, R = sum W Fx^2 recovered from K.
 // ---------------------------------------------------------------------------
 __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
-                              double* Fpart, double* amp) {
+                              double* Fpart, double* amp, const int* amp_exp) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= (int64_t)B * sg.Np) return;
@@ -462,6 +462,13 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
                 a4v[1] = rc.y * b1 + rc.x * b2;
                 a4v[2] = rc.x * b3 - rc.y * b4;
                 a4v[3] = rc.y * b3 + rc.x * b4;
+                if (amp_exp) {
+                    // sums from tables scaled by (2^-e/2, 2^-e) for (dw, W): a scales by 2^(e/2)
+                    int ex = *amp_exp;
+                    ex += ex & 1;
+                    const double sc = ldexp(1.0, -ex / 2);
+                    for (int i = 0; i < 4; i++) a4v[i] *= sc;
+                }
             }
             for (int i = 0; i < 4; i++) amp[wid * 4 + i] = a4v[i];
         }
@@ -509,12 +516,12 @@ __global__ void sum_segments_kernel(const Particle* __restrict__ parts, int B, i
 }
 
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
-                          double* Fpart, double* F, cudaStream_t s, double* amp) {
+                          double* Fpart, double* F, cudaStream_t s, double* amp, const int* amp_exp) {
     if (B <= 0) return cudaSuccess;
     const int threads = 256;
     int64_t warps = (int64_t)B * sg.Np;
     int64_t blocks = (warps * 32 + threads - 1) / threads;
-    reduce_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp);
+    reduce_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp, amp_exp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int64_t blocks2 = ((int64_t)B * 32 + threads - 1) / threads;

@@ -50,6 +50,7 @@ struct Partials {
     float2* rot32; // the same rotations in FP32 (mixed mode), or NULL
     int ntiles;   // number of tiles (slots of H and T per particle)
     int tile;     // bins per tile
+    unsigned long long* census = nullptr;   // [5] in-band bins per anchor mode (anchored kernels), or NULL
 };
 
 // Record an error message for fs_last_error() and return st.
@@ -65,7 +66,16 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
                              const Partials& pa, cudaStream_t s);
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
                           double* Fpart, double* F, cudaStream_t s,
-                          double* amp = nullptr);
+                          double* amp = nullptr, const int* amp_exp = nullptr);
+// In-band particle lists per span of span_len bins (list [nspans][B], cnt
+// [nspans]); with offsets, also the item prefix cnt[nspans..2 nspans] and the
+// persistent-kernel counters cnt[2 nspans + 1 ..].
+cudaError_t launch_span_lists(const Particle* parts, int B, const Segs& sg, int nspans, int span_len, int* list,
+                              int* cnt, bool offsets, cudaStream_t s);
+// FS_FP64 anchored form (spans of fp64a_span() bins; partial slots per span).
+int fp64a_span();
+cudaError_t launch_fp64a_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
+                              const Partials& pa, bool persistent, int* list, int* cnt, cudaStream_t s);
 cudaError_t launch_extrinsic(int64_t n, const double* amp, double* ext, cudaStream_t s);
 cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s);
 // variant 0: 2 CTAs/SM (up to 128 registers), 1: 3 CTAs/SM (up to 80 registers)

@@ -40,26 +40,6 @@ struct Anchor {
     int mode;                  // 0: no in-band bin, 1: polynomial, 2: bin-by-bin FP64
 };
 
-__device__ __forceinline__ unsigned long long to_fixed(double x) {
-    double y = x - floor(x);          // [0, 1)
-    double a = y * 4294967296.0;
-    double hi = floor(a);
-    double lo = (a - hi) * 4294967296.0;
-    return ((unsigned long long)hi << 32) + (unsigned long long)lo;
-}
-
-// Fixed-point fraction of a small value (|x| < 0.5 cycle) without the floor.
-__device__ __forceinline__ unsigned long long to_fixed_small(double x) {
-    if (!(fabs(x) < 0.5)) return to_fixed(x);
-    return (unsigned long long)__double2ll_rn(x * 18446744073709551616.0);
-}
-
-// Phase polynomial at integer offset d (exact modulo 2^64).
-__device__ __forceinline__ unsigned long long poly_fx(const unsigned long long c[4], long long d) {
-    unsigned long long u = (unsigned long long)d;
-    return c[0] + u * (c[1] + u * (c[2] + u * c[3]));
-}
-
 // Bin-by-bin FP64 evaluation for tiles where the anchor expansion is not
 // valid; returns the phase mod 1 and the rotated antenna pair (G1, G2).
 __device__ __noinline__ void eval_bin_fallback(const Particle& P, const Tables& tb, int64_t k, double alpha0,
@@ -256,12 +236,12 @@ __device__ __forceinline__ void mixed_bin(unsigned long long Fv, float d, float4
 // (counted on ctl[0]) also writes the exclusive prefix off[s] = sum of cnt
 // over spans before s, off[nspans] = the number of work items, and resets the
 // persistent kernel's item counter ctl[1] and ctl[0] itself to zero.
-__global__ void span_lists_kernel(const Particle* __restrict__ parts, int B, Segs sg, int nspans, int* list,
-                                  int* cnt, int* off, int* ctl) {
+__global__ void span_lists_kernel(const Particle* __restrict__ parts, int B, Segs sg, int nspans, int span_len,
+                                  int* list, int* cnt, int* off, int* ctl) {
     const int lane = threadIdx.x & 31;
     const int span = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (span < nspans) {   // warp-uniform
-        const int64_t lo = (int64_t)span * kSpanMix, hi = lo + kSpanMix - 1;
+        const int64_t lo = (int64_t)span * span_len, hi = lo + span_len - 1;
         int n = 0;
         for (int b0 = 0; b0 < B; b0 += 32) {
             const int b = b0 + lane;
@@ -304,6 +284,15 @@ __global__ void span_lists_kernel(const Particle* __restrict__ parts, int B, Seg
     }
 }
 
+cudaError_t launch_span_lists(const Particle* parts, int B, const Segs& sg, int nspans, int span_len, int* list,
+                              int* cnt, bool offsets, cudaStream_t s) {
+    int* off = cnt + nspans;
+    int* ctl = cnt + 2 * nspans + 1;
+    span_lists_kernel<<<(unsigned)((nspans * 32 + 255) / 256), 256, 0, s>>>(parts, B, sg, nspans, span_len, list,
+                                                                             cnt, offsets ? off : nullptr, ctl);
+    return cudaGetLastError();
+}
+
 // One work item: particle b over span `span`, by one warp.  Phase A: one
 // anchor per lane (tile `lane` of the span) into the warp's 32 anchor slots;
 // phase B: the warp walks the particle's tiles of the span.  Partial sums
@@ -320,6 +309,7 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
         if (lo < sv.lo) lo = sv.lo;
         if (hi > sv.hi + 1) hi = sv.hi + 1;
         make_anchor(g, tb, P, span_lo, lo, hi, anc[lane]);
+        if (pa.census && lo < hi) atomicAdd(&pa.census[anc[lane].mode], (unsigned long long)(hi - lo));
     }
     __syncwarp();
 
@@ -504,24 +494,6 @@ mixed_persistent_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const
     }
 }
 
-namespace {
-
-// Resident CTAs per SM times SMs for a persistent kernel, cached per device.
-template <typename K>
-int persistent_grid(K kernel, size_t smem, int variant_slot) {
-    static int cache[64][2];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    int& v = cache[dev][variant_slot];
-    if (v > 0) return v;
-    int nsm = 0, per = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kWarpsMix * 32, smem) != cudaSuccess) return 0;
-    v = nsm * (per > 0 ? per : 1);
-    return v;
-}
-
-}  // namespace
 
 cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
                               const Segs& sg, const Partials& pa, int variant, int* list, int* cnt,
@@ -532,14 +504,12 @@ cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32,
     int* off = cnt + nspans;            // [nspans + 1]
     int* ctl = cnt + 2 * nspans + 1;    // [3]: CTAs done, next item, spare
     const size_t smem = sizeof(Anchor) * kWarpsMix * 32;
-    span_lists_kernel<<<(unsigned)((nspans * 32 + 255) / 256), 256, 0, s>>>(parts, B, sg, nspans, list, cnt,
-                                                                             persistent ? off : nullptr, ctl);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_span_lists(parts, B, sg, nspans, kSpanMix, list, cnt, persistent, s);
     if (e != cudaSuccess) return e;
     if (persistent) {
         const bool three = variant == 3;
-        const int grid = three ? persistent_grid(mixed_persistent_kernel<3>, smem, 1)
-                               : persistent_grid(mixed_persistent_kernel<2>, smem, 0);
+        const int grid = three ? persistent_grid(mixed_persistent_kernel<3>, kWarpsMix * 32, smem, 1)
+                               : persistent_grid(mixed_persistent_kernel<2>, kWarpsMix * 32, smem, 0);
         if (grid <= 0) return cudaErrorInvalidConfiguration;
         if (three)
             mixed_persistent_kernel<3><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, off,

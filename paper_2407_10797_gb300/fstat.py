@@ -71,6 +71,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_plan_set_variant.argtypes = [_vp, C.c_int]
         L.fs_plan_set_variant_for.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
         L.fs_plan_get_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
+        L.fs_plan_census.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int64)]
         L.fs_plan_autotune.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int,
                                        C.POINTER(C.c_int), C.POINTER(C.c_float)]
         _sw = C.POINTER(fs_swarm)
@@ -102,7 +103,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                      "fs_fstat_batch", "fs_amplitudes", "fs_add_signal", "fs_constants", "fs_particle_bands",
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
                      "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
-                     "fs_plan_autotune", "fs_pso_autotune", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
+                     "fs_plan_autotune", "fs_pso_autotune", "fs_plan_census", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
                      "fs_pso_graph_build", "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
                      "fs_mlp_destroy", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
                      "fs_mlp_loss_grad", "fs_mlp_train", "fs_pso_step_screened"):
@@ -251,7 +252,7 @@ class Plan:
 
     @property
     def n_variants(self) -> int:
-        return 4 if self.mode == FS_MIXED else 3
+        return 4 if self.mode == FS_MIXED else 5
 
     def autotune(self, params, Np: int, edges=None, reps: int = 3):
         """Time every launch variant on this batch and keep the fastest for
@@ -259,10 +260,20 @@ class Plan:
         import torch
         arr, e = _edges_arg(edges, Np)
         v = C.c_int()
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 8)()
         _check(self._L.fs_plan_autotune(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
                                         e, int(Np), int(reps), C.byref(v), ms))
         return v.value, [ms[i] for i in range(self.n_variants)]
+
+    def census(self, params, Np: int, edges=None) -> list[int]:
+        """In-band particle*bins per anchor mode (fs_plan_census): [unused, wide or
+        FP32 body, bin-by-bin fallback, mid tier, narrow tier]."""
+        import torch
+        arr, e = _edges_arg(edges, Np)
+        out = (C.c_int64 * 5)()
+        _check(self._L.fs_plan_census(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
+                                      e, int(Np), out))
+        return [int(out[i]) for i in range(5)]
 
     def set_profiling(self, enable: bool):
         _check(self._L.fs_plan_set_profiling(self._h, 1 if enable else 0))
@@ -364,7 +375,7 @@ class Swarm:
         """fs_pso_autotune: pick the plan's fastest variant on the current positions."""
         arr, e = _edges_arg(edges, Np)
         v = C.c_int()
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 8)()
         _check(load().fs_pso_autotune(self.plan._h, C.byref(self.c), e, int(Np), int(reps), C.byref(v), ms))
         return v.value, [ms[i] for i in range(self.plan.n_variants)]
 
