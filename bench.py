@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--seeds", type=int, nargs="+", default=[0],
                     help="search mode: data/injection seeds (independent noise and injection per seed)")
     ap.add_argument("--iters", type=int, default=2000, help="search mode: PSO iterations per stage")
+    ap.add_argument("--stages", choices=["default", "paper"], default="default",
+                    help="search mode: N_p = 256/64/16/1 (default) or the paper's 16/16/1 schedule")
+    ap.add_argument("--snr", type=float, default=None, help="search mode: injection SNR (default: the workload's)")
     ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
                     help="one small evaluation for kernel profiling: paper grid, 64 particles, N_p = 16")
     return ap.parse_args()
@@ -619,6 +622,9 @@ def run_search(args):
     psd_dev = torch.from_numpy(psd).to(dev)
     # search prior: the injection prior's t_c window (0.5 yr, the paper's stage-1 range) and M_c in [10, 50]
     prior = S.Prior(Mc_lo=10.0, Mc_hi=50.0, tc_lo=0.9 * T, tc_hi=1.1 * T, e0_hi=0.1)
+    snr = w.snr if args.snr is None else args.snr
+    stages = search.default_stages(args.iters) if args.stages == "default" else search.paper_stages(args.iters)
+    np_list = [st.Np for st in stages]
     out = []
     for seed in args.seeds:
         stream = torch.cuda.Stream()
@@ -632,14 +638,14 @@ def run_search(args):
             h = torch.zeros_like(d_dev)
             plan.add_signal(inj, extrinsic_amplitudes(S.INJ_IOTA, S.INJ_PSI, S.INJ_PHIC), h)
             hh = float((4.0 * g.df * (h.abs() ** 2) / psd_dev).sum().item())
-            d_dev = d_dev + h * (w.snr / math.sqrt(hh))
+            d_dev = d_dev + h * (snr / math.sqrt(hh))
             del h
             plan.set_data(d_dev, psd_dev)
             plan.reserve(16 * 8 * 40, 256)
             truth = torch.from_numpy(inj[None].copy()).to(dev)
-            F_truth = {Np: float(plan.fstat(truth, Np)[0][0].item()) / Np for Np in NP_LIST}
+            F_truth = {Np: float(plan.fstat(truth, Np)[0][0].item()) / Np for Np in sorted(set(np_list))}
         torch.cuda.synchronize()
-        hs = search.HierarchicalSearch(plan, prior, search.default_stages(args.iters), n_boxes=16, runs_per_box=8,
+        hs = search.HierarchicalSearch(plan, prior, stages, n_boxes=16, runs_per_box=8,
                                        n_part=40, seed=seed,
                                        surrogate=search.SurrogateSpec() if args.search == "surrogate" else None)
         t0 = time.perf_counter()
@@ -647,7 +653,17 @@ def run_search(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         best = res["best"]
-        out.append({"seed": seed, "wall_s": wall, "stage_s": [st["seconds"] for st in res["stages"]],
+        per_stage = []
+        for st in res["stages"]:
+            wv = np.array(st["winners"])
+            k = int(np.argmax(st["winner_f"]))
+            near = int(np.argmin(np.abs(wv[:, 0] - inj[0]) / inj[0] + np.abs(wv[:, 1] - inj[1]) / (0.01 * S.YEAR_S)))
+            per_stage.append({"N_p": st["Np"], "best_F_hat": st["winner_f"][k],
+                              "best_Mc_rel_err": abs(wv[k, 0] - inj[0]) / inj[0], "best_tc_err_s": abs(wv[k, 1] - inj[1]),
+                              "nearest_box_Mc_rel_err": abs(wv[near, 0] - inj[0]) / inj[0],
+                              "nearest_box_tc_err_s": abs(wv[near, 1] - inj[1]),
+                              "nearest_box_F_hat": st["winner_f"][near]})
+        out.append({"stages": per_stage, "seed": seed, "wall_s": wall, "stage_s": [st["seconds"] for st in res["stages"]],
                     "stage_variant": [st["variant"] for st in res["stages"]],
                     "best_F_hat": res["best_F_hat"], "F_hat_at_truth": F_truth,
                     "truth": [float(x) for x in inj[:5]], "best": [float(x) for x in best[:5]],
@@ -659,12 +675,12 @@ def run_search(args):
     line = {"metric": "search wall time", "value": float(np.mean(walls)), "unit": "s", "higher_is_better": False,
             "mode": args.search, "n_gpus": 1, "dtype": "f64" if mode == fstat.FS_FP64 else "f64 anchors + f32",
             "data": "synthetic",
-            "config": {"workload": w.name, "n_bins": g.n, "stages_N_p": list(NP_LIST), "boxes": 16, "runs_per_box": 8,
-                       "particles": 40, "iterations_per_stage": args.iters, "snr": w.snr,
+            "config": {"workload": w.name, "n_bins": g.n, "stages_N_p": np_list, "schedule": args.stages, "boxes": 16,
+                       "runs_per_box": 8, "particles": 40, "iterations_per_stage": args.iters, "snr": snr,
                        "prior": {"Mc": [prior.Mc_lo, prior.Mc_hi], "tc": [prior.tc_lo, prior.tc_hi],
                                  "e0": [0.0, prior.e0_hi], "sky": "full sphere"},
                        "surrogate": args.search == "surrogate"},
-            "exact_F_evaluations": 4 * 16 * 8 * 40 * args.iters,
+            "exact_F_evaluations": len(stages) * 16 * 8 * 40 * args.iters,
             "Mc_rel_err": [o["Mc_rel_err"] for o in out], "runs": out}
     print(json.dumps(line), flush=True)
 

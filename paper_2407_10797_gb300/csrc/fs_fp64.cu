@@ -390,11 +390,15 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
 // The degenerate-segment rule is stated in the (F+, Fx) basis:
 // det <= 1e-12 P R with P = sum W F+^2, R = sum W Fx^2 recovered from K.
 // ---------------------------------------------------------------------------
+// G lanes per (particle, segment): G = 1 when a segment meets only a few
+// tiles (large N_p), up to a warp when it meets hundreds.  G depends only on
+// (n_bins, N_p, tile), so a plan's results stay bitwise reproducible.
+template <int G>
 __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
                               double* Fpart, double* amp, const int* amp_exp) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wid >= (int64_t)B * sg.Np) return;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if (wid >= (int64_t)B * sg.Np) return;   // uniform within a group
     const int b = (int)(wid / sg.Np);
     const int p = (int)(wid % sg.Np);
     const Particle& P = parts[b];
@@ -418,7 +422,7 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
     const int64_t nb = s1 > s0 ? s1 - s0 : 0;
     if (nb > 0) {
         const int64_t t0 = s0 / pa.tile, t1 = (s1 - 1) / pa.tile;
-        for (int64_t t = t0 + lane; t <= t1; t += 32) {
+        for (int64_t t = t0 + lane; t <= t1; t += G) {
             int64_t tlo = t * pa.tile, thi = tlo + pa.tile - 1;
             if (tlo < sv.lo) tlo = sv.lo;
             if (thi > sv.hi) thi = sv.hi;
@@ -431,8 +435,13 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
             for (int c = 0; c < 7; c++) acc[c] += src[c];
         }
     }
+    if (G > 1) {
+        // groups are aligned G-lane blocks of a warp whose members all reach this point
+        const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1)));
 #pragma unroll
-    for (int c = 0; c < 7; c++) acc[c] = warp_sum(acc[c]);
+        for (int c = 0; c < 7; c++)
+            for (int o = G / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(mask, acc[c], o);
+    }
     if (lane == 0) {
         double X1r = acc[0], X1i = acc[1], X2r = acc[2], X2i = acc[3];
         double K11 = acc[4], K12 = acc[5], K22 = acc[6];
@@ -519,9 +528,23 @@ cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Seg
                           double* Fpart, double* F, cudaStream_t s, double* amp, const int* amp_exp) {
     if (B <= 0) return cudaSuccess;
     const int threads = 256;
-    int64_t warps = (int64_t)B * sg.Np;
-    int64_t blocks = (warps * 32 + threads - 1) / threads;
-    reduce_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp, amp_exp);
+    const int64_t segs = (int64_t)B * sg.Np;
+    // about two tiles per lane for a segment spanning the whole grid
+    const int64_t tiles = (g.n + (int64_t)sg.Np * pa.tile - 1) / ((int64_t)sg.Np * pa.tile);
+    int G = 1;
+    while (G < 32 && 2 * G < tiles) G *= 2;
+    const int64_t blocks = (segs * G + threads - 1) / threads;
+#define FS_REDUCE(G_)                                                                                   \
+    reduce_kernel<G_><<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp, amp_exp)
+    switch (G) {
+        case 1: FS_REDUCE(1); break;
+        case 2: FS_REDUCE(2); break;
+        case 4: FS_REDUCE(4); break;
+        case 8: FS_REDUCE(8); break;
+        case 16: FS_REDUCE(16); break;
+        default: FS_REDUCE(32); break;
+    }
+#undef FS_REDUCE
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int64_t blocks2 = ((int64_t)B * 32 + threads - 1) / threads;

@@ -229,6 +229,81 @@ __device__ __forceinline__ void mixed_bin(unsigned long long Fv, float d, float4
     acc[6] = fmaf(tw.z * G2, G2, acc[6]);
 }
 
+// Two FP32 lanes in one 64-bit register: the packed f32x2 arithmetic of
+// sm_100-class GPUs does the same operation on both halves in one
+// instruction, each half rounded as its scalar counterpart.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Coefficients of one single-segment piece, each duplicated into both halves;
+// the Doppler ones negated so that one fused chain gives minus the offset.
+struct PairCoeffs {
+    f32x2 w1, w2;
+    f32x2 ne[5], nq[4];
+    f32x2 g1[7], g2[7];
+};
+
+// Bins k (low half) and k + 32 (high half) of a polynomial piece: the same
+// operations as mixed_bin on both, sums into the packed accumulators.
+__device__ __forceinline__ void mixed_pair(unsigned long long Fa, unsigned long long Fb, float d, float4 ta,
+                                           float4 tb, const PairCoeffs& C, f32x2 acc[7]) {
+    const f32x2 D = pk2(d, d + 32.f);
+    const f32x2 DA = mul2(fma2(C.w2, D, C.w1), D);
+    f32x2 G1 = C.g1[6], G2 = C.g2[6];
+#pragma unroll
+    for (int n = 5; n >= 0; n--) {
+        G1 = fma2(G1, DA, C.g1[n]);
+        G2 = fma2(G2, DA, C.g2[n]);
+    }
+    f32x2 E = C.ne[4];
+#pragma unroll
+    for (int n = 3; n >= 0; n--) E = fma2(E, DA, C.ne[n]);
+    f32x2 Q = C.nq[3];
+#pragma unroll
+    for (int n = 2; n >= 0; n--) Q = fma2(Q, DA, C.nq[n]);
+    const f32x2 ndop = fma2(DA, E, mul2(D, Q));
+    const f32x2 ph = fma2(pk2((float)(int)(Fa >> 32), (float)(int)(Fb >> 32)), pk2(2.3283064365386963e-10f,
+                          2.3283064365386963e-10f), ndop);
+    float pa, pb;
+    up2(ph, pa, pb);
+    pa -= rintf(pa);
+    pb -= rintf(pb);
+    float sa, ca, sb, cb;
+    __sincosf(6.283185307179586f * pa, &sa, &ca);
+    __sincosf(6.283185307179586f * pb, &sb, &cb);
+    const f32x2 CS = pk2(ca, cb), SN = pk2(sa, sb);
+    // table entry (dw_re, dw_im, W, -dw_im)
+    const f32x2 X = pk2(ta.x, tb.x), Y = pk2(ta.y, tb.y), Wt = pk2(ta.z, tb.z), YN = pk2(ta.w, tb.w);
+    const f32x2 zr = fma2(X, CS, mul2(YN, SN));
+    const f32x2 zi = fma2(X, SN, mul2(Y, CS));
+    acc[0] = fma2(G1, zr, acc[0]);
+    acc[1] = fma2(G1, zi, acc[1]);
+    acc[2] = fma2(G2, zr, acc[2]);
+    acc[3] = fma2(G2, zi, acc[3]);
+    const f32x2 wg = mul2(Wt, G1);
+    acc[4] = fma2(wg, G1, acc[4]);
+    acc[5] = fma2(wg, G2, acc[5]);
+    acc[6] = fma2(mul2(Wt, G2), G2, acc[6]);
+}
+
 // In-band particles of every span, in increasing particle order: one warp per
 // span.  list[span * B + j] is the j-th particle whose band meets the span and
 // cnt[span] their number, so no warp of the fused kernel idles on a particle
@@ -367,16 +442,38 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
                                    D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
                 float d = (float)(k0 - A.ja);
                 int k = k0;
-                // two bins per lane per iteration (k and k + 32): two independent chains
-                for (; k + 32 < pa_hi; k += 64, d += 64.f) {
-                    const float4 twa = tw_span[k];
-                    const float4 twb = tw_span[k + 32];
-                    const unsigned long long Fa = F, Fb = F + D1;
-                    F = Fb + D1 + D2;
-                    D1 += 2ull * D2 + D3;
-                    D2 += 2ull * D3;
-                    mixed_bin(Fa, d, twa, w1, w2, g1, g2, e, q, acc);
-                    mixed_bin(Fb, d + 32.f, twb, w1, w2, g1, g2, e, q, acc);
+                if (k + 32 < pa_hi) {
+                    // two bins per lane per iteration (k and k + 32), packed into f32x2 halves
+                    PairCoeffs C;
+                    C.w1 = pk2(w1, w1);
+                    C.w2 = pk2(w2, w2);
+#pragma unroll
+                    for (int n = 0; n < 5; n++) C.ne[n] = pk2(-e[n], -e[n]);
+#pragma unroll
+                    for (int n = 0; n < 4; n++) C.nq[n] = pk2(-q[n], -q[n]);
+#pragma unroll
+                    for (int n = 0; n < 7; n++) {
+                        C.g1[n] = pk2(g1[n], g1[n]);
+                        C.g2[n] = pk2(g2[n], g2[n]);
+                    }
+                    f32x2 acc2[7];
+#pragma unroll
+                    for (int c = 0; c < 7; c++) acc2[c] = 0ull;   // (+0.0f, +0.0f)
+                    for (; k + 32 < pa_hi; k += 64, d += 64.f) {
+                        const float4 twa = tw_span[k];
+                        const float4 twb = tw_span[k + 32];
+                        const unsigned long long Fa = F, Fb = F + D1;
+                        F = Fb + D1 + D2;
+                        D1 += 2ull * D2 + D3;
+                        D2 += 2ull * D3;
+                        mixed_pair(Fa, Fb, d, twa, twb, C, acc2);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 7; c++) {
+                        float lo2, hi2;
+                        up2(acc2[c], lo2, hi2);
+                        acc[c] += lo2 + hi2;
+                    }
                 }
                 if (k < pa_hi) mixed_bin(F, d, tw_span[k], w1, w2, g1, g2, e, q, acc);
                 pa_lo = pa_hi;
@@ -552,7 +649,8 @@ __global__ void tables32_kernel(Grid g, Tables t, const int* emax, float4* t32) 
     int e = *emax;
     e += e & 1;                       // even, so that the data scale is an exact power of two too
     const double sW = ldexp(1.0, -e), sd = ldexp(1.0, -e / 2);
-    t32[k] = make_float4((float)(t.dwr[k] * sd), (float)(t.dwi[k] * sd), (float)(t.W[k] * sW), 0.f);
+    const float di = (float)(t.dwi[k] * sd);
+    t32[k] = make_float4((float)(t.dwr[k] * sd), di, (float)(t.W[k] * sW), -di);
 }
 
 cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s) {

@@ -56,6 +56,18 @@ def default_stages(n_iter: int = 2000) -> list[StageSpec]:
     ]
 
 
+def paper_stages(n_iter: int = 2000) -> list[StageSpec]:
+    """The paper's three stages (Sec. III.B): N_seg = 16 over t_c sub-ranges;
+    N_seg = 16 in boxes of 0.01 yr x 0.6 Msun around the stage-1 winners;
+    N_seg = 1 in a box of 0.004 yr, 0.3 Msun, 0.4 rad, 0.4 rad, 0.006 around
+    the best winner and its theta -> pi - theta mirror."""
+    return [
+        StageSpec(16, n_iter, "split_tc"),
+        StageSpec(16, n_iter, "around", (0.6, 0.01 * YEAR, None, None, None)),
+        StageSpec(1, n_iter, "around_best_mirror", (0.3, 0.004 * YEAR, 0.4, 0.4, 0.006)),
+    ]
+
+
 def prior_box(prior: S.Prior) -> np.ndarray:
     return np.array([[prior.Mc_lo, prior.Mc_hi], [prior.tc_lo, prior.tc_hi], [-1.0, 1.0], [0.0, 2.0 * np.pi],
                      [0.0, prior.e0_hi]])
