@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--stages", choices=["default", "paper"], default="default",
                     help="search mode: N_p = 256/64/16/1 (default) or the paper's 16/16/1 schedule")
     ap.add_argument("--snr", type=float, default=None, help="search mode: injection SNR (default: the workload's)")
+    ap.add_argument("--prior", choices=["full", "targeted"], default="full",
+                    help="search mode: the full prior (M_c 10-50 Msun, 0.5 yr of t_c) or a follow-up box "
+                         "(M_c +-0.5 Msun, t_c +-0.005 yr around the injection; full sky and e0)")
     ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
                     help="one small evaluation for kernel profiling: paper grid, 64 particles, N_p = 16")
     return ap.parse_args()
@@ -631,6 +634,13 @@ def run_search(args):
         noise = S.gaussian_noise(g, psd, 7000 + seed)
         inj = S.draw_params(S.Prior(Mc_lo=20.0, Mc_hi=40.0, tc_lo=0.95 * T, tc_hi=1.05 * T, e0_hi=0.1), 1,
                             7000 + seed, stream=S.STREAM_INJECTION)[0]
+        if args.prior == "targeted":
+            # box centred on the injection shifted by a seeded offset (the search does not start at the truth)
+            u = S.uniforms(7000 + seed, 0x54475444, 2)
+            c_mc = inj[0] + 0.5 * (u[0] - 0.5)
+            c_tc = inj[1] + 0.005 * S.YEAR_S * (u[1] - 0.5)
+            prior = S.Prior(Mc_lo=c_mc - 0.5, Mc_hi=c_mc + 0.5, tc_lo=c_tc - 0.005 * S.YEAR_S,
+                            tc_hi=c_tc + 0.005 * S.YEAR_S, e0_hi=0.1)
         with torch.cuda.stream(stream):
             plan = fstat.Plan.from_grid(g, mode=mode, stream=stream)
             d_dev = torch.from_numpy(noise).to(dev)
@@ -675,7 +685,8 @@ def run_search(args):
     line = {"metric": "search wall time", "value": float(np.mean(walls)), "unit": "s", "higher_is_better": False,
             "mode": args.search, "n_gpus": 1, "dtype": "f64" if mode == fstat.FS_FP64 else "f64 anchors + f32",
             "data": "synthetic",
-            "config": {"workload": w.name, "n_bins": g.n, "stages_N_p": np_list, "schedule": args.stages, "boxes": 16,
+            "config": {"workload": w.name, "n_bins": g.n, "stages_N_p": np_list, "schedule": args.stages,
+                       "prior_kind": args.prior, "boxes": 16,
                        "runs_per_box": 8, "particles": 40, "iterations_per_stage": args.iters, "snr": snr,
                        "prior": {"Mc": [prior.Mc_lo, prior.Mc_hi], "tc": [prior.tc_lo, prior.tc_hi],
                                  "e0": [0.0, prior.e0_hi], "sky": "full sphere"},

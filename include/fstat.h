@@ -258,15 +258,49 @@ FS_API fs_status fs_mlp_train(fs_mlp* mlp, const float* X_dev, const float* t_de
 /* fs_pso_step with surrogate screening: after the personal-best update, n_cand
  * candidate moves are drawn per particle (candidate c uses the Philox counter
  * (k, particle, dim, run | c << 20), so candidate 0 is the fs_pso_step move),
- * the network predicts their fitness, and each particle takes the candidate
+ * a network predicts their fitness, and each particle takes the candidate
  * with the highest prediction (lowest index among equals; candidates outside
- * [0,1]^5 rank last).  1 <= n_cand <= 64; R * n_part * n_cand candidates go
- * through the network in chunks of its max_batch.  The network must run on the
- * plan's stream.  Asynchronous; allocates its candidate buffers in the plan
- * (synchronously) when they are too small. */
-FS_API fs_status fs_pso_step_screened(fs_plan* plan, const fs_swarm* swarm, fs_mlp* mlp, int n_cand, uint64_t seed,
-                                      int iteration, double w0, double w1, int n_iter, double c1, double c2,
-                                      double vmax);
+ * [0,1]^5 rank last).  mlps: n_mlp >= 1 networks; R must be a multiple of
+ * n_mlp and network g ranks the candidates of runs [g R/n_mlp, (g+1) R/n_mlp)
+ * (one network per search box, since positions are normalised to each
+ * run's box).  1 <= n_cand <= 64; candidates go through a network in chunks
+ * of its max_batch.  The networks must run on the plan's stream.
+ * Asynchronous; allocates its candidate buffers in the plan (synchronously)
+ * when they are too small. */
+FS_API fs_status fs_pso_step_screened(fs_plan* plan, const fs_swarm* swarm, fs_mlp* const* mlps, int n_mlp,
+                                      int n_cand, uint64_t seed, int iteration, double w0, double w1, int n_iter,
+                                      double c1, double c2, double vmax);
+
+/* Ring buffer of (position, fitness) samples a search collects to train the
+ * surrogate.  x: [cap][5] floats, f: [cap] floats, count: one unsigned
+ * 64-bit counter of samples appended so far (all device memory, owned by
+ * the caller; set count to 0 to start).  Sample i of an append of n goes to
+ * slot (count + i) mod cap, and count advances by n. */
+typedef struct {
+    float* x;
+    float* f;
+    int cap;
+    unsigned long long* count;
+} fs_sample_ring;
+
+/* Append the swarm's current positions (as floats) and fitness (NaN where
+ * not finite) to the rings: R must be a multiple of n_rings and ring g takes
+ * the particles of runs [g R/n_rings, (g+1) R/n_rings).  Asynchronous. */
+FS_API fs_status fs_pso_record(fs_plan* plan, const fs_swarm* swarm, const fs_sample_ring* rings, int n_rings);
+
+/* Capture a chosen part of a PSO iteration as a CUDA graph (as
+ * fs_pso_graph_build does for the whole of it).  parts: bit 1 = evaluate
+ * (fs_pso_evaluate), bit 2 = append to the rings (fs_pso_record), bit 4 =
+ * fs_pso_step, bit 8 = fs_pso_step_screened with the networks and n_cand (4
+ * and 8 exclusive); both steps use the device iteration counter.  The
+ * networks' stream must be the plan's stream; their weights are read when
+ * the graph runs, so training between launches takes effect.  The ring and
+ * network arrays are read at capture time.  Synchronous; runs one untimed
+ * evaluation first when bit 1 is set. */
+FS_API fs_status fs_pso_graph_build_ex(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p,
+                                       uint64_t seed, double w0, double w1, int n_iter, double c1, double c2,
+                                       double vmax, int parts, const fs_sample_ring* rings, int n_rings,
+                                       fs_mlp* const* mlps, int n_mlp, int n_cand, fs_graph** out);
 
 /* Launch variants of the fused bin-loop kernel (the tile shape of the
  * ragged batch, Sec. IV's particle x frequency parallelism).

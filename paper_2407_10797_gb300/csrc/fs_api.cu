@@ -220,6 +220,30 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
     return FS_OK;
 }
 
+// Candidate buffers of the screened step (grown synchronously, never during capture).
+fs_status ensure_candidates(fs_plan* p, int64_t nc) {
+    if (nc <= p->cand_cap) return FS_OK;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    cudaFree(p->cand_x);
+    cudaFree(p->cand_v);
+    cudaFree(p->cand_in);
+    cudaFree(p->cand_score);
+    cudaFree(p->cand_inside);
+    p->cand_x = p->cand_v = nullptr;
+    p->cand_in = p->cand_score = nullptr;
+    p->cand_inside = nullptr;
+    p->cand_cap = 0;
+    if ((e = cudaMalloc(&p->cand_x, sizeof(double) * 5 * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->cand_v, sizeof(double) * 5 * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->cand_in, sizeof(float) * 5 * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->cand_score, sizeof(float) * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->cand_inside, nc)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(candidates)");
+    p->cand_cap = nc;
+    return FS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -568,41 +592,28 @@ fs_status fs_pso_step(fs_plan* p, const fs_swarm* w, uint64_t seed, int iteratio
     return FS_OK;
 }
 
-fs_status fs_pso_step_screened(fs_plan* p, const fs_swarm* w, fs_mlp* mlp, int n_cand, uint64_t seed, int iteration,
-                               double w0, double w1, int n_iter, double c1, double c2, double vmax) {
+fs_status fs_pso_step_screened(fs_plan* p, const fs_swarm* w, fs_mlp* const* mlps, int n_mlp, int n_cand,
+                               uint64_t seed, int iteration, double w0, double w1, int n_iter, double c1, double c2,
+                               double vmax) {
     g_err[0] = 0;
-    if (!p || !mlp) return fail(FS_EINVAL, "fs_pso_step_screened: NULL plan or network");
+    if (!p || !mlps || n_mlp < 1) return fail(FS_EINVAL, "fs_pso_step_screened: NULL plan or no network");
     fs_status st = check_swarm(w);
     if (st != FS_OK) return st;
+    if (w->R % n_mlp != 0) return fail(FS_EINVAL, "fs_pso_step_screened: R = %d is not a multiple of n_mlp = %d",
+                                       w->R, n_mlp);
+    for (int i = 0; i < n_mlp; i++)
+        if (!mlps[i]) return fail(FS_EINVAL, "fs_pso_step_screened: network %d is NULL", i);
     if (n_cand < 1 || n_cand > 64) return fail(FS_EINVAL, "fs_pso_step_screened: n_cand must be in [1, 64]");
     if (n_iter < 1 || !(vmax > 0.0)) return fail(FS_EINVAL, "fs_pso_step_screened: need n_iter >= 1 and vmax > 0");
     if (iteration < 0 && !w->iter) return fail(FS_EINVAL, "fs_pso_step_screened: iteration < 0 needs swarm->iter");
     const int64_t nc = (int64_t)w->R * w->n_part * n_cand;
+    if ((st = ensure_candidates(p, nc)) != FS_OK) return st;
     cudaError_t e;
-    if (nc > p->cand_cap) {
-        if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-        cudaFree(p->cand_x);
-        cudaFree(p->cand_v);
-        cudaFree(p->cand_in);
-        cudaFree(p->cand_score);
-        cudaFree(p->cand_inside);
-        p->cand_x = p->cand_v = nullptr;
-        p->cand_in = p->cand_score = nullptr;
-        p->cand_inside = nullptr;
-        p->cand_cap = 0;
-        if ((e = cudaMalloc(&p->cand_x, sizeof(double) * 5 * nc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->cand_v, sizeof(double) * 5 * nc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->cand_in, sizeof(float) * 5 * nc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->cand_score, sizeof(float) * nc)) != cudaSuccess ||
-            (e = cudaMalloc(&p->cand_inside, nc)) != cudaSuccess)
-            return cuda_fail(e, "cudaMalloc(candidates)");
-        p->cand_cap = nc;
-    }
     const bool dev_iter = iteration < 0;
     e = fs::launch_pso_screened(w->R, w->n_part, n_cand, seed, dev_iter ? w->iter : nullptr,
                                 dev_iter ? 0u : (unsigned int)iteration, w0, w1, n_iter, c1, c2, vmax, w->x, w->v,
                                 w->pbest_x, w->pbest_f, w->fit, p->cand_x, p->cand_v, p->cand_in, p->cand_inside,
-                                p->cand_score, mlp, dev_iter ? w->iter : nullptr, p->stream);
+                                p->cand_score, mlps, n_mlp, dev_iter ? w->iter : nullptr, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "screened step");
     return FS_OK;
 }
@@ -653,6 +664,99 @@ fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges
     if (!gobj) {
         cudaGraphDestroy(gr);
         return fail(FS_ENOMEM, "fs_pso_graph_build: host allocation failed");
+    }
+    gobj->graph = gr;
+    gobj->stream = p->stream;
+    if ((e = cudaGraphInstantiate(&gobj->exec, gr, 0)) != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        delete gobj;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    *out = gobj;
+    return FS_OK;
+}
+
+fs_status fs_pso_record(fs_plan* p, const fs_swarm* w, const fs_sample_ring* rings, int n_rings) {
+    g_err[0] = 0;
+    if (!p || !rings || n_rings < 1) return fail(FS_EINVAL, "fs_pso_record: NULL plan or no ring");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    if (w->R % n_rings != 0)
+        return fail(FS_EINVAL, "fs_pso_record: R = %d is not a multiple of n_rings = %d", w->R, n_rings);
+    const int per = (w->R / n_rings) * w->n_part;   // particles per ring (their runs are contiguous)
+    for (int g = 0; g < n_rings; g++) {
+        const fs_sample_ring& r = rings[g];
+        if (!r.x || !r.f || !r.count || r.cap < 1)
+            return fail(FS_EINVAL, "fs_pso_record: ring %d needs x, f, count and cap >= 1", g);
+        cudaError_t e = fs::launch_pso_record(per, w->x + (int64_t)g * per * 5, w->fit + (int64_t)g * per, r.x, r.f,
+                                              r.cap, r.count, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "pso record launch");
+    }
+    return FS_OK;
+}
+
+fs_status fs_mlp_stream(fs_mlp* m, cudaStream_t* s);
+
+fs_status fs_pso_graph_build_ex(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np, uint64_t seed,
+                                double w0, double w1, int n_iter, double c1, double c2, double vmax, int parts,
+                                const fs_sample_ring* rings, int n_rings, fs_mlp* const* mlps, int n_mlp, int n_cand,
+                                fs_graph** out) {
+    g_err[0] = 0;
+    if (!out) return fail(FS_EINVAL, "fs_pso_graph_build_ex: out is NULL");
+    *out = nullptr;
+    if (!p) return fail(FS_EINVAL, "fs_pso_graph_build_ex: plan is NULL");
+    if (!p->stream) return fail(FS_EINVAL, "fs_pso_graph_build_ex: the plan's stream is the legacy default stream");
+    if (parts <= 0 || parts > 15 || ((parts & 4) && (parts & 8)))
+        return fail(FS_EINVAL, "fs_pso_graph_build_ex: parts must combine bits 1, 2 and one of 4, 8");
+    fs_status st = check_swarm(w);
+    if (st != FS_OK) return st;
+    if (!w->iter) return fail(FS_EINVAL, "fs_pso_graph_build_ex: swarm->iter is NULL");
+    if ((parts & 2) && (!rings || n_rings < 1)) return fail(FS_EINVAL, "fs_pso_graph_build_ex: bit 2 needs rings");
+    if (parts & 8) {
+        if (!mlps || n_mlp < 1) return fail(FS_EINVAL, "fs_pso_graph_build_ex: bit 8 needs networks");
+        for (int i = 0; i < n_mlp; i++) {
+            cudaStream_t ms = nullptr;
+            if (!mlps[i]) return fail(FS_EINVAL, "fs_pso_graph_build_ex: network %d is NULL", i);
+            if ((st = fs_mlp_stream(mlps[i], &ms)) != FS_OK) return st;
+            if (ms != p->stream)
+                return fail(FS_EINVAL, "fs_pso_graph_build_ex: the networks must use the plan's stream");
+        }
+    }
+    const int n = w->R * w->n_part;
+    if ((st = ensure_workspace(p, n > 0 ? n : 1, Np)) != FS_OK) return st;
+    if (parts & 1) {
+        if ((st = fs_pso_evaluate(p, w, edges_host, Np)) != FS_OK) return st;   // also uploads the edges
+    }
+    if (parts & 8) {
+        if (n_cand < 1 || n_cand > 64) return fail(FS_EINVAL, "fs_pso_graph_build_ex: n_cand must be in [1, 64]");
+        if ((st = ensure_candidates(p, (int64_t)n * n_cand)) != FS_OK) return st;   // outside the capture
+    }
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const int prof = p->profiling;
+    p->profiling = 0;
+    if ((e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        p->profiling = prof;
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    st = FS_OK;
+    if (parts & 1) st = fs_pso_evaluate(p, w, edges_host, Np);
+    if (st == FS_OK && (parts & 2)) st = fs_pso_record(p, w, rings, n_rings);
+    if (st == FS_OK && (parts & 4)) st = fs_pso_step(p, w, seed, -1, w0, w1, n_iter, c1, c2, vmax, nullptr);
+    if (st == FS_OK && (parts & 8))
+        st = fs_pso_step_screened(p, w, mlps, n_mlp, n_cand, seed, -1, w0, w1, n_iter, c1, c2, vmax);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(p->stream, &gr);
+    p->profiling = prof;
+    if (st != FS_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    fs_graph* gobj = new (std::nothrow) fs_graph;
+    if (!gobj) {
+        cudaGraphDestroy(gr);
+        return fail(FS_ENOMEM, "fs_pso_graph_build_ex: host allocation failed");
     }
     gobj->graph = gr;
     gobj->stream = p->stream;

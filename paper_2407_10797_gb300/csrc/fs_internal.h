@@ -97,7 +97,9 @@ cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, c
                                 unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2,
                                 double vmax, double* x, double* v, double* pbx, double* pbf, const double* fit,
                                 double* cx, double* cv, float* cin, unsigned char* inside, float* score,
-                                ::fs_mlp* mlp, unsigned int* iter_advance, cudaStream_t s);
+                                ::fs_mlp* const* mlps, int n_mlp, unsigned int* iter_advance, cudaStream_t s);
+cudaError_t launch_pso_record(int n, const double* x, const double* fit, float* rx, float* rf, int cap,
+                              unsigned long long* count, cudaStream_t s);
 cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);
 cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,
                               double* data, cudaStream_t s);

@@ -551,6 +551,14 @@ fs_status fs_mlp_get_params(fs_mlp* m, float* theta_dev) {
     return FS_OK;
 }
 
+// The network's stream (library-internal; the screened-step graph builder
+// checks that it matches the plan's).
+fs_status fs_mlp_stream(fs_mlp* m, cudaStream_t* s) {
+    if (!m || !s) return fs::set_error(FS_EINVAL, "fs_mlp_stream: NULL argument");
+    *s = m->stream;
+    return FS_OK;
+}
+
 fs_status fs_mlp_forward(fs_mlp* m, const float* X_dev, int N, float* y_dev) {
     fs::set_error(FS_OK, "");
     if (!m || N < 0 || (N > 0 && (!X_dev || !y_dev))) return fs::set_error(FS_EINVAL, "fs_mlp_forward: bad argument");

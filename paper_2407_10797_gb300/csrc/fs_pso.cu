@@ -296,11 +296,36 @@ cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsign
     return cudaGetLastError();
 }
 
+// Surrogate training samples: positions as floats, non-finite fitness as
+// NaN, into slot (count + i) mod cap of a ring; the counter advances after.
+__global__ void pso_record_kernel(int n, const double* __restrict__ x, const double* __restrict__ fit, float* rx,
+                                  float* rf, int cap, const unsigned long long* count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = (int64_t)((*count + (unsigned long long)i) % (unsigned long long)cap);
+#pragma unroll
+    for (int d = 0; d < 5; d++) rx[j * 5 + d] = (float)x[(int64_t)i * 5 + d];
+    const double f = fit[i];
+    rf[j] = isfinite(f) ? (float)f : __int_as_float(0x7fc00000);
+}
+
+__global__ void ring_advance_kernel(unsigned long long* count, int n) { *count += (unsigned long long)n; }
+
+cudaError_t launch_pso_record(int n, const double* x, const double* fit, float* rx, float* rf, int cap,
+                              unsigned long long* count, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    pso_record_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, x, fit, rx, rf, cap, count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ring_advance_kernel<<<1, 1, 0, s>>>(count, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, const unsigned int* iter_dev,
                                 unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2,
                                 double vmax, double* x, double* v, double* pbx, double* pbf, const double* fit,
                                 double* cx, double* cv, float* cin, unsigned char* inside, float* score,
-                                fs_mlp* mlp, unsigned int* iter_advance, cudaStream_t s) {
+                                fs_mlp* const* mlps, int n_mlp, unsigned int* iter_advance, cudaStream_t s) {
     const int n = R * Np;
     if (n == 0) return cudaSuccess;
     pso_pbest_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, x, fit, pbx, pbf);
@@ -310,7 +335,11 @@ cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, c
                                                                        cin, inside);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (fs_mlp_forward(mlp, cin, (int)nc, score) != FS_OK) return cudaErrorLaunchFailure;
+    // network g ranks the candidates of runs [g R / n_mlp, (g + 1) R / n_mlp), which are contiguous
+    const int64_t per = nc / n_mlp;
+    for (int g = 0; g < n_mlp; g++)
+        if (fs_mlp_forward(mlps[g], cin + g * per * 5, (int)per, score + g * per) != FS_OK)
+            return cudaErrorLaunchFailure;
     pso_select_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, C, score, inside, cx, cv, x, v);
     if ((e = cudaGetLastError()) != cudaSuccess || !iter_advance) return e;
     pso_advance_kernel<<<1, 1, 0, s>>>(iter_advance);

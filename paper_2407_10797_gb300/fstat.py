@@ -40,6 +40,10 @@ _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 
 
+class fs_sample_ring(C.Structure):
+    _fields_ = [("x", _vp), ("f", _vp), ("cap", C.c_int), ("count", _vp)]
+
+
 class fs_swarm(C.Structure):
     _fields_ = [("R", C.c_int), ("n_part", C.c_int), ("x", _vp), ("v", _vp), ("pbest_x", _vp),
                 ("pbest_f", _vp), ("fit", _vp), ("box", _vp), ("q", C.c_double), ("iter", _vp)]
@@ -85,9 +89,14 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_pso_graph_build.argtypes = [_vp, _sw, _ep, C.c_int, C.c_uint64, C.c_double, C.c_double, C.c_int,
                                          C.c_double, C.c_double, C.c_double, C.POINTER(_vp)]
         L.fs_graph_run.argtypes = [_vp, C.c_int]
+        _rp = C.POINTER(fs_sample_ring)
+        L.fs_pso_record.argtypes = [_vp, _sw, _rp, C.c_int]
+        L.fs_pso_graph_build_ex.argtypes = [_vp, _sw, _ep, C.c_int, C.c_uint64, C.c_double, C.c_double, C.c_int,
+                                            C.c_double, C.c_double, C.c_double, C.c_int, _rp, C.c_int,
+                                            C.POINTER(_vp), C.c_int, C.c_int, C.POINTER(_vp)]
         L.fs_graph_destroy.argtypes = [_vp]
-        L.fs_pso_step_screened.argtypes = [_vp, _sw, _vp, C.c_int, C.c_uint64, C.c_int, C.c_double, C.c_double,
-                                           C.c_int, C.c_double, C.c_double, C.c_double]
+        L.fs_pso_step_screened.argtypes = [_vp, _sw, C.POINTER(_vp), C.c_int, C.c_int, C.c_uint64, C.c_int,
+                                           C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_double]
         L.fs_mlp_num_params.argtypes = [C.c_int]
         L.fs_mlp_num_params.restype = C.c_int64
         L.fs_mlp_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_uint64, _vp]
@@ -104,7 +113,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
                      "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
                      "fs_plan_autotune", "fs_pso_autotune", "fs_plan_census", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
-                     "fs_pso_graph_build", "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
+                     "fs_pso_graph_build", "fs_pso_graph_build_ex", "fs_pso_record", "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
                      "fs_mlp_destroy", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
                      "fs_mlp_loss_grad", "fs_mlp_train", "fs_pso_step_screened"):
             getattr(L, name).restype = C.c_int
@@ -384,9 +393,11 @@ class Swarm:
                                   int(n_iter), float(c1), float(c2), float(vmax),
                                   None if lbest is None else C.c_void_p(lbest.data_ptr())))
 
-    def step_screened(self, mlp: "MLP", n_cand: int, seed: int, iteration: int, w0=0.9, w1=0.4, n_iter=2, c1=2.0,
+    def step_screened(self, mlp, n_cand: int, seed: int, iteration: int, w0=0.9, w1=0.4, n_iter=2, c1=2.0,
                       c2=2.0, vmax=0.5):
-        _check(load().fs_pso_step_screened(self.plan._h, C.byref(self.c), mlp._h, int(n_cand), int(seed),
+        """Screened step; mlp: one MLP or a list of them (one per equal group of runs)."""
+        arr = _mlp_array(mlp)
+        _check(load().fs_pso_step_screened(self.plan._h, C.byref(self.c), arr, len(arr), int(n_cand), int(seed),
                                            int(iteration), float(w0), float(w1), int(n_iter), float(c1), float(c2),
                                            float(vmax)))
 
@@ -408,6 +419,26 @@ class Swarm:
     def graph_run(self, n: int):
         _check(load().fs_graph_run(self._graph, int(n)))
 
+    def record(self, ring):
+        """Append the current (positions, fitness) to a sample ring, or to a list of
+        rings (one per equal group of runs) (fs_pso_record)."""
+        rings = _ring_array(ring)
+        _check(load().fs_pso_record(self.plan._h, C.byref(self.c), rings, len(rings)))
+
+    def graph_build_ex(self, parts: int, Np: int, seed: int, edges=None, ring=None, mlp=None, n_cand: int = 16,
+                       w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5) -> "Graph":
+        """Capture part of a PSO iteration (fs_pso_graph_build_ex; parts: 1 evaluate,
+        2 record to `ring` (one or a list), 4 step, 8 screened step with `mlp` (one or a list))."""
+        arr, e = _edges_arg(edges, Np)
+        rings = _ring_array(ring) if ring is not None else None
+        mlps = _mlp_array(mlp) if mlp is not None else None
+        h = C.c_void_p()
+        _check(load().fs_pso_graph_build_ex(self.plan._h, C.byref(self.c), e, int(Np), int(seed), float(w0),
+                                            float(w1), int(n_iter), float(c1), float(c2), float(vmax), int(parts),
+                                            rings, 0 if rings is None else len(rings), mlps,
+                                            0 if mlps is None else len(mlps), int(n_cand), C.byref(h)))
+        return Graph(h)
+
     def graph_free(self):
         g = getattr(self, "_graph", None)
         if g is not None and g.value:
@@ -419,6 +450,50 @@ class Swarm:
             self.graph_free()
         except Exception:
             pass
+
+
+def _mlp_array(mlp):
+    nets = list(mlp) if isinstance(mlp, (list, tuple)) else [mlp]
+    return (C.c_void_p * len(nets))(*[n._h.value for n in nets])
+
+
+def _ring_array(ring):
+    rings = list(ring) if isinstance(ring, (list, tuple)) else [ring]
+    return (fs_sample_ring * len(rings))(*[r.c for r in rings])
+
+
+class Graph:
+    """A captured part of a PSO iteration (fs_graph)."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def run(self, n: int = 1):
+        _check(load().fs_graph_run(self._h, int(n)))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().fs_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SampleRing:
+    """Device ring of (position, fitness) training samples (fs_sample_ring)."""
+
+    def __init__(self, cap: int, device=None):
+        import torch
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.cap = int(cap)
+        self.x = torch.zeros(self.cap, 5, dtype=torch.float32, device=dev)
+        self.f = torch.full((self.cap,), float("nan"), dtype=torch.float32, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.c = fs_sample_ring(self.x.data_ptr(), self.f.data_ptr(), self.cap, self.count.data_ptr())
 
 
 def torch_tensor(a):

@@ -135,12 +135,15 @@ class HierarchicalSearch:
                  n_boxes: int = 16, runs_per_box: int = 8, n_part: int = 40, seed: int = 0, q: float = 1.0,
                  checkpoint_dir: str | None = None, c1: float = 2.0, c2: float = 2.0, vmax: float = 0.5,
                  bounds: np.ndarray | None = None, surrogate: SurrogateSpec | None = None,
-                 autotune: bool | None = None):
+                 autotune: bool | None = None, use_graphs: bool = True, record_history: bool = False):
         """bounds: optional [5, 2] search bounds overriding the prior's (a zero
         width pins a coordinate).  autotune: time the fused kernel's launch
         variants on each stage's first swarm and use the fastest; None = only
         for FS_MIXED plans, whose variants give bitwise-equal F (FP64 variants
-        differ by rounding, which can steer a PSO run differently)."""
+        differ by rounding, which can steer a PSO run differently).  use_graphs:
+        replay captured iterations (eager launches otherwise; same results).
+        record_history: keep the best fitness after every iteration of a
+        surrogate-screened stage in `history`."""
         self.plan = plan
         self.prior = prior
         self.bounds = None if bounds is None else np.asarray(bounds, dtype=np.float64)
@@ -152,8 +155,11 @@ class HierarchicalSearch:
         self.results: list[StageResult] = []
         self.surrogate = surrogate
         self.mlp = None
+        self.mlps: list = []
         self.history: dict[int, list] = {}   # best fitness after each iteration (surrogate runs)
         self.autotune = (plan.mode == fstat.FS_MIXED) if autotune is None else bool(autotune)
+        self.use_graphs = use_graphs
+        self.record_history = record_history
 
     # ---------------------------------------------------------------- boxes
     def stage_boxes(self, i: int) -> np.ndarray:
@@ -217,35 +223,51 @@ class HierarchicalSearch:
         return res
 
     def _run_screened(self, sw, spec: StageSpec, stage_seed: int, stage: int):
-        """n_iter - 1 iterations of evaluate + (screened) step, collecting
-        training pairs; eager launches on the plan's stream."""
+        """n_iter - 1 iterations of evaluate + record + (screened) step with one
+        network and one sample ring per search box: positions are normalised
+        to each run's box, so the runs of a box share a landscape and the
+        boxes do not.  Every train_every iterations after the warm-up each
+        network trains on its box's ring.  With graphs (default) an iteration
+        is two captured launches, (evaluate + record) and the step, with the
+        training in between when due; the eager form makes the same calls."""
         import torch
         sp = self.surrogate
-        if self.mlp is None:
-            self.mlp = fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed, stream=self.plan.stream)
-        n = sw.R * sw.n_part
-        cap = sp.buffer
-        bx = torch.zeros(cap, 5, dtype=torch.float32, device=sw.x.device)
-        bt = torch.full((cap,), float("nan"), dtype=torch.float32, device=sw.x.device)
-        count = 0
+        nb = self.n_boxes
+        dev = sw.x.device
+        self.mlps = [fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed * 1000 + 97 * stage + k,
+                               stream=self.plan.stream) for k in range(nb)]
+        self.mlp = self.mlps[0]
+        rings = [fstat.SampleRing(sp.buffer, device=dev) for _ in range(nb)]
+        per_box = (sw.R // nb) * sw.n_part
+        step_kw = dict(w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter, c1=self.c1, c2=self.c2, vmax=self.vmax)
+        graphs = None
+        if self.use_graphs:
+            graphs = (sw.graph_build_ex(1 | 2, spec.Np, stage_seed, ring=rings, **step_kw),
+                      sw.graph_build_ex(4, spec.Np, stage_seed, **step_kw),
+                      sw.graph_build_ex(8, spec.Np, stage_seed, mlp=self.mlps, n_cand=sp.n_cand, **step_kw))
         hist = []
         for it in range(spec.n_iter - 1):
-            sw.evaluate(spec.Np)
-            idx = (torch.arange(n, device=sw.x.device) + count) % cap
-            bx[idx] = sw.x.reshape(-1, 5).float()
-            f = sw.fit.reshape(-1)
-            bt[idx] = torch.where(torch.isfinite(f), f, torch.full_like(f, float("nan"))).float()
-            count += n
-            if it >= sp.warm:
-                if (it - sp.warm) % sp.train_every == 0:
-                    m = min(count, cap)
-                    self.mlp.train(bx[:m], bt[:m], sp.train_steps, sp.lr)
-                sw.step_screened(self.mlp, sp.n_cand, stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter,
-                                 c1=self.c1, c2=self.c2, vmax=self.vmax)
+            if graphs:
+                graphs[0].run(1)
             else:
-                sw.step(stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter, c1=self.c1, c2=self.c2,
-                        vmax=self.vmax)
-            hist.append(sw.pbest_f.max())
+                sw.evaluate(spec.Np)
+                sw.record(rings)
+            screened = it >= sp.warm
+            if screened and (it - sp.warm) % sp.train_every == 0:
+                m = min((it + 1) * per_box, sp.buffer)
+                for net, ring in zip(self.mlps, rings):
+                    net.train(ring.x[:m], ring.f[:m], sp.train_steps, sp.lr)
+            if graphs:
+                graphs[2 if screened else 1].run(1)
+            elif screened:
+                sw.step_screened(self.mlps, sp.n_cand, stage_seed, -1, **step_kw)
+            else:
+                sw.step(stage_seed, -1, **step_kw)
+            if self.record_history:
+                hist.append(sw.pbest_f.max())
+        if graphs:
+            for gr in graphs:
+                gr.close()
         self.history[stage] = [float(h) for h in torch.stack(hist).cpu().numpy()] if hist else []
 
     # ---------------------------------------------------------------- checkpoints

@@ -121,7 +121,7 @@ def test_surrogate_screening_gains_over_plain_pso(setup):
             sp = search.SurrogateSpec(n_cand=16 if mode == "screened" else 1, warm=20 if mode == "screened" else 10 ** 9,
                                       train_every=10, train_steps=40, lr=1e-3, buffer=8192)
             hs = search.HierarchicalSearch(plan, prior, st, n_boxes=1, runs_per_box=8, n_part=40, seed=seed,
-                                           bounds=bounds, surrogate=sp)
+                                           bounds=bounds, surrogate=sp, record_history=True)
             hs.run()
             curves.setdefault(mode, []).append(hs.history[0])
     plain, scr = np.array(curves["plain"]), np.array(curves["screened"])
@@ -130,6 +130,24 @@ def test_surrogate_screening_gains_over_plain_pso(setup):
     hs = search.HierarchicalSearch(plan, prior, st, n_boxes=1, runs_per_box=8, n_part=40, seed=0, bounds=bounds)
     r_graph = hs.run()
     hs = search.HierarchicalSearch(plan, prior, st, n_boxes=1, runs_per_box=8, n_part=40, seed=0, bounds=bounds,
-                                   surrogate=search.SurrogateSpec(n_cand=1, warm=10 ** 9))
+                                   surrogate=search.SurrogateSpec(n_cand=1, warm=10 ** 9), use_graphs=False)
     r_eager = hs.run()
     assert r_graph["best"] == r_eager["best"]
+
+
+def test_screened_search_graphs_match_eager(setup):
+    """The captured screened iteration (evaluate + record, then the screened
+    step, training in between) gives the same search as the eager calls."""
+    fstat, search, plan, prior, stages, truth = setup
+    ls = math.sin(truth[2])
+    bounds = np.array([[29.8, 30.2], [truth[1] - 2e4, truth[1] + 2e4], [ls - 0.2, ls + 0.2],
+                       [truth[3] - 0.2, truth[3] + 0.2], [0.0, 0.05]])
+    st = [search.StageSpec(1, 60, "split_tc")]
+    out = []
+    for use_graphs in (True, False):
+        sp = search.SurrogateSpec(n_cand=16, warm=20, train_every=10, train_steps=20, lr=1e-3, buffer=4096)
+        hs = search.HierarchicalSearch(plan, prior, st, n_boxes=1, runs_per_box=4, n_part=40, seed=5, bounds=bounds,
+                                       surrogate=sp, use_graphs=use_graphs, record_history=True)
+        out.append((hs.run(), hs.history[0]))
+    assert out[0][0]["best"] == out[1][0]["best"]
+    assert out[0][1] == out[1][1]
