@@ -231,6 +231,18 @@ FS_API int64_t fs_mlp_num_params(int width);
 FS_API fs_status fs_mlp_create(fs_mlp** out, int width, int max_batch, uint64_t seed, void* stream);
 FS_API fs_status fs_mlp_destroy(fs_mlp* mlp);
 
+/* Tensor-core path of the network's GEMMs: 1 = tcgen05 (5th-generation
+ * tensor cores, accumulators in tensor memory) for the products whose
+ * output width is a multiple of 64 or equals 16, mma.sync for the others;
+ * 0 = mma.sync throughout (the default at creation).  Both accumulate bf16
+ * products in fp32; results differ only in summation order. */
+FS_API fs_status fs_mlp_set_tensor_path(fs_mlp* mlp, int tcgen05);
+
+/* FS_ETIMEOUT (and *timed_out = 1) if a tcgen05 GEMM of this network gave up
+ * waiting for its MMAs (its outputs are then invalid); FS_OK otherwise.
+ * Waits for the network's stream. */
+FS_API fs_status fs_mlp_tensor_status(fs_mlp* mlp, int* timed_out);
+
 /* Copy the fp32 master weights in or out (device buffers of
  * fs_mlp_num_params floats).  Setting weights resets the Adam step count
  * and the target standardisation.  set is synchronous, get asynchronous. */
@@ -301,6 +313,15 @@ FS_API fs_status fs_pso_graph_build_ex(fs_plan* plan, const fs_swarm* swarm, con
                                        uint64_t seed, double w0, double w1, int n_iter, double c1, double c2,
                                        double vmax, int parts, const fs_sample_ring* rings, int n_rings,
                                        fs_mlp* const* mlps, int n_mlp, int n_cand, fs_graph** out);
+
+/* Capture `steps` Adam steps of fs_mlp_train for each network on its ring's
+ * whole contents (all cap slots; empty slots hold NaN targets, which the loss
+ * ignores) as one CUDA graph, run with fs_graph_run.  The networks must share
+ * one stream that is not the legacy default stream; the rings' buffers are
+ * read when the graph runs.  The Adam step count lives on the device, so
+ * replays continue the optimisation.  Synchronous. */
+FS_API fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_sample_ring* rings, int steps,
+                                          float lr, fs_graph** out);
 
 /* Launch variants of the fused bin-loop kernel (the tile shape of the
  * ragged batch, Sec. IV's particle x frequency parallelism).

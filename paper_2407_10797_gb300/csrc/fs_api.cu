@@ -769,6 +769,54 @@ fs_status fs_pso_graph_build_ex(fs_plan* p, const fs_swarm* w, const int64_t* ed
     return FS_OK;
 }
 
+fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_sample_ring* rings, int steps, float lr,
+                                   fs_graph** out) {
+    g_err[0] = 0;
+    if (!out) return fail(FS_EINVAL, "fs_mlp_train_graph_build: out is NULL");
+    *out = nullptr;
+    if (!mlps || !rings || n < 1 || steps < 1 || !(lr > 0.f))
+        return fail(FS_EINVAL, "fs_mlp_train_graph_build: need n >= 1 networks and rings, steps >= 1, lr > 0");
+    cudaStream_t s = nullptr;
+    for (int i = 0; i < n; i++) {
+        cudaStream_t si = nullptr;
+        if (!mlps[i]) return fail(FS_EINVAL, "fs_mlp_train_graph_build: network %d is NULL", i);
+        fs_status st = fs_mlp_stream(mlps[i], &si);
+        if (st != FS_OK) return st;
+        if (i == 0) s = si;
+        if (si != s || !s) return fail(FS_EINVAL, "fs_mlp_train_graph_build: the networks must share one non-default stream");
+        if (!rings[i].x || !rings[i].f || rings[i].cap < 1)
+            return fail(FS_EINVAL, "fs_mlp_train_graph_build: ring %d needs x, f and cap >= 1", i);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    fs_status st = FS_OK;
+    for (int i = 0; i < n && st == FS_OK; i++)
+        st = fs_mlp_train(mlps[i], rings[i].x, rings[i].f, rings[i].cap, steps, lr, nullptr);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(s, &gr);
+    if (st != FS_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    fs_graph* gobj = new (std::nothrow) fs_graph;
+    if (!gobj) {
+        cudaGraphDestroy(gr);
+        return fail(FS_ENOMEM, "fs_mlp_train_graph_build: host allocation failed");
+    }
+    gobj->graph = gr;
+    gobj->stream = s;
+    if ((e = cudaGraphInstantiate(&gobj->exec, gr, 0)) != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        delete gobj;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    *out = gobj;
+    return FS_OK;
+}
+
 fs_status fs_graph_run(fs_graph* g, int n) {
     g_err[0] = 0;
     if (!g || n < 0) return fail(FS_EINVAL, "fs_graph_run: bad argument");

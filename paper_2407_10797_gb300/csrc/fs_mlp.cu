@@ -30,6 +30,7 @@ constexpr int kInPad = 16;   // input features padded to one mma K step
 enum Epi { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32 = 2 };
 
 constexpr int BM = 64, BN = 64, BK = 32, PAD = 8, GEMM_THREADS = 128;
+constexpr int kMaxSplits = 32;   // K chunks of the weight-gradient GEMMs
 
 __device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], const uint32_t b[2]) {
     asm volatile(
@@ -64,7 +65,13 @@ __device__ __forceinline__ void load_tile(bf16 (*S)[BK + PAD], const bf16* __res
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(GEMM_THREADS)
 gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb,
-                 const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, void* out, int ldo) {
+                 const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, void* out, int ldo,
+                 int kchunk) {
+    // split K: CTA z covers k in [z kchunk, min(K, (z + 1) kchunk)) and (EPI_F32 only) writes
+    // its partial product to the z-th M x ldo slab of out
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(K, kb + kchunk);
+    if (EPI == EPI_F32) out = static_cast<float*>(out) + (int64_t)blockIdx.z * M * ldo;
     __shared__ __align__(16) bf16 As[BM][BK + PAD];
     __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -79,9 +86,9 @@ gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[i][j][c] = 0.f;
 
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        load_tile<TA>(As, A, lda, m0, M, k0, K);
-        load_tile<TB>(Bs, B, ldb, n0, N, k0, K);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        load_tile<TA>(As, A, lda, m0, M, k0, ke);
+        load_tile<TB>(Bs, B, ldb, n0, N, k0, ke);
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
@@ -130,12 +137,321 @@ gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const
             }
 }
 
+// ---------------------------------------------------------------------------
+// The same GEMM on the 5th-generation tensor cores (tcgen05): a CTA owns a
+// 128 x NT tile of C whose fp32 accumulators live in tensor memory (TMEM).
+// Per K stage of 64 the 128 threads copy A (128 x 64) and B (NT x 64) into
+// shared memory as K-major 8 x 8 "core matrices" (no swizzle: element (r, k)
+// at byte (r/8) 1024 + (k/8) 128 + (r%8) 16 + (k%8) 2), transposing on the way
+// when an operand is stored the other way round; one thread issues four
+// 128 x NT x 16 bf16 MMAs and commits them to an mbarrier.  Two stages
+// alternate, so the copy of stage i+1 overlaps the MMAs of stage i.  The
+// epilogue reads TMEM with tcgen05.ld (warp w: rows 32w..32w+31, one row per
+// thread) and applies the same epilogues as the mma.sync kernel.  Every
+// mbarrier wait is bounded; on timeout the CTA records an error, stops
+// issuing work, still frees its TMEM and returns.
+// ---------------------------------------------------------------------------
+namespace tc5 {
+
+constexpr int TM = 128;          // tile rows = MMA M
+constexpr int TK = 64;           // K per stage
+constexpr int THREADS = 128;
+constexpr long long kMaxPolls = 1LL << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start address, leading (K) byte offset 128,
+// stride (M/N) byte offset 1024, fixed 0b001 at bits 46-48, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < kMaxPolls; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Copy rows [row0, row0 + R) x k [k0, k0 + TK) of an operand into a core-matrix tile.
+//   !T: element (r, k) at G[r * ld + k] (k contiguous): 16-byte loads along k
+//    T: element (r, k) at G[k * ld + r] (r contiguous): 16-byte loads along r, scattered
+template <bool T, int R>
+__device__ __forceinline__ void load_op(unsigned char* tile, const bf16* __restrict__ G, int ld, int row0, int rows,
+                                        int k0, int kend) {
+    constexpr int CH = R * TK / 8;   // 16-byte chunks per stage
+    for (int c = threadIdx.x; c < CH; c += THREADS) {
+        if (!T) {
+            const int r = c / (TK / 8), k = (c % (TK / 8)) * 8;
+            const int gr = row0 + r, gk = k0 + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gr < rows) {
+                if (gk + 8 <= kend) {
+                    v = *reinterpret_cast<const uint4*>(G + (int64_t)gr * ld + gk);
+                } else {
+                    bf16 e[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        e[j] = gk + j < kend ? G[(int64_t)gr * ld + gk + j] : __float2bfloat16(0.f);
+                    v = *reinterpret_cast<const uint4*>(e);
+                }
+            }
+            *reinterpret_cast<uint4*>(tile + core_off(r, k)) = v;
+        } else {
+            const int k = c / (R / 8), r = (c % (R / 8)) * 8;
+            const int gr = row0 + r, gk = k0 + k;
+            bf16 e[8];
+            if (gk < kend && gr + 8 <= rows) {
+                *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(G + (int64_t)gk * ld + gr);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    e[j] = (gk < kend && gr + j < rows) ? G[(int64_t)gk * ld + gr + j] : __float2bfloat16(0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) *reinterpret_cast<bf16*>(tile + core_off(r + j, k)) = e[j];
+        }
+    }
+}
+
+template <bool TA, bool TB, int EPI, int NT>
+__global__ void __launch_bounds__(THREADS)
+gemm_tc5_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb,
+                const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, void* out, int ldo, int kchunk,
+                int* err) {
+    constexpr int A_BYTES = TM * TK * 2, B_BYTES = NT * TK * 2, STAGE = A_BYTES + B_BYTES;
+    constexpr uint32_t NCOLS = NT < 32 ? 32 : NT;   // TMEM columns: a power of two >= 32
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * NT;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    if (EPI == EPI_F32) out = static_cast<float*>(out) + (int64_t)blockIdx.z * M * ldo;
+
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+        failed = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+
+    const int nk = ke > kb ? (ke - kb + TK - 1) / TK : 0;
+    uint32_t phase[2] = {0u, 0u};
+    int issued = 0;   // stages whose MMAs were committed
+    for (int i = 0; i < nk; i++) {
+        const int st = i & 1;
+        unsigned char* a_t = smem + st * STAGE;
+        unsigned char* b_t = a_t + A_BYTES;
+        if (i >= 2) {   // the MMAs of stage i - 2 used these buffers
+            if (!wait_bar(&bars[st], phase[st])) failed = 1;
+            phase[st] ^= 1u;
+        }
+        __syncthreads();
+        if (failed) break;
+        const int k0 = kb + i * TK;
+        load_op<TA, TM>(a_t, A, lda, m0, M, k0, ke);
+        load_op<TB, NT>(b_t, B, ldb, n0, N, k0, ke);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ab = smem_u32(a_t), bb = smem_u32(b_t);
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; kk++)
+                mma(tmem, sdesc(ab + kk * 256), sdesc(bb + kk * 256), idesc(TM, NT), (i > 0 || kk > 0) ? 1u : 0u);
+            commit(&bars[st]);
+        }
+        issued = i + 1;
+    }
+    // the last committed stage (MMAs complete in order); waited for even after a
+    // failure, so that no MMA is still writing when the TMEM is freed
+    if (issued > 0) {
+        const int st = (issued - 1) & 1;
+        if (!wait_bar(&bars[st], phase[st])) failed = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!failed) {
+        // phase 1: TMEM -> shared staging tile of raw fp32 accumulators (row stride NT + 4
+        // floats; the stage buffers are free: every MMA has completed)
+        float* stg = reinterpret_cast<float*>(smem);
+        constexpr int LDS = NT + 4;
+        const int row = warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t r[16];
+            if (nk > 0) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; j++) r[j] = 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4*>(stg + row * LDS + c0 + j) =
+                    make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                __uint_as_float(r[j + 3]));
+        }
+        __syncthreads();
+        // phase 2: coalesced epilogue, 4 consecutive columns per thread
+        constexpr int QPR = NT / 4;   // column quads per row
+        for (int q = threadIdx.x; q < TM * QPR; q += THREADS) {
+            const int rr = q / QPR, cc = (q % QPR) * 4;
+            const int m = m0 + rr, n = n0 + cc;
+            if (m >= M) continue;
+            const float4 v4 = *reinterpret_cast<const float4*>(stg + rr * LDS + cc);
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (n + j >= N) break;
+                if (EPI == EPI_BIAS_RELU_BF16) {
+                    static_cast<bf16*>(out)[(int64_t)m * ldo + n + j] = __float2bfloat16(fmaxf(v[j] + bias[n + j], 0.f));
+                } else if (EPI == EPI_MASK_BF16) {
+                    const float a = __bfloat162float(mask[(int64_t)m * ldm + n + j]);
+                    static_cast<bf16*>(out)[(int64_t)m * ldo + n + j] = __float2bfloat16(a > 0.f ? v[j] : 0.f);
+                } else {
+                    static_cast<float*>(out)[(int64_t)m * ldo + n + j] = v[j];
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+template <bool TA, bool TB, int EPI, int NT>
+cudaError_t launch(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias,
+                   const bf16* mask, int ldm, void* out, int ldo, int splits, int kchunk, int* err, cudaStream_t s) {
+    constexpr int STAGES = 2 * (TM * TK * 2 + NT * TK * 2), STAGING = TM * (NT + 4) * 4;
+    constexpr int SMEM = STAGES > STAGING ? STAGES : STAGING;
+    static bool attr[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        if ((e = cudaFuncSetAttribute(gemm_tc5_kernel<TA, TB, EPI, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM)) != cudaSuccess)
+            return e;
+        attr[dev] = true;
+    }
+    dim3 grid((unsigned)((N + NT - 1) / NT), (unsigned)((M + TM - 1) / TM), (unsigned)splits);
+    gemm_tc5_kernel<TA, TB, EPI, NT><<<grid, THREADS, SMEM, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo,
+                                                                 kchunk, err);
+    return cudaGetLastError();
+}
+
+}  // namespace tc5
+
 template <bool TA, bool TB, int EPI>
 static cudaError_t gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias,
-                        const bf16* mask, int ldm, void* out, int ldo, cudaStream_t s) {
+                        const bf16* mask, int ldm, void* out, int ldo, cudaStream_t s, int* tc_err = nullptr) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
-    gemm_bf16_kernel<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo);
+    if (tc_err && N % 128 == 0 && (int64_t)((M + 127) / 128) * (N / 128) >= 152)
+        return tc5::launch<TA, TB, EPI, 128>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, 1,
+                                             K > 0 ? K : 1, tc_err, s);
+    if (tc_err && N % 64 == 0)
+        return tc5::launch<TA, TB, EPI, 64>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, 1, K > 0 ? K : 1,
+                                            tc_err, s);
+    if (tc_err && N == 16)
+        return tc5::launch<TA, TB, EPI, 16>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, 1, K > 0 ? K : 1,
+                                            tc_err, s);
+    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), 1);
+    gemm_bf16_kernel<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo,
+                                                                K > 0 ? K : 1);
+    return cudaGetLastError();
+}
+
+__global__ void sum_splits_kernel(int S, int64_t MN, const float* __restrict__ ws, float* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= MN) return;
+    float v = 0.f;
+    for (int z = 0; z < S; z++) v += ws[(int64_t)z * MN + i];   // fixed order: deterministic
+    out[i] = v;
+}
+
+// Weight gradient C = A^T B (fp32, dense M x N) with the K = batch axis split into
+// chunks of 256 rows: one CTA per (tile, chunk) keeps the GPU busy when M x N is
+// only a few tiles; the chunk partials (ws: splits x M x N floats) are summed in order.
+template <bool TB>
+static cudaError_t gemm_wgrad(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, float* out,
+                              float* ws, int max_splits, cudaStream_t s, int* tc_err = nullptr) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const bool tc = tc_err && (N % 64 == 0 || N == 16);
+    int splits = (K + 255) / 256;
+    if (splits > max_splits) splits = max_splits;
+    if (splits < 1) splits = 1;
+    int kchunk = (K + splits - 1) / splits;
+    const int q = tc ? tc5::TK : BK;   // chunks start on a stage boundary
+    kchunk = (kchunk + q - 1) / q * q;
+    splits = (K + kchunk - 1) / kchunk;
+    if (splits <= 1) return gemm<true, TB, EPI_F32>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, out, N, s, tc_err);
+    cudaError_t e;
+    if (tc && N == 16) {
+        e = tc5::launch<true, TB, EPI_F32, 16>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, ws, N, splits, kchunk,
+                                               tc_err, s);
+    } else if (tc) {
+        e = tc5::launch<true, TB, EPI_F32, 64>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, ws, N, splits, kchunk,
+                                               tc_err, s);
+    } else {
+        dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)splits);
+        gemm_bf16_kernel<true, TB, EPI_F32><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, nullptr, nullptr,
+                                                                          0, ws, N, kchunk);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t MN = (int64_t)M * N;
+    sum_splits_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, s>>>(splits, MN, ws, out);
     return cudaGetLastError();
 }
 
@@ -237,22 +553,41 @@ __device__ __forceinline__ float as_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float as_f<bf16>(bf16 v) { return __bfloat162float(v); }
 
+// Column sums out[k] = sum_n wrow[n] Mx[n][k] in two deterministic passes:
+// block b (W threads, thread = column, coalesced) sums rows [b R, (b+1) R) into
+// part[b][k]; one pass over the blocks then adds the parts in order.
+constexpr int kColRows = 128;
+
 template <typename T>
-__global__ void colsum_kernel(int N, int W, const T* __restrict__ Mx, const float* __restrict__ wrow, float* out) {
-    const int k = blockIdx.x;
-    __shared__ float red[256];
+__global__ void colsum_part_kernel(int N, int W, const T* __restrict__ Mx, const float* __restrict__ wrow,
+                                   float* part) {
+    const int k = threadIdx.x;
+    if (k >= W) return;
+    const int n0 = blockIdx.x * kColRows, n1 = min(N, n0 + kColRows);
     float s = 0.f;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    for (int n = n0; n < n1; n++) {
         const float v = Mx ? as_f<T>(Mx[(int64_t)n * W + k]) : 1.f;
         s = fmaf(wrow ? wrow[n] : 1.f, v, s);
     }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = red[0];
+    part[(int64_t)blockIdx.x * W + k] = s;
+}
+
+__global__ void colsum_final_kernel(int nb, int W, const float* __restrict__ part, float* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= W) return;
+    float s = 0.f;
+    for (int b = 0; b < nb; b++) s += part[(int64_t)b * W + k];
+    out[k] = s;
+}
+
+template <typename T>
+static cudaError_t colsum(int N, int W, const T* Mx, const float* wrow, float* out, float* part, cudaStream_t s) {
+    const int nb = (N + kColRows - 1) / kColRows;
+    colsum_part_kernel<T><<<nb, W, 0, s>>>(N, W, Mx, wrow, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    colsum_final_kernel<<<(W + 255) / 256, 256, 0, s>>>(nb, W, part, out);
+    return cudaGetLastError();
 }
 
 __global__ void sum_kernel(int N, const float* __restrict__ v, float* out) {
@@ -295,10 +630,22 @@ __global__ void refresh_kernel(int W, const float* __restrict__ th, bf16* W1b, b
     if (i < W) W4b[i] = __float2bfloat16(W4[i]);
 }
 
+// Adam step counter and bias corrections on the device (so that training
+// steps can be captured in a CUDA graph): ac[0] = step (as unsigned int),
+// ac[1] = 1 / (1 - 0.9^step), ac[2] = 1 / (1 - 0.999^step).
+__global__ void adam_prep_kernel(float* ac) {
+    unsigned int* st = reinterpret_cast<unsigned int*>(ac);
+    const unsigned int k = *st + 1u;
+    *st = k;
+    ac[1] = (float)(1.0 / (1.0 - pow(0.9, (double)k)));
+    ac[2] = (float)(1.0 / (1.0 - pow(0.999, (double)k)));
+}
+
 __global__ void adam_kernel(int64_t P, float* th, const float* __restrict__ g, float* m, float* v, float lr,
-                            float c1, float c2) {
+                            const float* __restrict__ ac) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
+    const float c1 = ac[1], c2 = ac[2];
     const float gi = g[i];
     const float mi = 0.9f * m[i] + 0.1f * gi;
     const float vi = 0.999f * v[i] + 0.001f * gi * gi;
@@ -367,6 +714,11 @@ struct fs_mlp {
     fs::bf16 *W1b, *W2b, *W3b, *W4b;
     fs::bf16 *Xb, *A1, *A2, *A3, *dZa, *dZb;
     float *y, *dy, *sq, *g16, *stdz, *loss;
+    float* adamc;   // [4] Adam step counter and bias corrections (device)
+    float* ws;      // split-K partials: kMaxSplits x W x max(W, kInPad)
+    int tc5;        // 1: tcgen05 GEMMs, 0: mma.sync GEMMs
+    int* tc_err;    // device flag set by a tcgen05 GEMM whose mbarrier wait ran out
+    float* part;    // column-sum partials: ceil(cap / kColRows) x W
 };
 
 namespace {
@@ -380,11 +732,14 @@ fs_status mlp_fail(cudaError_t e, const char* what) {
 
 void mlp_free(fs_mlp* m) {
     void* ps[] = {m->th, m->gr, m->m, m->v, m->W1b, m->W2b, m->W3b, m->W4b, m->Xb, m->A1, m->A2, m->A3,
-                  m->dZa, m->dZb, m->y, m->dy, m->sq, m->g16, m->stdz, m->loss};
+                  m->dZa, m->dZb, m->y, m->dy, m->sq, m->g16, m->stdz, m->loss, m->adamc, m->ws, m->part,
+                  m->tc_err};
     for (void* p : ps) cudaFree(p);
 }
 
 // Forward pass for N <= cap rows of X (fp32 [N][5]); activations kept.
+int* tcp(fs_mlp* m) { return m->tc5 ? m->tc_err : nullptr; }
+
 cudaError_t mlp_forward(fs_mlp* m, const float* X, int N, float* y, bool destandardize) {
     using namespace fs;
     const int W = m->W;
@@ -396,12 +751,12 @@ cudaError_t mlp_forward(fs_mlp* m, const float* X, int N, float* y, bool destand
     const float* b4 = b3 + W + W;
     cudaError_t e;
     if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, kInPad, m->Xb, kInPad, m->W1b, kInPad, b1, nullptr, 0, m->A1,
-                                                     W, s)) != cudaSuccess)
+                                                     W, s, tcp(m))) != cudaSuccess)
         return e;
-    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A1, W, m->W2b, W, b2, nullptr, 0, m->A2, W, s)) !=
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A1, W, m->W2b, W, b2, nullptr, 0, m->A2, W, s, tcp(m))) !=
         cudaSuccess)
         return e;
-    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A2, W, m->W3b, W, b3, nullptr, 0, m->A3, W, s)) !=
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A2, W, m->W3b, W, b3, nullptr, 0, m->A3, W, s, tcp(m))) !=
         cudaSuccess)
         return e;
     output_kernel<<<(unsigned)(((int64_t)N * 32 + 255) / 256), 256, 0, s>>>(N, W, m->A3, m->W4b, b4,
@@ -432,29 +787,26 @@ cudaError_t mlp_backward(fs_mlp* m, const float* X, const float* t, int N, bool 
     float* gW4 = gb3 + W;
     float* gb4 = gW4 + W;
     // output layer
-    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->A3, m->dy, gW4);
+    if ((e = colsum<bf16>(N, W, m->A3, m->dy, gW4, m->part, s)) != cudaSuccess) return e;
     sum_kernel<<<1, 256, 0, s>>>(N, m->dy, gb4);
     dz_last_kernel<<<(unsigned)(((int64_t)N * W + 255) / 256), 256, 0, s>>>(N, W, m->dy, m->W4b, m->A3, m->dZa);
     // layer 3: dW3 = dZ3^T A2, db3, dZ2 = (dZ3 W3) * (A2 > 0)
-    if ((e = gemm<true, true, EPI_F32>(W, W, N, m->dZa, W, m->A2, W, nullptr, nullptr, 0, gW3, W, s)) != cudaSuccess)
-        return e;
-    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->dZa, nullptr, gb3);
-    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZa, W, m->W3b, W, nullptr, m->A2, W, m->dZb, W, s)) !=
+    if ((e = gemm_wgrad<true>(W, W, N, m->dZa, W, m->A2, W, gW3, m->ws, kMaxSplits, s, tcp(m))) != cudaSuccess) return e;
+    if ((e = colsum<bf16>(N, W, m->dZa, nullptr, gb3, m->part, s)) != cudaSuccess) return e;
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZa, W, m->W3b, W, nullptr, m->A2, W, m->dZb, W, s, tcp(m))) !=
         cudaSuccess)
         return e;
     // layer 2
-    if ((e = gemm<true, true, EPI_F32>(W, W, N, m->dZb, W, m->A1, W, nullptr, nullptr, 0, gW2, W, s)) != cudaSuccess)
-        return e;
-    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->dZb, nullptr, gb2);
-    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZb, W, m->W2b, W, nullptr, m->A1, W, m->dZa, W, s)) !=
+    if ((e = gemm_wgrad<true>(W, W, N, m->dZb, W, m->A1, W, gW2, m->ws, kMaxSplits, s, tcp(m))) != cudaSuccess) return e;
+    if ((e = colsum<bf16>(N, W, m->dZb, nullptr, gb2, m->part, s)) != cudaSuccess) return e;
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZb, W, m->W2b, W, nullptr, m->A1, W, m->dZa, W, s, tcp(m))) !=
         cudaSuccess)
         return e;
     // layer 1 (padded input)
-    if ((e = gemm<true, true, EPI_F32>(W, kInPad, N, m->dZa, W, m->Xb, kInPad, nullptr, nullptr, 0, m->g16, kInPad,
-                                       s)) != cudaSuccess)
+    if ((e = gemm_wgrad<true>(W, kInPad, N, m->dZa, W, m->Xb, kInPad, m->g16, m->ws, kMaxSplits, s, tcp(m))) != cudaSuccess)
         return e;
     unpad_kernel<<<(W * 5 + 255) / 256, 256, 0, s>>>(W, m->g16, gW1);
-    colsum_kernel<bf16><<<W, 256, 0, s>>>(N, W, m->dZa, nullptr, gb1);
+    if ((e = colsum<bf16>(N, W, m->dZa, nullptr, gb1, m->part, s)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -503,7 +855,13 @@ fs_status fs_mlp_create(fs_mlp** out, int width, int max_batch, uint64_t seed, v
         (e = cudaMalloc(&m->sq, sizeof(float) * max_batch)) != cudaSuccess ||
         (e = cudaMalloc(&m->g16, sizeof(float) * W * fs::kInPad)) != cudaSuccess ||
         (e = cudaMalloc(&m->stdz, sizeof(float) * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&m->loss, sizeof(float) * 1)) != cudaSuccess) {
+        (e = cudaMalloc(&m->loss, sizeof(float) * 1)) != cudaSuccess ||
+        (e = cudaMalloc(&m->adamc, sizeof(float) * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&m->tc_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&m->ws, sizeof(float) * fs::kMaxSplits * W * (W > fs::kInPad ? W : fs::kInPad))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&m->part, sizeof(float) * ((max_batch + fs::kColRows - 1) / fs::kColRows) * W)) !=
+            cudaSuccess) {
         mlp_free(m);
         delete m;
         return mlp_fail(e, "fs_mlp_create: cudaMalloc");
@@ -512,6 +870,8 @@ fs_status fs_mlp_create(fs_mlp** out, int width, int max_batch, uint64_t seed, v
     fs::init_kernel<<<(unsigned)((m->P + 255) / 256), 256, 0, m->stream>>>(W, seed, m->th);
     if ((e = cudaMemsetAsync(m->m, 0, sizeof(float) * m->P, m->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(m->v, 0, sizeof(float) * m->P, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->adamc, 0, sizeof(float) * 4, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(m->stdz, one, sizeof(one), cudaMemcpyHostToDevice, m->stream)) != cudaSuccess ||
         (e = mlp_refresh(m)) != cudaSuccess || (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
         mlp_free(m);
@@ -537,6 +897,7 @@ fs_status fs_mlp_set_params(fs_mlp* m, const float* theta_dev) {
     if (e != cudaSuccess || (e = mlp_refresh(m)) != cudaSuccess) return mlp_fail(e, "fs_mlp_set_params");
     const float one[4] = {0.f, 1.f, 0.f, 0.f};
     if ((e = cudaMemcpyAsync(m->stdz, one, sizeof(one), cudaMemcpyHostToDevice, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->adamc, 0, sizeof(float) * 4, m->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(m->stream)) != cudaSuccess)
         return mlp_fail(e, "fs_mlp_set_params");
     m->step = 0;
@@ -549,6 +910,25 @@ fs_status fs_mlp_get_params(fs_mlp* m, float* theta_dev) {
     cudaError_t e = cudaMemcpyAsync(theta_dev, m->th, sizeof(float) * m->P, cudaMemcpyDeviceToDevice, m->stream);
     if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_get_params");
     return FS_OK;
+}
+
+fs_status fs_mlp_set_tensor_path(fs_mlp* m, int tcgen05) {
+    fs::set_error(FS_OK, "");
+    if (!m || (tcgen05 != 0 && tcgen05 != 1)) return fs::set_error(FS_EINVAL, "fs_mlp_set_tensor_path: bad argument");
+    m->tc5 = tcgen05;
+    return FS_OK;
+}
+
+fs_status fs_mlp_tensor_status(fs_mlp* m, int* timed_out) {
+    fs::set_error(FS_OK, "");
+    if (!m || !timed_out) return fs::set_error(FS_EINVAL, "fs_mlp_tensor_status: NULL argument");
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_tensor_status");
+    *timed_out = h;
+    return h ? fs::set_error(FS_ETIMEOUT, "fs_mlp_tensor_status: a tcgen05 GEMM timed out waiting for its MMAs")
+             : FS_OK;
 }
 
 // The network's stream (library-internal; the screened-step graph builder
@@ -595,10 +975,9 @@ fs_status fs_mlp_train(fs_mlp* m, const float* X_dev, const float* t_dev, int N,
         cudaError_t e = mlp_backward(m, X_dev, t_dev, N, true);
         if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_train backward");
         m->step++;
-        const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)m->step)));
-        const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)m->step)));
-        fs::adam_kernel<<<(unsigned)((m->P + 255) / 256), 256, 0, m->stream>>>(m->P, m->th, m->gr, m->m, m->v, lr, c1,
-                                                                                c2);
+        fs::adam_prep_kernel<<<1, 1, 0, m->stream>>>(m->adamc);
+        fs::adam_kernel<<<(unsigned)((m->P + 255) / 256), 256, 0, m->stream>>>(m->P, m->th, m->gr, m->m, m->v, lr,
+                                                                                m->adamc);
         if ((e = cudaGetLastError()) != cudaSuccess || (e = mlp_refresh(m)) != cudaSuccess)
             return mlp_fail(e, "fs_mlp_train update");
         if (loss_dev && (e = cudaMemcpyAsync(loss_dev + it, m->loss, sizeof(float), cudaMemcpyDeviceToDevice,

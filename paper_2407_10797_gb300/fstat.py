@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_graph_run.argtypes = [_vp, C.c_int]
         _rp = C.POINTER(fs_sample_ring)
         L.fs_pso_record.argtypes = [_vp, _sw, _rp, C.c_int]
+        L.fs_mlp_train_graph_build.argtypes = [C.POINTER(_vp), C.c_int, _rp, C.c_int, C.c_float, C.POINTER(_vp)]
         L.fs_pso_graph_build_ex.argtypes = [_vp, _sw, _ep, C.c_int, C.c_uint64, C.c_double, C.c_double, C.c_int,
                                             C.c_double, C.c_double, C.c_double, C.c_int, _rp, C.c_int,
                                             C.POINTER(_vp), C.c_int, C.c_int, C.POINTER(_vp)]
@@ -101,6 +102,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_mlp_num_params.restype = C.c_int64
         L.fs_mlp_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_uint64, _vp]
         L.fs_mlp_destroy.argtypes = [_vp]
+        L.fs_mlp_set_tensor_path.argtypes = [_vp, C.c_int]
+        L.fs_mlp_tensor_status.argtypes = [_vp, C.POINTER(C.c_int)]
         L.fs_mlp_set_params.argtypes = [_vp, _vp]
         L.fs_mlp_get_params.argtypes = [_vp, _vp]
         L.fs_mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp]
@@ -113,8 +116,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
                      "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
                      "fs_plan_autotune", "fs_pso_autotune", "fs_plan_census", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
-                     "fs_pso_graph_build", "fs_pso_graph_build_ex", "fs_pso_record", "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
-                     "fs_mlp_destroy", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
+                     "fs_pso_graph_build", "fs_pso_graph_build_ex", "fs_pso_record", "fs_mlp_train_graph_build",
+                     "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
+                     "fs_mlp_destroy", "fs_mlp_set_tensor_path", "fs_mlp_tensor_status", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
                      "fs_mlp_loss_grad", "fs_mlp_train", "fs_pso_step_screened"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -462,8 +466,20 @@ def _ring_array(ring):
     return (fs_sample_ring * len(rings))(*[r.c for r in rings])
 
 
+def mlp_train_graph(nets, rings, steps: int, lr: float = 1e-3) -> "Graph":
+    """fs_mlp_train_graph_build: `steps` Adam steps of every network on its ring's
+    whole contents, captured as one graph."""
+    arr = _mlp_array(nets)
+    rarr = _ring_array(rings)
+    if len(arr) != len(rarr):
+        raise ValueError("one ring per network")
+    h = C.c_void_p()
+    _check(load().fs_mlp_train_graph_build(arr, len(arr), rarr, int(steps), float(lr), C.byref(h)))
+    return Graph(h)
+
+
 class Graph:
-    """A captured part of a PSO iteration (fs_graph)."""
+    """A captured part of a PSO iteration or a training round (fs_graph)."""
 
     def __init__(self, h):
         self._h = h
@@ -525,10 +541,22 @@ class MLP:
         except Exception:
             pass
 
+    def set_tensor_path(self, tcgen05: bool):
+        """True: tcgen05 GEMMs (TMEM accumulators); False: mma.sync GEMMs."""
+        _check(self._L.fs_mlp_set_tensor_path(self._h, 1 if tcgen05 else 0))
+
+    def tensor_status(self) -> bool:
+        """True if no tcgen05 GEMM of this network timed out (waits for its stream)."""
+        flag = C.c_int()
+        st = self._L.fs_mlp_tensor_status(self._h, C.byref(flag))
+        return st == FS_OK and flag.value == 0
+
     def params(self):
         import torch
         out = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        self.stream.synchronize()   # out was made on the current stream; the copy runs on the network's
         _check(self._L.fs_mlp_get_params(self._h, _cuda_ptr(out, torch.float32)))
+        self.stream.synchronize()
         return out
 
     def set_params(self, theta):

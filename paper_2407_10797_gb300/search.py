@@ -106,16 +106,19 @@ def box_around(center: np.ndarray, widths, prior: np.ndarray) -> np.ndarray:
 @dataclass
 class SurrogateSpec:
     """Surrogate screening of PSO moves (not in the paper): every exact
-    evaluation adds its (position, F-hat) pairs to a per-stage buffer, the MLP
-    is retrained every `train_every` iterations, and after `warm` iterations
-    each particle takes the best of `n_cand` candidate moves as ranked by the
-    network.  The number of exact F-statistic evaluations is unchanged."""
+    evaluation adds its (position, F-hat) pairs to its box's ring of `buffer`
+    samples (the latest ones: about six iterations of a box's 8 x 40
+    particles at the default), each box's MLP is retrained every
+    `train_every` iterations for `train_steps` full-ring Adam steps, and after
+    `warm` iterations each particle takes the best of `n_cand` candidate moves
+    as ranked by its box's network.  The number of exact F-statistic
+    evaluations is unchanged."""
     n_cand: int = 16
     warm: int = 20
     train_every: int = 10
-    train_steps: int = 40
+    train_steps: int = 20
     lr: float = 1e-3
-    buffer: int = 8192
+    buffer: int = 2048
     width: int = 256
 
 
@@ -229,7 +232,8 @@ class HierarchicalSearch:
         boxes do not.  Every train_every iterations after the warm-up each
         network trains on its box's ring.  With graphs (default) an iteration
         is two captured launches, (evaluate + record) and the step, with the
-        training in between when due; the eager form makes the same calls."""
+        captured training round in between when due; the eager form makes the
+        same calls."""
         import torch
         sp = self.surrogate
         nb = self.n_boxes
@@ -238,13 +242,13 @@ class HierarchicalSearch:
                                stream=self.plan.stream) for k in range(nb)]
         self.mlp = self.mlps[0]
         rings = [fstat.SampleRing(sp.buffer, device=dev) for _ in range(nb)]
-        per_box = (sw.R // nb) * sw.n_part
         step_kw = dict(w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter, c1=self.c1, c2=self.c2, vmax=self.vmax)
         graphs = None
         if self.use_graphs:
             graphs = (sw.graph_build_ex(1 | 2, spec.Np, stage_seed, ring=rings, **step_kw),
                       sw.graph_build_ex(4, spec.Np, stage_seed, **step_kw),
-                      sw.graph_build_ex(8, spec.Np, stage_seed, mlp=self.mlps, n_cand=sp.n_cand, **step_kw))
+                      sw.graph_build_ex(8, spec.Np, stage_seed, mlp=self.mlps, n_cand=sp.n_cand, **step_kw),
+                      fstat.mlp_train_graph(self.mlps, rings, sp.train_steps, sp.lr))
         hist = []
         for it in range(spec.n_iter - 1):
             if graphs:
@@ -254,9 +258,12 @@ class HierarchicalSearch:
                 sw.record(rings)
             screened = it >= sp.warm
             if screened and (it - sp.warm) % sp.train_every == 0:
-                m = min((it + 1) * per_box, sp.buffer)
-                for net, ring in zip(self.mlps, rings):
-                    net.train(ring.x[:m], ring.f[:m], sp.train_steps, sp.lr)
+                # the whole ring: slots not yet written hold NaN targets, which the loss ignores
+                if graphs:
+                    graphs[3].run(1)
+                else:
+                    for net, ring in zip(self.mlps, rings):
+                        net.train(ring.x, ring.f, sp.train_steps, sp.lr)
             if graphs:
                 graphs[2 if screened else 1].run(1)
             elif screened:

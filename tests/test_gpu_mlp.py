@@ -74,3 +74,59 @@ def test_training_fits_smooth_target_and_is_deterministic(fst):
     rel = np.sqrt(np.mean((y - t.cpu().numpy()) ** 2)) / np.std(t.cpu().numpy())
     assert rel < 0.15
     assert np.array_equal(runs[0][2], runs[1][2]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("W,N", [(256, 1000), (256, 77), (128, 300)])
+def test_tcgen05_path_matches_oracle_and_mma_sync(fst, W, N):
+    """The tcgen05 GEMMs (TMEM accumulators) give the oracle's forward pass,
+    loss and gradients to the same bf16 tolerance as the mma.sync GEMMs, and
+    agree with them closely (fp32 sums in another order)."""
+    theta = rand_theta(W, 4)
+    theta32 = theta.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(5)
+    X = rng.random((N, 5)).astype(np.float32)
+    t = (np.cos(3 * X[:, 0]) - X[:, 3] + X[:, 1] * X[:, 2]).astype(np.float32)
+    t[::11] = np.nan
+    out = {}
+    for tc in (False, True):
+        net = fst.MLP(W, max_batch=2048, seed=0)
+        net.set_tensor_path(tc)
+        net.set_params(torch.from_numpy(theta32.astype(np.float32)).cuda())
+        y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+        L, g = net.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+        assert net.tensor_status()
+        out[tc] = (y, float(L), g.cpu().numpy().astype(np.float64))
+        net.close()
+    yo = M.forward(theta32, X.astype(np.float64), W)
+    Lo, go = M.loss_and_grad(theta32, X.astype(np.float64), t.astype(np.float64), W)
+    scale = np.max(np.abs(yo))
+    y, L, g = out[True]
+    assert np.max(np.abs(y - yo)) <= 1e-2 * scale
+    assert np.median(np.abs(y - yo)) <= 1e-4 * scale
+    assert L == pytest.approx(Lo, rel=1e-2)
+    o = 0
+    for name, shp in M.param_shapes(W):
+        n = int(np.prod(shp))
+        assert np.linalg.norm(g[o:o + n] - go[o:o + n]) <= 1e-2 * np.linalg.norm(go[o:o + n]) + 1e-12, name
+        o += n
+    y0, L0, g0 = out[False]
+    assert np.max(np.abs(y - y0)) <= 1e-2 * scale
+    assert np.linalg.norm(g - g0) <= 1e-2 * np.linalg.norm(g0)
+
+
+def test_tcgen05_training_is_deterministic_and_fits(fst):
+    rng = np.random.default_rng(7)
+    X = torch.from_numpy(rng.random((4096, 5)).astype(np.float32)).cuda()
+    Xc = X.cpu().numpy()
+    t = torch.from_numpy((5.0 + 2.0 * (np.sin(3 * Xc[:, 0]) + Xc[:, 1] ** 2 - Xc[:, 2] * Xc[:, 3]))
+                         .astype(np.float32)).cuda()
+    runs = []
+    for _ in range(2):
+        net = fst.MLP(256, max_batch=4096, seed=13)
+        net.set_tensor_path(True)
+        losses = net.train(X, t, steps=200, lr=2e-3).cpu().numpy()
+        assert net.tensor_status()
+        runs.append((losses, net.params().cpu().numpy()))
+        net.close()
+    assert runs[0][0][-1] < 0.05 * runs[0][0][0]
+    assert np.array_equal(runs[0][1], runs[1][1])

@@ -130,3 +130,31 @@ def test_captured_screened_iteration_matches_eager(env):
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
     for a, b in zip(out[0][2], out[1][2]):
         assert torch.equal(a, b)
+
+
+def test_training_graph_matches_eager(env):
+    """A captured training round (every network on its whole ring, empty
+    slots ignored) replayed twice equals the same eager calls: the Adam step
+    count and bias corrections live on the device."""
+    fstat, plan, s, box = env
+    with torch.cuda.stream(s):
+        sw = fstat.Swarm(plan, 4, 40, box)
+        sw.init(8)
+        sw.evaluate(4)
+        rings = [fstat.SampleRing(512), fstat.SampleRing(512)]
+        for _ in range(3):
+            sw.record(rings)                   # 240 of 512 slots written per ring
+    torch.cuda.synchronize()
+    eager = nets(fstat, s, (31, 32))
+    captured = nets(fstat, s, (31, 32))
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            for net, r in zip(eager, rings):
+                net.train(r.x, r.f, 3, 2e-3)
+        g = fstat.mlp_train_graph(captured, rings, 3, 2e-3)
+        g.run(2)
+    torch.cuda.synchronize()
+    for a, b in zip(eager, captured):
+        assert torch.equal(a.params(), b.params())
+    assert not torch.equal(eager[0].params(), nets(fstat, s, (31,))[0].params())   # training moved the weights
+    g.close()
