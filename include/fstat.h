@@ -165,6 +165,8 @@ typedef struct {
                               sin(lat), lon [rad], e0; x maps linearly onto it */
     double q;              /* mass ratio of every particle */
     unsigned int* iter;    /* device iteration counter, used by fs_pso_step(iteration < 0) and the graph */
+    int run0;              /* global index of run 0: the Philox counters use run0 + r, so a process that
+                              holds runs [run0, run0 + R) of a larger search draws their numbers (0: default) */
 } fs_swarm;
 
 /* Initial state: x ~ U[0,1)^5, v ~ U[-x, 1-x) (Sec. III.A), pbest_x = x,

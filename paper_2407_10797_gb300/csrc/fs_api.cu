@@ -528,6 +528,8 @@ static fs_status check_swarm(const fs_swarm* w) {
     if (!w || w->R < 0 || w->n_part < 1 || !w->x || !w->v || !w->pbest_x || !w->pbest_f || !w->fit)
         return fail(FS_EINVAL, "swarm: need R >= 0, n_part >= 1 and non-NULL state arrays");
     if ((int64_t)w->R * w->n_part > 65535 * 8) return fail(FS_EINVAL, "swarm: R * n_part too large");
+    if (w->run0 < 0 || (int64_t)w->run0 + w->R > (1 << 20))
+        return fail(FS_EINVAL, "swarm: need 0 <= run0 and run0 + R <= 2^20 (the Philox run field)");
     return FS_OK;
 }
 
@@ -536,7 +538,8 @@ fs_status fs_pso_init(fs_plan* p, const fs_swarm* w, uint64_t seed) {
     if (!p) return fail(FS_EINVAL, "fs_pso_init: plan is NULL");
     fs_status st = check_swarm(w);
     if (st != FS_OK) return st;
-    cudaError_t e = fs::launch_pso_init(w->R, w->n_part, seed, w->x, w->v, w->pbest_x, w->pbest_f, w->fit, p->stream);
+    cudaError_t e = fs::launch_pso_init(w->R, w->n_part, seed, w->x, w->v, w->pbest_x, w->pbest_f, w->fit, w->run0,
+                                        p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso init launch");
     if (w->iter && (e = cudaMemsetAsync(w->iter, 0, sizeof(unsigned int), p->stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync(iter)");
@@ -587,7 +590,7 @@ fs_status fs_pso_step(fs_plan* p, const fs_swarm* w, uint64_t seed, int iteratio
     cudaError_t e = fs::launch_pso_step(w->R, w->n_part, seed, dev_iter ? w->iter : nullptr,
                                         dev_iter ? 0u : (unsigned int)iteration, w0, w1, n_iter, c1, c2, vmax, w->x,
                                         w->v, w->pbest_x, w->pbest_f, w->fit, lbest_dev,
-                                        dev_iter ? w->iter : nullptr, p->stream);
+                                        dev_iter ? w->iter : nullptr, w->run0, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso step launch");
     return FS_OK;
 }
@@ -613,7 +616,7 @@ fs_status fs_pso_step_screened(fs_plan* p, const fs_swarm* w, fs_mlp* const* mlp
     e = fs::launch_pso_screened(w->R, w->n_part, n_cand, seed, dev_iter ? w->iter : nullptr,
                                 dev_iter ? 0u : (unsigned int)iteration, w0, w1, n_iter, c1, c2, vmax, w->x, w->v,
                                 w->pbest_x, w->pbest_f, w->fit, p->cand_x, p->cand_v, p->cand_in, p->cand_inside,
-                                p->cand_score, mlps, n_mlp, dev_iter ? w->iter : nullptr, p->stream);
+                                p->cand_score, mlps, n_mlp, dev_iter ? w->iter : nullptr, w->run0, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "screened step");
     return FS_OK;
 }

@@ -84,20 +84,20 @@ cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32,
                               cudaStream_t s);
 int mixed_span();   // bins per H/T slot of the mixed path
 cudaError_t launch_pso_init(int R, int Np, unsigned long long seed, double* x, double* v, double* pbx, double* pbf,
-                            double* fit, cudaStream_t s);
+                            double* fit, int run0, cudaStream_t s);
 cudaError_t launch_pso_map(int R, int Np, const double* x, const double* box, double q, ::fs_params* out,
                            cudaStream_t s);
 cudaError_t launch_pso_fitness(int n, const double* F, int Np, double* fit, cudaStream_t s);
 cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsigned int* iter_dev, unsigned int iter_host,
                             double w0, double w1, int n_iter, double c1, double c2, double vmax, double* x, double* v,
                             double* pbx, double* pbf, const double* fit, int* lbest, unsigned int* iter_advance,
-                            cudaStream_t s);
+                            int run0, cudaStream_t s);
 cudaError_t launch_pso_best(int R, int Np, const double* pbf, double* best_f, int* best_i, cudaStream_t s);
 cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, const unsigned int* iter_dev,
                                 unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2,
                                 double vmax, double* x, double* v, double* pbx, double* pbf, const double* fit,
                                 double* cx, double* cv, float* cin, unsigned char* inside, float* score,
-                                ::fs_mlp* const* mlps, int n_mlp, unsigned int* iter_advance, cudaStream_t s);
+                                ::fs_mlp* const* mlps, int n_mlp, unsigned int* iter_advance, int run0, cudaStream_t s);
 cudaError_t launch_pso_record(int n, const double* x, const double* fit, float* rx, float* rf, int cap,
                               unsigned long long* count, cudaStream_t s);
 cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);

@@ -40,14 +40,14 @@ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
 
 // x ~ U[0,1)^D, v ~ U[-x, 1-x): counter (0xFFFFFFFF, particle, dim, run).
 __global__ void pso_init_kernel(int R, int Np, int D, unsigned long long seed, double* x, double* v, double* pbx,
-                                double* pbf, double* fit) {
+                                double* pbf, double* fit, int run0) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = (int64_t)R * Np * D;
     if (i >= n) return;
     const int j = (int)(i % D);
     const int p = (int)((i / D) % Np);
     const int r = (int)(i / ((int64_t)D * Np));
-    uint32_t c[4] = {0xFFFFFFFFu, (uint32_t)p, (uint32_t)j, (uint32_t)r};
+    uint32_t c[4] = {0xFFFFFFFFu, (uint32_t)p, (uint32_t)j, (uint32_t)(r + run0)};
     philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     const double u1 = u53(c[0], c[1]), u2 = u53(c[2], c[3]);
     x[i] = u1;
@@ -116,7 +116,7 @@ __global__ void pso_pbest_kernel(int R, int Np, int D, const double* __restrict_
 __global__ void pso_move_kernel(int R, int Np, int D, unsigned long long seed, const unsigned int* iter_dev,
                                 unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2,
                                 double vmax, double* x, double* v, const double* __restrict__ pbx,
-                                const double* __restrict__ pbf, int* lbest_out) {
+                                const double* __restrict__ pbf, int* lbest_out, int run0) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= R * Np) return;
     const unsigned int it = iter_dev ? *iter_dev : iter_host;
@@ -138,7 +138,7 @@ __global__ void pso_move_kernel(int R, int Np, int D, unsigned long long seed, c
     if (lbest_out) lbest_out[i] = best;
     const int64_t li = (int64_t)r * Np + best;
     for (int j = 0; j < D; j++) {
-        uint32_t c[4] = {it, (uint32_t)p, (uint32_t)j, (uint32_t)r};
+        uint32_t c[4] = {it, (uint32_t)p, (uint32_t)j, (uint32_t)(r + run0)};
         philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
         const double r1 = u53(c[0], c[1]), r2 = u53(c[2], c[3]);
         const int64_t ij = (int64_t)i * D + j;
@@ -168,7 +168,7 @@ __global__ void pso_candidates_kernel(int R, int Np, int D, int C, unsigned long
                                       int n_iter, double c1, double c2, double vmax, const double* __restrict__ x,
                                       const double* __restrict__ v, const double* __restrict__ pbx,
                                       const double* __restrict__ pbf, double* cx, double* cv, float* cin,
-                                      unsigned char* inside) {
+                                      unsigned char* inside, int run0) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)R * Np * C) return;
     const int c = (int)(idx % C);
@@ -191,7 +191,7 @@ __global__ void pso_candidates_kernel(int R, int Np, int D, int C, unsigned long
     const int64_t li = (int64_t)r * Np + best;
     bool in = true;
     for (int j = 0; j < D; j++) {
-        uint32_t ctr[4] = {it, (uint32_t)p, (uint32_t)j, (uint32_t)r | ((uint32_t)c << 20)};
+        uint32_t ctr[4] = {it, (uint32_t)p, (uint32_t)j, (uint32_t)(r + run0) | ((uint32_t)c << 20)};
         philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
         const double r1 = u53(ctr[0], ctr[1]), r2 = u53(ctr[2], ctr[3]);
         const int64_t ij = (int64_t)i * D + j;
@@ -260,10 +260,10 @@ __global__ void pso_best_kernel(int R, int Np, const double* __restrict__ pbf, d
 }
 
 cudaError_t launch_pso_init(int R, int Np, unsigned long long seed, double* x, double* v, double* pbx, double* pbf,
-                            double* fit, cudaStream_t s) {
+                            double* fit, int run0, cudaStream_t s) {
     const int64_t n = (int64_t)R * Np * 5;
     if (n == 0) return cudaSuccess;
-    pso_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, Np, 5, seed, x, v, pbx, pbf, fit);
+    pso_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, Np, 5, seed, x, v, pbx, pbf, fit, run0);
     return cudaGetLastError();
 }
 
@@ -284,12 +284,12 @@ cudaError_t launch_pso_fitness(int n, const double* F, int Np, double* fit, cuda
 cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsigned int* iter_dev, unsigned int iter_host,
                             double w0, double w1, int n_iter, double c1, double c2, double vmax, double* x, double* v,
                             double* pbx, double* pbf, const double* fit, int* lbest, unsigned int* iter_advance,
-                            cudaStream_t s) {
+                            int run0, cudaStream_t s) {
     const int n = R * Np;
     if (n == 0) return cudaSuccess;
     pso_pbest_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, x, fit, pbx, pbf);
     pso_move_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, seed, iter_dev, iter_host, w0, w1, n_iter, c1, c2, vmax,
-                                                    x, v, pbx, pbf, lbest);
+                                                    x, v, pbx, pbf, lbest, run0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !iter_advance) return e;
     pso_advance_kernel<<<1, 1, 0, s>>>(iter_advance);
@@ -325,14 +325,14 @@ cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, c
                                 unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2,
                                 double vmax, double* x, double* v, double* pbx, double* pbf, const double* fit,
                                 double* cx, double* cv, float* cin, unsigned char* inside, float* score,
-                                fs_mlp* const* mlps, int n_mlp, unsigned int* iter_advance, cudaStream_t s) {
+                                fs_mlp* const* mlps, int n_mlp, unsigned int* iter_advance, int run0, cudaStream_t s) {
     const int n = R * Np;
     if (n == 0) return cudaSuccess;
     pso_pbest_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, x, fit, pbx, pbf);
     const int64_t nc = (int64_t)n * C;
     pso_candidates_kernel<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(R, Np, 5, C, seed, iter_dev, iter_host, w0, w1,
                                                                        n_iter, c1, c2, vmax, x, v, pbx, pbf, cx, cv,
-                                                                       cin, inside);
+                                                                       cin, inside, run0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // network g ranks the candidates of runs [g R / n_mlp, (g + 1) R / n_mlp), which are contiguous

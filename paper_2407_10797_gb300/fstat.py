@@ -46,7 +46,7 @@ class fs_sample_ring(C.Structure):
 
 class fs_swarm(C.Structure):
     _fields_ = [("R", C.c_int), ("n_part", C.c_int), ("x", _vp), ("v", _vp), ("pbest_x", _vp),
-                ("pbest_f", _vp), ("fit", _vp), ("box", _vp), ("q", C.c_double), ("iter", _vp)]
+                ("pbest_f", _vp), ("fit", _vp), ("box", _vp), ("q", C.c_double), ("iter", _vp), ("run0", C.c_int)]
 
 
 def load(build_if_missing: bool = True) -> C.CDLL:
@@ -355,7 +355,7 @@ class Swarm:
     box: float64 [R, 5, 2] search boxes (lo, hi) of (M_c [Msun], t_c [s],
     sin(lat), lon [rad], e0)."""
 
-    def __init__(self, plan: "Plan", R: int, n_part: int, box, q: float = 1.0):
+    def __init__(self, plan: "Plan", R: int, n_part: int, box, q: float = 1.0, run0: int = 0):
         import torch
         self.plan = plan
         self.R, self.n_part = int(R), int(n_part)
@@ -372,7 +372,7 @@ class Swarm:
         self.best_i = torch.zeros(R, dtype=torch.int32, device=dev)
         self.c = fs_swarm(self.R, self.n_part, self.x.data_ptr(), self.v.data_ptr(), self.pbest_x.data_ptr(),
                           self.pbest_f.data_ptr(), self.fit.data_ptr(), self.box.data_ptr(), float(q),
-                          self.iter.data_ptr())
+                          self.iter.data_ptr(), int(run0))
 
     def set_box(self, box):
         self.box.copy_(torch_tensor(box).reshape(self.R, 5, 2))

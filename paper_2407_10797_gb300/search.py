@@ -133,12 +133,31 @@ class StageResult:
     variant: int = -1      # launch variant of the fused kernel this stage used
 
 
+class Comm:
+    """The search's only exchange between processes: gathering every
+    process's box winners at the end of a stage (torch.distributed, any
+    backend; objects of a few KB)."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self._dist = dist
+        self.group = group
+        self.rank = dist.get_rank(group)
+        self.world = dist.get_world_size(group)
+
+    def allgather(self, obj) -> list:
+        out = [None] * self.world
+        self._dist.all_gather_object(out, obj, group=self.group)
+        return out
+
+
 class HierarchicalSearch:
     def __init__(self, plan: "fstat.Plan", prior: S.Prior, stages: list[StageSpec] | None = None,
                  n_boxes: int = 16, runs_per_box: int = 8, n_part: int = 40, seed: int = 0, q: float = 1.0,
                  checkpoint_dir: str | None = None, c1: float = 2.0, c2: float = 2.0, vmax: float = 0.5,
                  bounds: np.ndarray | None = None, surrogate: SurrogateSpec | None = None,
-                 autotune: bool | None = None, use_graphs: bool = True, record_history: bool = False):
+                 autotune: bool | None = None, use_graphs: bool = True, record_history: bool = False,
+                 comm: "Comm | None" = None):
         """bounds: optional [5, 2] search bounds overriding the prior's (a zero
         width pins a coordinate).  autotune: time the fused kernel's launch
         variants on each stage's first swarm and use the fastest; None = only
@@ -146,7 +165,8 @@ class HierarchicalSearch:
         differ by rounding, which can steer a PSO run differently).  use_graphs:
         replay captured iterations (eager launches otherwise; same results).
         record_history: keep the best fitness after every iteration of a
-        surrogate-screened stage in `history`."""
+        surrogate-screened stage in `history`.  comm: split every stage's boxes
+        over processes (Comm), one GPU each; None = this process runs all."""
         self.plan = plan
         self.prior = prior
         self.bounds = None if bounds is None else np.asarray(bounds, dtype=np.float64)
@@ -163,6 +183,7 @@ class HierarchicalSearch:
         self.autotune = (plan.mode == fstat.FS_MIXED) if autotune is None else bool(autotune)
         self.use_graphs = use_graphs
         self.record_history = record_history
+        self.comm = comm
 
     # ---------------------------------------------------------------- boxes
     def stage_boxes(self, i: int) -> np.ndarray:
@@ -190,16 +211,52 @@ class HierarchicalSearch:
         return np.stack([box_around(c, spec.widths, pb) for c in centers])
 
     # ---------------------------------------------------------------- one stage
+    def local_boxes(self) -> tuple[int, int]:
+        """The contiguous block [k0, k1) of boxes this process searches (all of
+        them without a communicator)."""
+        if self.comm is None:
+            return 0, self.n_boxes
+        r, w = self.comm.rank, self.comm.world
+        return self.n_boxes * r // w, self.n_boxes * (r + 1) // w
+
     def run_stage(self, i: int) -> StageResult:
-        import torch
+        """One stage: every process runs the PSO runs of its block of boxes on
+        its GPU; the best of each box's runs (a few hundred bytes per box) is
+        then exchanged, so every process holds the stage's full result and
+        derives the next stage's boxes from it.  The Philox counters use
+        global run indices, so the result does not depend on the number of
+        processes."""
         spec = self.stages[i]
         boxes = self.stage_boxes(i)
-        R = self.n_boxes * self.runs_per_box
-        run_boxes = np.repeat(boxes, self.runs_per_box, axis=0)
-        stage_seed = (self.seed << 8) + i
+        k0, k1 = self.local_boxes()
         t0 = time.perf_counter()
+        local = self._run_boxes(i, boxes, k0, k1) if k1 > k0 else ([], [], -1)
+        seconds = time.perf_counter() - t0
+        winners, wf, variant = local
+        if self.comm is not None:
+            parts = self.comm.allgather((k0, winners, wf, seconds, variant))
+            parts.sort(key=lambda t: t[0])
+            winners = [w for part in parts for w in part[1]]
+            wf = [f for part in parts for f in part[2]]
+            seconds = max(part[3] for part in parts)
+            variant = parts[0][4]
+        res = StageResult(i, spec.Np, boxes.tolist(), winners, wf, seconds, int(variant))
+        if self.comm is None or self.comm.rank == 0:
+            self._save(res)
+        return res
+
+    def _run_boxes(self, i: int, boxes: np.ndarray, k0: int, k1: int):
+        """PSO runs of boxes [k0, k1) of stage i on this process's GPU: the
+        best position (physical parameters) and fitness of each box, and the
+        launch variant used."""
+        import torch
+        spec = self.stages[i]
+        nb = k1 - k0
+        R = nb * self.runs_per_box
+        run_boxes = np.repeat(boxes[k0:k1], self.runs_per_box, axis=0)
+        stage_seed = (self.seed << 8) + i
         with torch.cuda.stream(self.plan.stream):
-            sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q)
+            sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q, run0=k0 * self.runs_per_box)
             sw.init(stage_seed)
             variant = sw.autotune(spec.Np, reps=2)[0] if self.autotune else self.plan.get_variant(spec.Np)
             if self.surrogate is None:
@@ -208,7 +265,7 @@ class HierarchicalSearch:
                 sw.graph_run(spec.n_iter - 1)      # the graph does evaluate + step
                 sw.graph_free()
             else:
-                self._run_screened(sw, spec, stage_seed, i)
+                self._run_screened(sw, spec, stage_seed, i, k0, nb)
             sw.evaluate(spec.Np)               # fitness of the final positions
             sw.step(stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter)   # folds them into pbest
             best_f, best_i = sw.best()
@@ -216,16 +273,14 @@ class HierarchicalSearch:
             bi = best_i.cpu().numpy()
             pbx = sw.pbest_x.cpu().numpy()
         winners, wf = [], []
-        for k in range(self.n_boxes):
+        for k in range(nb):
             runs = np.arange(k * self.runs_per_box, (k + 1) * self.runs_per_box)
             r = runs[int(np.argmax(bf[runs]))]
             winners.append(to_physical(pbx[r, bi[r]], run_boxes[r], self.q).tolist())
             wf.append(float(bf[r]))
-        res = StageResult(i, spec.Np, boxes.tolist(), winners, wf, time.perf_counter() - t0, int(variant))
-        self._save(res)
-        return res
+        return winners, wf, int(variant)
 
-    def _run_screened(self, sw, spec: StageSpec, stage_seed: int, stage: int):
+    def _run_screened(self, sw, spec: StageSpec, stage_seed: int, stage: int, k0: int = 0, nb: int | None = None):
         """n_iter - 1 iterations of evaluate + record + (screened) step with one
         network and one sample ring per search box: positions are normalised
         to each run's box, so the runs of a box share a landscape and the
@@ -236,9 +291,10 @@ class HierarchicalSearch:
         same calls."""
         import torch
         sp = self.surrogate
-        nb = self.n_boxes
+        nb = self.n_boxes if nb is None else nb
         dev = sw.x.device
-        self.mlps = [fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed * 1000 + 97 * stage + k,
+        # one network per box, seeded by the box's global index
+        self.mlps = [fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed * 1000 + 97 * stage + k0 + k,
                                stream=self.plan.stream) for k in range(nb)]
         self.mlp = self.mlps[0]
         rings = [fstat.SampleRing(sp.buffer, device=dev) for _ in range(nb)]
@@ -301,7 +357,9 @@ class HierarchicalSearch:
         return StageResult(**d["result"])
 
     # ---------------------------------------------------------------- all stages
-    def run(self) -> dict:
+    def run(self, extrinsic: bool = True) -> dict:
+        """All stages (resuming from checkpoints); extrinsic: also report the
+        amplitudes and extrinsic parameters at the final best point."""
         self.results = []
         for i in range(len(self.stages)):
             res = self._load(i)
@@ -311,7 +369,7 @@ class HierarchicalSearch:
         last = self.results[-1]
         k = int(np.argmax(last.winner_f))
         return {"best": last.winners[k], "best_F_hat": last.winner_f[k],
-                "extrinsic": self.extrinsic(last.winners[k]),
+                "extrinsic": self.extrinsic(last.winners[k]) if extrinsic else None,
                 "stages": [asdict(r) for r in self.results],
                 "seconds": sum(r.seconds for r in self.results)}
 
