@@ -43,18 +43,18 @@ NP_LIST = (256, 64, 16, 1)
 # Direct form (launch variants 0-2) and the anchored form's bin-by-bin
 # fallback: the template + response + reduction arithmetic of every bin, each
 # of its two FP64 trig evaluations counted as 40.  Anchored form (variants 3,
-# 4), per degree tier (antenna NG, Doppler NE and NQ): 60 + 4 NG + 2 (NE - 1)
-# + 2 NQ, i.e. d^2 1, quartic/quintic phase 4, orbital-phase offset 7, Doppler
-# polynomials 2 (NE - 1) + 2 NQ + 3, fixed-point phase correction 2,
-# exp(2 pi i Phi) from the table and its Taylor series 21, antenna pair
-# 4 NG, z = dw e^{i Phi} 6, seven sums 16 (integer phase steps and
-# conversions not counted).  Keys: the anchor modes of fs_plan_census.
+# 4), per degree tier (antenna degree NG, phase-remainder degree 4 + NR):
+# 47 + 4 NG + 2 NR, i.e. d^2 and d^4 2, remainder polynomial 2 NR + 1, its
+# fixed-point conversion 1, exp(2 pi i Phi) from the table and its Taylor
+# series 21, antenna pair 4 NG, z = dw e^{i Phi} 6, seven sums 16 (integer
+# phase steps and conversions not counted).  Keys: the anchor modes of
+# fs_plan_census.
 FP64_DIRECT_FLOP = 203.0
-FP64_TIER_FLOP = {1: 114.0, 2: FP64_DIRECT_FLOP, 3: 100.0, 4: 92.0}
+FP64_TIER_FLOP = {1: 101.0, 2: FP64_DIRECT_FLOP, 3: 89.0, 4: 81.0, 5: 75.0}
 
 
 def census_sum(counts_by_np):
-    return [int(sum(c[m] for c in counts_by_np.values())) for m in range(5)]
+    return [int(sum(c[m] for c in counts_by_np.values())) for m in range(6)]
 
 
 def flop_per_pbin(counts_by_np, table, direct):

@@ -362,12 +362,13 @@ FS_API fs_status fs_plan_get_variant(fs_plan* plan, int N_p, int global_edges, i
 /* Census of the anchored kernels' evaluation modes for one batch: runs
  * fs_fstat_batch once (F to plan scratch) with the variant the call resolves
  * to, counting in-band particle*bins per tile mode, and returns them in
- * counts[5]: [1] expansion with the wide degrees (FS_FP64) or the FP32
- * polynomial body (FS_MIXED), [2] bin-by-bin fallback, [3] and [4] the mid and
- * narrow degree tiers (FS_FP64 only), [0] unused.  All zero for the direct
- * FS_FP64 variants (0-2), which have no anchors.  Synchronous; must not be
- * called while the plan's stream is being captured.  For roofline accounting
- * (the operation count per bin differs between modes and tiers). */
+ * counts[6]: [2] bin-by-bin fallback; FS_MIXED: [1] FP32 polynomial body;
+ * FS_FP64 anchored variants: the degree tiers (antenna polynomial degree,
+ * phase-remainder degree) [5] (6, 6), [4] (7, 7), [3] (8, 9), [1] (10, 11);
+ * [0] unused.  All zero for the direct FS_FP64 variants (0-2), which have no
+ * anchors.  Synchronous; must not be called while the plan's stream is being
+ * captured.  For roofline accounting (the operation count per bin differs
+ * between modes and tiers). */
 FS_API fs_status fs_plan_census(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
                                 int N_p, int64_t* counts);
 

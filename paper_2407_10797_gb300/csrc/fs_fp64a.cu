@@ -38,17 +38,36 @@ constexpr int kSpanA = kTileA * kTilesA;         // 32768 bins
 constexpr int kWarpsA = 4;                       // warps (particles) per CTA
 constexpr int kTabA = 256;                       // exp(2 pi i j / 256) table
 
+constexpr int kDeg = 12;                         // Taylor degree in the bin offset d computed at an anchor
+
 struct AnchorD {
-    unsigned long long c[4];   // cubic of the orbital-minus-Doppler phase, cycles mod 1 in units of 2^-64
-    double c4, c5;             // quartic and quintic phase terms, cycles per bin^4, bin^5
-    double w[4];               // d(alpha) = sum_j w_j d^j, j = 1..4, rad
-    double e[7];               // Doppler: AD f_a cos^(n)(x_a)/n!, n = 1..7 (cycles)
-    double q[6];               // Doppler: AD df cos^(n)(x_a)/n!, n = 0..5 (cycles per bin)
-    double Fpa, Fxa;           // F+ and Fx at alpha_a
-    double Fd[8][2];           // F+^(n)(alpha_a)/n!, Fx^(n)(alpha_a)/n!, n = 1..8
+    unsigned long long c[4];   // cubic of the total phase (orbital minus Doppler), cycles mod 1, units 2^-64
+    double R[kDeg - 3];        // its degree 4..12 coefficients (cycles per bin^k), FP64
+    double FU[2][kDeg + 1];    // F+ and Fx along the tile as polynomials in d (degree 0..12)
     int ja, lo, hi;            // anchor bin and in-band range [lo, hi) of the tile, relative to the span start
-    int mode;                  // 0: no in-band bin, 2: bin by bin, 1/3/4: expansion (wide/mid/narrow degrees)
+    int mode;                  // 0: no in-band bin, 2: bin by bin, 1/3/4/5: expansion tiers (see expansion_tile)
 };
+
+// p <- p * u, truncated at degree kDeg (u[0] = 0, u of degree 5)
+__device__ __forceinline__ void mul_u(double* p, const double* u) {
+    for (int k = kDeg; k >= 1; k--) {
+        double s = 0.0;
+        for (int j = 1; j <= 5 && j <= k; j++) s = fma(u[j], p[k - j], s);
+        p[k] = s;
+    }
+    p[0] = 0.0;
+}
+
+// Coefficients in d of sum_n a[n] u(d)^n (n = 0..na), u(d) of degree 5 with u[0] = 0,
+// by Horner's scheme on polynomials, truncated at degree kDeg.
+__device__ __forceinline__ void compose(const double* a, int na, const double* u, double* out) {
+    for (int k = 0; k <= kDeg; k++) out[k] = 0.0;
+    out[0] = a[na];
+    for (int n = na - 1; n >= 0; n--) {
+        mul_u(out, u);
+        out[0] += a[n];
+    }
+}
 
 __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, const Particle& P, int64_t span_lo,
                                            int64_t lo, int64_t hi, AnchorD& A) {
@@ -78,58 +97,77 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
     double rest = Tm[1] + Tm[2] + Tm[3] + Tm[4];
     acc += rest - rint(rest);
     // S_n = sum_m [p_m]_n T_m (falling factorials of the exponents p_m of the
-    // terms T_m = c_m f^p_m), so that d^n Phi_orb / df^n = S_n / f^n for n >= 2
-    // and t(f) = t_c + S_1 / f.
+    // terms T_m = c_m f^p_m): d^n Phi_orb / df^n = S_n / f^n for n >= 2 and
+    // t(f) = t_c + S_1 / f.
     const double pm[5] = {-5.0 / 3.0, -1.0, -2.0 / 3.0, -1.0 / 3.0, -34.0 / 9.0};
     double fac[5] = {1.0, 1.0, 1.0, 1.0, 1.0};
-    double S[7];
-#pragma unroll
-    for (int n = 1; n <= 6; n++) {
-        double s = 0.0;
+    double S[kDeg + 1];
+    S[0] = 0.0;
+    for (int n = 1; n <= kDeg; n++) {
+        double sn = 0.0;
 #pragma unroll
         for (int m = 0; m < 5; m++) {
             fac[m] *= pm[m] - (double)(n - 1);
-            s = fma(fac[m], Tm[m], s);
+            sn = fma(fac[m], Tm[m], sn);
         }
-        S[n] = s;
+        S[n] = sn;
     }
     const double inv = 1.0 / fh;
     const double r = g.df * inv;                    // df / f
     const double ta = P.tc + S[1] * inv;            // t(f_a)
-    // Taylor coefficients in d of Phi_orb: S_n r^n / n!
-    const double r2 = r * r, r3 = r2 * r, r4 = r2 * r2, r5 = r4 * r;
     const double Om = kTwoPi / kYearS;
     double sa, ca;
     sincos(fma(Om, ta, g.alpha0), &sa, &ca);
     const double cda = fma(ca, P.clon, sa * P.slon);   // cos(alpha_a - phi)
     const double sda = fma(sa, P.clon, -ca * P.slon);  // sin(alpha_a - phi)
-    acc -= fh * P.AD * cda;
-    A.c[0] = to_fixed(acc);
-    A.c[1] = to_fixed(ta * g.df);
-    A.c[2] = to_fixed_small(0.5 * S[2] * r2);
-    A.c[3] = to_fixed_small(S[3] * r3 * (1.0 / 6.0));
-    A.c4 = S[4] * r4 * (1.0 / 24.0);
-    A.c5 = S[5] * r5 * (1.0 / 120.0);
-    // d(alpha) = Om (t(f_a + d df) - t_a) = Om sum_j S_{j+1} r^j d^j / (f_a j!)
-    const double Omf = Om * inv;
-    A.w[0] = Omf * S[2] * r;
-    A.w[1] = Omf * S[3] * r2 * 0.5;
-    A.w[2] = Omf * S[4] * r3 * (1.0 / 6.0);
-    A.w[3] = Omf * S[5] * r4 * (1.0 / 24.0);
-    // Doppler phase minus its anchor value, x = alpha - phi = x_a + d(alpha):
-    //   AD [f_a (cos x - cos x_a) + d df cos x],  cos^(n)(x_a) cycles through (c, -s, -c, s)
+    // orbital Taylor coefficients in d: O_k = S_k r^k / k! (k >= 2), O_1 = t_a df
+    double O[kDeg + 1];
     {
-        const double cn[8] = {cda, -sda, -cda, sda, cda, -sda, -cda, sda};
-        double fact = 1.0;
-        const double ADfa = P.AD * fh, ADdf = P.AD * g.df;
-#pragma unroll
-        for (int n = 0; n <= 7; n++) {
-            if (n > 0) fact *= (double)n;
-            if (n >= 1) A.e[n - 1] = ADfa * cn[n] / fact;
-            if (n <= 5) A.q[n] = ADdf * cn[n] / fact;
+        double rk = r, kf = 1.0;
+        O[0] = 0.0;
+        O[1] = ta * g.df;
+        for (int k = 2; k <= kDeg; k++) {
+            rk *= r;
+            kf *= (double)k;
+            O[k] = S[k] * rk / kf;
         }
     }
-    // antenna: F(alpha_a + da) = sum_n F^(n)(alpha_a) da^n / n! from the harmonics
+    // orbital-phase offset d(alpha) = Om (t(f_a + d df) - t_a) = sum_{j=1..5} S_{j+1} r^j d^j Om / (f_a j!)
+    double U[6];
+    {
+        const double Omf = Om * inv;
+        double rj = 1.0, jf = 1.0;
+        U[0] = 0.0;
+        for (int j = 1; j <= 5; j++) {
+            rj *= r;
+            jf *= (double)j;
+            U[j] = Omf * S[j + 1] * rj / jf;
+        }
+    }
+    // Doppler phase AD (f_a + d df) cos(x_a + d(alpha)) as a polynomial in d:
+    // cos(x_a + u) = sum_n cos^(n)(x_a) u^n / n!, cos^(n) cycling through (c, -s, -c, s)
+    double Dk[kDeg + 1];
+    {
+        double cn[11];
+        const double cyc[4] = {cda, -sda, -cda, sda};
+        double nf = 1.0;
+        for (int n = 0; n <= 10; n++) {
+            if (n > 0) nf *= (double)n;
+            cn[n] = cyc[n & 3] / nf;
+        }
+        double CU[kDeg + 1];
+        compose(cn, 10, U, CU);
+        const double ADfa = P.AD * fh, ADdf = P.AD * g.df;
+        Dk[0] = ADfa * CU[0];
+        for (int k = 1; k <= kDeg; k++) Dk[k] = fma(ADfa, CU[k], ADdf * CU[k - 1]);
+    }
+    // total phase: the cubic in fixed point (exact steps), degree 4..12 in FP64
+    A.c[0] = to_fixed(acc - Dk[0]);
+    A.c[1] = to_fixed(O[1] - Dk[1]);
+    A.c[2] = to_fixed_small(O[2] - Dk[2]);
+    A.c[3] = to_fixed_small(O[3] - Dk[3]);
+    for (int k = 4; k <= kDeg; k++) A.R[k - 4] = O[k] - Dk[k];
+    // antenna along the tile: F(alpha_a + u) = sum_n F^(n)(alpha_a) u^n / n!, composed with u = d(alpha)
     {
         double ch[5], sh[5];
         ch[1] = ca;
@@ -142,70 +180,66 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
 #pragma unroll
         for (int f = 0; f < 2; f++) {
             const double* H = P.harm[f];
-            double F0 = H[0];
             double uu[5], vv[5];
+            double Fd[11];
+            Fd[0] = H[0];
 #pragma unroll
             for (int h = 1; h <= 4; h++) {
                 uu[h] = H[2 * h - 1] * ch[h] + H[2 * h] * sh[h];    // A cos + B sin
                 vv[h] = H[2 * h] * ch[h] - H[2 * h - 1] * sh[h];    // derivative / h
-                F0 += uu[h];
+                Fd[0] += uu[h];
             }
-            if (f == 0) A.Fpa = F0;
-            else A.Fxa = F0;
-            double fact = 1.0;
-#pragma unroll
-            for (int n = 1; n <= 8; n++) {
-                fact *= (double)n;
+            double nf = 1.0;
+            for (int n = 1; n <= 10; n++) {
+                nf *= (double)n;
                 double sum = 0.0;
 #pragma unroll
                 for (int h = 1; h <= 4; h++) {
                     double hn = 1.0;
-#pragma unroll
                     for (int j = 0; j < n; j++) hn *= (double)h;
                     const int rr = n & 3;
                     const double t = (rr == 0) ? uu[h] : (rr == 1) ? vv[h] : (rr == 2) ? -uu[h] : -vv[h];
                     sum = fma(hn, t, sum);
                 }
-                A.Fd[n - 1][f] = sum / fact;
+                Fd[n] = sum / nf;
             }
+            compose(Fd, 10, U, A.FU[f]);
         }
     }
-    // truncation remainders over |d| <= hmax (20% margin).  The polynomial
-    // degrees in d(alpha) go by tier: narrow (antenna 5, Doppler 4 and 3),
-    // mid (6, 5, 4), wide (8, 7, 5); each tier's remainders (antenna:
-    // (4 da)^(n+1)/(n+1)! times the pattern scale, Doppler: its scale times
-    // da^(n+1)/(n+1)!) must stay below 1e-12 (1e-11 for the wide antenna).
-    const double x = hmax * r;                      // H / f_a
-    const double x5 = x * x * x * x * x;
-    const double rem_phase = 1.2 * fabs(S[6]) * x5 * x * (1.0 / 720.0);   // cycles
-    const double rem_alpha = 1.2 * Omf * fabs(S[6]) * x5 * (1.0 / 120.0);  // rad
-    const double da =
-        1.2 * hmax * (fabs(A.w[0]) + hmax * (fabs(A.w[1]) + hmax * (fabs(A.w[2]) + hmax * fabs(A.w[3]))));
-    const double sE = fabs(P.AD * fh), sQ = fabs(P.AD * g.df) * hmax;
-    double sG = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; i++) sG += fabs(P.harm[0][i]) + fabs(P.harm[1][i]);
-    const double g4 = 4.0 * da;
-    // x^(n+1)/(n+1)! for the degrees used
-    const double da4 = da * da * da * da, da5 = da4 * da, da6 = da5 * da, da8 = da6 * da * da;
-    const double g6 = g4 * g4 * g4 * g4 * g4 * g4, g7 = g6 * g4, g9 = g7 * g4 * g4;
-    const bool narrow = sG * g6 / 720.0 <= 1e-12 && sE * da5 / 120.0 <= 1e-12 && sQ * da4 / 24.0 <= 1e-12;
-    const bool mid = sG * g7 / 5040.0 <= 1e-12 && sE * da6 / 720.0 <= 1e-12 && sQ * da5 / 120.0 <= 1e-12;
-    const bool wide = da <= 0.06 && sG * g9 / 362880.0 <= 1e-11 && sE * da8 / 40320.0 <= 1e-12 &&
-                      sQ * da6 / 720.0 <= 1e-12;
-    const bool finite = isfinite(rem_phase) && isfinite(da) && isfinite(A.c4) && isfinite(A.c5);
-    const bool phase_ok = finite && rem_phase <= 1e-11 && rem_alpha <= 1e-11;
-    A.mode = !phase_ok ? 2 : narrow ? 4 : mid ? 3 : wide ? 1 : 2;
+    // validity: the quintic d(alpha) (remainder from S_7, 20% margin) and the degree-12
+    // truncations (the last two terms over |d| <= hmax) must be negligible; then the
+    // tier is the lowest whose dropped terms, summed over |d| <= hmax, stay below
+    // 1e-13 cycle (phase) and 1e-15 (antenna: on a short segment G2 varies by as little
+    // as ~1e-4 of the pattern's scale, so its error budget is relative to that)
+    const double x = hmax * r;
+    double x6 = x * x * x;
+    x6 *= x6;
+    const double rem_alpha = 1.2 * Om * inv * fabs(S[7]) * x6 * (1.0 / 720.0);
+    double hk[kDeg + 1];
+    hk[0] = 1.0;
+    for (int k = 1; k <= kDeg; k++) hk[k] = hk[k - 1] * hmax;
+    double tG[kDeg + 2], tR[kDeg + 2];   // tails: sum over k >= n of |coef_k| hmax^k
+    tG[kDeg + 1] = 0.0;
+    tR[kDeg + 1] = 0.0;
+    for (int k = kDeg; k >= 0; k--) {
+        tG[k] = tG[k + 1] + (fabs(A.FU[0][k]) + fabs(A.FU[1][k])) * hk[k];
+        tR[k] = tR[k + 1] + (k >= 4 ? fabs(A.R[k - 4]) * hk[k] : 0.0);
+    }
+    const bool finite = isfinite(rem_alpha) && isfinite(tG[0]) && isfinite(tR[4]);
+    const bool converged = finite && rem_alpha <= 1e-13 && tG[kDeg - 1] <= 1e-17 && tR[kDeg - 1] <= 1e-16 &&
+                           fabs(U[1]) * hmax <= 0.1;
+    // tiers (antenna degree NG, phase remainder degree 4 + NR): 5:(6,2) 4:(7,3) 3:(8,5) 1:(10,7)
+    auto ok = [&](int NG, int NR) { return tG[NG + 1] <= 1e-15 && tR[5 + NR] <= 1e-13; };
+    A.mode = !converged ? 2 : ok(6, 2) ? 5 : ok(7, 3) ? 4 : ok(8, 5) ? 3 : ok(10, 7) ? 1 : 2;
 }
 
-// Per-segment antenna polynomials: G1 = c F+ + s Fx, G2 = c Fx - s F+ in powers of d(alpha).
-__device__ __forceinline__ void segment_coeffs_d(const AnchorD& A, double2 rc, double g1[9], double g2[9]) {
-    g1[0] = fma(rc.x, A.Fpa, rc.y * A.Fxa);
-    g2[0] = fma(rc.x, A.Fxa, -rc.y * A.Fpa);
+// Per-segment antenna polynomials in d: G1 = c F+ + s Fx, G2 = c Fx - s F+.
+template <int NG>
+__device__ __forceinline__ void segment_coeffs_d(const AnchorD& A, double2 rc, double g1[NG + 1], double g2[NG + 1]) {
 #pragma unroll
-    for (int n = 1; n <= 8; n++) {
-        g1[n] = fma(rc.x, A.Fd[n - 1][0], rc.y * A.Fd[n - 1][1]);
-        g2[n] = fma(rc.x, A.Fd[n - 1][1], -rc.y * A.Fd[n - 1][0]);
+    for (int n = 0; n <= NG; n++) {
+        g1[n] = fma(rc.x, A.FU[0][n], rc.y * A.FU[1][n]);
+        g2[n] = fma(rc.x, A.FU[1][n], -rc.y * A.FU[0][n]);
     }
 }
 
@@ -234,24 +268,21 @@ __device__ __forceinline__ void cis_fixed(unsigned long long Ft, const double2* 
     sn = fma(t.y, cr, t.x * sr);
 }
 
-// One bin of an expansion tile inside a single segment; NG, NE, NQ are the
-// degrees of the antenna, Doppler (f_a term, without its zero constant) and
-// Doppler (d df term) polynomials in d(alpha).
-template <int NG, int NE, int NQ>
+// One bin of an expansion tile inside a single segment: the phase is the
+// fixed-point cubic Fv plus the FP64 remainder d^4 (R_4 + R_5 d + ... ), NR + 1
+// terms, added as a 2^-48-cycle integer; the antenna pair is two degree-NG
+// polynomials in d.
+template <int NG, int NR>
 __device__ __forceinline__ void bin_d(unsigned long long Fv, double d, double dr, double di, double W,
-                                      const double w[4], double c4, double c5, const double e[7], const double q[6],
-                                      const double g1[9], const double g2[9], const double2* __restrict__ tab,
-                                      double acc[7]) {
+                                      const double Rc[NR + 1], const double g1[NG + 1], const double g2[NG + 1],
+                                      const double2* __restrict__ tab, double acc[7]) {
     const double dd = d * d;
-    const double ext = dd * dd * fma(c5, d, c4);
-    const double da = d * fma(fma(fma(w[3], d, w[2]), d, w[1]), d, w[0]);
-    const double dop = fma(da, horner<NE - 1>(e, da), d * horner<NQ>(q, da));
-    // quartic/quintic phase minus the Doppler offset, to 2^-48 cycle, added in fixed point
-    const long long corr = __double2ll_rn((ext - dop) * 0x1p48);
+    const double rem = (dd * dd) * horner<NR>(Rc, d);
+    const long long corr = __double2ll_rn(rem * 0x1p48);
     double cs, sn;
     cis_fixed(Fv + ((unsigned long long)corr << 16), tab, cs, sn);
-    const double G1 = horner<NG>(g1, da);
-    const double G2 = horner<NG>(g2, da);
+    const double G1 = horner<NG>(g1, d);
+    const double G2 = horner<NG>(g2, d);
     const double zr = fma(dr, cs, -di * sn);
     const double zi = fma(dr, sn, di * cs);
     acc[0] = fma(G1, zr, acc[0]);
@@ -275,21 +306,15 @@ __device__ __forceinline__ void flush_d(double acc[7], double* dst, int lane) {
 
 // An expansion tile walked as single-segment pieces [pa_lo, pa_hi): flushes the
 // running segment when a piece starts a new one.
-template <int NG, int NE, int NQ>
+template <int NG, int NR>
 __device__ __forceinline__ void expansion_tile(const AnchorD& A, const SegView& sv, int64_t span_lo, int lo, int hi,
                                                const double2* __restrict__ rot, const double* __restrict__ dwr,
                                                const double* __restrict__ dwi, const double* __restrict__ Wt,
                                                const double2* __restrict__ tab, const Partials& pa, int64_t slot,
                                                int b, int Np, int lane, int& cur, int& nflush, double acc[7]) {
-    double g1[9], g2[9];
-    double w[4], e[7], q[6];
+    double g1[NG + 1], g2[NG + 1], Rc[NR + 1];
 #pragma unroll
-    for (int i = 0; i < 4; i++) w[i] = A.w[i];
-#pragma unroll
-    for (int i = 0; i < 7; i++) e[i] = A.e[i];
-#pragma unroll
-    for (int i = 0; i < 6; i++) q[i] = A.q[i];
-    const double c4 = A.c4, c5 = A.c5;
+    for (int i = 0; i <= NR; i++) Rc[i] = A.R[i];
     int pa_lo = lo;
     while (pa_lo < hi) {
         const int sp = sv.seg(span_lo + pa_lo);   // warp-uniform
@@ -300,7 +325,7 @@ __device__ __forceinline__ void expansion_tile(const AnchorD& A, const SegView& 
         }
         const int64_t nb = sv.start(sp + 1) - span_lo;
         const int pa_hi = nb < hi ? (int)nb : hi;
-        segment_coeffs_d(A, rot[sp], g1, g2);
+        segment_coeffs_d<NG>(A, rot[sp], g1, g2);
         const int k0 = pa_lo + lane;
         const long long d0 = (long long)(k0 - A.ja);
         const unsigned long long y0 = poly_fx(A.c, d0), y1 = poly_fx(A.c, d0 + 32),
@@ -315,11 +340,10 @@ __device__ __forceinline__ void expansion_tile(const AnchorD& A, const SegView& 
             F = Fb + D1 + D2;
             D1 += 2ull * D2 + D3;
             D2 += 2ull * D3;
-            bin_d<NG, NE, NQ>(Fa, d, dwr[k], dwi[k], Wt[k], w, c4, c5, e, q, g1, g2, tab, acc);
-            bin_d<NG, NE, NQ>(Fb, d + 32.0, dwr[k + 32], dwi[k + 32], Wt[k + 32], w, c4, c5, e, q, g1, g2, tab,
-                              acc);
+            bin_d<NG, NR>(Fa, d, dwr[k], dwi[k], Wt[k], Rc, g1, g2, tab, acc);
+            bin_d<NG, NR>(Fb, d + 32.0, dwr[k + 32], dwi[k + 32], Wt[k + 32], Rc, g1, g2, tab, acc);
         }
-        if (k < pa_hi) bin_d<NG, NE, NQ>(F, d, dwr[k], dwi[k], Wt[k], w, c4, c5, e, q, g1, g2, tab, acc);
+        if (k < pa_hi) bin_d<NG, NR>(F, d, dwr[k], dwi[k], Wt[k], Rc, g1, g2, tab, acc);
         pa_lo = pa_hi;
     }
 }
@@ -360,15 +384,18 @@ __device__ __forceinline__ void fp64a_item(const Grid& g, const Tables& tb, cons
         const int lo = A.lo, hi = A.hi;
         if (cur < 0) cur = sv.seg(span_lo + lo);
         if (A.mode != 2) {
-            if (A.mode == 4)
-                expansion_tile<5, 4, 3>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane,
-                                        cur, nflush, acc);
+            if (A.mode == 5)
+                expansion_tile<6, 2>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
+                                     nflush, acc);
+            else if (A.mode == 4)
+                expansion_tile<7, 3>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
+                                     nflush, acc);
             else if (A.mode == 3)
-                expansion_tile<6, 5, 4>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane,
-                                        cur, nflush, acc);
+                expansion_tile<8, 5>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
+                                     nflush, acc);
             else
-                expansion_tile<8, 7, 5>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane,
-                                        cur, nflush, acc);
+                expansion_tile<10, 7>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
+                                      nflush, acc);
             pk = -1;
             nxt = -1;
         } else {

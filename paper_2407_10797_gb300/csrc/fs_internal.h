@@ -50,7 +50,7 @@ struct Partials {
     float2* rot32; // the same rotations in FP32 (mixed mode), or NULL
     int ntiles;   // number of tiles (slots of H and T per particle)
     int tile;     // bins per tile
-    unsigned long long* census = nullptr;   // [5] in-band bins per anchor mode (anchored kernels), or NULL
+    unsigned long long* census = nullptr;   // [6] in-band bins per anchor mode (anchored kernels), or NULL
 };
 
 // Record an error message for fs_last_error() and return st.

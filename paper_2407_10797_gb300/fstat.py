@@ -279,14 +279,14 @@ class Plan:
         return v.value, [ms[i] for i in range(self.n_variants)]
 
     def census(self, params, Np: int, edges=None) -> list[int]:
-        """In-band particle*bins per anchor mode (fs_plan_census): [unused, wide or
-        FP32 body, bin-by-bin fallback, mid tier, narrow tier]."""
+        """In-band particle*bins per anchor mode (fs_plan_census): [unused, widest
+        tier or FP32 body, bin-by-bin fallback, tiers 3, 4, 5 (narrowest)]."""
         import torch
         arr, e = _edges_arg(edges, Np)
-        out = (C.c_int64 * 5)()
+        out = (C.c_int64 * 6)()
         _check(self._L.fs_plan_census(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
                                       e, int(Np), out))
-        return [int(out[i]) for i in range(5)]
+        return [int(out[i]) for i in range(6)]
 
     def set_profiling(self, enable: bool):
         _check(self._L.fs_plan_set_profiling(self._h, 1 if enable else 0))

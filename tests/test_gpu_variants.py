@@ -243,10 +243,10 @@ def test_census_counts_every_in_band_bin(fst, small_case, mode):
         c = plan.census(Pt, Np)
         assert c[0] == 0 and sum(c) == inband, (Np, c)
         if mode == fst.FS_MIXED:
-            assert c[3] == 0 and c[4] == 0
+            assert c[3] == 0 and c[4] == 0 and c[5] == 0
     if mode == fst.FS_FP64:
         plan.set_variant(0)
-        assert plan.census(Pt, 16) == [0, 0, 0, 0, 0]
+        assert plan.census(Pt, 16) == [0, 0, 0, 0, 0, 0]
     plan.close()
     w = S.small_workload()
     g = w.grid
