@@ -93,6 +93,34 @@ __device__ __forceinline__ unsigned long long poly_fx(const unsigned long long c
 }
 
 // ---------------------------------------------------------------------------
+// Polynomials in the bin offset (anchored kernels)
+// ---------------------------------------------------------------------------
+// p <- p * u, truncated at degree KD (u[0] = 0, u of degree NU)
+template <int KD, int NU, typename T>
+__device__ __forceinline__ void poly_mul_u(T* p, const T* u) {
+#pragma unroll
+    for (int k = KD; k >= 1; k--) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 1; j <= NU && j <= k; j++) s = fma(u[j], p[k - j], s);
+        p[k] = s;
+    }
+    p[0] = T(0);
+}
+
+// Coefficients of sum_{n=0..na} a[n] u(d)^n, truncated at degree KD, by Horner's
+// scheme on polynomials (u of degree NU with u[0] = 0).
+template <int KD, int NU, typename T>
+__device__ __forceinline__ void poly_compose(const T* a, int na, const T* u, T* out) {
+    for (int k = 0; k <= KD; k++) out[k] = T(0);
+    out[0] = a[na];
+    for (int n = na - 1; n >= 0; n--) {
+        poly_mul_u<KD, NU, T>(out, u);
+        out[0] += a[n];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launch helpers (host)
 // ---------------------------------------------------------------------------
 // Resident CTAs per SM times SMs for a persistent kernel, cached per device.

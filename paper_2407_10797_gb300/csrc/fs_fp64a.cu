@@ -48,27 +48,6 @@ struct AnchorD {
     int mode;                  // 0: no in-band bin, 2: bin by bin, 1/3/4/5: expansion tiers (see expansion_tile)
 };
 
-// p <- p * u, truncated at degree kDeg (u[0] = 0, u of degree 5)
-__device__ __forceinline__ void mul_u(double* p, const double* u) {
-    for (int k = kDeg; k >= 1; k--) {
-        double s = 0.0;
-        for (int j = 1; j <= 5 && j <= k; j++) s = fma(u[j], p[k - j], s);
-        p[k] = s;
-    }
-    p[0] = 0.0;
-}
-
-// Coefficients in d of sum_n a[n] u(d)^n (n = 0..na), u(d) of degree 5 with u[0] = 0,
-// by Horner's scheme on polynomials, truncated at degree kDeg.
-__device__ __forceinline__ void compose(const double* a, int na, const double* u, double* out) {
-    for (int k = 0; k <= kDeg; k++) out[k] = 0.0;
-    out[0] = a[na];
-    for (int n = na - 1; n >= 0; n--) {
-        mul_u(out, u);
-        out[0] += a[n];
-    }
-}
-
 __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, const Particle& P, int64_t span_lo,
                                            int64_t lo, int64_t hi, AnchorD& A) {
     A.lo = (int)(lo - span_lo);
@@ -156,7 +135,7 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
             cn[n] = cyc[n & 3] / nf;
         }
         double CU[kDeg + 1];
-        compose(cn, 10, U, CU);
+        poly_compose<kDeg, 5, double>(cn, 10, U, CU);
         const double ADfa = P.AD * fh, ADdf = P.AD * g.df;
         Dk[0] = ADfa * CU[0];
         for (int k = 1; k <= kDeg; k++) Dk[k] = fma(ADfa, CU[k], ADdf * CU[k - 1]);
@@ -203,7 +182,7 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
                 }
                 Fd[n] = sum / nf;
             }
-            compose(Fd, 10, U, A.FU[f]);
+            poly_compose<kDeg, 5, double>(Fd, 10, U, A.FU[f]);
         }
     }
     // validity: the quintic d(alpha) (remainder from S_7, 20% margin) and the degree-12
