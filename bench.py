@@ -50,6 +50,15 @@ NP_LIST = (256, 64, 16, 1)
 # phase steps and conversions not counted).  Keys: the anchor modes of
 # fs_plan_census.
 FP64_DIRECT_FLOP = 203.0
+
+# DRAM bytes per fused launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture each of the bench's launch (320 particles, N_p = 16):
+# profiles/fp64a_persistent_paper_grid_B320_Np16.md and
+# profiles/mixed_persistent_paper_grid_B320_Np16.md.  Both are one pass over the
+# per-bin tables and do not depend on N_p; the FP64 figure holds for the
+# anchored variants (3, 4) only.
+TRAFFIC_FP64_ANCHORED = 76.16e6
+TRAFFIC_MIXED = 48.35e6
 FP64_TIER_FLOP = {1: 101.0, 2: FP64_DIRECT_FLOP, 3: 89.0, 4: 81.0, 5: 75.0}
 
 
@@ -552,12 +561,16 @@ def run_gpu(args, world, rank, local):
                                "of 8 runs x 40 particles from the same prior draw",
                        "inband_particle_bins_per_launch": inband, "grid_particle_bins_per_launch": B * g.n,
                        "l2": "inputs exceed L2: per-bin tables 227 MB > 129 MB L2", "parallelism": f"dp{world}"},
-            "gpu_launches": args.steps * len(NP_LIST) * 10,
+            # per N_p and step: map, setup, rotation, fused (+ the span-list kernel of the
+            # anchored variants), solve, segment sums, fitness, pbest, move, counter
+            "gpu_launches": args.steps * sum(10 + (tune64[Np]["variant"] >= 3) for Np in NP_LIST),
             "kernel_ms": {"fused_fp64_avg": main_avg_ms, "setup_avg": prof["setup"][0] / max(prof["setup"][1], 1),
                           "solve_avg": prof["reduce"][0] / max(prof["reduce"][1], 1),
                           "fused_share_of_step": main_ms / max(ms, 1e-9)},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / peak_tf, "traffic": None, "pipe": "fp64",
+                         "frac": achieved_tf / peak_tf,
+                         "traffic": TRAFFIC_FP64_ANCHORED if all(tune64[Np]["variant"] >= 3 for Np in NP_LIST) else None,
+                         "traffic_algorithmic": 24 * g.n, "pipe": "fp64",
                          "peak_source": "unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                          "flop_per_pbin": flop64, "census_bins_by_mode": census_sum(census64)},
             "clocks": clocks,
@@ -570,7 +583,8 @@ def run_gpu(args, world, rank, local):
                       "max_rel_err_vs_fp64": mix_err, "error_metric": "|dF|/max(|F|, 2 N_p)",
                       "kernel_ms": {"fused_mixed_avg": mm_avg, "fused_share_of_step": mm_ms / max(ms_m, 1e-9)},
                       "roofline": {"bound": "alu", "achieved": ach_m, "peak": peak_m, "unit": "TFLOP/s",
-                                   "frac": ach_m / peak_m, "traffic": None, "pipe": "fp32",
+                                   "frac": ach_m / peak_m, "traffic": TRAFFIC_MIXED,
+                                   "traffic_algorithmic": 16 * g.n, "pipe": "fp32",
                                    "peak_source": "unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
                                    "flop_per_pbin": flopm,
                                    "census_bins_by_mode": census_sum(censusm)},
@@ -581,8 +595,9 @@ def run_gpu(args, world, rank, local):
 
 
 def run_profile_case(args):
-    """Paper-scale grid (tables 227 MB > L2), 64 particles, one N_p = 16 launch
-    after one warm-up launch: a short capture target for kernel profilers."""
+    """Paper-scale grid (tables 227 MB > L2), the bench's 320 particles, one
+    N_p = 16 launch after one warm-up launch: the bench's launch size, as a
+    short capture target for kernel profilers."""
     import torch
     from paper_2407_10797_gb300 import fstat
     w, g, psd, noise, P, inj = workload_inputs(0)
@@ -591,7 +606,7 @@ def run_profile_case(args):
     plan.set_data(torch.from_numpy(noise).cuda(), torch.from_numpy(psd).cuda())
     if args.variant is not None:
         plan.set_variant(min(args.variant, plan.n_variants - 1))
-    P_dev = torch.from_numpy(P[:64] if mode == fstat.FS_FP64 else P).cuda()
+    P_dev = torch.from_numpy(P).cuda()
     for _ in range(2):
         F, _ = plan.fstat(P_dev, 16, want_parts=False)
     torch.cuda.synchronize()
