@@ -44,11 +44,11 @@ NP_LIST = (256, 64, 16, 1)
 # fallback: the template + response + reduction arithmetic of every bin, each
 # of its two FP64 trig evaluations counted as 40.  Anchored form (variants 3,
 # 4), per degree tier (antenna degree NG, phase-remainder degree 4 + NR):
-# 47 + 4 NG + 2 NR, i.e. d^2 and d^4 2, remainder polynomial 2 NR + 1, its
-# fixed-point conversion 1, exp(2 pi i Phi) from the table and its Taylor
-# series 21, antenna pair 4 NG, z = dw e^{i Phi} 6, seven sums 16 (integer
-# phase steps and conversions not counted).  Keys: the anchor modes of
-# fs_plan_census.
+# 42 + 4 NG + 2 NR, i.e. d^2 and d^4 2, remainder polynomial 2 NR + 1 (its
+# coefficients pre-scaled to the 2^-48-cycle fixed point), exp(2 pi i Phi)
+# from the 1024-entry table and its Taylor series 17, antenna pair 4 NG,
+# z = dw e^{i Phi} 6, seven sums 16 (integer phase steps and conversions not
+# counted).  Keys: the anchor modes of fs_plan_census.
 FP64_DIRECT_FLOP = 203.0
 
 # DRAM bytes per fused launch (dram__bytes_read.sum + dram__bytes_write.sum) from
@@ -59,7 +59,7 @@ FP64_DIRECT_FLOP = 203.0
 # anchored variants (3, 4) only.
 TRAFFIC_FP64_ANCHORED = 76.16e6
 TRAFFIC_MIXED = 48.35e6
-FP64_TIER_FLOP = {1: 101.0, 2: FP64_DIRECT_FLOP, 3: 89.0, 4: 81.0, 5: 75.0}
+FP64_TIER_FLOP = {1: 96.0, 2: FP64_DIRECT_FLOP, 3: 84.0, 4: 76.0, 5: 70.0}
 
 
 def census_sum(counts_by_np):

@@ -36,13 +36,13 @@ constexpr int kTileA = 1024;                     // bins per anchor
 constexpr int kTilesA = 32;                      // tiles per span (one anchor per lane)
 constexpr int kSpanA = kTileA * kTilesA;         // 32768 bins
 constexpr int kWarpsA = 4;                       // warps (particles) per CTA
-constexpr int kTabA = 256;                       // exp(2 pi i j / 256) table
+constexpr int kTabA = 1024;                      // exp(2 pi i j / 1024) table
 
 constexpr int kDeg = 12;                         // Taylor degree in the bin offset d computed at an anchor
 
 struct AnchorD {
     unsigned long long c[4];   // cubic of the total phase (orbital minus Doppler), cycles mod 1, units 2^-64
-    double R[kDeg - 3];        // its degree 4..12 coefficients (cycles per bin^k), FP64
+    double R[kDeg - 3];        // its degree 4..12 coefficients (2^-48 cycle per bin^k), FP64
     double FU[2][kDeg + 1];    // F+ and Fx along the tile as polynomials in d (degree 0..12)
     int ja, lo, hi;            // anchor bin and in-band range [lo, hi) of the tile, relative to the span start
     int mode;                  // 0: no in-band bin, 2: bin by bin, 1/3/4/5: expansion tiers (see expansion_tile)
@@ -145,7 +145,7 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
     A.c[1] = to_fixed(O[1] - Dk[1]);
     A.c[2] = to_fixed_small(O[2] - Dk[2]);
     A.c[3] = to_fixed_small(O[3] - Dk[3]);
-    for (int k = 4; k <= kDeg; k++) A.R[k - 4] = O[k] - Dk[k];
+    for (int k = 4; k <= kDeg; k++) A.R[k - 4] = O[k] - Dk[k];   // scaled by 2^48 once the tails are known
     // antenna along the tile: F(alpha_a + u) = sum_n F^(n)(alpha_a) u^n / n!, composed with u = d(alpha)
     {
         double ch[5], sh[5];
@@ -210,6 +210,8 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
     // tiers (antenna degree NG, phase remainder degree 4 + NR): 5:(6,2) 4:(7,3) 3:(8,5) 1:(10,7)
     auto ok = [&](int NG, int NR) { return tG[NG + 1] <= 1e-15 && tR[5 + NR] <= 1e-13; };
     A.mode = !converged ? 2 : ok(6, 2) ? 5 : ok(7, 3) ? 4 : ok(8, 5) ? 3 : ok(10, 7) ? 1 : 2;
+    // the remainder is added to the fixed-point phase in units of 2^-48 cycle
+    for (int k = 0; k <= kDeg - 4; k++) A.R[k] *= 0x1p48;
 }
 
 // Per-segment antenna polynomials in d: G1 = c F+ + s Fx, G2 = c Fx - s F+.
@@ -231,17 +233,17 @@ __device__ __forceinline__ double horner(const double* c, double x) {
 }
 
 // exp(2 pi i Phi) from the phase in 64-bit fixed point (cycles mod 1 in
-// units of 2^-64): the nearest multiple of 1/256 cycle indexes the table, the
-// remaining 56 bits give the angle |theta| <= pi/256, whose cos and sin come
-// from their Taylor series (cos to degree 6, sin to degree 7; truncation
-// below 1e-19).
+// units of 2^-64): the nearest multiple of 1/1024 cycle indexes the table, the
+// remaining 54 bits give the angle |theta| <= pi/1024, whose cos and sin come
+// from their Taylor series (cos to degree 4, sin to degree 5; truncation
+// below 2e-18).
 __device__ __forceinline__ void cis_fixed(unsigned long long Ft, const double2* __restrict__ tab, double& cs,
                                           double& sn) {
-    const int idx = (int)((Ft + (1ull << 55)) >> 56);
-    const double th = (double)(long long)(Ft << 8) * (kTwoPi * 0x1p-72);
+    const int idx = (int)((Ft + (1ull << 53)) >> 54);
+    const double th = (double)(long long)(Ft << 10) * (kTwoPi * 0x1p-74);
     const double t2 = th * th;
-    const double cr = fma(fma(fma(-1.0 / 720.0, t2, 1.0 / 24.0), t2, -0.5), t2, 1.0);
-    const double sr = th * fma(fma(fma(-1.0 / 5040.0, t2, 1.0 / 120.0), t2, -1.0 / 6.0), t2, 1.0);
+    const double cr = fma(fma(1.0 / 24.0, t2, -0.5), t2, 1.0);
+    const double sr = th * fma(fma(1.0 / 120.0, t2, -1.0 / 6.0), t2, 1.0);
     const double2 t = tab[idx & (kTabA - 1)];
     cs = fma(t.x, cr, -t.y * sr);
     sn = fma(t.y, cr, t.x * sr);
@@ -249,15 +251,14 @@ __device__ __forceinline__ void cis_fixed(unsigned long long Ft, const double2* 
 
 // One bin of an expansion tile inside a single segment: the phase is the
 // fixed-point cubic Fv plus the FP64 remainder d^4 (R_4 + R_5 d + ... ), NR + 1
-// terms, added as a 2^-48-cycle integer; the antenna pair is two degree-NG
-// polynomials in d.
+// terms in units of 2^-48 cycle, added as an integer; the antenna pair is two
+// degree-NG polynomials in d.
 template <int NG, int NR>
 __device__ __forceinline__ void bin_d(unsigned long long Fv, double d, double dr, double di, double W,
                                       const double Rc[NR + 1], const double g1[NG + 1], const double g2[NG + 1],
                                       const double2* __restrict__ tab, double acc[7]) {
     const double dd = d * d;
-    const double rem = (dd * dd) * horner<NR>(Rc, d);
-    const long long corr = __double2ll_rn(rem * 0x1p48);
+    const long long corr = __double2ll_rn((dd * dd) * horner<NR>(Rc, d));   // Rc scaled by 2^48
     double cs, sn;
     cis_fixed(Fv + ((unsigned long long)corr << 16), tab, cs, sn);
     const double G1 = horner<NG>(g1, d);
