@@ -233,6 +233,22 @@ FS_API int64_t fs_mlp_num_params(int width);
 FS_API fs_status fs_mlp_create(fs_mlp** out, int width, int max_batch, uint64_t seed, void* stream);
 FS_API fs_status fs_mlp_destroy(fs_mlp* mlp);
 
+/* A batch of `groups` independent networks (1 <= groups <= 1024) of one
+ * width, evaluated and trained together: every kernel of a pass, the GEMMs
+ * included, covers all of them in one launch.  Network g is initialised
+ * with key seed + g, so it starts as fs_mlp_create(seed + g) would; its
+ * results equal those of that single network run alone (same summation
+ * order).  max_batch counts rows per network.  Through the calls below a
+ * batch reads and writes per-network blocks laid end to end: parameters
+ * [groups][P], inputs X_dev [groups][N][5], targets and outputs
+ * [groups][N], losses [groups] (per step); the networks share the Adam step
+ * count.  fs_mlp_create is the case groups = 1. */
+FS_API fs_status fs_mlp_create_group(fs_mlp** out, int groups, int width, int max_batch, uint64_t seed,
+                                     void* stream);
+
+/* Networks in the batch (1 for fs_mlp_create), -1 for NULL. */
+FS_API int fs_mlp_groups(const fs_mlp* mlp);
+
 /* Tensor-core path of the network's GEMMs: 1 = tcgen05 (5th-generation
  * tensor cores, accumulators in tensor memory) for the products whose
  * output width is a multiple of 64 or equals 16, mma.sync for the others;
@@ -246,26 +262,28 @@ FS_API fs_status fs_mlp_set_tensor_path(fs_mlp* mlp, int tcgen05);
 FS_API fs_status fs_mlp_tensor_status(fs_mlp* mlp, int* timed_out);
 
 /* Copy the fp32 master weights in or out (device buffers of
- * fs_mlp_num_params floats).  Setting weights resets the Adam step count
+ * groups x fs_mlp_num_params floats).  Setting weights resets the Adam step count
  * and the target standardisation.  set is synchronous, get asynchronous. */
 FS_API fs_status fs_mlp_set_params(fs_mlp* mlp, const float* theta_dev);
 FS_API fs_status fs_mlp_get_params(fs_mlp* mlp, float* theta_dev);
 
-/* Predictions y_dev [N] for X_dev [N][5] (fp32, device), in the units of
+/* Predictions y_dev [groups][N] for X_dev [groups][N][5] (fp32, device), in the units of
  * the targets of the last fs_mlp_train call (raw network output before any
  * training).  Asynchronous. */
 FS_API fs_status fs_mlp_forward(fs_mlp* mlp, const float* X_dev, int N, float* y_dev);
 
-/* Loss L = (1/2n) sum (y - t)^2 over the n finite targets t_dev [N] (NaN =
- * ignored, no standardisation) and its gradient with respect to the fp32
- * master weights (grad_dev: fs_mlp_num_params floats, may be NULL; loss_dev:
- * 1 float, may be NULL).  1 <= N <= max_batch.  Asynchronous. */
+/* Loss L = (1/2n) sum (y - t)^2 over the n finite targets t_dev [groups][N]
+ * (NaN = ignored, no standardisation), per network, and its gradient with
+ * respect to the fp32 master weights (grad_dev: groups x fs_mlp_num_params
+ * floats, may be NULL; loss_dev: groups floats, may be NULL).
+ * 1 <= N <= max_batch.  Asynchronous. */
 FS_API fs_status fs_mlp_loss_grad(fs_mlp* mlp, const float* X_dev, const float* t_dev, int N, float* grad_dev,
                                   float* loss_dev);
 
 /* `steps` full-batch Adam steps (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8)
  * on (X_dev, t_dev) with the finite targets standardised by their mean and
- * standard deviation; loss_dev: optional [steps] losses.  Asynchronous. */
+ * standard deviation (per network); loss_dev: optional [steps][groups]
+ * losses.  Asynchronous. */
 FS_API fs_status fs_mlp_train(fs_mlp* mlp, const float* X_dev, const float* t_dev, int N, int steps, float lr,
                               float* loss_dev);
 
@@ -274,10 +292,10 @@ FS_API fs_status fs_mlp_train(fs_mlp* mlp, const float* X_dev, const float* t_de
  * (k, particle, dim, run | c << 20), so candidate 0 is the fs_pso_step move),
  * a network predicts their fitness, and each particle takes the candidate
  * with the highest prediction (lowest index among equals; candidates outside
- * [0,1]^5 rank last).  mlps: n_mlp >= 1 networks; R must be a multiple of
- * n_mlp and network g ranks the candidates of runs [g R/n_mlp, (g+1) R/n_mlp)
- * (one network per search box, since positions are normalised to each
- * run's box).  1 <= n_cand <= 64; candidates go through a network in chunks
+ * [0,1]^5 rank last).  mlps: n_mlp >= 1 network batches holding ng networks
+ * in all (in order); R must be a multiple of ng and the j-th network ranks
+ * the candidates of runs [j R/ng, (j+1) R/ng) (one network per search box,
+ * since positions are normalised to each run's box).  1 <= n_cand <= 64; candidates go through a network in chunks
  * of its max_batch.  The networks must run on the plan's stream.
  * Asynchronous; allocates its candidate buffers in the plan (synchronously)
  * when they are too small. */
@@ -318,7 +336,10 @@ FS_API fs_status fs_pso_graph_build_ex(fs_plan* plan, const fs_swarm* swarm, con
 
 /* Capture `steps` Adam steps of fs_mlp_train for each network on its ring's
  * whole contents (all cap slots; empty slots hold NaN targets, which the loss
- * ignores) as one CUDA graph, run with fs_graph_run.  The networks must share
+ * ignores) as one CUDA graph, run with fs_graph_run.  rings holds one ring
+ * per network (the sum of the batches' group counts); the rings of a batch
+ * of G networks must be consecutive slices of one buffer (ring j of the
+ * batch at x + j cap 5 and f + j cap, one cap).  The networks must share
  * one stream that is not the legacy default stream; the rings' buffers are
  * read when the graph runs.  The Adam step count lives on the device, so
  * replays continue the optimisation.  Synchronous. */

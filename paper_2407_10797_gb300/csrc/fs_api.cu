@@ -602,10 +602,13 @@ fs_status fs_pso_step_screened(fs_plan* p, const fs_swarm* w, fs_mlp* const* mlp
     if (!p || !mlps || n_mlp < 1) return fail(FS_EINVAL, "fs_pso_step_screened: NULL plan or no network");
     fs_status st = check_swarm(w);
     if (st != FS_OK) return st;
-    if (w->R % n_mlp != 0) return fail(FS_EINVAL, "fs_pso_step_screened: R = %d is not a multiple of n_mlp = %d",
-                                       w->R, n_mlp);
-    for (int i = 0; i < n_mlp; i++)
+    int ng = 0;
+    for (int i = 0; i < n_mlp; i++) {
         if (!mlps[i]) return fail(FS_EINVAL, "fs_pso_step_screened: network %d is NULL", i);
+        ng += fs_mlp_groups(mlps[i]);
+    }
+    if (w->R % ng != 0)
+        return fail(FS_EINVAL, "fs_pso_step_screened: R = %d is not a multiple of the %d network groups", w->R, ng);
     if (n_cand < 1 || n_cand > 64) return fail(FS_EINVAL, "fs_pso_step_screened: n_cand must be in [1, 64]");
     if (n_iter < 1 || !(vmax > 0.0)) return fail(FS_EINVAL, "fs_pso_step_screened: need n_iter >= 1 and vmax > 0");
     if (iteration < 0 && !w->iter) return fail(FS_EINVAL, "fs_pso_step_screened: iteration < 0 needs swarm->iter");
@@ -780,23 +783,32 @@ fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_sample_r
     if (!mlps || !rings || n < 1 || steps < 1 || !(lr > 0.f))
         return fail(FS_EINVAL, "fs_mlp_train_graph_build: need n >= 1 networks and rings, steps >= 1, lr > 0");
     cudaStream_t s = nullptr;
-    for (int i = 0; i < n; i++) {
+    for (int i = 0, k = 0; i < n; i++) {
         cudaStream_t si = nullptr;
         if (!mlps[i]) return fail(FS_EINVAL, "fs_mlp_train_graph_build: network %d is NULL", i);
         fs_status st = fs_mlp_stream(mlps[i], &si);
         if (st != FS_OK) return st;
         if (i == 0) s = si;
         if (si != s || !s) return fail(FS_EINVAL, "fs_mlp_train_graph_build: the networks must share one non-default stream");
-        if (!rings[i].x || !rings[i].f || rings[i].cap < 1)
-            return fail(FS_EINVAL, "fs_mlp_train_graph_build: ring %d needs x, f and cap >= 1", i);
+        // a batch of G networks trains on G consecutive rings that are slices of one buffer
+        const fs_sample_ring& r0 = rings[k];
+        for (int j = 0; j < fs_mlp_groups(mlps[i]); j++, k++) {
+            const fs_sample_ring& r = rings[k];
+            if (!r.x || !r.f || r.cap < 1)
+                return fail(FS_EINVAL, "fs_mlp_train_graph_build: ring %d needs x, f and cap >= 1", k);
+            if (r.cap != r0.cap || r.x != r0.x + (int64_t)j * r0.cap * 5 || r.f != r0.f + (int64_t)j * r0.cap)
+                return fail(FS_EINVAL,
+                            "fs_mlp_train_graph_build: the rings of network %d must be consecutive slices of one "
+                            "buffer with one capacity", i);
+        }
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
     fs_status st = FS_OK;
-    for (int i = 0; i < n && st == FS_OK; i++)
-        st = fs_mlp_train(mlps[i], rings[i].x, rings[i].f, rings[i].cap, steps, lr, nullptr);
+    for (int i = 0, k = 0; i < n && st == FS_OK; k += fs_mlp_groups(mlps[i]), i++)
+        st = fs_mlp_train(mlps[i], rings[k].x, rings[k].f, rings[k].cap, steps, lr, nullptr);
     cudaGraph_t gr = nullptr;
     e = cudaStreamEndCapture(s, &gr);
     if (st != FS_OK) {

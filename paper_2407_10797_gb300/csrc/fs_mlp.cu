@@ -32,6 +32,14 @@ enum Epi { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32 = 2 };
 constexpr int BM = 64, BN = 64, BK = 32, PAD = 8, GEMM_THREADS = 128;
 constexpr int kMaxSplits = 32;   // K chunks of the weight-gradient GEMMs
 
+// A batch of G networks of the same shape stored back to back: the GEMM grid's
+// z index is (network g, K chunk), and each operand advances by its stride (in
+// elements) from one network to the next.
+struct GS {
+    int64_t a = 0, b = 0, bias = 0, mask = 0, out = 0;
+    int splits = 1;
+};
+
 __device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], const uint32_t b[2]) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -66,12 +74,18 @@ template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(GEMM_THREADS)
 gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb,
                  const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, void* out, int ldo,
-                 int kchunk) {
-    // split K: CTA z covers k in [z kchunk, min(K, (z + 1) kchunk)) and (EPI_F32 only) writes
-    // its partial product to the z-th M x ldo slab of out
-    const int kb = blockIdx.z * kchunk;
+                 int kchunk, GS gs) {
+    // grid z = (network, K chunk): the chunk covers k in [c kchunk, min(K, (c + 1) kchunk)) and
+    // (EPI_F32 only) writes its partial product to the c-th M x ldo slab of the network's output
+    const int zg = blockIdx.z / gs.splits, zc = blockIdx.z % gs.splits;
+    A += zg * gs.a;
+    B += zg * gs.b;
+    if (bias) bias += zg * gs.bias;
+    if (mask) mask += zg * gs.mask;
+    const int kb = zc * kchunk;
     const int ke = min(K, kb + kchunk);
-    if (EPI == EPI_F32) out = static_cast<float*>(out) + (int64_t)blockIdx.z * M * ldo;
+    if (EPI == EPI_F32) out = static_cast<float*>(out) + zg * gs.out + (int64_t)zc * M * ldo;
+    else out = static_cast<bf16*>(out) + zg * gs.out;
     __shared__ __align__(16) bf16 As[BM][BK + PAD];
     __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -249,7 +263,7 @@ template <bool TA, bool TB, int EPI, int NT>
 __global__ void __launch_bounds__(THREADS)
 gemm_tc5_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb,
                 const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, void* out, int ldo, int kchunk,
-                int* err) {
+                int* err, GS gs) {
     constexpr int A_BYTES = TM * TK * 2, B_BYTES = NT * TK * 2, STAGE = A_BYTES + B_BYTES;
     constexpr uint32_t NCOLS = NT < 32 ? 32 : NT;   // TMEM columns: a power of two >= 32
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -258,8 +272,14 @@ gemm_tc5_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const 
     __shared__ int failed;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * NT;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    if (EPI == EPI_F32) out = static_cast<float*>(out) + (int64_t)blockIdx.z * M * ldo;
+    const int zg = blockIdx.z / gs.splits, zc = blockIdx.z % gs.splits;
+    A += zg * gs.a;
+    B += zg * gs.b;
+    if (bias) bias += zg * gs.bias;
+    if (mask) mask += zg * gs.mask;
+    const int kb = zc * kchunk, ke = min(K, kb + kchunk);
+    if (EPI == EPI_F32) out = static_cast<float*>(out) + zg * gs.out + (int64_t)zc * M * ldo;
+    else out = static_cast<bf16*>(out) + zg * gs.out;
 
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
@@ -372,7 +392,8 @@ gemm_tc5_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const 
 
 template <bool TA, bool TB, int EPI, int NT>
 cudaError_t launch(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias,
-                   const bf16* mask, int ldm, void* out, int ldo, int splits, int kchunk, int* err, cudaStream_t s) {
+                   const bf16* mask, int ldm, void* out, int ldo, int G, const GS& gs, int kchunk, int* err,
+                   cudaStream_t s) {
     constexpr int STAGES = 2 * (TM * TK * 2 + NT * TK * 2), STAGING = TM * (NT + 4) * 4;
     constexpr int SMEM = STAGES > STAGING ? STAGES : STAGING;
     static bool attr[64];
@@ -385,9 +406,9 @@ cudaError_t launch(int M, int N, int K, const bf16* A, int lda, const bf16* B, i
             return e;
         attr[dev] = true;
     }
-    dim3 grid((unsigned)((N + NT - 1) / NT), (unsigned)((M + TM - 1) / TM), (unsigned)splits);
+    dim3 grid((unsigned)((N + NT - 1) / NT), (unsigned)((M + TM - 1) / TM), (unsigned)(G * gs.splits));
     gemm_tc5_kernel<TA, TB, EPI, NT><<<grid, THREADS, SMEM, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo,
-                                                                 kchunk, err);
+                                                                 kchunk, err, gs);
     return cudaGetLastError();
 }
 
@@ -395,38 +416,43 @@ cudaError_t launch(int M, int N, int K, const bf16* A, int lda, const bf16* B, i
 
 template <bool TA, bool TB, int EPI>
 static cudaError_t gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias,
-                        const bf16* mask, int ldm, void* out, int ldo, cudaStream_t s, int* tc_err = nullptr) {
-    if (M <= 0 || N <= 0) return cudaSuccess;
-    if (tc_err && N % 128 == 0 && (int64_t)((M + 127) / 128) * (N / 128) >= 152)
-        return tc5::launch<TA, TB, EPI, 128>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, 1,
-                                             K > 0 ? K : 1, tc_err, s);
+                        const bf16* mask, int ldm, void* out, int ldo, cudaStream_t s, int* tc_err = nullptr,
+                        int G = 1, GS gs = GS()) {
+    if (M <= 0 || N <= 0 || G <= 0) return cudaSuccess;
+    gs.splits = 1;
+    const int kc = K > 0 ? K : 1;
+    if (tc_err && N % 128 == 0 && (int64_t)((M + 127) / 128) * (N / 128) * G >= 152)
+        return tc5::launch<TA, TB, EPI, 128>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, G, gs, kc, tc_err,
+                                             s);
     if (tc_err && N % 64 == 0)
-        return tc5::launch<TA, TB, EPI, 64>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, 1, K > 0 ? K : 1,
-                                            tc_err, s);
+        return tc5::launch<TA, TB, EPI, 64>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, G, gs, kc, tc_err, s);
     if (tc_err && N == 16)
-        return tc5::launch<TA, TB, EPI, 16>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, 1, K > 0 ? K : 1,
-                                            tc_err, s);
-    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), 1);
+        return tc5::launch<TA, TB, EPI, 16>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, G, gs, kc, tc_err, s);
+    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)G);
     gemm_bf16_kernel<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo,
-                                                                K > 0 ? K : 1);
+                                                                kc, gs);
     return cudaGetLastError();
 }
 
-__global__ void sum_splits_kernel(int S, int64_t MN, const float* __restrict__ ws, float* out) {
+// out[g][i] = sum_c ws[g][c][i] over the K chunks, in order (deterministic)
+__global__ void sum_splits_kernel(int S, int64_t MN, const float* __restrict__ ws, float* out, int64_t sout) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= MN) return;
+    const float* w = ws + (int64_t)blockIdx.y * S * MN;
     float v = 0.f;
-    for (int z = 0; z < S; z++) v += ws[(int64_t)z * MN + i];   // fixed order: deterministic
-    out[i] = v;
+    for (int z = 0; z < S; z++) v += w[(int64_t)z * MN + i];
+    out[blockIdx.y * sout + i] = v;
 }
 
-// Weight gradient C = A^T B (fp32, dense M x N) with the K = batch axis split into
-// chunks of 256 rows: one CTA per (tile, chunk) keeps the GPU busy when M x N is
-// only a few tiles; the chunk partials (ws: splits x M x N floats) are summed in order.
+// Weight gradient C = A^T B (fp32, dense M x N) of each of G networks, with the
+// K = batch axis split into chunks of 256 rows: one CTA per (tile, network,
+// chunk) keeps the GPU busy when M x N is only a few tiles; the chunk partials
+// (ws: G x splits x M x N floats) are summed in order into out + g sout.
 template <bool TB>
 static cudaError_t gemm_wgrad(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, float* out,
-                              float* ws, int max_splits, cudaStream_t s, int* tc_err = nullptr) {
-    if (M <= 0 || N <= 0) return cudaSuccess;
+                              float* ws, int max_splits, cudaStream_t s, int* tc_err = nullptr, int G = 1,
+                              int64_t sa = 0, int64_t sb = 0, int64_t sout = 0) {
+    if (M <= 0 || N <= 0 || G <= 0) return cudaSuccess;
     const bool tc = tc_err && (N % 64 == 0 || N == 16);
     int splits = (K + 255) / 256;
     if (splits > max_splits) splits = max_splits;
@@ -435,56 +461,69 @@ static cudaError_t gemm_wgrad(int M, int N, int K, const bf16* A, int lda, const
     const int q = tc ? tc5::TK : BK;   // chunks start on a stage boundary
     kchunk = (kchunk + q - 1) / q * q;
     splits = (K + kchunk - 1) / kchunk;
-    if (splits <= 1) return gemm<true, TB, EPI_F32>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, out, N, s, tc_err);
+    if (splits < 1) splits = 1;
+    GS gs;
+    gs.a = sa;
+    gs.b = sb;
+    gs.splits = splits;
+    gs.out = (int64_t)splits * M * N;
     cudaError_t e;
     if (tc && N == 16) {
-        e = tc5::launch<true, TB, EPI_F32, 16>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, ws, N, splits, kchunk,
+        e = tc5::launch<true, TB, EPI_F32, 16>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, ws, N, G, gs, kchunk,
                                                tc_err, s);
     } else if (tc) {
-        e = tc5::launch<true, TB, EPI_F32, 64>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, ws, N, splits, kchunk,
+        e = tc5::launch<true, TB, EPI_F32, 64>(M, N, K, A, lda, B, ldb, nullptr, nullptr, 0, ws, N, G, gs, kchunk,
                                                tc_err, s);
     } else {
-        dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)splits);
+        dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(G * splits));
         gemm_bf16_kernel<true, TB, EPI_F32><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, nullptr, nullptr,
-                                                                          0, ws, N, kchunk);
+                                                                          0, ws, N, kchunk, gs);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
     const int64_t MN = (int64_t)M * N;
-    sum_splits_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, s>>>(splits, MN, ws, out);
+    sum_splits_kernel<<<dim3((unsigned)((MN + 255) / 256), (unsigned)G), 256, 0, s>>>(splits, MN, ws, out, sout);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Small kernels
+// Small kernels. Each covers all G networks of a batch: network g's rows are
+// rows [g N, (g + 1) N) of the activations, its parameters th + g P.
 // ---------------------------------------------------------------------------
-__global__ void input_pad_kernel(int N, const float* __restrict__ X, bf16* Xb) {
+// Xb[g][r][c] = X[g sx + r][c] for c < 5, else 0 (sx: rows between networks' inputs)
+__global__ void input_pad_kernel(int G, int N, int64_t sx, const float* __restrict__ X, bf16* Xb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)N * kInPad) return;
-    const int64_t n = i / kInPad;
+    if (i >= (int64_t)G * N * kInPad) return;
+    const int64_t row = i / kInPad;
     const int c = (int)(i % kInPad);
-    Xb[i] = __float2bfloat16(c < 5 ? X[n * 5 + c] : 0.f);
+    const int64_t g = row / N, r = row % N;
+    Xb[i] = __float2bfloat16(c < 5 ? X[(g * sx + r) * 5 + c] : 0.f);
 }
 
-// y[n] = a3[n, :] . w4 + b4 (fp32 accumulation of bf16 products), then y * scale + shift
-__global__ void output_kernel(int N, int W, const bf16* __restrict__ A3, const bf16* __restrict__ w4,
-                              const float* __restrict__ b4, const float* __restrict__ stdz, float* y) {
+// y[g sy + r] = a3[g N + r, :] . w4_g + b4_g (fp32 accumulation of bf16 products), then * scale + shift
+__global__ void output_kernel(int G, int N, int W, const bf16* __restrict__ A3, const bf16* __restrict__ w4,
+                              const float* __restrict__ b4, int64_t P, const float* __restrict__ stdz, float* y,
+                              int64_t sy) {
     const int lane = threadIdx.x & 31;
-    const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (n >= N) return;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= (int64_t)G * N) return;
+    const int64_t g = row / N, r = row % N;
+    const bf16* wg = w4 + g * W;
     float s = 0.f;
-    for (int k = lane; k < W; k += 32) s = fmaf(__bfloat162float(A3[n * W + k]), __bfloat162float(w4[k]), s);
+    for (int k = lane; k < W; k += 32) s = fmaf(__bfloat162float(A3[row * W + k]), __bfloat162float(wg[k]), s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
-        const float v = s + b4[0];
-        y[n] = stdz ? fmaf(v, stdz[1], stdz[0]) : v;
+        const float v = s + b4[g * P];
+        y[g * sy + r] = stdz ? fmaf(v, stdz[g * 8 + 1], stdz[g * 8]) : v;
     }
 }
 
-// mean and standard deviation of the finite targets (single block, fixed order)
-__global__ void standardize_kernel(int N, const float* __restrict__ t, float* stdz) {
+// mean and standard deviation of the finite targets t[g st + (0..N)] (block g, fixed order)
+__global__ void standardize_kernel(int N, const float* __restrict__ t, int64_t st, float* stdz) {
     __shared__ double s1[256], s2[256], sc[256];
+    t += blockIdx.x * st;
+    stdz += blockIdx.x * 8;
     double a = 0.0, b = 0.0, c = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const float v = t[i];
@@ -517,35 +556,35 @@ __global__ void standardize_kernel(int N, const float* __restrict__ t, float* st
 }
 
 // dy[n] = (y[n] - t'[n]) / count for finite targets, t' = (t - mu)/sigma if
-// standardising; also the per-sample squared error for the loss.
-__global__ void dloss_kernel(int N, const float* __restrict__ y, const float* __restrict__ t,
+// standardising; also the per-sample squared error for the loss. Row n = g N + r
+// takes its target from t[g st + r] and its network's statistics from stdz + 8 g.
+__global__ void dloss_kernel(int G, int N, const float* __restrict__ y, const float* __restrict__ t, int64_t st,
                              const float* __restrict__ stdz, const float* __restrict__ count, float* dy, float* sq) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const float tv = t[i];
-    float r = 0.f;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)G * N) return;
+    const int64_t g = i / N, r = i % N;
+    const float tv = t[g * st + r];
+    float res = 0.f;
     if (isfinite(tv)) {
-        const float tt = stdz ? (tv - stdz[0]) / stdz[1] : tv;
-        r = y[i] - tt;
+        const float tt = stdz ? (tv - stdz[g * 8]) / stdz[g * 8 + 1] : tv;
+        res = y[i] - tt;
     }
-    const float c = count[0] > 0.f ? count[0] : 1.f;
-    dy[i] = r / c;
-    sq[i] = 0.5f * r * r / c;
+    const float c = count[g * 8] > 0.f ? count[g * 8] : 1.f;
+    dy[i] = res / c;
+    sq[i] = 0.5f * res * res / c;
 }
 
-// dZ3[n, k] = dy[n] * w4[k] * (a3[n, k] > 0)
-__global__ void dz_last_kernel(int N, int W, const float* __restrict__ dy, const bf16* __restrict__ w4,
+// dZ3[n, k] = dy[n] * w4[k] * (a3[n, k] > 0), with the w4 of row n's network
+__global__ void dz_last_kernel(int G, int N, int W, const float* __restrict__ dy, const bf16* __restrict__ w4,
                                const bf16* __restrict__ A3, bf16* dZ) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)N * W) return;
-    const int64_t n = i / W;
+    if (i >= (int64_t)G * N * W) return;
+    const int64_t row = i / W;
     const int k = (int)(i % W);
     const float a = __bfloat162float(A3[i]);
-    dZ[i] = __float2bfloat16(a > 0.f ? dy[n] * __bfloat162float(w4[k]) : 0.f);
+    dZ[i] = __float2bfloat16(a > 0.f ? dy[row] * __bfloat162float(w4[(row / N) * W + k]) : 0.f);
 }
 
-// column sums (fixed order): out[k] = sum_n M[n, k] (bf16 or fp32 input), and
-// the output-layer gradients dW4[k] = sum_n dy[n] a3[n, k], db4 = sum dy.
 template <typename T>
 __device__ __forceinline__ float as_f(T v);
 template <>
@@ -553,9 +592,10 @@ __device__ __forceinline__ float as_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float as_f<bf16>(bf16 v) { return __bfloat162float(v); }
 
-// Column sums out[k] = sum_n wrow[n] Mx[n][k] in two deterministic passes:
-// block b (W threads, thread = column, coalesced) sums rows [b R, (b+1) R) into
-// part[b][k]; one pass over the blocks then adds the parts in order.
+// Column sums out[g][k] = sum_n wrow[g][n] Mx[g][n][k] (bf16 or fp32 input) in two
+// deterministic passes: block (b, g) (W threads, thread = column, coalesced)
+// sums rows [b R, (b+1) R) of network g into part[g][b][k]; one pass over the
+// blocks then adds the parts in order.
 constexpr int kColRows = 128;
 
 template <typename T>
@@ -563,35 +603,43 @@ __global__ void colsum_part_kernel(int N, int W, const T* __restrict__ Mx, const
                                    float* part) {
     const int k = threadIdx.x;
     if (k >= W) return;
+    const int64_t g = blockIdx.y;
+    if (Mx) Mx += g * N * W;
+    if (wrow) wrow += g * N;
     const int n0 = blockIdx.x * kColRows, n1 = min(N, n0 + kColRows);
     float s = 0.f;
     for (int n = n0; n < n1; n++) {
         const float v = Mx ? as_f<T>(Mx[(int64_t)n * W + k]) : 1.f;
         s = fmaf(wrow ? wrow[n] : 1.f, v, s);
     }
-    part[(int64_t)blockIdx.x * W + k] = s;
+    part[(g * gridDim.x + blockIdx.x) * W + k] = s;
 }
 
-__global__ void colsum_final_kernel(int nb, int W, const float* __restrict__ part, float* out) {
+__global__ void colsum_final_kernel(int nb, int W, const float* __restrict__ part, float* out, int64_t sout) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= W) return;
+    const int64_t g = blockIdx.y;
+    part += g * nb * W;
     float s = 0.f;
     for (int b = 0; b < nb; b++) s += part[(int64_t)b * W + k];
-    out[k] = s;
+    out[g * sout + k] = s;
 }
 
 template <typename T>
-static cudaError_t colsum(int N, int W, const T* Mx, const float* wrow, float* out, float* part, cudaStream_t s) {
+static cudaError_t colsum(int G, int N, int W, const T* Mx, const float* wrow, float* out, int64_t sout, float* part,
+                          cudaStream_t s) {
     const int nb = (N + kColRows - 1) / kColRows;
-    colsum_part_kernel<T><<<nb, W, 0, s>>>(N, W, Mx, wrow, part);
+    colsum_part_kernel<T><<<dim3((unsigned)nb, (unsigned)G), W, 0, s>>>(N, W, Mx, wrow, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    colsum_final_kernel<<<(W + 255) / 256, 256, 0, s>>>(nb, W, part, out);
+    colsum_final_kernel<<<dim3((unsigned)((W + 255) / 256), (unsigned)G), 256, 0, s>>>(nb, W, part, out, sout);
     return cudaGetLastError();
 }
 
-__global__ void sum_kernel(int N, const float* __restrict__ v, float* out) {
+// out[g sout] = sum_n v[g N + n] (block g, fixed order)
+__global__ void sum_kernel(int N, const float* __restrict__ v, float* out, int64_t sout) {
     __shared__ float red[256];
+    v += (int64_t)blockIdx.x * N;
     float s = 0.f;
     for (int n = threadIdx.x; n < N; n += blockDim.x) s += v[n];
     red[threadIdx.x] = s;
@@ -600,39 +648,44 @@ __global__ void sum_kernel(int N, const float* __restrict__ v, float* out) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = red[0];
+    if (threadIdx.x == 0) out[blockIdx.x * sout] = red[0];
 }
 
-// gradient of the padded first layer [W][16] -> the [W][5] slot of the flat gradient
-__global__ void unpad_kernel(int W, const float* __restrict__ g16, float* g5) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= W * 5) return;
-    g5[i] = g16[(i / 5) * kInPad + i % 5];
-}
-
-// fp32 master weights -> bf16 copies (first layer padded to 16 inputs)
-__global__ void refresh_kernel(int W, const float* __restrict__ th, bf16* W1b, bf16* W2b, bf16* W3b, bf16* W4b) {
+// gradient of the padded first layer [W][16] -> the [W][5] slot of each network's flat gradient
+__global__ void unpad_kernel(int G, int W, int64_t P, const float* __restrict__ g16, float* g5) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)G * W * 5) return;
+    const int64_t g = i / (W * 5);
+    const int j = (int)(i % (W * 5));
+    g5[g * P + j] = g16[g * W * kInPad + (j / 5) * kInPad + j % 5];
+}
+
+// fp32 master weights -> bf16 copies (first layer padded to 16 inputs); grid y = network
+__global__ void refresh_kernel(int W, int64_t P, const float* __restrict__ th, bf16* W1b, bf16* W2b, bf16* W3b,
+                               bf16* W4b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = blockIdx.y;
     const int64_t nW1 = (int64_t)W * 5, nWW = (int64_t)W * W;
-    const float* W1 = th;
+    const float* W1 = th + g * P;
     const float* W2 = W1 + nW1 + W;
     const float* W3 = W2 + nWW + W;
     const float* W4 = W3 + nWW + W;
     if (i < (int64_t)W * kInPad) {
         const int64_t r = i / kInPad;
         const int c = (int)(i % kInPad);
-        W1b[i] = __float2bfloat16(c < 5 ? W1[r * 5 + c] : 0.f);
+        W1b[g * W * kInPad + i] = __float2bfloat16(c < 5 ? W1[r * 5 + c] : 0.f);
     }
     if (i < nWW) {
-        W2b[i] = __float2bfloat16(W2[i]);
-        W3b[i] = __float2bfloat16(W3[i]);
+        W2b[g * nWW + i] = __float2bfloat16(W2[i]);
+        W3b[g * nWW + i] = __float2bfloat16(W3[i]);
     }
-    if (i < W) W4b[i] = __float2bfloat16(W4[i]);
+    if (i < W) W4b[g * W + i] = __float2bfloat16(W4[i]);
 }
 
 // Adam step counter and bias corrections on the device (so that training
 // steps can be captured in a CUDA graph): ac[0] = step (as unsigned int),
-// ac[1] = 1 / (1 - 0.9^step), ac[2] = 1 / (1 - 0.999^step).
+// ac[1] = 1 / (1 - 0.9^step), ac[2] = 1 / (1 - 0.999^step). All networks of a
+// batch take their steps together and share the counter.
 __global__ void adam_prep_kernel(float* ac) {
     unsigned int* st = reinterpret_cast<unsigned int*>(ac);
     const unsigned int k = *st + 1u;
@@ -672,11 +725,19 @@ __device__ __forceinline__ void philox_mlp(uint32_t c[4], uint32_t k0, uint32_t 
     }
 }
 
+__global__ void stdz_reset_kernel(int G, float* stdz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < G * 8) stdz[i] = (i % 8 == 1 || i % 8 == 5) ? 1.f : 0.f;
+}
+
+// network g of a batch (grid y) takes key seed + g
 __global__ void init_kernel(int W, unsigned long long seed, float* th) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nW1 = (int64_t)W * 5, nWW = (int64_t)W * W;
     const int64_t P = nW1 + W + 2 * (nWW + W) + W + 1;
     if (i >= P) return;
+    seed += blockIdx.y;
+    th += blockIdx.y * P;
     int64_t o = i;
     float fan = 0.f;
     if (o < nW1) fan = 5.f;
@@ -703,22 +764,27 @@ __global__ void init_kernel(int W, unsigned long long seed, float* th) {
 // Module state and C ABI
 // ---------------------------------------------------------------------------
 struct fs_mlp {
-    int W, cap;
-    int64_t P;
+    int G;          // networks in the batch (same width, trained together)
+    int W, cap;     // width; rows per network per pass
+    int64_t P;      // parameters per network
+    int splits;     // most K chunks of a weight-gradient GEMM
     cudaStream_t stream;
-    float* th;      // fp32 master weights [P]
-    float* gr;      // gradient [P]
-    float* m;       // Adam moments
+    float* th;      // fp32 master weights [G][P]
+    float* gr;      // gradient [G][P]
+    float* m;       // Adam moments [G][P]
     float* v;
     int64_t step;
-    fs::bf16 *W1b, *W2b, *W3b, *W4b;
-    fs::bf16 *Xb, *A1, *A2, *A3, *dZa, *dZb;
-    float *y, *dy, *sq, *g16, *stdz, *loss;
+    fs::bf16 *W1b, *W2b, *W3b, *W4b;           // bf16 weights [G][...]
+    fs::bf16 *Xb, *A1, *A2, *A3, *dZa, *dZb;   // activations [G][cap][...]
+    float *y, *dy, *sq;                         // [G][cap]
+    float *g16;     // padded first-layer gradient [G][W][16]
+    float *stdz;    // [G][8]: target mean, deviation, count (training); [4..6] the same for the raw loss
+    float *loss;    // [G]
     float* adamc;   // [4] Adam step counter and bias corrections (device)
-    float* ws;      // split-K partials: kMaxSplits x W x max(W, kInPad)
+    float* ws;      // split-K partials: G x splits x W x max(W, kInPad)
     int tc5;        // 1: tcgen05 GEMMs, 0: mma.sync GEMMs
     int* tc_err;    // device flag set by a tcgen05 GEMM whose mbarrier wait ran out
-    float* part;    // column-sum partials: ceil(cap / kColRows) x W
+    float* part;    // column-sum partials: G x ceil(cap / kColRows) x W
 };
 
 namespace {
@@ -737,47 +803,69 @@ void mlp_free(fs_mlp* m) {
     for (void* p : ps) cudaFree(p);
 }
 
-// Forward pass for N <= cap rows of X (fp32 [N][5]); activations kept.
 int* tcp(fs_mlp* m) { return m->tc5 ? m->tc_err : nullptr; }
 
-cudaError_t mlp_forward(fs_mlp* m, const float* X, int N, float* y, bool destandardize) {
-    using namespace fs;
-    const int W = m->W;
-    cudaStream_t s = m->stream;
-    input_pad_kernel<<<(unsigned)(((int64_t)N * kInPad + 255) / 256), 256, 0, s>>>(N, X, m->Xb);
-    const float* b1 = m->th + (int64_t)W * 5;
-    const float* b2 = b1 + W + (int64_t)W * W;
-    const float* b3 = b2 + W + (int64_t)W * W;
-    const float* b4 = b3 + W + W;
-    cudaError_t e;
-    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, kInPad, m->Xb, kInPad, m->W1b, kInPad, b1, nullptr, 0, m->A1,
-                                                     W, s, tcp(m))) != cudaSuccess)
-        return e;
-    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A1, W, m->W2b, W, b2, nullptr, 0, m->A2, W, s, tcp(m))) !=
-        cudaSuccess)
-        return e;
-    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A2, W, m->W3b, W, b3, nullptr, 0, m->A3, W, s, tcp(m))) !=
-        cudaSuccess)
-        return e;
-    output_kernel<<<(unsigned)(((int64_t)N * 32 + 255) / 256), 256, 0, s>>>(N, W, m->A3, m->W4b, b4,
-                                                                          destandardize ? m->stdz : nullptr, y);
+// identity target scaling (mean 0, deviation 1) for every network
+cudaError_t reset_stdz(fs_mlp* m) {
+    fs::stdz_reset_kernel<<<(m->G * 8 + 255) / 256, 256, 0, m->stream>>>(m->G, m->stdz);
     return cudaGetLastError();
 }
 
-// Loss and gradient for N rows (targets t, NaN = ignored); stdz: standardise targets.
-cudaError_t mlp_backward(fs_mlp* m, const float* X, const float* t, int N, bool standardize) {
+// Forward pass of every network for N <= cap rows each: network g reads rows
+// X[g sx .. g sx + N) (fp32, 5 per row) and writes y[g sy .. g sy + N);
+// activations are kept (rows g N + r).
+cudaError_t mlp_forward(fs_mlp* m, const float* X, int64_t sx, int N, float* y, int64_t sy, bool destandardize) {
     using namespace fs;
-    const int W = m->W;
+    const int W = m->W, G = m->G;
+    const int64_t P = m->P, nWW = (int64_t)W * W, NW = (int64_t)N * W;
+    cudaStream_t s = m->stream;
+    input_pad_kernel<<<(unsigned)(((int64_t)G * N * kInPad + 255) / 256), 256, 0, s>>>(G, N, sx, X, m->Xb);
+    const float* b1 = m->th + (int64_t)W * 5;
+    const float* b2 = b1 + W + nWW;
+    const float* b3 = b2 + W + nWW;
+    const float* b4 = b3 + W + W;
+    GS g1, gh;
+    g1.a = (int64_t)N * kInPad;
+    g1.b = (int64_t)W * kInPad;
+    g1.bias = P;
+    g1.out = NW;
+    gh.a = NW;
+    gh.b = nWW;
+    gh.bias = P;
+    gh.out = NW;
+    cudaError_t e;
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, kInPad, m->Xb, kInPad, m->W1b, kInPad, b1, nullptr, 0, m->A1,
+                                                     W, s, tcp(m), G, g1)) != cudaSuccess)
+        return e;
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A1, W, m->W2b, W, b2, nullptr, 0, m->A2, W, s, tcp(m),
+                                                     G, gh)) != cudaSuccess)
+        return e;
+    if ((e = gemm<false, false, EPI_BIAS_RELU_BF16>(N, W, W, m->A2, W, m->W3b, W, b3, nullptr, 0, m->A3, W, s, tcp(m),
+                                                     G, gh)) != cudaSuccess)
+        return e;
+    output_kernel<<<(unsigned)(((int64_t)G * N * 32 + 255) / 256), 256, 0, s>>>(
+        G, N, W, m->A3, m->W4b, b4, P, destandardize ? m->stdz : nullptr, y, sy);
+    return cudaGetLastError();
+}
+
+// Loss and gradient of every network for N rows each (network g: inputs
+// X[g st ..], targets t[g st ..], NaN = ignored); standardize: standardise targets.
+cudaError_t mlp_backward(fs_mlp* m, const float* X, const float* t, int64_t st, int N, bool standardize) {
+    using namespace fs;
+    const int W = m->W, G = m->G;
+    const int64_t P = m->P, NW = (int64_t)N * W, nWW = (int64_t)W * W;
     cudaStream_t s = m->stream;
     cudaError_t e;
     // training standardises the targets with (mu, sigma) kept for inference
     // in stdz[0..2]; the raw-target loss uses stdz[4..6] only for the count
-    float* st = standardize ? m->stdz : m->stdz + 4;
-    standardize_kernel<<<1, 256, 0, s>>>(N, t, st);
-    if ((e = mlp_forward(m, X, N, m->y, false)) != cudaSuccess) return e;
-    dloss_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, m->y, t, standardize ? m->stdz : nullptr, st + 2, m->dy, m->sq);
-    sum_kernel<<<1, 256, 0, s>>>(N, m->sq, m->loss);
-    const int64_t nW1 = (int64_t)W * 5, nWW = (int64_t)W * W;
+    float* sd = standardize ? m->stdz : m->stdz + 4;
+    standardize_kernel<<<G, 256, 0, s>>>(N, t, st, sd);
+    if ((e = mlp_forward(m, X, st, N, m->y, N, false)) != cudaSuccess) return e;
+    dloss_kernel<<<(unsigned)(((int64_t)G * N + 255) / 256), 256, 0, s>>>(G, N, m->y, t, st,
+                                                                          standardize ? m->stdz : nullptr, sd + 2,
+                                                                          m->dy, m->sq);
+    sum_kernel<<<G, 256, 0, s>>>(N, m->sq, m->loss, 1);
+    const int64_t nW1 = (int64_t)W * 5;
     float* gW1 = m->gr;
     float* gb1 = gW1 + nW1;
     float* gW2 = gb1 + W;
@@ -786,34 +874,109 @@ cudaError_t mlp_backward(fs_mlp* m, const float* X, const float* t, int N, bool 
     float* gb3 = gW3 + nWW;
     float* gW4 = gb3 + W;
     float* gb4 = gW4 + W;
+    GS gm;   // masked back-propagation GEMMs
+    gm.a = NW;
+    gm.b = nWW;
+    gm.mask = NW;
+    gm.out = NW;
     // output layer
-    if ((e = colsum<bf16>(N, W, m->A3, m->dy, gW4, m->part, s)) != cudaSuccess) return e;
-    sum_kernel<<<1, 256, 0, s>>>(N, m->dy, gb4);
-    dz_last_kernel<<<(unsigned)(((int64_t)N * W + 255) / 256), 256, 0, s>>>(N, W, m->dy, m->W4b, m->A3, m->dZa);
+    if ((e = colsum<bf16>(G, N, W, m->A3, m->dy, gW4, P, m->part, s)) != cudaSuccess) return e;
+    sum_kernel<<<G, 256, 0, s>>>(N, m->dy, gb4, P);
+    dz_last_kernel<<<(unsigned)(((int64_t)G * NW + 255) / 256), 256, 0, s>>>(G, N, W, m->dy, m->W4b, m->A3, m->dZa);
     // layer 3: dW3 = dZ3^T A2, db3, dZ2 = (dZ3 W3) * (A2 > 0)
-    if ((e = gemm_wgrad<true>(W, W, N, m->dZa, W, m->A2, W, gW3, m->ws, kMaxSplits, s, tcp(m))) != cudaSuccess) return e;
-    if ((e = colsum<bf16>(N, W, m->dZa, nullptr, gb3, m->part, s)) != cudaSuccess) return e;
-    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZa, W, m->W3b, W, nullptr, m->A2, W, m->dZb, W, s, tcp(m))) !=
+    if ((e = gemm_wgrad<true>(W, W, N, m->dZa, W, m->A2, W, gW3, m->ws, m->splits, s, tcp(m), G, NW, NW, P)) !=
         cudaSuccess)
+        return e;
+    if ((e = colsum<bf16>(G, N, W, m->dZa, nullptr, gb3, P, m->part, s)) != cudaSuccess) return e;
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZa, W, m->W3b, W, nullptr, m->A2, W, m->dZb, W, s, tcp(m), G,
+                                              gm)) != cudaSuccess)
         return e;
     // layer 2
-    if ((e = gemm_wgrad<true>(W, W, N, m->dZb, W, m->A1, W, gW2, m->ws, kMaxSplits, s, tcp(m))) != cudaSuccess) return e;
-    if ((e = colsum<bf16>(N, W, m->dZb, nullptr, gb2, m->part, s)) != cudaSuccess) return e;
-    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZb, W, m->W2b, W, nullptr, m->A1, W, m->dZa, W, s, tcp(m))) !=
+    if ((e = gemm_wgrad<true>(W, W, N, m->dZb, W, m->A1, W, gW2, m->ws, m->splits, s, tcp(m), G, NW, NW, P)) !=
         cudaSuccess)
         return e;
-    // layer 1 (padded input)
-    if ((e = gemm_wgrad<true>(W, kInPad, N, m->dZa, W, m->Xb, kInPad, m->g16, m->ws, kMaxSplits, s, tcp(m))) != cudaSuccess)
+    if ((e = colsum<bf16>(G, N, W, m->dZb, nullptr, gb2, P, m->part, s)) != cudaSuccess) return e;
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZb, W, m->W2b, W, nullptr, m->A1, W, m->dZa, W, s, tcp(m), G,
+                                              gm)) != cudaSuccess)
         return e;
-    unpad_kernel<<<(W * 5 + 255) / 256, 256, 0, s>>>(W, m->g16, gW1);
-    if ((e = colsum<bf16>(N, W, m->dZa, nullptr, gb1, m->part, s)) != cudaSuccess) return e;
+    // layer 1 (padded input)
+    if ((e = gemm_wgrad<true>(W, kInPad, N, m->dZa, W, m->Xb, kInPad, m->g16, m->ws, m->splits, s, tcp(m), G, NW,
+                              (int64_t)N * kInPad, (int64_t)W * kInPad)) != cudaSuccess)
+        return e;
+    unpad_kernel<<<(unsigned)(((int64_t)G * W * 5 + 255) / 256), 256, 0, s>>>(G, W, P, m->g16, gW1);
+    if ((e = colsum<bf16>(G, N, W, m->dZa, nullptr, gb1, P, m->part, s)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t mlp_refresh(fs_mlp* m) {
     const int64_t n = (int64_t)m->W * (m->W > fs::kInPad ? m->W : fs::kInPad);
-    fs::refresh_kernel<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->W, m->th, m->W1b, m->W2b, m->W3b, m->W4b);
+    fs::refresh_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)m->G), 256, 0, m->stream>>>(
+        m->W, m->P, m->th, m->W1b, m->W2b, m->W3b, m->W4b);
     return cudaGetLastError();
+}
+
+fs_status mlp_create(fs_mlp** out, int groups, int width, int max_batch, uint64_t seed, void* stream,
+                     const char* who) {
+    fs::set_error(FS_OK, "");
+    if (!out) return fs::set_error(FS_EINVAL, "%s: out is NULL", who);
+    *out = nullptr;
+    if (width < 8 || width > 1024 || width % 8 != 0 || max_batch < 1 || groups < 1 || groups > 1024)
+        return fs::set_error(FS_EINVAL,
+                             "%s: need width in [8, 1024], a multiple of 8, max_batch >= 1, groups in [1, 1024]", who);
+    fs_mlp* m = new (std::nothrow) fs_mlp;
+    if (!m) return fs::set_error(FS_ENOMEM, "%s: host allocation failed", who);
+    memset(m, 0, sizeof(*m));
+    const int W = width;
+    const size_t G = (size_t)groups;
+    m->G = groups;
+    m->W = W;
+    m->cap = max_batch;
+    m->P = nparams(W);
+    m->stream = (cudaStream_t)stream;
+    // the weight-gradient GEMMs split K = rows into chunks of at least 256
+    m->splits = (max_batch + 255) / 256 < fs::kMaxSplits ? (max_batch + 255) / 256 : fs::kMaxSplits;
+    const size_t act = sizeof(fs::bf16) * G * max_batch * W;
+    const size_t PG = sizeof(float) * G * m->P;
+    const size_t nb = (size_t)(max_batch + fs::kColRows - 1) / fs::kColRows;
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->th, PG)) != cudaSuccess || (e = cudaMalloc(&m->gr, PG)) != cudaSuccess ||
+        (e = cudaMalloc(&m->m, PG)) != cudaSuccess || (e = cudaMalloc(&m->v, PG)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W1b, sizeof(fs::bf16) * G * W * fs::kInPad)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W2b, sizeof(fs::bf16) * G * W * W)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W3b, sizeof(fs::bf16) * G * W * W)) != cudaSuccess ||
+        (e = cudaMalloc(&m->W4b, sizeof(fs::bf16) * G * W)) != cudaSuccess ||
+        (e = cudaMalloc(&m->Xb, sizeof(fs::bf16) * G * max_batch * fs::kInPad)) != cudaSuccess ||
+        (e = cudaMalloc(&m->A1, act)) != cudaSuccess || (e = cudaMalloc(&m->A2, act)) != cudaSuccess ||
+        (e = cudaMalloc(&m->A3, act)) != cudaSuccess || (e = cudaMalloc(&m->dZa, act)) != cudaSuccess ||
+        (e = cudaMalloc(&m->dZb, act)) != cudaSuccess ||
+        (e = cudaMalloc(&m->y, sizeof(float) * G * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&m->dy, sizeof(float) * G * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&m->sq, sizeof(float) * G * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&m->g16, sizeof(float) * G * W * fs::kInPad)) != cudaSuccess ||
+        (e = cudaMalloc(&m->stdz, sizeof(float) * G * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&m->loss, sizeof(float) * G)) != cudaSuccess ||
+        (e = cudaMalloc(&m->adamc, sizeof(float) * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&m->tc_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&m->ws, sizeof(float) * G * m->splits * W * (W > fs::kInPad ? W : fs::kInPad))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&m->part, sizeof(float) * G * nb * W)) != cudaSuccess) {
+        mlp_free(m);
+        delete m;
+        return mlp_fail(e, who);
+    }
+    fs::init_kernel<<<dim3((unsigned)((m->P + 255) / 256), (unsigned)G), 256, 0, m->stream>>>(W, seed, m->th);
+    if ((e = cudaMemsetAsync(m->m, 0, PG, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->v, 0, PG, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->adamc, 0, sizeof(float) * 4, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream)) != cudaSuccess ||
+        (e = reset_stdz(m)) != cudaSuccess || (e = mlp_refresh(m)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+        mlp_free(m);
+        delete m;
+        return mlp_fail(e, who);
+    }
+    *out = m;
+    return FS_OK;
 }
 
 }  // namespace
@@ -823,64 +986,14 @@ extern "C" {
 int64_t fs_mlp_num_params(int width) { return width > 0 ? nparams(width) : -1; }
 
 fs_status fs_mlp_create(fs_mlp** out, int width, int max_batch, uint64_t seed, void* stream) {
-    fs::set_error(FS_OK, "");
-    if (!out) return fs::set_error(FS_EINVAL, "fs_mlp_create: out is NULL");
-    *out = nullptr;
-    if (width < 8 || width > 1024 || width % 8 != 0 || max_batch < 1)
-        return fs::set_error(FS_EINVAL, "fs_mlp_create: need width in [8, 1024], a multiple of 8, max_batch >= 1");
-    fs_mlp* m = new (std::nothrow) fs_mlp;
-    if (!m) return fs::set_error(FS_ENOMEM, "fs_mlp_create: host allocation failed");
-    memset(m, 0, sizeof(*m));
-    m->W = width;
-    m->cap = max_batch;
-    m->P = nparams(width);
-    m->stream = (cudaStream_t)stream;
-    const int W = width;
-    const size_t act = sizeof(fs::bf16) * (size_t)max_batch * W;
-    cudaError_t e;
-    if ((e = cudaMalloc(&m->th, sizeof(float) * m->P)) != cudaSuccess ||
-        (e = cudaMalloc(&m->gr, sizeof(float) * m->P)) != cudaSuccess ||
-        (e = cudaMalloc(&m->m, sizeof(float) * m->P)) != cudaSuccess ||
-        (e = cudaMalloc(&m->v, sizeof(float) * m->P)) != cudaSuccess ||
-        (e = cudaMalloc(&m->W1b, sizeof(fs::bf16) * W * fs::kInPad)) != cudaSuccess ||
-        (e = cudaMalloc(&m->W2b, sizeof(fs::bf16) * W * W)) != cudaSuccess ||
-        (e = cudaMalloc(&m->W3b, sizeof(fs::bf16) * W * W)) != cudaSuccess ||
-        (e = cudaMalloc(&m->W4b, sizeof(fs::bf16) * W)) != cudaSuccess ||
-        (e = cudaMalloc(&m->Xb, sizeof(fs::bf16) * (size_t)max_batch * fs::kInPad)) != cudaSuccess ||
-        (e = cudaMalloc(&m->A1, act)) != cudaSuccess || (e = cudaMalloc(&m->A2, act)) != cudaSuccess ||
-        (e = cudaMalloc(&m->A3, act)) != cudaSuccess || (e = cudaMalloc(&m->dZa, act)) != cudaSuccess ||
-        (e = cudaMalloc(&m->dZb, act)) != cudaSuccess ||
-        (e = cudaMalloc(&m->y, sizeof(float) * max_batch)) != cudaSuccess ||
-        (e = cudaMalloc(&m->dy, sizeof(float) * max_batch)) != cudaSuccess ||
-        (e = cudaMalloc(&m->sq, sizeof(float) * max_batch)) != cudaSuccess ||
-        (e = cudaMalloc(&m->g16, sizeof(float) * W * fs::kInPad)) != cudaSuccess ||
-        (e = cudaMalloc(&m->stdz, sizeof(float) * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&m->loss, sizeof(float) * 1)) != cudaSuccess ||
-        (e = cudaMalloc(&m->adamc, sizeof(float) * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&m->tc_err, sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&m->ws, sizeof(float) * fs::kMaxSplits * W * (W > fs::kInPad ? W : fs::kInPad))) !=
-            cudaSuccess ||
-        (e = cudaMalloc(&m->part, sizeof(float) * ((max_batch + fs::kColRows - 1) / fs::kColRows) * W)) !=
-            cudaSuccess) {
-        mlp_free(m);
-        delete m;
-        return mlp_fail(e, "fs_mlp_create: cudaMalloc");
-    }
-    const float one[4] = {0.f, 1.f, 0.f, 0.f};
-    fs::init_kernel<<<(unsigned)((m->P + 255) / 256), 256, 0, m->stream>>>(W, seed, m->th);
-    if ((e = cudaMemsetAsync(m->m, 0, sizeof(float) * m->P, m->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(m->v, 0, sizeof(float) * m->P, m->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(m->adamc, 0, sizeof(float) * 4, m->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(m->stdz, one, sizeof(one), cudaMemcpyHostToDevice, m->stream)) != cudaSuccess ||
-        (e = mlp_refresh(m)) != cudaSuccess || (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
-        mlp_free(m);
-        delete m;
-        return mlp_fail(e, "fs_mlp_create: initialisation");
-    }
-    *out = m;
-    return FS_OK;
+    return mlp_create(out, 1, width, max_batch, seed, stream, "fs_mlp_create");
 }
+
+fs_status fs_mlp_create_group(fs_mlp** out, int groups, int width, int max_batch, uint64_t seed, void* stream) {
+    return mlp_create(out, groups, width, max_batch, seed, stream, "fs_mlp_create_group");
+}
+
+int fs_mlp_groups(const fs_mlp* m) { return m ? m->G : -1; }
 
 fs_status fs_mlp_destroy(fs_mlp* m) {
     if (!m) return FS_OK;
@@ -893,10 +1006,10 @@ fs_status fs_mlp_destroy(fs_mlp* m) {
 fs_status fs_mlp_set_params(fs_mlp* m, const float* theta_dev) {
     fs::set_error(FS_OK, "");
     if (!m || !theta_dev) return fs::set_error(FS_EINVAL, "fs_mlp_set_params: NULL argument");
-    cudaError_t e = cudaMemcpyAsync(m->th, theta_dev, sizeof(float) * m->P, cudaMemcpyDeviceToDevice, m->stream);
+    cudaError_t e =
+        cudaMemcpyAsync(m->th, theta_dev, sizeof(float) * m->G * m->P, cudaMemcpyDeviceToDevice, m->stream);
     if (e != cudaSuccess || (e = mlp_refresh(m)) != cudaSuccess) return mlp_fail(e, "fs_mlp_set_params");
-    const float one[4] = {0.f, 1.f, 0.f, 0.f};
-    if ((e = cudaMemcpyAsync(m->stdz, one, sizeof(one), cudaMemcpyHostToDevice, m->stream)) != cudaSuccess ||
+    if ((e = reset_stdz(m)) != cudaSuccess ||
         (e = cudaMemsetAsync(m->adamc, 0, sizeof(float) * 4, m->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(m->stream)) != cudaSuccess)
         return mlp_fail(e, "fs_mlp_set_params");
@@ -907,7 +1020,8 @@ fs_status fs_mlp_set_params(fs_mlp* m, const float* theta_dev) {
 fs_status fs_mlp_get_params(fs_mlp* m, float* theta_dev) {
     fs::set_error(FS_OK, "");
     if (!m || !theta_dev) return fs::set_error(FS_EINVAL, "fs_mlp_get_params: NULL argument");
-    cudaError_t e = cudaMemcpyAsync(theta_dev, m->th, sizeof(float) * m->P, cudaMemcpyDeviceToDevice, m->stream);
+    cudaError_t e =
+        cudaMemcpyAsync(theta_dev, m->th, sizeof(float) * m->G * m->P, cudaMemcpyDeviceToDevice, m->stream);
     if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_get_params");
     return FS_OK;
 }
@@ -944,7 +1058,7 @@ fs_status fs_mlp_forward(fs_mlp* m, const float* X_dev, int N, float* y_dev) {
     if (!m || N < 0 || (N > 0 && (!X_dev || !y_dev))) return fs::set_error(FS_EINVAL, "fs_mlp_forward: bad argument");
     for (int off = 0; off < N; off += m->cap) {
         const int n = N - off < m->cap ? N - off : m->cap;
-        cudaError_t e = mlp_forward(m, X_dev + (int64_t)off * 5, n, y_dev + off, true);
+        cudaError_t e = mlp_forward(m, X_dev + (int64_t)off * 5, N, n, y_dev + off, N, true);
         if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_forward");
     }
     return FS_OK;
@@ -955,13 +1069,13 @@ fs_status fs_mlp_loss_grad(fs_mlp* m, const float* X_dev, const float* t_dev, in
     fs::set_error(FS_OK, "");
     if (!m || N < 1 || N > m->cap || !X_dev || !t_dev)
         return fs::set_error(FS_EINVAL, "fs_mlp_loss_grad: need 1 <= N <= max_batch and non-NULL X, t");
-    cudaError_t e = mlp_backward(m, X_dev, t_dev, N, false);
+    cudaError_t e = mlp_backward(m, X_dev, t_dev, N, N, false);
     if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_loss_grad");
-    if (grad_dev && (e = cudaMemcpyAsync(grad_dev, m->gr, sizeof(float) * m->P, cudaMemcpyDeviceToDevice,
+    if (grad_dev && (e = cudaMemcpyAsync(grad_dev, m->gr, sizeof(float) * m->G * m->P, cudaMemcpyDeviceToDevice,
                                          m->stream)) != cudaSuccess)
         return mlp_fail(e, "fs_mlp_loss_grad copy");
-    if (loss_dev && (e = cudaMemcpyAsync(loss_dev, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, m->stream)) !=
-                        cudaSuccess)
+    if (loss_dev && (e = cudaMemcpyAsync(loss_dev, m->loss, sizeof(float) * m->G, cudaMemcpyDeviceToDevice,
+                                         m->stream)) != cudaSuccess)
         return mlp_fail(e, "fs_mlp_loss_grad copy");
     return FS_OK;
 }
@@ -971,17 +1085,18 @@ fs_status fs_mlp_train(fs_mlp* m, const float* X_dev, const float* t_dev, int N,
     fs::set_error(FS_OK, "");
     if (!m || N < 1 || N > m->cap || steps < 0 || !X_dev || !t_dev || !(lr > 0.f))
         return fs::set_error(FS_EINVAL, "fs_mlp_train: need 1 <= N <= max_batch, steps >= 0, lr > 0");
+    const int64_t PG = (int64_t)m->G * m->P;
     for (int it = 0; it < steps; it++) {
-        cudaError_t e = mlp_backward(m, X_dev, t_dev, N, true);
+        cudaError_t e = mlp_backward(m, X_dev, t_dev, N, N, true);
         if (e != cudaSuccess) return mlp_fail(e, "fs_mlp_train backward");
         m->step++;
         fs::adam_prep_kernel<<<1, 1, 0, m->stream>>>(m->adamc);
-        fs::adam_kernel<<<(unsigned)((m->P + 255) / 256), 256, 0, m->stream>>>(m->P, m->th, m->gr, m->m, m->v, lr,
-                                                                                m->adamc);
+        fs::adam_kernel<<<(unsigned)((PG + 255) / 256), 256, 0, m->stream>>>(PG, m->th, m->gr, m->m, m->v, lr,
+                                                                              m->adamc);
         if ((e = cudaGetLastError()) != cudaSuccess || (e = mlp_refresh(m)) != cudaSuccess)
             return mlp_fail(e, "fs_mlp_train update");
-        if (loss_dev && (e = cudaMemcpyAsync(loss_dev + it, m->loss, sizeof(float), cudaMemcpyDeviceToDevice,
-                                             m->stream)) != cudaSuccess)
+        if (loss_dev && (e = cudaMemcpyAsync(loss_dev + (int64_t)it * m->G, m->loss, sizeof(float) * m->G,
+                                             cudaMemcpyDeviceToDevice, m->stream)) != cudaSuccess)
             return mlp_fail(e, "fs_mlp_train copy");
     }
     return FS_OK;

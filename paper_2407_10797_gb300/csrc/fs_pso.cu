@@ -335,10 +335,13 @@ cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, c
                                                                        cin, inside, run0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // network g ranks the candidates of runs [g R / n_mlp, (g + 1) R / n_mlp), which are contiguous
-    const int64_t per = nc / n_mlp;
-    for (int g = 0; g < n_mlp; g++)
-        if (fs_mlp_forward(mlps[g], cin + g * per * 5, (int)per, score + g * per) != FS_OK)
+    // the networks' groups, in order, split the runs into equal contiguous blocks:
+    // group j ranks the candidates of runs [j R / ng, (j + 1) R / ng)
+    int ng = 0;
+    for (int i = 0; i < n_mlp; i++) ng += fs_mlp_groups(mlps[i]);
+    const int64_t per = nc / ng;
+    for (int i = 0, j = 0; i < n_mlp; j += fs_mlp_groups(mlps[i]), i++)
+        if (fs_mlp_forward(mlps[i], cin + j * per * 5, (int)per, score + j * per) != FS_OK)
             return cudaErrorLaunchFailure;
     pso_select_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, C, score, inside, cx, cv, x, v);
     if ((e = cudaGetLastError()) != cudaSuccess || !iter_advance) return e;

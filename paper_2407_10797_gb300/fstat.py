@@ -101,6 +101,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_mlp_num_params.argtypes = [C.c_int]
         L.fs_mlp_num_params.restype = C.c_int64
         L.fs_mlp_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_uint64, _vp]
+        L.fs_mlp_create_group.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_uint64, _vp]
+        L.fs_mlp_groups.argtypes = [_vp]
+        L.fs_mlp_groups.restype = C.c_int
         L.fs_mlp_destroy.argtypes = [_vp]
         L.fs_mlp_set_tensor_path.argtypes = [_vp, C.c_int]
         L.fs_mlp_tensor_status.argtypes = [_vp, C.POINTER(C.c_int)]
@@ -117,7 +120,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                      "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
                      "fs_plan_autotune", "fs_pso_autotune", "fs_plan_census", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
                      "fs_pso_graph_build", "fs_pso_graph_build_ex", "fs_pso_record", "fs_mlp_train_graph_build",
-                     "fs_graph_run", "fs_graph_destroy", "fs_mlp_create",
+                     "fs_graph_run", "fs_graph_destroy", "fs_mlp_create", "fs_mlp_create_group",
                      "fs_mlp_destroy", "fs_mlp_set_tensor_path", "fs_mlp_tensor_status", "fs_mlp_set_params", "fs_mlp_get_params", "fs_mlp_forward",
                      "fs_mlp_loss_grad", "fs_mlp_train", "fs_pso_step_screened"):
             getattr(L, name).restype = C.c_int
@@ -471,8 +474,9 @@ def mlp_train_graph(nets, rings, steps: int, lr: float = 1e-3) -> "Graph":
     whole contents, captured as one graph."""
     arr = _mlp_array(nets)
     rarr = _ring_array(rings)
-    if len(arr) != len(rarr):
-        raise ValueError("one ring per network")
+    nlist = list(nets) if isinstance(nets, (list, tuple)) else [nets]
+    if sum(n.groups for n in nlist) != len(rarr):
+        raise ValueError("one ring per network (a batch of G networks takes G rings from SampleRing.batch)")
     h = C.c_void_p()
     _check(load().fs_mlp_train_graph_build(arr, len(arr), rarr, int(steps), float(lr), C.byref(h)))
     return Graph(h)
@@ -511,6 +515,24 @@ class SampleRing:
         self.count = torch.zeros(1, dtype=torch.int64, device=dev)
         self.c = fs_sample_ring(self.x.data_ptr(), self.f.data_ptr(), self.cap, self.count.data_ptr())
 
+    @classmethod
+    def batch(cls, n: int, cap: int, device=None) -> list:
+        """n rings of one capacity laid end to end in one buffer (x: [n][cap][5],
+        f: [n][cap]), the layout a batch of n networks trains on."""
+        import torch
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        x = torch.zeros(n, int(cap), 5, dtype=torch.float32, device=dev)
+        f = torch.full((n, int(cap)), float("nan"), dtype=torch.float32, device=dev)
+        count = torch.zeros(n, dtype=torch.int64, device=dev)
+        out = []
+        for j in range(n):
+            r = cls.__new__(cls)
+            r.cap = int(cap)
+            r.x, r.f, r.count = x[j], f[j], count[j:j + 1]
+            r.c = fs_sample_ring(r.x.data_ptr(), r.f.data_ptr(), r.cap, r.count.data_ptr())
+            out.append(r)
+        return out
+
 
 def torch_tensor(a):
     import torch
@@ -518,17 +540,36 @@ def torch_tensor(a):
 
 
 class MLP:
-    """Surrogate network (fs_mlp): 5 -> width^3 -> 1, bf16 tensor-core kernels."""
+    """Surrogate network (fs_mlp): 5 -> width^3 -> 1, bf16 tensor-core kernels.
 
-    def __init__(self, width: int = 256, max_batch: int = 8192, seed: int = 0, stream=None):
+    groups > 1 makes a batch of independent networks (network g seeded
+    seed + g) that every kernel evaluates and trains together; its inputs are
+    then [groups][N][5], targets and outputs [groups][N], parameters
+    [groups][P]."""
+
+    def __init__(self, width: int = 256, max_batch: int = 8192, seed: int = 0, stream=None, groups: int = 1):
         import torch
         self._L = load()
         self.width = int(width)
+        self.groups = int(groups)
         self.P = int(self._L.fs_mlp_num_params(self.width))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        _check(self._L.fs_mlp_create(C.byref(h), self.width, int(max_batch), int(seed), _stream_handle(self.stream)))
+        if self.groups == 1:
+            _check(self._L.fs_mlp_create(C.byref(h), self.width, int(max_batch), int(seed),
+                                         _stream_handle(self.stream)))
+        else:
+            _check(self._L.fs_mlp_create_group(C.byref(h), self.groups, self.width, int(max_batch), int(seed),
+                                               _stream_handle(self.stream)))
         self._h = h
+
+    def _rows(self, X):
+        """Rows per network of an input batch ([N][5] for one network, [G][N][5] for G)."""
+        if self.groups == 1:
+            return int(X.reshape(-1, 5).shape[0])
+        if X.dim() != 3 or X.shape[0] != self.groups or X.shape[2] != 5:
+            raise ValueError(f"a batch of {self.groups} networks takes inputs [{self.groups}][N][5]")
+        return int(X.shape[1])
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -553,7 +594,8 @@ class MLP:
 
     def params(self):
         import torch
-        out = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        out = torch.empty(self.P if self.groups == 1 else (self.groups, self.P), dtype=torch.float32,
+                          device="cuda")
         self.stream.synchronize()   # out was made on the current stream; the copy runs on the network's
         _check(self._L.fs_mlp_get_params(self._h, _cuda_ptr(out, torch.float32)))
         self.stream.synchronize()
@@ -567,26 +609,29 @@ class MLP:
     def forward(self, X, y=None):
         import torch
         X = X.to(torch.float32).contiguous()
+        n = self._rows(X)
         if y is None:
-            y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
-        _check(self._L.fs_mlp_forward(self._h, _cuda_ptr(X, torch.float32), int(X.shape[0]), _cuda_ptr(y, torch.float32)))
+            y = torch.empty(X.shape[:-1], dtype=torch.float32, device=X.device)
+        _check(self._L.fs_mlp_forward(self._h, _cuda_ptr(X, torch.float32), n, _cuda_ptr(y, torch.float32)))
         return y
 
     def loss_grad(self, X, t):
         import torch
         X = X.to(torch.float32).contiguous()
         t = t.to(torch.float32).contiguous()
-        g = torch.empty(self.P, dtype=torch.float32, device=X.device)
-        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        g = torch.empty(self.groups * self.P, dtype=torch.float32, device=X.device)
+        L = torch.empty(self.groups, dtype=torch.float32, device=X.device)
         _check(self._L.fs_mlp_loss_grad(self._h, _cuda_ptr(X, torch.float32), _cuda_ptr(t, torch.float32),
-                                        int(X.shape[0]), _cuda_ptr(g, torch.float32), _cuda_ptr(L, torch.float32)))
+                                        self._rows(X), _cuda_ptr(g, torch.float32), _cuda_ptr(L, torch.float32)))
         return L, g
 
     def train(self, X, t, steps: int, lr: float = 1e-3):
         import torch
         X = X.to(torch.float32).contiguous()
         t = t.to(torch.float32).contiguous()
-        losses = torch.empty(max(int(steps), 1), dtype=torch.float32, device=X.device)
+        losses = torch.empty(max(int(steps), 1) * self.groups, dtype=torch.float32, device=X.device)
         _check(self._L.fs_mlp_train(self._h, _cuda_ptr(X, torch.float32), _cuda_ptr(t, torch.float32),
-                                    int(X.shape[0]), int(steps), float(lr), _cuda_ptr(losses, torch.float32)))
+                                    self._rows(X), int(steps), float(lr), _cuda_ptr(losses, torch.float32)))
+        if self.groups > 1:
+            losses = losses.reshape(-1, self.groups)
         return losses

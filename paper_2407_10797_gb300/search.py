@@ -284,20 +284,22 @@ class HierarchicalSearch:
         """n_iter - 1 iterations of evaluate + record + (screened) step with one
         network and one sample ring per search box: positions are normalised
         to each run's box, so the runs of a box share a landscape and the
-        boxes do not.  Every train_every iterations after the warm-up each
-        network trains on its box's ring.  With graphs (default) an iteration
-        is two captured launches, (evaluate + record) and the step, with the
-        captured training round in between when due; the eager form makes the
-        same calls."""
+        boxes do not.  The boxes' networks form one batch (every kernel of a
+        forward or training pass covers all of them) and their rings are
+        slices of one buffer.  Every train_every iterations after the warm-up
+        each network trains on its box's ring.  With graphs (default) an
+        iteration is two captured launches, (evaluate + record) and the step,
+        with the captured training round in between when due; the eager form
+        makes the same calls."""
         import torch
         sp = self.surrogate
         nb = self.n_boxes if nb is None else nb
         dev = sw.x.device
-        # one network per box, seeded by the box's global index
-        self.mlps = [fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed * 1000 + 97 * stage + k0 + k,
-                               stream=self.plan.stream) for k in range(nb)]
-        self.mlp = self.mlps[0]
-        rings = [fstat.SampleRing(sp.buffer, device=dev) for _ in range(nb)]
+        # network k of the batch belongs to box k0 + k and is seeded by that global index
+        self.mlp = fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed * 1000 + 97 * stage + k0,
+                             stream=self.plan.stream, groups=nb)
+        self.mlps = [self.mlp]
+        rings = fstat.SampleRing.batch(nb, sp.buffer, device=dev)
         step_kw = dict(w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter, c1=self.c1, c2=self.c2, vmax=self.vmax)
         graphs = None
         if self.use_graphs:
@@ -318,8 +320,8 @@ class HierarchicalSearch:
                 if graphs:
                     graphs[3].run(1)
                 else:
-                    for net, ring in zip(self.mlps, rings):
-                        net.train(ring.x, ring.f, sp.train_steps, sp.lr)
+                    self.mlp.train(torch.stack([r.x for r in rings]), torch.stack([r.f for r in rings]),
+                                   sp.train_steps, sp.lr)
             if graphs:
                 graphs[2 if screened else 1].run(1)
             elif screened:
