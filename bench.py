@@ -57,7 +57,7 @@ FP64_DIRECT_FLOP = 203.0
 # profiles/mixed_persistent_paper_grid_B320_Np16.md.  Both are one pass over the
 # per-bin tables and do not depend on N_p; the FP64 figure holds for the
 # anchored variants (3, 4) only.
-TRAFFIC_FP64_ANCHORED = 76.16e6
+TRAFFIC_FP64_ANCHORED = 76.13e6
 TRAFFIC_MIXED = 48.35e6
 FP64_TIER_FLOP = {1: 96.0, 2: FP64_DIRECT_FLOP, 3: 84.0, 4: 76.0, 5: 70.0}
 
