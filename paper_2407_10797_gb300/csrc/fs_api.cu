@@ -694,8 +694,19 @@ fs_status fs_pso_record(fs_plan* p, const fs_swarm* w, const fs_sample_ring* rin
         const fs_sample_ring& r = rings[g];
         if (!r.x || !r.f || !r.count || r.cap < 1)
             return fail(FS_EINVAL, "fs_pso_record: ring %d needs x, f, count and cap >= 1", g);
-        cudaError_t e = fs::launch_pso_record(per, w->x + (int64_t)g * per * 5, w->fit + (int64_t)g * per, r.x, r.f,
-                                              r.cap, r.count, p->stream);
+    }
+    // one launch per kRingBatch rings
+    for (int g0 = 0; g0 < n_rings; g0 += fs::kRingBatch) {
+        const int nr = n_rings - g0 < fs::kRingBatch ? n_rings - g0 : fs::kRingBatch;
+        fs::RingBatch rb{};
+        for (int j = 0; j < nr; j++) {
+            rb.x[j] = rings[g0 + j].x;
+            rb.f[j] = rings[g0 + j].f;
+            rb.count[j] = rings[g0 + j].count;
+            rb.cap[j] = rings[g0 + j].cap;
+        }
+        cudaError_t e = fs::launch_pso_record(nr, per, w->x + (int64_t)g0 * per * 5, w->fit + (int64_t)g0 * per, rb,
+                                              p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "pso record launch");
     }
     return FS_OK;

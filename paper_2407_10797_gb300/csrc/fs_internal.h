@@ -98,8 +98,16 @@ cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, c
                                 double vmax, double* x, double* v, double* pbx, double* pbf, const double* fit,
                                 double* cx, double* cv, float* cin, unsigned char* inside, float* score,
                                 ::fs_mlp* const* mlps, int n_mlp, unsigned int* iter_advance, int run0, cudaStream_t s);
-cudaError_t launch_pso_record(int n, const double* x, const double* fit, float* rx, float* rf, int cap,
-                              unsigned long long* count, cudaStream_t s);
+// Up to kRingBatch sample rings, passed to the record kernels by value.
+constexpr int kRingBatch = 32;
+struct RingBatch {
+    float* x[kRingBatch];
+    float* f[kRingBatch];
+    unsigned long long* count[kRingBatch];
+    int cap[kRingBatch];
+};
+cudaError_t launch_pso_record(int nr, int per, const double* x, const double* fit, const RingBatch& rb,
+                              cudaStream_t s);
 cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);
 cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,
                               double* data, cudaStream_t s);

@@ -298,26 +298,34 @@ cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsign
 
 // Surrogate training samples: positions as floats, non-finite fitness as
 // NaN, into slot (count + i) mod cap of a ring; the counter advances after.
-__global__ void pso_record_kernel(int n, const double* __restrict__ x, const double* __restrict__ fit, float* rx,
-                                  float* rf, int cap, const unsigned long long* count) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t j = (int64_t)((*count + (unsigned long long)i) % (unsigned long long)cap);
+// Sample append for up to kRingBatch rings in one launch: particle k of ring g
+// (the g-th block of `per` particles) goes to slot (count_g + k) mod cap_g.
+__global__ void pso_record_kernel(int nr, int per, const double* __restrict__ x, const double* __restrict__ fit,
+                                  RingBatch rb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nr * per) return;
+    const int g = (int)(i / per), k = (int)(i % per);
+    const int64_t j = (int64_t)((*rb.count[g] + (unsigned long long)k) % (unsigned long long)rb.cap[g]);
+    float* rx = rb.x[g];
 #pragma unroll
-    for (int d = 0; d < 5; d++) rx[j * 5 + d] = (float)x[(int64_t)i * 5 + d];
+    for (int d = 0; d < 5; d++) rx[j * 5 + d] = (float)x[i * 5 + d];
     const double f = fit[i];
-    rf[j] = isfinite(f) ? (float)f : __int_as_float(0x7fc00000);
+    rb.f[g][j] = isfinite(f) ? (float)f : __int_as_float(0x7fc00000);
 }
 
-__global__ void ring_advance_kernel(unsigned long long* count, int n) { *count += (unsigned long long)n; }
+__global__ void ring_advance_kernel(int nr, int per, RingBatch rb) {
+    const int g = threadIdx.x;
+    if (g < nr) *rb.count[g] += (unsigned long long)per;
+}
 
-cudaError_t launch_pso_record(int n, const double* x, const double* fit, float* rx, float* rf, int cap,
-                              unsigned long long* count, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    pso_record_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, x, fit, rx, rf, cap, count);
+cudaError_t launch_pso_record(int nr, int per, const double* x, const double* fit, const RingBatch& rb,
+                              cudaStream_t s) {
+    if (nr <= 0 || per <= 0) return cudaSuccess;
+    const int64_t n = (int64_t)nr * per;
+    pso_record_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(nr, per, x, fit, rb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ring_advance_kernel<<<1, 1, 0, s>>>(count, n);
+    ring_advance_kernel<<<1, kRingBatch, 0, s>>>(nr, per, rb);
     return cudaGetLastError();
 }
 

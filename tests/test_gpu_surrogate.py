@@ -158,3 +158,33 @@ def test_training_graph_matches_eager(env):
         assert torch.equal(a.params(), b.params())
     assert not torch.equal(eager[0].params(), nets(fstat, s, (31,))[0].params())   # training moved the weights
     g.close()
+
+
+def test_many_rings_in_batches_of_launches(env):
+    """40 rings (one launch covers 32): every ring holds its own runs'
+    samples after two appends that wrap its 7 slots."""
+    fstat, plan, s, _ = env
+    box = np.zeros((40, 5, 2))
+    box[:, 0] = (20.0, 40.0)
+    box[:, 1] = (0.0, 1e7)
+    box[:, 2] = (-1.0, 1.0)
+    box[:, 3] = (0.0, 2 * np.pi)
+    box[:, 4] = (0.0, 0.1)
+    with torch.cuda.stream(s):
+        sw = fstat.Swarm(plan, 40, 4, box)
+        sw.init(5)
+        sw.evaluate(4)
+        rings = fstat.SampleRing.batch(40, 7)
+        sw.record(rings)
+        sw.record(rings)                       # 2 x 4 samples into 7 slots
+    torch.cuda.synchronize()
+    x = sw.x.reshape(40, 4, 5).float()
+    f = sw.fit.reshape(40, 4)
+    for g, r in enumerate(rings):
+        assert int(r.count.item()) == 8
+        for slot in range(7):
+            # append 1 wrote samples 0-3 to slots 0-3, append 2 samples 0-3 to slots 4, 5, 6, 0
+            i = 3 if slot == 0 else (slot if slot < 4 else slot - 4)
+            assert torch.equal(r.x[slot], x[g, i])
+            fv = float(f[g, i])
+            assert (np.isnan(float(r.f[slot])) if not np.isfinite(fv) else float(r.f[slot]) == np.float32(fv))
