@@ -94,6 +94,75 @@ __device__ int64_t warp_search_first(int64_t lo, int64_t hi, Pred pred) {
     return m ? lo + (__ffs(m) - 1) : hi;
 }
 
+// Continuous solution f of t(f) = target (the band edge's frequency, Sec. II's
+// band [f(t = 0), f(t = T_obs)]): the Newtonian chirp t - t_c = T0 f^-8/3 gives
+// the start, Newton steps with the slope of the same series refine it,
+//   dt/df = -(1/f) [8/3 T0 f^-8/3 + 2 T2 f^-2 + 5/3 T3 f^-5/3 + 4/3 T4 f^-4/3
+//                   + (8/3 + 19/9) TE f^-8/3 (f0/f)^(19/9)].
+// +inf when the target is at or after coalescence at Newtonian order, NaN if
+// the steps fail; the caller only uses it to place a window that it checks.
+__device__ double edge_freq(const Particle& P, double target) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (!(P.T0 < 0.0)) return nan;
+    const double x0 = (target - P.tc) / P.T0;
+    if (!(x0 > 0.0)) return __longlong_as_double(0x7ff0000000000000LL);
+    double f = pow(x0, -0.375);
+    for (int it = 0; it < 8; it++) {
+        const FreqPowers w = powers_of(f);
+        const double u2 = w.u * w.u, u3 = u2 * w.u, u4 = u2 * u2, u6 = u3 * u3;
+        const double g83 = w.g0h * u3;
+        double s = P.T0 * g83;
+        s = fma(P.T2, u6, s);
+        s = fma(P.T3, w.g0h, s);
+        s = fma(P.T4, u4, s);
+        s = fma(P.TE * g83, w.e19, s);
+        double sl = (8.0 / 3.0) * P.T0 * g83;
+        sl = fma(2.0 * P.T2, u6, sl);
+        sl = fma((5.0 / 3.0) * P.T3, w.g0h, sl);
+        sl = fma((4.0 / 3.0) * P.T4, u4, sl);
+        sl = fma((8.0 / 3.0 + 19.0 / 9.0) * P.TE * g83, w.e19, sl);
+        const double step = (P.tc + s - target) * f / sl;   // (t - target) / (dt/df), dt/df = -sl / f
+        const double fn = f + step;
+        if (!(fn > 0.0)) return nan;
+        f = fn;
+        if (fabs(step) <= 1e-10 * f) break;
+    }
+    return f;
+}
+
+constexpr int kEdgeWin = 16;   // bins per edge window (half a warp)
+
+// First bin of the window that should hold the boundary at frequency fe: 7
+// bins below it, clamped into [0, n - kEdgeWin]; -1 if fe gives no position.
+__device__ int64_t edge_window(const Grid& g, double fe) {
+    const int64_t top = g.n > kEdgeWin ? g.n - kEdgeWin : 0;
+    if (fe != fe) return -1;
+    const double kf = (fe - g.f_min) / g.df;
+    if (!(kf < (double)g.n)) return top;   // includes +inf: above the grid
+    if (kf < 8.0) return 0;
+    const int64_t k0 = (int64_t)floor(kf) - 7;
+    return k0 < top ? k0 : top;
+}
+
+// First k in [0, n) with pred(k) true (n if none), for a predicate that is
+// false then true along k, from the probes of the window [k0, k0 + kEdgeWin)
+// (bit j of m: pred(k0 + j), false for k0 + j >= n): exact when the window
+// shows the change (a false probe right before the first true one, or the
+// window at an end of [0, n)); *ok = false otherwise.
+__device__ int64_t first_in_window(int64_t n, int64_t k0, unsigned m, bool* ok) {
+    if (k0 < 0) {
+        *ok = false;
+        return n;
+    }
+    if (m) {
+        const int f = __ffs(m) - 1;
+        *ok = f > 0 || k0 == 0;
+        return k0 + f;
+    }
+    *ok = k0 + kEdgeWin - 1 >= n - 1;   // no true probe and the window reaches the last bin
+    return n;
+}
+
 // One warp per particle: lane 0 derives the coefficients, nine lanes sample the
 // antenna patterns for their harmonics, and the warp searches the band edges.
 __global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int B, Particle* parts, int global) {
@@ -217,11 +286,30 @@ __global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int
         }
     }
     __syncwarp();
-    // band: first bin with t >= 0 and last bin with t <= T_obs
+    // band: first bin with t >= 0 and last bin with t <= T_obs. Lanes 0 and 1
+    // solve t(f) = 0 and t(f) = T_obs for the edges' frequencies; one round of
+    // the predicates over a 16-bin window around each edge (lanes 0-15 and
+    // 16-31) settles the bins exactly, and a window that does not show the
+    // change falls back to the search over all bins (same predicate, same
+    // result).
     int64_t klo = 0, khi = g.n - 1;
     if (!global) {
-        klo = warp_search_first(0, g.n, [&](int64_t k) { return time_of(P, powers_of(bin_freq(g, k))) >= 0.0; });
-        khi = warp_search_first(0, g.n, [&](int64_t k) { return time_of(P, powers_of(bin_freq(g, k))) > g.T_obs; }) - 1;
+        auto before = [&](int64_t k) { return time_of(P, powers_of(bin_freq(g, k))) >= 0.0; };
+        auto after = [&](int64_t k) { return time_of(P, powers_of(bin_freq(g, k))) > g.T_obs; };
+        double fe = 0.0;
+        if (lane < 2) fe = edge_freq(P, lane == 0 ? 0.0 : g.T_obs);
+        const int64_t w_lo = edge_window(g, __shfl_sync(0xffffffffu, fe, 0));
+        const int64_t w_hi = edge_window(g, __shfl_sync(0xffffffffu, fe, 1));
+        const int half = lane / kEdgeWin;
+        const int64_t k = (half ? w_hi : w_lo) + (lane % kEdgeWin);
+        const bool probe = (half ? w_hi : w_lo) >= 0 && k < g.n && (half ? after(k) : before(k));
+        const unsigned m = __ballot_sync(0xffffffffu, probe);
+        bool ok;
+        klo = first_in_window(g.n, w_lo, m & 0xffffu, &ok);
+        if (!ok) klo = warp_search_first(0, g.n, before);
+        khi = first_in_window(g.n, w_hi, m >> 16, &ok);
+        if (!ok) khi = warp_search_first(0, g.n, after);
+        khi -= 1;
     }
     __syncwarp();
     if (lane == 0) {
