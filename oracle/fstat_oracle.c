@@ -24,7 +24,7 @@
  *   PSO update               Sec. III.A, Eqs. (pso_position_update), (pso_velocity_update)
  *   extrinsic parameters     Appendix B, Eqs. (B1)-(B3)
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - PN coefficients alpha_k: non-spinning TaylorF2 through 2PN (k <= 4).
  *   - phi_e: leading-order e0^2 correction with e0 defined at f0 = 10 mHz.
  *   - phi_p is carried by the F+/Fx basis (psi = 0); phi_D = 2 pi f R sin(theta)
