@@ -100,8 +100,10 @@ def parse():
     ap.add_argument("--prior", choices=["full", "targeted"], default="full",
                     help="search mode: the full prior (M_c 10-50 Msun, 0.5 yr of t_c) or a follow-up box "
                          "(M_c +-0.5 Msun, t_c +-0.005 yr around the injection; full sky and e0)")
-    ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
-                    help="one small evaluation for kernel profiling: paper grid, 64 particles, N_p = 16")
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "mlp"], default=None,
+                    help="one small run for kernel profiling: fp64/mixed = paper grid, the bench's 320 "
+                         "particles, N_p = 16; mlp = the search's surrogate batch (16 networks of width 256): "
+                         "one training round on 2048 rows each and one forward of 5120 rows each")
     return ap.parse_args()
 
 
@@ -594,12 +596,41 @@ def run_gpu(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_mlp_profile_case():
+    """The surrogate batch of a search stage (16 boxes, width 256): two
+    training rounds of 20 Adam steps on 2048 rows per network and two forward
+    passes over 5120 candidate rows per network (8 runs x 40 particles x 16
+    candidates), seeded synthetic inputs in [0, 1]^5."""
+    import torch
+    from paper_2407_10797_gb300 import fstat
+    G, W = 16, 256
+    s = torch.cuda.Stream()
+    gen = torch.Generator().manual_seed(5)
+    X = torch.rand(G, 2048, 5, generator=gen).cuda()
+    t = (X[..., 0] * 3 - X[..., 1] ** 2).contiguous() * 10
+    Xf = torch.rand(G, 5120, 5, generator=gen).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        net = fstat.MLP(W, max_batch=4096, seed=1, stream=s, groups=G)
+        for _ in range(2):
+            losses = net.train(X, t, 20, 1e-3)
+            y = net.forward(Xf)
+    s.synchronize()
+    print(json.dumps({"profile_case": "surrogate batch, 16 networks of width 256, 20 Adam steps on 2048 rows, "
+                                      "forward of 5120 rows", "loss_last": float(losses[-1].mean().item()),
+                      "y_mean": float(y.mean().item())}))
+    net.close()
+
+
 def run_profile_case(args):
     """Paper-scale grid (tables 227 MB > L2), the bench's 320 particles, one
     N_p = 16 launch after one warm-up launch: the bench's launch size, as a
     short capture target for kernel profilers."""
     import torch
     from paper_2407_10797_gb300 import fstat
+    if args.profile_case == "mlp":
+        run_mlp_profile_case()
+        return
     w, g, psd, noise, P, inj = workload_inputs(0)
     mode = fstat.FS_MIXED if args.profile_case == "mixed" else fstat.FS_FP64
     plan = fstat.Plan.from_grid(g, mode=mode)
