@@ -48,25 +48,71 @@ __device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// A 64 x 32 operand tile (64 rows of the output's M or N side, 32 k) is 256
+// chunks of 8 bf16 that are contiguous in memory, two per thread: with k
+// contiguous (not TRANS), chunk e holds row e / 4, k (e % 4) * 8 .. + 8 (four
+// threads cover a row's 64 bytes); with rows contiguous (TRANS), the chunk of
+// thread t in round i holds k = lane / 2 + 16 i and rows 8 (lane % 2) + 16 warp
+// .. + 8 (two threads cover a 32-byte sector, and the column stores into
+// shared memory meet at most two to a bank). A chunk is one 16-byte load when
+// `vec` (leading dimension a multiple of 8, base 16-byte aligned) and the
+// chunk lies inside the operand; otherwise its elements are loaded one by one
+// with bounds checks (zeros outside).
+__device__ __forceinline__ unsigned short bits_of(bf16 v) { return __bfloat16_as_ushort(v); }
+
 template <bool TRANS>
-__device__ __forceinline__ void load_tile(bf16 (*S)[BK + PAD], const bf16* __restrict__ G, int ld, int row0, int rows,
-                                          int k0, int K) {
-    const bf16 zero = __float2bfloat16(0.f);
+__device__ __forceinline__ void chunk_pos(int i, int& r, int& c) {
+    const int t = threadIdx.x;
+    if (!TRANS) {
+        const int e = t + i * GEMM_THREADS;
+        r = e >> 2;
+        c = (e & 3) * 8;
+    } else {
+        const int lane = t & 31, warp = t >> 5;
+        r = 8 * (lane & 1) + 16 * warp;
+        c = (lane >> 1) + 16 * i;
+    }
+}
+
+template <bool TRANS>
+__device__ __forceinline__ void fetch_tile(uint4 (&v)[2], const bf16* __restrict__ G, int ld, int row0, int rows,
+                                           int k0, int K, bool vec) {
 #pragma unroll
-    for (int i = 0; i < (BM * BK) / GEMM_THREADS; i++) {
-        const int e = threadIdx.x + i * GEMM_THREADS;
+    for (int i = 0; i < 2; i++) {
         int r, c;
-        if (!TRANS) {   // k contiguous in memory: consecutive threads walk k
-            r = e / BK;
-            c = e % BK;
-        } else {        // row contiguous in memory: consecutive threads walk rows
-            c = e / BM;
-            r = e % BM;
-        }
+        chunk_pos<TRANS>(i, r, c);
         const int gr = row0 + r, gk = k0 + c;
-        bf16 v = zero;
-        if (gr < rows && gk < K) v = TRANS ? G[(int64_t)gk * ld + gr] : G[(int64_t)gr * ld + gk];
-        S[r][c] = v;
+        const bool full = TRANS ? (gk < K && gr + 8 <= rows) : (gr < rows && gk + 8 <= K);
+        if (vec && full) {
+            const bf16* src = TRANS ? G + (int64_t)gk * ld + gr : G + (int64_t)gr * ld + gk;
+            v[i] = __ldg(reinterpret_cast<const uint4*>(src));
+        } else {
+            unsigned short h[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int rr = TRANS ? gr + j : gr, kk = TRANS ? gk : gk + j;
+                h[j] = (rr < rows && kk < K) ? bits_of(G[(int64_t)(TRANS ? kk : rr) * ld + (TRANS ? rr : kk)]) : 0;
+            }
+            v[i] = make_uint4(h[0] | (uint32_t)h[1] << 16, h[2] | (uint32_t)h[3] << 16, h[4] | (uint32_t)h[5] << 16,
+                              h[6] | (uint32_t)h[7] << 16);
+        }
+    }
+}
+
+template <bool TRANS>
+__device__ __forceinline__ void store_tile(bf16 (*S)[BK + PAD], const uint4 (&v)[2]) {
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        int r, c;
+        chunk_pos<TRANS>(i, r, c);
+        if (!TRANS) {
+            *reinterpret_cast<uint4*>(&S[r][c]) = v[i];
+        } else {
+            const uint32_t w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                S[r + j][c] = __ushort_as_bfloat16((unsigned short)(w[j >> 1] >> (16 * (j & 1))));
+        }
     }
 }
 
@@ -100,10 +146,23 @@ gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[i][j][c] = 0.f;
 
+    // 16-byte loads need a leading dimension that keeps every chunk aligned
+    const bool va = (lda & 7) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    const bool vb = (ldb & 7) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+    // the next k step's chunks are fetched into registers while this step's MMAs run
+    uint4 ra[2], rb[2];
+    if (kb < ke) {
+        fetch_tile<TA>(ra, A, lda, m0, M, kb, ke, va);
+        fetch_tile<TB>(rb, B, ldb, n0, N, kb, ke, vb);
+    }
     for (int k0 = kb; k0 < ke; k0 += BK) {
-        load_tile<TA>(As, A, lda, m0, M, k0, ke);
-        load_tile<TB>(Bs, B, ldb, n0, N, k0, ke);
+        store_tile<TA>(As, ra);
+        store_tile<TB>(Bs, rb);
         __syncthreads();
+        if (k0 + BK < ke) {
+            fetch_tile<TA>(ra, A, lda, m0, M, k0 + BK, ke, va);
+            fetch_tile<TB>(rb, B, ldb, n0, N, k0 + BK, ke, vb);
+        }
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             uint32_t af[2][4], bfr[4][2];
