@@ -7,6 +7,13 @@
 // with fused epilogues: bias + ReLU (forward), ReLU mask (backward through an
 // activation) and plain fp32 (weight gradients).  The 5-wide input layer is
 // padded to K = 16; the 1-wide output layer is a warp-per-row dot product.
+// An optional tcgen05 path (TMEM accumulators) covers the same products.
+//
+// One fs_mlp holds a batch of G networks of one width laid end to end (the
+// surrogate keeps one network per search box): every kernel of a forward or
+// training pass covers all G in one launch, network g's rows and parameters
+// sitting at fixed strides, with the same per-element summation order as a
+// network run alone.
 #include <cuda_bf16.h>
 
 #include <cmath>
