@@ -150,6 +150,12 @@ def _cuda_ptr(t, dtype=None):
     return C.c_void_p(t.data_ptr())
 
 
+def _check_size(t, n: int, what: str):
+    """The library reads or writes exactly n elements of t: refuse any other size."""
+    if t.numel() != n:
+        raise ValueError(f"{what} holds {t.numel()} elements, the call needs {n}")
+
+
 def _stream_handle(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -214,6 +220,9 @@ class Plan:
             F = torch.empty(B, dtype=torch.float64, device=dev)
         if want_parts and F_part is None:
             F_part = torch.empty(B, Np, dtype=torch.float64, device=dev)
+        _check_size(F, B, "F")
+        if F_part is not None:
+            _check_size(F_part, B * Np, "F_part")
         e = None
         if edges is not None:
             arr = np.ascontiguousarray(edges, dtype=np.int64)
@@ -245,9 +254,12 @@ class Plan:
     def bands(self, params, out=None):
         """Per-particle (first, last) in-band bin, int64 CUDA tensor [B, 2]."""
         import torch
+        if params.dim() != 2 or params.shape[1] != 6:
+            raise ValueError("params must be [B, 6]")
         B = params.shape[0]
         if out is None:
             out = torch.empty(B, 2, dtype=torch.int64, device=params.device)
+        _check_size(out, 2 * B, "out")
         _check(self._L.fs_particle_bands(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(B),
                                          _cuda_ptr(out, torch.int64)))
         return out
@@ -325,9 +337,16 @@ def fstat_batch_noalloc(grid, data, psd, params, Np: int, edges=None, F=None, F_
     L = load()
     if data.dtype == torch.complex128:
         data = torch.view_as_real(data)
+    if params.dim() != 2 or params.shape[1] != 6:
+        raise ValueError("params must be [B, 6]")
     B = params.shape[0]
     if F is None:
         F = torch.empty(B, dtype=torch.float64, device=params.device)
+    _check_size(data, 2 * int(grid.n), "data (re, im pairs)")
+    _check_size(psd, int(grid.n), "psd")
+    _check_size(F, B, "F")
+    if F_part is not None:
+        _check_size(F_part, B * Np, "F_part")
     e = None
     if edges is not None:
         arr = np.ascontiguousarray(edges, dtype=np.int64)
@@ -396,9 +415,12 @@ class Swarm:
         return v.value, [ms[i] for i in range(self.plan.n_variants)]
 
     def step(self, seed: int, iteration: int, w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5, lbest=None):
+        import torch
+        if lbest is not None:
+            _check_size(lbest, self.R * self.n_part, "lbest")
         _check(load().fs_pso_step(self.plan._h, C.byref(self.c), int(seed), int(iteration), float(w0), float(w1),
                                   int(n_iter), float(c1), float(c2), float(vmax),
-                                  None if lbest is None else C.c_void_p(lbest.data_ptr())))
+                                  None if lbest is None else _cuda_ptr(lbest, torch.int32)))
 
     def step_screened(self, mlp, n_cand: int, seed: int, iteration: int, w0=0.9, w1=0.4, n_iter=2, c1=2.0,
                       c2=2.0, vmax=0.5):
@@ -565,11 +587,18 @@ class MLP:
 
     def _rows(self, X):
         """Rows per network of an input batch ([N][5] for one network, [G][N][5] for G)."""
+        if X.dim() < 1 or X.shape[-1] != 5:
+            raise ValueError("inputs are rows of 5 normalised coordinates")
         if self.groups == 1:
-            return int(X.reshape(-1, 5).shape[0])
-        if X.dim() != 3 or X.shape[0] != self.groups or X.shape[2] != 5:
+            return int(X.numel() // 5)
+        if X.dim() != 3 or X.shape[0] != self.groups:
             raise ValueError(f"a batch of {self.groups} networks takes inputs [{self.groups}][N][5]")
         return int(X.shape[1])
+
+    def _check_len(self, v, n, what):
+        """The library reads or writes exactly n floats of v: refuse any other size."""
+        if v.numel() != n:
+            raise ValueError(f"{what} holds {v.numel()} values, the call needs {n}")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -604,6 +633,7 @@ class MLP:
     def set_params(self, theta):
         import torch
         theta = theta.to(torch.float32).contiguous()
+        self._check_len(theta, self.groups * self.P, "theta")
         _check(self._L.fs_mlp_set_params(self._h, _cuda_ptr(theta, torch.float32)))
 
     def forward(self, X, y=None):
@@ -612,6 +642,7 @@ class MLP:
         n = self._rows(X)
         if y is None:
             y = torch.empty(X.shape[:-1], dtype=torch.float32, device=X.device)
+        self._check_len(y, self.groups * n, "y")
         _check(self._L.fs_mlp_forward(self._h, _cuda_ptr(X, torch.float32), n, _cuda_ptr(y, torch.float32)))
         return y
 
@@ -619,6 +650,7 @@ class MLP:
         import torch
         X = X.to(torch.float32).contiguous()
         t = t.to(torch.float32).contiguous()
+        self._check_len(t, self.groups * self._rows(X), "t")
         g = torch.empty(self.groups * self.P, dtype=torch.float32, device=X.device)
         L = torch.empty(self.groups, dtype=torch.float32, device=X.device)
         _check(self._L.fs_mlp_loss_grad(self._h, _cuda_ptr(X, torch.float32), _cuda_ptr(t, torch.float32),
@@ -629,6 +661,7 @@ class MLP:
         import torch
         X = X.to(torch.float32).contiguous()
         t = t.to(torch.float32).contiguous()
+        self._check_len(t, self.groups * self._rows(X), "t")
         losses = torch.empty(max(int(steps), 1) * self.groups, dtype=torch.float32, device=X.device)
         _check(self._L.fs_mlp_train(self._h, _cuda_ptr(X, torch.float32), _cuda_ptr(t, torch.float32),
                                     self._rows(X), int(steps), float(lr), _cuda_ptr(losses, torch.float32)))
