@@ -4,21 +4,27 @@
 // The direct FP64 kernel evaluates the whole template at every bin (powers
 // of f, t(f), sin/cos of the orbital phase, the trig polynomials of the
 // antenna patterns and sin/cos of the phase).  Here every (particle, 1024-bin
-// tile) gets one FP64 anchor at its centre bin j_a, and each bin of the tile
-// j_a + d is evaluated from an expansion about it:
-//   - orbital phase: an exact cubic in d in 64-bit fixed point (cycles mod 1,
-//     units of 2^-64), stepped by integer forward differences, plus the FP64
-//     quartic and quintic terms;
-//   - orbital-phase offset d(alpha) = Om (t(f) - t_a) as a quartic in d;
-//   - Doppler phase and antenna patterns as FP64 polynomials in d(alpha)
-//     (degrees 7 and 8), the antenna ones folded with the segment's rotation;
-//   - exp(2 pi i Phi) as a 256-entry table value times a degree-6/7 Taylor
-//     series of the remaining angle (|angle| <= pi/256).
-// The truncation remainders are bounded at the anchor (phase <= 1e-11 cycle,
-// d(alpha) remainder <= 1e-11 rad, |d(alpha)| <= 0.06); a tile that fails a
-// bound is evaluated bin by bin exactly as the direct kernel does.  All
-// arithmetic is FP64 or exact integer; results agree with the direct form to
-// rounding level (relative 1e-12 or better on the F-statistic).
+// tile) gets one FP64 anchor at its central in-band bin j_a, and each bin of
+// the tile j_a + d is evaluated from expansions about it:
+//   - orbital phase: Taylor coefficients in d to degree 12 from the
+//     closed-form derivatives of its power-law terms;
+//   - orbital-phase offset d(alpha) = Om (t(f) - t_a) as a quintic in d;
+//   - Doppler phase and antenna patterns composed with d(alpha) into
+//     polynomials in d (Horner's scheme on polynomials, truncated at degree
+//     12), the antenna ones rotated into the segment's basis per piece;
+//   - total phase: its cubic part in 64-bit fixed point (cycles mod 1, units
+//     of 2^-64), stepped per lane by exact integer forward differences; the
+//     degree 4..4+NR part an FP64 remainder added in units of 2^-48 cycle;
+//   - exp(2 pi i Phi): a 1024-entry table value (top 10 bits, rounded) times
+//     the Taylor series of the remaining angle |theta| <= pi/1024 (cos to
+//     degree 4, sin to degree 5).
+// A tile takes the lowest degree tier (NG, NR) = (6, 2), (7, 3), (8, 5) or
+// (10, 7) whose dropped terms, summed over the tile at the anchor, stay below
+// 1e-13 cycle (phase) and 1e-15 (antenna); a tile whose d(alpha) quintic or
+// degree-12 series does not converge is evaluated bin by bin exactly as the
+// direct kernel does.  All arithmetic is FP64 or exact integer; results agree
+// with the direct form to rounding level (1e-10 on the F-statistic at full
+// size, 1e-9 against the oracle).
 //
 // Work decomposition (spans of 32 tiles, in-band particle lists per span,
 // grid or persistent form) is that of the mixed-precision kernel.
