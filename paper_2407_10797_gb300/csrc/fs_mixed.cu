@@ -9,13 +9,15 @@
 // The phase polynomial is kept in 64-bit fixed point (units of 2^-64 cycle):
 // integer arithmetic is exact modulo one cycle, so each lane walks its bins
 // (step 32) by forward differences with no phase drift.  The Doppler phase and
-// the antenna patterns are evaluated per bin as small-angle deltas from the
-// anchor's orbital phase alpha_a (FP32), the phase goes through the SFU sincos,
+// the antenna patterns are evaluated per bin as polynomials in the offset
+// d(alpha) from the anchor's orbital phase alpha_a (FP32; the antenna
+// patterns' constant terms in FP64), the phase goes through the SFU sincos,
 // and the seven segment sums accumulate in FP32 per lane (per tile, then per
 // span of 32 tiles), are summed across the warp in FP32 and stored as FP64
-// partials that the solve kernel adds in FP64.  A tile whose Taylor remainder bound exceeds 1e-6 cycle (or whose
-// orbital-phase excursion exceeds 0.25 rad) is evaluated bin by bin in FP64
-// instead, so the mode stays correct on any grid.
+// partials that the solve kernel adds in FP64.  A tile whose quartic phase
+// remainder exceeds 1e-6 cycle, whose t(f) remainder moves alpha by more than
+// 1e-6 rad, or whose |d(alpha)| exceeds 0.06 rad is evaluated bin by bin in
+// FP64 instead, so the mode stays correct on any grid.
 #include <cfloat>
 #include <climits>
 
