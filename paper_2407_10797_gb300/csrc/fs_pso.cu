@@ -10,6 +10,12 @@
 // linearly decaying inertia weight.  The update is written with explicit
 // round-to-nearest multiplies and adds (no contraction), so it is bit-exact
 // against a plain CPU implementation of the same order of operations.
+//
+// Not in the paper: a screened step (each particle draws several candidate
+// moves with distinct Philox counters, the surrogate networks of its run's
+// group rank them, and the best-ranked in-box candidate is taken), and the
+// recording of (position, fitness) samples into the device rings the
+// networks train on.
 #include <cmath>
 
 #include "fs_internal.h"
