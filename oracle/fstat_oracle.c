@@ -149,14 +149,9 @@ static void or_sc_offset(const or_model* m, int n, double alpha, double r[3]) {
     r[2] = -sqrt(3.0) * cos(alpha - beta);
 }
 
-/* F+ and Fx of the long-wavelength Michelson with vertex at spacecraft 0:
- * F_A = D : e_A, D = (a a - b b)/2, e+ = p p - q q, ex = p q + q p. */
-static void or_antenna(const or_params* P, const or_model* m, double t, double* Fp, double* Fx) {
-    if (m->response == 1) {
-        *Fp = 1.0;
-        *Fx = 0.0;
-        return;
-    }
+/* Detector tensor D = (a a - b b)/2 of the long-wavelength Michelson with
+ * vertex at spacecraft 0 (a, b: unit vectors along its two arms) at time t. */
+static void or_detector(const or_model* m, double t, double D[3][3]) {
     double alpha = or_orbit_phase(m, t);
     double r0[3], r1[3], r2[3], a[3], b[3];
     or_sc_offset(m, 0, alpha, r0);
@@ -175,9 +170,20 @@ static void or_antenna(const or_params* P, const or_model* m, double t, double* 
         a[i] /= na;
         b[i] /= nb;
     }
-    double D[3][3];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) D[i][j] = 0.5 * (a[i] * a[j] - b[i] * b[j]);
+}
+
+/* F+ and Fx of the long-wavelength Michelson with vertex at spacecraft 0:
+ * F_A = D : e_A, e+ = p p - q q, ex = p q + q p. */
+static void or_antenna(const or_params* P, const or_model* m, double t, double* Fp, double* Fx) {
+    if (m->response == 1) {
+        *Fp = 1.0;
+        *Fx = 0.0;
+        return;
+    }
+    double D[3][3];
+    or_detector(m, t, D);
     double sb = sin(P->lat), cb = cos(P->lat), sl = sin(P->lon), cl = cos(P->lon);
     /* theta = pi/2 - beta: p = theta-hat, q = phi-hat of the source direction */
     double p[3] = {sb * cl, sb * sl, -cb};
@@ -233,6 +239,13 @@ void or_antenna_at(const or_params* P, const or_model* m, double t, double* Fp, 
 }
 
 double or_doppler_at(const or_params* P, const or_model* m, double t) { return or_doppler_delay(P, m, t); }
+
+void or_detector_tensor_at(const or_model* m, double t, double* D9) {
+    double D[3][3];
+    or_detector(m, t, D);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) D9[3 * i + j] = D[i][j];
+}
 
 /* Basis waveforms A^i at bins k0..k1-1 (Eq. response with the Sec. IV
  * response): h0 = f^-7/6 e^{-2 pi i Phi}, A1 = F+ h0, A2 = Fx h0,

@@ -75,6 +75,8 @@ def lib():
             L.or_antenna_at.argtypes = [C.POINTER(Params), C.POINTER(Model), C.c_double, _dp, _dp]
             L.or_doppler_at.argtypes = [C.POINTER(Params), C.POINTER(Model), C.c_double]
             L.or_doppler_at.restype = C.c_double
+            L.or_detector_tensor_at.argtypes = [C.POINTER(Model), C.c_double, _dp]
+            L.or_detector_tensor_at.restype = None
             L.or_extrinsic_to_a.argtypes = [C.c_double] * 4 + [_dp]
             L.or_a_to_extrinsic.argtypes = [_dp, _dp, _dp, _dp, _dp]
             L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
@@ -219,6 +221,14 @@ def doppler_delay(p, model: OracleModel, t: float) -> float:
     m = model.c()
     P = _params(p)
     return lib().or_doppler_at(C.byref(P), C.byref(m), float(t))
+
+
+def detector_tensor(model: OracleModel, t: float) -> np.ndarray:
+    """Detector tensor D = (a a - b b)/2 of the Michelson at time t (Sec. IV), 3 x 3."""
+    m = model.c()
+    out = np.zeros(9)
+    lib().or_detector_tensor_at(C.byref(m), float(t), out.ctypes.data_as(_dp))
+    return out.reshape(3, 3)
 
 
 def extrinsic_to_a(DL, psi, iota, phic) -> np.ndarray:

@@ -272,6 +272,113 @@ def test_doppler_vanishes_at_ecliptic_poles_and_peaks_in_plane():
     assert O.doppler_delay([20, 0, 0.0, 0.0, 0, 1], m, 0.0) == pytest.approx(S.AU_S, rel=1e-15)
 
 
+def test_orbit_and_cartwheel_repeat_after_one_year():
+    """A 1 AU circular orbit takes one year (Kepler's third law) and the rigid
+    constellation turns once per orbit: the Doppler delay and the detector
+    tensor repeat after a year, and the delay changes sign after half a year
+    (the guiding centre on the far side of the Sun)."""
+    m = O.OracleModel.from_grid(S.tiny_grid(n=10))
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        p = [20.0, 0.0, math.asin(rng.uniform(-0.9, 0.9)), rng.uniform(0, 2 * np.pi), 0.0, 1.0]
+        t = rng.uniform(0, 2 * S.YEAR_S)
+        d = O.doppler_delay(p, m, t)
+        assert O.doppler_delay(p, m, t + S.YEAR_S) == pytest.approx(d, abs=1e-9 * S.AU_S)
+        assert O.doppler_delay(p, m, t + 0.5 * S.YEAR_S) == pytest.approx(-d, abs=1e-9 * S.AU_S)
+        assert np.allclose(O.detector_tensor(m, t + S.YEAR_S), O.detector_tensor(m, t), atol=1e-12)
+
+
+def test_detector_is_a_60_degree_michelson_in_a_plane_inclined_60_degrees():
+    """The constellation is an equilateral triangle whose plane is inclined by
+    60 degrees to the ecliptic. The tensor (a a - b b)/2 of two unit arms 60
+    degrees apart is traceless with eigenvalues -sin(60)/2, 0, +sin(60)/2; its
+    null vector is the normal of the plane, at 60 degrees from the ecliptic
+    pole."""
+    m = O.OracleModel.from_grid(S.tiny_grid(n=10))
+    for t in np.linspace(0.0, S.YEAR_S, 9):
+        D = O.detector_tensor(m, t)
+        assert np.allclose(D, D.T, atol=1e-15) and abs(np.trace(D)) < 1e-14
+        w, V = np.linalg.eigh(D)
+        assert np.allclose(w, [-math.sqrt(3) / 4, 0.0, math.sqrt(3) / 4], atol=1e-13)
+        assert abs(V[2, 1]) == pytest.approx(0.5, abs=1e-12)
+
+
+def test_antenna_is_the_transverse_traceless_projection_along_the_source():
+    """F+^2 + Fx^2 = 2 |D^TT|^2 with D^TT = P D P - (1/2) P tr(P D),
+    P = I - n n and n = (cos b cos l, cos b sin l, sin b) the source direction
+    of the Doppler delay: the basis-free form of the polarisation sum, which
+    holds only for polarisation tensors transverse to that same direction."""
+    m = O.OracleModel.from_grid(S.tiny_grid(n=10))
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        b, l, t = math.asin(rng.uniform(-1, 1)), rng.uniform(0, 2 * np.pi), rng.uniform(0, S.YEAR_S)
+        fp, fx = O.antenna([20.0, 0.0, b, l, 0.0, 1.0], m, t)
+        n = np.array([math.cos(b) * math.cos(l), math.cos(b) * math.sin(l), math.sin(b)])
+        P = np.eye(3) - np.outer(n, n)
+        D = O.detector_tensor(m, t)
+        Dtt = P @ D @ P - 0.5 * P * np.trace(P @ D)
+        assert fp * fp + fx * fx == pytest.approx(2.0 * np.sum(Dtt * Dtt), rel=1e-10, abs=1e-14)
+
+
+def test_doppler_phase_is_the_arrival_time_shift():
+    """A wave from direction n reaches a detector at r a time n.r/c before the
+    solar-system barycentre: h_det(t) = h_ssb(t + tau(t)), tau = n.r/c (the
+    Doppler delay), so the frequency f is observed at the detector time t with
+    f = F_ssb(t + tau(t)) (1 + tau'(t)), F_ssb the inverse of the barycentric
+    t(f). The template's group delay dPhi/df at f must be that time. The
+    template keeps the response to first order in the orbital motion (Sec.
+    IV, N = 0, d evaluated at t_f), so the two agree to a few per cent of the
+    shift."""
+    m0 = O.OracleModel.from_grid(S.tiny_grid(n=10, f_min=0.01))
+    Mc, f_star = 30.0, 0.02
+    alpha_star = 2 * np.pi * 0.3
+    for lon in (alpha_star - np.pi / 2, alpha_star + np.pi / 2, 2.0):
+        p = np.array([Mc, tc_for(Mc, f_star, 0.3 * S.YEAR_S), 0.0, lon, 0.0, 1.0])
+
+        def f_ssb(s):   # inverse of the barycentric t(f), by bisection
+            lo, hi = 1e-3, 0.2
+            for _ in range(200):
+                mid = 0.5 * (lo + hi)
+                lo, hi = (mid, hi) if O.time_of_freq(p, m0, mid) < s else (lo, mid)
+            return 0.5 * (lo + hi)
+
+        def observed(t):
+            tau = O.doppler_delay(p, m0, t)
+            rate = (O.doppler_delay(p, m0, t + 10.0) - O.doppler_delay(p, m0, t - 10.0)) / 20.0
+            return f_ssb(t + tau) * (1.0 + rate)
+
+        lo, hi = 0.2 * S.YEAR_S, 0.4 * S.YEAR_S
+        for _ in range(80):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if observed(mid) < f_star else (lo, mid)
+        t_det = 0.5 * (lo + hi)
+        shift = t_det - O.time_of_freq(p, m0, f_star)
+        df = 1e-10
+        m = O.OracleModel.from_grid(S.Grid(f_min=f_star - 5 * df, df=df, n=11, T_obs=2.5 * S.YEAR_S))
+        ph = np.unwrap(2 * np.pi * np.array([O.phase_frac(p, m, k) for k in range(11)])) / (2 * np.pi)
+        group_delay = (ph[6] - ph[4]) / (2 * df)
+        assert abs(shift) > 1000.0
+        assert abs(group_delay - t_det) <= 0.02 * abs(shift) + 1.0, (lon, shift, group_delay - t_det)
+
+
+def test_band_edges_by_brute_force():
+    """On a 2.5-yr grid (bins ~20 s of chirp time apart) the band is the first
+    bin with t(f_k) >= 0 and the last with t(f_k) <= T_obs, found by scanning
+    every bin."""
+    g = S.tiny_grid(n=3000, f_min=0.02)
+    m = O.OracleModel.from_grid(g)
+    f_mid = g.f_min + 1500 * g.df
+    for Mc, t_mid in [(30.0, 0.0), (12.0, 0.0), (45.0, g.T_obs), (25.0, g.T_obs)]:
+        p = np.array([Mc, 0.0, 0.3, 1.1, 0.02, 1.0])
+        p[1] = t_mid - O.time_of_freq(p, m, f_mid)   # the edge crossing at bin 1500
+        t = np.array([O.time_of_freq(p, m, g.f_min + k * g.df) for k in range(g.n)])
+        ok_lo, ok_hi = np.flatnonzero(t >= 0.0), np.flatnonzero(t <= g.T_obs)
+        klo, khi = O.band(p, m)
+        assert klo == (ok_lo[0] if ok_lo.size else g.n)
+        assert khi == (ok_hi[-1] if ok_hi.size else -1)
+        assert 0 < klo < g.n - 1 or 0 < khi < g.n - 1   # an edge inside the grid
+
+
 # ---------------------------------------------------------------- p8: eccentricity
 def test_eccentric_correction_scales_as_e0_squared():
     g = S.tiny_grid(n=10)
