@@ -495,6 +495,64 @@ def test_pso_step_rules():
     assert np.all(np.abs(v) <= 0.05)
 
 
+def test_pso_velocity_clamp_is_symmetric():
+    """Attractions of either sign beyond v_max are clamped to -v_max and +v_max
+    (reading c10)."""
+    R, Np, D = 1, 40, 5
+    x = np.full((R, Np, D), 0.5)
+    v = np.zeros_like(x)
+    pbx = np.where(np.arange(Np)[None, :, None] % 2 == 0, 0.0, 1.0) * np.ones_like(x)
+    pbf = np.zeros((R, Np))   # equal fitness: lbest = lowest ring index, an even particle for most
+    O.pso_step(x, v, pbx, pbf, np.full((R, Np), -np.inf), seed=3, iteration=0, w=0.0, vmax=0.05)
+    assert v.min() == -0.05 and v.max() == 0.05
+
+
+@pytest.mark.parametrize("which", ["cognitive", "social"])
+def test_pso_terms_pull_toward_their_own_attractor(which):
+    """With w = 0 and only one acceleration constant the step is c r (a - x)
+    with r in [0, 1): a = the particle's personal best for c1, its ring's best
+    for c2. Personal and ring bests are placed on opposite sides of x, so
+    every coordinate's ratio v / (a - x) must lie in [0, c)."""
+    R, Np, D = 2, 8, 5
+    rng = np.random.default_rng(6)
+    x = rng.uniform(0.4, 0.6, (R, Np, D))
+    v = np.zeros_like(x)
+    pbx = np.zeros_like(x)
+    pbx[:, 0] = 1.0                        # particle 0: personal best above every x
+    pbf = np.full((R, Np), -1.0)
+    pbf[:, 0] = 5.0                        # ... and the best of its ring
+    pbx[:, 1:] = 0.0                       # the others' personal bests below x
+    c1, c2 = (1.7, 0.0) if which == "cognitive" else (0.0, 1.7)
+    lb = O.pso_step(x, v, pbx, pbf, np.full((R, Np), -np.inf), seed=9, iteration=2, w=0.0,
+                    c1=c1, c2=c2, vmax=10.0)
+    x0 = x - v                             # the step moved x by v
+    for r in range(R):
+        for i in (1, 7):                   # ring best is particle 0, personal best below
+            a = pbx[r, i] if which == "cognitive" else pbx[r, lb[r, i]]
+            ratio = v[r, i] / (a - x0[r, i])
+            assert lb[r, i] == 0
+            assert np.all(ratio >= 0.0) and np.all(ratio < (c1 if which == "cognitive" else c2))
+
+
+def test_pso_random_numbers_are_uniform_on_the_unit_interval():
+    """With w = 0, c1 = 1, c2 = 0 and the personal best one unit above x, the
+    velocity is r1 itself: 10^4 draws must follow U[0, 1) (Kolmogorov-Smirnov)."""
+    from scipy import stats
+    R, Np, D = 10, 40, 5
+    draws = []
+    for it in range(5):
+        x = np.zeros((R, Np, D))
+        v = np.zeros_like(x)
+        pbx = np.ones_like(x)
+        pbf = np.zeros((R, Np))
+        O.pso_step(x, v, pbx, pbf, np.full((R, Np), -np.inf), seed=11, iteration=it, w=0.0, c1=1.0, c2=0.0,
+                   vmax=10.0)
+        draws.append(v.ravel())
+    u = np.concatenate(draws)
+    assert np.all((u >= 0) & (u < 1))
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
 def test_constants_agree_with_input_module():
     src = open(os.path.join(os.path.dirname(O.__file__), "fstat_oracle.c")).read()
 
