@@ -609,6 +609,42 @@ def test_mlp_oracle_gradient_matches_finite_differences():
         M.bf16 = orig
 
 
+def test_mlp_oracle_loss_of_a_constant_network():
+    """All weights zero: the network outputs b4 everywhere, so the loss is half
+    the mean squared difference to the finite targets (NaN targets are not
+    counted) and the only non-zero gradient is dL/db4 = mean(b4 - t)."""
+    from oracle import mlp_oracle as M
+    W = 8
+    theta = np.zeros(sum(int(np.prod(s)) for _, s in M.param_shapes(W)))
+    theta[-1] = 0.75
+    X = np.random.default_rng(3).random((6, 5))
+    t = np.array([1.0, np.nan, -0.5, 2.0, np.nan, 0.25])
+    L, g = M.loss_and_grad(theta, X, t, W)
+    ok = np.isfinite(t)
+    assert L == pytest.approx(0.5 * np.mean((0.75 - t[ok]) ** 2), rel=1e-15)
+    assert g[-1] == pytest.approx(np.mean(0.75 - t[ok]), rel=1e-15)
+    assert np.all(g[:-1] == 0.0)
+
+
+def test_mlp_oracle_adam_steps_have_closed_forms():
+    """Adam with bias correction (Kingma and Ba): under a constant gradient
+    every step is -lr sign(g) (to eps); after g then -g the second step is
+    +lr (1 - beta1)/(1 + beta1) sign(g), since the corrected second moment is
+    g^2 and the corrected first moment -(1 - beta1)/(1 + beta1) g."""
+    from oracle import mlp_oracle as M
+    g = np.array([3.0, -0.02, 1e3])
+    lr = 1e-3
+    th, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for step in range(1, 6):
+        th_new, m, v = M.adam(th, g, m, v, step, lr)
+        assert np.allclose(th_new - th, -lr * np.sign(g), rtol=1e-6, atol=0)
+        th = th_new
+    th, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    th1, m, v = M.adam(th, g, m, v, 1, lr)
+    th2, m, v = M.adam(th1, -g, m, v, 2, lr)
+    assert np.allclose(th2 - th1, lr * 0.1 / 1.9 * np.sign(g), rtol=1e-6, atol=0)
+
+
 def test_mlp_oracle_adam_fits_a_smooth_function():
     from oracle import mlp_oracle as M
     rng = np.random.default_rng(2)
