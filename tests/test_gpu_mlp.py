@@ -130,3 +130,29 @@ def test_tcgen05_training_is_deterministic_and_fits(fst):
         net.close()
     assert runs[0][0][-1] < 0.05 * runs[0][0][0]
     assert np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_first_adam_step_moves_each_weight_by_lr(fst):
+    """Adam's bias-corrected first step is -lr g / (|g| + eps) (Kingma and
+    Ba): every weight whose gradient is clearly non-zero moves by lr against
+    the sign of its gradient, and no weight moves by more than lr. Targets
+    are pre-standardised, so the training call's own standardisation leaves
+    the gradient of fs_mlp_loss_grad unchanged."""
+    rng = np.random.default_rng(8)
+    Xc = rng.random((512, 5)).astype(np.float32)
+    t = np.sin(3 * Xc[:, 0]) + Xc[:, 1]
+    t = ((t - t.mean()) / t.std()).astype(np.float32)
+    X = torch.from_numpy(Xc).cuda()
+    tt = torch.from_numpy(t).cuda()
+    net = fst.MLP(64, max_batch=512, seed=4)
+    th0 = net.params().cpu().numpy()
+    _, g = net.loss_grad(X, tt)
+    g = g.cpu().numpy()
+    lr = 1e-3
+    net.train(X, tt, 1, lr)
+    step = (net.params().cpu().numpy() - th0) / lr
+    clear = np.abs(g) > 1e-4 * np.abs(g).max()
+    assert clear.mean() > 0.25
+    assert np.all(np.abs(step) <= 1.0 + 1e-3)
+    assert np.allclose(step[clear], -np.sign(g[clear]), atol=1e-2)
+    net.close()
