@@ -39,3 +39,22 @@ def test_constants_agree():
     assert c[0] == S.MSUN_S and c[1] == S.YEAR_S and c[2] == S.AU_S and c[3] == 0.01
     src = open(os.path.join(ROOT, "oracle", "fstat_oracle.c")).read()
     assert f"#define OR_F0_ECC {c[3]}" in src
+
+
+def test_headers_are_plain_c_and_cpp():
+    """Every include/*.h compiles on its own as strict C99 and C11 (pedantic,
+    warnings as errors) and as C++ through its extern "C" guards: the boundary
+    carries only plain C types."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        import pytest
+        pytest.skip("gcc not found")
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = f'#include "{os.path.basename(h)}"\nint fs_header_check(void) {{ return 0; }}\n'
+        for lang, std in (("c", "-std=c99"), ("c", "-std=c11"), ("c++", "-std=c++17")):
+            r = subprocess.run([cc, "-x", lang, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                                "-I", os.path.join(ROOT, "include"), "-"], input=src, capture_output=True,
+                               text=True)
+            assert r.returncode == 0, (h, lang, std, r.stderr)
