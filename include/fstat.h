@@ -19,12 +19,19 @@
  *
  * Conventions
  *   - Units: G = c = 1 with times in seconds; masses in solar masses on input.
- *   - Frequency grid: f_k = f_min + k*df, k = 0..n_bins-1 (uniform).
+ *   - Frequency grid: f_k = f_min + k*df, k = 0..n_bins-1 (uniform; the
+ *     paper's data are the DFT grid of a regularly sampled series, Sec. V.A).
+ *   - Segment edges (Sec. II.B): N_p + 1 non-decreasing frequencies e_p (Hz) in
+ *     device memory; bin k lies in segment p iff e_p <= f_k < e_{p+1}, the last
+ *     segment closed at e_{N_p}; bins outside [e_0, e_{N_p}] take no part.  NULL
+ *     instead means per-particle edges (see fs_fstat_batch).
  *   - All `*_dev` pointers are device pointers owned by the caller; `*_host`
  *     pointers are host memory owned by the caller.  The plan owns its own
  *     workspace (per-bin tables, per-particle coefficients, partial sums).
  *   - Every call is asynchronous and ordered on the plan's stream, unless its
- *     comment says otherwise.  No call keeps a pointer to caller memory.
+ *     comment says otherwise.  A call reads caller memory when its work runs
+ *     on the stream, and keeps no pointer afterwards; a captured graph reads
+ *     the buffers it was built with every time it is launched.
  *   - Errors: every function returns fs_status; on failure fs_last_error()
  *     returns a message (thread-local, valid until the next call on the same
  *     thread).  Invalid sizes or arguments give FS_EINVAL and launch nothing.
@@ -84,12 +91,20 @@ FS_API fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, dou
 /* Free a plan and its workspace (waits for the plan's stream).  NULL is a no-op. */
 FS_API fs_status fs_plan_destroy(fs_plan* plan);
 
-/* Load one data set.  data_dev: n_bins complex values as interleaved FP64
- * (re, im); psd_dev: n_bins one-sided PSD values S_k > 0.  Precomputes the
- * particle-independent per-bin tables (noise-weighted data 4 df d_k f^-7/6 / S_k,
- * weights 4 df f^-7/3 / S_k, frequency powers).  Asynchronous; the caller's
- * buffers may be reused once the plan's stream has passed this call. */
-FS_API fs_status fs_plan_set_data(fs_plan* plan, const double* data_dev, const double* psd_dev);
+/* Load one data set (Sec. II.A, Eq. inner_product: the noise-weighted inner
+ * product on the frequency grid).  data_dev: n_bins complex values as
+ * interleaved FP64 (re, im); psd_dev: n_bins one-sided PSD values S_k > 0;
+ * f_grid_dev: NULL for the plan's grid f_k = f_min + k df, or the n_bins
+ * frequencies of the data (device, FP64), which must equal that grid to 4 units
+ * in the last place: the kernels step the template phase in the bin index, so
+ * a non-uniform grid returns FS_EUNSUPPORTED (and loads nothing).  Precomputes
+ * the particle-independent per-bin tables (noise-weighted data 4 df d_k
+ * f^-7/6 / S_k, weights 4 df f^-7/3 / S_k, frequency powers).  Asynchronous
+ * with f_grid_dev = NULL; with a grid it waits for the plan's stream to read
+ * the check's answer.  The caller's buffers may be reused once the plan's
+ * stream has passed this call. */
+FS_API fs_status fs_plan_set_data(fs_plan* plan, const double* data_dev, const double* psd_dev,
+                                  const double* f_grid_dev);
 
 /* Pre-size the plan's workspace for batches of up to B_max particles and
  * N_p_max segments, so that later fs_fstat_batch calls allocate nothing (and
@@ -99,12 +114,17 @@ FS_API fs_status fs_plan_reserve(fs_plan* plan, int B_max, int N_p_max);
 /* Batched semi-coherent F-statistic (Sec. II.B, Eq. semi-cohF).
  *   params_dev : B particles (device array of fs_params).
  *   B          : 0 <= B; B = 0 launches nothing.
- *   edges_host : NULL for per-particle segments: the outer edges are the first
- *                and last bin whose t(f_k) lies in [0, T_obs] and the N_p
- *                segments are equal-width in frequency between them (bin k is
- *                in segment p iff e_p <= f_k < e_{p+1}, the last one closed).
- *                Otherwise N_p + 1 non-decreasing bin indices in [0, n_bins]:
- *                segment p is bins [edges[p], edges[p+1]) for every particle.
+ *   partition_edges_dev : NULL for per-particle segments: the outer edges are
+ *                the first and last bin whose t(f_k) lies in [0, T_obs] and the
+ *                N_p segments are equal-width in frequency between them (bin k
+ *                is in segment p iff e_p <= f_k < e_{p+1}, the last one closed).
+ *                Otherwise N_p + 1 edge frequencies in device memory, the same
+ *                for every particle (see Conventions).  They are read on the
+ *                plan's stream when the call runs (also when it is replayed
+ *                from a captured graph), so the caller keeps the buffer alive
+ *                until then.  Edges that are not finite or decrease cannot be
+ *                refused without waiting for the device: F is then NaN for
+ *                every particle and fs_plan_check reports it.
  *   N_p        : 1 <= N_p <= 4096.
  *   F_dev      : B doubles, F_sum = sum_p F_p (the paper's F-hat times N_p).
  *   F_part_dev : B*N_p doubles (F_p, row-major by particle) or NULL.
@@ -112,8 +132,14 @@ FS_API fs_status fs_plan_reserve(fs_plan* plan, int B_max, int N_p_max);
  * contributes F_p = 0.  A particle with a non-finite parameter, Mc <= 0 or
  * q <= 0 gets F = NaN (and NaN segments).  Grows the workspace (synchronously)
  * if B or N_p exceed the reservation. */
-FS_API fs_status fs_fstat_batch(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
-                         int N_p, double* F_dev, double* F_part_dev);
+FS_API fs_status fs_fstat_batch(fs_plan* plan, const fs_params* params_dev, int B,
+                                const double* partition_edges_dev, int N_p, double* F_dev, double* F_part_dev);
+
+/* Errors the device found in earlier calls on this plan: waits for the plan's
+ * stream, writes the flag bits seen since the last check to *flags_out (may be
+ * NULL; bit 0: partition edges that were not finite or decreased) and clears
+ * them.  Returns FS_EINVAL with a message when bit 0 was set, FS_OK otherwise. */
+FS_API fs_status fs_plan_check(fs_plan* plan, int* flags_out);
 
 /* Maximum-likelihood amplitudes and extrinsic parameters (Eq. aandMN3 and
  * App. B, Eqs. B2-B3), per particle and segment.
@@ -130,7 +156,7 @@ FS_API fs_status fs_fstat_batch(fs_plan* plan, const fs_params* params_dev, int 
  *             1/D_L = the overall amplitude of a), NaN where a = 0; or NULL.
  * With N_p = 1 these are the fully coherent estimates the search reports
  * after its last stage.  Asynchronous, stream-ordered. */
-FS_API fs_status fs_amplitudes(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
+FS_API fs_status fs_amplitudes(fs_plan* plan, const fs_params* params_dev, int B, const double* edges_dev,
                                int N_p, double* F_dev, double* a_dev, double* ext_dev);
 
 /* Add the signal h = sum_i a_i A^i of one particle to data_dev (n_bins
@@ -175,10 +201,11 @@ typedef struct {
 FS_API fs_status fs_pso_init(fs_plan* plan, const fs_swarm* swarm, uint64_t seed);
 
 /* Fitness of the current positions: fit = F_sum / N_p (the paper's F-hat,
- * Eq. semi-cohF) with the segments of fs_fstat_batch (edges_host as there);
+ * Eq. semi-cohF) with the segments of fs_fstat_batch (edges_dev as its
+ * partition_edges_dev);
  * a particle outside [0,1]^5 is not evaluated and gets -inf ("let them fly").
  * R * n_part must not exceed the plan's reservation if the call is captured. */
-FS_API fs_status fs_pso_evaluate(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p);
+FS_API fs_status fs_pso_evaluate(fs_plan* plan, const fs_swarm* swarm, const double* edges_dev, int N_p);
 
 /* One PSO update (Eqs. pso_position_update, pso_velocity_update): personal
  * bests on a strictly greater fitness, ring local best {i-1, i, i+1} with ties
@@ -204,7 +231,7 @@ typedef struct fs_graph fs_graph;
  * alive and do not grow the workspace (reserve B >= R * n_part first).  Runs
  * one untimed evaluation before capturing.  Synchronous.  *out is NULL on
  * failure. */
-FS_API fs_status fs_pso_graph_build(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p,
+FS_API fs_status fs_pso_graph_build(fs_plan* plan, const fs_swarm* swarm, const double* edges_dev, int N_p,
                                     uint64_t seed, double w0, double w1, int n_iter, double c1, double c2,
                                     double vmax, fs_graph** out);
 
@@ -329,7 +356,7 @@ FS_API fs_status fs_pso_record(fs_plan* plan, const fs_swarm* swarm, const fs_sa
  * the graph runs, so training between launches takes effect.  The ring and
  * network arrays are read at capture time.  Synchronous; runs one untimed
  * evaluation first when bit 1 is set. */
-FS_API fs_status fs_pso_graph_build_ex(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p,
+FS_API fs_status fs_pso_graph_build_ex(fs_plan* plan, const fs_swarm* swarm, const double* edges_dev, int N_p,
                                        uint64_t seed, double w0, double w1, int n_iter, double c1, double c2,
                                        double vmax, int parts, const fs_sample_ring* rings, int n_rings,
                                        fs_mlp* const* mlps, int n_mlp, int n_cand, fs_graph** out);
@@ -373,7 +400,7 @@ FS_API fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_s
 FS_API fs_status fs_plan_set_variant(fs_plan* plan, int variant);
 
 /* Record `variant` for calls with this N_p and edge kind (global_edges != 0:
- * edges_host given; 0: per-particle edges), as the autotuner would.  Lets a
+ * edge frequencies given; 0: per-particle edges), as the autotuner would.  Lets a
  * resumed search reuse the choices of the run it continues. */
 FS_API fs_status fs_plan_set_variant_for(fs_plan* plan, int N_p, int global_edges, int variant);
 
@@ -390,7 +417,7 @@ FS_API fs_status fs_plan_get_variant(fs_plan* plan, int N_p, int global_edges, i
  * anchors.  Synchronous; must not be called while the plan's stream is being
  * captured.  For roofline accounting (the operation count per bin differs
  * between modes and tiers). */
-FS_API fs_status fs_plan_census(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
+FS_API fs_status fs_plan_census(fs_plan* plan, const fs_params* params_dev, int B, const double* edges_dev,
                                 int N_p, int64_t* counts);
 
 /* Autotuner: time every variant on this batch (one untimed call, then `reps`
@@ -400,12 +427,12 @@ FS_API fs_status fs_plan_census(fs_plan* plan, const fs_params* params_dev, int 
  * (4 entries in FS_MIXED, 5 in FS_FP64).  Synchronous; FS_EINVAL while the
  * plan's stream is being captured.  Arguments as in fs_fstat_batch; the F
  * values computed go to plan scratch, not to the caller. */
-FS_API fs_status fs_plan_autotune(fs_plan* plan, const fs_params* params_dev, int B, const int64_t* edges_host,
+FS_API fs_status fs_plan_autotune(fs_plan* plan, const fs_params* params_dev, int B, const double* edges_dev,
                                   int N_p, int reps, int* variant_out, float* ms_out);
 
 /* fs_plan_autotune on the swarm's current positions (mapped to physical
  * parameters as fs_pso_evaluate does).  The swarm is not modified. */
-FS_API fs_status fs_pso_autotune(fs_plan* plan, const fs_swarm* swarm, const int64_t* edges_host, int N_p,
+FS_API fs_status fs_pso_autotune(fs_plan* plan, const fs_swarm* swarm, const double* edges_dev, int N_p,
                                  int reps, int* variant_out, float* ms_out);
 
 /* Kernel timing on the plan's stream.  While enabled, every kernel the plan
@@ -423,22 +450,27 @@ FS_API fs_status fs_plan_read_profile(fs_plan* plan, int kernel, double* total_m
  * fixed memory budget).  The paper has no counterpart: it is a deployment
  * variant of fs_fstat_batch in FS_FP64 mode, not part of the method.
  *   Inputs are the grid (n_bins, f_min, df, T_obs as for fs_plan_create), the
- *   data and PSD (as for fs_plan_set_data), params_dev / B / edges_host / N_p
- *   (as for fs_fstat_batch); outputs F_dev and F_part_dev (may be NULL) as for
- *   fs_fstat_batch; stream is a cudaStream_t (NULL = legacy default stream).
+ *   data and PSD (as for fs_plan_set_data with f_grid_dev = NULL), params_dev
+ *   / B / edges_dev / N_p (as for fs_fstat_batch: edge frequencies in device
+ *   memory, converted to bins inside the call; invalid edges give F = NaN,
+ *   there is no flag word to check); outputs F_dev and F_part_dev (may be
+ *   NULL) as for fs_fstat_batch; stream is a cudaStream_t (NULL = legacy
+ *   default stream).
  *   Limits: n_bins <= 32768, 0 <= B <= 1024, 1 <= N_p <= 64; larger requests
  *   return FS_EINVAL with a message naming the limit.
  * Workspace: a 10 MiB file-scope device array of the library, held by every
  * GPU that loads the library until the process exits.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * device current and keeps it for the life of the process (a cudaDeviceReset
+ * afterwards is not supported); make that first call before any stream
+ * capture.  All calls
  * share the one array and each call overwrites what it needs, so calls that
  * may overlap on the GPU (different streams, or different host threads on the
  * same device) race and must be serialised by the caller.  Calls no
  * cudaMalloc, cudaFree or other allocating routine.  Asynchronous. */
 FS_API fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double df, double T_obs,
                                         const double* data_dev, const double* psd_dev, const fs_params* params_dev,
-                                        int B, const int64_t* edges_host, int N_p, double* F_dev,
+                                        int B, const double* edges_dev, int N_p, double* F_dev,
                                         double* F_part_dev, void* stream);
 
 /* Constants compiled into the library: out[0] = solar mass in s, out[1] =

@@ -329,6 +329,28 @@ static void or_segment_starts(const or_params* P, const or_model* m, const int64
         for (int p = 1; p < Np; p++) starts[p] = khi + 1;
 }
 
+/* Segment start bins from N_p + 1 global edge frequencies (Sec. II.B: bin k
+ * lies in segment p iff e_p <= f_k < e_{p+1}, the last segment closed at
+ * e_{N_p}), by the definition: starts[p] counts the bins with f_k < e_p for
+ * p < N_p and starts[N_p] those with f_k <= e_{N_p}, every bin tested.  Since
+ * f_k grows with k, segment p is then the bins [starts[p], starts[p+1]).
+ * Returns -1 (and writes nothing) if an edge is not finite or the edges
+ * decrease. */
+int or_edge_starts(const or_model* m, const double* e, int Np, int64_t* starts) {
+    for (int p = 0; p <= Np; p++) {
+        if (!isfinite(e[p])) return -1;
+        if (p > 0 && !(e[p - 1] <= e[p])) return -1;
+    }
+    for (int p = 0; p <= Np; p++) starts[p] = 0;
+    for (int64_t k = 0; k < m->n; k++) {
+        const double f = m->f_min + (double)k * m->df;
+        for (int p = 0; p < Np; p++)
+            if (f < e[p]) starts[p]++;
+        if (f <= e[Np]) starts[Np]++;
+    }
+    return 0;
+}
+
 /* Per-segment N^i = <d, A^i> and M^ij = <A^i, A^j> (Eqs. aandMN, aandMN2)
  * with the segment inner product <a,b>_l = 4 df Re sum_k a_k conj(b_k)/S_k.
  * Products and sums are formed in long double: on short segments F+ and Fx

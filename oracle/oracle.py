@@ -61,6 +61,8 @@ def lib():
             L.or_fstat_batch.restype = C.c_int
             L.or_segment_sums.argtypes = [C.POINTER(Params), C.POINTER(Model), _dp, _dp, _dp, _i64p,
                                           C.c_int, _dp, _dp, _i64p]
+            L.or_edge_starts.argtypes = [C.POINTER(Model), _dp, C.c_int, _i64p]
+            L.or_edge_starts.restype = C.c_int
             L.or_segment_F.argtypes = [_dp, _dp, C.c_int64]
             L.or_segment_F.restype = C.c_double
             L.or_basis.argtypes = [C.POINTER(Params), C.POINTER(Model), C.c_int64, C.c_int64, _dp, _dp]
@@ -128,9 +130,24 @@ def _params_array(P: np.ndarray):
     return arr
 
 
+def edge_starts(model: OracleModel, edges_hz, Np: int) -> np.ndarray:
+    """Segment start bins [Np + 1] of global edge frequencies (Sec. II.B membership rule)."""
+    e = np.ascontiguousarray(edges_hz, dtype=np.float64)
+    if e.shape != (Np + 1,):
+        raise ValueError("edges_hz must have N_p + 1 entries")
+    out = np.zeros(Np + 1, dtype=np.int64)
+    m = model.c()
+    if lib().or_edge_starts(C.byref(m), _ptr(e), int(Np), _ptr(out, C.c_int64)) != 0:
+        raise ValueError("edge frequencies must be finite and non-decreasing")
+    return out
+
+
 def fstat_batch(params: np.ndarray, model: OracleModel, data: np.ndarray, psd: np.ndarray,
-                Np: int, edges: np.ndarray | None = None, nthreads: int = 0):
-    """F[b] = sum over segments of F_p and Fpart[b, p] for params [B, 6]."""
+                Np: int, edges: np.ndarray | None = None, nthreads: int = 0, edges_hz=None):
+    """F[b] = sum over segments of F_p and Fpart[b, p] for params [B, 6].
+    Global segments as start bins (edges) or as edge frequencies (edges_hz)."""
+    if edges_hz is not None:
+        edges = edge_starts(model, edges_hz, Np)
     B = len(params)
     d_re = np.ascontiguousarray(data.real, dtype=np.float64)
     d_im = np.ascontiguousarray(data.imag, dtype=np.float64)

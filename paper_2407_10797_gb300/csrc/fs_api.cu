@@ -85,10 +85,10 @@ struct fs_plan {
     float *cand_in, *cand_score;
     unsigned char* cand_inside;
 
-    // segment edges (global mode)
+    // segment start bins of the current call (global mode; converted on the device from the
+    // caller's edge frequencies at the start of every evaluation) and the sticky error flags
     int64_t* edges_dev;
-    int64_t* edges_cache;
-    int edges_np;
+    int* flags_dev;
     // single-particle scratch for fs_add_signal
     fs_params* one_param;
     fs::Particle* one_part;
@@ -299,7 +299,9 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
     double** slots[fs::kNumTables] = {&p->tab.fh, &p->tab.fl, &p->tab.u, &p->tab.g0h, &p->tab.g0l,
                                       &p->tab.e19, &p->tab.dwr, &p->tab.dwi, &p->tab.W};
     for (int i = 0; i < fs::kNumTables; i++) *slots[i] = q + (size_t)i * n_bins;
-    if ((e = cudaMalloc(&p->edges_dev, sizeof(int64_t) * (fs::kNpMax + 1))) != cudaSuccess ||
+    if ((e = cudaMalloc(&p->edges_dev, sizeof(int64_t) * (fs::kNpMax + 2))) != cudaSuccess ||
+        (e = cudaMalloc(&p->flags_dev, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
         (e = cudaMalloc(&p->one_param, sizeof(fs_params))) != cudaSuccess ||
         (e = cudaMalloc(&p->one_part, sizeof(fs::Particle))) != cudaSuccess ||
         (e = cudaMalloc(&p->one_a, sizeof(double) * 4)) != cudaSuccess) {
@@ -312,8 +314,6 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
         fs_plan_destroy(p);
         return cuda_fail(e, "cudaMalloc(mixed tables)");
     }
-    p->edges_cache = (int64_t*)malloc(sizeof(int64_t) * (fs::kNpMax + 1));
-    p->edges_np = 0;
     p->prof = new std::vector<fs_plan::ProfRec>();
     p->spare = new std::vector<cudaEvent_t>();
     *out = p;
@@ -327,12 +327,12 @@ fs_status fs_plan_destroy(fs_plan* p) {
     cudaFree(p->census);
     cudaFree(p->tab_base);
     cudaFree(p->edges_dev);
+    cudaFree(p->flags_dev);
     cudaFree(p->one_param);
     cudaFree(p->one_part);
     cudaFree(p->one_a);
     cudaFree(p->tab32);
     cudaFree(p->emax);
-    free(p->edges_cache);
     cudaFree(p->cand_x);
     cudaFree(p->cand_v);
     cudaFree(p->cand_in);
@@ -353,9 +353,25 @@ fs_status fs_plan_destroy(fs_plan* p) {
     return FS_OK;
 }
 
-fs_status fs_plan_set_data(fs_plan* p, const double* data_dev, const double* psd_dev) {
+fs_status fs_plan_set_data(fs_plan* p, const double* data_dev, const double* psd_dev, const double* f_grid_dev) {
     g_err[0] = 0;
     if (!p || !data_dev || !psd_dev) return fail(FS_EINVAL, "fs_plan_set_data: NULL argument");
+    if (f_grid_dev) {
+        // the kernels step the phase in the bin index, which needs the uniform grid
+        // f_k = f_min + k df: check the caller's grid against it and wait for the answer
+        int h = 0;
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
+            (e = fs::launch_grid_check(p->grid, f_grid_dev, p->flags_dev, p->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&h, p->flags_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+            return cuda_fail(e, "fs_plan_set_data: grid check");
+        if (h & fs::kFlagBadGrid)
+            return fail(FS_EUNSUPPORTED,
+                        "fs_plan_set_data: f_grid is not the uniform grid f_min + k df of the plan (to 4 ulp); "
+                        "non-uniform grids are not supported");
+    }
     ProfScope ps(p, 3);
     cudaError_t e = fs::launch_precompute(p->grid, data_dev, psd_dev, p->tab, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
@@ -372,18 +388,35 @@ fs_status fs_plan_reserve(fs_plan* p, int B_max, int Np_max) {
     return ensure_workspace(p, B_max > 0 ? B_max : 1, Np_max);
 }
 
+fs_status fs_plan_check(fs_plan* p, int* flags_out) {
+    g_err[0] = 0;
+    if (flags_out) *flags_out = 0;
+    if (!p) return fail(FS_EINVAL, "fs_plan_check: plan is NULL");
+    int h = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&h, p->flags_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+        return cuda_fail(e, "fs_plan_check");
+    if (flags_out) *flags_out = h;
+    if (h & fs::kFlagBadEdges)
+        return fail(FS_EINVAL, "fs_plan_check: an earlier call was given partition edges that are not finite or "
+                               "decrease (its F values are NaN)");
+    return FS_OK;
+}
+
 namespace {
-fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const double* edges_dev, int Np,
                      double* F_dev, double* F_part_dev, double* amp_dev);
 }
 
-fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+fs_status fs_fstat_batch(fs_plan* p, const fs_params* params_dev, int B, const double* edges_dev, int Np,
                          double* F_dev, double* F_part_dev) {
     g_err[0] = 0;
-    return fstat_impl(p, params_dev, B, edges_host, Np, F_dev, F_part_dev, nullptr);
+    return fstat_impl(p, params_dev, B, edges_dev, Np, F_dev, F_part_dev, nullptr);
 }
 
-fs_status fs_amplitudes(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+fs_status fs_amplitudes(fs_plan* p, const fs_params* params_dev, int B, const double* edges_dev, int Np,
                         double* F_dev, double* a_dev, double* ext_dev) {
     g_err[0] = 0;
     if (!p) return fail(FS_EINVAL, "fs_amplitudes: plan is NULL");
@@ -392,7 +425,7 @@ fs_status fs_amplitudes(fs_plan* p, const fs_params* params_dev, int B, const in
     if (Np < 1 || Np > fs::kNpMax) return fail(FS_EINVAL, "fs_amplitudes: N_p = %d not in [1, %d]", Np, fs::kNpMax);
     fs_status st = ensure_workspace(p, B, Np);
     if (st != FS_OK) return st;
-    if ((st = fstat_impl(p, params_dev, B, edges_host, Np, F_dev ? F_dev : p->pso_F, nullptr, a_dev)) != FS_OK)
+    if ((st = fstat_impl(p, params_dev, B, edges_dev, Np, F_dev ? F_dev : p->pso_F, nullptr, a_dev)) != FS_OK)
         return st;
     if (ext_dev) {
         cudaError_t e = fs::launch_extrinsic((int64_t)B * Np, a_dev, ext_dev, p->stream);
@@ -401,7 +434,7 @@ fs_status fs_amplitudes(fs_plan* p, const fs_params* params_dev, int B, const in
     return FS_OK;
 }
 
-fs_status fs_plan_census(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+fs_status fs_plan_census(fs_plan* p, const fs_params* params_dev, int B, const double* edges_dev, int Np,
                          int64_t* counts) {
     g_err[0] = 0;
     if (!p || !counts) return fail(FS_EINVAL, "fs_plan_census: NULL plan or counts");
@@ -415,7 +448,7 @@ fs_status fs_plan_census(fs_plan* p, const fs_params* params_dev, int B, const i
     if ((e = cudaMemsetAsync(p->census, 0, 6 * sizeof(unsigned long long), p->stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync(census)");
     p->census_on = 1;
-    st = fstat_impl(p, params_dev, B, edges_host, Np, p->pso_F, nullptr, nullptr);
+    st = fstat_impl(p, params_dev, B, edges_dev, Np, p->pso_F, nullptr, nullptr);
     p->census_on = 0;
     if (st != FS_OK) return st;
     unsigned long long h[6];
@@ -427,7 +460,7 @@ fs_status fs_plan_census(fs_plan* p, const fs_params* params_dev, int B, const i
 }
 
 namespace {
-fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const double* edges_dev, int Np,
                      double* F_dev, double* F_part_dev, double* amp_dev) {
     if (!p) return fail(FS_EINVAL, "fs_fstat_batch: plan is NULL");
     if (B < 0) return fail(FS_EINVAL, "fs_fstat_batch: B = %d < 0", B);
@@ -436,31 +469,13 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const int64
     if (B == 0) return FS_OK;
     if (!params_dev || !F_dev) return fail(FS_EINVAL, "fs_fstat_batch: NULL params or F");
     if (!p->data_set) return fail(FS_EINVAL, "fs_fstat_batch: fs_plan_set_data was not called");
-    int global = edges_host != nullptr;
-    if (global) {
-        for (int i = 0; i <= Np; i++) {
-            if (edges_host[i] < 0 || edges_host[i] > p->grid.n)
-                return fail(FS_EINVAL, "fs_fstat_batch: edge %d = %lld outside [0, n_bins]", i,
-                            (long long)edges_host[i]);
-            if (i > 0 && edges_host[i] < edges_host[i - 1])
-                return fail(FS_EINVAL, "fs_fstat_batch: edges must be non-decreasing");
-        }
-        if (edges_host[Np] == edges_host[0])
-            return fail(FS_EINVAL, "fs_fstat_batch: edges span no bins");
-    }
+    const int global = edges_dev != nullptr;
     fs_status st = ensure_workspace(p, B, Np);
     if (st != FS_OK) return st;
     cudaError_t e;
-    if (global && (p->edges_np != Np || memcmp(p->edges_cache, edges_host, sizeof(int64_t) * (Np + 1)) != 0)) {
-        memcpy(p->edges_cache, edges_host, sizeof(int64_t) * (Np + 1));
-        p->edges_np = Np;
-        e = cudaMemcpyAsync(p->edges_dev, p->edges_cache, sizeof(int64_t) * (Np + 1), cudaMemcpyHostToDevice,
-                            p->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(edges)");
-        // the host cache is rewritten only on a change; wait so a later change cannot race this copy
-        e = cudaStreamSynchronize(p->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(edges)");
-    }
+    // segment starts from the caller's edge frequencies, on the stream (no host wait)
+    if (global && (e = fs::launch_edges(p->grid, edges_dev, Np, p->edges_dev, p->flags_dev, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "edges launch");
     fs::Segs sg;
     sg.Np = Np;
     sg.global = global;
@@ -546,7 +561,7 @@ fs_status fs_pso_init(fs_plan* p, const fs_swarm* w, uint64_t seed) {
     return FS_OK;
 }
 
-fs_status fs_pso_evaluate(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np) {
+fs_status fs_pso_evaluate(fs_plan* p, const fs_swarm* w, const double* edges_dev, int Np) {
     g_err[0] = 0;
     if (!p) return fail(FS_EINVAL, "fs_pso_evaluate: plan is NULL");
     fs_status st = check_swarm(w);
@@ -557,13 +572,13 @@ fs_status fs_pso_evaluate(fs_plan* p, const fs_swarm* w, const int64_t* edges_ho
     if ((st = ensure_workspace(p, n, Np)) != FS_OK) return st;
     cudaError_t e = fs::launch_pso_map(w->R, w->n_part, w->x, w->box, w->q, p->pso_params, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso map launch");
-    if ((st = fs_fstat_batch(p, p->pso_params, n, edges_host, Np, p->pso_F, nullptr)) != FS_OK) return st;
+    if ((st = fs_fstat_batch(p, p->pso_params, n, edges_dev, Np, p->pso_F, nullptr)) != FS_OK) return st;
     if ((e = fs::launch_pso_fitness(n, p->pso_F, Np, w->fit, p->stream)) != cudaSuccess)
         return cuda_fail(e, "pso fitness launch");
     return FS_OK;
 }
 
-fs_status fs_pso_autotune(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np, int reps,
+fs_status fs_pso_autotune(fs_plan* p, const fs_swarm* w, const double* edges_dev, int Np, int reps,
                           int* variant_out, float* ms_out) {
     g_err[0] = 0;
     if (!p) return fail(FS_EINVAL, "fs_pso_autotune: plan is NULL");
@@ -575,7 +590,7 @@ fs_status fs_pso_autotune(fs_plan* p, const fs_swarm* w, const int64_t* edges_ho
     if ((st = ensure_workspace(p, n, Np)) != FS_OK) return st;
     cudaError_t e = fs::launch_pso_map(w->R, w->n_part, w->x, w->box, w->q, p->pso_params, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso map launch");
-    return fs_plan_autotune(p, p->pso_params, n, edges_host, Np, reps, variant_out, ms_out);
+    return fs_plan_autotune(p, p->pso_params, n, edges_dev, Np, reps, variant_out, ms_out);
 }
 
 fs_status fs_pso_step(fs_plan* p, const fs_swarm* w, uint64_t seed, int iteration, double w0, double w1, int n_iter,
@@ -634,7 +649,7 @@ fs_status fs_pso_best(fs_plan* p, const fs_swarm* w, double* best_f, int* best_i
     return FS_OK;
 }
 
-fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np, uint64_t seed,
+fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const double* edges_dev, int Np, uint64_t seed,
                              double w0, double w1, int n_iter, double c1, double c2, double vmax, fs_graph** out) {
     g_err[0] = 0;
     if (!out) return fail(FS_EINVAL, "fs_pso_graph_build: out is NULL");
@@ -647,7 +662,7 @@ fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges
     const int n = w->R * w->n_part;
     // everything that may allocate, copy or synchronise happens before capture
     if ((st = ensure_workspace(p, n > 0 ? n : 1, Np)) != FS_OK) return st;
-    if ((st = fs_pso_evaluate(p, w, edges_host, Np)) != FS_OK) return st;   // also uploads the edges
+    if ((st = fs_pso_evaluate(p, w, edges_dev, Np)) != FS_OK) return st;
     cudaError_t e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     const int prof = p->profiling;
@@ -656,7 +671,7 @@ fs_status fs_pso_graph_build(fs_plan* p, const fs_swarm* w, const int64_t* edges
         p->profiling = prof;
         return cuda_fail(e, "cudaStreamBeginCapture");
     }
-    fs_status s1 = fs_pso_evaluate(p, w, edges_host, Np);
+    fs_status s1 = fs_pso_evaluate(p, w, edges_dev, Np);
     fs_status s2 = s1 == FS_OK ? fs_pso_step(p, w, seed, -1, w0, w1, n_iter, c1, c2, vmax, nullptr) : s1;
     cudaGraph_t gr = nullptr;
     e = cudaStreamEndCapture(p->stream, &gr);
@@ -714,7 +729,7 @@ fs_status fs_pso_record(fs_plan* p, const fs_swarm* w, const fs_sample_ring* rin
 
 fs_status fs_mlp_stream(fs_mlp* m, cudaStream_t* s);
 
-fs_status fs_pso_graph_build_ex(fs_plan* p, const fs_swarm* w, const int64_t* edges_host, int Np, uint64_t seed,
+fs_status fs_pso_graph_build_ex(fs_plan* p, const fs_swarm* w, const double* edges_dev, int Np, uint64_t seed,
                                 double w0, double w1, int n_iter, double c1, double c2, double vmax, int parts,
                                 const fs_sample_ring* rings, int n_rings, fs_mlp* const* mlps, int n_mlp, int n_cand,
                                 fs_graph** out) {
@@ -742,7 +757,7 @@ fs_status fs_pso_graph_build_ex(fs_plan* p, const fs_swarm* w, const int64_t* ed
     const int n = w->R * w->n_part;
     if ((st = ensure_workspace(p, n > 0 ? n : 1, Np)) != FS_OK) return st;
     if (parts & 1) {
-        if ((st = fs_pso_evaluate(p, w, edges_host, Np)) != FS_OK) return st;   // also uploads the edges
+        if ((st = fs_pso_evaluate(p, w, edges_dev, Np)) != FS_OK) return st;
     }
     if (parts & 8) {
         if (n_cand < 1 || n_cand > 64) return fail(FS_EINVAL, "fs_pso_graph_build_ex: n_cand must be in [1, 64]");
@@ -757,7 +772,7 @@ fs_status fs_pso_graph_build_ex(fs_plan* p, const fs_swarm* w, const int64_t* ed
         return cuda_fail(e, "cudaStreamBeginCapture");
     }
     st = FS_OK;
-    if (parts & 1) st = fs_pso_evaluate(p, w, edges_host, Np);
+    if (parts & 1) st = fs_pso_evaluate(p, w, edges_dev, Np);
     if (st == FS_OK && (parts & 2)) st = fs_pso_record(p, w, rings, n_rings);
     if (st == FS_OK && (parts & 4)) st = fs_pso_step(p, w, seed, -1, w0, w1, n_iter, c1, c2, vmax, nullptr);
     if (st == FS_OK && (parts & 8))
@@ -888,7 +903,7 @@ fs_status fs_plan_get_variant(fs_plan* p, int Np, int global_edges, int* variant
     return FS_OK;
 }
 
-fs_status fs_plan_autotune(fs_plan* p, const fs_params* params_dev, int B, const int64_t* edges_host, int Np,
+fs_status fs_plan_autotune(fs_plan* p, const fs_params* params_dev, int B, const double* edges_dev, int Np,
                            int reps, int* variant_out, float* ms_out) {
     g_err[0] = 0;
     if (!p) return fail(FS_EINVAL, "fs_plan_autotune: plan is NULL");
@@ -907,18 +922,18 @@ fs_status fs_plan_autotune(fs_plan* p, const fs_params* params_dev, int B, const
         return cuda_fail(e, "cudaEventCreate");
     }
     const int saved = p->variant_forced;
-    const int global = edges_host != nullptr;
+    const int global = edges_dev != nullptr;
     int best = 0;
     float best_ms = 0.f;
     st = FS_OK;
     for (int v = 0; v < n_variants(p->mode) && st == FS_OK; v++) {
         p->variant_forced = v;
-        if ((st = fs_fstat_batch(p, params_dev, B, edges_host, Np, F, nullptr)) != FS_OK) break;   // warm-up
+        if ((st = fs_fstat_batch(p, params_dev, B, edges_dev, Np, F, nullptr)) != FS_OK) break;   // warm-up
         if ((e = cudaEventRecord(ev[0], p->stream)) != cudaSuccess) {
             st = cuda_fail(e, "cudaEventRecord");
             break;
         }
-        for (int r = 0; r < reps && st == FS_OK; r++) st = fs_fstat_batch(p, params_dev, B, edges_host, Np, F, nullptr);
+        for (int r = 0; r < reps && st == FS_OK; r++) st = fs_fstat_batch(p, params_dev, B, edges_dev, Np, F, nullptr);
         if (st != FS_OK) break;
         float ms = 0.f;
         if ((e = cudaEventRecord(ev[1], p->stream)) != cudaSuccess || (e = cudaEventSynchronize(ev[1])) != cudaSuccess ||

@@ -490,7 +490,7 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
     const int b = (int)(wid / sg.Np);
     const int p = (int)(wid % sg.Np);
     const Particle& P = parts[b];
-    if (!P.valid) {
+    if (!P.valid || (sg.global && sg.edges[sg.Np + 1] == 0)) {   // invalid particle or invalid edge frequencies
         if (lane == 0) {
             Fpart[wid] = __longlong_as_double(0x7ff8000000000000LL);
             if (amp)

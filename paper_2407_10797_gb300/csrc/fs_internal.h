@@ -39,8 +39,13 @@ struct Grid {
 struct Segs {
     int Np;
     int global;               // 1: edges[] apply to every particle
-    const int64_t* edges;     // device, Np+1 (global mode only)
+    const int64_t* edges;     // device (global mode only): Np+1 segment start bins, then a validity word
+                              // at edges[Np+1] (0: the caller's edge frequencies were invalid)
 };
+
+// Bits of a plan's sticky device flag word (read and cleared by fs_plan_check).
+constexpr int kFlagBadEdges = 1;   // partition edges not finite or decreasing
+constexpr int kFlagBadGrid = 2;    // a caller's frequency grid is not f_min + k df
 
 struct Partials {
     double* H;    // [B][ntiles][7] first segment of each (particle, tile)
@@ -56,6 +61,10 @@ struct Partials {
 // Record an error message for fs_last_error() and return st.
 fs_status set_error(fs_status st, const char* fmt, ...);
 
+// Segment starts from N_p + 1 edge frequencies (device), validity word at starts[Np+1].
+cudaError_t launch_edges(const Grid& g, const double* edges_hz, int Np, int64_t* starts, int* flags,
+                         cudaStream_t s);
+cudaError_t launch_grid_check(const Grid& g, const double* f_grid, int* flags, cudaStream_t s);
 cudaError_t launch_precompute(const Grid& g, const double* data, const double* psd, const Tables& t,
                               cudaStream_t s);
 cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Particle* parts, int global,

@@ -56,7 +56,7 @@ constexpr Layout layout_for(int64_t n, int B, int Np) {
     L.rot = off;
     off += align256(sizeof(double2) * (size_t)Np * B);
     L.edges = off;
-    off += align256(sizeof(int64_t) * (size_t)(Np + 1));
+    off += align256(sizeof(int64_t) * (size_t)(Np + 2));   // segment starts and the validity word
     L.total = off;
     return L;
 }
@@ -64,7 +64,9 @@ constexpr Layout layout_for(int64_t n, int B, int Np) {
 static_assert(layout_for(kMaxBins, kMaxB, kMaxNp).total <= kScratchBytes,
               "the scratch array must hold a call at the stated limits");
 
-// Device address of g_scratch on the current device (looked up once per device).
+// Device address of g_scratch on the current device (looked up once per device
+// and kept for the life of the process, so a cudaDeviceReset after the first
+// call on a device is not supported).
 fs_status scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -86,7 +88,7 @@ fs_status scratch_address(void** out) {
 
 extern "C" fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double df, double T_obs,
                                             const double* data_dev, const double* psd_dev,
-                                            const fs_params* params_dev, int B, const int64_t* edges_host,
+                                            const fs_params* params_dev, int B, const double* edges_dev,
                                             int N_p, double* F_dev, double* F_part_dev, void* stream) {
     fs::set_error(FS_OK, "");
     if (n_bins <= 0 || !(f_min > 0.0) || !(df > 0.0) || !(T_obs > 0.0) || !isfinite(f_min) || !isfinite(df) ||
@@ -102,15 +104,7 @@ extern "C" fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double
     if (B == 0) return FS_OK;
     if (!data_dev || !psd_dev || !params_dev || !F_dev)
         return fs::set_error(FS_EINVAL, "fs_fstat_batch_noalloc: NULL data, psd, params or F");
-    const int global = edges_host != nullptr;
-    if (global) {
-        for (int i = 0; i <= N_p; i++) {
-            if (edges_host[i] < 0 || edges_host[i] > n_bins || (i > 0 && edges_host[i] < edges_host[i - 1]))
-                return fs::set_error(FS_EINVAL, "fs_fstat_batch_noalloc: edges must be non-decreasing in [0, n_bins]");
-        }
-        if (edges_host[N_p] == edges_host[0])
-            return fs::set_error(FS_EINVAL, "fs_fstat_batch_noalloc: edges span no bins");
-    }
+    const int global = edges_dev != nullptr;
     void* base = nullptr;
     fs_status st = scratch_address(&base);
     if (st != FS_OK) return st;
@@ -130,11 +124,11 @@ extern "C" fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double
     double** slots[fs::kNumTables] = {&tb.fh, &tb.fl, &tb.u, &tb.g0h, &tb.g0l, &tb.e19, &tb.dwr, &tb.dwi, &tb.W};
     for (int i = 0; i < fs::kNumTables; i++) *slots[i] = tab + (size_t)i * n_bins;
     fs::Particle* parts = (fs::Particle*)(sp + L.parts);
-    int64_t* edges_dev = (int64_t*)(sp + L.edges);
+    int64_t* starts = (int64_t*)(sp + L.edges);
     fs::Segs sg;
     sg.Np = N_p;
     sg.global = global;
-    sg.edges = edges_dev;
+    sg.edges = starts;
     fs::Partials pa;
     pa.H = (double*)(sp + L.H);
     pa.T = (double*)(sp + L.T);
@@ -146,13 +140,12 @@ extern "C" fs_status fs_fstat_batch_noalloc(int64_t n_bins, double f_min, double
     double* Fpart = F_part_dev ? F_part_dev : (double*)(sp + L.Fpart);
 
     // Every scratch byte a kernel reads is written earlier in this same call
-    // (tables, particles, rotations, the partial sums of the tiles a segment
-    // spans), so nothing needs clearing between calls.
+    // (segment starts, tables, particles, rotations, the partial sums of the
+    // tiles a segment spans), so nothing needs clearing between calls.  Edge
+    // frequencies that are not finite or decrease give F = NaN (no flag word).
     cudaError_t e;
-    if (global && (e = cudaMemcpyAsync(edges_dev, edges_host, sizeof(int64_t) * (N_p + 1), cudaMemcpyHostToDevice,
-                                       s)) != cudaSuccess)
-        return fs::set_error(FS_ECUDA, "cudaMemcpyAsync(edges): %s", cudaGetErrorString(e));
-    if ((e = fs::launch_precompute(g, data_dev, psd_dev, tb, s)) != cudaSuccess ||
+    if ((global && (e = fs::launch_edges(g, edges_dev, N_p, starts, nullptr, s)) != cudaSuccess) ||
+        (e = fs::launch_precompute(g, data_dev, psd_dev, tb, s)) != cudaSuccess ||
         (e = fs::launch_setup(g, params_dev, B, parts, global, s)) != cudaSuccess ||
         (e = fs::launch_rotation(g, parts, B, sg, pa.rot, nullptr, s)) != cudaSuccess ||
         (e = fs::launch_fp64_main(g, tb, parts, B, sg, pa, s)) != cudaSuccess ||

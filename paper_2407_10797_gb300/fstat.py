@@ -62,24 +62,25 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L = C.CDLL(_build.LIB)
         L.fs_plan_create.argtypes = [C.POINTER(_vp), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int, _vp]
         L.fs_plan_destroy.argtypes = [_vp]
-        L.fs_plan_set_data.argtypes = [_vp, _vp, _vp]
+        L.fs_plan_set_data.argtypes = [_vp, _vp, _vp, _vp]
+        L.fs_plan_check.argtypes = [_vp, C.POINTER(C.c_int)]
         L.fs_plan_reserve.argtypes = [_vp, C.c_int, C.c_int]
-        L.fs_fstat_batch.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp]
-        L.fs_amplitudes.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp, _vp]
+        L.fs_fstat_batch.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp]
+        L.fs_amplitudes.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]
         L.fs_add_signal.argtypes = [_vp, C.POINTER(fs_params), _dp, _vp]
         L.fs_constants.argtypes = [_dp]
         L.fs_particle_bands.argtypes = [_vp, _vp, C.c_int, _vp]
         L.fs_fstat_batch_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp,
-                                             C.c_int, C.POINTER(C.c_int64), C.c_int, _vp, _vp, _vp]
+                                             C.c_int, _vp, C.c_int, _vp, _vp, _vp]
         L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
         L.fs_plan_set_variant.argtypes = [_vp, C.c_int]
         L.fs_plan_set_variant_for.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
         L.fs_plan_get_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
-        L.fs_plan_census.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int64)]
-        L.fs_plan_autotune.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int,
+        L.fs_plan_census.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int64)]
+        L.fs_plan_autotune.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, C.c_int,
                                        C.POINTER(C.c_int), C.POINTER(C.c_float)]
         _sw = C.POINTER(fs_swarm)
-        _ep = C.POINTER(C.c_int64)
+        _ep = _vp   # edge frequencies: device pointer
         L.fs_pso_init.argtypes = [_vp, _sw, C.c_uint64]
         L.fs_pso_evaluate.argtypes = [_vp, _sw, _ep, C.c_int]
         L.fs_pso_autotune.argtypes = [_vp, _sw, _ep, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
@@ -114,7 +115,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_mlp_train.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp]
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
-        for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_reserve",
+        for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_check", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_amplitudes", "fs_add_signal", "fs_constants", "fs_particle_bands",
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
                      "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
@@ -192,18 +193,31 @@ class Plan:
         except Exception:
             pass
 
-    def set_data(self, data, psd):
-        """data: complex128 CUDA tensor [n] (or float64 [n, 2]); psd: float64 CUDA tensor [n]."""
+    def set_data(self, data, psd, f_grid=None):
+        """data: complex128 CUDA tensor [n] (or float64 [n, 2]); psd: float64 CUDA tensor [n];
+        f_grid: optional float64 CUDA tensor [n] of the data's frequencies (must be the
+        plan's uniform grid; FstatError FS_EUNSUPPORTED otherwise)."""
         import torch
         if data.dtype == torch.complex128:
             data = torch.view_as_real(data)
         if data.shape != (self.n, 2) or psd.shape != (self.n,):
             raise ValueError("data must be [n] complex and psd [n]")
+        if f_grid is not None:
+            _check_size(f_grid, self.n, "f_grid")
         # keep the inputs alive until the stream has consumed them
         self._data_keep = data.contiguous()
         self._psd_keep = psd.contiguous()
         _check(self._L.fs_plan_set_data(self._h, _cuda_ptr(self._data_keep, torch.float64),
-                                        _cuda_ptr(self._psd_keep, torch.float64)))
+                                        _cuda_ptr(self._psd_keep, torch.float64),
+                                        _cuda_ptr(f_grid.contiguous(), torch.float64) if f_grid is not None
+                                        else None))
+
+    def check(self) -> int:
+        """fs_plan_check: flag bits the device raised since the last check (raises
+        FstatError FS_EINVAL if a call was given invalid partition edges)."""
+        f = C.c_int()
+        _check(self._L.fs_plan_check(self._h, C.byref(f)))
+        return f.value
 
     def reserve(self, B_max: int, Np_max: int):
         _check(self._L.fs_plan_reserve(self._h, int(B_max), int(Np_max)))
@@ -223,12 +237,7 @@ class Plan:
         _check_size(F, B, "F")
         if F_part is not None:
             _check_size(F_part, B * Np, "F_part")
-        e = None
-        if edges is not None:
-            arr = np.ascontiguousarray(edges, dtype=np.int64)
-            if arr.shape != (Np + 1,):
-                raise ValueError("edges must have N_p + 1 entries")
-            e = arr.ctypes.data_as(C.POINTER(C.c_int64))
+        self._edges_keep, e = _edges_arg(edges, Np, dev, self.stream)
         _check(self._L.fs_fstat_batch(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(B), e, int(Np),
                                       _cuda_ptr(F, torch.float64),
                                       _cuda_ptr(F_part, torch.float64) if F_part is not None else None))
@@ -245,7 +254,7 @@ class Plan:
         F = torch.empty(B, dtype=torch.float64, device=dev)
         a = torch.empty(B, Np, 4, dtype=torch.float64, device=dev)
         ext = torch.empty(B, Np, 4, dtype=torch.float64, device=dev) if extrinsic else None
-        arr, e = _edges_arg(edges, Np)
+        self._edges_keep, e = _edges_arg(edges, Np, dev, self.stream)
         _check(self._L.fs_amplitudes(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(B), e, int(Np),
                                      _cuda_ptr(F, torch.float64), _cuda_ptr(a, torch.float64),
                                      _cuda_ptr(ext, torch.float64) if ext is not None else None))
@@ -286,7 +295,7 @@ class Plan:
         """Time every launch variant on this batch and keep the fastest for
         (N_p, edge kind).  Returns (variant, [mean ms per call of each variant])."""
         import torch
-        arr, e = _edges_arg(edges, Np)
+        self._edges_keep, e = _edges_arg(edges, Np, params.device, self.stream)
         v = C.c_int()
         ms = (C.c_float * 8)()
         _check(self._L.fs_plan_autotune(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
@@ -297,7 +306,7 @@ class Plan:
         """In-band particle*bins per anchor mode (fs_plan_census): [unused, widest
         tier or FP32 body, bin-by-bin fallback, tiers 3, 4, 5 (narrowest)]."""
         import torch
-        arr, e = _edges_arg(edges, Np)
+        self._edges_keep, e = _edges_arg(edges, Np, params.device, self.stream)
         out = (C.c_int64 * 6)()
         _check(self._L.fs_plan_census(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
                                       e, int(Np), out))
@@ -332,7 +341,8 @@ def fstat_batch_noalloc(grid, data, psd, params, Np: int, edges=None, F=None, F_
     B <= 1024, N_p <= 64).  For callers that cannot allocate device memory; the
     output tensors here are made by the caller (this wrapper creates them with
     torch if not given).  Calls that overlap on the GPU race on the shared
-    workspace."""
+    workspace.  Every tensor must be on one CUDA device; the call is made with
+    that device current (the library finds its array on the current device)."""
     import torch
     L = load()
     if data.dtype == torch.complex128:
@@ -340,35 +350,49 @@ def fstat_batch_noalloc(grid, data, psd, params, Np: int, edges=None, F=None, F_
     if params.dim() != 2 or params.shape[1] != 6:
         raise ValueError("params must be [B, 6]")
     B = params.shape[0]
+    dev = params.device
     if F is None:
-        F = torch.empty(B, dtype=torch.float64, device=params.device)
+        F = torch.empty(B, dtype=torch.float64, device=dev)
     _check_size(data, 2 * int(grid.n), "data (re, im pairs)")
     _check_size(psd, int(grid.n), "psd")
     _check_size(F, B, "F")
     if F_part is not None:
         _check_size(F_part, B * Np, "F_part")
-    e = None
-    if edges is not None:
-        arr = np.ascontiguousarray(edges, dtype=np.int64)
-        if arr.shape != (Np + 1,):
-            raise ValueError("edges must have N_p + 1 entries")
-        e = arr.ctypes.data_as(C.POINTER(C.c_int64))
-    _check(L.fs_fstat_batch_noalloc(int(grid.n), float(grid.f_min), float(grid.df), float(grid.T_obs),
-                                    _cuda_ptr(data, torch.float64), _cuda_ptr(psd, torch.float64),
-                                    _cuda_ptr(params, torch.float64), int(B), e, int(Np),
-                                    _cuda_ptr(F, torch.float64),
-                                    _cuda_ptr(F_part, torch.float64) if F_part is not None else None,
-                                    _stream_handle(stream)))
+    keep, e = _edges_arg(edges, Np, dev, stream)
+    for name, t in (("data", data), ("psd", psd), ("F", F), ("F_part", F_part), ("edges", keep)):
+        if t is not None and t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, params on {dev}: all tensors must share one device")
+    with torch.cuda.device(dev):
+        _check(L.fs_fstat_batch_noalloc(int(grid.n), float(grid.f_min), float(grid.df), float(grid.T_obs),
+                                        _cuda_ptr(data, torch.float64), _cuda_ptr(psd, torch.float64),
+                                        _cuda_ptr(params, torch.float64), int(B), e, int(Np),
+                                        _cuda_ptr(F, torch.float64),
+                                        _cuda_ptr(F_part, torch.float64) if F_part is not None else None,
+                                        _stream_handle(stream)))
     return F, F_part
 
 
-def _edges_arg(edges, Np):
+def _edges_arg(edges, Np, device, stream=None):
+    """Global segment edges as N_p + 1 frequencies (Hz) in device memory: a float64
+    CUDA tensor is passed as it is; other array-likes are copied to `device` on
+    the current stream, which `stream` (the stream the library will read them
+    on) then waits for.  Returns (tensor to keep alive while the stream or a
+    graph reads it, pointer)."""
     if edges is None:
         return None, None
-    arr = np.ascontiguousarray(edges, dtype=np.int64)
-    if arr.shape != (Np + 1,):
+    import torch
+    if isinstance(edges, torch.Tensor) and edges.is_cuda:
+        t = edges.contiguous()
+        if t.dtype != torch.float64:
+            raise TypeError("edges must be float64 frequencies")
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(edges, dtype=np.float64)).to(device)
+        if stream is not None and stream != torch.cuda.current_stream(device):
+            stream.wait_stream(torch.cuda.current_stream(device))
+            t.record_stream(stream)
+    if t.shape != (Np + 1,):
         raise ValueError("edges must have N_p + 1 entries")
-    return arr, arr.ctypes.data_as(C.POINTER(C.c_int64))
+    return t, C.c_void_p(t.data_ptr())
 
 
 class Swarm:
@@ -403,12 +427,12 @@ class Swarm:
         _check(load().fs_pso_init(self.plan._h, C.byref(self.c), int(seed)))
 
     def evaluate(self, Np: int, edges=None):
-        arr, e = _edges_arg(edges, Np)
+        self._edges_keep, e = _edges_arg(edges, Np, self.x.device, self.plan.stream)
         _check(load().fs_pso_evaluate(self.plan._h, C.byref(self.c), e, int(Np)))
 
     def autotune(self, Np: int, edges=None, reps: int = 3):
         """fs_pso_autotune: pick the plan's fastest variant on the current positions."""
-        arr, e = _edges_arg(edges, Np)
+        self._edges_keep, e = _edges_arg(edges, Np, self.x.device, self.plan.stream)
         v = C.c_int()
         ms = (C.c_float * 8)()
         _check(load().fs_pso_autotune(self.plan._h, C.byref(self.c), e, int(Np), int(reps), C.byref(v), ms))
@@ -437,13 +461,15 @@ class Swarm:
         return self.best_f, self.best_i
 
     def graph_build(self, Np: int, seed: int, edges=None, w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5):
-        """Capture one PSO iteration of this swarm as a CUDA graph (replaces a previous one)."""
-        arr, e = _edges_arg(edges, Np)
+        """Capture one PSO iteration of this swarm as a CUDA graph (replaces a previous one).
+        Edge frequencies are read from device memory each time the graph runs."""
+        keep, e = _edges_arg(edges, Np, self.x.device, self.plan.stream)
         self.graph_free()
         h = C.c_void_p()
         _check(load().fs_pso_graph_build(self.plan._h, C.byref(self.c), e, int(Np), int(seed), float(w0),
                                          float(w1), int(n_iter), float(c1), float(c2), float(vmax), C.byref(h)))
         self._graph = h
+        self._graph_edges = keep
 
     def graph_run(self, n: int):
         _check(load().fs_graph_run(self._graph, int(n)))
@@ -458,7 +484,7 @@ class Swarm:
                        w0=0.9, w1=0.4, n_iter=2, c1=2.0, c2=2.0, vmax=0.5) -> "Graph":
         """Capture part of a PSO iteration (fs_pso_graph_build_ex; parts: 1 evaluate,
         2 record to `ring` (one or a list), 4 step, 8 screened step with `mlp` (one or a list))."""
-        arr, e = _edges_arg(edges, Np)
+        keep, e = _edges_arg(edges, Np, self.x.device, self.plan.stream)
         rings = _ring_array(ring) if ring is not None else None
         mlps = _mlp_array(mlp) if mlp is not None else None
         h = C.c_void_p()
@@ -466,7 +492,7 @@ class Swarm:
                                             float(w1), int(n_iter), float(c1), float(c2), float(vmax), int(parts),
                                             rings, 0 if rings is None else len(rings), mlps,
                                             0 if mlps is None else len(mlps), int(n_cand), C.byref(h)))
-        return Graph(h)
+        return Graph(h, keep)
 
     def graph_free(self):
         g = getattr(self, "_graph", None)
@@ -507,8 +533,9 @@ def mlp_train_graph(nets, rings, steps: int, lr: float = 1e-3) -> "Graph":
 class Graph:
     """A captured part of a PSO iteration or a training round (fs_graph)."""
 
-    def __init__(self, h):
+    def __init__(self, h, keep=None):
         self._h = h
+        self._keep = keep   # device buffers the graph reads when it runs (edge frequencies)
 
     def run(self, n: int = 1):
         _check(load().fs_graph_run(self._h, int(n)))

@@ -114,6 +114,12 @@ class Grid:
     def freqs(self) -> np.ndarray:
         return self.f_min + np.arange(self.n, dtype=np.float64) * self.df
 
+    def edge_freqs(self, starts) -> np.ndarray:
+        """Edge frequencies half a bin below the given start bins, so that the
+        segments between them hold exactly the bins [starts[p], starts[p+1])."""
+        k = np.asarray(starts, dtype=np.float64)
+        return self.f_min + (k - 0.5) * self.df
+
 
 def lisa_like_psd(f: np.ndarray) -> np.ndarray:
     """Smooth analytic LISA-like one-sided noise PSD (strain^2/Hz).

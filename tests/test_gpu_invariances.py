@@ -52,7 +52,7 @@ def run(fst, g, d, psd, P, Np, mode, edges=None):
     plan = fst.Plan.from_grid(g, mode=mode)
     plan.set_data(torch.from_numpy(np.ascontiguousarray(d)).cuda(), torch.from_numpy(np.ascontiguousarray(psd)).cuda())
     Pt = torch.from_numpy(P).cuda()
-    F, Fp = plan.fstat(Pt, Np, edges=edges)
+    F, Fp = plan.fstat(Pt, Np, edges=None if edges is None else g.edge_freqs(edges))
     out = F.cpu().numpy(), Fp.cpu().numpy(), plan.bands(Pt).cpu().numpy()
     plan.close()
     return out

@@ -42,7 +42,8 @@ def rel_err(F, Fref, Np):
 def gpu_F(fst, g, d, psd, P, Np, mode, edges=None, parts=False):
     plan = fst.Plan.from_grid(g, mode=mode)
     plan.set_data(torch.as_tensor(d).cuda(), torch.as_tensor(psd).cuda())
-    F, Fp = plan.fstat(torch.as_tensor(np.ascontiguousarray(P)).cuda(), Np, edges=edges)
+    F, Fp = plan.fstat(torch.as_tensor(np.ascontiguousarray(P)).cuda(), Np,
+                       edges=None if edges is None else g.edge_freqs(edges))
     torch.cuda.synchronize()
     out = (F.cpu().numpy(), Fp.cpu().numpy())
     plan.close()

@@ -45,10 +45,13 @@ def make_data(grid, seed, inj=None, snr=12.0):
     return d, psd
 
 
-def run_gpu(fst, grid, d, psd, P, Np, edges=None, mode=0):
+def run_gpu(fst, grid, d, psd, P, Np, edges=None, mode=0, edges_hz=None):
+    """F and F_part on the GPU; global segments as start bins (edges) or frequencies (edges_hz)."""
     plan = fst.Plan.from_grid(grid, mode=mode)
     plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
-    F, Fp = plan.fstat(torch.from_numpy(np.ascontiguousarray(P)).cuda(), Np, edges=edges)
+    if edges is not None:
+        edges_hz = grid.edge_freqs(edges)
+    F, Fp = plan.fstat(torch.from_numpy(np.ascontiguousarray(P)).cuda(), Np, edges=edges_hz)
     torch.cuda.synchronize()
     out = F.cpu().numpy(), Fp.cpu().numpy()
     plan.close()
@@ -61,8 +64,9 @@ def assert_parity(Fg, Fpg, Fo, Fpo, Np, tol):
     err = np.abs(Fg[ok] - Fo[ok]) / np.maximum(np.abs(Fo[ok]), 2.0 * Np)
     assert np.all(np.isnan(Fg) == np.isnan(Fo))
     assert err.max(initial=0.0) <= tol, f"max rel err {err.max():.3e}"
-    errp = np.abs(Fpg[ok] - Fpo[ok]) / np.maximum(np.abs(Fpo[ok]), 2.0)
-    assert errp.max(initial=0.0) <= tol, f"max per-segment rel err {errp.max():.3e}"
+    if Fpg is not None:
+        errp = np.abs(Fpg[ok] - Fpo[ok]) / np.maximum(np.abs(Fpo[ok]), 2.0)
+        assert errp.max(initial=0.0) <= tol, f"max per-segment rel err {errp.max():.3e}"
     return err.max(initial=0.0)
 
 
@@ -106,6 +110,31 @@ def test_fp64_global_edges_small(fst, edges):
     assert_parity(Fg, Fpg, Fo, Fpo, Np, TOL64)
 
 
+def test_fp64_edge_frequencies_on_bins_and_outside_the_grid(fst):
+    """Edges given as frequencies that sit exactly on bin frequencies (the
+    bin belongs to the segment that starts there; the last edge is closed),
+    below the first bin and above the last one: the device's conversion to
+    bins matches the oracle's membership rule (e_p <= f_k < e_{p+1})."""
+    n = 8192
+    df = 0.01 / (1 << 15)
+    g = S.Grid(f_min=0.015, df=df, n=n, T_obs=1.0 / df)
+    P = S.draw_params(S.Prior(tc_lo=0.0, tc_hi=g.T_obs), 29, 12)
+    d, psd = make_data(g, 3)
+    f = g.freqs()
+    m = O.OracleModel.from_grid(g)
+    cases = [
+        np.array([f[0], f[100], f[100], f[4095], f[8191]]),
+        np.array([g.f_min - 10 * df, f[3] + 0.3 * df, f[7000], g.f_min + (n + 5) * df]),
+        np.array([f[2000], f[2000] + 0.49 * df, f[2001], f[2004]]),
+    ]
+    for e in cases:
+        Np = len(e) - 1
+        starts = O.edge_starts(m, e, Np)
+        Fg, Fpg = run_gpu(fst, g, d, psd, P, Np, edges_hz=e)
+        Fo, Fpo = O.fstat_batch(P, m, d, psd, Np, edges=starts)
+        assert_parity(Fg, Fpg, Fo, Fpo, Np, TOL64)
+
+
 def test_fp64_noise_free_injection_recovers_half_snr2(fst):
     g = S.tiny_grid(n=4096, f_min=0.02, stride=4)
     p = np.array([28.0, tc_for(28.0, 0.02 + 2048 * g.df, 0.5 * g.T_obs), 0.4, 2.0, 0.04, 1.0])
@@ -137,11 +166,26 @@ def test_edge_cases(fst):
     plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
     F, Fp = plan.fstat(torch.zeros(0, 6, dtype=torch.float64, device="cuda"), 4)
     assert F.numel() == 0
-    # invalid arguments are rejected before any launch
-    for bad in (dict(Np=0), dict(Np=5000), dict(Np=2, edges=[5, 3, 9]), dict(Np=1, edges=[0, g.n + 1])):
+    # invalid sizes are rejected before any launch
+    for bad in (dict(Np=0), dict(Np=5000)):
         with pytest.raises(fst.FstatError) as ei:
-            plan.fstat(torch.from_numpy(P).cuda(), bad["Np"], edges=bad.get("edges"))
+            plan.fstat(torch.from_numpy(P).cuda(), bad["Np"])
         assert ei.value.status == fst.FS_EINVAL
+    # edge frequencies live on the device: decreasing or non-finite ones give
+    # NaN for every particle, and fs_plan_check reports them afterwards
+    assert plan.check() == 0
+    f = g.freqs()
+    for bad in ([f[5], f[3], f[9]], [f[5], np.nan, f[9]]):
+        F, Fp = plan.fstat(torch.from_numpy(P).cuda(), 2, edges=bad)
+        assert torch.isnan(F).all() and torch.isnan(Fp).all()
+        with pytest.raises(fst.FstatError) as ei:
+            plan.check()
+        assert ei.value.status == fst.FS_EINVAL
+        assert plan.check() == 0          # the flag is cleared by the check
+    # a valid call after an invalid one is not affected
+    F, _ = plan.fstat(torch.from_numpy(P).cuda(), 2, edges=[f[0], f[1000], f[2999]])
+    Fo, _ = O.fstat_batch(P, O.OracleModel.from_grid(g), d, psd, 2, edges_hz=[f[0], f[1000], f[2999]])
+    assert_parity(F.cpu().numpy(), None, Fo, None, 2, TOL64)
     plan.close()
     with pytest.raises(fst.FstatError):
         fst.Plan(0, 0.01, 1e-6, 1e7)

@@ -130,3 +130,38 @@ def test_evaluate_is_F_hat_and_let_them_fly(fst, plan):
     # the host mapping rounds t_c differently from the device FMA by an ulp,
     # which moves F by ~1e-9; a wrong mapping would move it by O(1)
     assert np.allclose(fit[inside], Fh[inside], rtol=1e-6, atol=0)
+
+
+def test_graph_reads_its_own_edges_after_other_calls(fst, plan):
+    """A captured iteration with global edges A still uses A when it is
+    replayed after an evaluation with edges B (and after another graph with
+    edges B) on the same plan: each evaluation converts its own edge
+    frequencies on the stream, so no captured graph depends on what an
+    earlier call left in the plan."""
+    R, Np, seed = 2, 40, 21
+    g = plan.grid
+    box = unit_box(R)
+    box[:, 1] = [0.3 * g.T_obs, 1.5 * g.T_obs]
+    eA = torch.tensor(g.edge_freqs([0, 1500, 3000, 4500, 6000]), dtype=torch.float64, device="cuda")
+    eB = torch.tensor(g.edge_freqs([100, 200, 5900]), dtype=torch.float64, device="cuda")
+
+    def fresh():
+        sw = fst.Swarm(plan, R, Np, box)
+        with torch.cuda.stream(plan.stream):
+            sw.init(seed)
+        return sw
+
+    eager, graphed, other = fresh(), fresh(), fresh()
+    with torch.cuda.stream(plan.stream):
+        graphed.graph_build(4, seed, edges=eA, n_iter=6)
+        other.graph_build(2, seed, edges=eB, n_iter=6)
+        for it in range(3):
+            eager.evaluate(4, edges=eA)
+            eager.step(seed, -1, n_iter=6)
+            graphed.graph_run(1)
+            other.graph_run(1)
+            other.evaluate(2, edges=eB)       # overwrites the plan's segment starts with B
+    torch.cuda.synchronize()
+    for name in ("x", "v", "pbest_x", "pbest_f", "fit"):
+        assert torch.equal(getattr(eager, name), getattr(graphed, name)), name
+    assert plan.check() == 0

@@ -421,6 +421,39 @@ def test_segment_membership_exact():
         assert list(nb) == list(cnt)
 
 
+def test_global_edge_frequencies_follow_the_membership_rule():
+    """Global edges given as frequencies: the oracle's segment start bins give
+    each bin the segment p with e_p <= f_k < e_{p+1} (the last one closed at
+    e_{N_p}, bins outside [e_0, e_{N_p}] in none), checked bin by bin with the
+    grid's own frequencies: edges on bins, between bins, repeated, and outside
+    the grid; decreasing or non-finite edges are refused."""
+    g = S.Grid(f_min=0.02, df=1.0e-7, n=500, T_obs=1.0e7)
+    m = O.OracleModel.from_grid(g)
+    f = g.freqs()
+    cases = [
+        [f[0], f[100], f[100], f[250], f[499]],
+        [f[0] - 3e-7, f[7] + 0.4e-7, f[300], f[499] + 1e-3],
+        [f[10], f[10] + 0.5e-7, f[11], f[11]],
+        list(g.edge_freqs([0, 17, 17, 300, 500])),
+    ]
+    for e in cases:
+        Np = len(e) - 1
+        starts = O.edge_starts(m, e, Np)
+        seg = np.full(g.n, -1)
+        for k in range(g.n):
+            for p in range(Np):
+                if e[p] <= f[k] < e[p + 1] or (p == Np - 1 and f[k] == e[Np]):
+                    seg[k] = p
+                    break
+        for p in range(Np):
+            assert np.array_equal(np.nonzero(seg == p)[0], np.arange(starts[p], starts[p + 1])), (e, p)
+        assert np.all(seg[:starts[0]] == -1) and np.all(seg[starts[Np]:] == -1)
+    assert list(O.edge_starts(m, cases[3], 4)) == [0, 17, 17, 300, 500]
+    for bad in ([f[5], f[3], f[9]], [f[5], np.nan, f[9]], [f[5], f[6], np.inf]):
+        with pytest.raises(ValueError):
+            O.edge_starts(m, bad, 2)
+
+
 def test_degenerate_segments_give_zero():
     N = np.array([1.0, 2.0, 3.0, 4.0])
     M = np.eye(4)

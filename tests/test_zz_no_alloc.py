@@ -3,12 +3,15 @@ device memory (its workspace is the library's fixed device array).
 
 Two calls in a row, on different grids and segment layouts, must each match
 fs_fstat_batch (the plan-based entry point) to the FP64 parity bar, so a call
-never depends on what the previous call left in the shared workspace.  This
-file is collected last on purpose.
+never depends on what the previous call left in the shared workspace.  Sampled
+particles are also checked against the CPU oracle, a call without F_part
+(per-segment sums in the shared array) and a call at all three limits at once
+against the plan entry point.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2407_10797_gb300 import synth as S
 
 torch = pytest.importorskip("torch")
@@ -33,7 +36,7 @@ def _case(grid, B, seed, Np, global_edges):
     m = P[:, 0] * S.MSUN_S
     f_ref = grid.f_min + 0.5 * grid.n * grid.df
     P[:, 1] += 5.0 / 256.0 * m * (np.pi * m * f_ref) ** (-8.0 / 3.0) * (not global_edges)
-    edges = np.linspace(0, grid.n, Np + 1).astype(np.int64) if global_edges else None
+    edges = grid.edge_freqs(np.linspace(0, grid.n, Np + 1).astype(np.int64)) if global_edges else None
     return (torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda(), torch.from_numpy(P).cuda(), edges)
 
 
@@ -70,6 +73,30 @@ def test_noalloc_matches_plan_entry_point_on_two_calls(fst):
         Fr, Fpr = _with_plan(fst, g, d, psd, P, Np, edges)
         assert _close(F, Fr, Np)
         assert _close(Fp.ravel(), Fpr.ravel(), 1)
+        # a few particles against the oracle, which shares nothing with either entry point
+        idx = np.arange(0, P.shape[0], max(1, P.shape[0] // 6))[:6]
+        Pn = P.cpu().numpy()[idx]
+        Fo, _ = O.fstat_batch(Pn, O.OracleModel.from_grid(g), d.cpu().numpy(),
+                              psd.cpu().numpy(), Np, edges_hz=edges)
+        assert _close(F[idx], Fo, Np)
+
+
+def test_noalloc_without_F_part_and_at_every_limit_at_once(fst):
+    """n_bins = 32768, B = 1024 and N_p = 64 in one call (the largest layout
+    the fixed array holds), with F_part = NULL so that the per-segment values
+    go to the array's own region; then a small call, to see that the second
+    does not depend on the first."""
+    n = 1 << 15
+    df = 0.01 / n
+    g = S.Grid(f_min=0.015, df=df, n=n, T_obs=1.0 / df)
+    g2 = S.tiny_grid(n=5000, f_min=0.02, stride=8)
+    for grid, B, Np, glob, seed in ((g, 1024, 64, True, 6), (g2, 50, 3, False, 7)):
+        d, psd, P, edges = _case(grid, B, seed, Np, glob)
+        F, Fp = fst.fstat_batch_noalloc(grid, d, psd, P, Np, edges=edges)
+        assert Fp is None
+        F = F.cpu().numpy()
+        Fr, _ = _with_plan(fst, grid, d, psd, P, Np, edges)
+        assert _close(F, Fr, Np)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(fst):
