@@ -168,6 +168,33 @@ FS_API fs_status fs_amplitudes(fs_plan* plan, const fs_params* params_dev, int B
 FS_API fs_status fs_add_signal(fs_plan* plan, const fs_params* params_host, const double* a_host,
                         double* data_dev);
 
+/* Precision accounting of the FS_MIXED mode (the segment inner product of
+ * Sec. II.B evaluated with an FP32 body): per-bin values that the mixed kernel
+ * feeds into its sums, for particle b of a batch over the bins
+ * [k0, k0 + nbins), so that each stage can be compared with an FP64
+ * evaluation.  The values come from the production per-bin code (the same
+ * anchors, the same polynomial and fallback evaluation); nothing is summed.
+ *   Arguments as in fs_fstat_batch (the batch fixes the segments and their
+ *   rotated antenna bases); 0 <= b < B; 0 <= k0, k0 + nbins <= n_bins.
+ *   out_dev : nbins records of 28 floats (device):
+ *     [0] tile mode (0 no in-band anchor, 1 FP32 polynomial body, 2 bin-by-bin
+ *         FP64), [1] the tile's anchor bin, [2] segment index,
+ *     [3] fixed-point phase polynomial: orbital phase minus the anchor's
+ *         Doppler phase (cycles, mod 1), [4] orbital-phase offset d(alpha)
+ *         from the anchor (rad), [5] Doppler phase minus its anchor value
+ *         (cycles), [6] the phase fed to sincos (cycles in [-1/2, 1/2]),
+ *     [7] G1, [8] G2 (antenna patterns in the segment's rotated basis
+ *         G1 = c F+ + s Fx, G2 = c Fx - s F+), [9] c, [10] s,
+ *     [11] cos, [12] sin of 2 pi [6] (SFU), [13] Re dw, [14] Im dw, [15] W
+ *         (the FP32 tables, scaled by powers of two), [16..22] the seven
+ *         summed terms G1 zr, G1 zi, G2 zr, G2 zi, W G1^2, W G1 G2, W G2^2
+ *         with z = dw e^{2 pi i ph}, [23] c - [9], [24] s - [10] (the FP64
+ *         rotation's low parts), [25..27] unused.
+ *   Fields a mode does not produce are NaN.  FS_EINVAL unless the plan is
+ *   FS_MIXED.  Asynchronous. */
+FS_API fs_status fs_mixed_probe(fs_plan* plan, const fs_params* params_dev, int B, const double* edges_dev,
+                                int N_p, int b, int64_t k0, int64_t nbins, float* out_dev);
+
 /* Segment outer edges of each particle (Sec. II.B): bands_dev receives
  * 2*B int64 values (first, last) per particle, the first and last bin whose
  * stationary-phase time lies in [0, T_obs]; first > last means no such bin

@@ -524,6 +524,43 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
 }
 }  // namespace
 
+fs_status fs_mixed_probe(fs_plan* p, const fs_params* params_dev, int B, const double* edges_dev, int Np, int b,
+                         int64_t k0, int64_t nbins, float* out_dev) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_mixed_probe: plan is NULL");
+    if (p->mode != FS_MIXED) return fail(FS_EINVAL, "fs_mixed_probe: the plan is not FS_MIXED");
+    if (B < 1 || b < 0 || b >= B) return fail(FS_EINVAL, "fs_mixed_probe: need 0 <= b < B");
+    if (Np < 1 || Np > fs::kNpMax) return fail(FS_EINVAL, "fs_mixed_probe: N_p = %d not in [1, %d]", Np, fs::kNpMax);
+    if (k0 < 0 || nbins < 0 || k0 + nbins > p->grid.n)
+        return fail(FS_EINVAL, "fs_mixed_probe: bins [k0, k0 + nbins) must lie in [0, n_bins)");
+    if (!params_dev || (nbins > 0 && !out_dev)) return fail(FS_EINVAL, "fs_mixed_probe: NULL params or out");
+    if (!p->data_set) return fail(FS_EINVAL, "fs_mixed_probe: fs_plan_set_data was not called");
+    fs_status st = ensure_workspace(p, B, Np);
+    if (st != FS_OK) return st;
+    const int global = edges_dev != nullptr;
+    cudaError_t e;
+    if (global && (e = fs::launch_edges(p->grid, edges_dev, Np, p->edges_dev, p->flags_dev, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "edges launch");
+    fs::Segs sg;
+    sg.Np = Np;
+    sg.global = global;
+    sg.edges = p->edges_dev;
+    fs::Partials pa;
+    pa.H = p->H;
+    pa.T = p->T;
+    pa.S = p->S;
+    pa.rot = p->rot;
+    pa.rot32 = p->rot32;
+    pa.tile = fs::mixed_span();
+    pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
+    if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, global, p->stream)) != cudaSuccess ||
+        (e = fs::launch_rotation(p->grid, p->parts, B, sg, p->rot, p->rot32, p->stream)) != cudaSuccess ||
+        (e = fs::launch_mixed_probe(p->grid, p->tab, p->tab32, p->parts, sg, pa, b, k0, k0 + nbins, out_dev,
+                                    p->stream)) != cudaSuccess)
+        return cuda_fail(e, "probe launch");
+    return FS_OK;
+}
+
 fs_status fs_particle_bands(fs_plan* p, const fs_params* params_dev, int B, int64_t* bands_dev) {
     g_err[0] = 0;
     if (!p || B < 0) return fail(FS_EINVAL, "fs_particle_bands: bad plan or B");

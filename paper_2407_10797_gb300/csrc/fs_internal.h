@@ -92,6 +92,11 @@ cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32,
                               const Segs& sg, const Partials& pa, int variant, int* list, int* cnt,
                               cudaStream_t s);
 int mixed_span();   // bins per H/T slot of the mixed path
+// Per-bin values of the mixed body for particle b over bins [k0, k1): out [k1 - k0][mixed_probe_fields()].
+cudaError_t launch_mixed_probe(const Grid& g, const Tables& t, const float4* t32, const Particle* parts,
+                               const Segs& sg, const Partials& pa, int b, int64_t k0, int64_t k1, float* out,
+                               cudaStream_t s);
+int mixed_probe_fields();
 cudaError_t launch_pso_init(int R, int Np, unsigned long long seed, double* x, double* v, double* pbx, double* pbf,
                             double* fit, int run0, cudaStream_t s);
 cudaError_t launch_pso_map(int R, int Np, const double* x, const double* box, double q, ::fs_params* out,

@@ -12,9 +12,11 @@
 // the antenna patterns are evaluated per bin as polynomials in the offset
 // d(alpha) from the anchor's orbital phase alpha_a (FP32; the antenna
 // patterns' constant terms in FP64), the phase goes through the SFU sincos,
-// and the seven segment sums accumulate in FP32 per lane (per tile, then per
-// span of 32 tiles), are summed across the warp in FP32 and stored as FP64
-// partials that the solve kernel adds in FP64.  A tile whose quartic phase
+// and the seven segment sums accumulate with compensation: each lane sums a
+// tile's bins in FP32 (at most 16 terms per f32x2 half per single-segment
+// piece), folds the tile's sum into a per-lane (sum, error) pair by an exact
+// TwoSum, the pairs are combined across the warp by TwoSum as well, and the
+// result goes to FP64 partials that the solve kernel adds in FP64.  A tile whose quartic phase
 // remainder exceeds 1e-6 cycle, whose t(f) remainder moves alpha by more than
 // 1e-6 rad, or whose |d(alpha)| exceeds 0.06 rad is evaluated bin by bin in
 // FP64 instead, so the mode stays correct on any grid.
@@ -44,6 +46,7 @@ struct Anchor {
 
 // Bin-by-bin FP64 evaluation for tiles where the anchor expansion is not
 // valid; returns the phase mod 1 and the rotated antenna pair (G1, G2).
+// fallback_terms below turns them into the seven terms.
 __device__ __noinline__ void eval_bin_fallback(const Particle& P, const Tables& tb, int64_t k, double alpha0,
                                                double2 cs, float* ph, float* G1, float* G2) {
     FreqPowers fw;
@@ -54,6 +57,26 @@ __device__ __noinline__ void eval_bin_fallback(const Particle& P, const Tables& 
     *ph = (float)ev.frac;
     *G1 = (float)fma(cs.x, ev.Fp, cs.y * ev.Fx);
     *G2 = (float)fma(cs.x, ev.Fx, -cs.y * ev.Fp);
+}
+
+// The seven terms of one bin-by-bin FP64 bin (phase and antenna from
+// eval_bin_fallback, FP32 sincos and products).
+__device__ __forceinline__ void fallback_terms(float ph, float G1, float G2, float4 tw, float t7[7], float* cs_out,
+                                               float* sn_out) {
+    float sn, cs;
+    __sincosf(6.283185307179586f * ph, &sn, &cs);
+    const float zr = fmaf(tw.x, cs, -tw.y * sn);
+    const float zi = fmaf(tw.x, sn, tw.y * cs);
+    t7[0] = G1 * zr;
+    t7[1] = G1 * zi;
+    t7[2] = G2 * zr;
+    t7[3] = G2 * zi;
+    const float wg = tw.z * G1;
+    t7[4] = wg * G1;
+    t7[5] = wg * G2;
+    t7[6] = tw.z * G2 * G2;
+    *cs_out = cs;
+    *sn_out = sn;
 }
 
 __device__ __noinline__ void make_anchor(const Grid& g, const Tables& tb, const Particle& P, int64_t span_lo, int64_t lo,
@@ -196,18 +219,66 @@ __device__ __forceinline__ void segment_coeffs(const Anchor& A, double2 r64, flo
     }
 }
 
-__device__ __forceinline__ float warp_sum_f(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
+// Knuth's TwoSum in FP32: s + e = a + b exactly (round-to-nearest, no
+// overflow).  The explicit _rn intrinsics keep the compiler from reassociating.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
+
+// Compensated accumulation of x into the pair (s, c): s takes the rounded sum,
+// c collects the exact rounding errors.
+__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
+    float t, e;
+    two_sum_f(s, x, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+// Sum of the 32 lanes' (s, c) pairs, compensated at every level of the
+// butterfly; every lane ends with the same value (TwoSum is symmetric).
+__device__ __forceinline__ double warp_sum_comp(float s, float c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        float t, e;
+        two_sum_f(s, s2, t, e);
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, c2), e);
+    }
+    return (double)s + (double)c;
+}
+
+// Per-bin values of the FS_MIXED body that the probe entry point reports (one
+// record of kProbeFields floats per bin; the probe reuses the production code,
+// so the values are those the sums receive).
+enum ProbeField {
+    PR_MODE = 0,     // tile mode: 0 no anchor / out of band, 1 polynomial, 2 bin-by-bin FP64
+    PR_KA,           // anchor bin of the tile (absolute)
+    PR_SEG,          // segment index
+    PR_ORB,          // fixed-point phase polynomial (orbital phase minus the anchor's Doppler phase), cycles
+    PR_DALPHA,       // orbital-phase offset d(alpha) from the anchor, rad
+    PR_DOP,          // Doppler phase minus its anchor value, cycles
+    PR_PH,           // phase fed to the SFU sincos, cycles in [-1/2, 1/2]
+    PR_G1, PR_G2,    // antenna pair in the segment's rotated basis
+    PR_ROTC, PR_ROTS,  // the segment's rotation (c, s)
+    PR_COS, PR_SIN,  // SFU cos / sin of 2 pi ph
+    PR_TX, PR_TY, PR_TW,   // FP32 tables: dw (re, im), W (scaled by powers of two)
+    PR_T0,           // the seven terms G1 zr, G1 zi, G2 zr, G2 zi, W G1^2, W G1 G2, W G2^2 (PR_T0 .. PR_T0 + 6)
+    PR_ROTC_LO = PR_T0 + 7,   // c - (float)c and s - (float)s: the FP64 rotation as two floats each
+    PR_ROTS_LO,
+    kProbeFields = 28
+};
 
 // One bin of a polynomial tile inside a single segment: phase from the
 // fixed-point value Fv, antenna and Doppler from the orbital-phase offset,
 // seven sums into acc.
+template <bool PROBE = false>
 __device__ __forceinline__ void mixed_bin(unsigned long long Fv, float d, float4 tw, float w1, float w2,
                                           const float g1[7], const float g2[7], const float e[5], const float q[4],
-                                          float acc[7]) {
+                                          float acc[7], float* pr = nullptr) {
     const float da = fmaf(w2, d, w1) * d;
     const float G1 =
         fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g1[6], da, g1[5]), da, g1[4]), da, g1[3]), da, g1[2]), da, g1[1]), da, g1[0]);
@@ -221,6 +292,28 @@ __device__ __forceinline__ void mixed_bin(unsigned long long Fv, float d, float4
     __sincosf(6.283185307179586f * ph, &sn, &cs);
     const float zr = fmaf(tw.x, cs, -tw.y * sn);
     const float zi = fmaf(tw.x, sn, tw.y * cs);
+    if (PROBE) {
+        pr[PR_ORB] = (float)(int)(Fv >> 32) * 2.3283064365386963e-10f;
+        pr[PR_DALPHA] = da;
+        pr[PR_DOP] = dop;
+        pr[PR_PH] = ph;
+        pr[PR_G1] = G1;
+        pr[PR_G2] = G2;
+        pr[PR_COS] = cs;
+        pr[PR_SIN] = sn;
+        pr[PR_TX] = tw.x;
+        pr[PR_TY] = tw.y;
+        pr[PR_TW] = tw.z;
+        const float wg = tw.z * G1;
+        pr[PR_T0 + 0] = G1 * zr;
+        pr[PR_T0 + 1] = G1 * zi;
+        pr[PR_T0 + 2] = G2 * zr;
+        pr[PR_T0 + 3] = G2 * zi;
+        pr[PR_T0 + 4] = wg * G1;
+        pr[PR_T0 + 5] = wg * G2;
+        pr[PR_T0 + 6] = tw.z * G2 * G2;
+        return;
+    }
     acc[0] = fmaf(G1, zr, acc[0]);
     acc[1] = fmaf(G1, zi, acc[1]);
     acc[2] = fmaf(G2, zr, acc[2]);
@@ -396,9 +489,11 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
     const float2* rot32 = pa.rot32 + (int64_t)b * sg.Np;
     const float4* tw_span = t32 + span_lo;
 
-    float accS[7], acc[7];
+    // acc: this tile's FP32 sums; (accS, accC): the compensated per-lane sums
+    // of the tiles since the last flush
+    float accS[7], accC[7], acc[7];
 #pragma unroll
-    for (int c = 0; c < 7; c++) accS[c] = 0.f;
+    for (int c = 0; c < 7; c++) accS[c] = accC[c] = 0.f;
     int cur = -1;        // warp-uniform current segment
     int nflush = 0;
     int pk = -1;         // this lane's segment
@@ -425,10 +520,10 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
                     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
 #pragma unroll
                     for (int c = 0; c < 7; c++) {
-                        const float v = warp_sum_f(accS[c] + acc[c]);
-                        if (lane == 0) dst[c] = (double)v;
-                        accS[c] = 0.f;
-                        acc[c] = 0.f;
+                        comp_add(accS[c], accC[c], acc[c]);
+                        const double v = warp_sum_comp(accS[c], accC[c]);
+                        if (lane == 0) dst[c] = v;
+                        accS[c] = accC[c] = acc[c] = 0.f;
                     }
                     nflush++;
                     cur = sp;
@@ -497,20 +592,9 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
                         pk = sv.seg(span_lo + k);
                         nxt = (int)(sv.start(pk + 1) - span_lo);
                     }
-                    float ph, G1, G2;
+                    float ph, G1, G2, cs, sn;
                     eval_bin_fallback(P, tb, span_lo + k, g.alpha0, rot64[pk], &ph, &G1, &G2);
-                    float sn, cs;
-                    __sincosf(6.283185307179586f * ph, &sn, &cs);
-                    const float zr = fmaf(tw.x, cs, -tw.y * sn);
-                    const float zi = fmaf(tw.x, sn, tw.y * cs);
-                    t7[0] = G1 * zr;
-                    t7[1] = G1 * zi;
-                    t7[2] = G2 * zr;
-                    t7[3] = G2 * zi;
-                    const float wg = tw.z * G1;
-                    t7[4] = wg * G1;
-                    t7[5] = wg * G2;
-                    t7[6] = tw.z * G2 * G2;
+                    fallback_terms(ph, G1, G2, tw, t7, &cs, &sn);
                 }
                 while (true) {
                     if (valid && pk == cur) {
@@ -522,10 +606,10 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
                     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
 #pragma unroll
                     for (int c = 0; c < 7; c++) {
-                        const float v = warp_sum_f(accS[c] + acc[c]);
-                        if (lane == 0) dst[c] = (double)v;
-                        accS[c] = 0.f;
-                        acc[c] = 0.f;
+                        comp_add(accS[c], accC[c], acc[c]);
+                        const double v = warp_sum_comp(accS[c], accC[c]);
+                        if (lane == 0) dst[c] = v;
+                        accS[c] = accC[c] = acc[c] = 0.f;
                     }
                     nflush++;
                     int cand = (valid && pk > cur) ? pk : INT_MAX;
@@ -536,14 +620,14 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
             }
         }
 #pragma unroll
-        for (int c = 0; c < 7; c++) accS[c] += acc[c];
+        for (int c = 0; c < 7; c++) comp_add(accS[c], accC[c], acc[c]);
     }
     if (cur < 0) return;   // no in-band bin in this span (warp-uniform)
     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
 #pragma unroll
     for (int c = 0; c < 7; c++) {
-        const float v = warp_sum_f(accS[c]);
-        if (lane == 0) dst[c] = (double)v;
+        const double v = warp_sum_comp(accS[c], accC[c]);
+        if (lane == 0) dst[c] = v;
     }
 }
 
@@ -627,6 +711,92 @@ cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32,
 }
 
 int mixed_span() { return kSpanMix; }
+
+// ---------------------------------------------------------------------------
+// Probe: per-bin values of the FS_MIXED body for one particle over the bins
+// [k0, k1), one warp per span of 32768 bins.  Phase A is the production
+// anchor computation (same tiles, same band clipping); phase B evaluates each
+// requested bin with the production per-bin code (mixed_bin with the probe
+// record, or the bin-by-bin FP64 fallback), the fixed-point phase taken from
+// the anchor polynomial directly (integer arithmetic: the same value the
+// forward differences reach).  Nothing is accumulated.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32, 1)
+mixed_probe_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts, Segs sg,
+                   Partials pa, int b, int64_t k0, int64_t k1, float* __restrict__ out) {
+    __shared__ Anchor anc[kTilesPerSpan];
+    const int lane = threadIdx.x;
+    const int64_t span = k0 / kSpanMix + blockIdx.x;
+    const int64_t span_lo = span * kSpanMix;
+    const Particle& P = parts[b];
+    const SegView sv = seg_view(sg, P);
+    const bool live = P.valid && sv.lo <= sv.hi;
+    {
+        int64_t lo = span_lo + (int64_t)lane * kTileMix, hi = lo + kTileMix;
+        if (lo < sv.lo) lo = sv.lo;
+        if (hi > sv.hi + 1) hi = sv.hi + 1;
+        if (!live) hi = lo;
+        make_anchor(g, tb, P, span_lo, lo, hi, anc[lane]);
+    }
+    __syncwarp();
+    const double2* rot64 = pa.rot + (int64_t)b * sg.Np;
+    const float2* rot32 = pa.rot32 + (int64_t)b * sg.Np;
+    int64_t a = span_lo > k0 ? span_lo : k0;
+    int64_t e = span_lo + kSpanMix < k1 ? span_lo + kSpanMix : k1;
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int64_t k = a + lane; k < e; k += 32) {
+        float* pr = out + (k - k0) * kProbeFields;
+#pragma unroll 1
+        for (int f = 0; f < kProbeFields; f++) pr[f] = qnan;
+        const Anchor& A = anc[(k - span_lo) / kTileMix];
+        const int rel = (int)(k - span_lo);
+        if (A.mode == 0 || rel < A.lo || rel >= A.hi) {
+            pr[PR_MODE] = 0.f;
+            continue;
+        }
+        const int sp = sv.seg(k);
+        pr[PR_MODE] = (float)A.mode;
+        pr[PR_KA] = (float)(span_lo + A.ja);
+        pr[PR_SEG] = (float)sp;
+        pr[PR_ROTC] = (float)rot64[sp].x;
+        pr[PR_ROTS] = (float)rot64[sp].y;
+        pr[PR_ROTC_LO] = (float)(rot64[sp].x - (double)(float)rot64[sp].x);
+        pr[PR_ROTS_LO] = (float)(rot64[sp].y - (double)(float)rot64[sp].y);
+        const float4 tw = t32[k];
+        if (A.mode == 1) {
+            float g1[7], g2[7], acc[7];
+            segment_coeffs(A, rot64[sp], rot32[sp], g1, g2);
+            const float e5[5] = {A.e[0], A.e[1], A.e[2], A.e[3], A.e[4]};
+            const float q4[4] = {A.q[0], A.q[1], A.q[2], A.q[3]};
+            const long long d = (long long)(rel - A.ja);
+            mixed_bin<true>(poly_fx(A.c, d), (float)d, tw, A.w1, A.w2, g1, g2, e5, q4, acc, pr);
+        } else {
+            float ph, G1, G2, cs, sn, t7[7];
+            eval_bin_fallback(P, tb, k, g.alpha0, rot64[sp], &ph, &G1, &G2);
+            fallback_terms(ph, G1, G2, tw, t7, &cs, &sn);
+            pr[PR_PH] = ph;
+            pr[PR_G1] = G1;
+            pr[PR_G2] = G2;
+            pr[PR_COS] = cs;
+            pr[PR_SIN] = sn;
+            pr[PR_TX] = tw.x;
+            pr[PR_TY] = tw.y;
+            pr[PR_TW] = tw.z;
+            for (int c = 0; c < 7; c++) pr[PR_T0 + c] = t7[c];
+        }
+    }
+}
+
+cudaError_t launch_mixed_probe(const Grid& g, const Tables& t, const float4* t32, const Particle* parts,
+                               const Segs& sg, const Partials& pa, int b, int64_t k0, int64_t k1, float* out,
+                               cudaStream_t s) {
+    if (k1 <= k0) return cudaSuccess;
+    const int64_t nspans = (k1 - 1) / kSpanMix - k0 / kSpanMix + 1;
+    mixed_probe_kernel<<<(unsigned)nspans, 32, 0, s>>>(g, t, t32, parts, sg, pa, b, k0, k1, out);
+    return cudaGetLastError();
+}
+
+int mixed_probe_fields() { return kProbeFields; }
 
 // ---------------------------------------------------------------------------
 // FP32 tables of the mixed path: (dw_re, dw_im, W) scaled by powers of two so

@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_add_signal.argtypes = [_vp, C.POINTER(fs_params), _dp, _vp]
         L.fs_constants.argtypes = [_dp]
         L.fs_particle_bands.argtypes = [_vp, _vp, C.c_int, _vp]
+        L.fs_mixed_probe.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int64, C.c_int64, _vp]
         L.fs_fstat_batch_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp,
                                              C.c_int, _vp, C.c_int, _vp, _vp, _vp]
         L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
@@ -117,7 +118,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_last_error.restype = C.c_char_p
         for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_check", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_amplitudes", "fs_add_signal", "fs_constants", "fs_particle_bands",
-                     "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc",
+                     "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc", "fs_mixed_probe",
                      "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
                      "fs_plan_autotune", "fs_pso_autotune", "fs_plan_census", "fs_pso_init", "fs_pso_evaluate", "fs_pso_step", "fs_pso_best",
                      "fs_pso_graph_build", "fs_pso_graph_build_ex", "fs_pso_record", "fs_mlp_train_graph_build",
@@ -271,6 +272,23 @@ class Plan:
         _check_size(out, 2 * B, "out")
         _check(self._L.fs_particle_bands(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(B),
                                          _cuda_ptr(out, torch.int64)))
+        return out
+
+    PROBE_FIELDS = ("mode", "k_anchor", "seg", "orb", "dalpha", "dop", "ph", "G1", "G2", "rot_c", "rot_s",
+                    "cos", "sin", "tw_re", "tw_im", "tw_W", "t0", "t1", "t2", "t3", "t4", "t5", "t6", "rot_c_lo",
+                    "rot_s_lo", "unused0", "unused1", "unused2")
+
+    def mixed_probe(self, params, Np: int, b: int, k0: int, nbins: int, edges=None):
+        """fs_mixed_probe: per-bin values of the FS_MIXED body for particle b over
+        bins [k0, k0 + nbins); float32 CUDA tensor [nbins, 28] (PROBE_FIELDS)."""
+        import torch
+        if params.dim() != 2 or params.shape[1] != 6:
+            raise ValueError("params must be [B, 6]")
+        out = torch.empty(int(nbins), len(self.PROBE_FIELDS), dtype=torch.float32, device=params.device)
+        self._edges_keep, e = _edges_arg(edges, Np, params.device, self.stream)
+        _check(self._L.fs_mixed_probe(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
+                                      e, int(Np), int(b), int(k0), int(nbins),
+                                      _cuda_ptr(out, torch.float32) if nbins > 0 else None))
         return out
 
     KERNELS = {"setup": 0, "main": 1, "reduce": 2, "precompute": 3}
