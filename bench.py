@@ -521,7 +521,7 @@ def run_gpu(args, world, rank, local):
 
     # ---- mixed mode on the same data and particles
     runm = ModeRun(fstat, fstat.FS_MIXED, g, d_dev, psd_dev, box, stream, seed,
-                   variant=None if args.variant is None else min(args.variant, 3))
+                   variant=None if args.variant is None else min(args.variant, 4))
     censusm = runm.census(P0_dev)
     ms_m, prof_m, clocks_m = time_run(args, world, runm)
     value_m = total_pbins / (ms_m / 1e3)

@@ -66,6 +66,17 @@ typedef enum {
     FS_MIXED = 1   /* FP64 anchors + exact fixed-point phase steps, FP32 response and products */
 } fs_precision;
 
+/* TDI channels of the data (Sec. II.A, Eq. eq2: the log-likelihood, and with
+ * it N and M of every segment, sums over the channels).  In the
+ * long-wavelength response of Sec. IV (N = 0) the Michelson combinations X,
+ * Y, Z with vertices at the three spacecraft give A = (Z - X)/sqrt2 and
+ * E = (X - 2Y + Z)/sqrt6 (noise-orthogonal; T = (X + Y + Z)/sqrt3 vanishes
+ * identically in this limit and is not offered). */
+typedef enum {
+    FS_TDI_X = 0,   /* one channel: X (the paper's choice) */
+    FS_TDI_AE = 1   /* two channels: A, then E */
+} fs_tdi;
+
 /* Intrinsic parameters of one particle (Sec. II.A, Theta_I without delta_mu;
  * the mass ratio q = m1/m2 >= 1 fixes eta = q/(1+q)^2). */
 typedef struct {
@@ -88,12 +99,24 @@ typedef struct fs_plan fs_plan;
 FS_API fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df, double T_obs,
                          int mode, void* stream);
 
+/* fs_plan_create for data in the TDI channels `tdi` (an fs_tdi): every
+ * per-bin input (data, PSD) then holds one array per channel, channel after
+ * channel, and every F is the sum over the channels' inner products.
+ * fs_plan_create is the case FS_TDI_X.  Synchronous. */
+FS_API fs_status fs_plan_create_tdi(fs_plan** out, int64_t n_bins, double f_min, double df, double T_obs,
+                                    int mode, int tdi, void* stream);
+
+/* Number of channels of a plan (1 for FS_TDI_X, 2 for FS_TDI_AE), -1 for NULL. */
+FS_API int fs_plan_channels(const fs_plan* plan);
+
 /* Free a plan and its workspace (waits for the plan's stream).  NULL is a no-op. */
 FS_API fs_status fs_plan_destroy(fs_plan* plan);
 
 /* Load one data set (Sec. II.A, Eq. inner_product: the noise-weighted inner
  * product on the frequency grid).  data_dev: n_bins complex values as
- * interleaved FP64 (re, im); psd_dev: n_bins one-sided PSD values S_k > 0;
+ * interleaved FP64 (re, im) per channel; psd_dev: n_bins one-sided PSD
+ * values S_k > 0 per channel (channels one after the other, in the order of
+ * the plan's fs_tdi);
  * f_grid_dev: NULL for the plan's grid f_k = f_min + k df, or the n_bins
  * frequencies of the data (device, FP64), which must equal that grid to 4 units
  * in the last place: the kernels step the template phase in the bin index, so
@@ -137,8 +160,10 @@ FS_API fs_status fs_fstat_batch(fs_plan* plan, const fs_params* params_dev, int 
 
 /* Errors the device found in earlier calls on this plan: waits for the plan's
  * stream, writes the flag bits seen since the last check to *flags_out (may be
- * NULL; bit 0: partition edges that were not finite or decreased) and clears
- * them.  Returns FS_EINVAL with a message when bit 0 was set, FS_OK otherwise. */
+ * NULL; bit 0: partition edges that were not finite or decreased; bit 2: a
+ * bounded device-side wait ran out, so that call's F values are invalid) and
+ * clears them.  Returns FS_ETIMEOUT when bit 2 was set, else FS_EINVAL when
+ * bit 0 was set, FS_OK otherwise. */
 FS_API fs_status fs_plan_check(fs_plan* plan, int* flags_out);
 
 /* Maximum-likelihood amplitudes and extrinsic parameters (Eq. aandMN3 and
@@ -160,8 +185,10 @@ FS_API fs_status fs_amplitudes(fs_plan* plan, const fs_params* params_dev, int B
                                int N_p, double* F_dev, double* a_dev, double* ext_dev);
 
 /* Add the signal h = sum_i a_i A^i of one particle to data_dev (n_bins
- * interleaved complex FP64, device) at the bins of the particle's band
- * [first, last bin with t(f_k) in [0, T_obs]]; the other bins are untouched.
+ * interleaved complex FP64 per channel, device, as for fs_plan_set_data; each
+ * channel receives the signal through its own response) at the bins of the
+ * particle's band [first, last bin with t(f_k) in [0, T_obs]]; the other bins
+ * are untouched.
  * The basis is A1 = F+ h0, A2 = Fx h0, A3 = -i F+ h0, A4 = -i Fx h0 with
  * h0 = f^-7/6 exp(-i Psi(f)) (Appendix A with the Sec. IV response); a_host
  * holds the four amplitudes of Eq. (response).  Evaluated in FP64. */
@@ -191,7 +218,8 @@ FS_API fs_status fs_add_signal(fs_plan* plan, const fs_params* params_host, cons
  *         with z = dw e^{2 pi i ph}, [23] c - [9], [24] s - [10] (the FP64
  *         rotation's low parts), [25..27] unused.
  *   Fields a mode does not produce are NaN.  FS_EINVAL unless the plan is
- *   FS_MIXED.  Asynchronous. */
+ *   FS_MIXED.  With several channels the values are channel 0's.
+ *   Asynchronous. */
 FS_API fs_status fs_mixed_probe(fs_plan* plan, const fs_params* params_dev, int B, const double* edges_dev,
                                 int N_p, int b, int64_t k0, int64_t nbins, float* out_dev);
 
@@ -415,8 +443,11 @@ FS_API fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_s
  *             CTAs per SM; 1 = the same with 3 CTAs per SM; 2 = persistent
  *             kernel (one grid of SMs x resident CTAs whose warps take
  *             (span, particle) items from a device-side counter), 2 CTAs per
- *             SM; 3 = persistent, 3 CTAs per SM.  F is bit-identical across
- *             the four.
+ *             SM; 3 = persistent, 3 CTAs per SM; 4 = the CTA form of 0 with
+ *             each 1024-bin tile of the FP32 tables copied once per CTA into
+ *             shared memory by a bulk asynchronous copy and read by all 8
+ *             warps (bounded waits: a wait that runs out is reported by
+ *             fs_plan_check).  F is bit-identical across the five.
  * Which variant a call uses: the forced one if fs_plan_set_variant gave one
  * (>= 0), else the one recorded for (N_p, edge kind) by fs_plan_autotune,
  * fs_pso_autotune or fs_plan_set_variant_for, else the mode's default
@@ -451,7 +482,7 @@ FS_API fs_status fs_plan_census(fs_plan* plan, const fs_params* params_dev, int 
  * calls between CUDA events on the plan's stream, 1 <= reps <= 1000), record
  * the fastest for (N_p, edge kind) and return it in *variant_out (may be
  * NULL); ms_out (may be NULL) receives the mean ms per call of each variant
- * (4 entries in FS_MIXED, 5 in FS_FP64).  Synchronous; FS_EINVAL while the
+ * (5 entries in either mode).  Synchronous; FS_EINVAL while the
  * plan's stream is being captured.  Arguments as in fs_fstat_batch; the F
  * values computed go to plan scratch, not to the caller. */
 FS_API fs_status fs_plan_autotune(fs_plan* plan, const fs_params* params_dev, int B, const double* edges_dev,

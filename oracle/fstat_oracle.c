@@ -23,6 +23,8 @@
  *   t(f)                     Sec. IV, stationary-phase time t_f = (1/2pi) dPhi/df
  *   PSO update               Sec. III.A, Eqs. (pso_position_update), (pso_velocity_update)
  *   extrinsic parameters     Appendix B, Eqs. (B1)-(B3)
+ *   several TDI channels     Sec. II.A, Eq. (eq2): the log-likelihood sums over the
+ *                            combinations I, so N and M of a segment are sums over channels
  *
  * Readings of points the paper leaves open:
  *   - PN coefficients alpha_k: non-spinning TaylorF2 through 2PN (k <= 4).
@@ -40,6 +42,11 @@
  *   - the Gram sums and the 4x4 solve are carried in long double (see
  *     or_segment_sums_ld: short segments make M nearly singular).
  *   - the library returns the SUM over segments; F-hat = sum / N_seg.
+ *   - TDI channels in the long-wavelength limit: X is the Michelson with its
+ *     vertex at spacecraft 0, Y and Z those with vertices at spacecraft 1 and
+ *     2 (arms to the next two spacecraft in cyclic order); A = (Z - X)/sqrt2,
+ *     E = (X - 2Y + Z)/sqrt6 and T = (X + Y + Z)/sqrt3 as combinations of their
+ *     detector tensors.  T vanishes identically in this limit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -74,6 +81,7 @@ typedef struct {
     int pn_order; /* highest k kept in sum_k alpha_k x^(k/2), 0..4 */
     double alpha0; /* orbital phase of the guiding centre at t = 0, rad */
     double orient; /* orientation of the constellation at t = 0, rad */
+    int channel;   /* TDI channel: 0 X, 1 A, 2 E, 3 T */
 } or_model;
 
 /* ---- masses and PN coefficients (Appendix A) --------------------------- */
@@ -150,13 +158,13 @@ static void or_sc_offset(const or_model* m, int n, double alpha, double r[3]) {
 }
 
 /* Detector tensor D = (a a - b b)/2 of the long-wavelength Michelson with
- * vertex at spacecraft 0 (a, b: unit vectors along its two arms) at time t. */
-static void or_detector(const or_model* m, double t, double D[3][3]) {
-    double alpha = or_orbit_phase(m, t);
+ * vertex at spacecraft v (a, b: unit vectors along its arms to spacecraft
+ * v+1 and v+2, cyclic) at orbital phase alpha. */
+static void or_vertex_detector(const or_model* m, int v, double alpha, double D[3][3]) {
     double r0[3], r1[3], r2[3], a[3], b[3];
-    or_sc_offset(m, 0, alpha, r0);
-    or_sc_offset(m, 1, alpha, r1);
-    or_sc_offset(m, 2, alpha, r2);
+    or_sc_offset(m, v, alpha, r0);
+    or_sc_offset(m, (v + 1) % 3, alpha, r1);
+    or_sc_offset(m, (v + 2) % 3, alpha, r2);
     double na = 0.0, nb = 0.0;
     for (int i = 0; i < 3; i++) {
         a[i] = r1[i] - r0[i];
@@ -172,6 +180,26 @@ static void or_detector(const or_model* m, double t, double D[3][3]) {
     }
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) D[i][j] = 0.5 * (a[i] * a[j] - b[i] * b[j]);
+}
+
+/* Detector tensor of the model's TDI channel at time t: X itself, or the
+ * combinations A, E, T of the three vertex Michelsons X, Y, Z. */
+static void or_detector(const or_model* m, double t, double D[3][3]) {
+    double alpha = or_orbit_phase(m, t);
+    if (m->channel == 0) {
+        or_vertex_detector(m, 0, alpha, D);
+        return;
+    }
+    double X[3][3], Y[3][3], Z[3][3];
+    or_vertex_detector(m, 0, alpha, X);
+    or_vertex_detector(m, 1, alpha, Y);
+    or_vertex_detector(m, 2, alpha, Z);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            if (m->channel == 1) D[i][j] = (Z[i][j] - X[i][j]) / sqrt(2.0);
+            else if (m->channel == 2) D[i][j] = (X[i][j] - 2.0 * Y[i][j] + Z[i][j]) / sqrt(6.0);
+            else D[i][j] = (X[i][j] + Y[i][j] + Z[i][j]) / sqrt(3.0);
+        }
 }
 
 /* F+ and Fx of the long-wavelength Michelson with vertex at spacecraft 0:
@@ -476,6 +504,56 @@ int or_fstat_batch(const or_params* params, int B, const or_model* m, const doub
         F[b] = (double)tot;
         free(Nb);
         free(Mb);
+        free(nb);
+    }
+    return 0;
+}
+
+/* The same for data in several TDI channels (Sec. II.A, Eq. eq2): models[c]
+ * fixes channel c's response (its `channel` field; grid and orbit shared),
+ * d_re, d_im, psd hold nch arrays of n values one after the other, and N, M
+ * of each segment are summed over the channels before the 4x4 solve. */
+int or_fstat_batch_multi(const or_params* params, int B, const or_model* models, int nch, const double* d_re,
+                         const double* d_im, const double* psd, const int64_t* edges, int Np, double* F,
+                         double* Fpart, int nthreads) {
+    if (B < 0 || Np < 1 || nch < 1 || !models || models[0].n < 1) return -1;
+    const int64_t n = models[0].n;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < B; b++) {
+        const or_params* P = params + b;
+        long double* Nb = (long double*)malloc(sizeof(long double) * 4 * Np);
+        long double* Mb = (long double*)malloc(sizeof(long double) * 16 * Np);
+        long double* Nc = (long double*)malloc(sizeof(long double) * 4 * Np);
+        long double* Mc = (long double*)malloc(sizeof(long double) * 16 * Np);
+        int64_t* nb = (int64_t*)malloc(sizeof(int64_t) * Np);
+        long double tot = 0.0L;
+        if (!or_params_finite(P)) {
+            tot = NAN;
+            if (Fpart)
+                for (int p = 0; p < Np; p++) Fpart[(int64_t)b * Np + p] = NAN;
+        } else {
+            for (int i = 0; i < 4 * Np; i++) Nb[i] = 0.0L;
+            for (int i = 0; i < 16 * Np; i++) Mb[i] = 0.0L;
+            for (int c = 0; c < nch; c++) {
+                or_segment_sums_ld(P, models + c, d_re + (int64_t)c * n, d_im + (int64_t)c * n, psd + (int64_t)c * n,
+                                   edges, Np, Nc, Mc, nb);
+                for (int i = 0; i < 4 * Np; i++) Nb[i] += Nc[i];
+                for (int i = 0; i < 16 * Np; i++) Mb[i] += Mc[i];
+            }
+            for (int p = 0; p < Np; p++) {
+                long double Fp = or_segment_F_ld(Nb + 4 * p, Mb + 16 * p, nb[p]);
+                if (Fpart) Fpart[(int64_t)b * Np + p] = (double)Fp;
+                tot += Fp;
+            }
+        }
+        F[b] = (double)tot;
+        free(Nb);
+        free(Mb);
+        free(Nc);
+        free(Mc);
         free(nb);
     }
     return 0;

@@ -44,7 +44,7 @@ class Params(C.Structure):
 class Model(C.Structure):
     _fields_ = [("f_min", C.c_double), ("df", C.c_double), ("T_obs", C.c_double),
                 ("n", C.c_int64), ("response", C.c_int), ("pn_order", C.c_int),
-                ("alpha0", C.c_double), ("orient", C.c_double)]
+                ("alpha0", C.c_double), ("orient", C.c_double), ("channel", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -59,6 +59,9 @@ def lib():
             L.or_fstat_batch.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(Model), _dp, _dp, _dp,
                                          _i64p, C.c_int, _dp, _dp, C.c_int]
             L.or_fstat_batch.restype = C.c_int
+            L.or_fstat_batch_multi.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(Model), C.c_int, _dp, _dp, _dp,
+                                               _i64p, C.c_int, _dp, _dp, C.c_int]
+            L.or_fstat_batch_multi.restype = C.c_int
             L.or_segment_sums.argtypes = [C.POINTER(Params), C.POINTER(Model), _dp, _dp, _dp, _i64p,
                                           C.c_int, _dp, _dp, _i64p]
             L.or_edge_starts.argtypes = [C.POINTER(Model), _dp, C.c_int, _i64p]
@@ -107,6 +110,7 @@ class OracleModel:
     pn_order: int = 4
     alpha0: float = 0.0
     orient: float = 0.0
+    channel: int = 0       # TDI channel: 0 X, 1 A, 2 E, 3 T
 
     @staticmethod
     def from_grid(grid, **kw) -> "OracleModel":
@@ -114,7 +118,7 @@ class OracleModel:
 
     def c(self) -> Model:
         return Model(self.f_min, self.df, self.T_obs, self.n, self.response, self.pn_order,
-                     self.alpha0, self.orient)
+                     self.alpha0, self.orient, self.channel)
 
 
 def _params(p) -> Params:
@@ -161,6 +165,30 @@ def fstat_batch(params: np.ndarray, model: OracleModel, data: np.ndarray, psd: n
                               int(nthreads))
     if rc != 0:
         raise ValueError("or_fstat_batch rejected its arguments")
+    return F, Fp
+
+
+def fstat_batch_channels(params: np.ndarray, models, data: np.ndarray, psd: np.ndarray, Np: int,
+                         edges: np.ndarray | None = None, nthreads: int = 0, edges_hz=None):
+    """F and Fpart for data in several TDI channels: models[c] (same grid, its
+    own `channel`), data [nch, n] complex, psd [nch, n]."""
+    models = list(models)
+    nch = len(models)
+    if edges_hz is not None:
+        edges = edge_starts(models[0], edges_hz, Np)
+    data = np.asarray(data).reshape(nch, -1)
+    psd = np.ascontiguousarray(np.asarray(psd, dtype=np.float64).reshape(nch, -1))
+    d_re = np.ascontiguousarray(data.real, dtype=np.float64)
+    d_im = np.ascontiguousarray(data.imag, dtype=np.float64)
+    B = len(params)
+    F = np.zeros(B)
+    Fp = np.zeros((B, Np))
+    e = None if edges is None else np.ascontiguousarray(edges, dtype=np.int64)
+    ms = (Model * nch)(*[m.c() for m in models])
+    rc = lib().or_fstat_batch_multi(_params_array(params), B, ms, nch, _ptr(d_re), _ptr(d_im), _ptr(psd),
+                                    None if e is None else _ptr(e, C.c_int64), Np, _ptr(F), _ptr(Fp), int(nthreads))
+    if rc != 0:
+        raise ValueError("or_fstat_batch_multi rejected its arguments")
     return F, Fp
 
 

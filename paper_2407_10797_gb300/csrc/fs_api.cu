@@ -47,7 +47,9 @@ struct fs_plan {
     int mode;
     int device;
     cudaStream_t stream;
-    fs::Tables tab;
+    int tdi;                          // FS_TDI_X or FS_TDI_AE
+    int nch;                          // channels of the data (1 or 2)
+    fs::Tables tab[fs::kMaxChannels]; // per channel: shared frequency tables, the channel's dw and W
     double* tab_base;
     int data_set;
     // workspace
@@ -60,7 +62,7 @@ struct fs_plan {
     double2* rot;
     float2* rot32;
     int ntiles;
-    // mixed mode: FP32 (dw, W) tables and the scale exponent
+    // mixed mode: FP32 (dw, W) tables [nch][n] and their common scale exponent
     float4* tab32;
     int* emax;
     // launch variant of the fused kernel: forced (>= 0) or looked up per
@@ -110,10 +112,20 @@ constexpr int kKinds = 4;
 // Launch variants of the fused kernel.  FS_FP64: direct form with a tile of
 // 2048, 1024 or 4096 bins per (particle, tile) item, anchored form (grid or
 // persistent).  FS_MIXED: grid form with 2 or 3 resident CTAs per SM,
-// persistent form with 2 or 3.
-int n_variants(int mode) { return mode == FS_MIXED ? 4 : 5; }
+// persistent form with 2 or 3, grid form with the tables staged through
+// shared memory by bulk copies.
+int n_variants(int mode) { return 5; }
 
 int fp64_tile(int variant) { return variant == 1 ? 1024 : variant == 2 ? 4096 : fs::kTile; }
+
+// The grid as channel c of the plan's channel set sees it (orientation and projection scale).
+fs::Grid channel_grid(const fs_plan* p, int c) {
+    fs::Grid g = p->grid;
+    const fs::Channel ch = fs::channel_of(p->tdi, c);
+    g.orient += ch.orient_shift;
+    g.pscale = ch.pscale;
+    return g;
+}
 
 // Untuned default: the anchored persistent form (FS_FP64), the persistent
 // form with 3 CTAs per SM (FS_MIXED).
@@ -200,10 +212,11 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     free_workspace(p);
     size_t nt = (size_t)p->ntiles;
-    if ((e = cudaMalloc(&p->parts, sizeof(fs::Particle) * nb)) != cudaSuccess ||
-        (e = cudaMalloc(&p->H, sizeof(double) * 7 * nt * nb)) != cudaSuccess ||
-        (e = cudaMalloc(&p->T, sizeof(double) * 7 * nt * nb)) != cudaSuccess ||
-        (e = cudaMalloc(&p->S, sizeof(double) * 7 * (size_t)nn * nb)) != cudaSuccess ||
+    const size_t nc = (size_t)p->nch;
+    if ((e = cudaMalloc(&p->parts, sizeof(fs::Particle) * nb * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->H, sizeof(double) * 7 * nt * nb * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->T, sizeof(double) * 7 * nt * nb * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->S, sizeof(double) * 7 * (size_t)nn * nb * nc)) != cudaSuccess ||
         (e = cudaMalloc(&p->Fpart, sizeof(double) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess ||
@@ -261,8 +274,16 @@ fs_status fs_constants(double* out) {
 
 fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df, double T_obs, int mode,
                          void* stream) {
+    return fs_plan_create_tdi(out, n_bins, f_min, df, T_obs, mode, FS_TDI_X, stream);
+}
+
+int fs_plan_channels(const fs_plan* p) { return p ? p->nch : -1; }
+
+fs_status fs_plan_create_tdi(fs_plan** out, int64_t n_bins, double f_min, double df, double T_obs, int mode,
+                             int tdi, void* stream) {
     g_err[0] = 0;
     if (!out) return fail(FS_EINVAL, "fs_plan_create: out is NULL");
+    if (tdi != FS_TDI_X && tdi != FS_TDI_AE) return fail(FS_EINVAL, "fs_plan_create_tdi: unknown channel set %d", tdi);
     *out = nullptr;
     if (n_bins <= 0 || !(f_min > 0.0) || !(df > 0.0) || !(T_obs > 0.0) || !isfinite(f_min) || !isfinite(df) ||
         !isfinite(T_obs))
@@ -280,6 +301,9 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
     p->grid.T_obs = T_obs;
     p->grid.alpha0 = 0.0;
     p->grid.orient = 0.0;
+    p->grid.pscale = 1.0;
+    p->tdi = tdi;
+    p->nch = tdi == FS_TDI_AE ? 2 : 1;
     p->mode = mode;
     p->stream = (cudaStream_t)stream;
     p->ntiles = (int)((n_bins + fs::kTileMin - 1) / fs::kTileMin);
@@ -290,15 +314,21 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
         delete p;
         return cuda_fail(e, "cudaGetDevice");
     }
-    size_t bytes = sizeof(double) * (size_t)n_bins * fs::kNumTables;
+    // six frequency tables shared by the channels, then (dw re, dw im, W) per channel
+    size_t bytes = sizeof(double) * (size_t)n_bins * (6 + 3 * (size_t)p->nch);
     if ((e = cudaMalloc(&p->tab_base, bytes)) != cudaSuccess) {
         delete p;
         return cuda_fail(e, "cudaMalloc(tables)");
     }
     double* q = p->tab_base;
-    double** slots[fs::kNumTables] = {&p->tab.fh, &p->tab.fl, &p->tab.u, &p->tab.g0h, &p->tab.g0l,
-                                      &p->tab.e19, &p->tab.dwr, &p->tab.dwi, &p->tab.W};
-    for (int i = 0; i < fs::kNumTables; i++) *slots[i] = q + (size_t)i * n_bins;
+    for (int c = 0; c < p->nch; c++) {
+        fs::Tables& t = p->tab[c];
+        double** slots[fs::kNumTables] = {&t.fh, &t.fl, &t.u, &t.g0h, &t.g0l, &t.e19, &t.dwr, &t.dwi, &t.W};
+        for (int i = 0; i < fs::kNumTables; i++) {
+            const size_t slot = i < 6 ? (size_t)i : 6 + 3 * (size_t)c + (i - 6);
+            *slots[i] = q + slot * n_bins;
+        }
+    }
     if ((e = cudaMalloc(&p->edges_dev, sizeof(int64_t) * (fs::kNpMax + 2))) != cudaSuccess ||
         (e = cudaMalloc(&p->flags_dev, sizeof(int))) != cudaSuccess ||
         (e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
@@ -309,7 +339,7 @@ fs_status fs_plan_create(fs_plan** out, int64_t n_bins, double f_min, double df,
         return cuda_fail(e, "cudaMalloc(plan)");
     }
     if (mode == FS_MIXED &&
-        ((e = cudaMalloc(&p->tab32, sizeof(float4) * (size_t)n_bins)) != cudaSuccess ||
+        ((e = cudaMalloc(&p->tab32, sizeof(float4) * (size_t)n_bins * p->nch)) != cudaSuccess ||
          (e = cudaMalloc(&p->emax, sizeof(int))) != cudaSuccess)) {
         fs_plan_destroy(p);
         return cuda_fail(e, "cudaMalloc(mixed tables)");
@@ -373,9 +403,13 @@ fs_status fs_plan_set_data(fs_plan* p, const double* data_dev, const double* psd
                         "non-uniform grids are not supported");
     }
     ProfScope ps(p, 3);
-    cudaError_t e = fs::launch_precompute(p->grid, data_dev, psd_dev, p->tab, p->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
-    if (p->mode == FS_MIXED && (e = fs::launch_tables32(p->grid, p->tab, p->emax, p->tab32, p->stream)) != cudaSuccess)
+    cudaError_t e;
+    for (int c = 0; c < p->nch; c++)   // channel c's data and PSD follow channel c - 1's
+        if ((e = fs::launch_precompute(p->grid, data_dev + (size_t)2 * p->grid.n * c, psd_dev + (size_t)p->grid.n * c,
+                                       p->tab[c], p->stream)) != cudaSuccess)
+            return cuda_fail(e, "precompute launch");
+    if (p->mode == FS_MIXED &&
+        (e = fs::launch_tables32(p->grid, p->tab, p->nch, p->emax, p->tab32, p->stream)) != cudaSuccess)
         return cuda_fail(e, "mixed tables launch");
     p->data_set = 1;
     return FS_OK;
@@ -399,6 +433,9 @@ fs_status fs_plan_check(fs_plan* p, int* flags_out) {
         (e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return cuda_fail(e, "fs_plan_check");
     if (flags_out) *flags_out = h;
+    if (h & fs::kFlagTimeout)
+        return fail(FS_ETIMEOUT, "fs_plan_check: a bounded device-side wait of an earlier call ran out (its F values "
+                                 "are invalid)");
     if (h & fs::kFlagBadEdges)
         return fail(FS_EINVAL, "fs_plan_check: an earlier call was given partition edges that are not finite or "
                                "decrease (its F values are NaN)");
@@ -482,6 +519,7 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
     sg.edges = p->edges_dev;
     fs::Partials pa;
     pa.census = p->census_on ? p->census : nullptr;
+    pa.flags = p->flags_dev;
     pa.H = p->H;
     pa.T = p->T;
     pa.S = p->S;
@@ -493,25 +531,41 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
     pa.tile = mixed ? fs::mixed_span() : anchored ? fs::fp64a_span() : fp64_tile(variant);
     pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
+    // channel c: its response (turned orientation, scaled projections), its particles and partial sums
+    pa.nch = p->nch;
+    pa.ch_HT = (int64_t)7 * p->ntiles * p->B_cap;
+    pa.ch_S = (int64_t)7 * p->Np_cap * p->B_cap;
     {
         ProfScope ps(p, 0);
-        if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, global, p->stream)) != cudaSuccess)
-            return cuda_fail(e, "setup launch");
+        for (int c = 0; c < p->nch; c++)
+            if ((e = fs::launch_setup(channel_grid(p, c), params_dev, B, p->parts + (size_t)c * p->B_cap, global,
+                                      p->stream)) != cudaSuccess)
+                return cuda_fail(e, "setup launch");
+        // one basis rotation per segment for every channel (channel 0's patterns at its centre): the
+        // amplitudes are common to the channels, so their sums must share the basis
         if ((e = fs::launch_rotation(p->grid, p->parts, B, sg, p->rot, pa.rot32, p->stream)) != cudaSuccess)
             return cuda_fail(e, "rotation launch");
     }
     {
         ProfScope ps(p, 1);
-        if (mixed) {
-            if ((e = fs::launch_mixed_main(p->grid, p->tab, p->tab32, p->parts, B, sg, pa, variant,
-                                           p->span_list, p->span_cnt, p->stream)) != cudaSuccess)
-                return cuda_fail(e, "mixed main launch");
-        } else if (anchored) {
-            if ((e = fs::launch_fp64a_main(p->grid, p->tab, p->parts, B, sg, pa, variant == 4, p->span_list,
-                                           p->span_cnt, p->stream)) != cudaSuccess)
-                return cuda_fail(e, "fp64 anchored main launch");
-        } else if ((e = fs::launch_fp64_main(p->grid, p->tab, p->parts, B, sg, pa, p->stream)) != cudaSuccess) {
-            return cuda_fail(e, "fp64 main launch");
+        for (int c = 0; c < p->nch; c++) {
+            const fs::Grid gc = channel_grid(p, c);
+            const fs::Particle* pc = p->parts + (size_t)c * p->B_cap;
+            fs::Partials pc_pa = pa;
+            pc_pa.H = pa.H + c * pa.ch_HT;
+            pc_pa.T = pa.T + c * pa.ch_HT;
+            pc_pa.S = pa.S + c * pa.ch_S;
+            if (mixed) {
+                if ((e = fs::launch_mixed_main(gc, p->tab[c], p->tab32 + (size_t)c * p->grid.n, pc, B, sg, pc_pa,
+                                               variant, p->span_list, p->span_cnt, p->stream)) != cudaSuccess)
+                    return cuda_fail(e, "mixed main launch");
+            } else if (anchored) {
+                if ((e = fs::launch_fp64a_main(gc, p->tab[c], pc, B, sg, pc_pa, variant == 4, p->span_list,
+                                               p->span_cnt, p->stream)) != cudaSuccess)
+                    return cuda_fail(e, "fp64 anchored main launch");
+            } else if ((e = fs::launch_fp64_main(gc, p->tab[c], pc, B, sg, pc_pa, p->stream)) != cudaSuccess) {
+                return cuda_fail(e, "fp64 main launch");
+            }
         }
     }
     {
@@ -553,9 +607,10 @@ fs_status fs_mixed_probe(fs_plan* p, const fs_params* params_dev, int B, const d
     pa.rot32 = p->rot32;
     pa.tile = fs::mixed_span();
     pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
-    if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, global, p->stream)) != cudaSuccess ||
-        (e = fs::launch_rotation(p->grid, p->parts, B, sg, p->rot, p->rot32, p->stream)) != cudaSuccess ||
-        (e = fs::launch_mixed_probe(p->grid, p->tab, p->tab32, p->parts, sg, pa, b, k0, k0 + nbins, out_dev,
+    const fs::Grid g0 = channel_grid(p, 0);
+    if ((e = fs::launch_setup(g0, params_dev, B, p->parts, global, p->stream)) != cudaSuccess ||
+        (e = fs::launch_rotation(g0, p->parts, B, sg, p->rot, p->rot32, p->stream)) != cudaSuccess ||
+        (e = fs::launch_mixed_probe(g0, p->tab[0], p->tab32, p->parts, sg, pa, b, k0, k0 + nbins, out_dev,
                                     p->stream)) != cudaSuccess)
         return cuda_fail(e, "probe launch");
     return FS_OK;
@@ -569,7 +624,7 @@ fs_status fs_particle_bands(fs_plan* p, const fs_params* params_dev, int B, int6
     fs_status st = ensure_workspace(p, B, p->Np_cap > 0 ? p->Np_cap : 1);
     if (st != FS_OK) return st;
     cudaError_t e;
-    if ((e = fs::launch_setup(p->grid, params_dev, B, p->parts, 0, p->stream)) != cudaSuccess)
+    if ((e = fs::launch_setup(channel_grid(p, 0), params_dev, B, p->parts, 0, p->stream)) != cudaSuccess)
         return cuda_fail(e, "setup launch");
     if ((e = fs::launch_bands(p->parts, B, bands_dev, p->stream)) != cudaSuccess)
         return cuda_fail(e, "bands launch");
@@ -1038,10 +1093,14 @@ fs_status fs_add_signal(fs_plan* p, const fs_params* params_host, const double* 
         (e = cudaMemcpyAsync(p->one_a, a_host, sizeof(double) * 4, cudaMemcpyHostToDevice, p->stream)) !=
             cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync(signal parameters)");
-    if ((e = fs::launch_setup(p->grid, p->one_param, 1, p->one_part, 0, p->stream)) != cudaSuccess)
-        return cuda_fail(e, "setup launch");
-    if ((e = fs::launch_add_signal(p->grid, p->tab, p->one_part, p->one_a, data_dev, p->stream)) != cudaSuccess)
-        return cuda_fail(e, "add_signal launch");
+    for (int c = 0; c < p->nch; c++) {   // the signal as each channel sees it, into that channel's data
+        const fs::Grid gc = channel_grid(p, c);
+        if ((e = fs::launch_setup(gc, p->one_param, 1, p->one_part, 0, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "setup launch");
+        if ((e = fs::launch_add_signal(gc, p->tab[c], p->one_part, p->one_a, data_dev + (size_t)2 * p->grid.n * c,
+                                       p->stream)) != cudaSuccess)
+            return cuda_fail(e, "add_signal launch");
+    }
     e = cudaStreamSynchronize(p->stream);   // the host arguments are pageable: finish before returning
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return FS_OK;

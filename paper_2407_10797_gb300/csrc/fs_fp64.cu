@@ -250,11 +250,11 @@ __global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int
             for (int j = 0; j < 2; j++) {
                 const double* w = j == 0 ? pv : qv;
                 double* c = P.pr[arm * 2 + j];
-                c[0] = -3.0 * kap * (dc * w[0] + ds * w[1]);
-                c[1] = -0.5 * dc * w[2];
-                c[2] = -0.5 * ds * w[2];
-                c[3] = kap * (dc * w[0] - ds * w[1]);
-                c[4] = kap * (ds * w[0] + dc * w[1]);
+                c[0] = g.pscale * (-3.0 * kap * (dc * w[0] + ds * w[1]));
+                c[1] = g.pscale * (-0.5 * dc * w[2]);
+                c[2] = g.pscale * (-0.5 * ds * w[2]);
+                c[3] = g.pscale * (kap * (dc * w[0] - ds * w[1]));
+                c[4] = g.pscale * (kap * (ds * w[0] + dc * w[1]));
             }
         }
     }
@@ -516,11 +516,20 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
             if (thi > sv.hi) thi = sv.hi;
             const int pf = sv.seg(tlo), pl = sv.seg(thi);
             const double* src;
-            if (p == pf) src = pa.H + ((int64_t)b * pa.ntiles + t) * 7;
-            else if (p == pl) src = pa.T + ((int64_t)b * pa.ntiles + t) * 7;
-            else src = pa.S + ((int64_t)b * sg.Np + p) * 7;
+            int64_t stride;
+            if (p == pf) {
+                src = pa.H + ((int64_t)b * pa.ntiles + t) * 7;
+                stride = pa.ch_HT;
+            } else if (p == pl) {
+                src = pa.T + ((int64_t)b * pa.ntiles + t) * 7;
+                stride = pa.ch_HT;
+            } else {
+                src = pa.S + ((int64_t)b * sg.Np + p) * 7;
+                stride = pa.ch_S;
+            }
+            for (int ch = 0; ch < pa.nch; ch++)   // the channels' sums add (Sec. II.A, Eq. eq2)
 #pragma unroll
-            for (int c = 0; c < 7; c++) acc[c] += src[c];
+                for (int c = 0; c < 7; c++) acc[c] += src[ch * stride + c];
         }
     }
     if (G > 1) {

@@ -33,7 +33,25 @@ struct Grid {
     int64_t n;
     double f_min, df, T_obs;
     double alpha0, orient;   // detector orbital phase and orientation at t = 0
+    double pscale = 1.0;     // scale of the arm projections: the patterns, quadratic in them, carry pscale^2
 };
+
+// TDI channels in the long-wavelength limit (Sec. II.A, Eq. eq2): with the
+// vertex Michelsons X, Y, Z of the rigid constellation, A = (Z - X)/sqrt2 and
+// E = (X - 2Y + Z)/sqrt6 are the X Michelson with the constellation turned in
+// its plane by 75 and 30 degrees, times sqrt(3/2) (the three detector
+// tensors are 120 degrees apart in the plane of traceless in-plane tensors,
+// where a turn by r moves a tensor by 2r).
+constexpr int kMaxChannels = 2;
+struct Channel {
+    double orient_shift;   // rad, added to the grid's orientation
+    double pscale;         // arm-projection scale (patterns scale by its square)
+};
+__host__ __device__ constexpr Channel channel_of(int tdi, int c) {
+    return tdi == 0 ? Channel{0.0, 1.0}
+                    : (c == 0 ? Channel{1.3089969389957472, 1.1066819197003215}      // A: 75 deg, (3/2)^(1/4)
+                              : Channel{0.5235987755982988, 1.1066819197003215});    // E: 30 deg
+}
 
 // Segment description for one batch.
 struct Segs {
@@ -46,6 +64,7 @@ struct Segs {
 // Bits of a plan's sticky device flag word (read and cleared by fs_plan_check).
 constexpr int kFlagBadEdges = 1;   // partition edges not finite or decreasing
 constexpr int kFlagBadGrid = 2;    // a caller's frequency grid is not f_min + k df
+constexpr int kFlagTimeout = 4;    // a bounded device-side wait ran out (that call's F values are invalid)
 
 struct Partials {
     double* H;    // [B][ntiles][7] first segment of each (particle, tile)
@@ -56,6 +75,10 @@ struct Partials {
     int ntiles;   // number of tiles (slots of H and T per particle)
     int tile;     // bins per tile
     unsigned long long* census = nullptr;   // [6] in-band bins per anchor mode (anchored kernels), or NULL
+    int* flags = nullptr;                   // the plan's sticky flag word (kFlag*), for device-detected errors
+    // channels summed by the solve kernel: channel c's slots at H + c ch_HT, T + c ch_HT, S + c ch_S
+    int nch = 1;
+    int64_t ch_HT = 0, ch_S = 0;
 };
 
 // Record an error message for fs_last_error() and return st.
@@ -86,8 +109,10 @@ int fp64a_span();
 cudaError_t launch_fp64a_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
                               const Partials& pa, bool persistent, int* list, int* cnt, cudaStream_t s);
 cudaError_t launch_extrinsic(int64_t n, const double* amp, double* ext, cudaStream_t s);
-cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s);
-// variant 0: 2 CTAs/SM (up to 128 registers), 1: 3 CTAs/SM (up to 80 registers)
+// FP32 tables of nch channels (t32 [nch][n]) with one common power-of-two scale (exponent in *emax)
+cudaError_t launch_tables32(const Grid& g, const Tables* t, int nch, int* emax, float4* t32, cudaStream_t s);
+// variant 0: grid, 2 CTAs/SM (up to 128 registers); 1: grid, 3 CTAs/SM (up to 80 registers);
+// 2, 3: persistent with 2 or 3 CTAs/SM; 4: grid, tables staged through shared memory by bulk copies
 cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
                               const Segs& sg, const Partials& pa, int variant, int* list, int* cnt,
                               cudaStream_t s);

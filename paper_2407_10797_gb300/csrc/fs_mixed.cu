@@ -463,31 +463,41 @@ cudaError_t launch_span_lists(const Particle* parts, int B, const Segs& sg, int 
     return cudaGetLastError();
 }
 
-// One work item: particle b over span `span`, by one warp.  Phase A: one
-// anchor per lane (tile `lane` of the span) into the warp's 32 anchor slots;
-// phase B: the warp walks the particle's tiles of the span.  Partial sums
+// Phase A of a work item (particle b over span `span`, one warp): one anchor
+// per lane (tile `lane` of the span) into the warp's 32 anchor slots.
+__device__ __forceinline__ void mixed_anchors(const Grid& g, const Tables& tb, const Particle& P, const SegView& sv,
+                                              const Partials& pa, int64_t span_lo, Anchor* anc, int lane) {
+    int64_t lo = span_lo + (int64_t)lane * kTileMix, hi = lo + kTileMix;
+    if (lo < sv.lo) lo = sv.lo;
+    if (hi > sv.hi + 1) hi = sv.hi + 1;
+    make_anchor(g, tb, P, span_lo, lo, hi, anc[lane]);
+    if (pa.census && lo < hi) atomicAdd(&pa.census[anc[lane].mode], (unsigned long long)(hi - lo));
+    __syncwarp();
+}
+
+// Table source of phase B: every warp reads the span's FP32 tables from
+// global memory (served by L2 when several particles share a span).
+struct GlobalTables {
+    const float4* tw_span;
+    __device__ int first() const { return 0; }
+    __device__ int last() const { return kTilesPerSpan - 1; }
+    __device__ const float4* begin(int) const { return tw_span; }   // indexed by span-relative bin
+    __device__ void end(int, int) const {}
+};
+
+// Phase B: the warp walks tiles first()..last() of the span with the table
+// source Src (begin(ti) gives the tile's table entries, indexed by
+// span-relative bin, or NULL to stop; end(ti) releases them).  Partial sums
 // go to the slots of (b, span) and to the per-segment slots of the segments
 // that start and end inside the span.
-__device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, const float4* __restrict__ t32,
-                                           const Particle* __restrict__ parts, const Segs& sg, const Partials& pa,
-                                           int span, int b, Anchor* anc, int lane) {
+template <class Src>
+__device__ __forceinline__ void mixed_walk(const Grid& g, const Tables& tb, const Particle& P, const SegView& sv,
+                                           const Segs& sg, const Partials& pa, int span, int b, const Anchor* anc,
+                                           int lane, Src& src) {
     const int64_t span_lo = (int64_t)span * kSpanMix;
-    const Particle& P = parts[b];
-    const SegView sv = seg_view(sg, P);
-    {
-        int64_t lo = span_lo + (int64_t)lane * kTileMix, hi = lo + kTileMix;
-        if (lo < sv.lo) lo = sv.lo;
-        if (hi > sv.hi + 1) hi = sv.hi + 1;
-        make_anchor(g, tb, P, span_lo, lo, hi, anc[lane]);
-        if (pa.census && lo < hi) atomicAdd(&pa.census[anc[lane].mode], (unsigned long long)(hi - lo));
-    }
-    __syncwarp();
-
-    // ---- phase B
     const int64_t slot = (int64_t)b * pa.ntiles + span;
     const double2* rot64 = pa.rot + (int64_t)b * sg.Np;
     const float2* rot32 = pa.rot32 + (int64_t)b * sg.Np;
-    const float4* tw_span = t32 + span_lo;
 
     // acc: this tile's FP32 sums; (accS, accC): the compensated per-lane sums
     // of the tiles since the last flush
@@ -500,9 +510,14 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
     int nxt = -1;        // first bin (span-relative) of the segment after pk
     float g1[7], g2[7];
 
-    for (int ti = 0; ti < kTilesPerSpan; ti++) {
+    for (int ti = src.first(); ti <= src.last(); ti++) {
+        const float4* tw_span = src.begin(ti);
+        if (!tw_span) break;   // the staged source gave up waiting (flag set)
         const Anchor& A = anc[ti];
-        if (A.mode == 0) continue;
+        if (A.mode == 0) {
+            src.end(ti, lane);
+            continue;
+        }
         const int lo = A.lo, hi = A.hi;
         if (cur < 0) cur = sv.seg(span_lo + lo);
 #pragma unroll
@@ -621,6 +636,7 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
         }
 #pragma unroll
         for (int c = 0; c < 7; c++) comp_add(accS[c], accC[c], acc[c]);
+        src.end(ti, lane);
     }
     if (cur < 0) return;   // no in-band bin in this span (warp-uniform)
     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
@@ -629,6 +645,18 @@ __device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, cons
         const double v = warp_sum_comp(accS[c], accC[c]);
         if (lane == 0) dst[c] = v;
     }
+}
+
+// One work item, both phases, tables from global memory.
+__device__ __forceinline__ void mixed_item(const Grid& g, const Tables& tb, const float4* __restrict__ t32,
+                                           const Particle* __restrict__ parts, const Segs& sg, const Partials& pa,
+                                           int span, int b, Anchor* anc, int lane) {
+    const int64_t span_lo = (int64_t)span * kSpanMix;
+    const Particle& P = parts[b];
+    const SegView sv = seg_view(sg, P);
+    mixed_anchors(g, tb, P, sv, pa, span_lo, anc, lane);
+    GlobalTables src{t32 + span_lo};
+    mixed_walk(g, tb, P, sv, sg, pa, span, b, anc, lane, src);
 }
 
 // Grid form: CTA (span, group of 8 in-band particles of the span), one warp per particle.
@@ -677,13 +705,190 @@ mixed_persistent_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// Staged form: the CTA's 8 warps take 8 in-band particles of one span and
+// walk its tiles together.  Each 1024-bin tile of FP32 tables (16 KB) is
+// copied once per CTA from global memory into a ring of kStageBufs
+// shared-memory buffers by a bulk asynchronous copy (cp.async.bulk, the TMA
+// engine) and read by all 8 warps, instead of by each warp from L2.  Per
+// buffer a "full" mbarrier (one arrival plus the copy's transaction bytes)
+// tells the warps that a tile has landed, an "empty" mbarrier (one arrival
+// per warp) tells the copying thread (thread 0, which also computes) that
+// every warp is done with it.  Every wait is bounded: a wait that runs out
+// sets kFlagTimeout in the plan's flag word and a CTA-wide abort flag, the
+// warps stop, and thread 0 waits (bounded) for its copies still in flight
+// before the CTA exits.  The per-bin arithmetic and the order of every sum
+// are those of the other forms, so F is bit-identical to them.
+// ---------------------------------------------------------------------------
+constexpr int kStageBufs = 4;
+constexpr long long kMaxPolls = 1LL << 24;
+constexpr size_t kStageSmem = (size_t)kStageBufs * kTileMix * sizeof(float4) + sizeof(Anchor) * kWarpsMix * 32 +
+                              2 * kStageBufs * sizeof(unsigned long long) + 4 * sizeof(int);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < kMaxPolls; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// One bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct StagedTables {
+    float4* buf;                   // [kStageBufs][kTileMix] shared
+    unsigned long long* full;      // [kStageBufs]
+    unsigned long long* empty;     // [kStageBufs]
+    volatile int* abort_flag;      // shared: a wait of this CTA ran out
+    int* flags;                    // the plan's sticky flag word
+    const float4* g_span;          // the span's FP32 tables in global memory
+    int64_t bins_left;             // bins of the grid from the span's start
+    int t0, t1;                    // tiles of the CTA's walk
+    int issued;                    // thread 0: last tile whose copy was issued
+    int waited;                    // thread 0: last tile whose copy it saw land
+
+    __device__ int first() const { return t0; }
+    __device__ int last() const { return t1; }
+    __device__ int slot(int ti) const { return (ti - t0) % kStageBufs; }
+    __device__ uint32_t parity(int ti) const { return (uint32_t)((ti - t0) / kStageBufs) & 1u; }
+    __device__ void fail() {
+        *abort_flag = 1;
+        atomicOr(flags, kFlagTimeout);
+    }
+    // thread 0: copy tile j into its slot
+    __device__ void issue(int j) {
+        int64_t nb = bins_left - (int64_t)j * kTileMix;
+        if (nb > kTileMix) nb = kTileMix;
+        const uint32_t bytes = (uint32_t)nb * (uint32_t)sizeof(float4);
+        const int s = slot(j);
+        mbar_arrive_tx(&full[s], bytes);
+        bulk_copy(buf + (size_t)s * kTileMix, g_span + (int64_t)j * kTileMix, bytes, &full[s]);
+        issued = j;
+    }
+    __device__ const float4* begin(int ti) {
+        if (*abort_flag) return nullptr;
+        if (!mbar_wait(&full[slot(ti)], parity(ti))) {
+            fail();
+            return nullptr;
+        }
+        if (threadIdx.x == 0) waited = ti;
+        return buf + (size_t)slot(ti) * kTileMix - (int64_t)ti * kTileMix;
+    }
+    __device__ void end(int ti, int lane) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot(ti)]);
+        if (threadIdx.x == 0 && ti + kStageBufs <= t1 && !*abort_flag) {
+            // every warp is done with tile ti: its buffer takes tile ti + kStageBufs
+            if (mbar_wait(&empty[slot(ti)], parity(ti))) issue(ti + kStageBufs);
+            else fail();
+        }
+    }
+    // thread 0, before the CTA exits: wait (bounded) for copies it issued and has not seen land
+    __device__ void drain() {
+        for (int j = waited + 1; j <= issued; j++)
+            if (!mbar_wait(&full[slot(j)], parity(j))) atomicOr(flags, kFlagTimeout);
+    }
+};
+
+template <int MINB>
+__global__ void __launch_bounds__(kWarpsMix * 32, MINB)
+mixed_staged_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts, int B,
+                    Segs sg, Partials pa, const int* __restrict__ list, const int* __restrict__ cnt) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4* buf = reinterpret_cast<float4*>(smem_raw);
+    Anchor* anc_all = reinterpret_cast<Anchor*>(smem_raw + (size_t)kStageBufs * kTileMix * sizeof(float4));
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(anc_all + kWarpsMix * 32);
+    int* sh = reinterpret_cast<int*>(bars + 2 * kStageBufs);   // [0] first tile, [1] last tile, [2] abort
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int span = blockIdx.x;
+    const int n_here = cnt[span];
+    if ((int)blockIdx.y * kWarpsMix >= n_here) return;   // CTA-uniform: no particle for this CTA
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStageBufs; s++) {
+            mbar_init(&bars[s], 1);                     // full: the copying thread's arrival + bytes
+            mbar_init(&bars[kStageBufs + s], kWarpsMix);  // empty: one arrival per warp
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh[0] = INT_MAX;
+        sh[1] = -1;
+        sh[2] = 0;
+    }
+    __syncthreads();
+    const int64_t span_lo = (int64_t)span * kSpanMix;
+    const int j = blockIdx.y * kWarpsMix + w;
+    Anchor* anc = anc_all + w * 32;
+    int b = -1;
+    SegView sv{};
+    if (j < n_here) {   // warp-uniform
+        b = list[(int64_t)span * B + j];
+        sv = seg_view(sg, parts[b]);
+        mixed_anchors(g, tb, parts[b], sv, pa, span_lo, anc, lane);
+        const unsigned m = __ballot_sync(0xffffffffu, anc[lane].mode != 0);
+        if (lane == 0 && m) {
+            atomicMin(&sh[0], __ffs(m) - 1);
+            atomicMax(&sh[1], 31 - __clz(m));
+        }
+    }
+    __syncthreads();
+    StagedTables src;
+    src.buf = buf;
+    src.full = bars;
+    src.empty = bars + kStageBufs;
+    src.abort_flag = sh + 2;
+    src.flags = pa.flags;
+    src.g_span = t32 + span_lo;
+    src.bins_left = g.n - span_lo;
+    src.t0 = sh[0];
+    src.t1 = sh[1];
+    src.issued = src.t0 - 1;
+    src.waited = src.t0 - 1;
+    if (src.t0 > src.t1) return;   // CTA-uniform: no in-band tile
+    if (threadIdx.x == 0)
+        for (int t = src.t0; t <= src.t1 && t < src.t0 + kStageBufs; t++) src.issue(t);
+    if (b >= 0) {
+        mixed_walk(g, tb, parts[b], sv, sg, pa, span, b, anc, lane, src);
+    } else {
+        // a warp without a particle still takes part in every tile's hand-over
+        for (int ti = src.t0; ti <= src.t1; ti++) {
+            if (!src.begin(ti)) break;
+            src.end(ti, lane);
+        }
+    }
+    if (threadIdx.x == 0) src.drain();
+}
 
 cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32, const Particle* parts, int B,
                               const Segs& sg, const Partials& pa, int variant, int* list, int* cnt,
                               cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
     const int nspans = pa.ntiles;
-    const bool persistent = variant >= 2;
+    const bool persistent = variant == 2 || variant == 3;
     int* off = cnt + nspans;            // [nspans + 1]
     int* ctl = cnt + 2 * nspans + 1;    // [3]: CTAs done, next item, spare
     const size_t smem = sizeof(Anchor) * kWarpsMix * 32;
@@ -703,6 +908,20 @@ cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32,
         return cudaGetLastError();
     }
     dim3 grid((unsigned)nspans, (unsigned)((B + kWarpsMix - 1) / kWarpsMix));
+    if (variant == 4) {
+        static int attr_set[64];
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!attr_set[dev]) {
+            if ((e = cudaFuncSetAttribute(mixed_staged_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kStageSmem)) != cudaSuccess)
+                return e;
+            attr_set[dev] = 1;
+        }
+        mixed_staged_kernel<2><<<grid, kWarpsMix * 32, kStageSmem, s>>>(g, t, t32, parts, B, sg, pa, list, cnt);
+        return cudaGetLastError();
+    }
     if (variant == 1)
         mixed_main_kernel<3><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, cnt);
     else
@@ -801,7 +1020,9 @@ int mixed_probe_fields() { return kProbeFields; }
 // ---------------------------------------------------------------------------
 // FP32 tables of the mixed path: (dw_re, dw_im, W) scaled by powers of two so
 // that max W ~ 1 (F is invariant under (d, S) -> (c d, c^2 S), and a power of
-// two changes no mantissa).
+// two changes no mantissa).  With several channels the scale is common to
+// all of them: F is invariant under one scale for every channel, not under
+// one per channel.
 // ---------------------------------------------------------------------------
 __global__ void w_exponent_kernel(Grid g, Tables t, int* emax) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -825,15 +1046,20 @@ __global__ void tables32_kernel(Grid g, Tables t, const int* emax, float4* t32) 
     t32[k] = make_float4((float)(t.dwr[k] * sd), di, (float)(t.W[k] * sW), -di);
 }
 
-cudaError_t launch_tables32(const Grid& g, const Tables& t, int* emax, float4* t32, cudaStream_t s) {
+cudaError_t launch_tables32(const Grid& g, const Tables* t, int nch, int* emax, float4* t32, cudaStream_t s) {
     const int threads = 256;
     const int64_t blocks = (g.n + threads - 1) / threads;
     cudaError_t e = cudaMemsetAsync(emax, 0x80, sizeof(int), s);   // INT_MIN-ish start (0x80808080)
     if (e != cudaSuccess) return e;
-    w_exponent_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t, emax);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    tables32_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t, emax, t32);
-    return cudaGetLastError();
+    for (int c = 0; c < nch; c++) {
+        w_exponent_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t[c], emax);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (int c = 0; c < nch; c++) {
+        tables32_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t[c], emax, t32 + (size_t)c * g.n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace fs

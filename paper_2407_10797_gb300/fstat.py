@@ -18,6 +18,7 @@ from . import build as _build
 
 FS_OK, FS_EINVAL, FS_ECUDA, FS_ENOMEM, FS_ETIMEOUT, FS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 FS_FP64, FS_MIXED = 0, 1
+FS_TDI_X, FS_TDI_AE = 0, 1
 _STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ECUDA", -3: "FS_ENOMEM", -4: "FS_ETIMEOUT",
            -5: "FS_EUNSUPPORTED"}
 
@@ -61,6 +62,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             raise ImportError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
         L = C.CDLL(_build.LIB)
         L.fs_plan_create.argtypes = [C.POINTER(_vp), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int, _vp]
+        L.fs_plan_create_tdi.argtypes = [C.POINTER(_vp), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
+                                         C.c_int, _vp]
+        L.fs_plan_channels.argtypes = [_vp]
+        L.fs_plan_channels.restype = C.c_int
         L.fs_plan_destroy.argtypes = [_vp]
         L.fs_plan_set_data.argtypes = [_vp, _vp, _vp, _vp]
         L.fs_plan_check.argtypes = [_vp, C.POINTER(C.c_int)]
@@ -116,7 +121,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_mlp_train.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp]
         L.fs_plan_read_profile.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_int64)]
         L.fs_last_error.restype = C.c_char_p
-        for name in ("fs_plan_create", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_check", "fs_plan_reserve",
+        for name in ("fs_plan_create", "fs_plan_create_tdi", "fs_plan_destroy", "fs_plan_set_data", "fs_plan_check", "fs_plan_reserve",
                      "fs_fstat_batch", "fs_amplitudes", "fs_add_signal", "fs_constants", "fs_particle_bands",
                      "fs_plan_set_profiling", "fs_plan_read_profile", "fs_fstat_batch_noalloc", "fs_mixed_probe",
                      "fs_plan_set_variant", "fs_plan_set_variant_for", "fs_plan_get_variant",
@@ -167,7 +172,8 @@ def _stream_handle(stream):
 class Plan:
     """One frequency grid + precision mode; wraps fs_plan."""
 
-    def __init__(self, n_bins: int, f_min: float, df: float, T_obs: float, mode: int = FS_FP64, stream=None):
+    def __init__(self, n_bins: int, f_min: float, df: float, T_obs: float, mode: int = FS_FP64, stream=None,
+                 tdi: int = FS_TDI_X):
         import torch
         L = load()
         self._L = L
@@ -175,13 +181,14 @@ class Plan:
         self.mode = int(mode)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        _check(L.fs_plan_create(C.byref(h), self.n, float(f_min), float(df), float(T_obs), int(mode),
-                                _stream_handle(self.stream)))
+        _check(L.fs_plan_create_tdi(C.byref(h), self.n, float(f_min), float(df), float(T_obs), int(mode), int(tdi),
+                                    _stream_handle(self.stream)))
         self._h = h
+        self.nch = L.fs_plan_channels(h)
 
     @classmethod
-    def from_grid(cls, grid, mode: int = FS_FP64, stream=None) -> "Plan":
-        return cls(grid.n, grid.f_min, grid.df, grid.T_obs, mode, stream)
+    def from_grid(cls, grid, mode: int = FS_FP64, stream=None, tdi: int = FS_TDI_X) -> "Plan":
+        return cls(grid.n, grid.f_min, grid.df, grid.T_obs, mode, stream, tdi)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -195,14 +202,15 @@ class Plan:
             pass
 
     def set_data(self, data, psd, f_grid=None):
-        """data: complex128 CUDA tensor [n] (or float64 [n, 2]); psd: float64 CUDA tensor [n];
+        """data: complex128 CUDA tensor [n] (or float64 [n, 2]), [channels, n] for a
+        plan with several channels; psd: float64 CUDA tensor [n] ([channels, n]);
         f_grid: optional float64 CUDA tensor [n] of the data's frequencies (must be the
         plan's uniform grid; FstatError FS_EUNSUPPORTED otherwise)."""
         import torch
         if data.dtype == torch.complex128:
             data = torch.view_as_real(data)
-        if data.shape != (self.n, 2) or psd.shape != (self.n,):
-            raise ValueError("data must be [n] complex and psd [n]")
+        if data.numel() != 2 * self.nch * self.n or psd.numel() != self.nch * self.n or data.shape[-1] != 2:
+            raise ValueError(f"data must be [{self.nch}, {self.n}] complex and psd [{self.nch}, {self.n}]")
         if f_grid is not None:
             _check_size(f_grid, self.n, "f_grid")
         # keep the inputs alive until the stream has consumed them
@@ -215,7 +223,8 @@ class Plan:
 
     def check(self) -> int:
         """fs_plan_check: flag bits the device raised since the last check (raises
-        FstatError FS_EINVAL if a call was given invalid partition edges)."""
+        FstatError FS_EINVAL if a call was given invalid partition edges,
+        FS_ETIMEOUT if a bounded device-side wait ran out)."""
         f = C.c_int()
         _check(self._L.fs_plan_check(self._h, C.byref(f)))
         return f.value
@@ -307,7 +316,7 @@ class Plan:
 
     @property
     def n_variants(self) -> int:
-        return 4 if self.mode == FS_MIXED else 5
+        return 5
 
     def autotune(self, params, Np: int, edges=None, reps: int = 3):
         """Time every launch variant on this batch and keep the fastest for
@@ -341,12 +350,14 @@ class Plan:
         return ms.value, n.value
 
     def add_signal(self, p, a, data):
-        """data += sum_i a_i A^i(p) over the particle's band (data: complex128 CUDA tensor)."""
+        """data += sum_i a_i A^i(p) over the particle's band (data: complex128 CUDA tensor,
+        [channels, n] for a plan with several channels, each through its own response)."""
         import torch
         if data.dtype == torch.complex128:
             view = torch.view_as_real(data)
         else:
             view = data
+        _check_size(view, 2 * self.nch * self.n, "data (re, im pairs per channel)")
         pp = fs_params(*[float(x) for x in np.asarray(p, dtype=np.float64)[:6]])
         aa = np.ascontiguousarray(a, dtype=np.float64)
         _check(self._L.fs_add_signal(self._h, C.byref(pp), aa.ctypes.data_as(_dp), _cuda_ptr(view, torch.float64)))

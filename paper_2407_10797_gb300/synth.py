@@ -138,12 +138,25 @@ def lisa_like_psd(f: np.ndarray) -> np.ndarray:
         * (1.0 + 0.6 * (f / fstar) ** 2) / L ** 2
 
 
-def gaussian_noise(grid: Grid, psd: np.ndarray, seed: int) -> np.ndarray:
+def gaussian_noise(grid: Grid, psd: np.ndarray, seed: int, channel: int = 0) -> np.ndarray:
     """Complex frequency-domain noise: Re and Im of n_k are i.i.d.
-    N(0, S_k T/4), so E|n_k|^2 = S_k T/2 (one-sided PSD, bin width 1/T)."""
-    z0, z1 = standard_normal_pairs(seed, STREAM_NOISE, grid.n)
+    N(0, S_k T/4), so E|n_k|^2 = S_k T/2 (one-sided PSD, bin width 1/T).
+    Each channel draws from its own stream, so channels are independent."""
+    z0, z1 = standard_normal_pairs(seed, STREAM_NOISE + channel, grid.n)
     sigma = np.sqrt(psd * grid.T_obs / 4.0)
     return sigma * z0 + 1j * (sigma * z1)
+
+
+TDI_X, TDI_AE = 0, 1
+
+
+def tdi_psds(f: np.ndarray, tdi: int) -> np.ndarray:
+    """One-sided noise PSDs of the channels of a TDI set, [channels, n]: X
+    takes the LISA-like model, A and E (responses sqrt(3/2) times a Michelson
+    of the same arms, noise-orthogonal) 3/2 of it each, the long-wavelength
+    relation S_A = S_E = S_X - S_XY with S_XY = -S_X / 2."""
+    sx = lisa_like_psd(f)
+    return sx[None, :] if tdi == TDI_X else np.stack([1.5 * sx, 1.5 * sx])
 
 
 # --------------------------------------------------------------------------

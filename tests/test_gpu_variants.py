@@ -60,11 +60,13 @@ def test_mixed_variants_bitwise_equal(fst, small_case, Np):
     plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
     Pt = torch.from_numpy(P).cuda()
     outs = []
-    for v in range(4):
+    assert plan.n_variants == 5
+    for v in range(plan.n_variants):
         plan.set_variant(v)
         F, Fp = plan.fstat(Pt, Np)
         outs.append((F.clone(), Fp.clone()))
     torch.cuda.synchronize()
+    assert plan.check() == 0          # no bounded wait of the staged form ran out
     for F, Fp in outs[1:]:
         assert torch.equal(F, outs[0][0]) and torch.equal(Fp, outs[0][1])
     Fo, _ = O.fstat_batch(P, O.OracleModel.from_grid(g), d, psd, Np)
@@ -73,14 +75,16 @@ def test_mixed_variants_bitwise_equal(fst, small_case, Np):
     plan.close()
 
 
-def test_mixed_persistent_repeats_and_empty_batches(fst, small_case):
+@pytest.mark.parametrize("variant", [2, 4])
+def test_mixed_persistent_repeats_and_empty_batches(fst, small_case, variant):
     """The persistent form resets its device-side item counter on every
-    launch: repeated calls, a batch with no in-band particle and a single
-    particle all come out right."""
+    launch, and the staged form's barriers start afresh in every CTA:
+    repeated calls, a batch with no in-band particle and a single particle
+    (a CTA with one busy warp and seven idle ones) all come out right."""
     g, d, psd, P = small_case
     plan = fst.Plan.from_grid(g, mode=fst.FS_MIXED)
     plan.set_data(torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda())
-    plan.set_variant(2)
+    plan.set_variant(variant)
     Pt = torch.from_numpy(P).cuda()
     F0 = plan.fstat(Pt, 16)[0].clone()
     far = P.copy()
@@ -91,6 +95,7 @@ def test_mixed_persistent_repeats_and_empty_batches(fst, small_case):
     assert torch.equal(F0, F1)
     one = plan.fstat(Pt[5:6].contiguous(), 16)[0]
     assert torch.equal(one, F0[5:6])
+    assert plan.check() == 0
     plan.close()
 
 
@@ -221,7 +226,7 @@ def test_swarm_autotune_leaves_swarm_unchanged(fst, small_case):
     sw.init(5)
     before = [t.clone() for t in (sw.x, sw.v, sw.pbest_x, sw.pbest_f, sw.fit)]
     v, ms = sw.autotune(64, reps=1)
-    assert 0 <= v < 4 and plan.get_variant(64) == v
+    assert 0 <= v < plan.n_variants and plan.get_variant(64) == v
     after = (sw.x, sw.v, sw.pbest_x, sw.pbest_f, sw.fit)
     for a, b in zip(before, after):
         assert torch.equal(a, b)

@@ -693,3 +693,111 @@ def test_mlp_oracle_adam_fits_a_smooth_function():
         L, g = M.loss_and_grad(theta, X, t, W)
         theta, m, v = M.adam(theta, g, m, v, s, 3e-3)
     assert L < 0.05 * L_first
+
+
+# ---------------------------------------------------------------- TDI channels (Sec. II.A, Eq. eq2)
+def test_tdi_T_vanishes_and_A_E_are_orthogonal_michelsons_turned_in_the_plane():
+    """Long-wavelength TDI: X + Y + Z = 0, so T vanishes; A and E are
+    orthogonal, each of norm sqrt(3/2) times a Michelson's, and equal to the
+    X Michelson with the constellation turned in its plane by 75 and 30
+    degrees (three tensors 120 degrees apart in the plane of traceless
+    in-plane tensors, where a turn by r moves a tensor by 2r), times
+    sqrt(3/2)."""
+    g = S.tiny_grid(n=10)
+    ms = [O.OracleModel.from_grid(g, channel=c) for c in range(4)]
+    for t in (0.0, 0.37 * S.YEAR_S, 1.71 * S.YEAR_S):
+        DX, DA, DE, DT = (O.detector_tensor(m, t) for m in ms)
+        assert np.abs(DT).max() < 1e-15
+        assert abs(np.sum(DA * DE)) < 1e-15
+        assert np.sum(DA * DA) == pytest.approx(1.5 * np.sum(DX * DX), rel=1e-13)
+        assert np.sum(DE * DE) == pytest.approx(1.5 * np.sum(DX * DX), rel=1e-13)
+        for D, deg in ((DA, 75.0), (DE, 30.0)):
+            turned = O.detector_tensor(O.OracleModel.from_grid(g, channel=0, orient=np.deg2rad(deg)), t)
+            assert np.allclose(D, np.sqrt(1.5) * turned, rtol=0, atol=1e-15)
+
+
+def test_tdi_A_E_sky_averages():
+    """<F_A^2> = <F_E^2> = 3/2 x 3/20 (sky and polarisation average) and
+    <F_A F_E> = 0: A and E see the sky with equal sensitivity and their
+    responses are uncorrelated (Gauss-Legendre x uniform longitude, exact
+    for these degree-4 polynomials in the direction)."""
+    g = S.tiny_grid(n=10)
+    mA = O.OracleModel.from_grid(g, channel=1)
+    mE = O.OracleModel.from_grid(g, channel=2)
+    xs, ws = np.polynomial.legendre.leggauss(6)
+    nl = 12
+    for t in (0.0, 0.9 * S.YEAR_S):
+        aa = ee = ae = 0.0
+        for x, w in zip(xs, ws):
+            for j in range(nl):
+                p = np.array([20.0, 0.0, math.asin(x), 2 * np.pi * j / nl, 0.0, 1.0])
+                pa, xa = O.antenna(p, mA, t)
+                pe, xe = O.antenna(p, mE, t)
+                aa += w * (pa * pa + xa * xa) / nl
+                ee += w * (pe * pe + xe * xe) / nl
+                ae += w * (pa * pe + xa * xe) / nl
+        assert aa / 2.0 == pytest.approx(2 * 1.5 * 3.0 / 20.0, rel=1e-12)
+        assert ee / 2.0 == pytest.approx(2 * 1.5 * 3.0 / 20.0, rel=1e-12)
+        assert abs(ae) < 1e-13
+
+
+def _two_channel_case(g, p, snr, seed=None):
+    psd = S.tdi_psds(g.freqs(), S.TDI_AE)
+    ms = [O.OracleModel.from_grid(g, channel=1), O.OracleModel.from_grid(g, channel=2)]
+    a = O.extrinsic_to_a(1.0, S.INJ_PSI, S.INJ_IOTA, S.INJ_PHIC)
+    k0, k1 = O.band(p, ms[0])
+    h = np.stack([O.inject(p, m, a, k0, k1 + 1) for m in ms])
+    hh = sum(O.inner(h[c], h[c], psd[c], g.df) for c in range(2))
+    h *= snr / math.sqrt(hh)
+    d = h.copy()
+    if seed is not None:
+        d += np.stack([S.gaussian_noise(g, psd[c], seed, channel=c) for c in range(2)])
+    return d, psd, ms, h
+
+
+@pytest.mark.parametrize("Np", [1, 5])
+def test_two_channel_F_is_half_the_summed_snr_squared(Np):
+    """Noise-free A and E data: F_sum at the truth = (sum over channels of
+    (h_c|h_c)) / 2 = SNR^2 / 2 -- the amplitudes are common to the channels."""
+    g = S.tiny_grid(n=4096, f_min=0.02, stride=4)
+    p = np.array([30.0, tc_for(30.0, 0.02 + 2048 * g.df, 0.5 * g.T_obs), 0.3, 1.0, 0.05, 1.0])
+    d, psd, ms, h = _two_channel_case(g, p, 12.0)
+    F, _ = O.fstat_batch_channels(p[None], ms, d, psd, Np)
+    assert F[0] == pytest.approx(72.0, rel=1e-11)
+
+
+def test_two_channel_F_reduces_to_one_channel():
+    """With the second channel's data zero and its noise PSD 10^30 times
+    larger, its inner products vanish and F equals the one-channel F."""
+    g = S.tiny_grid(n=4096, f_min=0.02, stride=4)
+    p = np.array([26.0, tc_for(26.0, 0.02 + 2048 * g.df, 0.4 * g.T_obs), -0.4, 2.0, 0.03, 1.0])
+    d, psd, ms, h = _two_channel_case(g, p, 10.0, seed=3)
+    P = np.stack([p, p + np.array([0.2, 30.0, 0.01, 0.0, 0.0, 0.0])])
+    d2 = d.copy()
+    d2[1] = 0.0
+    psd2 = psd.copy()
+    psd2[1] *= 1e30
+    F2, Fp2 = O.fstat_batch_channels(P, ms, d2, psd2, 3)
+    F1, Fp1 = O.fstat_batch(P, ms[0], d2[0], psd2[0], 3)
+    assert np.allclose(F2, F1, rtol=1e-10, atol=1e-12)
+    assert np.allclose(Fp2, Fp1, rtol=1e-10, atol=1e-12)
+
+
+def test_two_channel_noise_only_2F_is_chi_square_4Np():
+    """Gaussian noise in A and E: 2 F_sum ~ chi^2 with 4 N_p degrees of
+    freedom (the four amplitudes per segment are common to the channels)."""
+    from scipy import stats
+    g = S.tiny_grid(n=3000, f_min=0.02)          # bins of width 1/T, as the noise model assumes
+    psd = S.tdi_psds(g.freqs(), S.TDI_AE)
+    ms = [O.OracleModel.from_grid(g, channel=1), O.OracleModel.from_grid(g, channel=2)]
+    Np = 2
+    P = S.draw_params(S.Prior(tc_lo=0.2 * g.T_obs, tc_hi=0.8 * g.T_obs), 40, 5)
+    P[:, 1] = tc_for(P[:, 0], 0.02 + 1500 * g.df, P[:, 1])
+    vals = []
+    for seed in range(40):
+        d = np.stack([S.gaussian_noise(g, psd[c], 100 + seed, channel=c) for c in range(2)])
+        F, _ = O.fstat_batch_channels(P[seed % 40:seed % 40 + 5], ms, d, psd, Np)
+        vals.extend(2.0 * F)
+    vals = np.array(vals)
+    assert abs(np.mean(vals) - 4 * Np) < 0.6
+    assert stats.kstest(vals, stats.chi2(4 * Np).cdf).pvalue > 1e-3
