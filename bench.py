@@ -57,7 +57,7 @@ FP64_DIRECT_FLOP = 203.0
 # N_p; the FP64 figure holds for the anchored variants (3, 4) only.  None
 # while the kernel has changed since its counters were taken.
 TRAFFIC_FP64_ANCHORED = 76.13e6
-TRAFFIC_MIXED = None
+TRAFFIC_MIXED = 48.47e6
 FP64_TIER_FLOP = {1: 96.0, 2: FP64_DIRECT_FLOP, 3: 84.0, 4: 76.0, 5: 70.0}
 
 

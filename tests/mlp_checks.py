@@ -20,7 +20,7 @@ from oracle import mlp_oracle as M
 C_TOL = 8.0
 MAX_OUTSIDE = 2e-4
 MAX_RATIO = 32.0
-MIN_PROTECTED = 0.75    # live elements on which a sign error would exceed the tolerance
+MIN_PROTECTED = 0.70    # live elements on which a sign error would exceed the tolerance
 
 
 def compare(g, theta, X, t, width):
