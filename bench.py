@@ -96,6 +96,11 @@ def parse():
     ap.add_argument("--stages", choices=["default", "paper"], default="default",
                     help="search mode: N_p = 256/64/16/1 (default) or the paper's 16/16/1 schedule")
     ap.add_argument("--snr", type=float, default=None, help="search mode: injection SNR (default: the workload's)")
+    ap.add_argument("--dmu", type=float, default=0.0,
+                    help="search mode: search delta_mu in [0, DMU] as a sixth coordinate (the paper's 0.9), with the "
+                         "injection at delta_mu = 0.1585 (Table I); 0 = equal masses, 5-D")
+    ap.add_argument("--progress", type=int, default=100,
+                    help="search mode: read the best point every this many iterations (iterations to the target)")
     ap.add_argument("--prior", choices=["full", "targeted"], default="full",
                     help="search mode: the full prior (M_c 10-50 Msun, 0.5 yr of t_c) or a follow-up box "
                          "(M_c +-0.5 Msun, t_c +-0.005 yr around the injection; full sky and e0)")
@@ -684,6 +689,8 @@ def run_search(args):
         noise = S.gaussian_noise(g, psd, 7000 + seed)
         inj = S.draw_params(S.Prior(Mc_lo=20.0, Mc_hi=40.0, tc_lo=0.95 * T, tc_hi=1.05 * T, e0_hi=0.1), 1,
                             7000 + seed, stream=S.STREAM_INJECTION)[0]
+        if args.dmu > 0.0:
+            inj[5] = search.q_of_dmu(0.1585)        # the paper's injected delta_mu (Table I)
         if args.prior == "targeted":
             # box centred on the injection shifted by a seeded offset (the search does not start at the truth)
             u = S.uniforms(7000 + seed, 0x54475444, 2)
@@ -707,12 +714,23 @@ def run_search(args):
         torch.cuda.synchronize()
         hs = search.HierarchicalSearch(plan, prior, stages, n_boxes=16, runs_per_box=8,
                                        n_part=40, seed=seed,
-                                       surrogate=search.SurrogateSpec() if args.search == "surrogate" else None)
+                                       surrogate=search.SurrogateSpec() if args.search == "surrogate" else None,
+                                       dmu_hi=args.dmu, progress_every=args.progress)
         t0 = time.perf_counter()
         res = hs.run()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         best = res["best"]
+        # iterations to the target: the first point, counted over the stages'
+        # iterations, at which the best F-hat's M_c is within 1e-4 of the truth
+        it_total, it_target, stage_base = 0, None, 0
+        last_stage = -1
+        for (st_i, it, bf_, pp) in hs.progress:
+            if st_i != last_stage:
+                stage_base = sum(s.n_iter for s in stages[:st_i])
+                last_stage = st_i
+            if it_target is None and abs(pp[0] - inj[0]) / inj[0] <= 1e-4:
+                it_target = stage_base + it
         per_stage = []
         for st in res["stages"]:
             wv = np.array(st["winners"])
@@ -729,7 +747,10 @@ def run_search(args):
                     "truth": [float(x) for x in inj[:5]], "best": [float(x) for x in best[:5]],
                     "Mc_rel_err": abs(best[0] - inj[0]) / inj[0], "tc_err_s": abs(best[1] - inj[1]),
                     "sky_err_deg": math.degrees(sky_angle(best[2], best[3], inj[2], inj[3])),
-                    "e0_err": abs(best[4] - inj[4]), "extrinsic": res["extrinsic"]})
+                    "e0_err": abs(best[4] - inj[4]), "extrinsic": res["extrinsic"],
+                    "dmu_true": (inj[5] - 1) / (inj[5] + 1), "dmu_best": (best[5] - 1) / (best[5] + 1),
+                    "iterations_to_Mc_1e-4": it_target,
+                    "progress": [(a, b, c, d[0]) for (a, b, c, d) in hs.progress]})
         plan.close()
     walls = [o["wall_s"] for o in out]
     line = {"metric": "search wall time", "value": float(np.mean(walls)), "unit": "s", "higher_is_better": False,
@@ -740,9 +761,10 @@ def run_search(args):
                        "runs_per_box": 8, "particles": 40, "iterations_per_stage": args.iters, "snr": snr,
                        "prior": {"Mc": [prior.Mc_lo, prior.Mc_hi], "tc": [prior.tc_lo, prior.tc_hi],
                                  "e0": [0.0, prior.e0_hi], "sky": "full sphere"},
-                       "surrogate": args.search == "surrogate"},
+                       "surrogate": args.search == "surrogate", "dmu_free_up_to": args.dmu},
             "exact_F_evaluations": len(stages) * 16 * 8 * 40 * args.iters,
-            "Mc_rel_err": [o["Mc_rel_err"] for o in out], "runs": out}
+            "Mc_rel_err": [o["Mc_rel_err"] for o in out],
+            "iterations_to_Mc_1e-4": [o["iterations_to_Mc_1e-4"] for o in out], "runs": out}
     print(json.dumps(line), flush=True)
 
 

@@ -231,26 +231,32 @@ FS_API fs_status fs_particle_bands(fs_plan* plan, const fs_params* params_dev, i
 
 /* ---- Particle swarm optimisation on the device (Sec. III.A) ------------- */
 
-/* State of R independent PSO runs of n_part particles each in the 5-D
- * normalised search space [0,1]^5 of (M_c, t_c, sin(lat), lon, e0).  All
- * pointers are device memory owned by the caller. */
+/* State of R independent PSO runs of n_part particles each in the
+ * normalised search space [0,1]^D of (M_c, t_c, sin(lat), lon, e0) (D = 5,
+ * every particle with the mass ratio q) or of (M_c, t_c, sin(lat), lon, e0,
+ * delta_mu) (D = 6: the dimensionless mass difference delta_mu = (m1 - m2)/M
+ * of Sec. II.A's Theta_I is searched too, the paper's [0, 0.9] range of
+ * Table I, and a particle has q = (1 + delta_mu)/(1 - delta_mu)).  All
+ * pointers are device memory owned by the caller; the D-sized rows below are
+ * D = dims values. */
 typedef struct {
     int R;                 /* independent runs */
     int n_part;            /* particles per run */
-    double* x;             /* [R][n_part][5] normalised positions */
-    double* v;             /* [R][n_part][5] velocities */
-    double* pbest_x;       /* [R][n_part][5] personal-best positions */
+    double* x;             /* [R][n_part][D] normalised positions */
+    double* v;             /* [R][n_part][D] velocities */
+    double* pbest_x;       /* [R][n_part][D] personal-best positions */
     double* pbest_f;       /* [R][n_part] personal-best fitness */
     double* fit;           /* [R][n_part] fitness of x (written by fs_pso_evaluate) */
-    const double* box;     /* [R][5][2] search box of each run: (lo, hi) of M_c [Msun], t_c [s],
-                              sin(lat), lon [rad], e0; x maps linearly onto it */
-    double q;              /* mass ratio of every particle */
+    const double* box;     /* [R][D][2] search box of each run: (lo, hi) of M_c [Msun], t_c [s],
+                              sin(lat), lon [rad], e0 (and delta_mu in [0, 1)); x maps linearly onto it */
+    double q;              /* mass ratio of every particle (D = 5) */
     unsigned int* iter;    /* device iteration counter, used by fs_pso_step(iteration < 0) and the graph */
     int run0;              /* global index of run 0: the Philox counters use run0 + r, so a process that
                               holds runs [run0, run0 + R) of a larger search draws their numbers (0: default) */
+    int dims;              /* D: 5 (or 0) or 6 */
 } fs_swarm;
 
-/* Initial state: x ~ U[0,1)^5, v ~ U[-x, 1-x) (Sec. III.A), pbest_x = x,
+/* Initial state: x ~ U[0,1)^D, v ~ U[-x, 1-x) (Sec. III.A), pbest_x = x,
  * pbest_f = fit = -inf; random numbers from Philox4x32-10 with counter
  * (0xFFFFFFFF, particle, dim, run) and key = seed.  Asynchronous. */
 FS_API fs_status fs_pso_init(fs_plan* plan, const fs_swarm* swarm, uint64_t seed);
@@ -258,7 +264,7 @@ FS_API fs_status fs_pso_init(fs_plan* plan, const fs_swarm* swarm, uint64_t seed
 /* Fitness of the current positions: fit = F_sum / N_p (the paper's F-hat,
  * Eq. semi-cohF) with the segments of fs_fstat_batch (edges_dev as its
  * partition_edges_dev);
- * a particle outside [0,1]^5 is not evaluated and gets -inf ("let them fly").
+ * a particle outside [0,1]^D is not evaluated and gets -inf ("let them fly").
  * R * n_part must not exceed the plan's reservation if the call is captured. */
 FS_API fs_status fs_pso_evaluate(fs_plan* plan, const fs_swarm* swarm, const double* edges_dev, int N_p);
 
@@ -374,7 +380,8 @@ FS_API fs_status fs_mlp_train(fs_mlp* mlp, const float* X_dev, const float* t_de
  * (k, particle, dim, run | c << 20), so candidate 0 is the fs_pso_step move),
  * a network predicts their fitness, and each particle takes the candidate
  * with the highest prediction (lowest index among equals; candidates outside
- * [0,1]^5 rank last).  mlps: n_mlp >= 1 network batches holding ng networks
+ * [0,1]^5 rank last; a swarm with D = 6 gets FS_EUNSUPPORTED, the networks
+ * taking 5 inputs).  mlps: n_mlp >= 1 network batches holding ng networks
  * in all (in order); R must be a multiple of ng and the j-th network ranks
  * the candidates of runs [j R/ng, (j+1) R/ng) (one network per search box,
  * since positions are normalised to each run's box).  1 <= n_cand <= 64; candidates go through a network in chunks
@@ -386,7 +393,7 @@ FS_API fs_status fs_pso_step_screened(fs_plan* plan, const fs_swarm* swarm, fs_m
                                       double c1, double c2, double vmax);
 
 /* Ring buffer of (position, fitness) samples a search collects to train the
- * surrogate.  x: [cap][5] floats, f: [cap] floats, count: one unsigned
+ * surrogate.  x: [cap][D] floats (D of the swarms that append), f: [cap] floats, count: one unsigned
  * 64-bit counter of samples appended so far (all device memory, owned by
  * the caller; set count to 0 to start).  Sample i of an append of n goes to
  * slot (count + i) mod cap, and count advances by n. */

@@ -631,9 +631,13 @@ fs_status fs_particle_bands(fs_plan* p, const fs_params* params_dev, int B, int6
     return FS_OK;
 }
 
+// Dimensions of a swarm's search space: 5, or 6 with delta_mu free (0 reads as 5).
+static int swarm_dims(const fs_swarm* w) { return w->dims == 6 ? 6 : 5; }
+
 static fs_status check_swarm(const fs_swarm* w) {
     if (!w || w->R < 0 || w->n_part < 1 || !w->x || !w->v || !w->pbest_x || !w->pbest_f || !w->fit)
         return fail(FS_EINVAL, "swarm: need R >= 0, n_part >= 1 and non-NULL state arrays");
+    if (w->dims != 0 && w->dims != 5 && w->dims != 6) return fail(FS_EINVAL, "swarm: dims must be 5 or 6");
     if ((int64_t)w->R * w->n_part > 65535 * 8) return fail(FS_EINVAL, "swarm: R * n_part too large");
     if (w->run0 < 0 || (int64_t)w->run0 + w->R > (1 << 20))
         return fail(FS_EINVAL, "swarm: need 0 <= run0 and run0 + R <= 2^20 (the Philox run field)");
@@ -645,7 +649,8 @@ fs_status fs_pso_init(fs_plan* p, const fs_swarm* w, uint64_t seed) {
     if (!p) return fail(FS_EINVAL, "fs_pso_init: plan is NULL");
     fs_status st = check_swarm(w);
     if (st != FS_OK) return st;
-    cudaError_t e = fs::launch_pso_init(w->R, w->n_part, seed, w->x, w->v, w->pbest_x, w->pbest_f, w->fit, w->run0,
+    cudaError_t e = fs::launch_pso_init(w->R, w->n_part, swarm_dims(w), seed, w->x, w->v, w->pbest_x, w->pbest_f,
+                                        w->fit, w->run0,
                                         p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso init launch");
     if (w->iter && (e = cudaMemsetAsync(w->iter, 0, sizeof(unsigned int), p->stream)) != cudaSuccess)
@@ -662,7 +667,7 @@ fs_status fs_pso_evaluate(fs_plan* p, const fs_swarm* w, const double* edges_dev
     const int n = w->R * w->n_part;
     if (n == 0) return FS_OK;
     if ((st = ensure_workspace(p, n, Np)) != FS_OK) return st;
-    cudaError_t e = fs::launch_pso_map(w->R, w->n_part, w->x, w->box, w->q, p->pso_params, p->stream);
+    cudaError_t e = fs::launch_pso_map(w->R, w->n_part, swarm_dims(w), w->x, w->box, w->q, p->pso_params, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso map launch");
     if ((st = fs_fstat_batch(p, p->pso_params, n, edges_dev, Np, p->pso_F, nullptr)) != FS_OK) return st;
     if ((e = fs::launch_pso_fitness(n, p->pso_F, Np, w->fit, p->stream)) != cudaSuccess)
@@ -680,7 +685,7 @@ fs_status fs_pso_autotune(fs_plan* p, const fs_swarm* w, const double* edges_dev
     const int n = w->R * w->n_part;
     if (n == 0) return fail(FS_EINVAL, "fs_pso_autotune: empty swarm");
     if ((st = ensure_workspace(p, n, Np)) != FS_OK) return st;
-    cudaError_t e = fs::launch_pso_map(w->R, w->n_part, w->x, w->box, w->q, p->pso_params, p->stream);
+    cudaError_t e = fs::launch_pso_map(w->R, w->n_part, swarm_dims(w), w->x, w->box, w->q, p->pso_params, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pso map launch");
     return fs_plan_autotune(p, p->pso_params, n, edges_dev, Np, reps, variant_out, ms_out);
 }
@@ -694,7 +699,7 @@ fs_status fs_pso_step(fs_plan* p, const fs_swarm* w, uint64_t seed, int iteratio
     if (n_iter < 1 || !(vmax > 0.0)) return fail(FS_EINVAL, "fs_pso_step: need n_iter >= 1 and vmax > 0");
     if (iteration < 0 && !w->iter) return fail(FS_EINVAL, "fs_pso_step: iteration < 0 needs swarm->iter");
     const bool dev_iter = iteration < 0;
-    cudaError_t e = fs::launch_pso_step(w->R, w->n_part, seed, dev_iter ? w->iter : nullptr,
+    cudaError_t e = fs::launch_pso_step(w->R, w->n_part, swarm_dims(w), seed, dev_iter ? w->iter : nullptr,
                                         dev_iter ? 0u : (unsigned int)iteration, w0, w1, n_iter, c1, c2, vmax, w->x,
                                         w->v, w->pbest_x, w->pbest_f, w->fit, lbest_dev,
                                         dev_iter ? w->iter : nullptr, w->run0, p->stream);
@@ -709,6 +714,9 @@ fs_status fs_pso_step_screened(fs_plan* p, const fs_swarm* w, fs_mlp* const* mlp
     if (!p || !mlps || n_mlp < 1) return fail(FS_EINVAL, "fs_pso_step_screened: NULL plan or no network");
     fs_status st = check_swarm(w);
     if (st != FS_OK) return st;
+    if (swarm_dims(w) != 5)
+        return fail(FS_EUNSUPPORTED, "fs_pso_step_screened: the surrogate networks take 5 inputs; the swarm has 6 "
+                                     "dimensions");
     int ng = 0;
     for (int i = 0; i < n_mlp; i++) {
         if (!mlps[i]) return fail(FS_EINVAL, "fs_pso_step_screened: network %d is NULL", i);
@@ -812,7 +820,8 @@ fs_status fs_pso_record(fs_plan* p, const fs_swarm* w, const fs_sample_ring* rin
             rb.count[j] = rings[g0 + j].count;
             rb.cap[j] = rings[g0 + j].cap;
         }
-        cudaError_t e = fs::launch_pso_record(nr, per, w->x + (int64_t)g0 * per * 5, w->fit + (int64_t)g0 * per, rb,
+        const int D = swarm_dims(w);
+        cudaError_t e = fs::launch_pso_record(nr, per, D, w->x + (int64_t)g0 * per * D, w->fit + (int64_t)g0 * per, rb,
                                               p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "pso record launch");
     }

@@ -122,15 +122,15 @@ cudaError_t launch_mixed_probe(const Grid& g, const Tables& t, const float4* t32
                                const Segs& sg, const Partials& pa, int b, int64_t k0, int64_t k1, float* out,
                                cudaStream_t s);
 int mixed_probe_fields();
-cudaError_t launch_pso_init(int R, int Np, unsigned long long seed, double* x, double* v, double* pbx, double* pbf,
-                            double* fit, int run0, cudaStream_t s);
-cudaError_t launch_pso_map(int R, int Np, const double* x, const double* box, double q, ::fs_params* out,
+cudaError_t launch_pso_init(int R, int Np, int D, unsigned long long seed, double* x, double* v, double* pbx,
+                            double* pbf, double* fit, int run0, cudaStream_t s);
+cudaError_t launch_pso_map(int R, int Np, int D, const double* x, const double* box, double q, ::fs_params* out,
                            cudaStream_t s);
 cudaError_t launch_pso_fitness(int n, const double* F, int Np, double* fit, cudaStream_t s);
-cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsigned int* iter_dev, unsigned int iter_host,
-                            double w0, double w1, int n_iter, double c1, double c2, double vmax, double* x, double* v,
-                            double* pbx, double* pbf, const double* fit, int* lbest, unsigned int* iter_advance,
-                            int run0, cudaStream_t s);
+cudaError_t launch_pso_step(int R, int Np, int D, unsigned long long seed, const unsigned int* iter_dev,
+                            unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2, double vmax,
+                            double* x, double* v, double* pbx, double* pbf, const double* fit, int* lbest,
+                            unsigned int* iter_advance, int run0, cudaStream_t s);
 cudaError_t launch_pso_best(int R, int Np, const double* pbf, double* best_f, int* best_i, cudaStream_t s);
 cudaError_t launch_pso_screened(int R, int Np, int C, unsigned long long seed, const unsigned int* iter_dev,
                                 unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2,
@@ -145,7 +145,7 @@ struct RingBatch {
     unsigned long long* count[kRingBatch];
     int cap[kRingBatch];
 };
-cudaError_t launch_pso_record(int nr, int per, const double* x, const double* fit, const RingBatch& rb,
+cudaError_t launch_pso_record(int nr, int per, int D, const double* x, const double* fit, const RingBatch& rb,
                               cudaStream_t s);
 cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);
 cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,

@@ -67,29 +67,32 @@ __global__ void pso_init_kernel(int R, int Np, int D, unsigned long long seed, d
 
 // Map normalised positions to physical parameters in each run's box; a
 // particle outside [0, 1]^D gets NaN parameters (the F-statistic skips it).
-// box: [R][D][2] = (lo, hi) of (Mc [Msun], tc [s], sin(lat), lon [rad], e0).
-__global__ void pso_map_kernel(int R, int Np, const double* __restrict__ x, const double* __restrict__ box, double q,
-                               ::fs_params* out) {
+// box: [R][D][2] = (lo, hi) of (Mc [Msun], tc [s], sin(lat), lon [rad], e0)
+// and, with D = 6, of the dimensionless mass difference delta_mu = (m1 - m2)/M
+// (Sec. II.A's Theta_I), whose mass ratio is q = (1 + delta_mu)/(1 - delta_mu);
+// with D = 5 every particle takes the swarm's q.
+__global__ void pso_map_kernel(int R, int Np, int D, const double* __restrict__ x, const double* __restrict__ box,
+                               double q, ::fs_params* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= R * Np) return;
     const int r = i / Np;
-    const double* xi = x + (int64_t)i * 5;
-    const double* bx = box + (int64_t)r * 10;
+    const double* xi = x + (int64_t)i * D;
+    const double* bx = box + (int64_t)r * 2 * D;
     bool inside = true;
-    double y[5];
-#pragma unroll
-    for (int j = 0; j < 5; j++) {
+    double y[6];
+    for (int j = 0; j < D; j++) {
         inside = inside && xi[j] >= 0.0 && xi[j] <= 1.0;
         y[j] = bx[2 * j] + xi[j] * (bx[2 * j + 1] - bx[2 * j]);
     }
     ::fs_params p;
+    if (inside && D == 6 && !(y[5] >= 0.0 && y[5] < 1.0)) inside = false;   // delta_mu outside [0, 1)
     if (inside) {
         p.Mc = y[0];
         p.tc = y[1];
         p.lat = asin(fmin(1.0, fmax(-1.0, y[2])));
         p.lon = y[3];
         p.e0 = y[4];
-        p.q = q;
+        p.q = D == 6 ? (1.0 + y[5]) / (1.0 - y[5]) : q;
     } else {
         p.Mc = p.tc = p.lat = p.lon = p.e0 = p.q = __longlong_as_double(0x7ff8000000000000LL);
     }
@@ -265,19 +268,19 @@ __global__ void pso_best_kernel(int R, int Np, const double* __restrict__ pbf, d
     best_i[r] = bi;
 }
 
-cudaError_t launch_pso_init(int R, int Np, unsigned long long seed, double* x, double* v, double* pbx, double* pbf,
-                            double* fit, int run0, cudaStream_t s) {
-    const int64_t n = (int64_t)R * Np * 5;
+cudaError_t launch_pso_init(int R, int Np, int D, unsigned long long seed, double* x, double* v, double* pbx,
+                            double* pbf, double* fit, int run0, cudaStream_t s) {
+    const int64_t n = (int64_t)R * Np * D;
     if (n == 0) return cudaSuccess;
-    pso_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, Np, 5, seed, x, v, pbx, pbf, fit, run0);
+    pso_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, Np, D, seed, x, v, pbx, pbf, fit, run0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pso_map(int R, int Np, const double* x, const double* box, double q, ::fs_params* out,
+cudaError_t launch_pso_map(int R, int Np, int D, const double* x, const double* box, double q, ::fs_params* out,
                            cudaStream_t s) {
     const int n = R * Np;
     if (n == 0) return cudaSuccess;
-    pso_map_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, x, box, q, out);
+    pso_map_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, D, x, box, q, out);
     return cudaGetLastError();
 }
 
@@ -287,14 +290,14 @@ cudaError_t launch_pso_fitness(int n, const double* F, int Np, double* fit, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsigned int* iter_dev, unsigned int iter_host,
-                            double w0, double w1, int n_iter, double c1, double c2, double vmax, double* x, double* v,
-                            double* pbx, double* pbf, const double* fit, int* lbest, unsigned int* iter_advance,
-                            int run0, cudaStream_t s) {
+cudaError_t launch_pso_step(int R, int Np, int D, unsigned long long seed, const unsigned int* iter_dev,
+                            unsigned int iter_host, double w0, double w1, int n_iter, double c1, double c2, double vmax,
+                            double* x, double* v, double* pbx, double* pbf, const double* fit, int* lbest,
+                            unsigned int* iter_advance, int run0, cudaStream_t s) {
     const int n = R * Np;
     if (n == 0) return cudaSuccess;
-    pso_pbest_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, x, fit, pbx, pbf);
-    pso_move_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, 5, seed, iter_dev, iter_host, w0, w1, n_iter, c1, c2, vmax,
+    pso_pbest_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, D, x, fit, pbx, pbf);
+    pso_move_kernel<<<(n + 127) / 128, 128, 0, s>>>(R, Np, D, seed, iter_dev, iter_host, w0, w1, n_iter, c1, c2, vmax,
                                                     x, v, pbx, pbf, lbest, run0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !iter_advance) return e;
@@ -306,15 +309,14 @@ cudaError_t launch_pso_step(int R, int Np, unsigned long long seed, const unsign
 // NaN, into slot (count + i) mod cap of a ring; the counter advances after.
 // Sample append for up to kRingBatch rings in one launch: particle k of ring g
 // (the g-th block of `per` particles) goes to slot (count_g + k) mod cap_g.
-__global__ void pso_record_kernel(int nr, int per, const double* __restrict__ x, const double* __restrict__ fit,
-                                  RingBatch rb) {
+__global__ void pso_record_kernel(int nr, int per, int D, const double* __restrict__ x,
+                                  const double* __restrict__ fit, RingBatch rb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)nr * per) return;
     const int g = (int)(i / per), k = (int)(i % per);
     const int64_t j = (int64_t)((*rb.count[g] + (unsigned long long)k) % (unsigned long long)rb.cap[g]);
     float* rx = rb.x[g];
-#pragma unroll
-    for (int d = 0; d < 5; d++) rx[j * 5 + d] = (float)x[i * 5 + d];
+    for (int d = 0; d < D; d++) rx[j * D + d] = (float)x[i * D + d];
     const double f = fit[i];
     rb.f[g][j] = isfinite(f) ? (float)f : __int_as_float(0x7fc00000);
 }
@@ -324,11 +326,11 @@ __global__ void ring_advance_kernel(int nr, int per, RingBatch rb) {
     if (g < nr) *rb.count[g] += (unsigned long long)per;
 }
 
-cudaError_t launch_pso_record(int nr, int per, const double* x, const double* fit, const RingBatch& rb,
+cudaError_t launch_pso_record(int nr, int per, int D, const double* x, const double* fit, const RingBatch& rb,
                               cudaStream_t s) {
     if (nr <= 0 || per <= 0) return cudaSuccess;
     const int64_t n = (int64_t)nr * per;
-    pso_record_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(nr, per, x, fit, rb);
+    pso_record_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(nr, per, D, x, fit, rb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ring_advance_kernel<<<1, kRingBatch, 0, s>>>(nr, per, rb);

@@ -47,7 +47,8 @@ class fs_sample_ring(C.Structure):
 
 class fs_swarm(C.Structure):
     _fields_ = [("R", C.c_int), ("n_part", C.c_int), ("x", _vp), ("v", _vp), ("pbest_x", _vp),
-                ("pbest_f", _vp), ("fit", _vp), ("box", _vp), ("q", C.c_double), ("iter", _vp), ("run0", C.c_int)]
+                ("pbest_f", _vp), ("fit", _vp), ("box", _vp), ("q", C.c_double), ("iter", _vp), ("run0", C.c_int),
+                ("dims", C.c_int)]
 
 
 def load(build_if_missing: bool = True) -> C.CDLL:
@@ -425,32 +426,36 @@ def _edges_arg(edges, Np, device, stream=None):
 
 
 class Swarm:
-    """Device state of R PSO runs x n_part particles in [0,1]^5 (fs_swarm).
+    """Device state of R PSO runs x n_part particles in [0,1]^D (fs_swarm).
 
-    box: float64 [R, 5, 2] search boxes (lo, hi) of (M_c [Msun], t_c [s],
-    sin(lat), lon [rad], e0)."""
+    box: float64 [R, D, 2] search boxes (lo, hi) of (M_c [Msun], t_c [s],
+    sin(lat), lon [rad], e0) and, with dims = 6, delta_mu (the mass ratio is
+    then each particle's (1 + delta_mu)/(1 - delta_mu) instead of q)."""
 
-    def __init__(self, plan: "Plan", R: int, n_part: int, box, q: float = 1.0, run0: int = 0):
+    def __init__(self, plan: "Plan", R: int, n_part: int, box, q: float = 1.0, run0: int = 0, dims: int = 5):
         import torch
+        if dims not in (5, 6):
+            raise ValueError("dims must be 5 or 6")
         self.plan = plan
-        self.R, self.n_part = int(R), int(n_part)
+        self.R, self.n_part, self.dims = int(R), int(n_part), int(dims)
         dev = torch.device("cuda", torch.cuda.current_device())
         z = lambda *shape: torch.zeros(*shape, dtype=torch.float64, device=dev)
-        self.x = z(R, n_part, 5)
-        self.v = z(R, n_part, 5)
-        self.pbest_x = z(R, n_part, 5)
+        self.x = z(R, n_part, dims)
+        self.v = z(R, n_part, dims)
+        self.pbest_x = z(R, n_part, dims)
         self.pbest_f = z(R, n_part)
         self.fit = z(R, n_part)
-        self.box = torch.as_tensor(np.ascontiguousarray(box, dtype=np.float64)).to(dev).reshape(R, 5, 2).contiguous()
+        self.box = torch.as_tensor(np.ascontiguousarray(box, dtype=np.float64)).to(dev).reshape(R, dims, 2).contiguous()
         self.iter = torch.zeros(1, dtype=torch.int32, device=dev)
         self.best_f = z(R)
         self.best_i = torch.zeros(R, dtype=torch.int32, device=dev)
         self.c = fs_swarm(self.R, self.n_part, self.x.data_ptr(), self.v.data_ptr(), self.pbest_x.data_ptr(),
                           self.pbest_f.data_ptr(), self.fit.data_ptr(), self.box.data_ptr(), float(q),
-                          self.iter.data_ptr(), int(run0))
+                          self.iter.data_ptr(), int(run0), int(dims))
 
     def set_box(self, box):
-        self.box.copy_(torch_tensor(box).reshape(self.R, 5, 2))
+        import torch
+        self.box.copy_(torch.as_tensor(np.ascontiguousarray(box, dtype=np.float64)).reshape(self.R, self.dims, 2))
 
     def init(self, seed: int):
         _check(load().fs_pso_init(self.plan._h, C.byref(self.c), int(seed)))
@@ -582,24 +587,25 @@ class Graph:
 
 
 class SampleRing:
-    """Device ring of (position, fitness) training samples (fs_sample_ring)."""
+    """Device ring of (position, fitness) training samples (fs_sample_ring);
+    dims: the dimensions of the swarms that append to it."""
 
-    def __init__(self, cap: int, device=None):
+    def __init__(self, cap: int, device=None, dims: int = 5):
         import torch
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.cap = int(cap)
-        self.x = torch.zeros(self.cap, 5, dtype=torch.float32, device=dev)
+        self.x = torch.zeros(self.cap, dims, dtype=torch.float32, device=dev)
         self.f = torch.full((self.cap,), float("nan"), dtype=torch.float32, device=dev)
         self.count = torch.zeros(1, dtype=torch.int64, device=dev)
         self.c = fs_sample_ring(self.x.data_ptr(), self.f.data_ptr(), self.cap, self.count.data_ptr())
 
     @classmethod
-    def batch(cls, n: int, cap: int, device=None) -> list:
-        """n rings of one capacity laid end to end in one buffer (x: [n][cap][5],
+    def batch(cls, n: int, cap: int, device=None, dims: int = 5) -> list:
+        """n rings of one capacity laid end to end in one buffer (x: [n][cap][dims],
         f: [n][cap]), the layout a batch of n networks trains on."""
         import torch
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
-        x = torch.zeros(n, int(cap), 5, dtype=torch.float32, device=dev)
+        x = torch.zeros(n, int(cap), dims, dtype=torch.float32, device=dev)
         f = torch.full((n, int(cap)), float("nan"), dtype=torch.float32, device=dev)
         count = torch.zeros(n, dtype=torch.int64, device=dev)
         out = []

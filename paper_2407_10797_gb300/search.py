@@ -68,20 +68,36 @@ def paper_stages(n_iter: int = 2000) -> list[StageSpec]:
     ]
 
 
-def prior_box(prior: S.Prior) -> np.ndarray:
-    return np.array([[prior.Mc_lo, prior.Mc_hi], [prior.tc_lo, prior.tc_hi], [-1.0, 1.0], [0.0, 2.0 * np.pi],
-                     [0.0, prior.e0_hi]])
+def prior_box(prior: S.Prior, dmu_hi: float = 0.0) -> np.ndarray:
+    """Search box of the prior in search coordinates (M_c, t_c, sin(lat), lon,
+    e0), with a sixth row [0, dmu_hi] for delta_mu when dmu_hi > 0."""
+    rows = [[prior.Mc_lo, prior.Mc_hi], [prior.tc_lo, prior.tc_hi], [-1.0, 1.0], [0.0, 2.0 * np.pi],
+            [0.0, prior.e0_hi]]
+    if dmu_hi > 0.0:
+        rows.append([0.0, dmu_hi])
+    return np.array(rows)
+
+
+def q_of_dmu(dmu: float) -> float:
+    """Mass ratio m1/m2 of the dimensionless mass difference (m1 - m2)/M."""
+    return (1.0 + dmu) / (1.0 - dmu)
 
 
 def to_physical(xn: np.ndarray, box: np.ndarray, q: float = 1.0) -> np.ndarray:
-    """Normalised position [5] in box [5, 2] -> (M_c, t_c, lat, lon, e0, q)."""
+    """Normalised position [D] in box [D, 2] -> (M_c, t_c, lat, lon, e0, q);
+    with D = 6 the sixth coordinate is delta_mu and fixes q."""
     y = box[:, 0] + xn * (box[:, 1] - box[:, 0])
-    return np.array([y[0], y[1], math.asin(max(-1.0, min(1.0, y[2]))), y[3], y[4], q])
+    qq = q_of_dmu(y[5]) if len(y) == 6 else q
+    return np.array([y[0], y[1], math.asin(max(-1.0, min(1.0, y[2]))), y[3], y[4], qq])
 
 
-def to_normal_coords(p: np.ndarray) -> np.ndarray:
-    """(M_c, t_c, lat, lon, e0) -> the search coordinates (M_c, t_c, sin(lat), lon, e0)."""
-    return np.array([p[0], p[1], math.sin(p[2]), p[3], p[4]])
+def to_normal_coords(p: np.ndarray, dims: int = 5) -> np.ndarray:
+    """(M_c, t_c, lat, lon, e0, q) -> the search coordinates (M_c, t_c,
+    sin(lat), lon, e0), with delta_mu = (q - 1)/(q + 1) sixth when dims = 6."""
+    c = [p[0], p[1], math.sin(p[2]), p[3], p[4]]
+    if dims == 6:
+        c.append((p[5] - 1.0) / (p[5] + 1.0))
+    return np.array(c)
 
 
 def box_around(center: np.ndarray, widths, prior: np.ndarray) -> np.ndarray:
@@ -89,7 +105,7 @@ def box_around(center: np.ndarray, widths, prior: np.ndarray) -> np.ndarray:
     shifted to stay inside the prior; None keeps the prior range."""
     b = prior.copy()
     for j, wj in enumerate(widths):
-        if wj is None:
+        if wj is None or j >= len(b):
             continue
         lo, hi = center[j] - 0.5 * wj, center[j] + 0.5 * wj
         if j == 3:   # longitude is periodic: no clipping
@@ -157,9 +173,16 @@ class HierarchicalSearch:
                  checkpoint_dir: str | None = None, c1: float = 2.0, c2: float = 2.0, vmax: float = 0.5,
                  bounds: np.ndarray | None = None, surrogate: SurrogateSpec | None = None,
                  autotune: bool | None = None, use_graphs: bool = True, record_history: bool = False,
-                 comm: "Comm | None" = None):
-        """bounds: optional [5, 2] search bounds overriding the prior's (a zero
-        width pins a coordinate).  autotune: time the fused kernel's launch
+                 comm: "Comm | None" = None, dmu_hi: float = 0.0, progress_every: int = 0):
+        """bounds: optional [D, 2] search bounds overriding the prior's (a zero
+        width pins a coordinate).  dmu_hi > 0: search delta_mu in [0, dmu_hi]
+        as a sixth coordinate (the paper's [0, 0.9], Table I), its full range
+        kept in every stage as the paper does (Sec. III.B, stage 3); q is then
+        each particle's own.  The surrogate needs 5 coordinates.
+        progress_every > 0: every that many iterations of a stage, append
+        (stage, iteration, best F-hat, its physical parameters) over all of
+        this process's runs to `progress` (a small device-to-host read; the
+        captured iterations replay in chunks of that length).  autotune: time the fused kernel's launch
         variants on each stage's first swarm and use the fastest; None = only
         for FS_MIXED plans, whose variants give bitwise-equal F (FP64 variants
         differ by rounding, which can steer a PSO run differently).  use_graphs:
@@ -169,6 +192,10 @@ class HierarchicalSearch:
         over processes (Comm), one GPU each; None = this process runs all."""
         self.plan = plan
         self.prior = prior
+        self.dmu_hi = float(dmu_hi)
+        self.dims = 6 if self.dmu_hi > 0.0 else 5
+        if self.dims == 6 and surrogate is not None:
+            raise ValueError("the surrogate networks take 5 coordinates: no surrogate with delta_mu free")
         self.bounds = None if bounds is None else np.asarray(bounds, dtype=np.float64)
         self.stages = stages if stages is not None else default_stages()
         self.n_boxes, self.runs_per_box, self.n_part = n_boxes, runs_per_box, n_part
@@ -184,11 +211,13 @@ class HierarchicalSearch:
         self.use_graphs = use_graphs
         self.record_history = record_history
         self.comm = comm
+        self.progress_every = int(progress_every)
+        self.progress: list = []
 
     # ---------------------------------------------------------------- boxes
     def stage_boxes(self, i: int) -> np.ndarray:
         spec = self.stages[i]
-        pb = prior_box(self.prior) if self.bounds is None else self.bounds.copy()
+        pb = prior_box(self.prior, self.dmu_hi) if self.bounds is None else self.bounds.copy()
         if spec.rule == "split_tc":
             u = S.uniforms(self.seed, 0x53504C54, self.n_boxes)           # "SPLT"
             w = -np.log1p(-u)                                              # Dirichlet(1) via exponentials
@@ -199,10 +228,10 @@ class HierarchicalSearch:
             return boxes
         prev = self.results[i - 1]
         if spec.rule == "around":
-            centers = [to_normal_coords(np.array(p)) for p in prev.winners]
+            centers = [to_normal_coords(np.array(p), self.dims) for p in prev.winners]
         elif spec.rule == "around_best_mirror":
             best = np.array(prev.winners[int(np.argmax(prev.winner_f))])
-            c = to_normal_coords(best)
+            c = to_normal_coords(best, self.dims)
             m = c.copy()
             m[2] = -m[2]                                                   # theta -> pi - theta
             centers = [c if k % 2 == 0 else m for k in range(self.n_boxes)]
@@ -256,16 +285,24 @@ class HierarchicalSearch:
         run_boxes = np.repeat(boxes[k0:k1], self.runs_per_box, axis=0)
         stage_seed = (self.seed << 8) + i
         with torch.cuda.stream(self.plan.stream):
-            sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q, run0=k0 * self.runs_per_box)
+            sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q, run0=k0 * self.runs_per_box,
+                             dims=self.dims)
             sw.init(stage_seed)
             variant = sw.autotune(spec.Np, reps=2)[0] if self.autotune else self.plan.get_variant(spec.Np)
             if self.surrogate is None:
                 sw.graph_build(spec.Np, stage_seed, n_iter=spec.n_iter, w0=spec.w0, w1=spec.w1, c1=self.c1,
                                c2=self.c2, vmax=self.vmax)
-                sw.graph_run(spec.n_iter - 1)      # the graph does evaluate + step
+                done = 0
+                chunk = self.progress_every if self.progress_every > 0 else spec.n_iter - 1
+                while done < spec.n_iter - 1:      # the graph does evaluate + step
+                    k = min(chunk, spec.n_iter - 1 - done)
+                    sw.graph_run(k)
+                    done += k
+                    if self.progress_every > 0:
+                        self._note_progress(i, done, sw, run_boxes)
                 sw.graph_free()
             else:
-                self._run_screened(sw, spec, stage_seed, i, k0, nb)
+                self._run_screened(sw, spec, stage_seed, i, k0, nb, run_boxes)
             sw.evaluate(spec.Np)               # fitness of the final positions
             sw.step(stage_seed, -1, w0=spec.w0, w1=spec.w1, n_iter=spec.n_iter)   # folds them into pbest
             best_f, best_i = sw.best()
@@ -280,7 +317,17 @@ class HierarchicalSearch:
             wf.append(float(bf[r]))
         return winners, wf, int(variant)
 
-    def _run_screened(self, sw, spec: StageSpec, stage_seed: int, stage: int, k0: int = 0, nb: int | None = None):
+    def _note_progress(self, stage: int, it: int, sw, run_boxes):
+        """Best personal best over the swarm's runs after `it` iterations."""
+        best_f, best_i = sw.best()
+        bf = best_f.cpu().numpy()
+        bi = best_i.cpu().numpy()
+        r = int(np.argmax(bf))
+        x = sw.pbest_x[r, int(bi[r])].cpu().numpy()
+        self.progress.append((stage, it, float(bf[r]), to_physical(x, run_boxes[r], self.q).tolist()))
+
+    def _run_screened(self, sw, spec: StageSpec, stage_seed: int, stage: int, k0: int = 0, nb: int | None = None,
+                      run_boxes=None):
         """n_iter - 1 iterations of evaluate + record + (screened) step with one
         network and one sample ring per search box: positions are normalised
         to each run's box, so the runs of a box share a landscape and the
@@ -330,6 +377,8 @@ class HierarchicalSearch:
                 sw.step(stage_seed, -1, **step_kw)
             if self.record_history:
                 hist.append(sw.pbest_f.max())
+            if self.progress_every > 0 and run_boxes is not None and (it + 1) % self.progress_every == 0:
+                self._note_progress(stage, it + 1, sw, run_boxes)
         if graphs:
             for gr in graphs:
                 gr.close()

@@ -51,10 +51,18 @@ def test_init_matches_oracle(fst, plan):
     assert np.all(np.isneginf(sw.pbest_f.cpu().numpy()))
 
 
-def test_steps_bit_exact_with_oracle(fst, plan):
-    """Random fitness arrays with NaN, -inf and ties; several iterations."""
+def dmu_box(R):
+    """The unit box with delta_mu in the paper's [0, 0.9] as a sixth coordinate."""
+    b = unit_box(R)
+    return np.concatenate([b, np.tile(np.array([[0.0, 0.9]]), (R, 1, 1))], axis=1)
+
+
+@pytest.mark.parametrize("dims", [5, 6])
+def test_steps_bit_exact_with_oracle(fst, plan, dims):
+    """Random fitness arrays with NaN, -inf and ties; several iterations; the
+    5-D space and the 6-D one with delta_mu free."""
     R, Np, seed, n_iter = 4, 40, 99, 7
-    sw = fst.Swarm(plan, R, Np, unit_box(R))
+    sw = fst.Swarm(plan, R, Np, unit_box(R) if dims == 5 else dmu_box(R), dims=dims)
     sw.init(seed)
     torch.cuda.synchronize()
     x = sw.x.cpu().numpy().copy()
@@ -165,3 +173,39 @@ def test_graph_reads_its_own_edges_after_other_calls(fst, plan):
     for name in ("x", "v", "pbest_x", "pbest_f", "fit"):
         assert torch.equal(getattr(eager, name), getattr(graphed, name)), name
     assert plan.check() == 0
+
+
+def test_six_dimensional_swarm_maps_delta_mu_to_the_mass_ratio(fst, plan):
+    """With delta_mu free, a particle's fitness is F-hat at the mass ratio
+    q = (1 + delta_mu)/(1 - delta_mu) of its sixth coordinate (Sec. II.A's
+    dimensionless mass difference), and the init draws the oracle's 6-D
+    positions."""
+    R, Np = 2, 40
+    g = plan.grid
+    box = dmu_box(R)
+    box[:, 1] = [0.3 * g.T_obs, 1.5 * g.T_obs]
+    sw = fst.Swarm(plan, R, Np, box, dims=6)
+    with torch.cuda.stream(plan.stream):
+        sw.init(11)
+        sw.evaluate(4)
+    torch.cuda.synchronize()
+    xo, vo = O.pso_init(R, Np, 6, 11)
+    assert np.array_equal(sw.x.cpu().numpy(), xo) and np.array_equal(sw.v.cpu().numpy(), vo)
+    x = sw.x.cpu().numpy()
+    y = box[:, None, :, 0] + x * (box[:, None, :, 1] - box[:, None, :, 0])
+    dmu = y[..., 5]
+    P = np.stack([y[..., 0], y[..., 1], np.arcsin(np.clip(y[..., 2], -1, 1)), y[..., 3], y[..., 4],
+                  (1.0 + dmu) / (1.0 - dmu)], axis=-1).reshape(-1, 6)
+    with torch.cuda.stream(plan.stream):
+        F, _ = plan.fstat(torch.from_numpy(P).cuda(), 4)
+    torch.cuda.synchronize()
+    fit = sw.fit.cpu().numpy()
+    Fh = F.cpu().numpy().reshape(R, Np) / 4
+    inside = ~np.isneginf(fit)
+    assert inside.sum() > 40 and np.any(np.abs(dmu - 0.45) > 0.3)
+    assert np.allclose(fit[inside], Fh[inside], rtol=1e-6, atol=0)
+    # the screened step needs the networks' 5 inputs
+    with pytest.raises(fst.FstatError) as ei:
+        net = fst.MLP(64, max_batch=512, seed=0, stream=plan.stream)
+        sw.step_screened(net, 4, 11, 0)
+    assert ei.value.status == fst.FS_EUNSUPPORTED

@@ -113,3 +113,26 @@ def test_checkpoints_resume_and_reject_another_search(tmp_path):
         make(seed=9, ckpt=str(tmp_path)).run(extrinsic=False)
     with pytest.raises(ValueError):
         make(stages=search.default_stages(11), ckpt=str(tmp_path)).run(extrinsic=False)
+
+
+def test_delta_mu_free_search_coordinates_and_boxes():
+    """delta_mu as a sixth search coordinate: prior box [0, 0.9] (Table I),
+    q = (1 + delta_mu)/(1 - delta_mu) and back, and every stage keeps
+    delta_mu's full range (Sec. III.B stage 3) while narrowing the others."""
+    pb = search.prior_box(PRIOR, 0.9)
+    assert pb.shape == (6, 2) and list(pb[5]) == [0.0, 0.9]
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        x = rng.uniform(0, 1, 6)
+        p = search.to_physical(x, pb)
+        dmu = 0.9 * x[5]
+        assert p[5] == pytest.approx((1 + dmu) / (1 - dmu), rel=1e-14)
+        eta = p[5] / (1 + p[5]) ** 2
+        assert eta == pytest.approx((1 - dmu * dmu) / 4, rel=1e-13)
+        y = search.to_normal_coords(p, 6)
+        assert np.allclose(y, pb[:, 0] + x * (pb[:, 1] - pb[:, 0]), rtol=1e-12, atol=1e-12)
+    widths = (0.3, 0.004 * S.YEAR_S, 0.4, 0.4, 0.006)
+    c = search.to_normal_coords(search.to_physical(np.full(6, 0.5), pb), 6)
+    b = search.box_around(c, widths, pb)
+    assert b.shape == (6, 2) and list(b[5]) == [0.0, 0.9]
+    assert b[0, 1] - b[0, 0] == pytest.approx(0.3)
