@@ -605,11 +605,13 @@ def run_gpu(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
-def run_mlp_profile_case():
-    """The surrogate batch of a search stage (16 boxes, width 256): two
-    training rounds of 20 Adam steps on 2048 rows per network and two forward
-    passes over 5120 candidate rows per network (8 runs x 40 particles x 16
-    candidates), seeded synthetic inputs in [0, 1]^5."""
+def run_mlp_profile_case(tensor_path: int = 0, reps: int = 2):
+    """The surrogate batch of a search stage (16 boxes, width 256): training
+    rounds of 20 Adam steps on 2048 rows per network and forward passes over
+    5120 candidate rows per network (8 runs x 40 particles x 16 candidates),
+    seeded synthetic inputs in [0, 1]^5; tensor_path 0 = mma.sync GEMMs, 1 =
+    tcgen05 (TMA-fed where both operands are K-contiguous).  After one untimed
+    round, `reps` rounds are timed with CUDA events on the networks' stream."""
     import torch
     from paper_2407_10797_gb300 import fstat
     G, W = 16, 256
@@ -619,14 +621,26 @@ def run_mlp_profile_case():
     t = (X[..., 0] * 3 - X[..., 1] ** 2).contiguous() * 10
     Xf = torch.rand(G, 5120, 5, generator=gen).cuda()
     torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     with torch.cuda.stream(s):
         net = fstat.MLP(W, max_batch=4096, seed=1, stream=s, groups=G)
-        for _ in range(2):
+        net.set_tensor_path(bool(tensor_path))
+        losses = net.train(X, t, 20, 1e-3)
+        y = net.forward(Xf)
+        ev[0].record(s)
+        for _ in range(reps):
             losses = net.train(X, t, 20, 1e-3)
+        ev[1].record(s)
+        ev[2].record(s)
+        for _ in range(reps):
             y = net.forward(Xf)
+        ev[3].record(s)
     s.synchronize()
+    ok = net.tensor_status()
     print(json.dumps({"profile_case": "surrogate batch, 16 networks of width 256, 20 Adam steps on 2048 rows, "
-                                      "forward of 5120 rows", "loss_last": float(losses[-1].mean().item()),
+                                      "forward of 5120 rows", "tensor_path": "tcgen05" if tensor_path else "mma.sync",
+                      "train_round_ms": ev[0].elapsed_time(ev[1]) / reps, "forward_ms": ev[2].elapsed_time(ev[3]) / reps,
+                      "tensor_status_ok": bool(ok), "loss_last": float(losses[-1].mean().item()),
                       "y_mean": float(y.mean().item())}))
     net.close()
 
@@ -638,7 +652,7 @@ def run_profile_case(args):
     import torch
     from paper_2407_10797_gb300 import fstat
     if args.profile_case == "mlp":
-        run_mlp_profile_case()
+        run_mlp_profile_case(tensor_path=1 if args.variant == 1 else 0, reps=max(args.steps, 2))
         return
     w, g, psd, noise, P, inj = workload_inputs(0)
     mode = fstat.FS_MIXED if args.profile_case == "mixed" else fstat.FS_FP64

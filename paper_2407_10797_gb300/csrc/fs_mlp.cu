@@ -14,6 +14,7 @@
 // training pass covers all G in one launch, network g's rows and parameters
 // sitting at fixed strides, with the same per-element summation order as a
 // network run alone.
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -237,6 +238,10 @@ constexpr int TM = 128;          // tile rows = MMA M
 constexpr int TK = 64;           // K per stage
 constexpr int THREADS = 128;
 constexpr long long kMaxPolls = 1LL << 24;
+// The last wait before the tensor memory is freed, after a wait has already
+// run out: far longer, so that the MMAs of a slow but live CTA finish before
+// the columns they write are released.
+constexpr long long kMaxPollsDrain = 1LL << 28;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -270,9 +275,9 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, long long polls = kMaxPolls) {
     const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < kMaxPolls; i++) {
+    for (long long i = 0; i < polls; i++) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -391,10 +396,11 @@ gemm_tc5_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const 
         issued = i + 1;
     }
     // the last committed stage (MMAs complete in order); waited for even after a
-    // failure, so that no MMA is still writing when the TMEM is freed
+    // failure -- then with the much longer drain bound -- so that no MMA is
+    // still writing when the TMEM is freed
     if (issued > 0) {
         const int st = (issued - 1) & 1;
-        if (!wait_bar(&bars[st], phase[st])) failed = 1;
+        if (!wait_bar(&bars[st], phase[st], failed ? kMaxPollsDrain : kMaxPolls)) failed = 1;
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -456,6 +462,248 @@ gemm_tc5_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
+// ---------------------------------------------------------------------------
+// The same product with both operands K-contiguous (the forward layers: A =
+// activations [M][K], B = weights [N][K]) fed by the tensor memory accelerator.
+// A 3-D tensor map (k, row, network) per operand; per stage of 64 k, thread 0
+// copies eight 8-wide k slices of the 128-row A tile and of the NT-row B tile
+// with cp.async.bulk.tensor, so that k slice j lands at j * rows * 16 bytes and
+// row r of a slice at r * 16: core matrices (8 rows x 16 bytes) 128 bytes
+// apart along the rows and rows * 16 bytes apart along k -- the same K-major
+// no-swizzle form as above with the two offsets of the descriptor set to
+// those strides.  Rows and k beyond the operands are filled with zeros by the
+// copy unit.  A ring of kStagesT stages: "full" barriers carry the copies'
+// bytes, thread 32 waits on them and issues the MMAs, whose commit frees the
+// stage on its "empty" barrier and, after the last stage, completes "done",
+// which every thread waits for before the epilogue.  Every wait is bounded;
+// after a failure the last wait on "done" uses the drain bound, and thread 0
+// waits for its copies in flight before the CTA leaves.
+// ---------------------------------------------------------------------------
+constexpr int kStagesT = 2;
+
+__device__ __forceinline__ uint64_t sdesc_t(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+template <int EPI, int NT>
+__global__ void __launch_bounds__(THREADS)
+gemm_tma_kernel(int M, int N, int K, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, void* out, int ldo, int* err,
+                GS gs) {
+    constexpr int A_BYTES = TM * TK * 2, B_BYTES = NT * TK * 2, STAGE = A_BYTES + B_BYTES;
+    constexpr uint32_t NCOLS = NT < 32 ? 32 : NT;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kStagesT], empty[kStagesT], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * NT;
+    const int zg = blockIdx.z;
+    if (bias) bias += zg * gs.bias;
+    if (mask) mask += zg * gs.mask;
+    if (EPI == EPI_F32) out = static_cast<float*>(out) + zg * gs.out;
+    else out = static_cast<bf16*>(out) + zg * gs.out;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kStagesT; st++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[st])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const int nk = (K + TK - 1) / TK;
+    int issued = 0;   // thread 0: stages whose copies were issued
+
+    if (threadIdx.x == 0) {
+        // copies: stage i into slot i % kStagesT once the MMAs of stage i - kStagesT have released it
+        for (int i = 0; i < nk; i++) {
+            const int st = i % kStagesT;
+            if (i >= kStagesT && !wait_bar(&empty[st], (uint32_t)((i / kStagesT) - 1) & 1u)) {
+                failed = 1;
+                break;
+            }
+            if (*(volatile int*)&failed) break;
+            unsigned char* a_t = smem + st * STAGE;
+            unsigned char* b_t = a_t + A_BYTES;
+            bar_arrive_tx(&full[st], (uint32_t)STAGE);
+#pragma unroll
+            for (int j = 0; j < TK / 8; j++) {
+                tma_load_3d(a_t + j * TM * 16, &mapA, i * TK + 8 * j, m0, zg, &full[st]);
+                tma_load_3d(b_t + j * NT * 16, &mapB, i * TK + 8 * j, n0, zg, &full[st]);
+            }
+            issued = i + 1;
+        }
+    } else if (threadIdx.x == 32) {
+        // MMAs: four K = 16 steps per stage, each two k slices (2 x rows x 16 bytes) further on
+        for (int i = 0; i < nk; i++) {
+            const int st = i % kStagesT;
+            if (*(volatile int*)&failed || !wait_bar(&full[st], (uint32_t)(i / kStagesT) & 1u)) {
+                failed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ab = smem_u32(smem + st * STAGE), bb = ab + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; kk++)
+                mma(tmem, sdesc_t(ab + kk * 2 * TM * 16, TM * 16, 128), sdesc_t(bb + kk * 2 * NT * 16, NT * 16, 128),
+                    idesc(TM, NT), (i > 0 || kk > 0) ? 1u : 0u);
+            commit(&empty[st]);
+        }
+        commit(&done);   // arrives when every MMA issued above has completed (at once if none was)
+    }
+    // every thread: the accumulators are final (or, after a failure, no MMA is still running)
+    if (!wait_bar(&done, 0u, kMaxPolls) && !wait_bar(&done, 0u, kMaxPollsDrain)) failed = 1;
+    if (threadIdx.x == 0) {
+        // the last copy issued into each slot has landed before the CTA leaves (after a failure
+        // some were never consumed)
+        for (int st = 0; st < kStagesT && st < issued; st++) {
+            const int last = st + ((issued - 1 - st) / kStagesT) * kStagesT;
+            if (!wait_bar(&full[st], (uint32_t)(last / kStagesT) & 1u, kMaxPollsDrain)) failed = 1;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!failed) {
+        float* stg = reinterpret_cast<float*>(smem);
+        constexpr int LDS = NT + 4;
+        const int row = warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4*>(stg + row * LDS + c0 + j) =
+                    make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                __uint_as_float(r[j + 3]));
+        }
+        __syncthreads();
+        constexpr int QPR = NT / 4;
+        for (int q = threadIdx.x; q < TM * QPR; q += THREADS) {
+            const int rr = q / QPR, cc = (q % QPR) * 4;
+            const int m = m0 + rr, n = n0 + cc;
+            if (m >= M) continue;
+            const float4 v4 = *reinterpret_cast<const float4*>(stg + rr * LDS + cc);
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (n + j >= N) break;
+                if (EPI == EPI_BIAS_RELU_BF16) {
+                    static_cast<bf16*>(out)[(int64_t)m * ldo + n + j] = __float2bfloat16(fmaxf(v[j] + bias[n + j], 0.f));
+                } else if (EPI == EPI_MASK_BF16) {
+                    const float a = __bfloat162float(mask[(int64_t)m * ldm + n + j]);
+                    static_cast<bf16*>(out)[(int64_t)m * ldo + n + j] = __float2bfloat16(a > 0.f ? v[j] : 0.f);
+                } else {
+                    static_cast<float*>(out)[(int64_t)m * ldo + n + j] = v[j];
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+// cuTensorMapEncodeTiled from the driver (fetched once; the library links only the runtime).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map of G operands [rows][K] (k contiguous, row stride ld, operand
+// stride `stride` elements), boxes of 8 k x box_rows rows x 1 operand.
+static bool make_map(CUtensorMap* map, const bf16* base, int K, int rows, int ld, int G, int64_t stride,
+                     int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const int64_t gstride = G > 1 ? stride : (int64_t)rows * ld;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)G};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)gstride * 2};
+    cuuint32_t box[3] = {8u, (cuuint32_t)box_rows, 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Both operands K-contiguous: the TMA-fed kernel.  cudaErrorNotSupported when
+// a tensor map cannot describe the operands (the caller then takes the
+// register-copied tcgen05 kernel).
+template <int EPI, int NT>
+cudaError_t launch_tma(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias,
+                       const bf16* mask, int ldm, void* out, int ldo, int G, const GS& gs, int* err, cudaStream_t s) {
+    constexpr int SMEM0 = kStagesT * (TM * TK * 2 + NT * TK * 2), STAGING = TM * (NT + 4) * 4;
+    constexpr int SMEM = SMEM0 > STAGING ? SMEM0 : STAGING;
+    if (K <= 0 || K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || gs.splits != 1 ||
+        (G > 1 && (gs.a < (int64_t)M * lda || gs.b < (int64_t)N * ldb || gs.a % 8 != 0 || gs.b % 8 != 0)) ||
+        (reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u))
+        return cudaErrorNotSupported;
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, A, K, M, lda, G, gs.a, TM) || !make_map(&mB, B, K, N, ldb, G, gs.b, NT))
+        return cudaErrorNotSupported;
+    static bool attr[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        if ((e = cudaFuncSetAttribute(gemm_tma_kernel<EPI, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM)) !=
+            cudaSuccess)
+            return e;
+        attr[dev] = true;
+    }
+    dim3 grid((unsigned)((N + NT - 1) / NT), (unsigned)((M + TM - 1) / TM), (unsigned)G);
+    gemm_tma_kernel<EPI, NT><<<grid, THREADS, SMEM, s>>>(M, N, K, mA, mB, bias, mask, ldm, out, ldo, err, gs);
+    return cudaGetLastError();
+}
+
 template <bool TA, bool TB, int EPI, int NT>
 cudaError_t launch(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias,
                    const bf16* mask, int ldm, void* out, int ldo, int G, const GS& gs, int kchunk, int* err,
@@ -487,6 +735,14 @@ static cudaError_t gemm(int M, int N, int K, const bf16* A, int lda, const bf16*
     if (M <= 0 || N <= 0 || G <= 0) return cudaSuccess;
     gs.splits = 1;
     const int kc = K > 0 ? K : 1;
+    if (tc_err && !TA && !TB && N % 64 == 0) {
+        // both operands K-contiguous: copies by the tensor memory accelerator
+        const cudaError_t e =
+            N % 128 == 0 && (int64_t)((M + 127) / 128) * (N / 128) * G >= 152
+                ? tc5::launch_tma<EPI, 128>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, G, gs, tc_err, s)
+                : tc5::launch_tma<EPI, 64>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, G, gs, tc_err, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     if (tc_err && N % 128 == 0 && (int64_t)((M + 127) / 128) * (N / 128) * G >= 152)
         return tc5::launch<TA, TB, EPI, 128>(M, N, K, A, lda, B, ldb, bias, mask, ldm, out, ldo, G, gs, kc, tc_err,
                                              s);
