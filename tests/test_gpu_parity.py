@@ -256,3 +256,28 @@ def test_paper_workload_full_size_sampled(fst):
         assert np.all(np.isfinite(Fg)) and np.all(Fg >= 0)
         Fo, Fpo = O.fstat_batch(P[idx], m, d, psd, Np)
         assert_parity(Fg[idx], Fpg[idx], Fo, Fpo, Np, TOL64)
+
+
+def test_set_data_with_a_frequency_grid(fst):
+    """fs_plan_set_data's f_grid: the plan's own uniform grid (computed here
+    in another order, so a few ulp apart) is accepted and gives the same F;
+    a grid with one bin moved by a millionth of a bin is refused with
+    FS_EUNSUPPORTED and loads nothing."""
+    g = S.tiny_grid(n=5000, f_min=0.02, stride=4)
+    d, psd = make_data(g, 7)
+    P = in_band_params(g, 16, 3, 0.02 + 2500 * g.df)
+    plan = fst.Plan.from_grid(g)
+    dt, pt = torch.from_numpy(d).cuda(), torch.from_numpy(psd).cuda()
+    plan.set_data(dt, pt)
+    F0 = plan.fstat(torch.from_numpy(P).cuda(), 4)[0].clone()
+    f = torch.from_numpy(g.f_min + g.df * np.arange(g.n, dtype=np.float64)).cuda()
+    plan.set_data(dt, pt, f_grid=f)
+    F1 = plan.fstat(torch.from_numpy(P).cuda(), 4)[0]
+    assert torch.equal(F0, F1)
+    bad = f.clone()
+    bad[1234] += 1e-6 * g.df
+    with pytest.raises(fst.FstatError) as ei:
+        plan.set_data(2.0 * dt, pt, f_grid=bad)
+    assert ei.value.status == fst.FS_EUNSUPPORTED
+    assert torch.equal(plan.fstat(torch.from_numpy(P).cuda(), 4)[0], F0)   # the earlier data stay loaded
+    plan.close()
