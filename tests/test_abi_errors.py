@@ -72,3 +72,26 @@ def test_noalloc_limits_are_checked_first(L):
     assert L.fs_fstat_batch_noalloc(1000, 0.01, 1e-6, 1e7, F, F, F, 4, None, 65, F, None, None) == EINVAL
     assert L.fs_fstat_batch_noalloc(1000, 0.01, 1e-6, 1e7, None, F, F, 4, None, 8, F, None, None) == EINVAL
     assert L.fs_fstat_batch_noalloc(1000, 0.01, 1e-6, 1e7, F, F, F, 0, None, 8, F, None, None) == 0   # B = 0
+
+
+def test_channel_sets_probe_and_check_refuse_bad_arguments(L):
+    h = C.c_void_p()
+    assert L.fs_plan_create_tdi(C.byref(h), 100, 0.01, 1e-6, 1e7, 0, 7, None) == EINVAL
+    assert h.value is None and "fs_plan_create_tdi" in err(L) and "channel set" in err(L)
+    assert L.fs_plan_create_tdi(C.byref(h), 0, 0.01, 1e-6, 1e7, 0, 1, None) == EINVAL   # the grid checks apply too
+    assert L.fs_plan_channels(None) == -1
+    assert L.fs_plan_check(None, None) == EINVAL and "fs_plan_check" in err(L)
+    assert L.fs_mixed_probe(None, None, 1, None, 1, 0, 0, 10, None) == EINVAL and "fs_mixed_probe" in err(L)
+    assert L.fs_plan_set_data(None, None, None, None) == EINVAL and "fs_plan_set_data" in err(L)
+
+
+def test_swarm_dimensions_are_checked(L):
+    """A swarm declares 5 or 6 dimensions (0 reads as 5); anything else is
+    refused before any launch (the plan is checked first, so a fake non-NULL
+    plan handle is never dereferenced on this path)."""
+    buf = (C.c_double * 64)()
+    p = C.cast(buf, C.c_void_p).value
+    for dims, ok in ((7, False), (4, False), (-1, False)):
+        sw = fstat.fs_swarm(1, 1, p, p, p, p, p, p, 1.0, None, 0, dims)
+        assert L.fs_pso_best(C.c_void_p(8), C.byref(sw), C.c_void_p(p), C.c_void_p(p)) == EINVAL
+        assert "dims" in err(L)
