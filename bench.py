@@ -401,6 +401,16 @@ class ModeRun:
             sw.graph_run(1)
             host["fit"][i].copy_(sw.fit, non_blocking=True)
 
+    def step_fstat_host(self, host):
+        """fs_fstat_batch as a caller with host data makes it: the batch's
+        parameters copied from pinned host memory, one call per N_p, the F
+        values read back into pinned host memory."""
+        P = host["P_dev"]
+        P.copy_(host["P"], non_blocking=True)
+        for i, Np in enumerate(NP_LIST):
+            F, _ = self.plan.fstat(P, Np, F=host["F_dev"][i], want_parts=False)
+            host["F"][i].copy_(F, non_blocking=True)
+
     def census(self, P_dev):
         """Anchor-mode bin counts of the prior draw per N_p (outside any timing)."""
         with self.torch.cuda.stream(self.stream):
@@ -521,6 +531,29 @@ def run_gpu(args, world, rank, local):
         barrier(world)
     e2e_ms = allmax(world, e0.elapsed_time(e1))
     e2e_value = total_pbins / (e2e_ms / 1e3)
+    # ---- end to end through fs_fstat_batch with host parameters and results
+    hostf = {"P": torch.from_numpy(P0).pin_memory(), "P_dev": torch.empty(P0.shape, dtype=torch.float64, device="cuda"),
+             "F": torch.empty(len(NP_LIST), B, dtype=torch.float64).pin_memory(),
+             "F_dev": torch.empty(len(NP_LIST), B, dtype=torch.float64, device="cuda")}
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            run64.step_fstat_host(hostf)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            run64.step_fstat_host(hostf)
+            stream.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    e2e_f_ms = allmax(world, e0.elapsed_time(e1))
+    e2e_fstat = {"value": total_pbins / (e2e_f_ms / 1e3), "unit": UNIT,
+                 "h2d_bytes_per_step": int(hostf["P"].numel() * 8),
+                 "d2h_bytes_per_step": int(hostf["F"].numel() * 8),
+                 "call": "fs_fstat_batch per N_p on the prior draw, parameters from and F to pinned host memory"}
     tune64 = run64.tuning
     run64.close()
 
@@ -589,6 +622,7 @@ def run_gpu(args, world, rank, local):
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(len(NP_LIST) * 2 * host["x"].numel() * 8),
                     "d2h_bytes_per_step": int(host["fit"].numel() * 8)},
+            "e2e_fstat_batch": e2e_fstat,
             "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps, "dtype": "f64 anchors + f32",
                       "max_rel_err_vs_fp64": mix_err, "error_metric": "|dF|/max(|F|, 2 N_p)",
                       "max_rel_err_vs_fp64_by_Np": {str(k): v for k, v in mix_err_np.items()},
