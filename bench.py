@@ -658,7 +658,7 @@ def run_mlp_profile_case(tensor_path: int = 0, reps: int = 2):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     with torch.cuda.stream(s):
         net = fstat.MLP(W, max_batch=4096, seed=1, stream=s, groups=G)
-        net.set_tensor_path(bool(tensor_path))
+        net.set_tensor_path(int(tensor_path))
         losses = net.train(X, t, 20, 1e-3)
         y = net.forward(Xf)
         ev[0].record(s)
@@ -672,7 +672,7 @@ def run_mlp_profile_case(tensor_path: int = 0, reps: int = 2):
     s.synchronize()
     ok = net.tensor_status()
     print(json.dumps({"profile_case": "surrogate batch, 16 networks of width 256, 20 Adam steps on 2048 rows, "
-                                      "forward of 5120 rows", "tensor_path": "tcgen05" if tensor_path else "mma.sync",
+                                      "forward of 5120 rows", "tensor_path": {0: "mma.sync", 1: "tcgen05", 2: "tcgen05 forward, mma.sync backward"}[tensor_path],
                       "train_round_ms": ev[0].elapsed_time(ev[1]) / reps, "forward_ms": ev[2].elapsed_time(ev[3]) / reps,
                       "tensor_status_ok": bool(ok), "loss_last": float(losses[-1].mean().item()),
                       "y_mean": float(y.mean().item())}))
@@ -686,7 +686,7 @@ def run_profile_case(args):
     import torch
     from paper_2407_10797_gb300 import fstat
     if args.profile_case == "mlp":
-        run_mlp_profile_case(tensor_path=1 if args.variant == 1 else 0, reps=max(args.steps, 2))
+        run_mlp_profile_case(tensor_path=args.variant if args.variant in (1, 2) else 0, reps=max(args.steps, 2))
         return
     w, g, psd, noise, P, inj = workload_inputs(0)
     mode = fstat.FS_MIXED if args.profile_case == "mixed" else fstat.FS_FP64

@@ -339,9 +339,12 @@ FS_API int fs_mlp_groups(const fs_mlp* mlp);
 
 /* Tensor-core path of the network's GEMMs: 1 = tcgen05 (5th-generation
  * tensor cores, accumulators in tensor memory) for the products whose
- * output width is a multiple of 64 or equals 16, mma.sync for the others;
- * 0 = mma.sync throughout (the default at creation).  Both accumulate bf16
- * products in fp32; results differ only in summation order. */
+ * output width is a multiple of 64 or equals 16 -- the forward layers' with
+ * operands copied by the tensor memory accelerator, the backward ones' by the
+ * CTA's threads -- mma.sync for the others; 2 = tcgen05 for the forward
+ * layers, mma.sync for the backward pass; 0 = mma.sync throughout (the
+ * default at creation).  All accumulate bf16 products in fp32; results
+ * differ only in summation order. */
 FS_API fs_status fs_mlp_set_tensor_path(fs_mlp* mlp, int tcgen05);
 
 /* FS_ETIMEOUT (and *timed_out = 1) if a tcgen05 GEMM of this network gave up

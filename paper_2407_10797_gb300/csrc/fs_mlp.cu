@@ -1104,7 +1104,7 @@ struct fs_mlp {
     float *loss;    // [G]
     float* adamc;   // [4] Adam step counter and bias corrections (device)
     float* ws;      // split-K partials: G x splits x W x max(W, kInPad)
-    int tc5;        // 1: tcgen05 GEMMs, 0: mma.sync GEMMs
+    int tc5;        // 0: mma.sync GEMMs; 1: tcgen05 throughout; 2: tcgen05 forward layers, mma.sync backward
     int* tc_err;    // device flag set by a tcgen05 GEMM whose mbarrier wait ran out
     float* part;    // column-sum partials: G x ceil(cap / kColRows) x W
 };
@@ -1125,7 +1125,9 @@ void mlp_free(fs_mlp* m) {
     for (void* p : ps) cudaFree(p);
 }
 
+// tcgen05 error flag for the GEMMs of the forward layers / of the backward pass (NULL: mma.sync)
 int* tcp(fs_mlp* m) { return m->tc5 ? m->tc_err : nullptr; }
+int* tcp_bwd(fs_mlp* m) { return m->tc5 == 1 ? m->tc_err : nullptr; }
 
 // identity target scaling (mean 0, deviation 1) for every network
 cudaError_t reset_stdz(fs_mlp* m) {
@@ -1206,23 +1208,23 @@ cudaError_t mlp_backward(fs_mlp* m, const float* X, const float* t, int64_t st, 
     sum_kernel<<<G, 256, 0, s>>>(N, m->dy, gb4, P);
     dz_last_kernel<<<(unsigned)(((int64_t)G * NW + 255) / 256), 256, 0, s>>>(G, N, W, m->dy, m->W4b, m->A3, m->dZa);
     // layer 3: dW3 = dZ3^T A2, db3, dZ2 = (dZ3 W3) * (A2 > 0)
-    if ((e = gemm_wgrad<true>(W, W, N, m->dZa, W, m->A2, W, gW3, m->ws, m->splits, s, tcp(m), G, NW, NW, P)) !=
+    if ((e = gemm_wgrad<true>(W, W, N, m->dZa, W, m->A2, W, gW3, m->ws, m->splits, s, tcp_bwd(m), G, NW, NW, P)) !=
         cudaSuccess)
         return e;
     if ((e = colsum<bf16>(G, N, W, m->dZa, nullptr, gb3, P, m->part, s)) != cudaSuccess) return e;
-    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZa, W, m->W3b, W, nullptr, m->A2, W, m->dZb, W, s, tcp(m), G,
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZa, W, m->W3b, W, nullptr, m->A2, W, m->dZb, W, s, tcp_bwd(m), G,
                                               gm)) != cudaSuccess)
         return e;
     // layer 2
-    if ((e = gemm_wgrad<true>(W, W, N, m->dZb, W, m->A1, W, gW2, m->ws, m->splits, s, tcp(m), G, NW, NW, P)) !=
+    if ((e = gemm_wgrad<true>(W, W, N, m->dZb, W, m->A1, W, gW2, m->ws, m->splits, s, tcp_bwd(m), G, NW, NW, P)) !=
         cudaSuccess)
         return e;
     if ((e = colsum<bf16>(G, N, W, m->dZb, nullptr, gb2, P, m->part, s)) != cudaSuccess) return e;
-    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZb, W, m->W2b, W, nullptr, m->A1, W, m->dZa, W, s, tcp(m), G,
+    if ((e = gemm<false, true, EPI_MASK_BF16>(N, W, W, m->dZb, W, m->W2b, W, nullptr, m->A1, W, m->dZa, W, s, tcp_bwd(m), G,
                                               gm)) != cudaSuccess)
         return e;
     // layer 1 (padded input)
-    if ((e = gemm_wgrad<true>(W, kInPad, N, m->dZa, W, m->Xb, kInPad, m->g16, m->ws, m->splits, s, tcp(m), G, NW,
+    if ((e = gemm_wgrad<true>(W, kInPad, N, m->dZa, W, m->Xb, kInPad, m->g16, m->ws, m->splits, s, tcp_bwd(m), G, NW,
                               (int64_t)N * kInPad, (int64_t)W * kInPad)) != cudaSuccess)
         return e;
     unpad_kernel<<<(unsigned)(((int64_t)G * W * 5 + 255) / 256), 256, 0, s>>>(G, W, P, m->g16, gW1);
@@ -1350,7 +1352,7 @@ fs_status fs_mlp_get_params(fs_mlp* m, float* theta_dev) {
 
 fs_status fs_mlp_set_tensor_path(fs_mlp* m, int tcgen05) {
     fs::set_error(FS_OK, "");
-    if (!m || (tcgen05 != 0 && tcgen05 != 1)) return fs::set_error(FS_EINVAL, "fs_mlp_set_tensor_path: bad argument");
+    if (!m || tcgen05 < 0 || tcgen05 > 2) return fs::set_error(FS_EINVAL, "fs_mlp_set_tensor_path: bad argument");
     m->tc5 = tcgen05;
     return FS_OK;
 }

@@ -673,9 +673,11 @@ class MLP:
         except Exception:
             pass
 
-    def set_tensor_path(self, tcgen05: bool):
-        """True: tcgen05 GEMMs (TMEM accumulators); False: mma.sync GEMMs."""
-        _check(self._L.fs_mlp_set_tensor_path(self._h, 1 if tcgen05 else 0))
+    def set_tensor_path(self, tcgen05):
+        """True or 1: tcgen05 GEMMs (TMEM accumulators; TMA-fed forward layers);
+        2: tcgen05 forward layers, mma.sync backward; False or 0: mma.sync GEMMs."""
+        path = int(tcgen05) if not isinstance(tcgen05, bool) else (1 if tcgen05 else 0)
+        _check(self._L.fs_mlp_set_tensor_path(self._h, path))
 
     def tensor_status(self) -> bool:
         """True if no tcgen05 GEMM of this network timed out (waits for its stream)."""
