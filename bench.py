@@ -433,6 +433,45 @@ class ModeRun:
         self.plan.close()
 
 
+def two_channel_lines(args, world, fstat, g, psd, P_dev, stream, pbins):
+    """Throughput on data in the A and E channels (PSDs 3/2 of the X model,
+    independent noise per channel): fs_fstat_batch of the bench's particles at
+    every N_p, per mode, after `warmup` untimed rounds; particle*bins counted
+    once per particle and bin (each covers both channels)."""
+    import torch
+    dev = P_dev.device
+    psd2 = S.tdi_psds(g.freqs(), S.TDI_AE)
+    d2 = np.stack([S.gaussian_noise(g, psd2[c], 3000 + c, channel=c) for c in range(2)])
+    out = {}
+    for name, mode in (("fp64", fstat.FS_FP64), ("mixed", fstat.FS_MIXED)):
+        with torch.cuda.stream(stream):
+            plan = fstat.Plan.from_grid(g, mode=mode, stream=stream, tdi=fstat.FS_TDI_AE)
+            plan.set_data(torch.from_numpy(d2).to(dev), torch.from_numpy(psd2).to(dev))
+            plan.reserve(P_dev.shape[0], max(NP_LIST))
+            F = torch.empty(P_dev.shape[0], dtype=torch.float64, device=dev)
+            if mode == fstat.FS_MIXED:   # FP64: the default anchored persistent form, which its tuner picks
+                for Np in NP_LIST:
+                    plan.autotune(P_dev, Np, reps=2)
+            for _ in range(max(args.warmup, 1)):
+                for Np in NP_LIST:
+                    plan.fstat(P_dev, Np, F=F, want_parts=False)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier(world)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                for Np in NP_LIST:
+                    plan.fstat(P_dev, Np, F=F, want_parts=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            ms = allmax(world, e0.elapsed_time(e1))
+            plan.close()
+        out[name] = {"value": pbins / (ms / 1e3), "unit": UNIT + " (A and E channels)",
+                     "ms_per_step": ms / args.steps}
+    return out
+
+
 def time_run(args, world, run: ModeRun, kernel_prof=True):
     import torch
     stream = run.stream
@@ -573,6 +612,9 @@ def run_gpu(args, world, rank, local):
     tunem = runm.tuning
     runm.close()
 
+    # ---- the A and E channels (two-channel data), both modes, fs_fstat_batch on the prior draw
+    channels = two_channel_lines(args, world, fstat, g, psd, P0_dev, stream, total_pbins)
+
     # ---- roofline of the dominant kernels (average launch duration, live events)
     main_avg_ms = main_ms / max(main_n, 1)
     # flops per fused launch from the anchor-mode census of the same particles
@@ -623,6 +665,7 @@ def run_gpu(args, world, rank, local):
                     "h2d_bytes_per_step": int(len(NP_LIST) * 2 * host["x"].numel() * 8),
                     "d2h_bytes_per_step": int(host["fit"].numel() * 8)},
             "e2e_fstat_batch": e2e_fstat,
+            "channels_AE": channels,
             "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps, "dtype": "f64 anchors + f32",
                       "max_rel_err_vs_fp64": mix_err, "error_metric": "|dF|/max(|F|, 2 N_p)",
                       "max_rel_err_vs_fp64_by_Np": {str(k): v for k, v in mix_err_np.items()},
