@@ -235,6 +235,8 @@ class Plan:
 
     def fstat(self, params, Np: int, edges=None, F=None, F_part=None, want_parts: bool = True):
         """Semi-coherent F for params (float64 CUDA tensor [B, 6]: Mc, tc, lat, lon, e0, q).
+        edges: None (per-particle segments) or N_p + 1 edge frequencies in Hz, best
+        as a float64 CUDA tensor (any other array is copied to the device on every call).
         Returns (F [B], F_part [B, Np] or None) as CUDA tensors."""
         import torch
         if params.dim() != 2 or params.shape[1] != 6:
