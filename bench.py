@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=None,
                     help="force one launch variant of the fused kernel instead of autotuning")
+    ap.add_argument("--variant-mixed", type=int, default=None,
+                    help="the mixed mode's forced variant when --variant is given (default: the same number)")
     ap.add_argument("--search", choices=["fp64", "mixed", "surrogate"], default=None,
                     help="time the full hierarchical search (4 stages) instead of the F-statistic step")
     ap.add_argument("--seeds", type=int, nargs="+", default=[0],
@@ -598,7 +600,8 @@ def run_gpu(args, world, rank, local):
 
     # ---- mixed mode on the same data and particles
     runm = ModeRun(fstat, fstat.FS_MIXED, g, d_dev, psd_dev, box, stream, seed,
-                   variant=None if args.variant is None else min(args.variant, 4))
+                   variant=None if args.variant is None else
+                   (args.variant_mixed if args.variant_mixed is not None else min(args.variant, 4)))
     censusm = runm.census(P0_dev)
     ms_m, prof_m, clocks_m = time_run(args, world, runm)
     value_m = total_pbins / (ms_m / 1e3)
