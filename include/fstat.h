@@ -405,6 +405,7 @@ typedef struct {
     float* f;
     int cap;
     unsigned long long* count;
+    int dims;   /* floats per sample: 5 (or 0) or 6; must equal the appending swarm's D */
 } fs_sample_ring;
 
 /* Append the swarm's current positions (as floats) and fitness (NaN where

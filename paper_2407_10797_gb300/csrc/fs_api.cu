@@ -90,7 +90,7 @@ struct fs_plan {
     // segment start bins of the current call (global mode; converted on the device from the
     // caller's edge frequencies at the start of every evaluation) and the sticky error flags
     int64_t* edges_dev;
-    int* flags_dev;
+    int* flags_dev;   // [0] sticky flags (fs_plan_check), [1] scratch of the grid check
     // single-particle scratch for fs_add_signal
     fs_params* one_param;
     fs::Particle* one_part;
@@ -330,8 +330,8 @@ fs_status fs_plan_create_tdi(fs_plan** out, int64_t n_bins, double f_min, double
         }
     }
     if ((e = cudaMalloc(&p->edges_dev, sizeof(int64_t) * (fs::kNpMax + 2))) != cudaSuccess ||
-        (e = cudaMalloc(&p->flags_dev, sizeof(int))) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
+        (e = cudaMalloc(&p->flags_dev, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->flags_dev, 0, 2 * sizeof(int), p->stream)) != cudaSuccess ||
         (e = cudaMalloc(&p->one_param, sizeof(fs_params))) != cudaSuccess ||
         (e = cudaMalloc(&p->one_part, sizeof(fs::Particle))) != cudaSuccess ||
         (e = cudaMalloc(&p->one_a, sizeof(double) * 4)) != cudaSuccess) {
@@ -389,12 +389,12 @@ fs_status fs_plan_set_data(fs_plan* p, const double* data_dev, const double* psd
     if (f_grid_dev) {
         // the kernels step the phase in the bin index, which needs the uniform grid
         // f_k = f_min + k df: check the caller's grid against it and wait for the answer
+        // the check's own word (flags_dev[1]), so that the sticky word keeps what it holds
         int h = 0;
         cudaError_t e;
-        if ((e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
-            (e = fs::launch_grid_check(p->grid, f_grid_dev, p->flags_dev, p->stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(&h, p->flags_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->flags_dev, 0, sizeof(int), p->stream)) != cudaSuccess ||
+        if ((e = cudaMemsetAsync(p->flags_dev + 1, 0, sizeof(int), p->stream)) != cudaSuccess ||
+            (e = fs::launch_grid_check(p->grid, f_grid_dev, p->flags_dev + 1, p->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&h, p->flags_dev + 1, sizeof(int), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
             return cuda_fail(e, "fs_plan_set_data: grid check");
         if (h & fs::kFlagBadGrid)
@@ -809,6 +809,9 @@ fs_status fs_pso_record(fs_plan* p, const fs_swarm* w, const fs_sample_ring* rin
         const fs_sample_ring& r = rings[g];
         if (!r.x || !r.f || !r.count || r.cap < 1)
             return fail(FS_EINVAL, "fs_pso_record: ring %d needs x, f, count and cap >= 1", g);
+        if ((r.dims == 6 ? 6 : 5) != swarm_dims(w) || (r.dims != 0 && r.dims != 5 && r.dims != 6))
+            return fail(FS_EINVAL, "fs_pso_record: ring %d holds %d floats per sample, the swarm has %d dimensions",
+                        g, r.dims == 0 ? 5 : r.dims, swarm_dims(w));
     }
     // one launch per kRingBatch rings
     for (int g0 = 0; g0 < n_rings; g0 += fs::kRingBatch) {
@@ -923,6 +926,9 @@ fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_sample_r
             const fs_sample_ring& r = rings[k];
             if (!r.x || !r.f || r.cap < 1)
                 return fail(FS_EINVAL, "fs_mlp_train_graph_build: ring %d needs x, f and cap >= 1", k);
+            if (r.dims != 0 && r.dims != 5)
+                return fail(FS_EINVAL, "fs_mlp_train_graph_build: ring %d holds %d floats per sample; the networks "
+                                       "take 5 inputs", k, r.dims);
             if (r.cap != r0.cap || r.x != r0.x + (int64_t)j * r0.cap * 5 || r.f != r0.f + (int64_t)j * r0.cap)
                 return fail(FS_EINVAL,
                             "fs_mlp_train_graph_build: the rings of network %d must be consecutive slices of one "

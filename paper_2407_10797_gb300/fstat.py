@@ -42,7 +42,7 @@ _dp = C.POINTER(C.c_double)
 
 
 class fs_sample_ring(C.Structure):
-    _fields_ = [("x", _vp), ("f", _vp), ("cap", C.c_int), ("count", _vp)]
+    _fields_ = [("x", _vp), ("f", _vp), ("cap", C.c_int), ("count", _vp), ("dims", C.c_int)]
 
 
 class fs_swarm(C.Structure):
@@ -417,6 +417,8 @@ def _edges_arg(edges, Np, device, stream=None):
         t = edges.contiguous()
         if t.dtype != torch.float64:
             raise TypeError("edges must be float64 frequencies")
+        if t.device != torch.device(device):
+            raise ValueError(f"edges are on {t.device}, the call runs on {device}")
     else:
         t = torch.as_tensor(np.ascontiguousarray(edges, dtype=np.float64)).to(device)
         if stream is not None and stream != torch.cuda.current_stream(device):
@@ -599,7 +601,7 @@ class SampleRing:
         self.x = torch.zeros(self.cap, dims, dtype=torch.float32, device=dev)
         self.f = torch.full((self.cap,), float("nan"), dtype=torch.float32, device=dev)
         self.count = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.c = fs_sample_ring(self.x.data_ptr(), self.f.data_ptr(), self.cap, self.count.data_ptr())
+        self.c = fs_sample_ring(self.x.data_ptr(), self.f.data_ptr(), self.cap, self.count.data_ptr(), int(dims))
 
     @classmethod
     def batch(cls, n: int, cap: int, device=None, dims: int = 5) -> list:
@@ -615,7 +617,7 @@ class SampleRing:
             r = cls.__new__(cls)
             r.cap = int(cap)
             r.x, r.f, r.count = x[j], f[j], count[j:j + 1]
-            r.c = fs_sample_ring(r.x.data_ptr(), r.f.data_ptr(), r.cap, r.count.data_ptr())
+            r.c = fs_sample_ring(r.x.data_ptr(), r.f.data_ptr(), r.cap, r.count.data_ptr(), int(dims))
             out.append(r)
         return out
 

@@ -209,3 +209,22 @@ def test_six_dimensional_swarm_maps_delta_mu_to_the_mass_ratio(fst, plan):
         net = fst.MLP(64, max_batch=512, seed=0, stream=plan.stream)
         sw.step_screened(net, 4, 11, 0)
     assert ei.value.status == fst.FS_EUNSUPPORTED
+
+
+def test_rings_hold_the_swarms_dimensions(fst, plan):
+    """A ring declares its floats per sample; a 6-D swarm appends only to a
+    6-float ring (a 5-float one would overflow and is refused), and the
+    samples are the positions as floats."""
+    R, Np = 2, 40
+    sw = fst.Swarm(plan, R, Np, dmu_box(R), dims=6)
+    with torch.cuda.stream(plan.stream):
+        sw.init(3)
+        sw.evaluate(4)
+        with pytest.raises(fst.FstatError) as ei:
+            sw.record(fst.SampleRing(256))
+        assert ei.value.status == fst.FS_EINVAL
+        ring = fst.SampleRing(256, dims=6)
+        sw.record(ring)
+    torch.cuda.synchronize()
+    assert int(ring.count.item()) == R * Np
+    assert torch.equal(ring.x[:R * Np], sw.x.reshape(-1, 6).float())
