@@ -95,8 +95,12 @@ def parse():
     ap.add_argument("--seeds", type=int, nargs="+", default=[0],
                     help="search mode: data/injection seeds (independent noise and injection per seed)")
     ap.add_argument("--iters", type=int, default=2000, help="search mode: PSO iterations per stage")
-    ap.add_argument("--stages", choices=["default", "paper"], default="default",
-                    help="search mode: N_p = 256/64/16/1 (default) or the paper's 16/16/1 schedule")
+    ap.add_argument("--stages", choices=["default", "paper", "paper-budget"], default="default",
+                    help="search mode: N_p = 256/64/16/1 (default), the paper's 16/16/1 schedule with the default "
+                         "layout, or the paper's schedule with its own layout and iteration counts "
+                         "(24x24x128 / 24x8x128 / 2x48x128 particles, 8000/8000/15000 iterations x --iter-scale)")
+    ap.add_argument("--iter-scale", type=float, default=1.0,
+                    help="search mode, --stages paper-budget: factor on the paper's iteration counts")
     ap.add_argument("--snr", type=float, default=None, help="search mode: injection SNR (default: the workload's)")
     ap.add_argument("--dmu", type=float, default=0.0,
                     help="search mode: search delta_mu in [0, DMU] as a sixth coordinate (the paper's 0.9), with the "
@@ -775,8 +779,15 @@ def run_search(args):
     # search prior: the injection prior's t_c window (0.5 yr, the paper's stage-1 range) and M_c in [10, 50]
     prior = S.Prior(Mc_lo=10.0, Mc_hi=50.0, tc_lo=0.9 * T, tc_hi=1.1 * T, e0_hi=0.1)
     snr = w.snr if args.snr is None else args.snr
-    stages = search.default_stages(args.iters) if args.stages == "default" else search.paper_stages(args.iters)
+    if args.stages == "default":
+        stages = search.default_stages(args.iters)
+    elif args.stages == "paper":
+        stages = search.paper_stages(args.iters)
+    else:
+        stages = search.paper_budget_stages(args.iter_scale)
     np_list = [st.Np for st in stages]
+    layout = [((st.boxes or 16), (st.runs or 8), (st.particles or 40)) for st in stages]
+    B_max = max(a * b * c for a, b, c in layout)
     out = []
     for seed in args.seeds:
         stream = torch.cuda.Stream()
@@ -802,7 +813,7 @@ def run_search(args):
             d_dev = d_dev + h * (snr / math.sqrt(hh))
             del h
             plan.set_data(d_dev, psd_dev)
-            plan.reserve(16 * 8 * 40, 256)
+            plan.reserve(B_max, max(np_list))
             truth = torch.from_numpy(inj[None].copy()).to(dev)
             F_truth = {Np: float(plan.fstat(truth, Np)[0][0].item()) / Np for Np in sorted(set(np_list))}
         torch.cuda.synchronize()
@@ -851,12 +862,12 @@ def run_search(args):
             "mode": args.search, "n_gpus": 1, "dtype": "f64" if mode == fstat.FS_FP64 else "f64 anchors + f32",
             "data": "synthetic",
             "config": {"workload": w.name, "n_bins": g.n, "stages_N_p": np_list, "schedule": args.stages,
-                       "prior_kind": args.prior, "boxes": 16,
-                       "runs_per_box": 8, "particles": 40, "iterations_per_stage": args.iters, "snr": snr,
+                       "prior_kind": args.prior, "boxes_runs_particles": layout,
+                       "iterations_per_stage": [st.n_iter for st in stages], "snr": snr,
                        "prior": {"Mc": [prior.Mc_lo, prior.Mc_hi], "tc": [prior.tc_lo, prior.tc_hi],
                                  "e0": [0.0, prior.e0_hi], "sky": "full sphere"},
                        "surrogate": args.search == "surrogate", "dmu_free_up_to": args.dmu},
-            "exact_F_evaluations": len(stages) * 16 * 8 * 40 * args.iters,
+            "exact_F_evaluations": int(sum(a * b * c * st.n_iter for (a, b, c), st in zip(layout, stages))),
             "Mc_rel_err": [o["Mc_rel_err"] for o in out],
             "iterations_to_Mc_1e-4": [o["iterations_to_Mc_1e-4"] for o in out], "runs": out}
     print(json.dumps(line), flush=True)

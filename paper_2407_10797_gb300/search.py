@@ -43,6 +43,9 @@ class StageSpec:
     widths: tuple = ()             # full widths (M_c [Msun], t_c [s], sin(lat), lon [rad], e0); None = prior
     w0: float = 0.9
     w1: float = 0.4
+    boxes: int | None = None       # boxes, runs per box and particles per run of this stage
+    runs: int | None = None        # (None: the search's n_boxes, runs_per_box, n_part)
+    particles: int | None = None
 
 
 def default_stages(n_iter: int = 2000) -> list[StageSpec]:
@@ -65,6 +68,23 @@ def paper_stages(n_iter: int = 2000) -> list[StageSpec]:
         StageSpec(16, n_iter, "split_tc"),
         StageSpec(16, n_iter, "around", (0.6, 0.01 * YEAR, None, None, None)),
         StageSpec(1, n_iter, "around_best_mirror", (0.3, 0.004 * YEAR, 0.4, 0.4, 0.006)),
+    ]
+
+
+def paper_budget_stages(scale: float = 1.0) -> list[StageSpec]:
+    """The paper's three stages with its own layout and budget (Sec. III.B):
+    stage 1, N_seg = 16, the t_c range in 24 intervals x 24 PSO runs of 128
+    particles, 8000 iterations; stage 2, N_seg = 16, 24 boxes (0.01 yr x 0.6
+    Msun) around the stage-1 winners x 8 runs, 8000 iterations; stage 3,
+    N_seg = 1, the best winner's box (0.004 yr, 0.3 Msun, 0.4 rad, 0.4 rad,
+    0.006) and its theta -> pi - theta mirror x 48 runs, 15000 iterations.
+    scale multiplies every iteration count."""
+    it = lambda n: max(2, int(round(n * scale)))
+    return [
+        StageSpec(16, it(8000), "split_tc", boxes=24, runs=24, particles=128),
+        StageSpec(16, it(8000), "around", (0.6, 0.01 * YEAR, None, None, None), boxes=24, runs=8, particles=128),
+        StageSpec(1, it(15000), "around_best_mirror", (0.3, 0.004 * YEAR, 0.4, 0.4, 0.006), boxes=2, runs=48,
+                  particles=128),
     ]
 
 
@@ -215,38 +235,47 @@ class HierarchicalSearch:
         self.progress: list = []
 
     # ---------------------------------------------------------------- boxes
+    def stage_layout(self, i: int) -> tuple[int, int, int]:
+        """(boxes, runs per box, particles per run) of stage i."""
+        spec = self.stages[i]
+        return (spec.boxes or self.n_boxes, spec.runs or self.runs_per_box, spec.particles or self.n_part)
+
     def stage_boxes(self, i: int) -> np.ndarray:
         spec = self.stages[i]
+        n_boxes = self.stage_layout(i)[0]
         pb = prior_box(self.prior, self.dmu_hi) if self.bounds is None else self.bounds.copy()
         if spec.rule == "split_tc":
-            u = S.uniforms(self.seed, 0x53504C54, self.n_boxes)           # "SPLT"
+            u = S.uniforms(self.seed, 0x53504C54, n_boxes)                # "SPLT"
             w = -np.log1p(-u)                                              # Dirichlet(1) via exponentials
             edges = pb[1, 0] + (pb[1, 1] - pb[1, 0]) * np.concatenate([[0.0], np.cumsum(w) / np.sum(w)])
-            boxes = np.repeat(pb[None], self.n_boxes, axis=0)
+            boxes = np.repeat(pb[None], n_boxes, axis=0)
             boxes[:, 1, 0] = edges[:-1]
             boxes[:, 1, 1] = edges[1:]
             return boxes
         prev = self.results[i - 1]
         if spec.rule == "around":
-            centers = [to_normal_coords(np.array(p), self.dims) for p in prev.winners]
+            # box k around winner k of the previous stage (cyclically if this stage has more boxes)
+            centers = [to_normal_coords(np.array(prev.winners[k % len(prev.winners)]), self.dims)
+                       for k in range(n_boxes)]
         elif spec.rule == "around_best_mirror":
             best = np.array(prev.winners[int(np.argmax(prev.winner_f))])
             c = to_normal_coords(best, self.dims)
             m = c.copy()
             m[2] = -m[2]                                                   # theta -> pi - theta
-            centers = [c if k % 2 == 0 else m for k in range(self.n_boxes)]
+            centers = [c if k % 2 == 0 else m for k in range(n_boxes)]
         else:
             raise ValueError(spec.rule)
         return np.stack([box_around(c, spec.widths, pb) for c in centers])
 
     # ---------------------------------------------------------------- one stage
-    def local_boxes(self) -> tuple[int, int]:
-        """The contiguous block [k0, k1) of boxes this process searches (all of
-        them without a communicator)."""
+    def local_boxes(self, i: int = 0) -> tuple[int, int]:
+        """The contiguous block [k0, k1) of stage i's boxes this process
+        searches (all of them without a communicator)."""
+        n_boxes = self.stage_layout(i)[0] if self.stages else self.n_boxes
         if self.comm is None:
-            return 0, self.n_boxes
+            return 0, n_boxes
         r, w = self.comm.rank, self.comm.world
-        return self.n_boxes * r // w, self.n_boxes * (r + 1) // w
+        return n_boxes * r // w, n_boxes * (r + 1) // w
 
     def run_stage(self, i: int) -> StageResult:
         """One stage: every process runs the PSO runs of its block of boxes on
@@ -257,7 +286,7 @@ class HierarchicalSearch:
         processes."""
         spec = self.stages[i]
         boxes = self.stage_boxes(i)
-        k0, k1 = self.local_boxes()
+        k0, k1 = self.local_boxes(i)
         t0 = time.perf_counter()
         local = self._run_boxes(i, boxes, k0, k1) if k1 > k0 else ([], [], -1)
         seconds = time.perf_counter() - t0
@@ -280,13 +309,13 @@ class HierarchicalSearch:
         launch variant used."""
         import torch
         spec = self.stages[i]
+        _, runs_per_box, n_part = self.stage_layout(i)
         nb = k1 - k0
-        R = nb * self.runs_per_box
-        run_boxes = np.repeat(boxes[k0:k1], self.runs_per_box, axis=0)
+        R = nb * runs_per_box
+        run_boxes = np.repeat(boxes[k0:k1], runs_per_box, axis=0)
         stage_seed = (self.seed << 8) + i
         with torch.cuda.stream(self.plan.stream):
-            sw = fstat.Swarm(self.plan, R, self.n_part, run_boxes, self.q, run0=k0 * self.runs_per_box,
-                             dims=self.dims)
+            sw = fstat.Swarm(self.plan, R, n_part, run_boxes, self.q, run0=k0 * runs_per_box, dims=self.dims)
             sw.init(stage_seed)
             variant = sw.autotune(spec.Np, reps=2)[0] if self.autotune else self.plan.get_variant(spec.Np)
             if self.surrogate is None:
@@ -311,7 +340,7 @@ class HierarchicalSearch:
             pbx = sw.pbest_x.cpu().numpy()
         winners, wf = [], []
         for k in range(nb):
-            runs = np.arange(k * self.runs_per_box, (k + 1) * self.runs_per_box)
+            runs = np.arange(k * runs_per_box, (k + 1) * runs_per_box)
             r = runs[int(np.argmax(bf[runs]))]
             winners.append(to_physical(pbx[r, bi[r]], run_boxes[r], self.q).tolist())
             wf.append(float(bf[r]))
@@ -340,7 +369,7 @@ class HierarchicalSearch:
         makes the same calls."""
         import torch
         sp = self.surrogate
-        nb = self.n_boxes if nb is None else nb
+        nb = self.stage_layout(stage)[0] if nb is None else nb
         dev = sw.x.device
         # network k of the batch belongs to box k0 + k and is seeded by that global index
         self.mlp = fstat.MLP(sp.width, max_batch=max(sp.buffer, 4096), seed=self.seed * 1000 + 97 * stage + k0,

@@ -136,3 +136,34 @@ def test_delta_mu_free_search_coordinates_and_boxes():
     b = search.box_around(c, widths, pb)
     assert b.shape == (6, 2) and list(b[5]) == [0.0, 0.9]
     assert b[0, 1] - b[0, 0] == pytest.approx(0.3)
+
+
+def test_paper_budget_layout_per_stage():
+    """The paper's own layout (Sec. III.B): 24 t_c intervals x 24 runs x 128
+    particles, then 24 boxes x 8 runs around the 24 stage-1 winners, then the
+    best winner and its mirror x 48 runs; iterations 8000/8000/15000 x scale."""
+    st = search.paper_budget_stages(1.0)
+    assert [s.Np for s in st] == [16, 16, 1]
+    assert [s.n_iter for s in st] == [8000, 8000, 15000]
+    assert [s.n_iter for s in search.paper_budget_stages(0.25)] == [2000, 2000, 3750]
+    s = make(stages=st)
+    assert [s.stage_layout(i) for i in range(3)] == [(24, 24, 128), (24, 8, 128), (2, 48, 128)]
+    # a stage without its own counts takes the search's
+    assert make().stage_layout(0) == (6, 2, 4)
+    res = s.run(extrinsic=False)
+    assert [len(r["winners"]) for r in res["stages"]] == [24, 24, 2]
+    b0 = s.stage_boxes(0)
+    assert b0.shape[0] == 24 and np.all(b0[1:, 1, 0] == b0[:-1, 1, 1])
+    b1 = s.stage_boxes(1)
+    for k, w in enumerate(s.results[0].winners):
+        c = search.to_normal_coords(np.array(w))
+        assert b1[k, 0, 0] <= c[0] <= b1[k, 0, 1] and b1[k, 1, 0] <= c[1] <= b1[k, 1, 1]
+    assert s.stage_boxes(2).shape[0] == 2
+    for world in (1, 2, 5):
+        seen = []
+        for rank in range(world):
+            s.comm = types.SimpleNamespace(rank=rank, world=world)
+            k0, k1 = s.local_boxes(2)
+            seen.extend(range(k0, k1))
+        assert seen == [0, 1]
+    s.comm = None
