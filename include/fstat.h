@@ -342,8 +342,8 @@ FS_API int fs_mlp_groups(const fs_mlp* mlp);
  * output width is a multiple of 64 or equals 16 -- the forward layers' with
  * operands copied by the tensor memory accelerator, the backward ones' by the
  * CTA's threads -- mma.sync for the others; 2 = tcgen05 for the forward
- * layers, mma.sync for the backward pass; 0 = mma.sync throughout (the
- * default at creation).  All accumulate bf16 products in fp32; results
+ * layers, mma.sync for the backward pass (the default at creation); 0 =
+ * mma.sync throughout.  All accumulate bf16 products in fp32; results
  * differ only in summation order. */
 FS_API fs_status fs_mlp_set_tensor_path(fs_mlp* mlp, int tcgen05);
 

@@ -611,12 +611,46 @@ gemm_tma_kernel(int M, int N, int K, const __grid_constant__ CUtensorMap mapA, c
         }
         __syncthreads();
         constexpr int QPR = NT / 4;
+        // four outputs per store where the output rows, the bias and the mask allow it (CTA-uniform)
+        const bool vec = N % 4 == 0 && ldo % 4 == 0 &&
+                         (reinterpret_cast<uintptr_t>(out) & (EPI == EPI_F32 ? 15u : 7u)) == 0 &&
+                         (EPI != EPI_BIAS_RELU_BF16 || (reinterpret_cast<uintptr_t>(bias) & 15u) == 0) &&
+                         (EPI != EPI_MASK_BF16 || (ldm % 4 == 0 && (reinterpret_cast<uintptr_t>(mask) & 7u) == 0));
         for (int q = threadIdx.x; q < TM * QPR; q += THREADS) {
             const int rr = q / QPR, cc = (q % QPR) * 4;
             const int m = m0 + rr, n = n0 + cc;
             if (m >= M) continue;
             const float4 v4 = *reinterpret_cast<const float4*>(stg + rr * LDS + cc);
             const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+            if (vec && n + 4 <= N) {
+                if (EPI == EPI_F32) {
+                    *reinterpret_cast<float4*>(static_cast<float*>(out) + (int64_t)m * ldo + n) = v4;
+                } else {
+                    float o[4];
+                    if (EPI == EPI_BIAS_RELU_BF16) {
+                        const float4 b4 = *reinterpret_cast<const float4*>(bias + n);
+                        o[0] = fmaxf(v[0] + b4.x, 0.f);
+                        o[1] = fmaxf(v[1] + b4.y, 0.f);
+                        o[2] = fmaxf(v[2] + b4.z, 0.f);
+                        o[3] = fmaxf(v[3] + b4.w, 0.f);
+                    } else {
+                        const uint2 mk = *reinterpret_cast<const uint2*>(mask + (int64_t)m * ldm + n);
+                        const __nv_bfloat162 m01 = *reinterpret_cast<const __nv_bfloat162*>(&mk.x);
+                        const __nv_bfloat162 m23 = *reinterpret_cast<const __nv_bfloat162*>(&mk.y);
+                        o[0] = __low2float(m01) > 0.f ? v[0] : 0.f;
+                        o[1] = __high2float(m01) > 0.f ? v[1] : 0.f;
+                        o[2] = __low2float(m23) > 0.f ? v[2] : 0.f;
+                        o[3] = __high2float(m23) > 0.f ? v[3] : 0.f;
+                    }
+                    const __nv_bfloat162 p01 = __floats2bfloat162_rn(o[0], o[1]);
+                    const __nv_bfloat162 p23 = __floats2bfloat162_rn(o[2], o[3]);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<const uint32_t*>(&p01);
+                    pk.y = *reinterpret_cast<const uint32_t*>(&p23);
+                    *reinterpret_cast<uint2*>(static_cast<bf16*>(out) + (int64_t)m * ldo + n) = pk;
+                }
+                continue;
+            }
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 if (n + j >= N) break;
@@ -1252,6 +1286,7 @@ fs_status mlp_create(fs_mlp** out, int groups, int width, int max_batch, uint64_
     memset(m, 0, sizeof(*m));
     const int W = width;
     const size_t G = (size_t)groups;
+    m->tc5 = 2;   // tcgen05 forward layers (TMA-fed where the operands allow), mma.sync backward
     m->G = groups;
     m->W = W;
     m->cap = max_batch;

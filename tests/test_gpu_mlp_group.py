@@ -30,7 +30,7 @@ def data(n, seed, nan_every=0):
     return X.cuda(), t.cuda()
 
 
-@pytest.mark.parametrize("tc5", [False, True])
+@pytest.mark.parametrize("tc5", [0, 1, 2])
 def test_batch_equals_separate_networks(fs, tc5):
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
