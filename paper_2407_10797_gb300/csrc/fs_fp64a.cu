@@ -281,13 +281,37 @@ __device__ __forceinline__ void bin_d(unsigned long long Fv, double d, double dr
     acc[6] = fma(W * G2, G2, acc[6]);
 }
 
+// The warp's sums of acc[0..6] into dst[0..6], and acc cleared: a
+// reduce-scatter butterfly over eight slots (the eighth zero).  At the XOR
+// distances 16, 8 and 4 each lane keeps half of its slots -- the upper half
+// if its lane bit is set -- and adds the partner's copies, so that lane l then
+// holds slot 4 b4 + 2 b3 + b2 (b_j bit j of l); distances 2 and 1 sum the
+// four lanes that hold the same slot, and the first of them writes it.
+// 9 FP64 additions per lane instead of the 35 of seven warp trees.
 __device__ __forceinline__ void flush_d(double acc[7], double* dst, int lane) {
+    double v4[4];
+    const bool h16 = (lane & 16) != 0;
 #pragma unroll
-    for (int c = 0; c < 7; c++) {
-        const double v = warp_sum(acc[c]);
-        if (lane == 0) dst[c] = v;
-        acc[c] = 0.0;
+    for (int i = 0; i < 4; i++) {
+        const double lo = acc[i], hi = i + 4 < 7 ? acc[i + 4] : 0.0;
+        const double give = h16 ? lo : hi;
+        v4[i] = (h16 ? hi : lo) + __shfl_xor_sync(0xffffffffu, give, 16);
     }
+    double v2[2];
+    const bool h8 = (lane & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const double give = h8 ? v4[i] : v4[i + 2];
+        v2[i] = (h8 ? v4[i + 2] : v4[i]) + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    const bool h4 = (lane & 4) != 0;
+    double v1 = (h4 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? v2[0] : v2[1], 4);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+    const int slot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && slot < 7) dst[slot] = v1;
+#pragma unroll
+    for (int c = 0; c < 7; c++) acc[c] = 0.0;
 }
 
 // An expansion tile walked as single-segment pieces [pa_lo, pa_hi): flushes the
@@ -297,19 +321,31 @@ __device__ __forceinline__ void expansion_tile(const AnchorD& A, const SegView& 
                                                const double2* __restrict__ rot, const double* __restrict__ dwr,
                                                const double* __restrict__ dwi, const double* __restrict__ Wt,
                                                const double2* __restrict__ tab, const Partials& pa, int64_t slot,
-                                               int b, int Np, int lane, int& cur, int& nflush, double acc[7]) {
+                                               int b, int Np, int lane, int& cur, int& nflush, int& trk,
+                                               int64_t& trk_nxt, double acc[7]) {
     double g1[NG + 1], g2[NG + 1], Rc[NR + 1];
 #pragma unroll
     for (int i = 0; i <= NR; i++) Rc[i] = A.R[i];
     int pa_lo = lo;
     while (pa_lo < hi) {
-        const int sp = sv.seg(span_lo + pa_lo);   // warp-uniform
+        // segment of the piece's first bin (sv.seg of it), tracked forward across the item's
+        // pieces: a segment boundary costs one sv.start
+        const int64_t kabs = span_lo + pa_lo;
+        if (trk < 0) {
+            trk = sv.seg(kabs);
+            trk_nxt = sv.start(trk + 1);
+        }
+        while (kabs >= trk_nxt) {
+            trk++;
+            trk_nxt = sv.start(trk + 1);
+        }
+        const int sp = trk;   // warp-uniform
         if (sp != cur) {
             flush_d(acc, (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * Np + cur) * 7, lane);
             nflush++;
             cur = sp;
         }
-        const int64_t nb = sv.start(sp + 1) - span_lo;
+        const int64_t nb = trk_nxt - span_lo;
         const int pa_hi = nb < hi ? (int)nb : hi;
         segment_coeffs_d<NG>(A, rot[sp], g1, g2);
         const int k0 = pa_lo + lane;
@@ -363,6 +399,8 @@ __device__ __forceinline__ void fp64a_item(const Grid& g, const Tables& tb, cons
     int nflush = 0;
     int pk = -1;         // this lane's segment (bin-by-bin tiles)
     int nxt = -1;        // first bin (span-relative) of the segment after pk
+    int trk = -1;        // warp-uniform segment of the latest piece start (expansion tiles) and
+    int64_t trk_nxt = 0; // the first bin (absolute) of the segment after it
 
     for (int ti = 0; ti < kTilesA; ti++) {
         const AnchorD& A = anc[ti];
@@ -372,16 +410,16 @@ __device__ __forceinline__ void fp64a_item(const Grid& g, const Tables& tb, cons
         if (A.mode != 2) {
             if (A.mode == 5)
                 expansion_tile<6, 2>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
-                                     nflush, acc);
+                                     nflush, trk, trk_nxt, acc);
             else if (A.mode == 4)
                 expansion_tile<7, 3>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
-                                     nflush, acc);
+                                     nflush, trk, trk_nxt, acc);
             else if (A.mode == 3)
                 expansion_tile<8, 5>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
-                                     nflush, acc);
+                                     nflush, trk, trk_nxt, acc);
             else
                 expansion_tile<10, 7>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
-                                      nflush, acc);
+                                      nflush, trk, trk_nxt, acc);
             pk = -1;
             nxt = -1;
         } else {

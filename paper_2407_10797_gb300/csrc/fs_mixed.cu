@@ -15,8 +15,8 @@
 // and the seven segment sums accumulate with compensation: each lane sums a
 // tile's bins in FP32 (at most 16 terms per f32x2 half per single-segment
 // piece), folds the tile's sum into a per-lane (sum, error) pair by an exact
-// TwoSum, the pairs are combined across the warp by TwoSum as well, and the
-// result goes to FP64 partials that the solve kernel adds in FP64.  A tile whose quartic phase
+// TwoSum, the pairs are combined across the warp by TwoSum as well (a
+// reduce-scatter over the seven sums), and the result goes to FP64 partials that the solve kernel adds in FP64.  A tile whose quartic phase
 // remainder exceeds 1e-6 cycle, whose t(f) remainder moves alpha by more than
 // 1e-6 rad, or whose |d(alpha)| exceeds 0.06 rad is evaluated bin by bin in
 // FP64 instead, so the mode stays correct on any grid.
@@ -236,19 +236,60 @@ __device__ __forceinline__ void comp_add(float& s, float& c, float x) {
     c = __fadd_rn(c, e);
 }
 
-// Sum of the 32 lanes' (s, c) pairs, compensated at every level of the
-// butterfly; every lane ends with the same value (TwoSum is symmetric).
-__device__ __forceinline__ double warp_sum_comp(float s, float c) {
+// One compensated TwoSum step of the flush below: the pair kept by this lane
+// plus the partner's copy of the same slot.
+__device__ __forceinline__ void comp_merge(float ks, float kc, float rs, float rc, float& s, float& c) {
+    float t, e;
+    two_sum_f(ks, rs, t, e);
+    s = t;
+    c = __fadd_rn(__fadd_rn(kc, rc), e);
+}
+
+// The warp's sums of the seven compensated pairs (s[i], c[i]) into dst[0..6]:
+// a reduce-scatter butterfly over eight slots (the eighth zero).  At the XOR
+// distances 16, 8 and 4 each lane keeps half of its slots -- the upper half
+// if its lane bit is set -- and adds the partner's copies of them, so that
+// after three steps lane l holds slot 4 b4 + 2 b3 + b2 (b_j bit j of l) of
+// its group of eight; distances 2 and 1 then sum the four lanes that hold
+// the same slot, and the first of them writes it.  Every addition is a
+// TwoSum with the rounding errors carried in c.  9 merges instead of the 35
+// of seven separate warp trees.
+__device__ __forceinline__ void warp_flush7_comp(const float s[7], const float c[7], double* dst, int lane) {
+    float S4[4], C4[4];
+    const bool h16 = (lane & 16) != 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-        float t, e;
-        two_sum_f(s, s2, t, e);
-        s = t;
-        c = __fadd_rn(__fadd_rn(c, c2), e);
+    for (int i = 0; i < 4; i++) {
+        const float lo_s = s[i], lo_c = c[i];
+        const float hi_s = i + 4 < 7 ? s[i + 4] : 0.f, hi_c = i + 4 < 7 ? c[i + 4] : 0.f;
+        const float ks = h16 ? hi_s : lo_s, kc = h16 ? hi_c : lo_c;
+        const float gs = h16 ? lo_s : hi_s, gc = h16 ? lo_c : hi_c;
+        const float rs = __shfl_xor_sync(0xffffffffu, gs, 16), rc = __shfl_xor_sync(0xffffffffu, gc, 16);
+        comp_merge(ks, kc, rs, rc, S4[i], C4[i]);
     }
-    return (double)s + (double)c;
+    float S2[2], C2[2];
+    const bool h8 = (lane & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float ks = h8 ? S4[i + 2] : S4[i], kc = h8 ? C4[i + 2] : C4[i];
+        const float gs = h8 ? S4[i] : S4[i + 2], gc = h8 ? C4[i] : C4[i + 2];
+        const float rs = __shfl_xor_sync(0xffffffffu, gs, 8), rc = __shfl_xor_sync(0xffffffffu, gc, 8);
+        comp_merge(ks, kc, rs, rc, S2[i], C2[i]);
+    }
+    float S1, C1;
+    {
+        const bool h4 = (lane & 4) != 0;
+        const float ks = h4 ? S2[1] : S2[0], kc = h4 ? C2[1] : C2[0];
+        const float gs = h4 ? S2[0] : S2[1], gc = h4 ? C2[0] : C2[1];
+        const float rs = __shfl_xor_sync(0xffffffffu, gs, 4), rc = __shfl_xor_sync(0xffffffffu, gc, 4);
+        comp_merge(ks, kc, rs, rc, S1, C1);
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+        const float rs = __shfl_xor_sync(0xffffffffu, S1, o), rc = __shfl_xor_sync(0xffffffffu, C1, o);
+        comp_merge(S1, C1, rs, rc, S1, C1);
+    }
+    const int slot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && slot < 7) dst[slot] = (double)S1 + (double)C1;
 }
 
 // Per-bin values of the FS_MIXED body that the probe entry point reports (one
@@ -508,6 +549,8 @@ __device__ __forceinline__ void mixed_walk(const Grid& g, const Tables& tb, cons
     int nflush = 0;
     int pk = -1;         // this lane's segment
     int nxt = -1;        // first bin (span-relative) of the segment after pk
+    int trk = -1;        // warp-uniform segment of the latest piece start (polynomial tiles) and
+    int64_t trk_nxt = 0; // the first bin (absolute) of the segment after it
     float g1[7], g2[7];
 
     for (int ti = src.first(); ti <= src.last(); ti++) {
@@ -529,21 +572,30 @@ __device__ __forceinline__ void mixed_walk(const Grid& g, const Tables& tb, cons
             const float q[4] = {A.q[0], A.q[1], A.q[2], A.q[3]};
             int pa_lo = lo;
             while (pa_lo < hi) {
-                const int sp = sv.seg(span_lo + pa_lo);   // warp-uniform
+                // segment of the piece's first bin (sv.seg of it), tracked forward: piece starts only
+                // increase within a work item, so a segment boundary costs one sv.start
+                const int64_t kabs = span_lo + pa_lo;
+                if (trk < 0) {
+                    trk = sv.seg(kabs);
+                    trk_nxt = sv.start(trk + 1);
+                }
+                while (kabs >= trk_nxt) {
+                    trk++;
+                    trk_nxt = sv.start(trk + 1);
+                }
+                const int sp = trk;   // warp-uniform
                 if (sp != cur) {
                     // segment `cur` ended before this piece: flush it
                     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
 #pragma unroll
-                    for (int c = 0; c < 7; c++) {
-                        comp_add(accS[c], accC[c], acc[c]);
-                        const double v = warp_sum_comp(accS[c], accC[c]);
-                        if (lane == 0) dst[c] = v;
-                        accS[c] = accC[c] = acc[c] = 0.f;
-                    }
+                    for (int c = 0; c < 7; c++) comp_add(accS[c], accC[c], acc[c]);
+                    warp_flush7_comp(accS, accC, dst, lane);
+#pragma unroll
+                    for (int c = 0; c < 7; c++) accS[c] = accC[c] = acc[c] = 0.f;
                     nflush++;
                     cur = sp;
                 }
-                const int64_t nb = sv.start(sp + 1) - span_lo;
+                const int64_t nb = trk_nxt - span_lo;
                 const int pa_hi = nb < hi ? (int)nb : hi;
                 segment_coeffs(A, rot64[sp], rot32[sp], g1, g2);
                 const int k0 = pa_lo + lane;
@@ -620,12 +672,10 @@ __device__ __forceinline__ void mixed_walk(const Grid& g, const Tables& tb, cons
                     if (!more) break;
                     double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
 #pragma unroll
-                    for (int c = 0; c < 7; c++) {
-                        comp_add(accS[c], accC[c], acc[c]);
-                        const double v = warp_sum_comp(accS[c], accC[c]);
-                        if (lane == 0) dst[c] = v;
-                        accS[c] = accC[c] = acc[c] = 0.f;
-                    }
+                    for (int c = 0; c < 7; c++) comp_add(accS[c], accC[c], acc[c]);
+                    warp_flush7_comp(accS, accC, dst, lane);
+#pragma unroll
+                    for (int c = 0; c < 7; c++) accS[c] = accC[c] = acc[c] = 0.f;
                     nflush++;
                     int cand = (valid && pk > cur) ? pk : INT_MAX;
 #pragma unroll
@@ -639,12 +689,7 @@ __device__ __forceinline__ void mixed_walk(const Grid& g, const Tables& tb, cons
         src.end(ti, lane);
     }
     if (cur < 0) return;   // no in-band bin in this span (warp-uniform)
-    double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
-#pragma unroll
-    for (int c = 0; c < 7; c++) {
-        const double v = warp_sum_comp(accS[c], accC[c]);
-        if (lane == 0) dst[c] = v;
-    }
+    warp_flush7_comp(accS, accC, (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7, lane);
 }
 
 // One work item, both phases, tables from global memory.
