@@ -338,7 +338,10 @@ def fp32_peak_tflops() -> float:
 # are FP64 work; the census reports how many there are (none on the paper
 # workload).
 MIXED_FLOP_PER_PBIN = 80.0 + 49.0 / 32.0
-MIXED_TIER_FLOP = {1: MIXED_FLOP_PER_PBIN, 2: MIXED_FLOP_PER_PBIN}
+# the low-degree tier (census mode 3): antenna pair of degree 3 (12 instead of
+# 24) and Doppler polynomials of degrees 2 and 2 (11 instead of 17)
+MIXED_LOW_FLOP_PER_PBIN = 62.0 + 49.0 / 32.0
+MIXED_TIER_FLOP = {1: MIXED_FLOP_PER_PBIN, 2: MIXED_FLOP_PER_PBIN, 3: MIXED_LOW_FLOP_PER_PBIN}
 
 RUNS, NPART = 8, 40
 

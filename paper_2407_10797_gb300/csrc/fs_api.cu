@@ -77,7 +77,7 @@ struct fs_plan {
     TuneRec tuned[kTuneMax];
     int n_tuned;
     int* span_list;      // [B][nspans] in-band particles per span (mixed path)
-    int* span_cnt;       // [nspans] counts, [nspans + 1] item offsets, [3] persistent-kernel counters
+    int* span_cnt;       // span_sched_ints(nspans): counts, item prefixes, persistent-kernel counters
     // swarm evaluation scratch and the captured PSO iteration
     fs_params* pso_params;   // [B_cap]
     double* pso_F;           // [B_cap]
@@ -221,8 +221,8 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
         (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->span_list, sizeof(int) * (size_t)nb * (nt > 0 ? nt : 1))) != cudaSuccess ||
-        (e = cudaMalloc(&p->span_cnt, sizeof(int) * (2 * nt + 4))) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->span_cnt, 0, sizeof(int) * (2 * nt + 4), p->stream)) != cudaSuccess ||
+        (e = cudaMalloc(&p->span_cnt, sizeof(int) * fs::span_sched_ints(nt))) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->span_cnt, 0, sizeof(int) * fs::span_sched_ints(nt), p->stream)) != cudaSuccess ||
         (e = cudaMalloc(&p->pso_params, sizeof(fs_params) * (size_t)nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->pso_F, sizeof(double) * (size_t)nb)) != cudaSuccess) {
         free_workspace(p);

@@ -63,6 +63,31 @@ __device__ __forceinline__ SegView seg_view(const Segs& sg, const Particle& P) {
     return v;
 }
 
+// Work item `item` of the persistent kernels' order (every heavy item, then
+// the others; the span-list buffer layout is launch_span_lists'): its span
+// and particle.  Warp-uniform; false once item is past the last one.
+__device__ __forceinline__ bool sched_item(const int* __restrict__ sched, int nspans, int B,
+                                           const int* __restrict__ list, int item, int& span, int& b) {
+    const int* off_h = sched + nspans;
+    const int* nh = sched + 2 * nspans + 4;
+    const int* off_l = sched + 3 * nspans + 4;
+    const int th = off_h[nspans];
+    const bool heavy = item < th;
+    const int i = heavy ? item : item - th;
+    const int* off = heavy ? off_h : off_l;
+    if (i >= off[nspans]) return false;
+    // span = the last s with off[s] <= i (off is non-decreasing, off[0] = 0)
+    int lo = 0, hi = nspans;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    span = lo;
+    b = list[(int64_t)lo * B + (i - off[lo]) + (heavy ? 0 : nh[lo])];
+    return true;
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

@@ -507,27 +507,20 @@ fp64a_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, 
 // Persistent form: warps take (span, particle) items from a device counter.
 __global__ void __launch_bounds__(kWarpsA * 32, 3)
 fp64a_persistent_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
-                        const int* __restrict__ list, const int* __restrict__ off, int nspans, int* ctl) {
+                        const int* __restrict__ list, const int* __restrict__ sched, int nspans, int* ctl) {
     __shared__ double2 tab[kTabA];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AnchorD* anc = reinterpret_cast<AnchorD*>(smem_raw) + (threadIdx.x >> 5) * 32;
     fill_table(tab);
     const int lane = threadIdx.x & 31;
-    const int total = off[nspans];
     while (true) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&ctl[1], 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
-        int lo = 0, hi = nspans;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (off[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int b = list[(int64_t)lo * B + (item - off[lo])];
+        int span, b;
+        if (!sched_item(sched, nspans, B, list, item, span, b)) break;   // heavy items first
         __syncwarp();
-        fp64a_item(g, tb, parts, sg, pa, tab, lo, b, anc, lane);
+        fp64a_item(g, tb, parts, sg, pa, tab, span, b, anc, lane);
     }
 }
 
@@ -559,7 +552,7 @@ cudaError_t launch_fp64a_main(const Grid& g, const Tables& t, const Particle* pa
         if ((e = allow_smem(fp64a_persistent_kernel, smem, 1)) != cudaSuccess) return e;
         const int grid = persistent_grid(fp64a_persistent_kernel, kWarpsA * 32, smem, 2);
         if (grid <= 0) return cudaErrorInvalidConfiguration;
-        fp64a_persistent_kernel<<<grid, kWarpsA * 32, smem, s>>>(g, t, parts, B, sg, pa, list, cnt + nspans, nspans,
+        fp64a_persistent_kernel<<<grid, kWarpsA * 32, smem, s>>>(g, t, parts, B, sg, pa, list, cnt, nspans,
                                                                  cnt + 2 * nspans + 1);
         return cudaGetLastError();
     }

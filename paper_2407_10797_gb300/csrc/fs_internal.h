@@ -99,9 +99,19 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
                           double* Fpart, double* F, cudaStream_t s,
                           double* amp = nullptr, const int* amp_exp = nullptr);
-// In-band particle lists per span of span_len bins (list [nspans][B], cnt
-// [nspans]); with offsets, also the item prefix cnt[nspans..2 nspans] and the
-// persistent-kernel counters cnt[2 nspans + 1 ..].
+// In-band particle lists per span of span_len bins: list [nspans][B] holds
+// span s's in-band particles, the heavy ones (kHeavyBounds or more segment
+// boundaries inside the span) first, each class in increasing particle
+// order.  The int buffer `cnt` (span_sched_ints(nspans) entries) holds
+//   [0, ns)            cnt[s]: in-band particles of span s
+//   [ns, 2 ns + 1)     exclusive prefix over spans of the heavy counts (with offsets)
+//   [2 ns + 1, +3)     persistent-kernel counters
+//   [2 ns + 4, 3 ns + 4)  heavy count of span s
+//   [3 ns + 4, 4 ns + 5)  exclusive prefix over spans of the other counts (with offsets)
+// The persistent kernels take every heavy item before the others, so that
+// the items with the most per-segment work do not start last.
+constexpr int kHeavyBounds = 16;
+inline int span_sched_ints(int nspans) { return 4 * nspans + 8; }
 cudaError_t launch_span_lists(const Particle* parts, int B, const Segs& sg, int nspans, int span_len, int* list,
                               int* cnt, bool offsets, cudaStream_t s);
 // FS_FP64 anchored form (spans of fp64a_span() bins; partial slots per span).

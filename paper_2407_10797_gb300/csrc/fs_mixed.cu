@@ -32,6 +32,11 @@ constexpr int kTileMix = 1024;                        // bins per anchor: 32 lan
 constexpr int kTilesPerSpan = 32;                     // anchors per warp span (one per lane in phase A)
 constexpr int kSpanMix = kTileMix * kTilesPerSpan;    // 32768 bins: H/T granularity of this path
 constexpr int kWarpsMix = 8;                          // particles per CTA
+// Polynomial degrees of the FP32 body: antenna pair in d(alpha), Doppler
+// E (times d(alpha)) and Q (times dk) -- the full tier (mode 1) and the
+// low-degree tier (mode 3) that tiles with a small d(alpha) range take
+constexpr int kNGFull = 6, kNEFull = 4, kNQFull = 3;
+constexpr int kNGLow = 3, kNELow = 2, kNQLow = 2;
 
 struct Anchor {
     unsigned long long c[4];   // c0..c3 of the orbital-minus-Doppler phase polynomial, cycles mod 1, units 2^-64
@@ -41,7 +46,7 @@ struct Anchor {
     float q[4];                // Doppler: AU cos(beta) df cos^(n)(alpha_a - phi)/n!, n = 0..3 (cycles per bin)
     float Fd[6][2];            // F+^(n)(alpha_a)/n!, Fx^(n)(alpha_a)/n!, n = 1..6
     int ja, lo, hi;            // anchor bin and in-band range [lo, hi) of the tile, relative to the span start
-    int mode;                  // 0: no in-band bin, 1: polynomial, 2: bin-by-bin FP64
+    int mode;                  // 0: no in-band bin, 1: polynomial, 3: low-degree polynomial, 2: bin-by-bin FP64
 };
 
 // Bin-by-bin FP64 evaluation for tiles where the anchor expansion is not
@@ -204,6 +209,31 @@ __device__ __noinline__ void make_anchor(const Grid& g, const Tables& tb, const 
     const float da_max = fabsf(A.w1) * hm + fabsf(A.w2) * hm * hm;
     const bool finite = isfinite(rem_phase) && isfinite(da_max);
     A.mode = (finite && rem_phase <= 1e-6f && rem_alpha <= 1e-6f && da_max <= 0.06f) ? 1 : 2;
+    if (A.mode == 1) {
+        // low-degree tier (antenna degree kNGLow, Doppler terms to d(alpha)^(kNELow + 1) and
+        // dk d(alpha)^kNQLow): the dropped terms, bounded over |d(alpha)| <= da_max, stay below
+        // 2^-26 of the antenna pair's magnitude and below 1e-8 cycle of Doppler phase -- under the
+        // FP32 rounding of the values they would have changed
+        float tG = 0.f, sF = fabsf((float)A.Fpa) + fabsf((float)A.Fxa), p = 1.f;
+        for (int n = 1; n <= 6; n++) {
+            p *= da_max;
+            const float t = (fabsf(A.Fd[n - 1][0]) + fabsf(A.Fd[n - 1][1])) * p;
+            sF += t;
+            if (n > kNGLow) tG += t;
+        }
+        float tD = 0.f;
+        p = 1.f;
+        for (int n = 1; n <= 5; n++) {
+            p *= da_max;
+            if (n > kNELow + 1) tD += fabsf(A.e[n - 1]) * p;
+        }
+        p = 1.f;
+        for (int n = 0; n <= 3; n++) {
+            if (n > kNQLow) tD += hm * fabsf(A.q[n]) * p;
+            p *= da_max;
+        }
+        if (tG <= 0x1p-26f * sF && tD <= 1e-8f) A.mode = 3;
+    }
 }
 
 // Coefficients of G1 = c F+ + s Fx and G2 = c Fx - s F+ in powers of d(alpha)
@@ -316,17 +346,23 @@ enum ProbeField {
 // One bin of a polynomial tile inside a single segment: phase from the
 // fixed-point value Fv, antenna and Doppler from the orbital-phase offset,
 // seven sums into acc.
-template <bool PROBE = false>
+// Horner's scheme on the first N + 1 coefficients.
+template <int N>
+__device__ __forceinline__ float horner_f(const float* c, float x) {
+    float v = c[N];
+#pragma unroll
+    for (int n = N - 1; n >= 0; n--) v = fmaf(v, x, c[n]);
+    return v;
+}
+
+template <bool PROBE, int NG, int NE, int NQ>
 __device__ __forceinline__ void mixed_bin(unsigned long long Fv, float d, float4 tw, float w1, float w2,
                                           const float g1[7], const float g2[7], const float e[5], const float q[4],
                                           float acc[7], float* pr = nullptr) {
     const float da = fmaf(w2, d, w1) * d;
-    const float G1 =
-        fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g1[6], da, g1[5]), da, g1[4]), da, g1[3]), da, g1[2]), da, g1[1]), da, g1[0]);
-    const float G2 =
-        fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(g2[6], da, g2[5]), da, g2[4]), da, g2[3]), da, g2[2]), da, g2[1]), da, g2[0]);
-    const float dop = fmaf(da, fmaf(fmaf(fmaf(fmaf(e[4], da, e[3]), da, e[2]), da, e[1]), da, e[0]),
-                           d * fmaf(fmaf(fmaf(q[3], da, q[2]), da, q[1]), da, q[0]));
+    const float G1 = horner_f<NG>(g1, da);
+    const float G2 = horner_f<NG>(g2, da);
+    const float dop = fmaf(da, horner_f<NE>(e, da), d * horner_f<NQ>(q, da));
     float ph = fmaf((float)(int)(Fv >> 32), 2.3283064365386963e-10f, -dop);
     ph -= rintf(ph);
     float sn, cs;
@@ -391,30 +427,32 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
 
 // Coefficients of one single-segment piece, each duplicated into both halves;
 // the Doppler ones negated so that one fused chain gives minus the offset.
+template <int NG, int NE, int NQ>
 struct PairCoeffs {
     f32x2 w1, w2;
-    f32x2 ne[5], nq[4];
-    f32x2 g1[7], g2[7];
+    f32x2 ne[NE + 1], nq[NQ + 1];
+    f32x2 g1[NG + 1], g2[NG + 1];
 };
 
 // Bins k (low half) and k + 32 (high half) of a polynomial piece: the same
 // operations as mixed_bin on both, sums into the packed accumulators.
+template <int NG, int NE, int NQ>
 __device__ __forceinline__ void mixed_pair(unsigned long long Fa, unsigned long long Fb, float d, float4 ta,
-                                           float4 tb, const PairCoeffs& C, f32x2 acc[7]) {
+                                           float4 tb, const PairCoeffs<NG, NE, NQ>& C, f32x2 acc[7]) {
     const f32x2 D = pk2(d, d + 32.f);
     const f32x2 DA = mul2(fma2(C.w2, D, C.w1), D);
-    f32x2 G1 = C.g1[6], G2 = C.g2[6];
+    f32x2 G1 = C.g1[NG], G2 = C.g2[NG];
 #pragma unroll
-    for (int n = 5; n >= 0; n--) {
+    for (int n = NG - 1; n >= 0; n--) {
         G1 = fma2(G1, DA, C.g1[n]);
         G2 = fma2(G2, DA, C.g2[n]);
     }
-    f32x2 E = C.ne[4];
+    f32x2 E = C.ne[NE];
 #pragma unroll
-    for (int n = 3; n >= 0; n--) E = fma2(E, DA, C.ne[n]);
-    f32x2 Q = C.nq[3];
+    for (int n = NE - 1; n >= 0; n--) E = fma2(E, DA, C.ne[n]);
+    f32x2 Q = C.nq[NQ];
 #pragma unroll
-    for (int n = 2; n >= 0; n--) Q = fma2(Q, DA, C.nq[n]);
+    for (int n = NQ - 1; n >= 0; n--) Q = fma2(Q, DA, C.nq[n]);
     const f32x2 ndop = fma2(DA, E, mul2(D, Q));
     const f32x2 ph = fma2(pk2((float)(int)(Fa >> 32), (float)(int)(Fb >> 32)), pk2(2.3283064365386963e-10f,
                           2.3283064365386963e-10f), ndop);
@@ -440,32 +478,53 @@ __device__ __forceinline__ void mixed_pair(unsigned long long Fa, unsigned long 
     acc[6] = fma2(mul2(Wt, G2), G2, acc[6]);
 }
 
-// In-band particles of every span, in increasing particle order: one warp per
-// span.  list[span * B + j] is the j-th particle whose band meets the span and
-// cnt[span] their number, so no warp of the fused kernel idles on a particle
-// that has no bin in the span.  With `off` given, the last CTA to finish
-// (counted on ctl[0]) also writes the exclusive prefix off[s] = sum of cnt
-// over spans before s, off[nspans] = the number of work items, and resets the
+// Whether particle b's band meets bins [lo, hi], and whether the span holds
+// kHeavyBounds or more of its segment boundaries.
+__device__ __forceinline__ void span_member(const Particle* __restrict__ parts, int B, const Segs& sg, int b,
+                                            int64_t lo, int64_t hi, bool& in, bool& heavy) {
+    in = heavy = false;
+    if (b >= B || !parts[b].valid) return;
+    const SegView sv = seg_view(sg, parts[b]);
+    in = sv.lo <= sv.hi && sv.lo <= hi && sv.hi >= lo;
+    if (in) heavy = sv.seg(sv.hi < hi ? sv.hi : hi) - sv.seg(sv.lo > lo ? sv.lo : lo) >= kHeavyBounds;
+}
+
+// In-band particles of every span: one warp per span.  list[span * B + j] is
+// the j-th particle whose band meets the span -- the heavy ones (kHeavyBounds
+// or more segment boundaries in the span) first, each class in increasing
+// particle order -- cnt[span] their number and nh[span] the heavy ones', so
+// no warp of the fused kernel idles on a particle that has no bin in the
+// span.  With `off` given, the last CTA to finish (counted on ctl[0]) also
+// writes the exclusive prefixes over spans of the heavy counts (off) and of
+// the others (off_l), each with its total at [nspans], and resets the
 // persistent kernel's item counter ctl[1] and ctl[0] itself to zero.
 __global__ void span_lists_kernel(const Particle* __restrict__ parts, int B, Segs sg, int nspans, int span_len,
-                                  int* list, int* cnt, int* off, int* ctl) {
+                                  int* list, int* cnt, int* off, int* ctl, int* nh, int* off_l) {
     const int lane = threadIdx.x & 31;
     const int span = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (span < nspans) {   // warp-uniform
         const int64_t lo = (int64_t)span * span_len, hi = lo + span_len - 1;
-        int n = 0;
+        const unsigned below = (1u << lane) - 1u;
+        int nheavy = 0;
+        for (int b0 = 0; b0 < B; b0 += 32) {
+            bool in, heavy;
+            span_member(parts, B, sg, b0 + lane, lo, hi, in, heavy);
+            nheavy += __popc(__ballot_sync(0xffffffffu, in && heavy));
+        }
+        int wh = 0, wl = nheavy;
         for (int b0 = 0; b0 < B; b0 += 32) {
             const int b = b0 + lane;
-            bool in = false;
-            if (b < B && parts[b].valid) {
-                const SegView sv = seg_view(sg, parts[b]);
-                in = sv.lo <= sv.hi && sv.lo <= hi && sv.hi >= lo;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, in);
-            if (in) list[(int64_t)span * B + n + __popc(m & ((1u << lane) - 1u))] = b;
-            n += __popc(m);
+            bool in, heavy;
+            span_member(parts, B, sg, b, lo, hi, in, heavy);
+            const unsigned mh = __ballot_sync(0xffffffffu, in && heavy), ml = __ballot_sync(0xffffffffu, in && !heavy);
+            if (in) list[(int64_t)span * B + (heavy ? wh + __popc(mh & below) : wl + __popc(ml & below))] = b;
+            wh += __popc(mh);
+            wl += __popc(ml);
         }
-        if (lane == 0) cnt[span] = n;
+        if (lane == 0) {
+            cnt[span] = wl;
+            nh[span] = nheavy;
+        }
     }
     if (off == nullptr) return;   // uniform over the grid
     __shared__ int last;
@@ -475,21 +534,30 @@ __global__ void span_lists_kernel(const Particle* __restrict__ parts, int B, Seg
     __syncthreads();
     if (!last || threadIdx.x >= 32) return;
     __threadfence();
-    int run = 0;
+    int run_h = 0, run_l = 0;
     for (int s0 = 0; s0 < nspans; s0 += 32) {
         const int s = s0 + lane;
-        const int v = s < nspans ? __ldcg(&cnt[s]) : 0;
-        int x = v;
+        const int vh = s < nspans ? __ldcg(&nh[s]) : 0;
+        const int vl = s < nspans ? __ldcg(&cnt[s]) - vh : 0;
+        int xh = vh, xl = vl;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const int yh = __shfl_up_sync(0xffffffffu, xh, o), yl = __shfl_up_sync(0xffffffffu, xl, o);
+            if (lane >= o) {
+                xh += yh;
+                xl += yl;
+            }
         }
-        if (s < nspans) off[s] = run + x - v;
-        run += __shfl_sync(0xffffffffu, x, 31);
+        if (s < nspans) {
+            off[s] = run_h + xh - vh;
+            off_l[s] = run_l + xl - vl;
+        }
+        run_h += __shfl_sync(0xffffffffu, xh, 31);
+        run_l += __shfl_sync(0xffffffffu, xl, 31);
     }
     if (lane == 0) {
-        off[nspans] = run;
+        off[nspans] = run_h;
+        off_l[nspans] = run_l;
         ctl[1] = 0;
         ctl[0] = 0;
     }
@@ -499,8 +567,10 @@ cudaError_t launch_span_lists(const Particle* parts, int B, const Segs& sg, int 
                               int* cnt, bool offsets, cudaStream_t s) {
     int* off = cnt + nspans;
     int* ctl = cnt + 2 * nspans + 1;
-    span_lists_kernel<<<(unsigned)((nspans * 32 + 255) / 256), 256, 0, s>>>(parts, B, sg, nspans, span_len, list,
-                                                                             cnt, offsets ? off : nullptr, ctl);
+    int* nh = cnt + 2 * nspans + 4;
+    int* off_l = cnt + 3 * nspans + 4;
+    span_lists_kernel<<<(unsigned)((nspans * 32 + 255) / 256), 256, 0, s>>>(
+        parts, B, sg, nspans, span_len, list, cnt, offsets ? off : nullptr, ctl, nh, off_l);
     return cudaGetLastError();
 }
 
@@ -525,6 +595,59 @@ struct GlobalTables {
     __device__ const float4* begin(int) const { return tw_span; }   // indexed by span-relative bin
     __device__ void end(int, int) const {}
 };
+
+// The bins [pa_lo, pa_hi) of one single-segment piece of a polynomial tile
+// with antenna degree NG and Doppler degrees NE, NQ: each lane walks bins
+// pa_lo + lane + 32 j, two per iteration (k and k + 32, the f32x2 halves),
+// the fixed-point phase by forward differences; sums into acc.
+template <int NG, int NE, int NQ>
+__device__ __forceinline__ void piece_bins(const Anchor& A, int pa_lo, int pa_hi, int lane, const float4* tw_span,
+                                           const float g1[7], const float g2[7], const float e[5], const float q[4],
+                                           float acc[7]) {
+    const float w1 = A.w1, w2 = A.w2;
+    const int k0 = pa_lo + lane;
+    const long long d0 = (long long)(k0 - A.ja);
+    const unsigned long long y0 = poly_fx(A.c, d0), y1 = poly_fx(A.c, d0 + 32),
+                             y2 = poly_fx(A.c, d0 + 64), y3 = poly_fx(A.c, d0 + 96);
+    unsigned long long F = y0, D1 = y1 - y0, D2 = y2 - 2ull * y1 + y0,
+                       D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
+    float d = (float)(k0 - A.ja);
+    int k = k0;
+    if (k + 32 < pa_hi) {
+        // two bins per lane per iteration (k and k + 32), packed into f32x2 halves
+        PairCoeffs<NG, NE, NQ> C;
+        C.w1 = pk2(w1, w1);
+        C.w2 = pk2(w2, w2);
+#pragma unroll
+        for (int n = 0; n <= NE; n++) C.ne[n] = pk2(-e[n], -e[n]);
+#pragma unroll
+        for (int n = 0; n <= NQ; n++) C.nq[n] = pk2(-q[n], -q[n]);
+#pragma unroll
+        for (int n = 0; n <= NG; n++) {
+            C.g1[n] = pk2(g1[n], g1[n]);
+            C.g2[n] = pk2(g2[n], g2[n]);
+        }
+        f32x2 acc2[7];
+#pragma unroll
+        for (int c = 0; c < 7; c++) acc2[c] = 0ull;   // (+0.0f, +0.0f)
+        for (; k + 32 < pa_hi; k += 64, d += 64.f) {
+            const float4 twa = tw_span[k];
+            const float4 twb = tw_span[k + 32];
+            const unsigned long long Fa = F, Fb = F + D1;
+            F = Fb + D1 + D2;
+            D1 += 2ull * D2 + D3;
+            D2 += 2ull * D3;
+            mixed_pair(Fa, Fb, d, twa, twb, C, acc2);
+        }
+#pragma unroll
+        for (int c = 0; c < 7; c++) {
+            float lo2, hi2;
+            up2(acc2[c], lo2, hi2);
+            acc[c] += lo2 + hi2;
+        }
+    }
+    if (k < pa_hi) mixed_bin<false, NG, NE, NQ>(F, d, tw_span[k], w1, w2, g1, g2, e, q, acc);
+}
 
 // Phase B: the warp walks tiles first()..last() of the span with the table
 // source Src (begin(ti) gives the tile's table entries, indexed by
@@ -565,9 +688,8 @@ __device__ __forceinline__ void mixed_walk(const Grid& g, const Tables& tb, cons
         if (cur < 0) cur = sv.seg(span_lo + lo);
 #pragma unroll
         for (int c = 0; c < 7; c++) acc[c] = 0.f;
-        if (A.mode == 1) {
+        if (A.mode == 1 || A.mode == 3) {
             // polynomial tile, walked as single-segment pieces [pa_lo, pa_hi)
-            const float w1 = A.w1, w2 = A.w2;
             const float e[5] = {A.e[0], A.e[1], A.e[2], A.e[3], A.e[4]};
             const float q[4] = {A.q[0], A.q[1], A.q[2], A.q[3]};
             int pa_lo = lo;
@@ -598,48 +720,10 @@ __device__ __forceinline__ void mixed_walk(const Grid& g, const Tables& tb, cons
                 const int64_t nb = trk_nxt - span_lo;
                 const int pa_hi = nb < hi ? (int)nb : hi;
                 segment_coeffs(A, rot64[sp], rot32[sp], g1, g2);
-                const int k0 = pa_lo + lane;
-                const long long d0 = (long long)(k0 - A.ja);
-                const unsigned long long y0 = poly_fx(A.c, d0), y1 = poly_fx(A.c, d0 + 32),
-                                         y2 = poly_fx(A.c, d0 + 64), y3 = poly_fx(A.c, d0 + 96);
-                unsigned long long F = y0, D1 = y1 - y0, D2 = y2 - 2ull * y1 + y0,
-                                   D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
-                float d = (float)(k0 - A.ja);
-                int k = k0;
-                if (k + 32 < pa_hi) {
-                    // two bins per lane per iteration (k and k + 32), packed into f32x2 halves
-                    PairCoeffs C;
-                    C.w1 = pk2(w1, w1);
-                    C.w2 = pk2(w2, w2);
-#pragma unroll
-                    for (int n = 0; n < 5; n++) C.ne[n] = pk2(-e[n], -e[n]);
-#pragma unroll
-                    for (int n = 0; n < 4; n++) C.nq[n] = pk2(-q[n], -q[n]);
-#pragma unroll
-                    for (int n = 0; n < 7; n++) {
-                        C.g1[n] = pk2(g1[n], g1[n]);
-                        C.g2[n] = pk2(g2[n], g2[n]);
-                    }
-                    f32x2 acc2[7];
-#pragma unroll
-                    for (int c = 0; c < 7; c++) acc2[c] = 0ull;   // (+0.0f, +0.0f)
-                    for (; k + 32 < pa_hi; k += 64, d += 64.f) {
-                        const float4 twa = tw_span[k];
-                        const float4 twb = tw_span[k + 32];
-                        const unsigned long long Fa = F, Fb = F + D1;
-                        F = Fb + D1 + D2;
-                        D1 += 2ull * D2 + D3;
-                        D2 += 2ull * D3;
-                        mixed_pair(Fa, Fb, d, twa, twb, C, acc2);
-                    }
-#pragma unroll
-                    for (int c = 0; c < 7; c++) {
-                        float lo2, hi2;
-                        up2(acc2[c], lo2, hi2);
-                        acc[c] += lo2 + hi2;
-                    }
-                }
-                if (k < pa_hi) mixed_bin(F, d, tw_span[k], w1, w2, g1, g2, e, q, acc);
+                if (A.mode == 1)
+                    piece_bins<kNGFull, kNEFull, kNQFull>(A, pa_lo, pa_hi, lane, tw_span, g1, g2, e, q, acc);
+                else
+                    piece_bins<kNGLow, kNELow, kNQLow>(A, pa_lo, pa_hi, lane, tw_span, g1, g2, e, q, acc);
                 pa_lo = pa_hi;
             }
             // lanes' segment trackers are stale after this tile; the fallback path re-derives them
@@ -720,33 +804,26 @@ mixed_main_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Parti
 }
 
 // Persistent form: a grid of (SMs x resident CTAs) whose warps take work
-// items (span, in-band particle) from a shared counter, in span-major order,
-// until the list is exhausted.  No warp waits on another: a warp that finds
-// the counter past the end returns.
+// items (span, in-band particle) from a shared counter -- every heavy item
+// (many segment boundaries in the span) first, then the others, each class
+// in span-major order -- until the list is exhausted.  No warp waits on
+// another: a warp that finds the counter past the end returns.
 template <int MINB>
 __global__ void __launch_bounds__(kWarpsMix * 32, MINB)
 mixed_persistent_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Particle* __restrict__ parts,
-                        int B, Segs sg, Partials pa, const int* __restrict__ list, const int* __restrict__ off,
+                        int B, Segs sg, Partials pa, const int* __restrict__ list, const int* __restrict__ sched,
                         int nspans, int* ctl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Anchor* anc = reinterpret_cast<Anchor*>(smem_raw) + (threadIdx.x >> 5) * 32;
     const int lane = threadIdx.x & 31;
-    const int total = off[nspans];
     while (true) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&ctl[1], 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
-        // span = the last s with off[s] <= item (off is non-decreasing, off[0] = 0)
-        int lo = 0, hi = nspans;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (off[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int b = list[(int64_t)lo * B + (item - off[lo])];
+        int span, b;
+        if (!sched_item(sched, nspans, B, list, item, span, b)) break;
         __syncwarp();   // every lane is done with the previous item's anchors
-        mixed_item(g, tb, t32, parts, sg, pa, lo, b, anc, lane);
+        mixed_item(g, tb, t32, parts, sg, pa, span, b, anc, lane);
     }
 }
 
@@ -945,10 +1022,10 @@ cudaError_t launch_mixed_main(const Grid& g, const Tables& t, const float4* t32,
                                : persistent_grid(mixed_persistent_kernel<2>, kWarpsMix * 32, smem, 0);
         if (grid <= 0) return cudaErrorInvalidConfiguration;
         if (three)
-            mixed_persistent_kernel<3><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, off,
+            mixed_persistent_kernel<3><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, cnt,
                                                                           nspans, ctl);
         else
-            mixed_persistent_kernel<2><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, off,
+            mixed_persistent_kernel<2><<<grid, kWarpsMix * 32, smem, s>>>(g, t, t32, parts, B, sg, pa, list, cnt,
                                                                           nspans, ctl);
         return cudaGetLastError();
     }
@@ -1027,13 +1104,18 @@ mixed_probe_kernel(Grid g, Tables tb, const float4* __restrict__ t32, const Part
         pr[PR_ROTC_LO] = (float)(rot64[sp].x - (double)(float)rot64[sp].x);
         pr[PR_ROTS_LO] = (float)(rot64[sp].y - (double)(float)rot64[sp].y);
         const float4 tw = t32[k];
-        if (A.mode == 1) {
+        if (A.mode == 1 || A.mode == 3) {
             float g1[7], g2[7], acc[7];
             segment_coeffs(A, rot64[sp], rot32[sp], g1, g2);
             const float e5[5] = {A.e[0], A.e[1], A.e[2], A.e[3], A.e[4]};
             const float q4[4] = {A.q[0], A.q[1], A.q[2], A.q[3]};
             const long long d = (long long)(rel - A.ja);
-            mixed_bin<true>(poly_fx(A.c, d), (float)d, tw, A.w1, A.w2, g1, g2, e5, q4, acc, pr);
+            if (A.mode == 1)
+                mixed_bin<true, kNGFull, kNEFull, kNQFull>(poly_fx(A.c, d), (float)d, tw, A.w1, A.w2, g1, g2, e5, q4,
+                                                           acc, pr);
+            else
+                mixed_bin<true, kNGLow, kNELow, kNQLow>(poly_fx(A.c, d), (float)d, tw, A.w1, A.w2, g1, g2, e5, q4,
+                                                        acc, pr);
         } else {
             float ph, G1, G2, cs, sn, t7[7];
             eval_bin_fallback(P, tb, k, g.alpha0, rot64[sp], &ph, &G1, &G2);
