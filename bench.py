@@ -56,13 +56,15 @@ FP64_DIRECT_FLOP = 203.0
 # N_p = 16).  Both are one pass over the per-bin tables and do not depend on
 # N_p; the FP64 figure holds for the anchored variants (3, 4) only.  None
 # while the kernel has changed since its counters were taken.
-TRAFFIC_FP64_ANCHORED = 76.13e6
-TRAFFIC_MIXED = 48.47e6
-FP64_TIER_FLOP = {1: 96.0, 2: FP64_DIRECT_FLOP, 3: 84.0, 4: 76.0, 5: 70.0}
+TRAFFIC_FP64_ANCHORED = None
+TRAFFIC_MIXED = None
+# mode 6 is tier (6, 2) with the phase remainder in FP32: its FP64 operations
+# are those of mode 5 less d^2, d^4 and the remainder polynomial (7)
+FP64_TIER_FLOP = {1: 96.0, 2: FP64_DIRECT_FLOP, 3: 84.0, 4: 76.0, 5: 70.0, 6: 63.0}
 
 
 def census_sum(counts_by_np):
-    return [int(sum(c[m] for c in counts_by_np.values())) for m in range(6)]
+    return [int(sum(c[m] for c in counts_by_np.values())) for m in range(8)]
 
 
 def flop_per_pbin(counts_by_np, table, direct):

@@ -68,7 +68,7 @@ struct fs_plan {
     // launch variant of the fused kernel: forced (>= 0) or looked up per
     // (N_p, edge kind) among the autotuned choices, else variant 0
     int variant_forced;
-    unsigned long long* census;   // [6] device counters of fs_plan_census
+    unsigned long long* census;   // [fs::kCensusModes] device counters of fs_plan_census
     int census_on;
     struct TuneRec {
         int Np, global, variant;
@@ -475,24 +475,24 @@ fs_status fs_plan_census(fs_plan* p, const fs_params* params_dev, int B, const d
                          int64_t* counts) {
     g_err[0] = 0;
     if (!p || !counts) return fail(FS_EINVAL, "fs_plan_census: NULL plan or counts");
-    for (int i = 0; i < 6; i++) counts[i] = 0;
+    for (int i = 0; i < fs::kCensusModes; i++) counts[i] = 0;
     if (B <= 0) return B == 0 ? FS_OK : fail(FS_EINVAL, "fs_plan_census: B = %d < 0", B);
     cudaError_t e;
-    if (!p->census && (e = cudaMalloc(&p->census, 6 * sizeof(unsigned long long))) != cudaSuccess)
+    if (!p->census && (e = cudaMalloc(&p->census, fs::kCensusModes * sizeof(unsigned long long))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(census)");
     fs_status st = ensure_workspace(p, B, Np);
     if (st != FS_OK) return st;
-    if ((e = cudaMemsetAsync(p->census, 0, 6 * sizeof(unsigned long long), p->stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(p->census, 0, fs::kCensusModes * sizeof(unsigned long long), p->stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync(census)");
     p->census_on = 1;
     st = fstat_impl(p, params_dev, B, edges_dev, Np, p->pso_F, nullptr, nullptr);
     p->census_on = 0;
     if (st != FS_OK) return st;
-    unsigned long long h[6];
+    unsigned long long h[fs::kCensusModes];
     if ((e = cudaMemcpyAsync(h, p->census, sizeof(h), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return cuda_fail(e, "census read-back");
-    for (int i = 0; i < 6; i++) counts[i] = (int64_t)h[i];
+    for (int i = 0; i < fs::kCensusModes; i++) counts[i] = (int64_t)h[i];
     return FS_OK;
 }
 

@@ -14,7 +14,9 @@
 //     12), the antenna ones rotated into the segment's basis per piece;
 //   - total phase: its cubic part in 64-bit fixed point (cycles mod 1, units
 //     of 2^-64), stepped per lane by exact integer forward differences; the
-//     degree 4..4+NR part an FP64 remainder added in units of 2^-48 cycle;
+//     degree 4..4+NR part a remainder added in units of 2^-48 cycle (FP64, or
+//     FP32 in the lowest tier when it is at most 6.7e-8 cycle: error below
+//     2.5e-14 cycle);
 //   - exp(2 pi i Phi): a 1024-entry table value (top 10 bits, rounded) times
 //     the Taylor series of the remaining angle |theta| <= pi/1024 (cos to
 //     degree 4, sin to degree 5).
@@ -22,7 +24,7 @@
 // (10, 7) whose dropped terms, summed over the tile at the anchor, stay below
 // 1e-13 cycle (phase) and 1e-15 (antenna); a tile whose d(alpha) quintic or
 // degree-12 series does not converge is evaluated bin by bin exactly as the
-// direct kernel does.  All arithmetic is FP64 or exact integer; results agree
+// direct kernel does.  All other arithmetic is FP64 or exact integer; results agree
 // with the direct form to rounding level (1e-10 on the F-statistic at full
 // size, 1e-9 against the oracle).
 //
@@ -45,13 +47,14 @@ constexpr int kWarpsA = 4;                       // warps (particles) per CTA
 constexpr int kTabA = 1024;                      // exp(2 pi i j / 1024) table
 
 constexpr int kDeg = 12;                         // Taylor degree in the bin offset d computed at an anchor
+constexpr double kRem32Max = 6.7e-8;             // largest phase remainder (cycles) evaluated in FP32
 
 struct AnchorD {
     unsigned long long c[4];   // cubic of the total phase (orbital minus Doppler), cycles mod 1, units 2^-64
     double R[kDeg - 3];        // its degree 4..12 coefficients (2^-48 cycle per bin^k), FP64
     double FU[2][kDeg + 1];    // F+ and Fx along the tile as polynomials in d (degree 0..12)
     int ja, lo, hi;            // anchor bin and in-band range [lo, hi) of the tile, relative to the span start
-    int mode;                  // 0: no in-band bin, 2: bin by bin, 1/3/4/5: expansion tiers (see expansion_tile)
+    int mode;                  // 0: no in-band bin, 2: bin by bin, 1/3/4/5/6: expansion tiers (see expansion_tile)
 };
 
 __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, const Particle& P, int64_t span_lo,
@@ -216,6 +219,10 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
     // tiers (antenna degree NG, phase remainder degree 4 + NR): 5:(6,2) 4:(7,3) 3:(8,5) 1:(10,7)
     auto ok = [&](int NG, int NR) { return tG[NG + 1] <= 1e-15 && tR[5 + NR] <= 1e-13; };
     A.mode = !converged ? 2 : ok(6, 2) ? 5 : ok(7, 3) ? 4 : ok(8, 5) ? 3 : ok(10, 7) ? 1 : 2;
+    // tier (6, 2) with the remainder evaluated in FP32 (mode 6): when the remainder is at most
+    // kRem32Max cycle over the tile, the FP32 evaluation's error (within 6 roundings of 2^-24 of
+    // sum_k |R_k| hmax^k) stays below 2.5e-14 cycle
+    if (A.mode == 5 && tR[4] <= kRem32Max) A.mode = 6;
     // the remainder is added to the fixed-point phase in units of 2^-48 cycle
     for (int k = 0; k <= kDeg - 4; k++) A.R[k] *= 0x1p48;
 }
@@ -259,12 +266,22 @@ __device__ __forceinline__ void cis_fixed(unsigned long long Ft, const double2* 
 // fixed-point cubic Fv plus the FP64 remainder d^4 (R_4 + R_5 d + ... ), NR + 1
 // terms in units of 2^-48 cycle, added as an integer; the antenna pair is two
 // degree-NG polynomials in d.
-template <int NG, int NR>
-__device__ __forceinline__ void bin_d(unsigned long long Fv, double d, double dr, double di, double W,
-                                      const double Rc[NR + 1], const double g1[NG + 1], const double g2[NG + 1],
-                                      const double2* __restrict__ tab, double acc[7]) {
-    const double dd = d * d;
-    const long long corr = __double2ll_rn((dd * dd) * horner<NR>(Rc, d));   // Rc scaled by 2^48
+template <int NG, int NR, bool R32>
+__device__ __forceinline__ void bin_d(unsigned long long Fv, double d, float dfl, double dr, double di, double W,
+                                      const double Rc[NR + 1], const float Rcf[NR + 1], const double g1[NG + 1],
+                                      const double g2[NG + 1], const double2* __restrict__ tab, double acc[7]) {
+    long long corr;   // the remainder in units of 2^-48 cycle (Rc, Rcf scaled by 2^48)
+    if (R32) {
+        // |remainder| <= kRem32Max cycle: FP32 (|corr| < 2^31), error below 2.5e-14 cycle
+        const float dd = dfl * dfl;
+        float v = Rcf[NR];
+#pragma unroll
+        for (int i = NR - 1; i >= 0; i--) v = fmaf(v, dfl, Rcf[i]);
+        corr = (long long)__float2int_rn((dd * dd) * v);
+    } else {
+        const double dd = d * d;
+        corr = __double2ll_rn((dd * dd) * horner<NR>(Rc, d));
+    }
     double cs, sn;
     cis_fixed(Fv + ((unsigned long long)corr << 16), tab, cs, sn);
     const double G1 = horner<NG>(g1, d);
@@ -316,7 +333,7 @@ __device__ __forceinline__ void flush_d(double acc[7], double* dst, int lane) {
 
 // An expansion tile walked as single-segment pieces [pa_lo, pa_hi): flushes the
 // running segment when a piece starts a new one.
-template <int NG, int NR>
+template <int NG, int NR, bool R32 = false>
 __device__ __forceinline__ void expansion_tile(const AnchorD& A, const SegView& sv, int64_t span_lo, int lo, int hi,
                                                const double2* __restrict__ rot, const double* __restrict__ dwr,
                                                const double* __restrict__ dwi, const double* __restrict__ Wt,
@@ -324,8 +341,12 @@ __device__ __forceinline__ void expansion_tile(const AnchorD& A, const SegView& 
                                                int b, int Np, int lane, int& cur, int& nflush, int& trk,
                                                int64_t& trk_nxt, double acc[7]) {
     double g1[NG + 1], g2[NG + 1], Rc[NR + 1];
+    float Rcf[NR + 1];
 #pragma unroll
-    for (int i = 0; i <= NR; i++) Rc[i] = A.R[i];
+    for (int i = 0; i <= NR; i++) {
+        Rc[i] = A.R[i];
+        Rcf[i] = (float)A.R[i];
+    }
     int pa_lo = lo;
     while (pa_lo < hi) {
         // segment of the piece's first bin (sv.seg of it), tracked forward across the item's
@@ -355,17 +376,19 @@ __device__ __forceinline__ void expansion_tile(const AnchorD& A, const SegView& 
         unsigned long long F = y0, D1 = y1 - y0, D2 = y2 - 2ull * y1 + y0,
                            D3 = y3 - 3ull * y2 + 3ull * y1 - y0;
         double d = (double)(k0 - A.ja);
+        float dfl = (float)(k0 - A.ja);   // the same offset in FP32 (exact: |d| < 2^24)
         int k = k0;
         // two bins per lane per iteration (k and k + 32): two independent chains
-        for (; k + 32 < pa_hi; k += 64, d += 64.0) {
+        for (; k + 32 < pa_hi; k += 64, d += 64.0, dfl += 64.f) {
             const unsigned long long Fa = F, Fb = F + D1;
             F = Fb + D1 + D2;
             D1 += 2ull * D2 + D3;
             D2 += 2ull * D3;
-            bin_d<NG, NR>(Fa, d, dwr[k], dwi[k], Wt[k], Rc, g1, g2, tab, acc);
-            bin_d<NG, NR>(Fb, d + 32.0, dwr[k + 32], dwi[k + 32], Wt[k + 32], Rc, g1, g2, tab, acc);
+            bin_d<NG, NR, R32>(Fa, d, dfl, dwr[k], dwi[k], Wt[k], Rc, Rcf, g1, g2, tab, acc);
+            bin_d<NG, NR, R32>(Fb, d + 32.0, dfl + 32.f, dwr[k + 32], dwi[k + 32], Wt[k + 32], Rc, Rcf, g1, g2, tab,
+                               acc);
         }
-        if (k < pa_hi) bin_d<NG, NR>(F, d, dwr[k], dwi[k], Wt[k], Rc, g1, g2, tab, acc);
+        if (k < pa_hi) bin_d<NG, NR, R32>(F, d, dfl, dwr[k], dwi[k], Wt[k], Rc, Rcf, g1, g2, tab, acc);
         pa_lo = pa_hi;
     }
 }
@@ -408,7 +431,10 @@ __device__ __forceinline__ void fp64a_item(const Grid& g, const Tables& tb, cons
         const int lo = A.lo, hi = A.hi;
         if (cur < 0) cur = sv.seg(span_lo + lo);
         if (A.mode != 2) {
-            if (A.mode == 5)
+            if (A.mode == 6)
+                expansion_tile<6, 2, true>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane,
+                                           cur, nflush, trk, trk_nxt, acc);
+            else if (A.mode == 5)
                 expansion_tile<6, 2>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane, cur,
                                      nflush, trk, trk_nxt, acc);
             else if (A.mode == 4)
