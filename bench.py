@@ -56,8 +56,8 @@ FP64_DIRECT_FLOP = 203.0
 # N_p = 16).  Both are one pass over the per-bin tables and do not depend on
 # N_p; the FP64 figure holds for the anchored variants (3, 4) only.  None
 # while the kernel has changed since its counters were taken.
-TRAFFIC_FP64_ANCHORED = None
-TRAFFIC_MIXED = None
+TRAFFIC_FP64_ANCHORED = 75.92e6
+TRAFFIC_MIXED = 48.59e6
 # mode 6 is tier (6, 2) with the phase remainder in FP32: its FP64 operations
 # are those of mode 5 less d^2, d^4 and the remainder polynomial (7)
 FP64_TIER_FLOP = {1: 96.0, 2: FP64_DIRECT_FLOP, 3: 84.0, 4: 76.0, 5: 70.0, 6: 63.0}
@@ -825,7 +825,9 @@ def run_search(args):
         hs = search.HierarchicalSearch(plan, prior, stages, n_boxes=16, runs_per_box=8,
                                        n_part=40, seed=seed,
                                        surrogate=search.SurrogateSpec() if args.search == "surrogate" else None,
-                                       dmu_hi=args.dmu, progress_every=args.progress)
+                                       dmu_hi=args.dmu, progress_every=args.progress,
+                                       on_progress=lambda e: print(json.dumps({"seed": seed, "progress": e}),
+                                                                   file=sys.stderr, flush=True))
         t0 = time.perf_counter()
         res = hs.run()
         torch.cuda.synchronize()

@@ -193,7 +193,8 @@ class HierarchicalSearch:
                  checkpoint_dir: str | None = None, c1: float = 2.0, c2: float = 2.0, vmax: float = 0.5,
                  bounds: np.ndarray | None = None, surrogate: SurrogateSpec | None = None,
                  autotune: bool | None = None, use_graphs: bool = True, record_history: bool = False,
-                 comm: "Comm | None" = None, dmu_hi: float = 0.0, progress_every: int = 0):
+                 comm: "Comm | None" = None, dmu_hi: float = 0.0, progress_every: int = 0,
+                 on_progress=None):
         """bounds: optional [D, 2] search bounds overriding the prior's (a zero
         width pins a coordinate).  dmu_hi > 0: search delta_mu in [0, dmu_hi]
         as a sixth coordinate (the paper's [0, 0.9], Table I), its full range
@@ -233,6 +234,7 @@ class HierarchicalSearch:
         self.comm = comm
         self.progress_every = int(progress_every)
         self.progress: list = []
+        self.on_progress = on_progress   # optional callable, given each progress entry as it is made
 
     # ---------------------------------------------------------------- boxes
     def stage_layout(self, i: int) -> tuple[int, int, int]:
@@ -354,6 +356,8 @@ class HierarchicalSearch:
         r = int(np.argmax(bf))
         x = sw.pbest_x[r, int(bi[r])].cpu().numpy()
         self.progress.append((stage, it, float(bf[r]), to_physical(x, run_boxes[r], self.q).tolist()))
+        if self.on_progress is not None:
+            self.on_progress(self.progress[-1])
 
     def _run_screened(self, sw, spec: StageSpec, stage_seed: int, stage: int, k0: int = 0, nb: int | None = None,
                       run_boxes=None):
