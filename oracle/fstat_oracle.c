@@ -20,6 +20,9 @@
  *   segment outer edges      Sec. II.B, last paragraph before Fig. 1
  *   waveform h(f), Psi(f)    Appendix A, Eqs. (A1)-(A3)
  *   response x(f) = T(f)h(f) Sec. IV, Eq. (freDres) with N = 0 and no higher d(t) terms
+ *                            (the paper's form), or the series of Eq. (freDres) itself: the
+ *                            filter F^N_{T_f} of order N <= 2 and the terms k <= 1, with the
+ *                            retarded time and the ddot(t) factors of its kernel G (or_mb_response)
  *   t(f)                     Sec. IV, stationary-phase time t_f = (1/2pi) dPhi/df
  *   PSO update               Sec. III.A, Eqs. (pso_position_update), (pso_velocity_update)
  *   extrinsic parameters     Appendix B, Eqs. (B1)-(B3)
@@ -48,6 +51,7 @@
  *     E = (X - 2Y + Z)/sqrt6 and T = (X + Y + Z)/sqrt3 as combinations of their
  *     detector tensors.  T vanishes identically in this limit.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -82,6 +86,9 @@ typedef struct {
     double alpha0; /* orbital phase of the guiding centre at t = 0, rad */
     double orient; /* orientation of the constellation at t = 0, rad */
     int channel;   /* TDI channel: 0 X, 1 A, 2 E, 3 T */
+    int mb_order;  /* -1: the paper's response T = F(t_f) e^{2 pi i f d(t_f)}; 0..2: Eq. (freDres)
+                      with the filter F^N_{T_f} of this order N (see or_mb_response) */
+    int mb_kmax;   /* highest k of the sum in Eq. (freDres), 0 or 1 (only T_A1 is defined) */
 } or_model;
 
 /* ---- masses and PN coefficients (Appendix A) --------------------------- */
@@ -235,6 +242,130 @@ static double or_doppler_delay(const or_params* P, const or_model* m, double t) 
     return OR_AU_S * cos(P->lat) * cos(alpha - P->lon);
 }
 
+/* ---- the series of Eq. (freDres) (Sec. IV) ----------------------------- */
+
+/* First and second time derivatives of the Doppler delay above (closed forms
+ * of d/dt R cos(beta) cos(2 pi t / yr + alpha0 - lambda)). */
+static void or_doppler_rates(const or_params* P, const or_model* m, double t, double* dd, double* d2) {
+    if (m->response == 1) {
+        *dd = 0.0;
+        *d2 = 0.0;
+        return;
+    }
+    double Om = 2.0 * OR_PI / OR_YEAR_S;
+    double x = or_orbit_phase(m, t) - P->lon;
+    double R = OR_AU_S * cos(P->lat);
+    *dd = -R * Om * sin(x);
+    *d2 = -R * Om * Om * cos(x);
+}
+
+/* T_f of Sec. IV: T_f^2 = |d^2 Psi/df^2| / (4 pi) for the waveform phase
+ * Psi = 2 pi Phi_orb, whose first derivative is 2 pi t_f; so T_f^2 =
+ * |dt_f/df| / 2, dt_f/df by the five-point central difference of t(f) with
+ * step 1e-4 f (truncation ~ (1e-4)^4 relative). */
+static double or_tf_width(const or_params* P, const or_model* m, double f) {
+    double h = 1e-4 * f;
+    double d = (-or_time(P, m, f + 2.0 * h) + 8.0 * or_time(P, m, f + h) - 8.0 * or_time(P, m, f - h) +
+                or_time(P, m, f - 2.0 * h)) / (12.0 * h);
+    return sqrt(0.5 * fabs(d));
+}
+
+/* Weights a_j (j = 0..N) of the filter
+ *   F^N_{T_f}[G](t) = 1/2 sum_j a_j (G(t + j T_f) + G(t - j T_f)).
+ * The paper takes them from its ref. marsat2018fourier (App. 2), which is not
+ * at hand.  Reading: the filter stands for the average of G over the
+ * stationary-phase kernel exp(i pi fdot s^2) of the chirp around t_f
+ * (fdot = 1/(2 T_f^2)), whose even moments are <s^2m> = (2m-1)!! (i T_f^2/pi)^m;
+ * the weights make the filter reproduce them for m = 0..N, i.e. exact for G
+ * polynomial of degree <= 2N+1: sum_j a_j j^(2m) = (2m-1)!! (i/pi)^m (with
+ * 0^0 = 1).  Solved by Gaussian elimination (the system is a Vandermonde
+ * system in j^2, well conditioned for N <= 2). */
+void or_mb_weights(int N, double* a_re, double* a_im) {
+    double complex A[3][4];
+    for (int m = 0; m <= N; m++) {
+        double complex rhs = 1.0;
+        for (int i = 1; i <= m; i++) rhs *= (2.0 * i - 1.0) * (I / OR_PI);
+        for (int j = 0; j <= N; j++) {
+            double pw = 1.0;
+            for (int i = 0; i < m; i++) pw *= (double)(j * j);
+            A[m][j] = pw;
+        }
+        A[m][N + 1] = rhs;
+    }
+    for (int c = 0; c <= N; c++) {
+        int piv = c;
+        for (int r = c + 1; r <= N; r++)
+            if (cabs(A[r][c]) > cabs(A[piv][c])) piv = r;
+        for (int j = 0; j <= N + 1; j++) {
+            double complex t = A[c][j];
+            A[c][j] = A[piv][j];
+            A[piv][j] = t;
+        }
+        for (int r = 0; r <= N; r++) {
+            if (r == c) continue;
+            double complex fct = A[r][c] / A[c][c];
+            for (int j = c; j <= N + 1; j++) A[r][j] -= fct * A[c][j];
+        }
+    }
+    for (int j = 0; j <= N; j++) {
+        double complex v = A[j][N + 1] / A[j][j];
+        a_re[j] = creal(v);
+        a_im[j] = cimag(v);
+    }
+}
+
+/* The kernel of Eq. (freDres) for (F+, Fx), times exp(-2 pi i f D0):
+ *   G(tau) = F(tau - d(tau)) / (1 + ddot(tau)) exp(2 pi i f d(tau) (1 - ddot(tau)))
+ * D0 = d(t_f) (1 - ddot(t_f)) is the phase factor at t_f, which the template
+ * phase carries instead. */
+static void or_mb_G(const or_params* P, const or_model* m, double f, double tau, double D0, double complex G[2]) {
+    double d = or_doppler_delay(P, m, tau), dd, d2;
+    or_doppler_rates(P, m, tau, &dd, &d2);
+    double Fp, Fx;
+    or_antenna(P, m, tau - d, &Fp, &Fx);
+    double ph = 2.0 * OR_PI * f * (d * (1.0 - dd) - D0);
+    double complex c = (cos(ph) + I * sin(ph)) / (1.0 + dd);
+    G[0] = Fp * c;
+    G[1] = Fx * c;
+}
+
+/* Eq. (freDres) at frequency f with t_f = t, divided by exp(2 pi i f D0):
+ *   T = sum_{k=0}^{kmax} (-i T_A1)^k / k!  F^N_{T_f}[d^k G / dtau^k](t_f),
+ *   T_A1 = (7/6) / (2 pi f)  (the k = 1 coefficient the paper prints; k <= 1).
+ * dG/dtau by the five-point central difference with step 20 s (G turns at
+ * most 2 pi f |ddot| ~ 3e-5 rad/s at 50 mHz: truncation ~ 1e-13 relative). */
+static void or_mb_response(const or_params* P, const or_model* m, double f, double t, double D0,
+                           double complex T[2]) {
+    const int N = m->mb_order;
+    double a_re[3], a_im[3];
+    or_mb_weights(N, a_re, a_im);
+    const double Tf = or_tf_width(P, m, f);
+    const double TA1 = (7.0 / 6.0) / (2.0 * OR_PI * f);
+    const double h = 20.0;
+    T[0] = 0.0;
+    T[1] = 0.0;
+    for (int j = -N; j <= N; j++) {
+        const int aj = j < 0 ? -j : j;
+        const double complex w = (j == 0 ? 1.0 : 0.5) * (a_re[aj] + I * a_im[aj]);
+        const double tau = t + (double)j * Tf;
+        double complex G[2];
+        or_mb_G(P, m, f, tau, D0, G);
+        T[0] += w * G[0];
+        T[1] += w * G[1];
+        if (m->mb_kmax >= 1) {
+            double complex Gp2[2], Gp1[2], Gm1[2], Gm2[2];
+            or_mb_G(P, m, f, tau + 2.0 * h, D0, Gp2);
+            or_mb_G(P, m, f, tau + h, D0, Gp1);
+            or_mb_G(P, m, f, tau - h, D0, Gm1);
+            or_mb_G(P, m, f, tau - 2.0 * h, D0, Gm2);
+            for (int c = 0; c < 2; c++) {
+                double complex dG = (-Gp2[c] + 8.0 * Gp1[c] - 8.0 * Gm1[c] + Gm2[c]) / (12.0 * h);
+                T[c] += w * (-I * TA1) * dG;
+            }
+        }
+    }
+}
+
 static int or_params_finite(const or_params* P) {
     return isfinite(P->Mc) && isfinite(P->tc) && isfinite(P->lat) && isfinite(P->lon) &&
            isfinite(P->e0) && isfinite(P->q) && P->Mc > 0.0 && P->q > 0.0;
@@ -252,6 +383,26 @@ double or_phase_frac(const or_params* P, const or_model* m, double f_min, double
     ph -= f * (long double)or_doppler_delay(P, m, t);
     long double fr = ph - roundl(ph);
     return (double)fr;
+}
+
+/* The response of Eq. (freDres) at frequency f (t_f from the model):
+ * out = (Re T+, Im T+, Re Tx, Im Tx, D0, T_f), T divided by exp(2 pi i f D0). */
+void or_mb_response_at(const or_params* P, const or_model* m, double f, double* out) {
+    double t = or_time(P, m, f);
+    double d = or_doppler_delay(P, m, t), dd, d2;
+    or_doppler_rates(P, m, t, &dd, &d2);
+    double complex T[2];
+    or_mb_response(P, m, f, t, d * (1.0 - dd), T);
+    out[0] = creal(T[0]);
+    out[1] = cimag(T[0]);
+    out[2] = creal(T[1]);
+    out[3] = cimag(T[1]);
+    out[4] = d * (1.0 - dd);
+    out[5] = or_tf_width(P, m, f);
+}
+
+void or_doppler_rates_at(const or_params* P, const or_model* m, double t, double* dd, double* d2) {
+    or_doppler_rates(P, m, t, dd, d2);
 }
 
 long double or_phase_orb_cycles_ld(const or_params* P, const or_model* m, long double f) {
@@ -284,6 +435,29 @@ void or_basis(const or_params* P, const or_model* m, int64_t k0, int64_t k1, dou
         int64_t k = k0 + j;
         double f = m->f_min + (double)k * m->df;
         double t = or_time(P, m, f);
+        if (m->mb_order >= 0) {
+            /* Eq. (freDres): A1 = T+ h0, A2 = Tx h0, A3 = -i T+ h0, A4 = -i Tx h0 with the
+             * complex responses T of or_mb_response and h0 = f^-7/6 e^{-2 pi i Phi},
+             * Phi = Phi_orb - f D0 (the phase factor of G at t_f) */
+            double d = or_doppler_delay(P, m, t), dd, d2;
+            or_doppler_rates(P, m, t, &dd, &d2);
+            const double D0 = d * (1.0 - dd);
+            long double fl = (long double)m->f_min + (long double)k * (long double)m->df;
+            long double ph = or_phase_orb_cycles(P, m, fl) - fl * (long double)D0;
+            double fr = (double)(ph - roundl(ph));
+            double complex T[2];
+            or_mb_response(P, m, f, t, D0, T);
+            double amp = pow(f, -7.0 / 6.0);
+            double complex h0 = amp * (cos(2.0 * OR_PI * fr) - I * sin(2.0 * OR_PI * fr));
+            for (int c = 0; c < 2; c++) {
+                double complex A = T[c] * h0, Am = -I * A;
+                re[c * n + j] = creal(A);
+                im[c * n + j] = cimag(A);
+                re[(c + 2) * n + j] = creal(Am);
+                im[(c + 2) * n + j] = cimag(Am);
+            }
+            continue;
+        }
         double Fp, Fx;
         or_antenna(P, m, t, &Fp, &Fx);
         double fr = or_phase_frac(P, m, m->f_min, m->df, k);

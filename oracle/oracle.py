@@ -44,7 +44,8 @@ class Params(C.Structure):
 class Model(C.Structure):
     _fields_ = [("f_min", C.c_double), ("df", C.c_double), ("T_obs", C.c_double),
                 ("n", C.c_int64), ("response", C.c_int), ("pn_order", C.c_int),
-                ("alpha0", C.c_double), ("orient", C.c_double), ("channel", C.c_int)]
+                ("alpha0", C.c_double), ("orient", C.c_double), ("channel", C.c_int),
+                ("mb_order", C.c_int), ("mb_kmax", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -91,6 +92,12 @@ def lib():
                                       C.c_uint32, C.c_double, C.c_double, C.c_double, C.c_double,
                                       C.POINTER(C.c_int)]
             L.or_num_threads.restype = C.c_int
+            L.or_mb_weights.argtypes = [C.c_int, _dp, _dp]
+            L.or_mb_weights.restype = None
+            L.or_mb_response_at.argtypes = [C.POINTER(Params), C.POINTER(Model), C.c_double, _dp]
+            L.or_mb_response_at.restype = None
+            L.or_doppler_rates_at.argtypes = [C.POINTER(Params), C.POINTER(Model), C.c_double, _dp, _dp]
+            L.or_doppler_rates_at.restype = None
             _lib = L
     return _lib
 
@@ -111,6 +118,8 @@ class OracleModel:
     alpha0: float = 0.0
     orient: float = 0.0
     channel: int = 0       # TDI channel: 0 X, 1 A, 2 E, 3 T
+    mb_order: int = -1     # -1 the paper's response; 0..2 the Eq. (freDres) series with filter order N
+    mb_kmax: int = 0       # highest k of that series (0 or 1)
 
     @staticmethod
     def from_grid(grid, **kw) -> "OracleModel":
@@ -118,7 +127,7 @@ class OracleModel:
 
     def c(self) -> Model:
         return Model(self.f_min, self.df, self.T_obs, self.n, self.response, self.pn_order,
-                     self.alpha0, self.orient, self.channel)
+                     self.alpha0, self.orient, self.channel, self.mb_order, self.mb_kmax)
 
 
 def _params(p) -> Params:
@@ -334,3 +343,31 @@ def inject(p, model: OracleModel, a, k0: int = 0, k1: int | None = None) -> np.n
 def inner(a, b, psd, df) -> float:
     """<a, b> = 4 df Re sum a conj(b) / S  (Eq. inner_product on the grid)."""
     return float(4.0 * df * np.sum((a * np.conj(b)).real / psd))
+
+
+def mb_weights(N: int) -> np.ndarray:
+    """Complex weights a_0..a_N of the filter of order N in Eq. (freDres)."""
+    re = np.zeros(3)
+    im = np.zeros(3)
+    lib().or_mb_weights(int(N), _ptr(re), _ptr(im))
+    return (re + 1j * im)[:N + 1]
+
+
+def mb_response(p, model: OracleModel, f: float):
+    """(T+, Tx, D0, T_f) of the Eq. (freDres) response at frequency f; T+ and Tx
+    are divided by exp(2 pi i f D0), which the template phase carries."""
+    out = np.zeros(6)
+    m = model.c()
+    P = _params(p)
+    lib().or_mb_response_at(C.byref(P), C.byref(m), float(f), _ptr(out))
+    return out[0] + 1j * out[1], out[2] + 1j * out[3], out[4], out[5]
+
+
+def doppler_rates(p, model: OracleModel, t: float) -> tuple[float, float]:
+    """First and second time derivatives of the Doppler delay at time t."""
+    a = C.c_double()
+    b = C.c_double()
+    m = model.c()
+    P = _params(p)
+    lib().or_doppler_rates_at(C.byref(P), C.byref(m), float(t), C.byref(a), C.byref(b))
+    return a.value, b.value
