@@ -483,6 +483,46 @@ def two_channel_lines(args, world, fstat, g, psd, P_dev, stream, pbins):
     return out
 
 
+def response_series_line(args, world, fstat, g, d_dev, psd_dev, P_dev, stream, inband, Np=16, order=(2, 1)):
+    """The response series of Eq. (freDres) (filter order 2, k <= 1) in FP64 mode:
+    fs_fstat_batch of the bench's particles at one N_p after one untimed call,
+    `reps` timed calls, the fused kernel's launches timed by the plan's events;
+    and the change of F against the paper's form on the same data."""
+    import torch
+    dev = P_dev.device
+    reps = 3
+    with torch.cuda.stream(stream):
+        plan = fstat.Plan.from_grid(g, mode=fstat.FS_FP64, stream=stream)
+        plan.set_data(d_dev, psd_dev)
+        plan.reserve(P_dev.shape[0], Np)
+        F0 = plan.fstat(P_dev, Np, want_parts=False)[0].clone()
+        plan.set_response(*order)
+        F = torch.empty(P_dev.shape[0], dtype=torch.float64, device=dev)
+        plan.fstat(P_dev, Np, F=F, want_parts=False)
+        plan.read_profile("main")
+        plan.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            plan.fstat(P_dev, Np, F=F, want_parts=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = allmax(world, e0.elapsed_time(e1))
+        plan.set_profiling(False)
+        main_ms, main_n = plan.read_profile("main")
+        a, b = F.cpu().numpy(), F0.cpu().numpy()
+        ok = np.isfinite(b)
+        change = float(np.max(np.abs(a[ok] - b[ok]) / np.maximum(np.abs(b[ok]), 2.0 * Np)))
+        plan.close()
+    return {"filter_order": order[0], "k_max": order[1], "N_p": Np, "mode": "fp64 (direct form)",
+            "value": inband * reps / (ms / 1e3), "unit": UNIT, "ms_per_call": ms / reps,
+            "fused_ms_avg": main_ms / max(main_n, 1),
+            "max_change_vs_paper_form": change, "change_metric": "|dF|/max(|F|, 2 N_p)"}
+
+
 def time_run(args, world, run: ModeRun, kernel_prof=True):
     import torch
     stream = run.stream
@@ -626,6 +666,8 @@ def run_gpu(args, world, rank, local):
 
     # ---- the A and E channels (two-channel data), both modes, fs_fstat_batch on the prior draw
     channels = two_channel_lines(args, world, fstat, g, psd, P0_dev, stream, total_pbins)
+    # ---- the response series of Eq. (freDres) on the same data and particles
+    series = response_series_line(args, world, fstat, g, d_dev, psd_dev, P0_dev, stream, inband)
 
     # ---- roofline of the dominant kernels (average launch duration, live events)
     main_avg_ms = main_ms / max(main_n, 1)
@@ -678,6 +720,7 @@ def run_gpu(args, world, rank, local):
                     "d2h_bytes_per_step": int(host["fit"].numel() * 8)},
             "e2e_fstat_batch": e2e_fstat,
             "channels_AE": channels,
+            "response_series": series,
             "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps, "dtype": "f64 anchors + f32",
                       "max_rel_err_vs_fp64": mix_err, "error_metric": "|dF|/max(|F|, 2 N_p)",
                       "max_rel_err_vs_fp64_by_Np": {str(k): v for k, v in mix_err_np.items()},

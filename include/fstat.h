@@ -439,6 +439,33 @@ FS_API fs_status fs_pso_graph_build_ex(fs_plan* plan, const fs_swarm* swarm, con
 FS_API fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_sample_ring* rings, int steps,
                                           float lr, fs_graph** out);
 
+/* Response model of the FS_FP64 path (Sec. IV, Eq. freDres).
+ *   filter_order = -1 (default): the paper's own choice, N = 0 with the
+ *     higher-order d(t) terms neglected: T(f) = F(t_f) e^{2 pi i f d(t_f)}.
+ *   filter_order = N in 0..2: the series of Eq. (freDres) itself,
+ *     T(f) = sum_{k=0}^{k_max} (-i T_A1)^k / k!  F^N_{T_f}[d^k G/dtau^k](t_f),
+ *     G(tau) = F(tau - d(tau)) / (1 + ddot(tau)) e^{2 pi i f d(tau)(1 - ddot(tau))},
+ *     F^N_{T_f}[G](t) = 1/2 sum_{j=0}^{N} a_j (G(t + j T_f) + G(t - j T_f)),
+ *     T_A1 = (7/6)/(2 pi f), T_f^2 = |d^2 Psi/df^2|/(4 pi), with the antenna
+ *     pattern at the retarded time, the 1/(1 + ddot) factor and the ddot
+ *     phase term.  The weights a_j (defined in a reference the paper cites)
+ *     are taken as those that make the filter reproduce the even moments of
+ *     the stationary-phase kernel e^{i pi fdot s^2} up to order 2N: a_0 = 1
+ *     (N = 0); 1 - i/pi, i/pi (N = 1); 1 - 3/(4 pi^2) - 5i/(4 pi),
+ *     1/pi^2 + 4i/(3 pi), -1/(4 pi^2) - i/(12 pi) (N = 2).
+ *   k_max: 0 or 1 (the paper defines T_A1 only).
+ * With the series the responses are complex, so each segment carries an
+ * eighth sum (the imaginary part of the cross Gram term) and the 4x4 solve
+ * of Eq. (aandMN3) takes the Hermitian 2x2 form.  It applies to every later
+ * F-statistic, amplitude, swarm evaluation and fs_add_signal of the plan;
+ * graphs built earlier keep the response they were captured with.  It runs
+ * in the direct form of the fused kernel (launch variants 0-2; variants 3
+ * and 4 take variant 0's tile), at several times the per-bin cost.
+ * FS_EINVAL for arguments out of range, FS_EUNSUPPORTED for a series on an
+ * FS_MIXED plan.  Host only, no device work. */
+FS_API fs_status fs_plan_set_response(fs_plan* plan, int filter_order, int k_max);
+FS_API fs_status fs_plan_get_response(const fs_plan* plan, int* filter_order, int* k_max);
+
 /* Launch variants of the fused bin-loop kernel (the tile shape of the
  * ragged batch, Sec. IV's particle x frequency parallelism).
  *   FS_FP64 : direct form, the whole template evaluated at every bin:

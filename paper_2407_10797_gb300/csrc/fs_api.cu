@@ -68,6 +68,9 @@ struct fs_plan {
     // launch variant of the fused kernel: forced (>= 0) or looked up per
     // (N_p, edge kind) among the autotuned choices, else variant 0
     int variant_forced;
+    // response of the FP64 path: the paper's form (resp_on = 0) or the series of Eq. (freDres)
+    int resp_on;
+    fs::Resp resp;
     unsigned long long* census;   // [fs::kCensusModes] device counters of fs_plan_census
     int census_on;
     struct TuneRec {
@@ -204,6 +207,9 @@ void free_workspace(fs_plan* p) {
     p->B_cap = p->Np_cap = 0;
 }
 
+// sums per partial slot the workspace is sized for: 7, or 8 with the response series
+constexpr size_t kSlotMax = 8;
+
 fs_status ensure_workspace(fs_plan* p, int B, int Np) {
     if (B <= p->B_cap && Np <= p->Np_cap) return FS_OK;
     int nb = B > p->B_cap ? B : p->B_cap;
@@ -214,9 +220,9 @@ fs_status ensure_workspace(fs_plan* p, int B, int Np) {
     size_t nt = (size_t)p->ntiles;
     const size_t nc = (size_t)p->nch;
     if ((e = cudaMalloc(&p->parts, sizeof(fs::Particle) * nb * nc)) != cudaSuccess ||
-        (e = cudaMalloc(&p->H, sizeof(double) * 7 * nt * nb * nc)) != cudaSuccess ||
-        (e = cudaMalloc(&p->T, sizeof(double) * 7 * nt * nb * nc)) != cudaSuccess ||
-        (e = cudaMalloc(&p->S, sizeof(double) * 7 * (size_t)nn * nb * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->H, sizeof(double) * kSlotMax * nt * nb * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->T, sizeof(double) * kSlotMax * nt * nb * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&p->S, sizeof(double) * kSlotMax * (size_t)nn * nb * nc)) != cudaSuccess ||
         (e = cudaMalloc(&p->Fpart, sizeof(double) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot, sizeof(double2) * (size_t)nn * nb)) != cudaSuccess ||
         (e = cudaMalloc(&p->rot32, sizeof(float2) * (size_t)nn * nb)) != cudaSuccess ||
@@ -527,14 +533,18 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
     const bool mixed = p->mode == FS_MIXED;
     pa.rot32 = mixed ? p->rot32 : nullptr;
     const int variant = resolve_variant(p, Np, global);
-    const bool anchored = !mixed && variant >= 3;
-    pa.tile = mixed ? fs::mixed_span() : anchored ? fs::fp64a_span() : fp64_tile(variant);
+    // the response series runs in the direct form only (the anchored form's expansions
+    // are built for the paper's response): its variants 3 and 4 take the default tile
+    const bool mb = !mixed && p->resp_on;
+    const bool anchored = !mixed && !mb && variant >= 3;
+    pa.nsum = mb ? 8 : 7;
+    pa.tile = mixed ? fs::mixed_span() : anchored ? fs::fp64a_span() : fp64_tile(mb && variant >= 3 ? 0 : variant);
     pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
     // channel c: its response (turned orientation, scaled projections), its particles and partial sums
     pa.nch = p->nch;
-    pa.ch_HT = (int64_t)7 * p->ntiles * p->B_cap;
-    pa.ch_S = (int64_t)7 * p->Np_cap * p->B_cap;
+    pa.ch_HT = (int64_t)pa.nsum * p->ntiles * p->B_cap;
+    pa.ch_S = (int64_t)pa.nsum * p->Np_cap * p->B_cap;
     {
         ProfScope ps(p, 0);
         for (int c = 0; c < p->nch; c++)
@@ -563,7 +573,8 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
                 if ((e = fs::launch_fp64a_main(gc, p->tab[c], pc, B, sg, pc_pa, variant == 4, p->span_list,
                                                p->span_cnt, p->stream)) != cudaSuccess)
                     return cuda_fail(e, "fp64 anchored main launch");
-            } else if ((e = fs::launch_fp64_main(gc, p->tab[c], pc, B, sg, pc_pa, p->stream)) != cudaSuccess) {
+            } else if ((e = fs::launch_fp64_main(gc, p->tab[c], pc, B, sg, pc_pa, p->stream,
+                                                 mb ? &p->resp : nullptr)) != cudaSuccess) {
                 return cuda_fail(e, "fp64 main launch");
             }
         }
@@ -1113,11 +1124,55 @@ fs_status fs_add_signal(fs_plan* p, const fs_params* params_host, const double* 
         if ((e = fs::launch_setup(gc, p->one_param, 1, p->one_part, 0, p->stream)) != cudaSuccess)
             return cuda_fail(e, "setup launch");
         if ((e = fs::launch_add_signal(gc, p->tab[c], p->one_part, p->one_a, data_dev + (size_t)2 * p->grid.n * c,
-                                       p->stream)) != cudaSuccess)
+                                       p->stream, p->resp_on ? &p->resp : nullptr)) != cudaSuccess)
             return cuda_fail(e, "add_signal launch");
     }
     e = cudaStreamSynchronize(p->stream);   // the host arguments are pageable: finish before returning
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return FS_OK;
+}
+
+fs_status fs_plan_set_response(fs_plan* p, int filter_order, int k_max) {
+    g_err[0] = 0;
+    if (filter_order < -1 || filter_order > 2)
+        return fail(FS_EINVAL, "fs_plan_set_response: filter order %d not in [-1, 2]", filter_order);
+    if (k_max < 0 || k_max > 1) return fail(FS_EINVAL, "fs_plan_set_response: k_max %d not in [0, 1]", k_max);
+    if (!p) return fail(FS_EINVAL, "fs_plan_set_response: plan is NULL");
+    if (filter_order >= 0 && p->mode != FS_FP64)
+        return fail(FS_EUNSUPPORTED, "fs_plan_set_response: the response series needs an FS_FP64 plan");
+    if (filter_order < 0) {
+        p->resp_on = 0;
+        return FS_OK;
+    }
+    // weights a_j solving sum_j a_j j^(2m) = (2m-1)!! (i/pi)^m, m = 0..N (closed forms)
+    const double pi = fs::kPi, pi2 = fs::kPi * fs::kPi;
+    fs::Resp r{};
+    r.N = filter_order;
+    r.K = k_max;
+    if (filter_order == 0) {
+        r.ar[0] = 1.0;
+    } else if (filter_order == 1) {
+        r.ar[0] = 1.0;
+        r.ai[0] = -1.0 / pi;
+        r.ai[1] = 1.0 / pi;
+    } else {
+        r.ar[0] = 1.0 - 3.0 / (4.0 * pi2);
+        r.ai[0] = -5.0 / (4.0 * pi);
+        r.ar[1] = 1.0 / pi2;
+        r.ai[1] = 4.0 / (3.0 * pi);
+        r.ar[2] = -1.0 / (4.0 * pi2);
+        r.ai[2] = -1.0 / (12.0 * pi);
+    }
+    p->resp = r;
+    p->resp_on = 1;
+    return FS_OK;
+}
+
+fs_status fs_plan_get_response(const fs_plan* p, int* filter_order, int* k_max) {
+    g_err[0] = 0;
+    if (!p || !filter_order || !k_max) return fail(FS_EINVAL, "fs_plan_get_response: NULL argument");
+    *filter_order = p->resp_on ? p->resp.N : -1;
+    *k_max = p->resp_on ? p->resp.K : 0;
     return FS_OK;
 }
 

@@ -152,6 +152,149 @@ __device__ __forceinline__ BinEval eval_bin_fp64(const Particle& P, double fh, d
     return r;
 }
 
+// ---- the response series of Sec. IV, Eq. (freDres) -------------------------
+//   T(f) = sum_{k=0}^{K} (-i T_A1)^k / k!  F^N_{T_f}[d^k G / dtau^k](t_f),
+//   G(tau) = F(tau - d(tau)) / (1 + ddot(tau)) exp(2 pi i f d(tau) (1 - ddot(tau))),
+//   F^N_{T_f}[G](t) = 1/2 sum_{j=0}^{N} a_j (G(t + j T_f) + G(t - j T_f)),
+//   T_A1 = (7/6) / (2 pi f),  T_f^2 = |d^2 Psi/df^2| / (4 pi) = |dt_f/df| / 2.
+// The weights a_j make the filter reproduce the even moments (2m-1)!! (i T_f^2/pi)^m
+// (m <= N) of the stationary-phase kernel exp(i pi fdot s^2) around t_f; they are
+// filled in by the host (fs_plan_set_response).  The phase factor of G at t_f,
+// exp(2 pi i f D0) with D0 = d(t_f)(1 - ddot(t_f)), is carried by the template phase.
+struct Resp {
+    int N;               // filter order, 0..2
+    int K;               // highest k, 0 or 1
+    double ar[3], ai[3]; // a_0..a_N
+};
+
+// dt_f/df: the derivative of each power-law term of time_of.
+__device__ __forceinline__ double dtime_df(const Particle& P, const FreqPowers& w, double f) {
+    double u2 = w.u * w.u;
+    double u3 = u2 * w.u;
+    double u4 = u2 * u2;
+    double u6 = u3 * u3;
+    double g83 = w.g0h * u3;   // f^-8/3
+    double s = (-8.0 / 3.0) * P.T0 * g83;
+    s = fma(-2.0 * P.T2, u6, s);
+    s = fma((-5.0 / 3.0) * P.T3, w.g0h, s);
+    s = fma((-4.0 / 3.0) * P.T4, u4, s);
+    s = fma((-43.0 / 9.0) * P.TE * g83, w.e19, s);
+    return s / f;
+}
+
+// Antenna patterns (as antenna_of) and their derivatives with respect to alpha.
+__device__ __forceinline__ void antenna_deriv(const Particle& P, double c1, double s1, double& Fp, double& Fx,
+                                              double& dFp, double& dFx) {
+    double c2 = fma(c1, c1, -s1 * s1);
+    double s2 = 2.0 * s1 * c1;
+    double pj[4], qj[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        double v = P.pr[i][0];
+        v = fma(P.pr[i][1], c1, v);
+        v = fma(P.pr[i][2], s1, v);
+        v = fma(P.pr[i][3], c2, v);
+        v = fma(P.pr[i][4], s2, v);
+        pj[i] = v;
+        double dv = -P.pr[i][1] * s1;
+        dv = fma(P.pr[i][2], c1, dv);
+        dv = fma(-2.0 * P.pr[i][3], s2, dv);
+        dv = fma(2.0 * P.pr[i][4], c2, dv);
+        qj[i] = dv;
+    }
+    Fp = 0.5 * ((pj[0] * pj[0] - pj[1] * pj[1]) - (pj[2] * pj[2] - pj[3] * pj[3]));
+    Fx = pj[0] * pj[1] - pj[2] * pj[3];
+    dFp = (pj[0] * qj[0] - pj[1] * qj[1]) - (pj[2] * qj[2] - pj[3] * qj[3]);
+    dFx = (qj[0] * pj[1] + pj[0] * qj[1]) - (qj[2] * pj[3] + pj[2] * qj[3]);
+}
+
+// Phase (mod 1, with the phase factor of G at t_f) and the complex responses
+// T+ and Tx of one bin under the series above.
+struct BinEvalMB {
+    double frac;
+    double Tpr, Tpi, Txr, Txi;
+};
+
+__device__ __forceinline__ BinEvalMB eval_bin_mb(const Particle& P, double fh, double fl, const FreqPowers& w,
+                                                 double g0l, double alpha0, const Resp& R) {
+    BinEvalMB r;
+    // orbital phase as in eval_bin_fp64
+    double p, e;
+    two_prod(P.P0h, w.g0h, p, e);
+    e = fma(P.P0h, g0l, e);
+    e = fma(P.P0l, w.g0h, e);
+    double acc = (p - rint(p)) + e;
+    double q, eq;
+    two_prod(fh, P.tc, q, eq);
+    eq = fma(fl, P.tc, eq);
+    acc += (q - rint(q)) + eq;
+    double u2 = w.u * w.u;
+    double u3 = u2 * w.u;
+    double rest = P.P2 * u3;
+    rest = fma(P.P3, u2, rest);
+    rest = fma(P.P4, w.u, rest);
+    rest = fma(P.E0 * w.g0h, w.e19, rest);
+    const double Om = kTwoPi / kYearS;
+    const double t = time_of(P, w);
+    double s1, c1;
+    sincos(fma(Om, t, alpha0), &s1, &c1);
+    const double cd = fma(c1, P.clon, s1 * P.slon);    // cos(alpha - phi)
+    const double sd = fma(s1, P.clon, -c1 * P.slon);   // sin(alpha - phi)
+    const double d0 = P.AD * cd, dd0 = -P.AD * Om * sd;
+    rest = fma(-fh * P.AD, cd, rest);   // - f d(t_f)
+    rest = fma(fh * d0, dd0, rest);     // + f d(t_f) ddot(t_f)
+    acc += rest - rint(rest);
+    r.frac = acc - rint(acc);
+    const double D0 = d0 * (1.0 - dd0);
+    // the stencil t_f + j T_f: alpha advances by j Om T_f
+    const double Tf = sqrt(0.5 * fabs(dtime_df(P, w, fh)));
+    double sdl, cdl;
+    sincos(Om * Tf, &sdl, &cdl);
+    const double c2dl = fma(-2.0 * sdl, sdl, 1.0), s2dl = 2.0 * sdl * cdl;
+    const double TA1 = 7.0 / (12.0 * kPi * fh);
+    double gr[2] = {0.0, 0.0}, gi[2] = {0.0, 0.0}, hr[2] = {0.0, 0.0}, hi[2] = {0.0, 0.0};
+    for (int j = -R.N; j <= R.N; j++) {
+        const int aj = j < 0 ? -j : j;
+        const double cj = aj == 0 ? 1.0 : aj == 1 ? cdl : c2dl;
+        const double sj = (aj == 0 ? 0.0 : aj == 1 ? sdl : s2dl) * (j < 0 ? -1.0 : 1.0);
+        const double ca = fma(c1, cj, -s1 * sj), sa = fma(s1, cj, c1 * sj);
+        const double cdj = fma(ca, P.clon, sa * P.slon), sdj = fma(sa, P.clon, -ca * P.slon);
+        const double dj = P.AD * cdj, ddj = -P.AD * Om * sdj, d2j = -P.AD * Om * Om * cdj;
+        // retarded orbital phase alpha - Om d (|Om d| < 1e-4 rad: series to x^5 exact in FP64)
+        const double x = Om * dj, x2 = x * x;
+        const double cx = fma(-0.5 * x2, fma(-x2, 1.0 / 12.0, 1.0), 1.0), sx = x * fma(-x2, 1.0 / 6.0, 1.0);
+        const double cr = fma(ca, cx, sa * sx), sr = fma(sa, cx, -ca * sx);
+        double F[2], dF[2];
+        antenna_deriv(P, cr, sr, F[0], F[1], dF[0], dF[1]);
+        const double inv = 1.0 / (1.0 + ddj);
+        double cph = 1.0, sph = 0.0;
+        if (j != 0) sincos(kTwoPi * fh * (dj * (1.0 - ddj) - D0), &sph, &cph);
+        const double h = j == 0 ? 1.0 : 0.5;   // (weights selected without a dynamic index: no local memory)
+        const double wr = h * (aj == 0 ? R.ar[0] : aj == 1 ? R.ar[1] : R.ar[2]);
+        const double wi = h * (aj == 0 ? R.ai[0] : aj == 1 ? R.ai[1] : R.ai[2]);
+        const double Cr = cph * inv, Ci = sph * inv;
+        const double wCr = fma(wr, Cr, -wi * Ci), wCi = fma(wr, Ci, wi * Cr);
+        const double kr = -d2j * inv, ki = kTwoPi * fh * fma(ddj, 1.0 - ddj, -dj * d2j);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            gr[c] = fma(wCr, F[c], gr[c]);
+            gi[c] = fma(wCi, F[c], gi[c]);
+            if (R.K >= 1) {
+                // G' = C (Om dF/dalpha (1 - ddot) + F kappa), kappa = -d''/(1 + d') + 2 pi i f (d'(1 - d') - d d'')
+                const double ur = fma(Om * dF[c], 1.0 - ddj, F[c] * kr), ui = F[c] * ki;
+                hr[c] += fma(wCr, ur, -wCi * ui);
+                hi[c] += fma(wCr, ui, wCi * ur);
+            }
+        }
+    }
+    // T = sum w G - i T_A1 sum w G'
+    r.Tpr = fma(TA1, hi[0], gr[0]);
+    r.Tpi = fma(-TA1, hr[0], gi[0]);
+    r.Txr = fma(TA1, hi[1], gr[1]);
+    r.Txi = fma(-TA1, hr[1], gi[1]);
+    return r;
+}
+
 // Segment index of bin k for a particle with per-particle segments.
 __device__ __forceinline__ int seg_of_bin(int64_t k, int64_t klo, int64_t khi, int Np) {
     int64_t w = khi - klo;

@@ -379,9 +379,14 @@ cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const S
 //   X1 = sum G1 z, X2 = sum G2 z, K11 = sum W G1^2, K12 = sum W G1 G2, K22 = sum W G2^2
 // per segment.  The first segment touched in the tile goes to H, the last to
 // T, segments that start and end inside the tile go straight to S.
+// NS = 8: the response series of Eq. (freDres) (eval_bin_mb), whose T+ and Tx
+// are complex; the rotated responses G1 = c T+ + s Tx, G2 = c Tx - s T+ give
+//   X1 = sum z conj(G1), X2 = sum z conj(G2), K11 = sum W |G1|^2,
+//   K12 = sum W Re(G1 conj G2), K22 = sum W |G2|^2 and K12' = sum W Im(G1 conj G2).
 // ---------------------------------------------------------------------------
+template <int NS>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 1)
-fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa) {
+fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa, Resp resp) {
     const int lane = threadIdx.x & 31;
     const int b = blockIdx.y * kWarpsPerCta + (threadIdx.x >> 5);
     const int tile = blockIdx.x;
@@ -395,9 +400,9 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
     if (lo >= hi) return;
     const int64_t slot = (int64_t)b * pa.ntiles + tile;
 
-    double acc[7];
+    double acc[NS];
 #pragma unroll
-    for (int c = 0; c < 7; c++) acc[c] = 0.0;
+    for (int c = 0; c < NS; c++) acc[c] = 0.0;
     int cur = sv.seg(lo);
     int nflush = 0;
 
@@ -405,44 +410,63 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
         const int64_t k = base + lane;
         const bool valid = k < hi;
         int pk = INT_MAX;
-        double t7[7];
+        double t7[NS];
 #pragma unroll
-        for (int c = 0; c < 7; c++) t7[c] = 0.0;
+        for (int c = 0; c < NS; c++) t7[c] = 0.0;
         if (valid) {
             pk = sv.seg(k);
             FreqPowers w;
             w.u = tb.u[k];
             w.g0h = tb.g0h[k];
             w.e19 = tb.e19[k];
-            BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
-            double sn, cs;
-            sincospi(2.0 * ev.frac, &sn, &cs);
             const double2 rc = pa.rot[(int64_t)b * sg.Np + pk];
-            const double G1 = fma(rc.x, ev.Fp, rc.y * ev.Fx);
-            const double G2 = fma(rc.x, ev.Fx, -rc.y * ev.Fp);
             double dr = tb.dwr[k], di = tb.dwi[k], W = tb.W[k];
-            double zr = fma(dr, cs, -di * sn);
-            double zi = fma(dr, sn, di * cs);
-            t7[0] = G1 * zr;
-            t7[1] = G1 * zi;
-            t7[2] = G2 * zr;
-            t7[3] = G2 * zi;
-            double wg = W * G1;
-            t7[4] = wg * G1;
-            t7[5] = wg * G2;
-            t7[6] = W * G2 * G2;
+            if constexpr (NS == 7) {
+                BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
+                double sn, cs;
+                sincospi(2.0 * ev.frac, &sn, &cs);
+                const double G1 = fma(rc.x, ev.Fp, rc.y * ev.Fx);
+                const double G2 = fma(rc.x, ev.Fx, -rc.y * ev.Fp);
+                double zr = fma(dr, cs, -di * sn);
+                double zi = fma(dr, sn, di * cs);
+                t7[0] = G1 * zr;
+                t7[1] = G1 * zi;
+                t7[2] = G2 * zr;
+                t7[3] = G2 * zi;
+                double wg = W * G1;
+                t7[4] = wg * G1;
+                t7[5] = wg * G2;
+                t7[6] = W * G2 * G2;
+            } else {
+                BinEvalMB ev = eval_bin_mb(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp);
+                double sn, cs;
+                sincospi(2.0 * ev.frac, &sn, &cs);
+                const double G1r = fma(rc.x, ev.Tpr, rc.y * ev.Txr), G1i = fma(rc.x, ev.Tpi, rc.y * ev.Txi);
+                const double G2r = fma(rc.x, ev.Txr, -rc.y * ev.Tpr), G2i = fma(rc.x, ev.Txi, -rc.y * ev.Tpi);
+                double zr = fma(dr, cs, -di * sn);
+                double zi = fma(dr, sn, di * cs);
+                // z conj(G) = (zr G_r + zi G_i) + i (zi G_r - zr G_i)
+                t7[0] = fma(zr, G1r, zi * G1i);
+                t7[1] = fma(zi, G1r, -zr * G1i);
+                t7[2] = fma(zr, G2r, zi * G2i);
+                t7[3] = fma(zi, G2r, -zr * G2i);
+                t7[4] = W * fma(G1r, G1r, G1i * G1i);
+                t7[5] = W * fma(G1r, G2r, G1i * G2i);
+                t7[6] = W * fma(G2r, G2r, G2i * G2i);
+                t7[7] = W * fma(G1i, G2r, -G1r * G2i);
+            }
         }
         while (true) {
             if (valid && pk == cur) {
 #pragma unroll
-                for (int c = 0; c < 7; c++) acc[c] += t7[c];
+                for (int c = 0; c < NS; c++) acc[c] += t7[c];
             }
             unsigned more = __ballot_sync(0xffffffffu, valid && pk > cur);
             if (!more) break;
             // segment `cur` ends inside this tile: flush it
-            double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.S + ((int64_t)b * sg.Np + cur) * 7;
+            double* dst = (nflush == 0) ? pa.H + slot * NS : pa.S + ((int64_t)b * sg.Np + cur) * NS;
 #pragma unroll
-            for (int c = 0; c < 7; c++) {
+            for (int c = 0; c < NS; c++) {
                 double v = warp_sum(acc[c]);
                 if (lane == 0) dst[c] = v;
                 acc[c] = 0.0;
@@ -454,19 +478,24 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
             cur = cand;
         }
     }
-    double* dst = (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7;
+    double* dst = (nflush == 0) ? pa.H + slot * NS : pa.T + slot * NS;
 #pragma unroll
-    for (int c = 0; c < 7; c++) {
+    for (int c = 0; c < NS; c++) {
         double v = warp_sum(acc[c]);
         if (lane == 0) dst[c] = v;
     }
 }
 
 cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
-                             const Partials& pa, cudaStream_t s) {
+                             const Partials& pa, cudaStream_t s, const Resp* resp) {
     if (B <= 0) return cudaSuccess;
     dim3 grid((unsigned)pa.ntiles, (unsigned)((B + kWarpsPerCta - 1) / kWarpsPerCta));
-    fp64_main_kernel<<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa);
+    if (resp) {
+        if (pa.nsum != 8) return cudaErrorInvalidValue;
+        fp64_main_kernel<8><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
+    } else {
+        fp64_main_kernel<7><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
+    }
     return cudaGetLastError();
 }
 
@@ -481,7 +510,13 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
 // G lanes per (particle, segment): G = 1 when a segment meets only a few
 // tiles (large N_p), up to a warp when it meets hundreds.  G depends only on
 // (n_bins, N_p, tile), so a plan's results stay bitwise reproducible.
-template <int G>
+// NS = 8 (the response series): K = [[K11, K12 - i K12'], [K12 + i K12', K22]] is
+// the Hermitian Gram matrix of the complex responses (the 4x4 M is its real
+// form) and F_p = X^H K^-1 X / 2:
+//   F_p = [K22 |X1|^2 + K11 |X2|^2 - 2 K12 Re(conj X1 X2) - 2 K12' Im(conj X1 X2)]
+//         / (2 (K11 K22 - K12^2 - K12'^2)),
+// with the same degenerate-segment rule on K11 K22 - K12^2.
+template <int G, int NS>
 __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
                               double* Fpart, double* amp, const int* amp_exp) {
     const int lane = threadIdx.x & (G - 1);
@@ -499,9 +534,9 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
         return;
     }
     const SegView sv = seg_view(sg, P);
-    double acc[7];
+    double acc[NS];
 #pragma unroll
-    for (int c = 0; c < 7; c++) acc[c] = 0.0;
+    for (int c = 0; c < NS; c++) acc[c] = 0.0;
     int64_t s0 = 0, s1 = 0;
     if (sv.lo <= sv.hi) {
         s0 = sv.start(p);
@@ -518,30 +553,31 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
             const double* src;
             int64_t stride;
             if (p == pf) {
-                src = pa.H + ((int64_t)b * pa.ntiles + t) * 7;
+                src = pa.H + ((int64_t)b * pa.ntiles + t) * NS;
                 stride = pa.ch_HT;
             } else if (p == pl) {
-                src = pa.T + ((int64_t)b * pa.ntiles + t) * 7;
+                src = pa.T + ((int64_t)b * pa.ntiles + t) * NS;
                 stride = pa.ch_HT;
             } else {
-                src = pa.S + ((int64_t)b * sg.Np + p) * 7;
+                src = pa.S + ((int64_t)b * sg.Np + p) * NS;
                 stride = pa.ch_S;
             }
             for (int ch = 0; ch < pa.nch; ch++)   // the channels' sums add (Sec. II.A, Eq. eq2)
 #pragma unroll
-                for (int c = 0; c < 7; c++) acc[c] += src[ch * stride + c];
+                for (int c = 0; c < NS; c++) acc[c] += src[ch * stride + c];
         }
     }
     if (G > 1) {
         // groups are aligned G-lane blocks of a warp whose members all reach this point
         const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1)));
 #pragma unroll
-        for (int c = 0; c < 7; c++)
+        for (int c = 0; c < NS; c++)
             for (int o = G / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(mask, acc[c], o);
     }
     if (lane == 0) {
         double X1r = acc[0], X1i = acc[1], X2r = acc[2], X2i = acc[3];
         double K11 = acc[4], K12 = acc[5], K22 = acc[6];
+        const double K12p = NS == 8 ? acc[NS - 1] : 0.0;
         double det = K11 * K22 - K12 * K12;
         const double2 rc = pa.rot[wid];
         const double cc = rc.x * rc.x, ss = rc.y * rc.y, cs2 = 2.0 * rc.x * rc.y;
@@ -549,10 +585,12 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
         double Rr = ss * K11 + cs2 * K12 + cc * K22;   // sum W Fx^2
         double F = 0.0;
         const bool solvable = nb >= 4 && det > 1e-12 * Pp * Rr;
+        const double detH = NS == 8 ? det - K12p * K12p : det;
         if (solvable) {
             double num = K22 * (X1r * X1r + X1i * X1i) - 2.0 * K12 * (X1r * X2r + X1i * X2i) +
                          K11 * (X2r * X2r + X2i * X2i);
-            F = 0.5 * num / det;
+            if (NS == 8) num -= 2.0 * K12p * (X1r * X2i - X1i * X2r);
+            F = 0.5 * num / detH;
         }
         Fpart[wid] = F;
         if (amp) {
@@ -561,9 +599,12 @@ __global__ void reduce_kernel(Grid g, const Particle* __restrict__ parts, int B,
             // (F+ h0, Fx h0, -i F+ h0, -i Fx h0) basis: G1 = c F+ + s Fx, G2 = c Fx - s F+.
             double a4v[4] = {0.0, 0.0, 0.0, 0.0};
             if (solvable) {
-                const double id = 1.0 / det;
-                const double b1 = (K22 * X1r - K12 * X2r) * id, b2 = (K11 * X2r - K12 * X1r) * id;
-                const double b3 = -(K22 * X1i - K12 * X2i) * id, b4 = -(K11 * X2i - K12 * X1i) * id;
+                // c = K^-1 X with c1 = b1 - i b3, c2 = b2 - i b4 (K12' = 0 unless NS = 8)
+                const double id = 1.0 / detH;
+                const double b1 = (K22 * X1r - K12 * X2r - K12p * X2i) * id;
+                const double b2 = (K11 * X2r - K12 * X1r + K12p * X1i) * id;
+                const double b3 = -(K22 * X1i - K12 * X2i + K12p * X2r) * id;
+                const double b4 = -(K11 * X2i - K12 * X1i - K12p * X1r) * id;
                 a4v[0] = rc.x * b1 - rc.y * b2;
                 a4v[1] = rc.y * b1 + rc.x * b2;
                 a4v[2] = rc.x * b3 - rc.y * b4;
@@ -632,7 +673,12 @@ cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Seg
     while (G < 32 && 2 * G < tiles) G *= 2;
     const int64_t blocks = (segs * G + threads - 1) / threads;
 #define FS_REDUCE(G_)                                                                                   \
-    reduce_kernel<G_><<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp, amp_exp)
+    do {                                                                                                \
+        if (pa.nsum == 8)                                                                               \
+            reduce_kernel<G_, 8><<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp, amp_exp); \
+        else                                                                                            \
+            reduce_kernel<G_, 7><<<(unsigned)blocks, threads, 0, s>>>(g, parts, B, sg, pa, Fpart, amp, amp_exp); \
+    } while (0)
     switch (G) {
         case 1: FS_REDUCE(1); break;
         case 2: FS_REDUCE(2); break;
@@ -671,8 +717,10 @@ cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStrea
 // ---------------------------------------------------------------------------
 // Signal synthesis: data += sum_i a_i A^i over the particle's band (FP64).
 // ---------------------------------------------------------------------------
+// With the response series (MB): h = (a1 - i a3) T+ h0 + (a2 - i a4) Tx h0.
+template <bool MB>
 __global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict__ part, const double* a,
-                                  double* data) {
+                                  double* data, Resp resp) {
     const Particle P = *part;
     if (!P.valid) return;
     int64_t k = P.klo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -681,22 +729,36 @@ __global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict_
     w.u = tb.u[k];
     w.g0h = tb.g0h[k];
     w.e19 = tb.e19[k];
-    BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
-    double sn, cs;
-    sincospi(2.0 * ev.frac, &sn, &cs);
     double amp = pow(tb.fh[k], -7.0 / 6.0);
-    double c = a[0] * ev.Fp + a[1] * ev.Fx;   // coefficient of h0
-    double s = a[2] * ev.Fp + a[3] * ev.Fx;   // coefficient of -i h0
-    // (c - i s) (cos - i sin) * amp
-    data[2 * k] += amp * (c * cs - s * sn);
-    data[2 * k + 1] += amp * (-c * sn - s * cs);
+    double sn, cs;
+    if constexpr (MB) {
+        BinEvalMB ev = eval_bin_mb(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp);
+        sincospi(2.0 * ev.frac, &sn, &cs);
+        // coefficient of h0: (a1 - i a3)(Tpr + i Tpi) + (a2 - i a4)(Txr + i Txi) = cr + i ci
+        const double cr = a[0] * ev.Tpr + a[2] * ev.Tpi + a[1] * ev.Txr + a[3] * ev.Txi;
+        const double ci = a[0] * ev.Tpi - a[2] * ev.Tpr + a[1] * ev.Txi - a[3] * ev.Txr;
+        // (cr + i ci) (cos - i sin) * amp
+        data[2 * k] += amp * (cr * cs + ci * sn);
+        data[2 * k + 1] += amp * (ci * cs - cr * sn);
+    } else {
+        BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
+        sincospi(2.0 * ev.frac, &sn, &cs);
+        double c = a[0] * ev.Fp + a[1] * ev.Fx;   // coefficient of h0
+        double s = a[2] * ev.Fp + a[3] * ev.Fx;   // coefficient of -i h0
+        // (c - i s) (cos - i sin) * amp
+        data[2 * k] += amp * (c * cs - s * sn);
+        data[2 * k + 1] += amp * (-c * sn - s * cs);
+    }
 }
 
 cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,
-                              double* data, cudaStream_t s) {
+                              double* data, cudaStream_t s, const Resp* resp) {
     int threads = 256;
     int64_t blocks = (g.n + threads - 1) / threads;
-    add_signal_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data);
+    if (resp)
+        add_signal_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
+    else
+        add_signal_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
     return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ struct Partials {
     // channels summed by the solve kernel: channel c's slots at H + c ch_HT, T + c ch_HT, S + c ch_S
     int nch = 1;
     int64_t ch_HT = 0, ch_S = 0;
+    int nsum = 7;   // sums per slot: 7, or 8 for the response series (K12' of the complex responses)
 };
 
 // Record an error message for fs_last_error() and return st.
@@ -94,8 +95,9 @@ cudaError_t launch_setup(const Grid& g, const ::fs_params* params, int B, Partic
                          cudaStream_t s);
 cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const Segs& sg, double2* rot,
                             float2* rot32, cudaStream_t s);
+// resp != NULL: the response series (eight sums per slot, pa.nsum = 8)
 cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
-                             const Partials& pa, cudaStream_t s);
+                             const Partials& pa, cudaStream_t s, const Resp* resp = nullptr);
 cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Segs& sg, const Partials& pa,
                           double* Fpart, double* F, cudaStream_t s,
                           double* amp = nullptr, const int* amp_exp = nullptr);
@@ -160,6 +162,6 @@ cudaError_t launch_pso_record(int nr, int per, int D, const double* x, const dou
                               cudaStream_t s);
 cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStream_t s);
 cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* part, const double* a,
-                              double* data, cudaStream_t s);
+                              double* data, cudaStream_t s, const Resp* resp = nullptr);
 
 }  // namespace fs

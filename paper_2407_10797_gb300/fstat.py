@@ -81,6 +81,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                              C.c_int, _vp, C.c_int, _vp, _vp, _vp]
         L.fs_plan_set_profiling.argtypes = [_vp, C.c_int]
         L.fs_plan_set_variant.argtypes = [_vp, C.c_int]
+        L.fs_plan_set_response.argtypes = [_vp, C.c_int, C.c_int]
+        L.fs_plan_get_response.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.fs_plan_set_variant_for.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
         L.fs_plan_get_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
         L.fs_plan_census.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int64)]
@@ -304,6 +306,16 @@ class Plan:
         return out
 
     KERNELS = {"setup": 0, "main": 1, "reduce": 2, "precompute": 3}
+
+    def set_response(self, filter_order: int = -1, k_max: int = 0):
+        """Response model of the FS_FP64 path: -1 the paper's form, 0..2 the series of
+        Eq. (freDres) with that filter order and terms up to k_max (0 or 1)."""
+        _check(self._L.fs_plan_set_response(self._h, int(filter_order), int(k_max)))
+
+    def get_response(self) -> tuple[int, int]:
+        n, k = C.c_int(), C.c_int()
+        _check(self._L.fs_plan_get_response(self._h, C.byref(n), C.byref(k)))
+        return n.value, k.value
 
     def set_variant(self, variant: int):
         """Force a launch variant of the fused kernel for every call (-1: per-N_p choice)."""

@@ -47,6 +47,15 @@ def test_calls_on_a_null_plan_are_refused(L):
     assert L.fs_mlp_destroy(None) == 0
 
 
+def test_response_model_arguments_are_checked(L):
+    for N, K, word in ((3, 0, "filter order"), (-2, 0, "filter order"), (1, 2, "k_max"), (0, -1, "k_max"),
+                       (2, 1, "plan is NULL")):
+        assert L.fs_plan_set_response(None, N, K) == EINVAL
+        assert "fs_plan_set_response" in err(L) and word in err(L), (N, K, err(L))
+    n, k = C.c_int(), C.c_int()
+    assert L.fs_plan_get_response(None, C.byref(n), C.byref(k)) == EINVAL
+
+
 def test_network_creation_rejects_bad_shapes(L):
     h = C.c_void_p()
     for width, batch in ((7, 16), (2048, 16), (0, 16), (64, 0)):
