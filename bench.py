@@ -112,10 +112,12 @@ def parse():
     ap.add_argument("--prior", choices=["full", "targeted"], default="full",
                     help="search mode: the full prior (M_c 10-50 Msun, 0.5 yr of t_c) or a follow-up box "
                          "(M_c +-0.5 Msun, t_c +-0.005 yr around the injection; full sky and e0)")
-    ap.add_argument("--profile-case", choices=["fp64", "mixed", "mlp"], default=None,
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "mlp", "series"], default=None,
                     help="one small run for kernel profiling: fp64/mixed = paper grid, the bench's 320 "
                          "particles, N_p = 16; mlp = the search's surrogate batch (16 networks of width 256): "
-                         "one training round on 2048 rows each and one forward of 5120 rows each")
+                         "one training round on 2048 rows each and one forward of 5120 rows each; series = "
+                         "the fp64 case's grid with the Eq. (freDres) response series (order 2, k <= 1) on 48 of "
+                         "its particles")
     return ap.parse_args()
 
 
@@ -792,6 +794,10 @@ def run_profile_case(args):
     plan.set_data(torch.from_numpy(noise).cuda(), torch.from_numpy(psd).cuda())
     if args.variant is not None:
         plan.set_variant(min(args.variant, plan.n_variants - 1))
+    if args.profile_case == "series":
+        # the response series (order 2, k <= 1) on the first 48 particles: a launch of ~0.1 s
+        plan.set_response(2, 1)
+        P = P[:48]
     P_dev = torch.from_numpy(P).cuda()
     for _ in range(2):
         F, _ = plan.fstat(P_dev, 16, want_parts=False)
