@@ -34,7 +34,10 @@
  *   - phi_e: leading-order e0^2 correction with e0 defined at f0 = 10 mHz.
  *   - phi_p is carried by the F+/Fx basis (psi = 0); phi_D = 2 pi f R sin(theta)
  *     cos(alpha(t_f) - phi); t(f) uses the orbital phase only.
- *   - rigid equilateral constellation on a 1 AU circular guiding-centre orbit
+ *   - spacecraft orbits: Keplerian ellipses (semi-major axis 1 AU, eccentricity e,
+ *     inclination sqrt(3) e, perihelia 120 degrees apart) expanded to first order in
+ *     e -- the rigid equilateral constellation -- or, on request (model.ecc = e),
+ *     to second order in e (Sec. IV); the rigid form is the default:
  *     (first-order-in-eccentricity orbits), long-wavelength Michelson X.
  *   - constants -phi_c - pi/4 of Psi are carried by the amplitudes a_i.
  *   - segment outer edges at the first/last bin whose t(f_k) lies in [0, T];
@@ -89,6 +92,8 @@ typedef struct {
     int mb_order;  /* -1: the paper's response T = F(t_f) e^{2 pi i f d(t_f)}; 0..2: Eq. (freDres)
                       with the filter F^N_{T_f} of this order N (see or_mb_response) */
     int mb_kmax;   /* highest k of the sum in Eq. (freDres), 0 or 1 (only T_A1 is defined) */
+    double ecc;    /* 0: rigid constellation (first-order orbits); > 0: the spacecraft orbits to
+                      second order in this eccentricity (or_sc_offset) */
 } or_model;
 
 /* ---- masses and PN coefficients (Appendix A) --------------------------- */
@@ -155,14 +160,33 @@ static double or_orbit_phase(const or_model* m, double t) {
     return 2.0 * OR_PI * t / OR_YEAR_S + m->alpha0;
 }
 
-/* Position of spacecraft n (0,1,2) relative to the guiding centre, in units
- * of e*R (first-order-in-eccentricity orbits; only directions are used). */
+/* Position of spacecraft n (0,1,2) relative to the guiding centre
+ * R (cos alpha, sin alpha, 0), in units of e*R: the Keplerian ellipse of
+ * semi-major axis R and eccentricity e whose mean anomaly is alpha - beta_n
+ * (beta_n = 2 pi n/3 + orient), its plane tilted by sqrt(3) e about the axis
+ * normal to the apsidal line and turned by beta_n about the ecliptic pole,
+ * expanded in e (eccentric anomaly to second order by Kepler's equation):
+ *   order 1: (cos(2a - b) - 3 cos b) / 2, (sin(2a - b) - 3 sin b) / 2, -sqrt3 cos(a - b)
+ *   order 2 (times e): -5/4 cos a - 5/8 cos(a - 2b) + 3/8 cos(3a - 2b),
+ *                      -5/4 sin a + 5/8 sin(a - 2b) + 3/8 sin(3a - 2b),
+ *                      sqrt3/2 (3 - cos(2a - 2b)).
+ * With model.ecc = 0 only the first order is kept (the rigid constellation).
+ * Only differences of positions are used (arm directions). */
 static void or_sc_offset(const or_model* m, int n, double alpha, double r[3]) {
     double beta = 2.0 * OR_PI * n / 3.0 + m->orient;
     r[0] = 0.5 * (cos(2.0 * alpha - beta) - 3.0 * cos(beta));
     r[1] = 0.5 * (sin(2.0 * alpha - beta) - 3.0 * sin(beta));
     r[2] = -sqrt(3.0) * cos(alpha - beta);
+    if (m->ecc != 0.0) {
+        const double e = m->ecc;
+        r[0] += e * (-1.25 * cos(alpha) - 0.625 * cos(alpha - 2.0 * beta) + 0.375 * cos(3.0 * alpha - 2.0 * beta));
+        r[1] += e * (-1.25 * sin(alpha) + 0.625 * sin(alpha - 2.0 * beta) + 0.375 * sin(3.0 * alpha - 2.0 * beta));
+        r[2] += e * (0.5 * sqrt(3.0) * (3.0 - cos(2.0 * alpha - 2.0 * beta)));
+    }
 }
+
+/* Public: spacecraft offset above (units of e R). */
+void or_sc_offset_at(const or_model* m, int n, double alpha, double* r) { or_sc_offset(m, n, alpha, r); }
 
 /* Detector tensor D = (a a - b b)/2 of the long-wavelength Michelson with
  * vertex at spacecraft v (a, b: unit vectors along its arms to spacecraft

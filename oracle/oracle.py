@@ -45,7 +45,7 @@ class Model(C.Structure):
     _fields_ = [("f_min", C.c_double), ("df", C.c_double), ("T_obs", C.c_double),
                 ("n", C.c_int64), ("response", C.c_int), ("pn_order", C.c_int),
                 ("alpha0", C.c_double), ("orient", C.c_double), ("channel", C.c_int),
-                ("mb_order", C.c_int), ("mb_kmax", C.c_int)]
+                ("mb_order", C.c_int), ("mb_kmax", C.c_int), ("ecc", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -98,6 +98,8 @@ def lib():
             L.or_mb_response_at.restype = None
             L.or_doppler_rates_at.argtypes = [C.POINTER(Params), C.POINTER(Model), C.c_double, _dp, _dp]
             L.or_doppler_rates_at.restype = None
+            L.or_sc_offset_at.argtypes = [C.POINTER(Model), C.c_int, C.c_double, _dp]
+            L.or_sc_offset_at.restype = None
             _lib = L
     return _lib
 
@@ -120,6 +122,7 @@ class OracleModel:
     channel: int = 0       # TDI channel: 0 X, 1 A, 2 E, 3 T
     mb_order: int = -1     # -1 the paper's response; 0..2 the Eq. (freDres) series with filter order N
     mb_kmax: int = 0       # highest k of that series (0 or 1)
+    ecc: float = 0.0       # 0 the rigid constellation; > 0 the orbits to second order in this eccentricity
 
     @staticmethod
     def from_grid(grid, **kw) -> "OracleModel":
@@ -127,7 +130,7 @@ class OracleModel:
 
     def c(self) -> Model:
         return Model(self.f_min, self.df, self.T_obs, self.n, self.response, self.pn_order,
-                     self.alpha0, self.orient, self.channel, self.mb_order, self.mb_kmax)
+                     self.alpha0, self.orient, self.channel, self.mb_order, self.mb_kmax, self.ecc)
 
 
 def _params(p) -> Params:
@@ -371,3 +374,11 @@ def doppler_rates(p, model: OracleModel, t: float) -> tuple[float, float]:
     P = _params(p)
     lib().or_doppler_rates_at(C.byref(P), C.byref(m), float(t), C.byref(a), C.byref(b))
     return a.value, b.value
+
+
+def sc_offset(model: OracleModel, n: int, alpha: float) -> np.ndarray:
+    """Offset of spacecraft n from the guiding centre at orbital phase alpha, in units of e R."""
+    out = np.zeros(3)
+    m = model.c()
+    lib().or_sc_offset_at(C.byref(m), int(n), float(alpha), _ptr(out))
+    return out
