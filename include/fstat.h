@@ -466,6 +466,29 @@ FS_API fs_status fs_mlp_train_graph_build(fs_mlp* const* mlps, int n, const fs_s
 FS_API fs_status fs_plan_set_response(fs_plan* plan, int filter_order, int k_max);
 FS_API fs_status fs_plan_get_response(const fs_plan* plan, int* filter_order, int* k_max);
 
+/* Spacecraft orbits of the FS_FP64 path (Sec. IV: the paper's analytic orbit
+ * is accurate to second order in eccentricity).
+ *   eccentricity = 0 (default): the rigid equilateral constellation (the
+ *     orbits to first order in e), whose patterns are trig polynomials of
+ *     degree 4 in the orbital phase alpha.
+ *   eccentricity = e in (0, 0.05]: each spacecraft on the Keplerian ellipse
+ *     of semi-major axis 1 AU, eccentricity e and inclination sqrt(3) e,
+ *     perihelia 120 degrees apart in mean anomaly, expanded to second order
+ *     in e; arms normalised exactly, patterns of the long-wavelength
+ *     Michelsons (and of A and E) from the three arm directions at each bin.
+ *     The first order in e gives the rigid form; the second makes the arms
+ *     breathe and tilt by O(e).  LISA's 2.5e9 m arms give
+ *     e = L / (2 sqrt(3) AU) = 4.824e-3.
+ * The Doppler delay stays that of the guiding centre.  The eccentric orbits
+ * run in the direct form of the fused kernel (launch variants 0-2; 3 and 4
+ * take variant 0's tile) and combine with fs_plan_set_response.  It applies
+ * to every later F-statistic, amplitude, swarm evaluation and fs_add_signal
+ * of the plan; graphs built earlier keep the orbits they were captured with.
+ * FS_EINVAL for e outside [0, 0.05], FS_EUNSUPPORTED for e > 0 on an
+ * FS_MIXED plan.  Host only, no device work. */
+FS_API fs_status fs_plan_set_orbit(fs_plan* plan, double eccentricity);
+FS_API fs_status fs_plan_get_orbit(const fs_plan* plan, double* eccentricity);
+
 /* Launch variants of the fused bin-loop kernel (the tile shape of the
  * ragged batch, Sec. IV's particle x frequency parallelism).
  *   FS_FP64 : direct form, the whole template evaluated at every bin:

@@ -71,6 +71,8 @@ struct fs_plan {
     // response of the FP64 path: the paper's form (resp_on = 0) or the series of Eq. (freDres)
     int resp_on;
     fs::Resp resp;
+    // orbits of the FP64 path: 0 the rigid constellation, > 0 to second order in this eccentricity
+    double orbit_e;
     unsigned long long* census;   // [fs::kCensusModes] device counters of fs_plan_census
     int census_on;
     struct TuneRec {
@@ -125,6 +127,18 @@ int fp64_tile(int variant) { return variant == 1 ? 1024 : variant == 2 ? 4096 : 
 fs::Grid channel_grid(const fs_plan* p, int c) {
     fs::Grid g = p->grid;
     const fs::Channel ch = fs::channel_of(p->tdi, c);
+    if (p->orbit_e > 0.0 && p->mode == FS_FP64) {
+        // the eccentric orbits' patterns are formed per channel from the three arms
+        g.orb.e = p->orbit_e;
+        g.orb.chan = p->tdi == FS_TDI_X ? 0 : 1 + c;
+        for (int k = 0; k < 3; k++) {
+            const double b = 2.0 * fs::kPi * k / 3.0 + p->grid.orient;
+            g.orb.cb[k] = cos(b);
+            g.orb.sb[k] = sin(b);
+            g.orb.c2b[k] = cos(2.0 * b);
+            g.orb.s2b[k] = sin(2.0 * b);
+        }
+    }
     g.orient += ch.orient_shift;
     g.pscale = ch.pscale;
     return g;
@@ -536,9 +550,10 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
     // the response series runs in the direct form only (the anchored form's expansions
     // are built for the paper's response): its variants 3 and 4 take the default tile
     const bool mb = !mixed && p->resp_on;
-    const bool anchored = !mixed && !mb && variant >= 3;
+    const bool direct_only = mb || (!mixed && p->orbit_e > 0.0);   // the eccentric orbits: direct form too
+    const bool anchored = !mixed && !direct_only && variant >= 3;
     pa.nsum = mb ? 8 : 7;
-    pa.tile = mixed ? fs::mixed_span() : anchored ? fs::fp64a_span() : fp64_tile(mb && variant >= 3 ? 0 : variant);
+    pa.tile = mixed ? fs::mixed_span() : anchored ? fs::fp64a_span() : fp64_tile(direct_only && variant >= 3 ? 0 : variant);
     pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
     // channel c: its response (turned orientation, scaled projections), its particles and partial sums
@@ -1165,6 +1180,24 @@ fs_status fs_plan_set_response(fs_plan* p, int filter_order, int k_max) {
     }
     p->resp = r;
     p->resp_on = 1;
+    return FS_OK;
+}
+
+fs_status fs_plan_set_orbit(fs_plan* p, double eccentricity) {
+    g_err[0] = 0;
+    if (!(eccentricity >= 0.0 && eccentricity <= 0.05))
+        return fail(FS_EINVAL, "fs_plan_set_orbit: eccentricity %g not in [0, 0.05]", eccentricity);
+    if (!p) return fail(FS_EINVAL, "fs_plan_set_orbit: plan is NULL");
+    if (eccentricity > 0.0 && p->mode != FS_FP64)
+        return fail(FS_EUNSUPPORTED, "fs_plan_set_orbit: the eccentric orbits need an FS_FP64 plan");
+    p->orbit_e = eccentricity;
+    return FS_OK;
+}
+
+fs_status fs_plan_get_orbit(const fs_plan* p, double* eccentricity) {
+    g_err[0] = 0;
+    if (!p || !eccentricity) return fail(FS_EINVAL, "fs_plan_get_orbit: NULL argument");
+    *eccentricity = p->orbit_e;
     return FS_OK;
 }
 

@@ -68,6 +68,15 @@ struct Particle {
     int64_t klo, khi;         // band: first/last bin with t(f_k) in [0, T_obs] (klo > khi: empty)
     int valid;                // 0: non-finite or unphysical parameters
     int pad;
+    double pq[6];             // polarisation basis of the source: p = theta-hat (0..2), q = phi-hat (3..5)
+};
+
+// Spacecraft orbits to second order in eccentricity (Sec. IV): e > 0 selects
+// them (direct kernels only), e = 0 the rigid constellation of antenna_of.
+struct Orbit {
+    double e;                          // eccentricity
+    int chan;                          // TDI channel the patterns are formed for: 0 X, 1 A, 2 E
+    double cb[3], sb[3], c2b[3], s2b[3];   // cos, sin of beta_k and 2 beta_k, beta_k = 2 pi k/3 + orientation
 };
 
 // Powers of the bin frequency that the phase and t(f) need.
@@ -111,15 +120,117 @@ __device__ __forceinline__ void antenna_of(const Particle& P, double c1, double 
     Fx = pj[0] * pj[1] - pj[2] * pj[3];
 }
 
+// Antenna patterns of the channel O.chan for the orbits of Orbit (and, with
+// DERIV, their derivatives with respect to alpha) from cos/sin of alpha.
+// Spacecraft k sits at the guiding centre plus e R times
+//   (cos(2a - b)/2 - 3/2 cos b + e (-5/8 cos(a - 2b) + 3/8 cos(3a - 2b)),
+//    sin(2a - b)/2 - 3/2 sin b + e (5/8 sin(a - 2b) + 3/8 sin(3a - 2b)),
+//    -sqrt3 cos(a - b) - e sqrt3/2 cos(2a - 2b)),   b = beta_k
+// (the terms common to the three spacecraft, which cancel in the arms,
+// left out).  Arms n1 = r1 - r0, n2 = r2 - r1, n3 = r0 - r2, normalised;
+// A_i = ((n_i.p)^2 - (n_i.q)^2)/2, B_i = (n_i.p)(n_i.q); the vertex
+// Michelsons are X = (1, 3), Y = (2, 1), Z = (3, 2) (first arm minus second)
+// and A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6.
+template <bool DERIV>
+__device__ __forceinline__ void antenna_ecc(const Orbit& O, const Particle& P, double c1, double s1, double& Fp,
+                                            double& Fx, double& dFp, double& dFx) {
+    const double c2 = fma(c1, c1, -s1 * s1), s2 = 2.0 * s1 * c1;
+    const double c3 = fma(c2, c1, -s2 * s1), s3 = fma(s2, c1, c2 * s1);
+    const double e = O.e, r3 = 1.7320508075688772;
+    double r[3][3], dr[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const double cb = O.cb[k], sb = O.sb[k], c2b = O.c2b[k], s2b = O.s2b[k];
+        const double c2ab = fma(c2, cb, s2 * sb), s2ab = fma(s2, cb, -c2 * sb);      // 2a - b
+        const double cab = fma(c1, cb, s1 * sb), sab = fma(s1, cb, -c1 * sb);        // a - b
+        const double ca2b = fma(c1, c2b, s1 * s2b), sa2b = fma(s1, c2b, -c1 * s2b);  // a - 2b
+        const double c32 = fma(c3, c2b, s3 * s2b), s32 = fma(s3, c2b, -c3 * s2b);    // 3a - 2b
+        const double c22 = fma(c2, c2b, s2 * s2b), s22 = fma(s2, c2b, -c2 * s2b);    // 2a - 2b
+        r[k][0] = fma(0.5, c2ab, -1.5 * cb) + e * fma(-0.625, ca2b, 0.375 * c32);
+        r[k][1] = fma(0.5, s2ab, -1.5 * sb) + e * fma(0.625, sa2b, 0.375 * s32);
+        r[k][2] = -r3 * fma(0.5 * e, c22, cab);
+        if (DERIV) {
+            dr[k][0] = -s2ab + e * fma(0.625, sa2b, -1.125 * s32);
+            dr[k][1] = c2ab + e * fma(0.625, ca2b, 1.125 * c32);
+            dr[k][2] = r3 * fma(e, s22, sab);
+        }
+    }
+    const double* p = P.pq;
+    const double* q = P.pq + 3;
+    double A[3], Bq[3], dA[3], dB[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int k0 = i, k1 = i == 2 ? 0 : i + 1;   // n_{i+1} = r_{k1} - r_{k0}
+        double n[3], dn[3], nn = 0.0, nd = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            n[j] = r[k1][j] - r[k0][j];
+            nn = fma(n[j], n[j], nn);
+            if (DERIV) {
+                dn[j] = dr[k1][j] - dr[k0][j];
+                nd = fma(n[j], dn[j], nd);
+            }
+        }
+        const double inv = 1.0 / sqrt(nn);
+        const double Pp = (n[0] * p[0] + n[1] * p[1] + n[2] * p[2]) * inv;
+        const double Qq = (n[0] * q[0] + n[1] * q[1] + n[2] * q[2]) * inv;
+        A[i] = 0.5 * (Pp * Pp - Qq * Qq);
+        Bq[i] = Pp * Qq;
+        if (DERIV) {
+            // d(n/|n|) = (dn - (n/|n|) ((n/|n|).dn)) / |n|
+            const double u = nd * inv * inv;
+            const double dP = ((dn[0] * p[0] + dn[1] * p[1] + dn[2] * p[2]) * inv - Pp * u);
+            const double dQ = ((dn[0] * q[0] + dn[1] * q[1] + dn[2] * q[2]) * inv - Qq * u);
+            dA[i] = Pp * dP - Qq * dQ;
+            dB[i] = dP * Qq + Pp * dQ;
+        }
+    }
+    if (O.chan == 0) {
+        Fp = A[0] - A[2];
+        Fx = Bq[0] - Bq[2];
+        if (DERIV) {
+            dFp = dA[0] - dA[2];
+            dFx = dB[0] - dB[2];
+        }
+    } else if (O.chan == 1) {
+        const double k = 0.7071067811865476;   // 1/sqrt2
+        Fp = k * (2.0 * A[2] - A[0] - A[1]);
+        Fx = k * (2.0 * Bq[2] - Bq[0] - Bq[1]);
+        if (DERIV) {
+            dFp = k * (2.0 * dA[2] - dA[0] - dA[1]);
+            dFx = k * (2.0 * dB[2] - dB[0] - dB[1]);
+        }
+    } else {
+        const double k = 1.224744871391589;    // sqrt(3/2)
+        Fp = k * (A[0] - A[1]);
+        Fx = k * (Bq[0] - Bq[1]);
+        if (DERIV) {
+            dFp = k * (dA[0] - dA[1]);
+            dFx = k * (dB[0] - dB[1]);
+        }
+    }
+}
+
 // Fractional part of the total phase in cycles (in [-1/2, 1/2]) at a bin with
-// double-double frequency (fh, fl), plus the response there.
+// double-double frequency (fh, fl), plus the response there (antenna patterns
+// of the rigid constellation, or with ECC those of the orbits of O).
 struct BinEval {
     double frac;   // Phi mod 1
     double Fp, Fx;
 };
 
+template <bool ECC>
+__device__ __forceinline__ BinEval eval_bin_fp64_t(const Particle& P, double fh, double fl, const FreqPowers& w,
+                                                   double g0l, double alpha0, const Orbit& O);
+
 __device__ __forceinline__ BinEval eval_bin_fp64(const Particle& P, double fh, double fl, const FreqPowers& w,
                                                  double g0l, double alpha0) {
+    return eval_bin_fp64_t<false>(P, fh, fl, w, g0l, alpha0, Orbit{});
+}
+
+template <bool ECC>
+__device__ __forceinline__ BinEval eval_bin_fp64_t(const Particle& P, double fh, double fl, const FreqPowers& w,
+                                                   double g0l, double alpha0, const Orbit& O) {
     BinEval r;
     // leading PN term P0 * f^-5/3 in double-double, reduced mod 1 exactly
     double p, e;
@@ -148,7 +259,12 @@ __device__ __forceinline__ BinEval eval_bin_fp64(const Particle& P, double fh, d
     rest = fma(-fh * P.AD, cd, rest);            // - f d(t_f)
     acc += rest - rint(rest);
     r.frac = acc - rint(acc);
-    antenna_of(P, c1, s1, r.Fp, r.Fx);
+    if (ECC) {
+        double dp, dx;
+        antenna_ecc<false>(O, P, c1, s1, r.Fp, r.Fx, dp, dx);
+    } else {
+        antenna_of(P, c1, s1, r.Fp, r.Fx);
+    }
     return r;
 }
 
@@ -215,8 +331,9 @@ struct BinEvalMB {
     double Tpr, Tpi, Txr, Txi;
 };
 
+template <bool ECC>
 __device__ __forceinline__ BinEvalMB eval_bin_mb(const Particle& P, double fh, double fl, const FreqPowers& w,
-                                                 double g0l, double alpha0, const Resp& R) {
+                                                 double g0l, double alpha0, const Resp& R, const Orbit& O) {
     BinEvalMB r;
     // orbital phase as in eval_bin_fp64
     double p, e;
@@ -265,7 +382,10 @@ __device__ __forceinline__ BinEvalMB eval_bin_mb(const Particle& P, double fh, d
         const double cx = fma(-0.5 * x2, fma(-x2, 1.0 / 12.0, 1.0), 1.0), sx = x * fma(-x2, 1.0 / 6.0, 1.0);
         const double cr = fma(ca, cx, sa * sx), sr = fma(sa, cx, -ca * sx);
         double F[2], dF[2];
-        antenna_deriv(P, cr, sr, F[0], F[1], dF[0], dF[1]);
+        if (ECC)
+            antenna_ecc<true>(O, P, cr, sr, F[0], F[1], dF[0], dF[1]);
+        else
+            antenna_deriv(P, cr, sr, F[0], F[1], dF[0], dF[1]);
         const double inv = 1.0 / (1.0 + ddj);
         double cph = 1.0, sph = 0.0;
         if (j != 0) sincos(kTwoPi * fh * (dj * (1.0 - ddj) - D0), &sph, &cph);

@@ -244,6 +244,10 @@ __global__ void setup_kernel(Grid g, const ::fs_params* __restrict__ params, int
         const double kap = 1.0 / (4.0 * sqrt(3.0));
         const double pv[3] = {sb * cl, sb * sl, -cb};   // theta-hat
         const double qv[3] = {-sl, cl, 0.0};            // phi-hat
+        for (int j = 0; j < 3; j++) {
+            P.pq[j] = pv[j];
+            P.pq[3 + j] = qv[j];
+        }
         for (int arm = 0; arm < 2; arm++) {
             const int m = arm + 1;
             const double dc = cbn[m] - cbn[0], ds = sbn[m] - sbn[0];
@@ -384,7 +388,8 @@ cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const S
 //   X1 = sum z conj(G1), X2 = sum z conj(G2), K11 = sum W |G1|^2,
 //   K12 = sum W Re(G1 conj G2), K22 = sum W |G2|^2 and K12' = sum W Im(G1 conj G2).
 // ---------------------------------------------------------------------------
-template <int NS>
+// ECC: antenna patterns of the orbits to second order in eccentricity (g.orb).
+template <int NS, bool ECC>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 1)
 fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa, Resp resp) {
     const int lane = threadIdx.x & 31;
@@ -422,7 +427,7 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
             const double2 rc = pa.rot[(int64_t)b * sg.Np + pk];
             double dr = tb.dwr[k], di = tb.dwi[k], W = tb.W[k];
             if constexpr (NS == 7) {
-                BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
+                BinEval ev = eval_bin_fp64_t<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, g.orb);
                 double sn, cs;
                 sincospi(2.0 * ev.frac, &sn, &cs);
                 const double G1 = fma(rc.x, ev.Fp, rc.y * ev.Fx);
@@ -438,7 +443,7 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
                 t7[5] = wg * G2;
                 t7[6] = W * G2 * G2;
             } else {
-                BinEvalMB ev = eval_bin_mb(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp);
+                BinEvalMB ev = eval_bin_mb<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp, g.orb);
                 double sn, cs;
                 sincospi(2.0 * ev.frac, &sn, &cs);
                 const double G1r = fma(rc.x, ev.Tpr, rc.y * ev.Txr), G1i = fma(rc.x, ev.Tpi, rc.y * ev.Txi);
@@ -490,11 +495,17 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
                              const Partials& pa, cudaStream_t s, const Resp* resp) {
     if (B <= 0) return cudaSuccess;
     dim3 grid((unsigned)pa.ntiles, (unsigned)((B + kWarpsPerCta - 1) / kWarpsPerCta));
+    const bool ecc = g.orb.e > 0.0;
     if (resp) {
         if (pa.nsum != 8) return cudaErrorInvalidValue;
-        fp64_main_kernel<8><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
+        if (ecc)
+            fp64_main_kernel<8, true><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
+        else
+            fp64_main_kernel<8, false><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
+    } else if (ecc) {
+        fp64_main_kernel<7, true><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
     } else {
-        fp64_main_kernel<7><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
+        fp64_main_kernel<7, false><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
     }
     return cudaGetLastError();
 }
@@ -718,7 +729,7 @@ cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStrea
 // Signal synthesis: data += sum_i a_i A^i over the particle's band (FP64).
 // ---------------------------------------------------------------------------
 // With the response series (MB): h = (a1 - i a3) T+ h0 + (a2 - i a4) Tx h0.
-template <bool MB>
+template <bool MB, bool ECC>
 __global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict__ part, const double* a,
                                   double* data, Resp resp) {
     const Particle P = *part;
@@ -732,7 +743,7 @@ __global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict_
     double amp = pow(tb.fh[k], -7.0 / 6.0);
     double sn, cs;
     if constexpr (MB) {
-        BinEvalMB ev = eval_bin_mb(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp);
+        BinEvalMB ev = eval_bin_mb<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp, g.orb);
         sincospi(2.0 * ev.frac, &sn, &cs);
         // coefficient of h0: (a1 - i a3)(Tpr + i Tpi) + (a2 - i a4)(Txr + i Txi) = cr + i ci
         const double cr = a[0] * ev.Tpr + a[2] * ev.Tpi + a[1] * ev.Txr + a[3] * ev.Txi;
@@ -741,7 +752,7 @@ __global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict_
         data[2 * k] += amp * (cr * cs + ci * sn);
         data[2 * k + 1] += amp * (ci * cs - cr * sn);
     } else {
-        BinEval ev = eval_bin_fp64(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0);
+        BinEval ev = eval_bin_fp64_t<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, g.orb);
         sincospi(2.0 * ev.frac, &sn, &cs);
         double c = a[0] * ev.Fp + a[1] * ev.Fx;   // coefficient of h0
         double s = a[2] * ev.Fp + a[3] * ev.Fx;   // coefficient of -i h0
@@ -755,10 +766,15 @@ cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* pa
                               double* data, cudaStream_t s, const Resp* resp) {
     int threads = 256;
     int64_t blocks = (g.n + threads - 1) / threads;
-    if (resp)
-        add_signal_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
+    const bool ecc = g.orb.e > 0.0;
+    if (resp && ecc)
+        add_signal_kernel<true, true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
+    else if (resp)
+        add_signal_kernel<true, false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
+    else if (ecc)
+        add_signal_kernel<false, true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
     else
-        add_signal_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
+        add_signal_kernel<false, false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
     return cudaGetLastError();
 }
 

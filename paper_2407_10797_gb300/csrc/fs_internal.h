@@ -34,6 +34,7 @@ struct Grid {
     double f_min, df, T_obs;
     double alpha0, orient;   // detector orbital phase and orientation at t = 0
     double pscale = 1.0;     // scale of the arm projections: the patterns, quadratic in them, carry pscale^2
+    Orbit orb{};             // orbits to second order in eccentricity when orb.e > 0 (direct kernels only)
 };
 
 // TDI channels in the long-wavelength limit (Sec. II.A, Eq. eq2): with the

@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_plan_set_variant.argtypes = [_vp, C.c_int]
         L.fs_plan_set_response.argtypes = [_vp, C.c_int, C.c_int]
         L.fs_plan_get_response.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.fs_plan_set_orbit.argtypes = [_vp, C.c_double]
+        L.fs_plan_get_orbit.argtypes = [_vp, C.POINTER(C.c_double)]
         L.fs_plan_set_variant_for.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
         L.fs_plan_get_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
         L.fs_plan_census.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int64)]
@@ -316,6 +318,16 @@ class Plan:
         n, k = C.c_int(), C.c_int()
         _check(self._L.fs_plan_get_response(self._h, C.byref(n), C.byref(k)))
         return n.value, k.value
+
+    def set_orbit(self, eccentricity: float = 0.0):
+        """Spacecraft orbits of the FS_FP64 path: 0 the rigid constellation, e > 0 the
+        orbits to second order in eccentricity e (LISA: 4.824e-3)."""
+        _check(self._L.fs_plan_set_orbit(self._h, float(eccentricity)))
+
+    def get_orbit(self) -> float:
+        e = C.c_double()
+        _check(self._L.fs_plan_get_orbit(self._h, C.byref(e)))
+        return e.value
 
     def set_variant(self, variant: int):
         """Force a launch variant of the fused kernel for every call (-1: per-N_p choice)."""

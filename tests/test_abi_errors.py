@@ -56,6 +56,15 @@ def test_response_model_arguments_are_checked(L):
     assert L.fs_plan_get_response(None, C.byref(n), C.byref(k)) == EINVAL
 
 
+def test_orbit_arguments_are_checked(L):
+    for e, word in ((-1e-3, "eccentricity"), (0.06, "eccentricity"), (float("nan"), "eccentricity"),
+                    (0.0048, "plan is NULL")):
+        assert L.fs_plan_set_orbit(None, C.c_double(e)) == EINVAL
+        assert "fs_plan_set_orbit" in err(L) and word in err(L), (e, err(L))
+    v = C.c_double()
+    assert L.fs_plan_get_orbit(None, C.byref(v)) == EINVAL
+
+
 def test_network_creation_rejects_bad_shapes(L):
     h = C.c_void_p()
     for width, batch in ((7, 16), (2048, 16), (0, 16), (64, 0)):
