@@ -166,6 +166,16 @@ FS_API fs_status fs_fstat_batch(fs_plan* plan, const fs_params* params_dev, int 
  * bit 0 was set, FS_OK otherwise. */
 FS_API fs_status fs_plan_check(fs_plan* plan, int* flags_out);
 
+/* Self-test of the timeout path that fs_plan_check reports (bit 2): launches
+ * on the plan's stream one device wait that runs out by design -- an
+ * mbarrier that nothing arrives at, polled a bounded number of times, as the
+ * staged FS_MIXED kernel polls its copies -- which sets the plan's timeout
+ * bit and returns.  The next fs_plan_check returns FS_ETIMEOUT and clears the
+ * bit; the plan and its context stay usable.  No counterpart in the paper:
+ * it lets a caller (and the tests) see that a device-side wait that gives up
+ * is reported on the host without faulting the GPU.  Asynchronous. */
+FS_API fs_status fs_plan_selftest_timeout(fs_plan* plan);
+
 /* Maximum-likelihood amplitudes and extrinsic parameters (Eq. aandMN3 and
  * App. B, Eqs. B2-B3), per particle and segment.
  *   Arguments as in fs_fstat_batch; F_dev may be NULL (plan scratch).

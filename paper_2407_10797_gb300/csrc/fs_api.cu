@@ -1194,6 +1194,14 @@ fs_status fs_plan_set_orbit(fs_plan* p, double eccentricity) {
     return FS_OK;
 }
 
+fs_status fs_plan_selftest_timeout(fs_plan* p) {
+    g_err[0] = 0;
+    if (!p) return fail(FS_EINVAL, "fs_plan_selftest_timeout: plan is NULL");
+    cudaError_t e = fs::launch_wait_probe(p->flags_dev, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe launch");
+    return FS_OK;
+}
+
 fs_status fs_plan_get_orbit(const fs_plan* p, double* eccentricity) {
     g_err[0] = 0;
     if (!p || !eccentricity) return fail(FS_EINVAL, "fs_plan_get_orbit: NULL argument");

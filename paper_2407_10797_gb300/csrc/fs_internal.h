@@ -123,6 +123,8 @@ int fp64a_span();
 cudaError_t launch_fp64a_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
                               const Partials& pa, bool persistent, int* list, int* cnt, cudaStream_t s);
 cudaError_t launch_extrinsic(int64_t n, const double* amp, double* ext, cudaStream_t s);
+// One bounded mbarrier wait that runs out (nothing arrives): sets kFlagTimeout in *flags.
+cudaError_t launch_wait_probe(int* flags, cudaStream_t s);
 // FP32 tables of nch channels (t32 [nch][n]) with one common power-of-two scale (exponent in *emax)
 cudaError_t launch_tables32(const Grid& g, const Tables* t, int nch, int* emax, float4* t32, cudaStream_t s);
 // variant 0: grid, 2 CTAs/SM (up to 128 registers); 1: grid, 3 CTAs/SM (up to 80 registers);

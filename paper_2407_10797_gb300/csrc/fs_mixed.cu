@@ -860,10 +860,10 @@ __device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t
                  "r"(bytes)
                  : "memory");
 }
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete (at most `polls` polls).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, long long polls = kMaxPolls) {
     const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < kMaxPolls; i++) {
+    for (long long i = 0; i < polls; i++) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -880,6 +880,18 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Self-test of the timeout path: one thread initialises an mbarrier that
+// nothing arrives at and waits for its phase with a short bound (4096 polls);
+// the wait runs out and the kernel sets kFlagTimeout in the plan's flag word
+// and returns, as the staged kernel does when a copy never lands.
+__global__ void wait_probe_kernel(int* flags) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0u, 4096)) atomicOr(flags, kFlagTimeout);
 }
 
 struct StagedTables {
@@ -1189,4 +1201,11 @@ cudaError_t launch_tables32(const Grid& g, const Tables* t, int nch, int* emax, 
     return cudaSuccess;
 }
 
+}  // namespace fs
+
+namespace fs {
+cudaError_t launch_wait_probe(int* flags, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(flags);
+    return cudaGetLastError();
+}
 }  // namespace fs

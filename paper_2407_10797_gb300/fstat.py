@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_plan_set_response.argtypes = [_vp, C.c_int, C.c_int]
         L.fs_plan_get_response.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.fs_plan_set_orbit.argtypes = [_vp, C.c_double]
+        L.fs_plan_selftest_timeout.argtypes = [_vp]
         L.fs_plan_get_orbit.argtypes = [_vp, C.POINTER(C.c_double)]
         L.fs_plan_set_variant_for.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
         L.fs_plan_get_variant.argtypes = [_vp, C.c_int, C.c_int, C.POINTER(C.c_int)]
@@ -233,6 +234,11 @@ class Plan:
         f = C.c_int()
         _check(self._L.fs_plan_check(self._h, C.byref(f)))
         return f.value
+
+    def selftest_timeout(self):
+        """fs_plan_selftest_timeout: one device wait that runs out by design; the next
+        check() raises FstatError FS_ETIMEOUT."""
+        _check(self._L.fs_plan_selftest_timeout(self._h))
 
     def reserve(self, B_max: int, Np_max: int):
         _check(self._L.fs_plan_reserve(self._h, int(B_max), int(Np_max)))

@@ -63,6 +63,7 @@ def test_orbit_arguments_are_checked(L):
         assert "fs_plan_set_orbit" in err(L) and word in err(L), (e, err(L))
     v = C.c_double()
     assert L.fs_plan_get_orbit(None, C.byref(v)) == EINVAL
+    assert L.fs_plan_selftest_timeout(None) == EINVAL and "fs_plan_selftest_timeout" in err(L)
 
 
 def test_network_creation_rejects_bad_shapes(L):
