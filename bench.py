@@ -109,6 +109,10 @@ def parse():
                          "injection at delta_mu = 0.1585 (Table I); 0 = equal masses, 5-D")
     ap.add_argument("--progress", type=int, default=100,
                     help="search mode: read the best point every this many iterations (iterations to the target)")
+    ap.add_argument("--case", choices=["A", "B", "C"], default=None,
+                    help="search mode: inject the paper's Case A, B or C signal (Table III: t_c = 3.5 yr, its M_c, "
+                         "delta_mu, sky, e0, extrinsic parameters and SNR) instead of a drawn one; the full prior is "
+                         "then the paper's search range (t_c 3.3-3.8 yr, M_c 20-80 Msun, e0 0-0.05)")
     ap.add_argument("--prior", choices=["full", "targeted"], default="full",
                     help="search mode: the full prior (M_c 10-50 Msun, 0.5 yr of t_c) or a follow-up box "
                          "(M_c +-0.5 Msun, t_c +-0.005 yr around the injection; full sky and e0)")
@@ -842,6 +846,12 @@ def run_search(args):
     np_list = [st.Np for st in stages]
     layout = [((st.boxes or 16), (st.runs or 8), (st.particles or 40)) for st in stages]
     B_max = max(a * b * c for a, b, c in layout)
+    # Table III of the paper: (M_c / Msun, delta_mu, SNR); t_c = 3.5 yr, theta = 0.7854 rad,
+    # phi = 2.1216 rad, e0 = 0.01 and the extrinsic parameters are common to the three cases
+    cases = {"A": (70.3032, 0.1585, 11.3137), "B": (54.3572, 0.0400, 11.1723), "C": (28.1923, 0.2485, 14.1421)}
+    if args.case:
+        prior = S.Prior(Mc_lo=20.0, Mc_hi=80.0, tc_lo=3.3 * S.YEAR_S, tc_hi=3.8 * S.YEAR_S, e0_hi=0.05)
+        snr = cases[args.case][2] if args.snr is None else args.snr
     out = []
     for seed in args.seeds:
         stream = torch.cuda.Stream()
@@ -850,13 +860,16 @@ def run_search(args):
                             7000 + seed, stream=S.STREAM_INJECTION)[0]
         if args.dmu > 0.0:
             inj[5] = search.q_of_dmu(0.1585)        # the paper's injected delta_mu (Table I)
+        if args.case:
+            mc, dmu, _ = cases[args.case]
+            inj = np.array([mc, 3.5 * S.YEAR_S, 0.5 * math.pi - 0.7854, 2.1216, 0.01, search.q_of_dmu(dmu)])
         if args.prior == "targeted":
             # box centred on the injection shifted by a seeded offset (the search does not start at the truth)
             u = S.uniforms(7000 + seed, 0x54475444, 2)
             c_mc = inj[0] + 0.5 * (u[0] - 0.5)
             c_tc = inj[1] + 0.005 * S.YEAR_S * (u[1] - 0.5)
             prior = S.Prior(Mc_lo=c_mc - 0.5, Mc_hi=c_mc + 0.5, tc_lo=c_tc - 0.005 * S.YEAR_S,
-                            tc_hi=c_tc + 0.005 * S.YEAR_S, e0_hi=0.1)
+                            tc_hi=c_tc + 0.005 * S.YEAR_S, e0_hi=0.05 if args.case else 0.1)
         with torch.cuda.stream(stream):
             plan = fstat.Plan.from_grid(g, mode=mode, stream=stream)
             d_dev = torch.from_numpy(noise).to(dev)
@@ -922,7 +935,8 @@ def run_search(args):
                        "iterations_per_stage": [st.n_iter for st in stages], "snr": snr,
                        "prior": {"Mc": [prior.Mc_lo, prior.Mc_hi], "tc": [prior.tc_lo, prior.tc_hi],
                                  "e0": [0.0, prior.e0_hi], "sky": "full sphere"},
-                       "surrogate": args.search == "surrogate", "dmu_free_up_to": args.dmu},
+                       "surrogate": args.search == "surrogate", "dmu_free_up_to": args.dmu,
+                       "case": args.case},
             "exact_F_evaluations": int(sum(a * b * c * st.n_iter for (a, b, c), st in zip(layout, stages))),
             "Mc_rel_err": [o["Mc_rel_err"] for o in out],
             "iterations_to_Mc_1e-4": [o["iterations_to_Mc_1e-4"] for o in out], "runs": out}
