@@ -58,6 +58,14 @@ FP64_DIRECT_FLOP = 203.0
 # while the kernel has changed since its counters were taken.
 TRAFFIC_FP64_ANCHORED = 75.92e6
 TRAFFIC_MIXED = 48.59e6
+# Warp instructions issued by the mixed kernel in the same capture (smsp__inst_executed.sum at
+# N_p = 16): the kernel is bound by instruction issue (no pipe saturated), so its issue rate
+# against 152 SMs x 4 schedulers x 1 instruction per clock is reported beside the flop rate.
+INST_MIXED = 7.37e8
+
+
+def issue_peak_per_s():
+    return 152 * 4 * 2.07e9
 # mode 6 is tier (6, 2) with the phase remainder in FP32: its FP64 operations
 # are those of mode 5 less d^2, d^4 and the remainder polynomial (7)
 FP64_TIER_FLOP = {1: 96.0, 2: FP64_DIRECT_FLOP, 3: 84.0, 4: 76.0, 5: 70.0, 6: 63.0}
@@ -736,7 +744,14 @@ def run_gpu(args, world, rank, local):
                                    "traffic_algorithmic": 16 * g.n, "pipe": "fp32",
                                    "peak_source": "unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
                                    "flop_per_pbin": flopm,
-                                   "census_bins_by_mode": census_sum(censusm)},
+                                   "census_bins_by_mode": census_sum(censusm),
+                                   "issue": {"inst_per_launch": INST_MIXED,
+                                             "achieved_per_s": INST_MIXED / (mm_avg / 1e3),
+                                             "peak_per_s": issue_peak_per_s(),
+                                             "frac": INST_MIXED / (mm_avg / 1e3) / issue_peak_per_s(),
+                                             "source": "warp instructions of one N_p = 16 launch (ncu) over the "
+                                                       "live average launch time; peak = 152 SMs x 4 schedulers "
+                                                       "x 2.07 GHz"}},
                       "clocks": clocks_m},
             "cpu_baseline": cpu,
         }
