@@ -94,6 +94,9 @@ typedef struct {
     int mb_kmax;   /* highest k of the sum in Eq. (freDres), 0 or 1 (only T_A1 is defined) */
     double ecc;    /* 0: rigid constellation (first-order orbits); > 0: the spacecraft orbits to
                       second order in this eccentricity (or_sc_offset) */
+    double arm_s;  /* 0: long-wavelength response; > 0: the finite-arm TDI response
+                      (or_tdi_response) with nominal arm length arm_s light seconds */
+    int no_doppler; /* 1: drop the Doppler delay of the guiding centre (test knob) */
 } or_model;
 
 /* ---- masses and PN coefficients (Appendix A) --------------------------- */
@@ -259,9 +262,93 @@ static void or_antenna(const or_params* P, const or_model* m, double t, double* 
     *Fx = fx;
 }
 
+/* Finite-arm response of the first-generation TDI Michelsons (Sec. IV: a TDI
+ * combination is a sum of time-delayed single-arm responses), for the
+ * constellation frozen at time t, at frequency f, for the polarisations + and x.
+ * Spacecraft i sits at the guiding centre plus dx_i = L/(2 sqrt3) rho_i
+ * (rho of or_sc_offset: its arms are 2 sqrt3 long at first order, so L is the
+ * nominal arm length in seconds).  Link s -> r (emitted at s, received at r),
+ * n = (x_r - x_s)/L_sr, k = -(source direction):
+ *   y_sr = (n.e_A.n) [exp(-2 pi i f (L_sr + k.dx_s)) - exp(-2 pi i f k.dx_r)] / (2 (1 - k.n))
+ * per unit h_A(f) (the guiding centre's own delay is the Doppler factor that
+ * the template phase carries).  Michelson with vertex v and arms to a = v+1,
+ * b = v+2 (cyclic), normalised by -4 pi i f L:
+ *   R_v = [exp(-2 pi i f L_va) y_va + y_av - exp(-2 pi i f L_vb) y_vb - y_bv] / (-4 pi i f L),
+ * which tends to D_v : e_A (the long-wavelength pattern) as f L -> 0; the
+ * common TDI factor 1 - exp(-4 pi i f L) of signal and noise is divided out.
+ * Channels: X = R_0, A = (R_2 - R_0)/sqrt2, E = (R_0 - 2 R_1 + R_2)/sqrt6. */
+static void or_tdi_response(const or_params* P, const or_model* m, double f, double t, double complex T[2]) {
+    const double L = m->arm_s;
+    const double alpha = or_orbit_phase(m, t);
+    double x[3][3];
+    for (int i = 0; i < 3; i++) {
+        or_sc_offset(m, i, alpha, x[i]);
+        for (int j = 0; j < 3; j++) x[i][j] *= L / (2.0 * sqrt(3.0));
+    }
+    double sb = sin(P->lat), cb = cos(P->lat), sl = sin(P->lon), cl = cos(P->lon);
+    double p[3] = {sb * cl, sb * sl, -cb};
+    double q[3] = {-sl, cl, 0.0};
+    double k[3] = {-cb * cl, -cb * sl, -sb};
+    /* y[s][r][A] for every ordered pair s != r, and the link lengths */
+    double complex y[3][3][2];
+    double Lsr[3][3];
+    for (int s_ = 0; s_ < 3; s_++)
+        for (int r = 0; r < 3; r++) {
+            if (r == s_) continue;
+            double n[3], len = 0.0;
+            for (int j = 0; j < 3; j++) {
+                n[j] = x[r][j] - x[s_][j];
+                len += n[j] * n[j];
+            }
+            len = sqrt(len);
+            for (int j = 0; j < 3; j++) n[j] /= len;
+            Lsr[s_][r] = len;
+            double np = 0.0, nq = 0.0, kn = 0.0, kxs = 0.0, kxr = 0.0;
+            for (int j = 0; j < 3; j++) {
+                np += n[j] * p[j];
+                nq += n[j] * q[j];
+                kn += k[j] * n[j];
+                kxs += k[j] * x[s_][j];
+                kxr += k[j] * x[r][j];
+            }
+            double complex ph = cexp(-2.0 * I * OR_PI * f * (len + kxs)) - cexp(-2.0 * I * OR_PI * f * kxr);
+            double complex w = ph / (2.0 * (1.0 - kn));
+            y[s_][r][0] = (np * np - nq * nq) * w;
+            y[s_][r][1] = 2.0 * np * nq * w;
+        }
+    double complex R[3][2];
+    const double complex norm = -4.0 * I * OR_PI * f * L;
+    for (int v = 0; v < 3; v++) {
+        int a = (v + 1) % 3, b = (v + 2) % 3;
+        for (int A = 0; A < 2; A++)
+            R[v][A] = (cexp(-2.0 * I * OR_PI * f * Lsr[v][a]) * y[v][a][A] + y[a][v][A] -
+                       cexp(-2.0 * I * OR_PI * f * Lsr[v][b]) * y[v][b][A] - y[b][v][A]) / norm;
+    }
+    for (int A = 0; A < 2; A++) {
+        if (m->channel == 0) T[A] = R[0][A];
+        else if (m->channel == 1) T[A] = (R[2][A] - R[0][A]) / sqrt(2.0);
+        else if (m->channel == 2) T[A] = (R[0][A] - 2.0 * R[1][A] + R[2][A]) / sqrt(6.0);
+        else T[A] = (R[0][A] + R[1][A] + R[2][A]) / sqrt(3.0);
+    }
+}
+
+/* The response's pattern at time t and frequency f: the long-wavelength
+ * (F+, Fx) of or_antenna, or with model.arm_s > 0 the finite-arm TDI
+ * response of or_tdi_response (complex). */
+static void or_pattern(const or_params* P, const or_model* m, double f, double t, double complex F[2]) {
+    if (m->arm_s > 0.0 && m->response != 1) {
+        or_tdi_response(P, m, f, t, F);
+        return;
+    }
+    double Fp, Fx;
+    or_antenna(P, m, t, &Fp, &Fx);
+    F[0] = Fp;
+    F[1] = Fx;
+}
+
 /* Doppler delay d(t) = n . r_gc(t) = R sin(theta) cos(alpha(t) - phi). */
 static double or_doppler_delay(const or_params* P, const or_model* m, double t) {
-    if (m->response == 1) return 0.0;
+    if (m->response == 1 || m->no_doppler) return 0.0;
     double alpha = or_orbit_phase(m, t);
     return OR_AU_S * cos(P->lat) * cos(alpha - P->lon);
 }
@@ -271,7 +358,7 @@ static double or_doppler_delay(const or_params* P, const or_model* m, double t) 
 /* First and second time derivatives of the Doppler delay above (closed forms
  * of d/dt R cos(beta) cos(2 pi t / yr + alpha0 - lambda)). */
 static void or_doppler_rates(const or_params* P, const or_model* m, double t, double* dd, double* d2) {
-    if (m->response == 1) {
+    if (m->response == 1 || m->no_doppler) {
         *dd = 0.0;
         *d2 = 0.0;
         return;
@@ -345,12 +432,12 @@ void or_mb_weights(int N, double* a_re, double* a_im) {
 static void or_mb_G(const or_params* P, const or_model* m, double f, double tau, double D0, double complex G[2]) {
     double d = or_doppler_delay(P, m, tau), dd, d2;
     or_doppler_rates(P, m, tau, &dd, &d2);
-    double Fp, Fx;
-    or_antenna(P, m, tau - d, &Fp, &Fx);
+    double complex F[2];
+    or_pattern(P, m, f, tau - d, F);
     double ph = 2.0 * OR_PI * f * (d * (1.0 - dd) - D0);
     double complex c = (cos(ph) + I * sin(ph)) / (1.0 + dd);
-    G[0] = Fp * c;
-    G[1] = Fx * c;
+    G[0] = F[0] * c;
+    G[1] = F[1] * c;
 }
 
 /* Eq. (freDres) at frequency f with t_f = t, divided by exp(2 pi i f D0):
@@ -425,6 +512,16 @@ void or_mb_response_at(const or_params* P, const or_model* m, double f, double* 
     out[5] = or_tf_width(P, m, f);
 }
 
+/* Public: the finite-arm TDI response (Re T+, Im T+, Re Tx, Im Tx) at frequency f and time t. */
+void or_tdi_response_at(const or_params* P, const or_model* m, double f, double t, double* out) {
+    double complex T[2];
+    or_tdi_response(P, m, f, t, T);
+    out[0] = creal(T[0]);
+    out[1] = cimag(T[0]);
+    out[2] = creal(T[1]);
+    out[3] = cimag(T[1]);
+}
+
 void or_doppler_rates_at(const or_params* P, const or_model* m, double t, double* dd, double* d2) {
     or_doppler_rates(P, m, t, dd, d2);
 }
@@ -471,6 +568,22 @@ void or_basis(const or_params* P, const or_model* m, int64_t k0, int64_t k1, dou
             double fr = (double)(ph - roundl(ph));
             double complex T[2];
             or_mb_response(P, m, f, t, D0, T);
+            double amp = pow(f, -7.0 / 6.0);
+            double complex h0 = amp * (cos(2.0 * OR_PI * fr) - I * sin(2.0 * OR_PI * fr));
+            for (int c = 0; c < 2; c++) {
+                double complex A = T[c] * h0, Am = -I * A;
+                re[c * n + j] = creal(A);
+                im[c * n + j] = cimag(A);
+                re[(c + 2) * n + j] = creal(Am);
+                im[(c + 2) * n + j] = cimag(Am);
+            }
+            continue;
+        }
+        if (m->arm_s > 0.0 && m->response != 1) {
+            /* the paper's form with the finite-arm TDI response: A1 = T+ h0, A3 = -i T+ h0, ... */
+            double complex T[2];
+            or_tdi_response(P, m, f, t, T);
+            double fr = or_phase_frac(P, m, m->f_min, m->df, k);
             double amp = pow(f, -7.0 / 6.0);
             double complex h0 = amp * (cos(2.0 * OR_PI * fr) - I * sin(2.0 * OR_PI * fr));
             for (int c = 0; c < 2; c++) {

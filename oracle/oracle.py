@@ -45,7 +45,8 @@ class Model(C.Structure):
     _fields_ = [("f_min", C.c_double), ("df", C.c_double), ("T_obs", C.c_double),
                 ("n", C.c_int64), ("response", C.c_int), ("pn_order", C.c_int),
                 ("alpha0", C.c_double), ("orient", C.c_double), ("channel", C.c_int),
-                ("mb_order", C.c_int), ("mb_kmax", C.c_int), ("ecc", C.c_double)]
+                ("mb_order", C.c_int), ("mb_kmax", C.c_int), ("ecc", C.c_double), ("arm_s", C.c_double),
+                ("no_doppler", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -100,6 +101,8 @@ def lib():
             L.or_doppler_rates_at.restype = None
             L.or_sc_offset_at.argtypes = [C.POINTER(Model), C.c_int, C.c_double, _dp]
             L.or_sc_offset_at.restype = None
+            L.or_tdi_response_at.argtypes = [C.POINTER(Params), C.POINTER(Model), C.c_double, C.c_double, _dp]
+            L.or_tdi_response_at.restype = None
             _lib = L
     return _lib
 
@@ -123,6 +126,8 @@ class OracleModel:
     mb_order: int = -1     # -1 the paper's response; 0..2 the Eq. (freDres) series with filter order N
     mb_kmax: int = 0       # highest k of that series (0 or 1)
     ecc: float = 0.0       # 0 the rigid constellation; > 0 the orbits to second order in this eccentricity
+    arm_s: float = 0.0     # 0 the long-wavelength response; > 0 the finite-arm TDI response, arm length in s
+    no_doppler: int = 0    # 1: no Doppler delay of the guiding centre (test knob)
 
     @staticmethod
     def from_grid(grid, **kw) -> "OracleModel":
@@ -130,7 +135,8 @@ class OracleModel:
 
     def c(self) -> Model:
         return Model(self.f_min, self.df, self.T_obs, self.n, self.response, self.pn_order,
-                     self.alpha0, self.orient, self.channel, self.mb_order, self.mb_kmax, self.ecc)
+                     self.alpha0, self.orient, self.channel, self.mb_order, self.mb_kmax, self.ecc,
+                     self.arm_s, self.no_doppler)
 
 
 def _params(p) -> Params:
@@ -382,3 +388,12 @@ def sc_offset(model: OracleModel, n: int, alpha: float) -> np.ndarray:
     m = model.c()
     lib().or_sc_offset_at(C.byref(m), int(n), float(alpha), _ptr(out))
     return out
+
+
+def tdi_response(p, model: OracleModel, f: float, t: float):
+    """(T+, Tx) of the finite-arm TDI response at frequency f, constellation at time t."""
+    out = np.zeros(4)
+    m = model.c()
+    P = _params(p)
+    lib().or_tdi_response_at(C.byref(P), C.byref(m), float(f), float(t), _ptr(out))
+    return out[0] + 1j * out[1], out[2] + 1j * out[3]
