@@ -499,6 +499,31 @@ FS_API fs_status fs_plan_get_response(const fs_plan* plan, int* filter_order, in
 FS_API fs_status fs_plan_set_orbit(fs_plan* plan, double eccentricity);
 FS_API fs_status fs_plan_get_orbit(const fs_plan* plan, double* eccentricity);
 
+/* Arm transfer of the FS_FP64 path's response (Sec. IV: a TDI combination is
+ * a sum of time-delayed single-arm responses).
+ *   arm_seconds = 0 (default): the long-wavelength limit, patterns
+ *     D : e_A of the Michelson detector tensors.
+ *   arm_seconds = L > 0: the finite-arm response of the first-generation TDI
+ *     Michelsons with nominal arm L (LISA: 2.5e9 m = 8.339 s), constellation
+ *     frozen at t_f.  Link s -> r (n = (x_r - x_s)/L_sr, k the propagation
+ *     direction): y = (n.e_A.n) (-i pi f L_sr) sinc(pi f L_sr (1 - k.n))
+ *     e^{-i pi f (L_sr + k.(x_s + x_r))}; vertex v with arms to a and b:
+ *     R_v = [e^{-2 pi i f L_va} y_va + y_av - e^{-2 pi i f L_vb} y_vb - y_bv]
+ *     / (-4 pi i f L), which tends to the long-wavelength pattern as f L -> 0
+ *     (the TDI factor 1 - e^{-4 pi i f L}, common to signal and noise, is
+ *     divided out); X = R_0, A = (R_2 - R_0)/sqrt2, E = (R_0 - 2R_1 + R_2)/sqrt6.
+ *     Positions x are the guiding centre (whose delay is the Doppler term of
+ *     the template phase) plus L/(2 sqrt3) times the orbit offsets, rigid or
+ *     to second order in eccentricity (fs_plan_set_orbit).  The responses are
+ *     complex, so each segment carries eight sums, as for the series.
+ * It applies to every later evaluation and fs_add_signal of the plan (graphs
+ * built earlier keep what they were captured with); it runs in the direct
+ * form of the fused kernel.  FS_EINVAL for L outside [0, 100] s;
+ * FS_EUNSUPPORTED for L > 0 on an FS_MIXED plan or together with the response
+ * series (fs_plan_set_response with a filter order >= 0).  Host only. */
+FS_API fs_status fs_plan_set_arm(fs_plan* plan, double arm_seconds);
+FS_API fs_status fs_plan_get_arm(const fs_plan* plan, double* arm_seconds);
+
 /* Launch variants of the fused bin-loop kernel (the tile shape of the
  * ragged batch, Sec. IV's particle x frequency parallelism).
  *   FS_FP64 : direct form, the whole template evaluated at every bin:

@@ -73,6 +73,8 @@ struct fs_plan {
     fs::Resp resp;
     // orbits of the FP64 path: 0 the rigid constellation, > 0 to second order in this eccentricity
     double orbit_e;
+    // response of the FP64 path: 0 long-wavelength, > 0 the finite-arm TDI response with this arm (s)
+    double arm_s;
     unsigned long long* census;   // [fs::kCensusModes] device counters of fs_plan_census
     int census_on;
     struct TuneRec {
@@ -127,9 +129,11 @@ int fp64_tile(int variant) { return variant == 1 ? 1024 : variant == 2 ? 4096 : 
 fs::Grid channel_grid(const fs_plan* p, int c) {
     fs::Grid g = p->grid;
     const fs::Channel ch = fs::channel_of(p->tdi, c);
-    if (p->orbit_e > 0.0 && p->mode == FS_FP64) {
-        // the eccentric orbits' patterns are formed per channel from the three arms
+    if ((p->orbit_e > 0.0 || p->arm_s > 0.0) && p->mode == FS_FP64) {
+        // the eccentric orbits' patterns (and the finite-arm response) are formed per channel
+        // from the three arms
         g.orb.e = p->orbit_e;
+        g.orb.L = p->arm_s;
         g.orb.chan = p->tdi == FS_TDI_X ? 0 : 1 + c;
         for (int k = 0; k < 3; k++) {
             const double b = 2.0 * fs::kPi * k / 3.0 + p->grid.orient;
@@ -550,9 +554,11 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
     // the response series runs in the direct form only (the anchored form's expansions
     // are built for the paper's response): its variants 3 and 4 take the default tile
     const bool mb = !mixed && p->resp_on;
-    const bool direct_only = mb || (!mixed && p->orbit_e > 0.0);   // the eccentric orbits: direct form too
+    const bool fin = !mixed && p->arm_s > 0.0;
+    // the eccentric orbits and the finite-arm response run in the direct form too
+    const bool direct_only = mb || fin || (!mixed && p->orbit_e > 0.0);
     const bool anchored = !mixed && !direct_only && variant >= 3;
-    pa.nsum = mb ? 8 : 7;
+    pa.nsum = (mb || fin) ? 8 : 7;
     pa.tile = mixed ? fs::mixed_span() : anchored ? fs::fp64a_span() : fp64_tile(direct_only && variant >= 3 ? 0 : variant);
     pa.ntiles = (int)((p->grid.n + pa.tile - 1) / pa.tile);
     double* Fpart = F_part_dev ? F_part_dev : p->Fpart;
@@ -1155,6 +1161,8 @@ fs_status fs_plan_set_response(fs_plan* p, int filter_order, int k_max) {
     if (!p) return fail(FS_EINVAL, "fs_plan_set_response: plan is NULL");
     if (filter_order >= 0 && p->mode != FS_FP64)
         return fail(FS_EUNSUPPORTED, "fs_plan_set_response: the response series needs an FS_FP64 plan");
+    if (filter_order >= 0 && p->arm_s > 0.0)
+        return fail(FS_EUNSUPPORTED, "fs_plan_set_response: the series is not offered with the finite-arm response");
     if (filter_order < 0) {
         p->resp_on = 0;
         return FS_OK;
@@ -1191,6 +1199,26 @@ fs_status fs_plan_set_orbit(fs_plan* p, double eccentricity) {
     if (eccentricity > 0.0 && p->mode != FS_FP64)
         return fail(FS_EUNSUPPORTED, "fs_plan_set_orbit: the eccentric orbits need an FS_FP64 plan");
     p->orbit_e = eccentricity;
+    return FS_OK;
+}
+
+fs_status fs_plan_set_arm(fs_plan* p, double arm_seconds) {
+    g_err[0] = 0;
+    if (!(arm_seconds >= 0.0 && arm_seconds <= 100.0))
+        return fail(FS_EINVAL, "fs_plan_set_arm: arm length %g s not in [0, 100]", arm_seconds);
+    if (!p) return fail(FS_EINVAL, "fs_plan_set_arm: plan is NULL");
+    if (arm_seconds > 0.0 && p->mode != FS_FP64)
+        return fail(FS_EUNSUPPORTED, "fs_plan_set_arm: the finite-arm response needs an FS_FP64 plan");
+    if (arm_seconds > 0.0 && p->resp_on)
+        return fail(FS_EUNSUPPORTED, "fs_plan_set_arm: the finite-arm response is not offered with the series");
+    p->arm_s = arm_seconds;
+    return FS_OK;
+}
+
+fs_status fs_plan_get_arm(const fs_plan* p, double* arm_seconds) {
+    g_err[0] = 0;
+    if (!p || !arm_seconds) return fail(FS_EINVAL, "fs_plan_get_arm: NULL argument");
+    *arm_seconds = p->arm_s;
     return FS_OK;
 }
 

@@ -77,6 +77,7 @@ struct Orbit {
     double e;                          // eccentricity
     int chan;                          // TDI channel the patterns are formed for: 0 X, 1 A, 2 E
     double cb[3], sb[3], c2b[3], s2b[3];   // cos, sin of beta_k and 2 beta_k, beta_k = 2 pi k/3 + orientation
+    double L;                          // > 0: finite-arm TDI response with this nominal arm (s); 0: long wavelength
 };
 
 // Powers of the bin frequency that the phase and t(f) need.
@@ -211,6 +212,113 @@ __device__ __forceinline__ void antenna_ecc(const Orbit& O, const Particle& P, d
     }
 }
 
+// Finite-arm response of the first-generation TDI Michelsons (Sec. IV: a TDI
+// combination is a sum of time-delayed single-arm responses), constellation
+// frozen at orbital phase alpha (cos/sin c1, s1), frequency f, for + and x.
+// Spacecraft k at the guiding centre plus L/(2 sqrt3) times the orbit offsets
+// (first order, plus e times the second order including its terms common to
+// the three spacecraft, which shift the phase reference).  For the arm
+// (i, j), u = (x_j - x_i)/L_ij, the link i -> j (n = u) and j -> i (n = -u):
+//   y = (n.e_A.n) (-i pi f L_ij) sinc(pi f L_ij (1 - k.n)) exp(-i pi f (L_ij + k.(x_i + x_j))),
+// k = -(source direction) = -(p x q).  Vertex v, arms to a = v+1, b = v+2:
+//   R_v = [exp(-2 pi i f L_va) y_va + y_av - exp(-2 pi i f L_vb) y_vb - y_bv] / (-4 pi i f L);
+// channels X = R_0, A = (R_2 - R_0)/sqrt2, E = (R_0 - 2 R_1 + R_2)/sqrt6.
+__device__ __forceinline__ double sinc_d(double x) {
+    const double x2 = x * x;
+    return fabs(x) < 1e-4 ? fma(x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), 1.0) : sin(x) / x;
+}
+
+__device__ __forceinline__ void tdi_response(const Orbit& O, const Particle& P, double c1, double s1, double f,
+                                             double T[4]) {
+    const double c2 = fma(c1, c1, -s1 * s1), s2 = 2.0 * s1 * c1;
+    const double c3 = fma(c2, c1, -s2 * s1), s3 = fma(s2, c1, c2 * s1);
+    const double e = O.e, r3 = 1.7320508075688772, sc = O.L / (2.0 * r3);
+    double x[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const double cb = O.cb[k], sb = O.sb[k], c2b = O.c2b[k], s2b = O.s2b[k];
+        const double c2ab = fma(c2, cb, s2 * sb), s2ab = fma(s2, cb, -c2 * sb);
+        const double cab = fma(c1, cb, s1 * sb);
+        const double ca2b = fma(c1, c2b, s1 * s2b), sa2b = fma(s1, c2b, -c1 * s2b);
+        const double c32 = fma(c3, c2b, s3 * s2b), s32 = fma(s3, c2b, -c3 * s2b);
+        const double c22 = fma(c2, c2b, s2 * s2b);
+        x[k][0] = sc * (fma(0.5, c2ab, -1.5 * cb) + e * (fma(-0.625, ca2b, 0.375 * c32) - 1.25 * c1));
+        x[k][1] = sc * (fma(0.5, s2ab, -1.5 * sb) + e * (fma(0.625, sa2b, 0.375 * s32) - 1.25 * s1));
+        x[k][2] = sc * (-r3 * cab + e * (0.5 * r3) * (3.0 - c22));
+    }
+    const double* p = P.pq;
+    const double* q = P.pq + 3;
+    const double kv[3] = {-(p[1] * q[2] - p[2] * q[1]), -(p[2] * q[0] - p[0] * q[2]), -(p[0] * q[1] - p[1] * q[0])};
+    // per arm i = (i, i+1): projections, forward and backward link factors (without n.e.n), delay
+    double qp[3], qx[3], yfr[3], yfi[3], ybr[3], ybi[3], dr[3], di[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int j = i == 2 ? 0 : i + 1;
+        double u[3], L2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            u[c] = x[j][c] - x[i][c];
+            L2 = fma(u[c], u[c], L2);
+        }
+        const double Lij = sqrt(L2), inv = 1.0 / Lij;
+        const double up = (u[0] * p[0] + u[1] * p[1] + u[2] * p[2]) * inv;
+        const double uq = (u[0] * q[0] + u[1] * q[1] + u[2] * q[2]) * inv;
+        const double ku = (u[0] * kv[0] + u[1] * kv[1] + u[2] * kv[2]) * inv;
+        const double ks = kv[0] * (x[i][0] + x[j][0]) + kv[1] * (x[i][1] + x[j][1]) + kv[2] * (x[i][2] + x[j][2]);
+        qp[i] = fma(up, up, -uq * uq);
+        qx[i] = 2.0 * up * uq;
+        const double pfl = kPi * f * Lij;
+        double sp, cp;
+        sincos(kPi * f * (Lij + ks), &sp, &cp);
+        // (-i pfl) sinc * (cp - i sp) = pfl sinc (-sp - i cp)
+        const double af = pfl * sinc_d(pfl * (1.0 - ku)), ab = pfl * sinc_d(pfl * (1.0 + ku));
+        yfr[i] = -af * sp;
+        yfi[i] = -af * cp;
+        ybr[i] = -ab * sp;
+        ybi[i] = -ab * cp;
+        double sd, cd;
+        sincos(2.0 * kPi * f * Lij, &sd, &cd);
+        dr[i] = cd;
+        di[i] = -sd;
+    }
+    // R_v per polarisation, divided by -4 pi i f L: 1/(-i c) = i/c
+    double Rr[3][2], Ri[3][2];
+    const double cn = 4.0 * kPi * f * O.L;
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+        const int a = v == 2 ? 0 : v + 1, b = v == 0 ? 2 : v - 1;
+        // links v -> a: arm v forward; a -> v: arm v backward; v -> b: arm b backward; b -> v: arm b forward
+        const double mra = fma(dr[v], yfr[v], -di[v] * yfi[v]) + ybr[v];
+        const double mia = fma(dr[v], yfi[v], di[v] * yfr[v]) + ybi[v];
+        const double mrb = fma(dr[b], ybr[b], -di[b] * ybi[b]) + yfr[b];
+        const double mib = fma(dr[b], ybi[b], di[b] * ybr[b]) + yfi[b];
+#pragma unroll
+        for (int A = 0; A < 2; A++) {
+            const double wa = A == 0 ? qp[v] : qx[v], wb = A == 0 ? qp[b] : qx[b];
+            const double Mr = wa * mra - wb * mrb, Mi = wa * mia - wb * mib;
+            // (Mr + i Mi) * i / cn
+            Rr[v][A] = -Mi / cn;
+            Ri[v][A] = Mr / cn;
+        }
+    }
+#pragma unroll
+    for (int A = 0; A < 2; A++) {
+        double tr, ti;
+        if (O.chan == 0) {
+            tr = Rr[0][A];
+            ti = Ri[0][A];
+        } else if (O.chan == 1) {
+            tr = (Rr[2][A] - Rr[0][A]) * 0.7071067811865476;
+            ti = (Ri[2][A] - Ri[0][A]) * 0.7071067811865476;
+        } else {
+            tr = (Rr[0][A] - 2.0 * Rr[1][A] + Rr[2][A]) * 0.4082482904638631;
+            ti = (Ri[0][A] - 2.0 * Ri[1][A] + Ri[2][A]) * 0.4082482904638631;
+        }
+        T[2 * A] = tr;
+        T[2 * A + 1] = ti;
+    }
+}
+
 // Fractional part of the total phase in cycles (in [-1/2, 1/2]) at a bin with
 // double-double frequency (fh, fl), plus the response there (antenna patterns
 // of the rigid constellation, or with ECC those of the orbits of O).
@@ -228,10 +336,10 @@ __device__ __forceinline__ BinEval eval_bin_fp64(const Particle& P, double fh, d
     return eval_bin_fp64_t<false>(P, fh, fl, w, g0l, alpha0, Orbit{});
 }
 
-template <bool ECC>
-__device__ __forceinline__ BinEval eval_bin_fp64_t(const Particle& P, double fh, double fl, const FreqPowers& w,
-                                                   double g0l, double alpha0, const Orbit& O) {
-    BinEval r;
+// The template phase mod 1 (orbital phase minus f d(t_f)) and cos/sin of the
+// orbital phase alpha(t_f) at a bin.
+__device__ __forceinline__ double phase_and_alpha(const Particle& P, double fh, double fl, const FreqPowers& w,
+                                                  double g0l, double alpha0, double& c1, double& s1) {
     // leading PN term P0 * f^-5/3 in double-double, reduced mod 1 exactly
     double p, e;
     two_prod(P.P0h, w.g0h, p, e);
@@ -253,12 +361,19 @@ __device__ __forceinline__ BinEval eval_bin_fp64_t(const Particle& P, double fh,
     // response along t(f)
     double t = time_of(P, w);
     double alpha = fma(kTwoPi / kYearS, t, alpha0);
-    double s1, c1;
     sincos(alpha, &s1, &c1);
     double cd = fma(c1, P.clon, s1 * P.slon);   // cos(alpha - phi)
     rest = fma(-fh * P.AD, cd, rest);            // - f d(t_f)
     acc += rest - rint(rest);
-    r.frac = acc - rint(acc);
+    return acc - rint(acc);
+}
+
+template <bool ECC>
+__device__ __forceinline__ BinEval eval_bin_fp64_t(const Particle& P, double fh, double fl, const FreqPowers& w,
+                                                   double g0l, double alpha0, const Orbit& O) {
+    BinEval r;
+    double c1, s1;
+    r.frac = phase_and_alpha(P, fh, fl, w, g0l, alpha0, c1, s1);
     if (ECC) {
         double dp, dx;
         antenna_ecc<false>(O, P, c1, s1, r.Fp, r.Fx, dp, dx);
@@ -330,6 +445,23 @@ struct BinEvalMB {
     double frac;
     double Tpr, Tpi, Txr, Txi;
 };
+
+// The paper's form of the response (N = 0, no higher d(t) terms) with the
+// finite-arm TDI response of tdi_response in place of the long-wavelength
+// pattern: the same phase as eval_bin_fp64, complex T+ and Tx.
+__device__ __forceinline__ BinEvalMB eval_bin_fin(const Particle& P, double fh, double fl, const FreqPowers& w,
+                                                  double g0l, double alpha0, const Orbit& O) {
+    BinEvalMB r;
+    double c1, s1;
+    r.frac = phase_and_alpha(P, fh, fl, w, g0l, alpha0, c1, s1);
+    double T[4];
+    tdi_response(O, P, c1, s1, fh, T);
+    r.Tpr = T[0];
+    r.Tpi = T[1];
+    r.Txr = T[2];
+    r.Txi = T[3];
+    return r;
+}
 
 template <bool ECC>
 __device__ __forceinline__ BinEvalMB eval_bin_mb(const Particle& P, double fh, double fl, const FreqPowers& w,

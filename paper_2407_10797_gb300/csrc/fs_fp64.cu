@@ -388,10 +388,13 @@ cudaError_t launch_rotation(const Grid& g, const Particle* parts, int B, const S
 //   X1 = sum z conj(G1), X2 = sum z conj(G2), K11 = sum W |G1|^2,
 //   K12 = sum W Re(G1 conj G2), K22 = sum W |G2|^2 and K12' = sum W Im(G1 conj G2).
 // ---------------------------------------------------------------------------
+// RESP: 0 the paper's form (real patterns, seven sums), 1 the response series,
+// 2 the paper's form with the finite-arm TDI response (complex, eight sums).
 // ECC: antenna patterns of the orbits to second order in eccentricity (g.orb).
-template <int NS, bool ECC>
+template <int RESP, bool ECC>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 1)
 fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa, Resp resp) {
+    constexpr int NS = RESP == 0 ? 7 : 8;
     const int lane = threadIdx.x & 31;
     const int b = blockIdx.y * kWarpsPerCta + (threadIdx.x >> 5);
     const int tile = blockIdx.x;
@@ -426,7 +429,7 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
             w.e19 = tb.e19[k];
             const double2 rc = pa.rot[(int64_t)b * sg.Np + pk];
             double dr = tb.dwr[k], di = tb.dwi[k], W = tb.W[k];
-            if constexpr (NS == 7) {
+            if constexpr (RESP == 0) {
                 BinEval ev = eval_bin_fp64_t<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, g.orb);
                 double sn, cs;
                 sincospi(2.0 * ev.frac, &sn, &cs);
@@ -443,7 +446,9 @@ fp64_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, S
                 t7[5] = wg * G2;
                 t7[6] = W * G2 * G2;
             } else {
-                BinEvalMB ev = eval_bin_mb<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp, g.orb);
+                const BinEvalMB ev = RESP == 1
+                                         ? eval_bin_mb<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp, g.orb)
+                                         : eval_bin_fin(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, g.orb);
                 double sn, cs;
                 sincospi(2.0 * ev.frac, &sn, &cs);
                 const double G1r = fma(rc.x, ev.Tpr, rc.y * ev.Txr), G1i = fma(rc.x, ev.Tpi, rc.y * ev.Txi);
@@ -495,17 +500,20 @@ cudaError_t launch_fp64_main(const Grid& g, const Tables& t, const Particle* par
                              const Partials& pa, cudaStream_t s, const Resp* resp) {
     if (B <= 0) return cudaSuccess;
     dim3 grid((unsigned)pa.ntiles, (unsigned)((B + kWarpsPerCta - 1) / kWarpsPerCta));
-    const bool ecc = g.orb.e > 0.0;
-    if (resp) {
+    const bool ecc = g.orb.e > 0.0, fin = g.orb.L > 0.0;
+    if (fin) {
+        if (pa.nsum != 8 || resp) return cudaErrorInvalidValue;
+        fp64_main_kernel<2, false><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
+    } else if (resp) {
         if (pa.nsum != 8) return cudaErrorInvalidValue;
         if (ecc)
-            fp64_main_kernel<8, true><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
+            fp64_main_kernel<1, true><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
         else
-            fp64_main_kernel<8, false><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
+            fp64_main_kernel<1, false><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, *resp);
     } else if (ecc) {
-        fp64_main_kernel<7, true><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
+        fp64_main_kernel<0, true><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
     } else {
-        fp64_main_kernel<7, false><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
+        fp64_main_kernel<0, false><<<grid, kWarpsPerCta * 32, 0, s>>>(g, t, parts, B, sg, pa, Resp{});
     }
     return cudaGetLastError();
 }
@@ -729,7 +737,8 @@ cudaError_t launch_bands(const Particle* parts, int B, int64_t* bands, cudaStrea
 // Signal synthesis: data += sum_i a_i A^i over the particle's band (FP64).
 // ---------------------------------------------------------------------------
 // With the response series (MB): h = (a1 - i a3) T+ h0 + (a2 - i a4) Tx h0.
-template <bool MB, bool ECC>
+// RESP as for fp64_main_kernel.
+template <int RESP, bool ECC>
 __global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict__ part, const double* a,
                                   double* data, Resp resp) {
     const Particle P = *part;
@@ -742,8 +751,9 @@ __global__ void add_signal_kernel(Grid g, Tables tb, const Particle* __restrict_
     w.e19 = tb.e19[k];
     double amp = pow(tb.fh[k], -7.0 / 6.0);
     double sn, cs;
-    if constexpr (MB) {
-        BinEvalMB ev = eval_bin_mb<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp, g.orb);
+    if constexpr (RESP != 0) {
+        const BinEvalMB ev = RESP == 1 ? eval_bin_mb<ECC>(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, resp, g.orb)
+                                       : eval_bin_fin(P, tb.fh[k], tb.fl[k], w, tb.g0l[k], g.alpha0, g.orb);
         sincospi(2.0 * ev.frac, &sn, &cs);
         // coefficient of h0: (a1 - i a3)(Tpr + i Tpi) + (a2 - i a4)(Txr + i Txi) = cr + i ci
         const double cr = a[0] * ev.Tpr + a[2] * ev.Tpi + a[1] * ev.Txr + a[3] * ev.Txi;
@@ -767,14 +777,16 @@ cudaError_t launch_add_signal(const Grid& g, const Tables& t, const Particle* pa
     int threads = 256;
     int64_t blocks = (g.n + threads - 1) / threads;
     const bool ecc = g.orb.e > 0.0;
-    if (resp && ecc)
-        add_signal_kernel<true, true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
+    if (g.orb.L > 0.0)
+        add_signal_kernel<2, false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
+    else if (resp && ecc)
+        add_signal_kernel<1, true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
     else if (resp)
-        add_signal_kernel<true, false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
+        add_signal_kernel<1, false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, *resp);
     else if (ecc)
-        add_signal_kernel<false, true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
+        add_signal_kernel<0, true><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
     else
-        add_signal_kernel<false, false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
+        add_signal_kernel<0, false><<<(unsigned)blocks, threads, 0, s>>>(g, t, part, a, data, Resp{});
     return cudaGetLastError();
 }
 

@@ -84,6 +84,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fs_plan_set_response.argtypes = [_vp, C.c_int, C.c_int]
         L.fs_plan_get_response.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.fs_plan_set_orbit.argtypes = [_vp, C.c_double]
+        L.fs_plan_set_arm.argtypes = [_vp, C.c_double]
+        L.fs_plan_get_arm.argtypes = [_vp, C.POINTER(C.c_double)]
         L.fs_plan_selftest_timeout.argtypes = [_vp]
         L.fs_plan_get_orbit.argtypes = [_vp, C.POINTER(C.c_double)]
         L.fs_plan_set_variant_for.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
@@ -329,6 +331,16 @@ class Plan:
         """Spacecraft orbits of the FS_FP64 path: 0 the rigid constellation, e > 0 the
         orbits to second order in eccentricity e (LISA: 4.824e-3)."""
         _check(self._L.fs_plan_set_orbit(self._h, float(eccentricity)))
+
+    def set_arm(self, arm_seconds: float = 0.0):
+        """Arm transfer of the FS_FP64 response: 0 the long-wavelength limit, L > 0 the
+        finite-arm TDI response with nominal arm L seconds (LISA: 8.339)."""
+        _check(self._L.fs_plan_set_arm(self._h, float(arm_seconds)))
+
+    def get_arm(self) -> float:
+        v = C.c_double()
+        _check(self._L.fs_plan_get_arm(self._h, C.byref(v)))
+        return v.value
 
     def get_orbit(self) -> float:
         e = C.c_double()

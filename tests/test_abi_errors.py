@@ -64,6 +64,11 @@ def test_orbit_arguments_are_checked(L):
     v = C.c_double()
     assert L.fs_plan_get_orbit(None, C.byref(v)) == EINVAL
     assert L.fs_plan_selftest_timeout(None) == EINVAL and "fs_plan_selftest_timeout" in err(L)
+    for a, word in ((-1.0, "arm length"), (101.0, "arm length"), (float("inf"), "arm length"),
+                    (8.339, "plan is NULL")):
+        assert L.fs_plan_set_arm(None, C.c_double(a)) == EINVAL
+        assert "fs_plan_set_arm" in err(L) and word in err(L), (a, err(L))
+    assert L.fs_plan_get_arm(None, C.byref(v)) == EINVAL
 
 
 def test_network_creation_rejects_bad_shapes(L):
