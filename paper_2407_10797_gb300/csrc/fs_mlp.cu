@@ -397,7 +397,11 @@ gemm_tc5_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda, const 
     }
     // the last committed stage (MMAs complete in order); waited for even after a
     // failure -- then with the much longer drain bound -- so that no MMA is
-    // still writing when the TMEM is freed
+    // still writing when the TMEM is freed.  Should the drain bound run out too
+    // (an MMA that never completes), the TMEM is freed all the same: a CTA that
+    // exits holding its columns would leave the next CTA's allocation on this
+    // SM waiting for ever, while the error flag already makes the host discard
+    // this launch's output.
     if (issued > 0) {
         const int st = (issued - 1) & 1;
         if (!wait_bar(&bars[st], phase[st], failed ? kMaxPollsDrain : kMaxPolls)) failed = 1;
