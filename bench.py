@@ -62,6 +62,12 @@ TRAFFIC_MIXED = 48.59e6
 # N_p = 16): the kernel is bound by instruction issue (no pipe saturated), so its issue rate
 # against 152 SMs x 4 schedulers x 1 instruction per clock is reported beside the flop rate.
 INST_MIXED = 7.37e8
+# FP64 / FP32 flop executed per launch in the same kind of capture of each fused kernel (N_p = 16,
+# 320 particles), from the SASS instruction counts: DADD + DMUL + 2 DFMA; FADD + FMUL + 2 FFMA +
+# 2 FMUL2 + 4 FFMA2 (packed f32x2 instructions do two lanes).  They include the per-tile anchors and
+# per-piece work that the per-bin tier counts leave out.
+EXEC_FLOP_FP64_ANCHORED = 3.480e10
+EXEC_FLOP_MIXED = 2.878e10
 
 
 def issue_peak_per_s():
@@ -100,6 +106,10 @@ def parse():
                     help="force one launch variant of the fused kernel instead of autotuning")
     ap.add_argument("--variant-mixed", type=int, default=None,
                     help="the mixed mode's forced variant when --variant is given (default: the same number)")
+    ap.add_argument("--fidelity", action="store_true",
+                    help="also time the higher-fidelity response options (the Eq. freDres series of order 2 with "
+                         "k <= 1, the second-order orbit, the finite-arm TDI response) at N_p = 16 on the bench's "
+                         "particles, outside the timed step, with the change of F against the paper's form")
     ap.add_argument("--search", choices=["fp64", "mixed", "surrogate"], default=None,
                     help="time the full hierarchical search (4 stages) instead of the F-statistic step")
     ap.add_argument("--seeds", type=int, nargs="+", default=[0],
@@ -497,11 +507,18 @@ def two_channel_lines(args, world, fstat, g, psd, P_dev, stream, pbins):
     return out
 
 
-def response_series_line(args, world, fstat, g, d_dev, psd_dev, P_dev, stream, inband, Np=16, order=(2, 1)):
-    """The response series of Eq. (freDres) (filter order 2, k <= 1) in FP64 mode:
-    fs_fstat_batch of the bench's particles at one N_p after one untimed call,
-    `reps` timed calls, the fused kernel's launches timed by the plan's events;
-    and the change of F against the paper's form on the same data."""
+ECC_LISA = 2.5e9 / (2.0 * math.sqrt(3.0) * 1.495978707e11)   # 2.5 Gm arms at 1 AU
+ARM_LISA = 2.5e9 / 299792458.0                                 # s
+
+
+def response_series_line(args, world, fstat, g, d_dev, psd_dev, P_dev, stream, inband, Np=16, order=(2, 1),
+                         orbit=0.0, arm=0.0):
+    """A higher-fidelity response option in FP64 mode (by default the response
+    series of Eq. (freDres), filter order 2, k <= 1; or the second-order orbit, or
+    the finite-arm TDI response): fs_fstat_batch of the bench's particles at one
+    N_p after one untimed call, `reps` timed calls, the fused kernel's launches
+    timed by the plan's events; and the change of F against the paper's form on
+    the same data."""
     import torch
     dev = P_dev.device
     reps = 3
@@ -510,7 +527,10 @@ def response_series_line(args, world, fstat, g, d_dev, psd_dev, P_dev, stream, i
         plan.set_data(d_dev, psd_dev)
         plan.reserve(P_dev.shape[0], Np)
         F0 = plan.fstat(P_dev, Np, want_parts=False)[0].clone()
-        plan.set_response(*order)
+        if order is not None:
+            plan.set_response(*order)
+        plan.set_orbit(orbit)
+        plan.set_arm(arm)
         F = torch.empty(P_dev.shape[0], dtype=torch.float64, device=dev)
         plan.fstat(P_dev, Np, F=F, want_parts=False)
         plan.read_profile("main")
@@ -531,7 +551,8 @@ def response_series_line(args, world, fstat, g, d_dev, psd_dev, P_dev, stream, i
         ok = np.isfinite(b)
         change = float(np.max(np.abs(a[ok] - b[ok]) / np.maximum(np.abs(b[ok]), 2.0 * Np)))
         plan.close()
-    return {"filter_order": order[0], "k_max": order[1], "N_p": Np, "mode": "fp64 (direct form)",
+    return {"filter_order": None if order is None else order[0], "k_max": None if order is None else order[1],
+            "eccentricity": orbit, "arm_s": arm, "N_p": Np, "mode": "fp64 (direct form)",
             "value": inband * reps / (ms / 1e3), "unit": UNIT, "ms_per_call": ms / reps,
             "fused_ms_avg": main_ms / max(main_n, 1),
             "max_change_vs_paper_form": change, "change_metric": "|dF|/max(|F|, 2 N_p)"}
@@ -680,8 +701,15 @@ def run_gpu(args, world, rank, local):
 
     # ---- the A and E channels (two-channel data), both modes, fs_fstat_batch on the prior draw
     channels = two_channel_lines(args, world, fstat, g, psd, P0_dev, stream, total_pbins)
-    # ---- the response series of Eq. (freDres) on the same data and particles
-    series = response_series_line(args, world, fstat, g, d_dev, psd_dev, P0_dev, stream, inband)
+    # ---- the higher-fidelity response options on the same data and particles (--fidelity)
+    fidelity = None
+    if args.fidelity:
+        fidelity = {
+            "response_series": response_series_line(args, world, fstat, g, d_dev, psd_dev, P0_dev, stream, inband),
+            "orbit_second_order": response_series_line(args, world, fstat, g, d_dev, psd_dev, P0_dev, stream, inband,
+                                                       order=None, orbit=ECC_LISA),
+            "finite_arm_tdi": response_series_line(args, world, fstat, g, d_dev, psd_dev, P0_dev, stream, inband,
+                                                   order=None, arm=ARM_LISA)}
 
     # ---- roofline of the dominant kernels (average launch duration, live events)
     main_avg_ms = main_ms / max(main_n, 1)
@@ -725,7 +753,9 @@ def run_gpu(args, world, rank, local):
                          "traffic": TRAFFIC_FP64_ANCHORED if all(tune64[Np]["variant"] >= 3 for Np in NP_LIST) else None,
                          "traffic_algorithmic": 24 * g.n, "pipe": "fp64",
                          "peak_source": "unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                         "flop_per_pbin": flop64, "census_bins_by_mode": census_sum(census64)},
+                         "flop_per_pbin": flop64, "census_bins_by_mode": census_sum(census64),
+                         "executed_flop_frac": (EXEC_FLOP_FP64_ANCHORED / (main_avg_ms / 1e3) / 1e12 / peak_tf
+                                                if all(tune64[Np]["variant"] >= 3 for Np in NP_LIST) else None)},
             "clocks": clocks,
             "autotune": {"fp64": {str(k): v for k, v in tune64.items()},
                          "mixed": {str(k): v for k, v in tunem.items()}},
@@ -734,7 +764,7 @@ def run_gpu(args, world, rank, local):
                     "d2h_bytes_per_step": int(host["fit"].numel() * 8)},
             "e2e_fstat_batch": e2e_fstat,
             "channels_AE": channels,
-            "response_series": series,
+            "fidelity_options": fidelity,
             "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps, "dtype": "f64 anchors + f32",
                       "max_rel_err_vs_fp64": mix_err, "error_metric": "|dF|/max(|F|, 2 N_p)",
                       "max_rel_err_vs_fp64_by_Np": {str(k): v for k, v in mix_err_np.items()},
@@ -745,6 +775,7 @@ def run_gpu(args, world, rank, local):
                                    "peak_source": "unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
                                    "flop_per_pbin": flopm,
                                    "census_bins_by_mode": census_sum(censusm),
+                                   "executed_flop_frac": EXEC_FLOP_MIXED / (mm_avg / 1e3) / 1e12 / peak_m,
                                    "issue": {"inst_per_launch": INST_MIXED,
                                              "achieved_per_s": INST_MIXED / (mm_avg / 1e3),
                                              "peak_per_s": issue_peak_per_s(),
