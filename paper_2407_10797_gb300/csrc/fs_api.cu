@@ -98,6 +98,7 @@ struct fs_plan {
     // caller's edge frequencies at the start of every evaluation) and the sticky error flags
     int64_t* edges_dev;
     int* flags_dev;   // [0] sticky flags (fs_plan_check), [1] scratch of the grid check
+    double2* cis;     // FS_FP64: exp(2 pi i j 2^-20) table of the anchored kernels (16 MB)
     // single-particle scratch for fs_add_signal
     fs_params* one_param;
     fs::Particle* one_part;
@@ -362,6 +363,12 @@ fs_status fs_plan_create_tdi(fs_plan** out, int64_t n_bins, double f_min, double
         fs_plan_destroy(p);
         return cuda_fail(e, "cudaMalloc(plan)");
     }
+    if (mode == FS_FP64 &&
+        ((e = cudaMalloc(&p->cis, sizeof(double2) << fs::kCisBits)) != cudaSuccess ||
+         (e = fs::launch_cis_table(p->cis, p->stream)) != cudaSuccess)) {
+        fs_plan_destroy(p);
+        return cuda_fail(e, "exp table");
+    }
     if (mode == FS_MIXED &&
         ((e = cudaMalloc(&p->tab32, sizeof(float4) * (size_t)n_bins * p->nch)) != cudaSuccess ||
          (e = cudaMalloc(&p->emax, sizeof(int))) != cudaSuccess)) {
@@ -382,6 +389,7 @@ fs_status fs_plan_destroy(fs_plan* p) {
     cudaFree(p->tab_base);
     cudaFree(p->edges_dev);
     cudaFree(p->flags_dev);
+    cudaFree(p->cis);
     cudaFree(p->one_param);
     cudaFree(p->one_part);
     cudaFree(p->one_a);
@@ -544,6 +552,7 @@ fs_status fstat_impl(fs_plan* p, const fs_params* params_dev, int B, const doubl
     fs::Partials pa;
     pa.census = p->census_on ? p->census : nullptr;
     pa.flags = p->flags_dev;
+    pa.cis = p->cis;
     pa.H = p->H;
     pa.T = p->T;
     pa.S = p->S;

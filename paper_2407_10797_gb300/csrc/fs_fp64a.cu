@@ -17,9 +17,10 @@
 //     degree 4..4+NR part a remainder added in units of 2^-48 cycle (FP64, or
 //     FP32 in the lowest tier when it is at most 6.7e-8 cycle: error below
 //     2.5e-14 cycle);
-//   - exp(2 pi i Phi): a 1024-entry table value (top 10 bits, rounded) times
-//     the Taylor series of the remaining angle |theta| <= pi/1024 (cos to
-//     degree 4, sin to degree 5).
+//   - exp(2 pi i Phi): a 2^20-entry table value in global memory (top 20
+//     bits of the phase, rounded; 16 MB per plan, served by L2) times
+//     1 - theta^2/2 + i theta for the remaining angle |theta| <= pi 2^-20
+//     (dropped terms below 5e-18), folded into four FMAs.
 // A tile takes the lowest degree tier (NG, NR) = (6, 2), (7, 3), (8, 5) or
 // (10, 7) whose dropped terms, summed over the tile at the anchor, stay below
 // 1e-13 cycle (phase) and 1e-15 (antenna); a tile whose d(alpha) quintic or
@@ -44,7 +45,7 @@ constexpr int kTileA = 1024;                     // bins per anchor
 constexpr int kTilesA = 32;                      // tiles per span (one anchor per lane)
 constexpr int kSpanA = kTileA * kTilesA;         // 32768 bins
 constexpr int kWarpsA = 4;                       // warps (particles) per CTA
-constexpr int kTabA = 1024;                      // exp(2 pi i j / 1024) table
+
 
 constexpr int kDeg = 12;                         // Taylor degree in the bin offset d computed at an anchor
 constexpr double kRem32Max = 6.7e-8;             // largest phase remainder (cycles) evaluated in FP32
@@ -246,20 +247,19 @@ __device__ __forceinline__ double horner(const double* c, double x) {
 }
 
 // exp(2 pi i Phi) from the phase in 64-bit fixed point (cycles mod 1 in
-// units of 2^-64): the nearest multiple of 1/1024 cycle indexes the table, the
-// remaining 54 bits give the angle |theta| <= pi/1024, whose cos and sin come
-// from their Taylor series (cos to degree 4, sin to degree 5; truncation
-// below 2e-18).
+// units of 2^-64): the nearest multiple of 2^-20 cycle indexes the table
+// (kCisBits bits), the remaining 44 bits give the angle |theta| <= pi 2^-20,
+// and exp(i theta) = 1 - theta^2/2 + i theta to below 5e-18 (the theta^3/6 of
+// the sine is the largest dropped term):
+//   cos = t.x + theta (t.x (-theta/2) - t.y),  sin = t.y + theta (t.y (-theta/2) + t.x).
 __device__ __forceinline__ void cis_fixed(unsigned long long Ft, const double2* __restrict__ tab, double& cs,
                                           double& sn) {
-    const int idx = (int)((Ft + (1ull << 53)) >> 54);
-    const double th = (double)(long long)(Ft << 10) * (kTwoPi * 0x1p-74);
-    const double t2 = th * th;
-    const double cr = fma(fma(1.0 / 24.0, t2, -0.5), t2, 1.0);
-    const double sr = th * fma(fma(1.0 / 120.0, t2, -1.0 / 6.0), t2, 1.0);
-    const double2 t = tab[idx & (kTabA - 1)];
-    cs = fma(t.x, cr, -t.y * sr);
-    sn = fma(t.y, cr, t.x * sr);
+    const unsigned idx = (unsigned)((Ft + (1ull << (63 - kCisBits))) >> (64 - kCisBits));
+    const double th = (double)(long long)(Ft << kCisBits) * (kTwoPi * 0x1p-84);
+    const double hth = -0.5 * th;
+    const double2 t = __ldg(&tab[idx & ((1u << kCisBits) - 1u)]);
+    cs = fma(th, fma(t.x, hth, -t.y), t.x);
+    sn = fma(th, fma(t.y, hth, t.x), t.y);
 }
 
 // One bin of an expansion tile inside a single segment: the phase is the
@@ -505,23 +505,22 @@ __device__ __forceinline__ void fp64a_item(const Grid& g, const Tables& tb, cons
     flush_d(acc, (nflush == 0) ? pa.H + slot * 7 : pa.T + slot * 7, lane);
 }
 
-__device__ __forceinline__ void fill_table(double2* tab) {
-    for (int i = threadIdx.x; i < kTabA; i += blockDim.x) {
-        double s, c;
-        sincospi((double)i * (2.0 / kTabA), &s, &c);
-        tab[i] = make_double2(c, s);
-    }
-    __syncthreads();
+// The plan's exp(2 pi i j 2^-kCisBits) table (filled once per plan).
+__global__ void cis_table_kernel(double2* tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (1 << kCisBits)) return;
+    double s, c;
+    sincospi((double)i * 0x1p-19, &s, &c);   // 2 i / 2^20
+    tab[i] = make_double2(c, s);
 }
 
 // Grid form: CTA (span, group of 4 in-band particles of the span).
 __global__ void __launch_bounds__(kWarpsA * 32, 3)
 fp64a_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
                   const int* __restrict__ list, const int* __restrict__ cnt) {
-    __shared__ double2 tab[kTabA];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AnchorD* anc = reinterpret_cast<AnchorD*>(smem_raw);
-    fill_table(tab);
+    const double2* __restrict__ tab = pa.cis;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int span = blockIdx.x;
@@ -534,10 +533,9 @@ fp64a_main_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, 
 __global__ void __launch_bounds__(kWarpsA * 32, 3)
 fp64a_persistent_kernel(Grid g, Tables tb, const Particle* __restrict__ parts, int B, Segs sg, Partials pa,
                         const int* __restrict__ list, const int* __restrict__ sched, int nspans, int* ctl) {
-    __shared__ double2 tab[kTabA];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AnchorD* anc = reinterpret_cast<AnchorD*>(smem_raw) + (threadIdx.x >> 5) * 32;
-    fill_table(tab);
+    const double2* __restrict__ tab = pa.cis;
     const int lane = threadIdx.x & 31;
     while (true) {
         int item = 0;
@@ -570,6 +568,7 @@ int fp64a_span() { return kSpanA; }
 cudaError_t launch_fp64a_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
                               const Partials& pa, bool persistent, int* list, int* cnt, cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
+    if (!pa.cis) return cudaErrorInvalidValue;   // the plan's exp table is required
     const int nspans = pa.ntiles;
     const size_t smem = sizeof(AnchorD) * kWarpsA * 32;
     cudaError_t e = launch_span_lists(parts, B, sg, nspans, kSpanA, list, cnt, persistent, s);
@@ -585,6 +584,11 @@ cudaError_t launch_fp64a_main(const Grid& g, const Tables& t, const Particle* pa
     if ((e = allow_smem(fp64a_main_kernel, smem, 0)) != cudaSuccess) return e;
     dim3 grid((unsigned)nspans, (unsigned)((B + kWarpsA - 1) / kWarpsA));
     fp64a_main_kernel<<<grid, kWarpsA * 32, smem, s>>>(g, t, parts, B, sg, pa, list, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cis_table(double2* tab, cudaStream_t s) {
+    cis_table_kernel<<<(1 << kCisBits) / 256, 256, 0, s>>>(tab);
     return cudaGetLastError();
 }
 

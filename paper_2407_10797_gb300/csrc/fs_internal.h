@@ -14,6 +14,7 @@ constexpr int kTile = 2048;          // bins per (particle, tile) work item of t
 constexpr int kTileMin = 1024;       // smallest FP64 tile a launch variant uses (sizes the workspace)
 constexpr int kWarpsPerCta = 8;      // particles per CTA of the FP64 kernel
 constexpr int kNpMax = 4096;
+constexpr int kCisBits = 20;         // entries 2^kCisBits of the anchored FP64 kernels' exp table
 
 // Per-bin tables (structure of arrays, length n).
 struct Tables {
@@ -81,6 +82,7 @@ struct Partials {
     int nch = 1;
     int64_t ch_HT = 0, ch_S = 0;
     int nsum = 7;   // sums per slot: 7, or 8 for the response series (K12' of the complex responses)
+    const double2* cis = nullptr;   // the plan's exp(2 pi i j 2^-kCisBits) table (anchored FP64 kernels)
 };
 
 // Record an error message for fs_last_error() and return st.
@@ -123,6 +125,8 @@ int fp64a_span();
 cudaError_t launch_fp64a_main(const Grid& g, const Tables& t, const Particle* parts, int B, const Segs& sg,
                               const Partials& pa, bool persistent, int* list, int* cnt, cudaStream_t s);
 cudaError_t launch_extrinsic(int64_t n, const double* amp, double* ext, cudaStream_t s);
+// Fill the 2^kCisBits-entry table of exp(2 pi i j 2^-kCisBits) (double2: cos, sin).
+cudaError_t launch_cis_table(double2* tab, cudaStream_t s);
 // One bounded mbarrier wait that runs out (nothing arrives): sets kFlagTimeout in *flags.
 cudaError_t launch_wait_probe(int* flags, cudaStream_t s);
 // FP32 tables of nch channels (t32 [nch][n]) with one common power-of-two scale (exponent in *emax)
