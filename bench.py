@@ -74,12 +74,12 @@ def issue_peak_per_s():
     return 152 * 4 * 2.07e9
 # mode 6 is tier (6, 2) with the phase remainder in FP32: its FP64 operations
 # are those of mode 5 less d^2, d^4 and the remainder polynomial (7); mode 7
-# the same with antenna degree 5 (two FMAs fewer)
-FP64_TIER_FLOP = {1: 89.0, 2: FP64_DIRECT_FLOP, 3: 77.0, 4: 69.0, 5: 63.0, 6: 56.0, 7: 52.0}
+# the same with antenna degree 5 (two FMAs fewer), mode 8 with degree 4
+FP64_TIER_FLOP = {1: 89.0, 2: FP64_DIRECT_FLOP, 3: 77.0, 4: 69.0, 5: 63.0, 6: 56.0, 7: 52.0, 8: 48.0}
 
 
 def census_sum(counts_by_np):
-    return [int(sum(c[m] for c in counts_by_np.values())) for m in range(8)]
+    return [int(sum(c[m] for c in counts_by_np.values())) for m in range(9)]
 
 
 def flop_per_pbin(counts_by_np, table, direct):

@@ -21,7 +21,7 @@
 //     bits of the phase, rounded; 16 MB per plan, served by L2) times
 //     1 - theta^2/2 + i theta for the remaining angle |theta| <= pi 2^-20
 //     (dropped terms below 5e-18), folded into four FMAs.
-// A tile takes the lowest degree tier (NG, NR) = (5, 2), (6, 2), (7, 3), (8, 5) or
+// A tile takes the lowest degree tier (NG, NR) = (4, 2), (5, 2), (6, 2), (7, 3), (8, 5) or
 // (10, 7) whose dropped terms, summed over the tile at the anchor, stay below
 // 1e-13 cycle (phase) and 1e-15 (antenna); a tile whose d(alpha) quintic or
 // degree-12 series does not converge is evaluated bin by bin exactly as the
@@ -226,6 +226,7 @@ __device__ __noinline__ void make_anchor_d(const Grid& g, const Tables& tb, cons
     if (A.mode == 5 && tR[4] <= kRem32Max) A.mode = 6;
     // the same with antenna degree 5 (mode 7) when the antenna terms beyond degree 5 meet the budget
     if (A.mode == 6 && tG[6] <= 1e-15) A.mode = 7;
+    if (A.mode == 7 && tG[5] <= 1e-15) A.mode = 8;   // and antenna degree 4
     // the remainder is added to the fixed-point phase in units of 2^-48 cycle
     for (int k = 0; k <= kDeg - 4; k++) A.R[k] *= 0x1p48;
 }
@@ -433,7 +434,10 @@ __device__ __forceinline__ void fp64a_item(const Grid& g, const Tables& tb, cons
         const int lo = A.lo, hi = A.hi;
         if (cur < 0) cur = sv.seg(span_lo + lo);
         if (A.mode != 2) {
-            if (A.mode == 7)
+            if (A.mode == 8)
+                expansion_tile<4, 2, true>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane,
+                                           cur, nflush, trk, trk_nxt, acc);
+            else if (A.mode == 7)
                 expansion_tile<5, 2, true>(A, sv, span_lo, lo, hi, rot, dwr, dwi, Wt, tab, pa, slot, b, sg.Np, lane,
                                            cur, nflush, trk, trk_nxt, acc);
             else if (A.mode == 6)

@@ -116,7 +116,7 @@ cudaError_t launch_reduce(const Grid& g, const Particle* parts, int B, const Seg
 // The persistent kernels take every heavy item before the others, so that
 // the items with the most per-segment work do not start last.
 constexpr int kHeavyBounds = 16;
-constexpr int kCensusModes = 8;   // anchor modes counted by fs_plan_census
+constexpr int kCensusModes = 9;   // anchor modes counted by fs_plan_census
 inline int span_sched_ints(int nspans) { return 4 * nspans + 8; }
 cudaError_t launch_span_lists(const Particle* parts, int B, const Segs& sg, int nspans, int span_len, int* list,
                               int* cnt, bool offsets, cudaStream_t s);

@@ -375,13 +375,13 @@ class Plan:
         return v.value, [ms[i] for i in range(self.n_variants)]
 
     def census(self, params, Np: int, edges=None) -> list[int]:
-        """In-band particle*bins per anchor mode (fs_plan_census), 8 entries:
+        """In-band particle*bins per anchor mode (fs_plan_census), 9 entries:
         [unused, widest tier or FP32 body, bin-by-bin fallback, tier 3 or the
         mixed low-degree tier, tiers 4, 5 (narrowest), tier 5 with the FP32
-        phase remainder, unused]."""
+        phase remainder, the same with antenna degree 5, with degree 4]."""
         import torch
         self._edges_keep, e = _edges_arg(edges, Np, params.device, self.stream)
-        out = (C.c_int64 * 8)()
+        out = (C.c_int64 * 9)()
         _check(self._L.fs_plan_census(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
                                       e, int(Np), out))
         return [int(out[i]) for i in range(8)]

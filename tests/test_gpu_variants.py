@@ -209,11 +209,11 @@ def test_fp64_anchored_paper_workload(fst):
         if Np == 16:
             Fo, _ = O.fstat_batch(P[wide:wide + 1], m, d, psd, Np)
             assert rel_err(out[4][wide:wide + 1], Fo, Np) <= 1e-9
-            # the tiers that evaluate the phase remainder in FP32 (census modes 6 and 7, antenna degree 6
-            # and 5) carry most bins here, so the 1e-10 agreement above covers them
+            # the tiers that evaluate the phase remainder in FP32 (census modes 6, 7 and 8, antenna degree
+            # 6, 5 and 4) carry most bins here, so the 1e-10 agreement above covers them
             plan.set_variant(4)
             c = plan.census(Pt, Np)
-            assert c[6] + c[7] > 0.5 * sum(c), c
+            assert c[6] + c[7] + c[8] > 0.5 * sum(c), c
     plan.close()
 
 
@@ -254,10 +254,10 @@ def test_census_counts_every_in_band_bin(fst, small_case, mode):
         c = plan.census(Pt, Np)
         assert c[0] == 0 and sum(c) == inband, (Np, c)
         if mode == fst.FS_MIXED:
-            assert c[4] == 0 and c[5] == 0 and c[6] == 0 and c[7] == 0
+            assert c[4] == 0 and c[5] == 0 and c[6] == 0 and c[7] == 0 and c[8] == 0
     if mode == fst.FS_FP64:
         plan.set_variant(0)
-        assert plan.census(Pt, 16) == [0] * 8
+        assert plan.census(Pt, 16) == [0] * 9
     plan.close()
     w = S.small_workload()
     g = w.grid
