@@ -384,7 +384,7 @@ class Plan:
         out = (C.c_int64 * 9)()
         _check(self._L.fs_plan_census(self._h, _cuda_ptr(params.contiguous(), torch.float64), int(params.shape[0]),
                                       e, int(Np), out))
-        return [int(out[i]) for i in range(8)]
+        return [int(out[i]) for i in range(9)]
 
     def set_profiling(self, enable: bool):
         _check(self._L.fs_plan_set_profiling(self._h, 1 if enable else 0))
