@@ -328,20 +328,26 @@ def run_reference(args, world, rank):
     per_step = max(1.0, min(10.0, 120.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
         oracle_sample(g, P, psd, data, per_step / 2)
-    tot_pb, tot_s, thr, npart = 0, 0.0, 1, 0
-    for _ in range(args.steps):
-        pb, el, thr, npart = oracle_sample(g, P, psd, data, per_step)
+    # the steps cycle through the GPU arm's partition counts, one N_p per step
+    tot_pb, tot_s, thr, npart = 0, 0.0, 1, []
+    for i in range(args.steps):
+        pb, el, thr, n = oracle_sample(g, P, psd, data, per_step, Np=NP_LIST[i % len(NP_LIST)])
         tot_pb += pb
         tot_s += el
+        npart.append(n)
     value = tot_pb / tot_s
+    nps = [NP_LIST[i % len(NP_LIST)] for i in range(args.steps)]
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_bins": g.n, "B": w.B, "N_p": [16],
-                   "sample": "whole in-band particles of the batch, N_p = 16, about %.0f s per step" % per_step},
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_bins": g.n, "f_band_hz": [0.01, 0.05], "T_obs_s": g.T_obs, "B": w.B,
+                   "N_p": list(NP_LIST), "mode": "fp64", "runs_on": "host cores of rank 0 (the CPU oracle)",
+                   "sample": "whole in-band particles of the batch, about %.0f s per step; N_p by step %s"
+                             % (per_step, nps)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
-                         "sample": f"{npart} particles x all their in-band bins per step, N_p = 16"},
+                         "sample": f"{min(npart)}-{max(npart)} particles x all their in-band bins per step, "
+                                   f"N_p cycling through {list(NP_LIST)}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
