@@ -58,7 +58,7 @@ typedef enum {
     FS_ECUDA = -2,         /* a CUDA runtime call failed */
     FS_ENOMEM = -3,        /* device allocation failed */
     FS_ETIMEOUT = -4,      /* a bounded device-side wait expired */
-    FS_EUNSUPPORTED = -5   /* valid request this build does not implement */
+    FS_EUNSUPPORTED = -5   /* valid request the library does not implement */
 } fs_status;
 
 typedef enum {
