@@ -28,6 +28,9 @@
  *   extrinsic parameters     Appendix B, Eqs. (B1)-(B3)
  *   several TDI channels     Sec. II.A, Eq. (eq2): the log-likelihood sums over the
  *                            combinations I, so N and M of a segment are sums over channels
+ *   finite-arm TDI response  Sec. IV (a TDI combination is a sum of time-delayed single-arm
+ *                            responses): first-generation Michelsons built from the retarded
+ *                            link responses of the constellation frozen at t_f (or_tdi_response)
  *
  * Readings of points the paper leaves open:
  *   - PN coefficients alpha_k: non-spinning TaylorF2 through 2PN (k <= 4).
@@ -37,8 +40,8 @@
  *   - spacecraft orbits: Keplerian ellipses (semi-major axis 1 AU, eccentricity e,
  *     inclination sqrt(3) e, perihelia 120 degrees apart) expanded to first order in
  *     e -- the rigid equilateral constellation -- or, on request (model.ecc = e),
- *     to second order in e (Sec. IV); the rigid form is the default:
- *     (first-order-in-eccentricity orbits), long-wavelength Michelson X.
+ *     to second order in e (Sec. IV); the rigid form and the long-wavelength
+ *     Michelson X are the defaults.
  *   - constants -phi_c - pi/4 of Psi are carried by the amplitudes a_i.
  *   - segment outer edges at the first/last bin whose t(f_k) lies in [0, T];
  *     interior edges equal-width in frequency; a bin belongs to segment p iff
