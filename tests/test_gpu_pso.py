@@ -1,6 +1,5 @@
 """Device PSO step (Sec. III.A) against the CPU oracle, bit for bit, and the
 captured PSO iteration against eager launches."""
-import math
 
 import numpy as np
 import pytest

@@ -12,7 +12,6 @@ long-wavelength form misses it at order one.  The Doppler delay is switched
 off on both sides so that the arm transfer is tested alone.
 """
 import numpy as np
-import pytest
 
 from oracle import oracle as O
 
