@@ -8,8 +8,11 @@ H = h e_A with h(t) the exact inverse DFT of a tapered chirp, evaluated at
 each retarded time by the band-limited Fourier sum; the Michelson is
 y_12(t - L) + y_21(t) - y_13(t - L) - y_31(t); its FFT divided by -4 pi i f L
 must equal the oracle's A1 = T+ h0 (A2 = Tx h0).  At 52 mHz (pi f L = 1.4) the
-long-wavelength form misses it at order one.  The Doppler delay is switched
-off on both sides so that the arm transfer is tested alone.
+long-wavelength form misses it at order one.  On the orbits to second order
+in eccentricity the three vertex Michelsons, each arm delayed by its own
+length, combine into X, A, E and T, which the oracle's channels must match.
+The Doppler delay is switched off on both sides so that the arm transfer is
+tested alone.
 """
 import numpy as np
 
