@@ -569,7 +569,8 @@ FS_API fs_status fs_plan_get_variant(fs_plan* plan, int N_p, int global_edges, i
  * FS_FP64 anchored variants: the degree tiers (antenna polynomial degree,
  * phase-remainder degree) [5] (6, 6), [4] (7, 7), [3] (8, 9), [1] (10, 11),
  * [6] (6, 6) with the phase remainder (at most 6.7e-8 cycle) evaluated
- * in FP32, [7] the same with antenna degree 5 and [8] with degree 4; [0] unused.  All zero for the direct FS_FP64 variants (0-2), which have no
+ * in FP32, [7] the same with antenna degree 5 and [8] with degree 4; [0]
+ * unused.  All zero for the direct FS_FP64 variants (0-2), which have no
  * anchors.  Synchronous; must not be called while the plan's stream is being
  * captured.  For roofline accounting (the operation count per bin differs
  * between modes and tiers). */
