@@ -66,3 +66,28 @@ def test_noalloc_wrapper_checks_sizes_against_the_grid():
     with pytest.raises(ValueError):
         fstat.fstat_batch_noalloc(g, d, psd, P, 2, F=torch.zeros(4, dtype=torch.float64),
                                   F_part=torch.zeros(4, 3, dtype=torch.float64))
+
+
+def test_missing_library_is_an_error_not_a_fallback():
+    """Without the CUDA library the binding raises: there is no CPU path to
+    fall back to (run in a child process so the loaded library of this
+    session is not disturbed)."""
+    import os
+    import subprocess
+    import sys
+    code = ("import paper_2407_10797_gb300.build as b\n"
+            "b.LIB = '/nonexistent/libfs_gb300.so'\n"
+            "b.up_to_date = lambda: True\n"
+            "from paper_2407_10797_gb300 import fstat\n"
+            "for call in (lambda: fstat.load(build_if_missing=False),\n"
+            "             lambda: fstat.Plan(100, 0.01, 1e-6, 1e7)):\n"
+            "    try:\n"
+            "        call()\n"
+            "        print('loaded')\n"
+            "    except ImportError as e:\n"
+            "        print('refused', 'missing' in str(e))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.split() == ["refused", "True", "refused", "True"], r.stdout
