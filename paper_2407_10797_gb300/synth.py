@@ -179,8 +179,10 @@ class Prior:
 
 def draw_params(prior: Prior, B: int, seed: int, stream: int = STREAM_PARTICLES,
                 offset: int = 0) -> np.ndarray:
-    """B particles as a float64 array [B, 6] with columns PARAM_FIELDS."""
-    u = uniforms(seed, stream, 5 * B, offset=offset * 5 // 2).reshape(B, 5)
+    """B particles as a float64 array [B, 6] with columns PARAM_FIELDS; with
+    `offset` = o they are particles o .. o + B - 1 of one long draw."""
+    first = 5 * offset                      # index of the first uniform used
+    u = uniforms(seed, stream, 5 * B + 1, offset=first // 2)[first % 2:first % 2 + 5 * B].reshape(B, 5)
     out = np.empty((B, 6))
     out[:, 0] = prior.Mc_lo + (prior.Mc_hi - prior.Mc_lo) * u[:, 0]
     out[:, 1] = prior.tc_lo + (prior.tc_hi - prior.tc_lo) * u[:, 1]
