@@ -282,7 +282,8 @@ def fp64_peak_tflops() -> float:
 # ---------------------------------------------------------------------------
 def oracle_sample(g, P, psd, data, seconds: float, Np: int = 16):
     """Run the oracle on whole particles (all their in-band bins) until about
-    `seconds` of wall time; returns (pbins, elapsed s, threads, n particles)."""
+    `seconds` of wall time; returns (pbins, elapsed s, threads, n particles,
+    single-thread particle*bins/s of the calibration particle)."""
     from oracle import oracle as O
     m = O.OracleModel.from_grid(g)
     bands = np.array([O.band(p, m) for p in P])
@@ -295,6 +296,7 @@ def oracle_sample(g, P, psd, data, seconds: float, Np: int = 16):
     t0 = time.perf_counter()
     O.fstat_batch(P[i0:i0 + 1], m, data, psd, Np, nthreads=1)
     per_bin = (time.perf_counter() - t0) / max(nb[i0], 1)
+    one_core = 1.0 / per_bin if per_bin > 0 else None
     budget_bins = seconds * threads / per_bin
     pick, tot = [], 0
     for i in order[len(order) // 4:] + order[:len(order) // 4]:
@@ -307,7 +309,7 @@ def oracle_sample(g, P, psd, data, seconds: float, Np: int = 16):
     t0 = time.perf_counter()
     O.fstat_batch(P[pick], m, data, psd, Np, nthreads=threads)
     el = time.perf_counter() - t0
-    return int(nb[pick].sum()), el, threads, len(pick)
+    return int(nb[pick].sum()), el, threads, len(pick), one_core
 
 
 def run_reference(args, world, rank):
@@ -329,12 +331,13 @@ def run_reference(args, world, rank):
     for _ in range(args.warmup):
         oracle_sample(g, P, psd, data, per_step / 2)
     # the steps cycle through the GPU arm's partition counts, one N_p per step
-    tot_pb, tot_s, thr, npart = 0, 0.0, 1, []
+    tot_pb, tot_s, thr, npart, ones = 0, 0.0, 1, [], []
     for i in range(args.steps):
-        pb, el, thr, n = oracle_sample(g, P, psd, data, per_step, Np=NP_LIST[i % len(NP_LIST)])
+        pb, el, thr, n, one = oracle_sample(g, P, psd, data, per_step, Np=NP_LIST[i % len(NP_LIST)])
         tot_pb += pb
         tot_s += el
         npart.append(n)
+        ones.append(one)
     value = tot_pb / tot_s
     nps = [NP_LIST[i % len(NP_LIST)] for i in range(args.steps)]
     line = {
@@ -347,7 +350,9 @@ def run_reference(args, world, rank):
                              % (per_step, nps)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": f"{min(npart)}-{max(npart)} particles x all their in-band bins per step, "
-                                   f"N_p cycling through {list(NP_LIST)}"},
+                                   f"N_p cycling through {list(NP_LIST)}",
+                         "value_1core": float(np.median([o for o in ones if o])) if any(ones) else None,
+                         "sample_1core": "one particle of at least 2e4 in-band bins per step, one thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -735,10 +740,11 @@ def run_gpu(args, world, rank, local):
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             data_h = d_dev.cpu().numpy()
-            pb, el, thr, npart = oracle_sample(g, P0, psd, data_h, args.cpu_seconds)
+            pb, el, thr, npart, one = oracle_sample(g, P0, psd, data_h, args.cpu_seconds)
             cpu = {"value": pb / el, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{npart} particles x all their in-band bins ({pb} particle*bins), N_p = 16, "
-                             f"{el:.1f} s"}
+                             f"{el:.1f} s",
+                   "value_1core": one, "sample_1core": "one particle of at least 2e4 in-band bins, one thread"}
         # kernels per step: per N_p 2 state resets are torch copies; the graph
         # runs map, setup, rotation, fused, reduce, sum, fitness, pbest, move, advance
         out = {

@@ -33,6 +33,7 @@ def _check_line(line, world):
     assert line["config"]["workload"] and line["config"]["N_p"] == [256, 64, 16, 1]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert 0 < cb["value_1core"] <= 2.0 * cb["value"]
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
 
 
